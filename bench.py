@@ -1,0 +1,410 @@
+"""Benchmark: concrete data-race-freedom checking of a memory access protocol
+on the GPU, in access tuples checked per second.
+
+Workload (the one-protocol configuration): 1024 threads, two arrays of 2^20
+cells, loop nests of depth <= 3 with trip counts in 1..64, indices
+(a*tid + b*x + c*y + d) mod 2^20 with coefficients in [-8, 8], 1..6 syncs,
+reads and writes 50/50, about 10^7 access tuples; seeded synthetic input
+(generator seed 0).  A step is one complete check: count, scan, key emission,
+radix sort, segmented detection, witness -- every kernel, launched as one
+CUDA graph, with the protocol's device program already resident.  L2 is
+flushed (a 256 MiB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `--impl reference` times the oracle (the plain CPU
+checker used by the tests) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "access tuples checked/sec"
+UNIT = "tuples/s"
+WORKLOAD = ("one seeded protocol (generator seed 0): 1024 threads, 2 arrays x 2^20 cells, loop depth <= 3, "
+            "trip counts 1..64, affine indices mod 2^20 with coefficients in [-8,8], 1-6 syncs, rd/wr 50/50")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:6]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _pipeline_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_2203_12878_b300/csrc/cuda/pipeline.cu", "paper_2203_12878_b300/csrc/cuda/pipeline.cuh",
+                "paper_2203_12878_b300/csrc/devprog.h"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
+    None when there is none or the kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_config2_traffic.txt")
+    try:
+        vals = {}
+        for line in open(path):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("pipeline_hash") != _pipeline_hash():
+            return None
+        return float(vals[f"{kernel}_dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def workload():
+    from paper_2203_12878_b300 import protogen
+    return protogen.config2(0, "literal")
+
+
+def cpu_sample(p, threads=128):
+    """The same protocol restricted to its first `threads` threads."""
+    from paper_2203_12878_b300 import protogen
+    return protogen.Protocol(p.text, threads, p.cells, p.params, p.meta)
+
+
+def time_oracle(p, min_seconds):
+    from oracle import oracle
+    oracle.build()
+    runs, tuples, t0 = 0, 0, time.perf_counter()
+    while True:
+        r = oracle.check(p.text, p.nthreads, p.cells, p.params, 1)
+        tuples += r["tuples"]
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            return tuples / el, runs, el, r
+
+
+# ------------------------------------------------------------------ ours --
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2203_12878_b300 import drf
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    p = workload()
+    if world > 1:   # each rank checks its own seeded protocol of the same shape
+        from paper_2203_12878_b300 import protogen
+        p = protogen.config2(rank, "literal")
+    bc = drf.drf_protocol_compile(p.text)
+    ctx = drf.drf_ctx_create(dev, flags=drf.OPT_PROFILE_STAGES)
+    plan = drf.drf_plan_create(ctx, [bc], [(p.nthreads, p.cells, p.params)])
+    info = drf.drf_plan_info(plan)
+    n = info["tuples"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    stage_acc = {}
+    def step(timed, evs):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            drf.drf_plan_launch(plan, stream)
+            e.record(stream)
+        if timed:
+            evs.append((s, e))
+
+    for _ in range(args.warmup):
+        step(False, None)
+    torch.cuda.synchronize()
+    res = drf.result_dict(drf.drf_plan_results(plan)[0])
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    evs, per_stage = [], []
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(True, evs)
+            stream.synchronize()
+            per_stage.append(drf.drf_plan_stage_times(plan))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in evs]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # per-kernel device times (events inside the graph, on the launching stream)
+    kinds = {}
+    for st in per_stage:
+        for name, t in st:
+            kind = "radix" if name.startswith("radix") else name
+            kinds.setdefault(kind, []).append((name, t))
+    totals = {k: sum(t for _, t in v) / args.steps for k, v in kinds.items()}
+    dominant = max(totals, key=totals.get)
+    peak, peak_kind = _peaks()
+    # algorithmic bytes per launch: radix pass = read + write every key (16 B);
+    # emit = write every key (8 B); detect = read every key (8 B)
+    bytes_per = {"radix": 16 * n, "emit": 8 * n, "detect": 8 * n}
+    radix_launches = [t for _, t in kinds.get("radix", []) if t > 0.002]
+    dom_ms = (statistics.mean(radix_launches) if dominant == "radix" and radix_launches
+              else totals[dominant] / max(1, len(kinds[dominant]) // args.steps))
+    if dominant in bytes_per:
+        achieved = bytes_per[dominant] / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"k_{dominant}", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": _profiled_traffic(dominant), "launch_ms": round(dom_ms, 4),
+                "algorithmic_bytes_per_launch": bytes_per[dominant]}
+    else:
+        roof = {"bound": "alu", "kernel": f"k_{dominant}", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "launch_ms": round(dom_ms, 4)}
+
+    # end to end through the public API: host bytecode in, host result out
+    e2e_t = []
+    for i in range(max(3, min(args.steps, 10))):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = drf.drf_check(ctx, bc, p.nthreads, p.cells, p.params, stream)
+        e2e_t.append(time.perf_counter() - t1)
+        assert drf.result_dict(r) == res
+    h2d, d2h = drf.drf_ctx_transfer_bytes(ctx)
+    e2e_s = statistics.median(e2e_t)
+
+    extra = {}
+    if not args.quick and rank == 0:
+        extra["batched"] = bench_batched(ctx, args)
+        extra["served"] = bench_served(args)
+
+    out = None
+    if rank == 0:
+        cpu_v, cpu_runs, cpu_el, _ = time_oracle(cpu_sample(p), args.cpu_seconds)
+        out = {
+            "metric": METRIC, "value": world * n / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys, int32/int64 index arithmetic",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tuples_per_step": n, "sort_passes": info["sort_passes"],
+                       "sort_bits": info["sort_bits"], "verdict": res.get("verdict"),
+                       "l2": "flushed before every step (256 MiB write, outside the timed events)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "stages_ms": {k: round(v, 4) for k, v in sorted(totals.items())},
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the same protocol with its first 128 of 1024 threads, "
+                                       f"per-cell-record checker, {cpu_runs} runs in {cpu_el:.1f} s"},
+            "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_s * 1e3,
+                    "path": "drf_check: host bytecode -> validate/lower -> H2D -> all kernels -> D2H result"},
+            "gpu_launches": info["kernels_per_launch"] * args.steps,
+            "clocks": clk.summary(),
+            "wall_s_timed_region": wall,
+        }
+        out.update(extra)
+    drf.drf_plan_destroy(plan)
+    drf.drf_ctx_destroy(ctx)
+    return out
+
+
+def bench_batched(ctx, args):
+    """Protocols per second on the batched workload: 4096 seeded protocols in
+    one pipeline pass (protocol id in the key's top bits), as a CUDA graph."""
+    import torch
+    from paper_2203_12878_b300 import drf, protogen
+    ps = protogen.config4(master_seed=1, count=4096)
+    bcs = [drf.drf_protocol_compile(p.text) for p in ps]
+    plan = drf.drf_plan_create(ctx, bcs, [(p.nthreads, p.cells, p.params) for p in ps])
+    info = drf.drf_plan_info(plan)
+    stream = torch.cuda.Stream()
+    for _ in range(3):
+        drf.drf_plan_launch(plan, stream)
+    stream.synchronize()
+    reps = 10
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(reps):
+        drf.drf_plan_launch(plan, stream)
+    e.record(stream)
+    e.synchronize()
+    ms = s.elapsed_time(e) / reps
+    res = drf.drf_plan_results(plan)
+    racy = sum(1 for r in res if r.verdict == 1)
+    drf.drf_plan_destroy(plan)
+    # the plain path: one protocol per launch, same protocols (a sample)
+    sample = list(zip(bcs, ps))[:256]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for bc, p in sample:
+        drf.drf_check(ctx, bc, p.nthreads, p.cells, p.params, stream)
+    plain_s = (time.perf_counter() - t0) / len(sample)
+    return {"protocols": len(ps), "tuples": info["tuples"], "ms_per_batch": ms,
+            "protocols_per_s": len(ps) / (ms * 1e-3), "tuples_per_s": info["tuples"] / (ms * 1e-3),
+            "racy": racy, "plain_protocols_per_s": 1.0 / plain_s}
+
+
+def bench_served(args, rate=5000.0, seconds=2.0):
+    """Continuous-batching server under a Poisson stream: 90% batched-family
+    protocols, 10% one-protocol-family (scaled to 3x10^5 accesses)."""
+    import random
+    from paper_2203_12878_b300 import drf, protogen
+    arr = protogen.config5_arrivals(rate, seconds)
+    r = random.Random(9)
+    pool_b = [drf.drf_protocol_compile(p.text) for p in protogen.config4(master_seed=5, count=512)]
+    pool_b_meta = protogen.config4(master_seed=5, count=512)
+    singles = [protogen.config2(s, target=3e5) for s in range(4)]
+    pool_s = [(drf.drf_protocol_compile(p.text), p) for p in singles]
+    ctx = drf.drf_ctx_create(0)
+    drf.drf_server_start(ctx)
+    tickets = []
+    t0 = time.perf_counter()
+    for t, fam in arr:
+        while time.perf_counter() - t0 < t:
+            pass
+        if fam == "batch":
+            i = r.randrange(len(pool_b))
+            p = pool_b_meta[i]
+            tickets.append(drf.drf_server_submit(ctx, pool_b[i], p.nthreads, p.cells, p.params))
+        else:
+            bc, p = pool_s[r.randrange(len(pool_s))]
+            tickets.append(drf.drf_server_submit(ctx, bc, p.nthreads, p.cells, p.params))
+    lat = []
+    for tk in tickets:
+        got = drf.drf_server_poll(ctx, tk, 120_000_000)
+        lat.append(got[1] / 1e6)
+    wall = time.perf_counter() - t0
+    stats = drf.drf_server_stats(ctx)
+    drf.drf_server_stop(ctx)
+    drf.drf_ctx_destroy(ctx)
+    lat.sort()
+    return {"rate_req_s": rate, "requests": len(lat), "p50_ms": lat[len(lat) // 2],
+            "p99_ms": lat[min(len(lat) - 1, int(len(lat) * 0.99))], "throughput_req_s": len(lat) / wall,
+            "rounds": stats["rounds"], "max_round": stats["max_round"]}
+
+
+# ------------------------------------------------------------- reference --
+
+def run_reference(args):
+    p = cpu_sample(workload())
+    from oracle import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.check(p.text, p.nthreads, p.cells, p.params, 1)
+    times, n = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.check(p.text, p.nthreads, p.cells, p.params, 1)
+        times.append(time.perf_counter() - t0)
+        n = r["tuples"]
+    ms = statistics.mean(times) * 1e3
+    v = n / (ms * 1e-3)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "first 128 of 1024 threads", "tuples_per_step": n},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "the same protocol with its first 128 of 1024 threads"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--quick", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,291 @@
+/*
+ * drf.h -- C ABI of the B300 data-race-freedom checker for memory access
+ * protocols (MAPs).
+ *
+ * A memory access protocol (paper: "Provable GPU Data-Races in Static Race
+ * Detection", PLACES 2022, Fig. 1 "Syntax of MAPs") abstracts a GPU kernel
+ * into the array accesses each thread makes: reads rd A[n] and writes
+ * wr A[n] whose indices n are integer expressions of the thread id `tid`,
+ * loop variables and parameters, inside conditionals, unsynchronized loops
+ * (forU) and synchronized loops (forS) whose bodies may contain the barrier
+ * `sync`.  Every thread runs the protocol with its own tid (rule par, Fig. 3);
+ * the syncs a thread has executed so far number its current phase.  A
+ * protocol is data-race free (Definition 1, Sec. 3) iff no phase has two
+ * distinct threads i != j and a cell (array, index) that i writes and j reads
+ * or writes.  One behavioural type per array (Sec. 3): accesses to different
+ * arrays never conflict.
+ *
+ * This library decides that predicate exactly and concretely for a given
+ * thread count, array sizes and parameter values, on the GPU: every thread
+ * and every loop iteration is enumerated.  It returns the verdict and, for a
+ * racy protocol, the lexicographically smallest witness
+ * (phase, array, index, i, j) with i < j.
+ *
+ * Conventions for every function below:
+ *   - The return value is a status: DRF_OK (0) or a negative DRF_E_* code.
+ *     A result struct is meaningful only when its own `status` is DRF_OK.
+ *   - Pointers are host pointers unless a comment says "device".
+ *   - The caller owns every buffer it passes in; the library copies what it
+ *     needs before returning and never keeps a caller pointer.
+ *   - Streams are passed as `void*` holding a cudaStream_t; NULL means the
+ *     context's own stream.
+ *   - A context is not thread-safe: use one per host thread, or the server
+ *     functions (which are).
+ *
+ * Protocol text syntax (compiled by drf_protocol_compile):
+ *   program := decl* stmt*
+ *   decl    := "array" NAME ("," NAME)* ";"  |  "param" NAME ("," NAME)* ";"
+ *   stmt    := "skip" ";" | "sync" ";" | ("rd" | "wr") NAME "[" expr "]" ";"
+ *            | "if" "(" cond ")" "{" stmt* "}" ["else" "{" stmt* "}"]
+ *            | ("forU" | "forS") NAME "in" expr ".." expr "{" stmt* "}"
+ *   expr    := integer | "tid" | NAME | expr (+ - * / %) expr | "-" expr
+ *            | "min(" expr "," expr ")" | "max(" expr "," expr ")" | "(" expr ")"
+ *   cond    := "true" | "false" | expr (== = != < <= > >=) expr
+ *            | cond "&&" cond | cond "||" cond | "!" cond | "(" cond ")"
+ * Arrays and parameters are numbered in declaration order; their sizes and
+ * values come from drf_bounds at check time.  `forU x in lo .. hi` runs
+ * x = lo, ..., hi-1 (rules for-1 / for-2, Fig. 3).  `sync` and `forS` may only
+ * appear in the synchronized fragment: at top level or inside forS bodies,
+ * never inside forU or if bodies (Fig. 1).  A loop variable may not rebind a
+ * name in scope (rule t-for, Fig. 4).  `/` is floor division and `%` the
+ * Euclidean remainder (always in [0, |divisor|)).
+ */
+#ifndef DRF_H
+#define DRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status -- */
+#define DRF_OK                   0
+#define DRF_E_INVALID_ARG       -1   /* null pointer, count mismatch, bad option */
+#define DRF_E_PARSE             -2   /* protocol text does not parse */
+#define DRF_E_INVALID_BYTECODE  -3   /* malformed or truncated bytecode */
+#define DRF_E_UNBOUND_VAR       -4   /* a name that is not tid, a parameter or an enclosing loop variable (rule t-n) */
+#define DRF_E_UNKNOWN_ARRAY     -5   /* access to an undeclared array */
+#define DRF_E_REBIND            -6   /* loop variable rebinds a name in scope, or a duplicate declaration */
+#define DRF_E_SYNC_IN_UNSYNC    -7   /* sync or forS inside forU / if (Fig. 1) */
+#define DRF_E_OVERFLOW_RISK     -8   /* some intermediate value may leave int64 (interval analysis) */
+#define DRF_E_INDEX_OOB         -9   /* an evaluated index is outside [0, cells) */
+#define DRF_E_DIV_ZERO         -10   /* division or remainder by zero */
+#define DRF_E_KEY_TOO_WIDE     -11   /* phase+array+index+tid bits exceed the 64-bit access key */
+#define DRF_E_NOMEM            -12   /* device or host allocation failed */
+#define DRF_E_CUDA             -13   /* a CUDA runtime call failed */
+#define DRF_E_TIMEOUT          -14   /* a bounded device-side wait gave up, or a poll timed out */
+#define DRF_E_BUSY             -15   /* server queue full / server not running */
+#define DRF_E_LIMIT            -16   /* a size limit of this implementation (nesting, items, threads) */
+#define DRF_E_NOT_FOUND        -17   /* unknown server ticket */
+#define DRF_E_INTERNAL         -18   /* an internal consistency check failed */
+
+/* verdicts (drf_result.verdict) */
+#define DRF_VERDICT_DRF                 0
+#define DRF_VERDICT_RACY                1
+#define DRF_VERDICT_BARRIER_DIVERGENCE  2
+
+/* ------------------------------------------------------------------ types -- */
+typedef struct drf_ctx drf_ctx;      /* device buffers, streams, tuning state */
+typedef struct drf_plan drf_plan;    /* a fixed batch prepared for repeated launches */
+
+/* Bounds a protocol is checked under.  loc_cells[l] is the size of array l
+ * (declaration order, nlocs entries); params[k] the value of parameter k. */
+typedef struct {
+    uint32_t nthreads;           /* thread ids 0 .. nthreads-1 */
+    uint32_t nlocs;              /* must equal the protocol's array count */
+    const uint64_t *loc_cells;   /* host, nlocs entries */
+    uint32_t nparams;            /* must equal the protocol's parameter count */
+    const int64_t *params;       /* host, nparams entries */
+} drf_bounds;
+
+/* Result of one check.
+ *   status != DRF_OK: an evaluation error (DRF_E_INDEX_OOB, DRF_E_DIV_ZERO)
+ *     or a rejection; for evaluation errors err_tid is the smallest failing
+ *     thread and err_ordinal the number of accesses it completed first.
+ *   verdict RACY: the lexicographically smallest (phase, loc, index, tid_i,
+ *     tid_j) with tid_i < tid_j both accessing cell (loc, index) in `phase`
+ *     and at least one writing; i_writes / j_writes say which do.
+ *   verdict BARRIER_DIVERGENCE: threads ran different numbers of syncs;
+ *     div_tid is the smallest thread whose count differs from thread 0's.
+ *   tuples: dynamic accesses of all threads; phases: 1 + syncs of thread 0
+ *   (0 when nthreads is 0). */
+typedef struct {
+    int32_t status;
+    int32_t verdict;
+    uint32_t phase, loc;
+    uint64_t index;
+    uint32_t tid_i, tid_j;
+    uint32_t i_writes, j_writes;
+    uint32_t div_tid, sync_count_0, sync_count_div;
+    uint32_t phases;
+    uint64_t tuples;
+    uint32_t err_tid, reserved0;
+    uint64_t err_ordinal;
+} drf_result;
+
+/* Context options (all zero = defaults). */
+typedef struct {
+    uint32_t radix_bits;         /* radix digit width 4..8; 0 = autotuned */
+    uint32_t flags;              /* DRF_OPT_* */
+    uint64_t max_device_bytes;   /* cap on the context's device workspace; 0 = none */
+} drf_opts;
+
+#define DRF_OPT_PROFILE_STAGES 0x1u   /* record per-kernel CUDA events in plans */
+
+/* ------------------------------------------------------- library / errors -- */
+
+/* Library ABI version (this header: 1). */
+int drf_version(void);
+
+/* Static name of a status code ("DRF_E_INDEX_OOB", ...). */
+const char *drf_status_string(int status);
+
+/* --------------------------------------------------------------- contexts -- */
+
+/* Creates a context on CUDA device `device` (the library calls
+ * cudaSetDevice(device) on every entry that touches the GPU).  opts may be
+ * NULL.  *out receives the context; release it with drf_ctx_destroy. */
+int drf_ctx_create(int device, const drf_opts *opts, drf_ctx **out);
+
+/* Waits for the context's work, frees its device memory and streams. */
+void drf_ctx_destroy(drf_ctx *ctx);
+
+/* Message for the context's last failed call ("" if none).  Valid until the
+ * next call on the same context. */
+const char *drf_last_error(const drf_ctx *ctx);
+
+/* ------------------------------------------------------- protocol front-end */
+
+/* Compiles protocol text (syntax above; Fig. 1 with the synchronized fragment
+ * admitting accesses) into the library's portable bytecode.  On success
+ * *bytecode is a malloc'd buffer of *len bytes (free with drf_free).  On
+ * failure returns DRF_E_PARSE / _UNBOUND_VAR / _UNKNOWN_ARRAY / _REBIND /
+ * _SYNC_IN_UNSYNC and writes a message into err (errlen bytes, may be 0).
+ * Host only; no GPU needed. */
+int drf_protocol_compile(const char *text, uint8_t **bytecode, size_t *len,
+                         char *err, size_t errlen);
+
+/* Array and parameter counts a bytecode declares (validates it fully). */
+int drf_protocol_info(const uint8_t *bytecode, size_t len, uint32_t *nlocs, uint32_t *nparams);
+
+/* Static facts about a protocol under given bounds, from the host-side
+ * validation and interval analysis that every check runs first (no GPU):
+ * upper bounds on access tuples (all threads) and syncs (one thread), the
+ * number of work items each thread is cut into, whether 64-bit arithmetic is
+ * needed, and the sorted key bits.  Returns the status a check would return
+ * before touching the GPU (DRF_E_OVERFLOW_RISK, DRF_E_LIMIT, ...). */
+typedef struct {
+    uint64_t tuple_bound;
+    uint64_t sync_bound;
+    uint32_t items;
+    uint32_t wide_arithmetic;
+    uint32_t sort_bits;
+    uint32_t key_bits;
+} drf_analysis;
+
+int drf_protocol_analyze(const uint8_t *bytecode, size_t len, const drf_bounds *bounds, drf_analysis *out);
+
+/* Frees memory returned by this library. */
+void drf_free(void *p);
+
+/* ------------------------------------------------------------------ checks -- */
+
+/* Checks one protocol (bytecode of `len` bytes) under `bounds` and writes
+ * the result to *out.  Runs the whole device pipeline on `stream` -- count,
+ * scan, key emission, radix sort, segmented detection, witness -- and blocks
+ * until the result is on the host.  Returns out->status. */
+int drf_check(drf_ctx *ctx, const uint8_t *bytecode, size_t len,
+              const drf_bounds *bounds, drf_result *out, void *stream);
+
+/* Checks n protocols in one pass of the device pipeline (the protocol id
+ * rides in the top bits of every access key).  out has n entries; each
+ * protocol gets its own status, identical to what drf_check returns for it
+ * alone.  The call's return value is DRF_OK unless the batch as a whole
+ * failed (then no out entry is meaningful). */
+int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes,
+                    const size_t *lens, const drf_bounds *bounds, drf_result *out,
+                    void *stream);
+
+/* Bytes the context's last drf_check / drf_check_batch copied host->device
+ * (bytecode-derived device programs, items, schedules) and device->host
+ * (tuple count, control block, results). */
+int drf_ctx_transfer_bytes(const drf_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
+
+/* Diagnostics: copies the sorted access keys of the context's last
+ * drf_check / drf_check_batch into keys (device -> host, at most cap) and
+ * sets *n to their number.  layout[0..4] receive the key's field widths:
+ * tid, index, array, phase and protocol bits; a key is, from its most
+ * significant field down, protocol | phase | array | index | tid | mode
+ * (mode 1 = write). */
+int drf_debug_sorted_keys(drf_ctx *ctx, uint64_t *keys, uint64_t cap, uint64_t *n, uint32_t layout[5]);
+
+/* ------------------------------------------------------------------- plans -- */
+
+/* Prepares a fixed batch for repeated checks: validates and lowers every
+ * protocol, uploads the device programs, sizes every buffer (one sizing run
+ * of the count pass), and records the whole pipeline as a CUDA graph.  A
+ * protocol that fails validation or evaluation makes plan creation fail with
+ * its status (use drf_check_batch to get per-protocol statuses). */
+int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes,
+                    const size_t *lens, const drf_bounds *bounds, drf_plan **out);
+
+/* Enqueues one complete check of the plan's batch on `stream` (every kernel
+ * of the pipeline runs again; nothing is cached between launches) and
+ * returns without waiting.  Results stay on the device. */
+int drf_plan_launch(drf_plan *plan, void *stream);
+
+/* Waits for the plan's last launch and copies its n results to the host. */
+int drf_plan_results(drf_plan *plan, drf_result *out);
+
+/* Statistics of the plan: total access tuples, number of sort passes run,
+ * number of kernels one launch runs, sorted key bits. */
+int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
+                  uint32_t *kernels_per_launch, uint32_t *sort_bits);
+
+/* Per-stage device times (milliseconds) of the last launch, when the context
+ * was created with DRF_OPT_PROFILE_STAGES: names[i] (static strings) and
+ * ms[i] for i < *count (cap entries at most).  Waits for the launch. */
+int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap, int *count);
+
+/* Releases the plan's device memory and graph. */
+void drf_plan_destroy(drf_plan *plan);
+
+/* ----------------------------------------------------------------- server -- */
+
+/* Continuous-batching check server on the context.  Requests submitted from
+ * any host thread are admitted into device rounds as device memory (counted
+ * from each request's bound on its access tuples) and batch slots allow;
+ * up to two rounds overlap on the GPU.  Each result equals drf_check's. */
+typedef struct {
+    uint64_t max_round_tuples;   /* tuple budget of one round; 0 = default */
+    uint32_t max_round_protocols;/* protocols per round; 0 = default */
+    uint32_t max_queue;          /* pending requests before submit returns BUSY; 0 = default */
+} drf_server_opts;
+
+int drf_server_start(drf_ctx *ctx, const drf_server_opts *opts);
+
+/* Queues one check (bytecode and bounds are copied).  *ticket identifies it. */
+int drf_server_submit(drf_ctx *ctx, const uint8_t *bytecode, size_t len,
+                      const drf_bounds *bounds, uint64_t *ticket);
+
+/* Waits up to timeout_us microseconds (negative: forever) for a ticket's
+ * result.  DRF_E_TIMEOUT if not done yet; the ticket stays valid.  Once a
+ * result has been returned the ticket is released.  latency_ns (may be NULL)
+ * receives the time from submit to completion. */
+int drf_server_poll(drf_ctx *ctx, uint64_t ticket, drf_result *out, int64_t timeout_us,
+                    uint64_t *latency_ns);
+
+/* Counters of the running server: rounds launched, requests completed and
+ * the largest number of protocols one round held. */
+int drf_server_stats(drf_ctx *ctx, uint64_t *rounds, uint64_t *completed, uint32_t *max_round);
+
+/* Drains in-flight work and stops the server thread. */
+int drf_server_stop(drf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DRF_H */

@@ -1,0 +1,71 @@
+// Device pipeline of the checker: argument block and host-side launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../devprog.h"
+
+namespace drf {
+
+// Everything the kernels of one launch touch.  Device pointers unless noted.
+struct BatchArgs {
+    // device programs of the batch
+    const Insn *insns;
+    const uint64_t *xcode;
+    const ItemDesc *items;
+    const DevProto *protos;
+    const uint64_t *cells;
+    const WarpItem *witems;
+    uint32_t nwitems;
+    uint32_t nprotos;
+    uint64_t ncols;                  // sum of thread counts (per-thread arrays)
+    // per (item, thread)
+    uint32_t *cnt;                   // accesses
+    uint32_t *syn;                   // syncs
+    uint32_t *phs;                   // phase at item start (exclusive scan of syn)
+    unsigned long long *erro;        // (local ordinal << 8) | error code
+    // per (protocol, thread)
+    uint32_t *totsyn;
+    // per warp-item
+    uint32_t *wcnt;
+    unsigned long long *wbase;
+    unsigned long long *blocksum;    // per 4096 warp-items
+    uint32_t nwblocks;
+    // keys
+    unsigned long long *keys[2];
+    uint64_t nkeys;                  // tuples this launch must produce (plan size)
+    unsigned long long *hist;        // [kMaxPasses][kRadixBins]
+    unsigned long long *status;      // [passes][ntiles][kRadixBins] look-back words
+    uint32_t ntiles;
+    // per protocol
+    unsigned long long *err_key;     // min (tid << 32 | item) with an evaluation error
+    uint32_t *div_tid;               // min tid whose sync count differs from thread 0's
+    unsigned long long *best_pos;    // min sorted position of a racy segment
+    unsigned long long *ptuples;
+    DevResult *results;
+    Control *ctrl;
+    uint32_t *epoch;                 // persists across launches
+    KeyLayout L;
+};
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;     // 4096 keys
+constexpr int kDetectThreads = 256;
+constexpr int kDetectItems = 8;
+constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 2048 keys
+constexpr int kScanThreads = 256;
+constexpr int kWScanPerBlock = 4096;                        // warp-items per scan block
+
+inline uint32_t radix_tiles(uint64_t n) { return (uint32_t)((n + kRadixTile - 1) / kRadixTile); }
+
+// Stage launchers (all asynchronous on `s`).  Each returns cudaGetLastError().
+// When ev is non-null, an event is recorded before the first kernel of
+// launch_front and after every kernel; *nev counts the events recorded.
+cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev);  // init, count, scan
+cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev);   // emit, radix, detect, finalize
+
+// Names of the stages whose boundaries launch_front / launch_back record.
+int stage_names(const char **names, int cap, uint32_t passes);
+
+}  // namespace drf

@@ -1,0 +1,416 @@
+// The C ABI of include/drf.h.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "engine.h"
+#include "server.h"
+
+using namespace drf;
+
+namespace {
+
+int fail(drf_ctx *ctx, int status, const std::string &msg)
+{
+    if (ctx) ctx->last_error = msg;
+    return status;
+}
+
+int cuda_fail(drf_ctx *ctx, cudaError_t e)
+{
+    cudaGetLastError();
+    return fail(ctx, S_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+}
+
+cudaStream_t pick(drf_ctx *ctx, void *stream) { return stream ? (cudaStream_t)stream : ctx->stream; }
+
+Error prepare_one(const uint8_t *bc, size_t len, const drf_bounds *b, const PrepareOpts &po, Prepared &out)
+{
+    if (!bc || !b) return Error::make(S_INVALID_ARG, "null bytecode or bounds");
+    return prepare(bc, len, b->nthreads, b->nlocs, b->loc_cells, b->nparams, b->params, po, out);
+}
+
+void error_result(int status, drf_result *out)
+{
+    std::memset(out, 0, sizeof *out);
+    out->status = status;
+    out->verdict = -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int drf_version(void) { return 1; }
+
+const char *drf_status_string(int s)
+{
+    switch (s) {
+    case DRF_OK: return "DRF_OK";
+    case DRF_E_INVALID_ARG: return "DRF_E_INVALID_ARG";
+    case DRF_E_PARSE: return "DRF_E_PARSE";
+    case DRF_E_INVALID_BYTECODE: return "DRF_E_INVALID_BYTECODE";
+    case DRF_E_UNBOUND_VAR: return "DRF_E_UNBOUND_VAR";
+    case DRF_E_UNKNOWN_ARRAY: return "DRF_E_UNKNOWN_ARRAY";
+    case DRF_E_REBIND: return "DRF_E_REBIND";
+    case DRF_E_SYNC_IN_UNSYNC: return "DRF_E_SYNC_IN_UNSYNC";
+    case DRF_E_OVERFLOW_RISK: return "DRF_E_OVERFLOW_RISK";
+    case DRF_E_INDEX_OOB: return "DRF_E_INDEX_OOB";
+    case DRF_E_DIV_ZERO: return "DRF_E_DIV_ZERO";
+    case DRF_E_KEY_TOO_WIDE: return "DRF_E_KEY_TOO_WIDE";
+    case DRF_E_NOMEM: return "DRF_E_NOMEM";
+    case DRF_E_CUDA: return "DRF_E_CUDA";
+    case DRF_E_TIMEOUT: return "DRF_E_TIMEOUT";
+    case DRF_E_BUSY: return "DRF_E_BUSY";
+    case DRF_E_LIMIT: return "DRF_E_LIMIT";
+    case DRF_E_NOT_FOUND: return "DRF_E_NOT_FOUND";
+    case DRF_E_INTERNAL: return "DRF_E_INTERNAL";
+    default: return "DRF_E_UNKNOWN";
+    }
+}
+
+int drf_ctx_create(int device, const drf_opts *opts, drf_ctx **out)
+{
+    if (!out) return DRF_E_INVALID_ARG;
+    *out = nullptr;
+    if (opts && opts->radix_bits && (opts->radix_bits < 4 || opts->radix_bits > 8)) return DRF_E_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { cudaGetLastError(); return DRF_E_CUDA; }
+    drf_ctx *ctx = new (std::nothrow) drf_ctx;
+    if (!ctx) return DRF_E_NOMEM;
+    ctx->device = device;
+    if (opts) ctx->opts = *opts;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0) ctx->sms = sms;
+    if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&ctx->pinned_ctrl, sizeof(Control))) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return DRF_E_CUDA;
+    }
+    *out = ctx;
+    return DRF_OK;
+}
+
+void drf_ctx_destroy(drf_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->server) drf_server_stop(ctx);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFreeHost(ctx->pinned_ctrl);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;                       // frees the workspace's device buffers
+}
+
+const char *drf_last_error(const drf_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int drf_protocol_compile(const char *text, uint8_t **bytecode, size_t *len, char *err, size_t errlen)
+{
+    if (err && errlen) err[0] = 0;
+    if (!text || !bytecode || !len) return DRF_E_INVALID_ARG;
+    *bytecode = nullptr;
+    *len = 0;
+    Protocol p;
+    Error e = parse_text(text, p);
+    if (!e.ok()) {
+        if (err && errlen) { std::strncpy(err, e.message.c_str(), errlen - 1); err[errlen - 1] = 0; }
+        return e.status;
+    }
+    std::vector<uint8_t> bc = encode_bytecode(p);
+    uint8_t *buf = (uint8_t *)std::malloc(bc.size());
+    if (!buf) return DRF_E_NOMEM;
+    std::memcpy(buf, bc.data(), bc.size());
+    *bytecode = buf;
+    *len = bc.size();
+    return DRF_OK;
+}
+
+int drf_protocol_info(const uint8_t *bytecode, size_t len, uint32_t *nlocs, uint32_t *nparams)
+{
+    Protocol p;
+    Error e = decode_bytecode(bytecode, len, p);
+    if (!e.ok()) return e.status;
+    if (nlocs) *nlocs = p.narrays;
+    if (nparams) *nparams = p.nparams;
+    return DRF_OK;
+}
+
+int drf_protocol_analyze(const uint8_t *bytecode, size_t len, const drf_bounds *bounds, drf_analysis *out)
+{
+    if (!out) return DRF_E_INVALID_ARG;
+    std::memset(out, 0, sizeof *out);
+    Prepared p;
+    Error e = prepare_one(bytecode, len, bounds, PrepareOpts{}, p);
+    if (!e.ok()) return e.status;
+    BatchHost bh;
+    e = pack_batch({&p}, bh);
+    out->tuple_bound = p.tuple_bound();
+    out->sync_bound = p.max_syncs;
+    out->items = (uint32_t)p.items.size();
+    out->wide_arithmetic = p.wide ? 1 : 0;
+    out->sort_bits = bh.L.sort_bits;
+    out->key_bits = bh.L.sort_lo + bh.L.sort_bits;
+    return e.status;
+}
+
+void drf_free(void *p) { std::free(p); }
+
+int drf_check(drf_ctx *ctx, const uint8_t *bytecode, size_t len, const drf_bounds *bounds, drf_result *out,
+              void *stream)
+{
+    if (!ctx || !out) return DRF_E_INVALID_ARG;
+    const uint8_t *const bcs[1] = {bytecode};
+    const size_t lens[1] = {len};
+    int st = drf_check_batch(ctx, 1, bcs, lens, bounds, out, stream);
+    return st ? st : out->status;
+}
+
+int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const size_t *lens,
+                    const drf_bounds *bounds, drf_result *out, void *stream)
+{
+    if (!ctx || !out || (n && (!bytecodes || !lens || !bounds))) return DRF_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaError_t ce = cudaSetDevice(ctx->device);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce);
+    ctx->last_error.clear();
+    PrepareOpts po;
+    po.desired_warp_items = (uint64_t)ctx->sms * 128;
+    std::vector<Prepared> preps(n);
+    std::vector<const Prepared *> valid;
+    std::vector<uint32_t> where;
+    for (uint32_t i = 0; i < n; i++) {
+        Error e = prepare_one(bytecodes[i], lens[i], &bounds[i], po, preps[i]);
+        if (!e.ok()) {
+            error_result(e.status, &out[i]);
+            if (n == 1) ctx->last_error = e.message;
+            continue;
+        }
+        valid.push_back(&preps[i]);
+        where.push_back(i);
+    }
+    if (valid.empty()) return DRF_OK;
+    cudaStream_t s = pick(ctx, stream);
+    BatchHost bh;
+    Error e = pack_batch(valid, bh);
+    if (e.status == S_KEY_TOO_WIDE && valid.size() > 1) {
+        // the combined key does not fit: check the protocols one by one
+        for (size_t j = 0; j < valid.size(); j++) {
+            Error ej = pack_batch({valid[j]}, bh);
+            if (!ej.ok()) { error_result(ej.status, &out[where[j]]); continue; }
+            std::vector<DevResult> r;
+            int st = run_batch(ctx, bh, s, r);
+            if (st) return st;
+            to_public(r[0], &out[where[j]]);
+        }
+        return DRF_OK;
+    }
+    if (!e.ok()) {
+        for (uint32_t i : where) error_result(e.status, &out[i]);
+        if (n == 1) ctx->last_error = e.message;
+        return DRF_OK;
+    }
+    std::vector<DevResult> r;
+    int st = run_batch(ctx, bh, s, r);
+    if (st) return st;
+    for (size_t j = 0; j < where.size(); j++) to_public(r[j], &out[where[j]]);
+    return DRF_OK;
+}
+
+int drf_ctx_transfer_bytes(const drf_ctx *ctx, uint64_t *h2d, uint64_t *d2h)
+{
+    if (!ctx) return DRF_E_INVALID_ARG;
+    if (h2d) *h2d = ctx->work.h2d_bytes;
+    if (d2h) *d2h = ctx->work.d2h_bytes;
+    return DRF_OK;
+}
+
+int drf_debug_sorted_keys(drf_ctx *ctx, uint64_t *keys, uint64_t cap, uint64_t *n, uint32_t layout[5])
+{
+    if (!ctx || !n) return DRF_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaError_t ce = cudaSetDevice(ctx->device);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce);
+    const BatchArgs &a = ctx->work.args;
+    *n = a.nkeys;
+    if (layout) {
+        layout[0] = a.L.tid_bits; layout[1] = a.L.idx_bits; layout[2] = a.L.loc_bits;
+        layout[3] = a.L.phase_bits; layout[4] = a.L.proto_bits;
+    }
+    if (!keys || !cap || !a.nkeys) return DRF_OK;
+    // the sorted keys sit in the buffer the last non-trivial pass wrote
+    std::vector<unsigned long long> hist((size_t)kMaxPasses * kRadixBins);
+    if ((ce = cudaMemcpy(hist.data(), a.hist, hist.size() * 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(ctx, ce);
+    int passes = 0;
+    for (uint32_t q = 0; q < a.L.passes; q++) {
+        int nz = 0;
+        for (int d = 0; d < kRadixBins; d++) nz += hist[(size_t)q * kRadixBins + d] != 0;
+        passes += nz > 1;
+    }
+    uint64_t m = std::min<uint64_t>(cap, a.nkeys);
+    if ((ce = cudaMemcpy(keys, a.keys[passes & 1], m * 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(ctx, ce);
+    return DRF_OK;
+}
+
+// ------------------------------------------------------------------- plans
+
+int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const size_t *lens,
+                    const drf_bounds *bounds, drf_plan **out)
+{
+    if (!ctx || !out || !n || !bytecodes || !lens || !bounds) return DRF_E_INVALID_ARG;
+    *out = nullptr;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaError_t ce = cudaSetDevice(ctx->device);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce);
+    PrepareOpts po;
+    po.desired_warp_items = (uint64_t)ctx->sms * 128;
+    std::vector<Prepared> preps(n);
+    std::vector<const Prepared *> ptrs;
+    for (uint32_t i = 0; i < n; i++) {
+        Error e = prepare_one(bytecodes[i], lens[i], &bounds[i], po, preps[i]);
+        if (!e.ok()) return fail(ctx, e.status, "protocol " + std::to_string(i) + ": " + e.message);
+        ptrs.push_back(&preps[i]);
+    }
+    drf_plan *plan = new (std::nothrow) drf_plan;
+    if (!plan) return DRF_E_NOMEM;
+    plan->ctx = ctx;
+    plan->n = n;
+    Error e = pack_batch(ptrs, plan->host);
+    if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
+    cudaStream_t s = ctx->stream;
+    DeviceBatch &d = plan->dev;
+    d.limit = ctx->opts.max_device_bytes;
+    e = d.load(plan->host, s);
+    if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
+    // sizing run: the count pass gives the number of access keys
+    if ((ce = launch_front(d.args, s, ctx->sms, nullptr, nullptr)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(ctx->pinned_ctrl, d.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
+        delete plan;
+        return cuda_fail(ctx, ce);
+    }
+    plan->tuples = ctx->pinned_ctrl->total;
+    e = d.size_keys(plan->tuples, s);
+    if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
+    d.status_launches++;
+    // complete the sizing run so evaluation errors surface now
+    std::vector<DevResult> res(n);
+    if ((ce = launch_back(d.args, s, ctx->sms, nullptr, nullptr)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(res.data(), d.args.results, n * sizeof(DevResult), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
+        delete plan;
+        return cuda_fail(ctx, ce);
+    }
+    for (uint32_t i = 0; i < n; i++)
+        if (res[i].status) { delete plan; return fail(ctx, res[i].status, "protocol " + std::to_string(i) + " fails to evaluate"); }
+    // record the whole pipeline as a graph (with timing events when asked)
+    plan->profiled = (ctx->opts.flags & DRF_OPT_PROFILE_STAGES) != 0;
+    if (plan->profiled) {
+        plan->events.resize(4 + kMaxPasses + 3);
+        for (auto &ev : plan->events) cudaEventCreate(&ev);
+    }
+    cudaEvent_t *evp = plan->profiled ? plan->events.data() : nullptr;
+    int nev = 0;
+    if ((ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        drf_plan_destroy(plan);
+        return cuda_fail(ctx, ce);
+    }
+    cudaError_t e1 = launch_front(d.args, s, ctx->sms, evp, &nev);
+    cudaError_t e2 = launch_back(d.args, s, ctx->sms, evp, &nev);
+    ce = cudaStreamEndCapture(s, &plan->graph);
+    plan->nevents = nev;
+    if (e1 != cudaSuccess || e2 != cudaSuccess || ce != cudaSuccess ||
+        (ce = cudaGraphInstantiate(&plan->exec, plan->graph, 0)) != cudaSuccess) {
+        drf_plan_destroy(plan);
+        return cuda_fail(ctx, ce != cudaSuccess ? ce : (e1 != cudaSuccess ? e1 : e2));
+    }
+    *out = plan;
+    return DRF_OK;
+}
+
+int drf_plan_launch(drf_plan *plan, void *stream)
+{
+    if (!plan || !plan->exec) return DRF_E_INVALID_ARG;
+    drf_ctx *ctx = plan->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = pick(ctx, stream);
+    DeviceBatch &d = plan->dev;
+    if (++d.status_launches >= (1ull << 21)) {
+        if (cudaMemsetAsync(d.status.p, 0, d.status.cap, s) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError());
+        d.status_launches = 0;
+    }
+    cudaError_t e = cudaGraphLaunch(plan->exec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    plan->last_stream = s;
+    return DRF_OK;
+}
+
+int drf_plan_results(drf_plan *plan, drf_result *out)
+{
+    if (!plan || !out) return DRF_E_INVALID_ARG;
+    drf_ctx *ctx = plan->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = plan->last_stream ? plan->last_stream : ctx->stream;
+    std::vector<DevResult> res(plan->n);
+    Control c{};
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(res.data(), plan->dev.args.results, plan->n * sizeof(DevResult), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&c, plan->dev.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(ctx, e);
+    if (c.flags & CF_LOOKBACK_TIMEOUT) return fail(ctx, DRF_E_TIMEOUT, "radix look-back gave up waiting");
+    if (c.flags) return fail(ctx, DRF_E_INTERNAL, "device consistency flags " + std::to_string(c.flags));
+    for (uint32_t i = 0; i < plan->n; i++) to_public(res[i], &out[i]);
+    return DRF_OK;
+}
+
+int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes, uint32_t *kernels_per_launch,
+                  uint32_t *sort_bits)
+{
+    if (!plan) return DRF_E_INVALID_ARG;
+    if (tuples) *tuples = plan->tuples;
+    if (sort_passes) *sort_passes = plan->host.L.passes;
+    if (kernels_per_launch) *kernels_per_launch = 6 + plan->host.L.passes;
+    if (sort_bits) *sort_bits = plan->host.L.sort_bits;
+    return DRF_OK;
+}
+
+int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap, int *count)
+{
+    if (!plan || !count) return DRF_E_INVALID_ARG;
+    *count = 0;
+    if (!plan->profiled) return fail(plan->ctx, DRF_E_INVALID_ARG, "context created without DRF_OPT_PROFILE_STAGES");
+    cudaSetDevice(plan->ctx->device);
+    cudaStream_t s = plan->last_stream ? plan->last_stream : plan->ctx->stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(plan->ctx, e);
+    const char *all[4 + kMaxPasses + 2];
+    int nn = stage_names(all, 4 + kMaxPasses + 2, plan->host.L.passes);
+    int n = std::min(nn, plan->nevents - 1);
+    for (int i = 0; i < n && i < cap; i++) {
+        float t = 0;
+        if ((e = cudaEventElapsedTime(&t, plan->events[i], plan->events[i + 1])) != cudaSuccess) return cuda_fail(plan->ctx, e);
+        if (names) names[i] = all[i];
+        if (ms) ms[i] = t;
+        (*count)++;
+    }
+    return DRF_OK;
+}
+
+void drf_plan_destroy(drf_plan *plan)
+{
+    if (!plan) return;
+    cudaSetDevice(plan->ctx->device);
+    if (plan->last_stream) cudaStreamSynchronize(plan->last_stream);
+    cudaStreamSynchronize(plan->ctx->stream);
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    for (auto ev : plan->events) cudaEventDestroy(ev);
+    delete plan;
+}
+
+}  // extern "C"

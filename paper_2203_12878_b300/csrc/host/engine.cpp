@@ -1,0 +1,271 @@
+// Batch packing, device buffers and the two-phase pipeline run.
+#include "engine.h"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+namespace drf {
+
+bool ensure(DevBuf &b, size_t bytes, size_t *in_use, uint64_t limit)
+{
+    if (b.cap >= bytes) return true;
+    size_t want = std::max(bytes, b.cap + b.cap / 4);       // grow by at least 25%
+    if (limit && *in_use - b.cap + want > limit) want = bytes;
+    if (limit && *in_use - b.cap + want > limit) return false;
+    release(b, in_use);
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return false;
+    }
+    b.cap = want;
+    *in_use += want;
+    return true;
+}
+
+void release(DevBuf &b, size_t *in_use)
+{
+    if (b.p) {
+        cudaFree(b.p);
+        *in_use -= b.cap;
+    }
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
+{
+    out = BatchHost{};
+    KeyLayout L{};
+    const uint32_t n = (uint32_t)ps.size();
+    L.proto_bits = n > 1 ? bits_for(n - 1) : 0;
+    for (const Prepared *p : ps) {
+        L.phase_bits = std::max(L.phase_bits, bits_for(p->max_syncs));
+        L.loc_bits = std::max(L.loc_bits, bits_for(p->narrays ? p->narrays - 1 : 0));
+        for (uint64_t c : p->cells) L.idx_bits = std::max(L.idx_bits, bits_for(c ? c - 1 : 0));
+        L.tid_bits = std::max(L.tid_bits, bits_for(p->nthreads ? p->nthreads - 1 : 0));
+    }
+    L.sort_lo = L.tid_bits + 1;
+    L.sort_bits = L.proto_bits + L.phase_bits + L.loc_bits + L.idx_bits;
+    if (L.sort_lo + L.sort_bits > 64)
+        return Error::make(S_KEY_TOO_WIDE, "phase, array, index and thread fields need " +
+                                               std::to_string(L.sort_lo + L.sort_bits) + " bits");
+    L.passes = (L.sort_bits + kRadixBits - 1) / kRadixBits;
+    out.L = L;
+
+    struct W { WarpItem wi; uint64_t steps; };
+    std::vector<W> ws;
+    for (uint32_t i = 0; i < n; i++) {
+        const Prepared &p = *ps[i];
+        DevProto d{};
+        d.insn_off = (uint32_t)out.insns.size();
+        d.xcode_off = (uint32_t)out.xcode.size();
+        d.item_off = (uint32_t)out.items.size();
+        d.nitems = (uint32_t)p.items.size();
+        d.nthreads = p.nthreads;
+        d.wide = p.wide ? 1 : 0;
+        d.nlocs = p.narrays;
+        d.cells_off = (uint32_t)out.cells.size();
+        d.lane_off = out.lanes;
+        d.tid_off = out.ncols;
+        out.insns.insert(out.insns.end(), p.insns.begin(), p.insns.end());
+        out.xcode.insert(out.xcode.end(), p.xcode.begin(), p.xcode.end());
+        out.items.insert(out.items.end(), p.items.begin(), p.items.end());
+        out.cells.insert(out.cells.end(), p.cells.begin(), p.cells.end());
+        out.protos.push_back(d);
+        out.lanes += (uint64_t)d.nitems * p.nthreads;
+        out.ncols += p.nthreads;
+        out.tuple_bound += p.tuple_bound();
+        uint32_t groups = (p.nthreads + 31) / 32;
+        for (uint32_t k = 0; k < d.nitems; k++)
+            for (uint32_t g = 0; g < groups; g++) ws.push_back(W{WarpItem{i, k, g}, p.item_steps[k]});
+    }
+    if (out.insns.size() >= (1ull << 31) || out.xcode.size() >= (1ull << 31) || out.items.size() >= (1ull << 31) ||
+        ws.size() >= (1ull << 31) || out.lanes >= (1ull << 31))
+        return Error::make(S_LIMIT, "batch too large");
+    // longest items first, so that the grid-stride loops end together
+    std::stable_sort(ws.begin(), ws.end(), [](const W &x, const W &y) { return x.steps > y.steps; });
+    out.witems.reserve(ws.size());
+    for (auto &w : ws) out.witems.push_back(w.wi);
+    return Error{};
+}
+
+DeviceBatch::~DeviceBatch()
+{
+    DevBuf *all[] = {&insns, &xcode, &items, &protos, &cells, &witems, &cnt, &syn, &phs, &erro, &totsyn,
+                     &wcnt, &wbase, &blocksum, &keys0, &keys1, &hist, &status, &err_key, &div_tid,
+                     &best_pos, &ptuples, &results, &ctrl, &epoch};
+    for (DevBuf *b : all) release(*b, &in_use);
+}
+
+namespace {
+
+template <typename T>
+bool upload(DevBuf &b, const std::vector<T> &v, size_t *in_use, uint64_t limit, cudaStream_t s, uint64_t *bytes_out)
+{
+    *bytes_out += v.size() * sizeof(T);
+    size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
+    if (!ensure(b, bytes, in_use, limit)) return false;
+    if (!v.empty() && cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return false;
+    return true;
+}
+
+}  // namespace
+
+Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
+{
+    const uint64_t np = b.protos.size();
+    const uint64_t nw = b.witems.size();
+    const uint32_t nwblocks = (uint32_t)std::max<uint64_t>(1, (nw + kWScanPerBlock - 1) / kWScanPerBlock);
+    h2d_bytes = 0;
+    d2h_bytes = 0;
+    uint64_t *hb = &h2d_bytes;
+    bool ok = upload(insns, b.insns, &in_use, limit, s, hb) && upload(xcode, b.xcode, &in_use, limit, s, hb) &&
+              upload(items, b.items, &in_use, limit, s, hb) && upload(protos, b.protos, &in_use, limit, s, hb) &&
+              upload(cells, b.cells, &in_use, limit, s, hb) && upload(witems, b.witems, &in_use, limit, s, hb);
+    const size_t lanes = std::max<uint64_t>(b.lanes, 1);
+    ok = ok && ensure(cnt, lanes * 4, &in_use, limit) && ensure(syn, lanes * 4, &in_use, limit) &&
+         ensure(phs, lanes * 4, &in_use, limit) && ensure(erro, lanes * 8, &in_use, limit) &&
+         ensure(totsyn, std::max<uint64_t>(b.ncols, 1) * 4, &in_use, limit) &&
+         ensure(wcnt, std::max<uint64_t>(nw, 1) * 4, &in_use, limit) &&
+         ensure(wbase, std::max<uint64_t>(nw, 1) * 8, &in_use, limit) &&
+         ensure(blocksum, (size_t)nwblocks * 8, &in_use, limit) &&
+         ensure(hist, (size_t)kMaxPasses * kRadixBins * 8, &in_use, limit) &&
+         ensure(err_key, np * 8, &in_use, limit) && ensure(div_tid, np * 4, &in_use, limit) &&
+         ensure(best_pos, np * 8, &in_use, limit) && ensure(ptuples, np * 8, &in_use, limit) &&
+         ensure(results, np * sizeof(DevResult), &in_use, limit) && ensure(ctrl, sizeof(Control), &in_use, limit);
+    if (ok && !epoch.p) {
+        ok = ensure(epoch, 16, &in_use, limit) && cudaMemsetAsync(epoch.p, 0, 16, s) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        return Error::make(S_NOMEM, "device allocation failed");
+    }
+    BatchArgs &a = args;
+    a.insns = (const Insn *)insns.p;
+    a.xcode = (const uint64_t *)xcode.p;
+    a.items = (const ItemDesc *)items.p;
+    a.protos = (const DevProto *)protos.p;
+    a.cells = (const uint64_t *)cells.p;
+    a.witems = (const WarpItem *)witems.p;
+    a.nwitems = (uint32_t)nw;
+    a.nprotos = (uint32_t)np;
+    a.ncols = b.ncols;
+    a.cnt = (uint32_t *)cnt.p;
+    a.syn = (uint32_t *)syn.p;
+    a.phs = (uint32_t *)phs.p;
+    a.erro = (unsigned long long *)erro.p;
+    a.totsyn = (uint32_t *)totsyn.p;
+    a.wcnt = (uint32_t *)wcnt.p;
+    a.wbase = (unsigned long long *)wbase.p;
+    a.blocksum = (unsigned long long *)blocksum.p;
+    a.nwblocks = nwblocks;
+    a.hist = (unsigned long long *)hist.p;
+    a.err_key = (unsigned long long *)err_key.p;
+    a.div_tid = (uint32_t *)div_tid.p;
+    a.best_pos = (unsigned long long *)best_pos.p;
+    a.ptuples = (unsigned long long *)ptuples.p;
+    a.results = (DevResult *)results.p;
+    a.ctrl = (Control *)ctrl.p;
+    a.epoch = (uint32_t *)epoch.p;
+    a.L = b.L;
+    a.nkeys = 0;
+    a.ntiles = 0;
+    a.keys[0] = (unsigned long long *)keys0.p;
+    a.keys[1] = (unsigned long long *)keys1.p;
+    a.status = (unsigned long long *)status.p;
+    return Error{};
+}
+
+Error DeviceBatch::size_keys(uint64_t n, cudaStream_t s)
+{
+    const uint32_t tiles = radix_tiles(n);
+    const size_t kb = std::max<uint64_t>(n, 1) * 8;
+    const size_t sb = std::max<size_t>((size_t)args.L.passes * tiles * kRadixBins * 8, 16);
+    size_t old_status = status.cap;
+    bool ok = ensure(keys0, kb, &in_use, limit) && ensure(keys1, kb, &in_use, limit) &&
+              ensure(status, sb, &in_use, limit);
+    if (!ok) {
+        cudaGetLastError();
+        return Error::make(S_NOMEM, "device allocation for " + std::to_string(n) + " access keys failed");
+    }
+    // fresh look-back words must not carry a stale tag; clear them when the
+    // buffer is new and well before the 22-bit launch tag wraps
+    if (status.cap != old_status || status_launches >= (1ull << 21)) {
+        if (cudaMemsetAsync(status.p, 0, status.cap, s) != cudaSuccess) return Error::make(S_CUDA, "memset failed");
+        status_launches = 0;
+    }
+    args.nkeys = n;
+    args.ntiles = tiles;
+    args.keys[0] = (unsigned long long *)keys0.p;
+    args.keys[1] = (unsigned long long *)keys1.p;
+    args.status = (unsigned long long *)status.p;
+    return Error{};
+}
+
+static int flags_status(unsigned flags)
+{
+    if (flags & CF_LOOKBACK_TIMEOUT) return S_TIMEOUT;
+    if (flags) return S_INTERNAL;
+    return S_OK;
+}
+
+int run_batch(DeviceBatch &w, Control *pinned, int sms, cudaStream_t s, const BatchHost &b,
+              std::vector<DevResult> &out, std::string &err)
+{
+    Error e = w.load(b, s);
+    if (!e.ok()) { err = e.message; return e.status; }
+    if (launch_front(w.args, s, sms, nullptr, nullptr) != cudaSuccess ||
+        cudaMemcpyAsync(pinned, w.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        err = cudaGetErrorString(cudaGetLastError());
+        return S_CUDA;
+    }
+    const uint64_t n = pinned->total;
+    e = w.size_keys(n, s);
+    if (!e.ok()) { err = e.message; return e.status; }
+    w.status_launches++;
+    out.resize(b.protos.size());
+    if (launch_back(w.args, s, sms, nullptr, nullptr) != cudaSuccess ||
+        cudaMemcpyAsync(out.data(), w.args.results, out.size() * sizeof(DevResult), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(pinned, w.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        err = cudaGetErrorString(cudaGetLastError());
+        return S_CUDA;
+    }
+    w.d2h_bytes = 2 * sizeof(Control) + out.size() * sizeof(DevResult);
+    int st = flags_status(pinned->flags);
+    if (st) err = "device pipeline consistency check failed (flags " + std::to_string(pinned->flags) + ")";
+    return st;
+}
+
+int run_batch(drf_ctx *ctx, const BatchHost &b, cudaStream_t s, std::vector<DevResult> &out)
+{
+    ctx->work.limit = ctx->opts.max_device_bytes;
+    return run_batch(ctx->work, ctx->pinned_ctrl, ctx->sms, s, b, out, ctx->last_error);
+}
+
+void to_public(const DevResult &d, drf_result *o)
+{
+    std::memset(o, 0, sizeof *o);
+    o->status = d.status;
+    o->verdict = d.status ? -1 : d.verdict;
+    o->phase = d.phase;
+    o->loc = d.loc;
+    o->index = d.index;
+    o->tid_i = d.tid_i;
+    o->tid_j = d.tid_j;
+    o->i_writes = d.i_writes;
+    o->j_writes = d.j_writes;
+    o->div_tid = d.div_tid;
+    o->sync_count_0 = d.sync_count_0;
+    o->sync_count_div = d.sync_count_div;
+    o->phases = d.phases;
+    o->tuples = d.tuples;
+    o->err_tid = d.err_tid;
+    o->err_ordinal = d.err_ordinal;
+}
+
+}  // namespace drf

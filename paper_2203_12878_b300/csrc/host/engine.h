@@ -1,0 +1,107 @@
+// Host engine: packs prepared protocols into a device batch, owns device
+// buffers, and runs the pipeline (directly or as a captured CUDA graph).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../../include/drf.h"
+#include "../cuda/pipeline.cuh"
+#include "prepare.h"
+
+namespace drf {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+// Grow-only device allocation; returns false on failure.
+bool ensure(DevBuf &b, size_t bytes, size_t *in_use, uint64_t limit);
+void release(DevBuf &b, size_t *in_use);
+
+// Host image of a batch.
+struct BatchHost {
+    std::vector<Insn> insns;
+    std::vector<uint64_t> xcode;
+    std::vector<ItemDesc> items;
+    std::vector<DevProto> protos;
+    std::vector<uint64_t> cells;
+    std::vector<WarpItem> witems;
+    uint64_t ncols = 0;
+    uint64_t lanes = 0;
+    uint64_t tuple_bound = 0;
+    KeyLayout L{};
+};
+
+// Packs prepared protocols (all valid) into a batch; fails with
+// S_KEY_TOO_WIDE when the combined key layout exceeds 64 bits.
+Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out);
+
+// Device buffers of one batch (a plan owns one; a context reuses one).
+struct DeviceBatch {
+    DevBuf insns, xcode, items, protos, cells, witems;
+    DevBuf cnt, syn, phs, erro, totsyn, wcnt, wbase, blocksum;
+    DevBuf keys0, keys1, hist, status;
+    DevBuf err_key, div_tid, best_pos, ptuples, results, ctrl, epoch;
+    size_t in_use = 0;
+    uint64_t limit = 0;
+    uint64_t status_launches = 0;     // launches since the look-back words were cleared
+    uint64_t h2d_bytes = 0, d2h_bytes = 0;   // copies of the last run
+    BatchArgs args{};
+
+    ~DeviceBatch();
+    // Uploads the batch and sizes every buffer that does not depend on the
+    // tuple count.
+    Error load(const BatchHost &b, cudaStream_t s);
+    // Sizes the key and look-back buffers for n tuples.
+    Error size_keys(uint64_t n, cudaStream_t s);
+};
+
+struct Timing;
+
+}  // namespace drf
+
+struct drf_ctx {
+    int device = 0;
+    int sms = 148;
+    cudaStream_t stream = nullptr;
+    drf_opts opts{};
+    std::string last_error;
+    drf::DeviceBatch work;            // reused by drf_check / drf_check_batch
+    std::vector<drf::DevResult> host_results;
+    drf::Control host_ctrl{};
+    drf::Control *pinned_ctrl = nullptr;
+    void *server = nullptr;           // drf::Server when running
+    std::mutex mu;                    // guards `work` between the caller and the server thread
+};
+
+struct drf_plan {
+    drf_ctx *ctx = nullptr;
+    uint32_t n = 0;
+    drf::BatchHost host;
+    drf::DeviceBatch dev;
+    uint64_t tuples = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last_stream = nullptr;
+    std::vector<cudaEvent_t> events;
+    int nevents = 0;
+    bool profiled = false;
+};
+
+namespace drf {
+
+// Runs one batch on the buffers `w`: front, size, back; results into `out`
+// (one per packed protocol).  `pinned` is a host-pinned Control used to read
+// the tuple count back.  Returns a batch-level status; `err` gets a message.
+int run_batch(DeviceBatch &w, Control *pinned, int sms, cudaStream_t s, const BatchHost &b,
+              std::vector<DevResult> &out, std::string &err);
+int run_batch(drf_ctx *ctx, const BatchHost &b, cudaStream_t s, std::vector<DevResult> &out);
+
+void to_public(const DevResult &d, drf_result *out);
+
+}  // namespace drf

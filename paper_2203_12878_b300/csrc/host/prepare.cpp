@@ -1,0 +1,595 @@
+// Interval analysis, lowering to the device program, and work
+// decomposition (see prepare.h).
+//
+// Interval analysis: every expression node gets the range of values it can
+// take over tid in [0, T), parameters at their given values and each loop
+// variable over [min lo, max hi - 1] of its loop's bounds.  A node whose
+// range leaves int64 makes the protocol OVERFLOW_RISK (arithmetic is on
+// mathematical integers held in int64; the paper's expressions are over the
+// naturals, Fig. 1, with operators left open).  If every range fits int32
+// the GPU evaluates in 32-bit arithmetic.  An access whose index provably
+// lies in [0, cells) and cannot divide by zero needs no evaluation in the
+// count pass.  Trip counts give static upper bounds on syncs (phase-field
+// width), accesses and interpreter steps per thread.
+#include <algorithm>
+#include <cstring>
+#include <unordered_map>
+
+#include "prepare.h"
+
+namespace drf {
+namespace {
+
+using i128 = __int128;
+constexpr i128 kI64Min = INT64_MIN, kI64Max = INT64_MAX;
+constexpr i128 kI32Min = INT32_MIN, kI32Max = INT32_MAX;
+constexpr i128 kHuge = (i128)1 << 100;     // saturation for counts
+
+struct Iv {
+    i128 lo = 0, hi = -1;                  // empty when lo > hi
+    bool empty() const { return lo > hi; }
+    static Iv point(i128 v) { return Iv{v, v}; }
+};
+
+i128 sat(i128 v) { return v > kHuge ? kHuge : v; }
+i128 mul_sat(i128 a, i128 b)
+{
+    if (a == 0 || b == 0) return 0;
+    if (a > kHuge / b) return kHuge;
+    return sat(a * b);
+}
+
+i128 floor_div(i128 a, i128 b)
+{
+    i128 q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) q -= 1;
+    return q;
+}
+
+struct LoopInfo {
+    i128 trip_max = 0;       // over all threads and outer iterations
+    i128 body_steps = 0;     // steps per iteration, upper bound
+    i128 body_tuples = 0;
+};
+
+struct Work {
+    i128 tuples = 0, steps = 0, syncs = 0;
+};
+
+class Analyzer {
+public:
+    Analyzer(uint32_t T, const uint64_t *cells, const int64_t *params, uint16_t nslots)
+        : T_(T), cells_(cells), params_(params), var_(nslots) {}
+
+    bool risk = false;
+    bool wide = false;
+    std::unordered_map<const Stmt *, LoopInfo> loops;
+    std::unordered_map<const Stmt *, bool> count_eval;   // access -> evaluate index in the count pass
+    std::unordered_map<const Expr *, Iv> ranges;
+
+    std::unordered_map<const Stmt *, Work> work;          // per statement, upper bounds per thread
+
+    Work stmt(const Stmt &s, bool reachable)
+    {
+        Work w = stmt_inner(s, reachable);
+        work[&s] = w;
+        return w;
+    }
+
+    Work stmt_inner(const Stmt &s, bool reachable)
+    {
+        Work w;
+        switch (s.op) {
+        case SOp::Skip:
+            return w;
+        case SOp::Sync:
+            w.steps = 1; w.syncs = 1;
+            return w;
+        case SOp::Access: {
+            bool div0 = false;
+            Iv ix = expr(*s.index, div0, reachable);
+            bool in_range = !ix.empty() && ix.lo >= 0 && ix.hi < (i128)cells_[s.loc];
+            count_eval[&s] = !(in_range && !div0);
+            w.tuples = 1; w.steps = 1;
+            return w;
+        }
+        case SOp::Seq:
+            for (auto &it : s.items) {
+                Work x = stmt(*it, reachable);
+                w.tuples = sat(w.tuples + x.tuples);
+                w.steps = sat(w.steps + x.steps);
+                w.syncs = sat(w.syncs + x.syncs);
+            }
+            return w;
+        case SOp::If: {
+            cond(*s.cond, reachable);
+            Work a = stmt(*s.then_s, reachable), b = stmt(*s.else_s, reachable);
+            w.tuples = std::max(a.tuples, b.tuples);
+            w.steps = sat(std::max(a.steps, b.steps) + 2);
+            w.syncs = std::max(a.syncs, b.syncs);
+            return w;
+        }
+        case SOp::ForU:
+        case SOp::ForS: {
+            bool d0 = false;
+            Iv lo = expr(*s.lo, d0, reachable), hi = expr(*s.hi, d0, reachable);
+            LoopInfo li;
+            Iv v;
+            if (!lo.empty() && !hi.empty()) { v.lo = lo.lo; v.hi = hi.hi - 1; }
+            li.trip_max = v.empty() ? 0 : sat(hi.hi - lo.lo);
+            var_[s.slot] = v;
+            Work b = stmt(*s.body, reachable && !v.empty());
+            li.body_steps = sat(b.steps + 1);
+            li.body_tuples = b.tuples;
+            loops[&s] = li;
+            w.tuples = mul_sat(li.trip_max, b.tuples);
+            w.steps = sat(1 + mul_sat(li.trip_max, li.body_steps));
+            w.syncs = mul_sat(li.trip_max, b.syncs);
+            return w;
+        }
+        }
+        return w;
+    }
+
+private:
+    uint32_t T_;
+    const uint64_t *cells_;
+    const int64_t *params_;
+    std::vector<Iv> var_;
+
+    void note(const Iv &v, bool reachable)
+    {
+        if (!reachable || v.empty()) return;
+        if (v.lo < kI64Min || v.hi > kI64Max) risk = true;
+        if (v.lo < kI32Min || v.hi > kI32Max) wide = true;
+    }
+
+    void cond(const Cond &c, bool reachable)
+    {
+        bool d0 = false;
+        switch (c.op) {
+        case COp::True: case COp::False: return;
+        case COp::And: case COp::Or: cond(*c.l, reachable); cond(*c.r, reachable); return;
+        case COp::Not: cond(*c.l, reachable); return;
+        default: expr(*c.a, d0, reachable); expr(*c.b, d0, reachable); return;
+        }
+    }
+
+    Iv expr(const Expr &e, bool &div0, bool reachable)
+    {
+        Iv r = expr_inner(e, div0, reachable);
+        note(r, reachable);
+        // once a value may leave int64 the protocol is rejected; clamping just
+        // past that range keeps every later product inside 128 bits
+        const i128 clamp = kI64Max + 2;
+        if (!r.empty()) { r.lo = std::max(r.lo, -clamp); r.hi = std::min(r.hi, clamp); }
+        ranges[&e] = r;
+        return r;
+    }
+
+    Iv expr_inner(const Expr &e, bool &div0, bool reachable)
+    {
+        switch (e.op) {
+        case EOp::Const: return Iv::point(e.value);
+        case EOp::Tid: return Iv{0, (i128)T_ - 1};
+        case EOp::Param: return Iv::point(params_[e.slot]);
+        case EOp::Var: return var_[e.slot];
+        case EOp::Neg: {
+            Iv a = expr(*e.a, div0, reachable);
+            if (a.empty()) return a;
+            return Iv{-a.hi, -a.lo};
+        }
+        default: break;
+        }
+        Iv a = expr(*e.a, div0, reachable), b = expr(*e.b, div0, reachable);
+        if (a.empty() || b.empty()) return Iv{};
+        switch (e.op) {
+        case EOp::Add: return Iv{a.lo + b.lo, a.hi + b.hi};
+        case EOp::Sub: return Iv{a.lo - b.hi, a.hi - b.lo};
+        case EOp::Mul: {
+            i128 c[4] = {a.lo * b.lo, a.lo * b.hi, a.hi * b.lo, a.hi * b.hi};
+            return Iv{*std::min_element(c, c + 4), *std::max_element(c, c + 4)};
+        }
+        case EOp::Min: return Iv{std::min(a.lo, b.lo), std::min(a.hi, b.hi)};
+        case EOp::Max: return Iv{std::max(a.lo, b.lo), std::max(a.hi, b.hi)};
+        case EOp::Div:
+        case EOp::Mod: {
+            if (b.lo <= 0 && b.hi >= 0) div0 = true;
+            Iv parts[2] = {Iv{b.lo, std::min(b.hi, (i128)-1)}, Iv{std::max(b.lo, (i128)1), b.hi}};
+            Iv r;
+            bool any = false;
+            for (const Iv &p : parts) {
+                if (p.empty()) continue;
+                Iv q;
+                if (e.op == EOp::Div) {
+                    // floor(a / b) is monotone in a, and in b on a sign-constant range
+                    i128 c[4] = {floor_div(a.lo, p.lo), floor_div(a.lo, p.hi), floor_div(a.hi, p.lo),
+                                 floor_div(a.hi, p.hi)};
+                    q = Iv{*std::min_element(c, c + 4), *std::max_element(c, c + 4)};
+                } else {
+                    i128 m = std::max(p.lo < 0 ? -p.lo : p.lo, p.hi < 0 ? -p.hi : p.hi);
+                    i128 mmin = std::min(p.lo < 0 ? -p.lo : p.lo, p.hi < 0 ? -p.hi : p.hi);
+                    if (a.lo >= 0 && a.hi < mmin) q = a;        // already reduced
+                    else q = Iv{0, m - 1};
+                }
+                if (!any) r = q;
+                else r = Iv{std::min(r.lo, q.lo), std::max(r.hi, q.hi)};
+                any = true;
+            }
+            return any ? r : Iv{};                        // divisor always zero
+        }
+        default: return Iv{};
+        }
+    }
+};
+
+// ------------------------------------------------------------------ lowering
+
+struct Lowerer {
+    const int64_t *params;
+    const std::unordered_map<const Expr *, Iv> &ranges;
+    const std::unordered_map<const Stmt *, bool> &count_eval;
+    std::vector<Insn> insns;
+    std::vector<uint64_t> xcode;
+    std::vector<int> slot_reg;        // AST slot -> device register (nesting depth)
+    int max_stack = 0;
+    bool too_deep = false;
+
+    // Folded form of an expression: a constant, or a linear combination of
+    // tid / registers, or neither.
+    struct Lin {
+        bool ok = false;
+        i128 c0 = 0;
+        std::vector<std::pair<uint32_t, i128>> terms;   // (register or kAffTid, coefficient)
+    };
+
+    static void add_term(Lin &l, uint32_t reg, i128 c)
+    {
+        for (auto &t : l.terms)
+            if (t.first == reg) { t.second += c; return; }
+        l.terms.emplace_back(reg, c);
+    }
+
+    Lin linear(const Expr &e)
+    {
+        Lin l;
+        const i128 lim = (i128)1 << 62;
+        switch (e.op) {
+        case EOp::Const: l.ok = true; l.c0 = e.value; return l;
+        case EOp::Param: l.ok = true; l.c0 = params[e.slot]; return l;
+        case EOp::Tid: l.ok = true; add_term(l, kAffTid, 1); return l;
+        case EOp::Var: l.ok = true; add_term(l, (uint32_t)slot_reg[e.slot], 1); return l;
+        case EOp::Neg: {
+            Lin a = linear(*e.a);
+            if (!a.ok) return l;
+            a.c0 = -a.c0;
+            for (auto &t : a.terms) t.second = -t.second;
+            return a;
+        }
+        case EOp::Add:
+        case EOp::Sub: {
+            Lin a = linear(*e.a), b = linear(*e.b);
+            if (!a.ok || !b.ok) return l;
+            i128 s = e.op == EOp::Add ? 1 : -1;
+            a.c0 += s * b.c0;
+            for (auto &t : b.terms) add_term(a, t.first, s * t.second);
+            if (a.c0 > lim || a.c0 < -lim) return l;
+            for (auto &t : a.terms) if (t.second > lim || t.second < -lim) return l;
+            return a;
+        }
+        case EOp::Mul: {
+            Lin a = linear(*e.a), b = linear(*e.b);
+            if (!a.ok || !b.ok) return l;
+            if (!a.terms.empty() && !b.terms.empty()) return l;       // not linear
+            Lin &v = a.terms.empty() ? b : a;
+            i128 k = a.terms.empty() ? a.c0 : b.c0;
+            if (k > lim || k < -lim) return l;
+            v.c0 *= k;
+            for (auto &t : v.terms) t.second *= k;
+            if (v.c0 > lim || v.c0 < -lim) return l;
+            for (auto &t : v.terms) if (t.second > lim || t.second < -lim) return l;
+            return v;
+        }
+        default: return l;
+        }
+    }
+
+    void word(uint8_t op, int64_t arg = 0) { xcode.push_back((uint64_t)op | ((uint64_t)arg << 8)); }
+    void lit(int64_t v) { xcode.push_back((uint64_t)v); }
+
+    // Emits code for e; depth is the stack height before it runs.
+    void emit_expr(const Expr &e, int depth)
+    {
+        if (depth + 1 > max_stack) max_stack = depth + 1;
+        Lin l = linear(e);
+        if (l.ok) {
+            std::vector<std::pair<uint32_t, i128>> terms;
+            for (auto &t : l.terms) if (t.second != 0) terms.push_back(t);
+            if (terms.empty()) { word(X_CONST); lit((int64_t)l.c0); return; }
+            if (terms.size() == 1 && terms[0].second == 1 && l.c0 == 0) {
+                if (terms[0].first == kAffTid) word(X_TID);
+                else word(X_VAR, terms[0].first);
+                return;
+            }
+            word(X_AFF, (int64_t)terms.size());
+            for (auto &t : terms) { lit(t.first); lit((int64_t)t.second); }
+            lit((int64_t)l.c0);
+            return;
+        }
+        switch (e.op) {
+        case EOp::Neg: emit_expr(*e.a, depth); word(X_NEG); return;
+        case EOp::Div:
+        case EOp::Mod: {
+            Lin d = linear(*e.b);
+            bool konst = d.ok && d.terms.empty() && d.c0 != 0;
+            emit_expr(*e.a, depth);
+            if (konst) {
+                i128 m = d.c0;
+                if (e.op == EOp::Mod && m > 0 && (m & (m - 1)) == 0) { word(X_MASK); lit((int64_t)(m - 1)); }
+                else { word(e.op == EOp::Div ? X_DIVC : X_MODC); lit((int64_t)m); }
+                return;
+            }
+            emit_expr(*e.b, depth + 1);
+            word(e.op == EOp::Div ? X_DIV : X_MOD);
+            return;
+        }
+        default: break;
+        }
+        emit_expr(*e.a, depth);
+        emit_expr(*e.b, depth + 1);
+        static const uint8_t code[] = {0, 0, 0, 0, X_ADD, X_SUB, X_MUL, 0, 0, X_MIN, X_MAX};
+        word(code[(int)e.op]);
+    }
+
+    void emit_cond(const Cond &c, int depth)
+    {
+        if (depth + 1 > max_stack) max_stack = depth + 1;
+        switch (c.op) {
+        case COp::True: word(X_CONST); lit(1); return;
+        case COp::False: word(X_CONST); lit(0); return;
+        case COp::Not: emit_cond(*c.l, depth); word(X_NOT); return;
+        case COp::And: case COp::Or:
+            emit_cond(*c.l, depth); emit_cond(*c.r, depth + 1);
+            word(c.op == COp::And ? X_AND : X_OR);
+            return;
+        default: break;
+        }
+        emit_expr(*c.a, depth);
+        emit_expr(*c.b, depth + 1);
+        static const uint8_t code[] = {0, 0, X_EQ, X_NE, X_LT, X_LE, X_GT, X_GE};
+        word(code[(int)c.op]);
+    }
+
+    int32_t expr_code(const Expr &e)
+    {
+        int32_t off = (int32_t)xcode.size();
+        emit_expr(e, 0);
+        word(X_RET);
+        return off;
+    }
+
+    int32_t cond_code(const Cond &c)
+    {
+        int32_t off = (int32_t)xcode.size();
+        emit_cond(c, 0);
+        word(X_RET);
+        return off;
+    }
+
+    int32_t pc() const { return (int32_t)insns.size(); }
+
+    int32_t emit(uint8_t op, uint8_t a = 0, uint16_t b = 0, int32_t c = 0, int32_t d = 0, int32_t e = 0)
+    {
+        insns.push_back(Insn{op, a, b, c, d, e});
+        return pc() - 1;
+    }
+
+    std::unordered_map<const Stmt *, std::pair<int32_t, int32_t>> range;   // [begin, end) pcs
+
+    void stmt(const Stmt &s, int depth)
+    {
+        int32_t begin = pc();
+        stmt_inner(s, depth);
+        range[&s] = {begin, pc()};
+    }
+
+    void stmt_inner(const Stmt &s, int depth)
+    {
+        switch (s.op) {
+        case SOp::Skip: return;
+        case SOp::Sync: emit(I_SYNC); return;
+        case SOp::Access: {
+            uint8_t flags = (s.write ? AF_WRITE : 0) | (count_eval.at(&s) ? AF_EVAL_IN_COUNT : 0);
+            emit(I_ACCESS, flags, s.loc, expr_code(*s.index));
+            return;
+        }
+        case SOp::Seq:
+            for (auto &it : s.items) stmt(*it, depth);
+            return;
+        case SOp::If: {
+            int32_t ip = emit(I_IF, 0, 0, cond_code(*s.cond));
+            stmt(*s.then_s, depth);
+            bool has_else = !(s.else_s->op == SOp::Skip ||
+                              (s.else_s->op == SOp::Seq && s.else_s->items.empty()));
+            if (has_else) {
+                int32_t jp = emit(I_JUMP);
+                insns[ip].d = pc();
+                stmt(*s.else_s, depth);
+                insns[jp].c = pc();
+            } else {
+                insns[ip].d = pc();
+            }
+            return;
+        }
+        case SOp::ForU:
+        case SOp::ForS: {
+            if (depth >= kMaxVars) { too_deep = true; return; }
+            slot_reg[s.slot] = depth;
+            int32_t lo = expr_code(*s.lo), hi = expr_code(*s.hi);
+            int32_t lp = emit(I_LOOP, (uint8_t)depth, 0, lo, hi);
+            int32_t body = pc();
+            stmt(*s.body, depth + 1);
+            int32_t ep = emit(I_ENDLOOP, (uint8_t)depth, 0, body);
+            insns[lp].e = ep;
+            return;
+        }
+        }
+    }
+};
+
+// Cuts a statement list into items in program order.  A loop that deserves
+// at least two items is split: into chunks of iterations when it deserves no
+// more items than it has iterations, otherwise into single iterations whose
+// bodies are cut recursively.  Consecutive statements that are not split form
+// one "run" item.
+struct Splitter {
+    const Analyzer &an;
+    const Lowerer &lw;
+    std::vector<ItemDesc> &items;
+    std::vector<uint64_t> &isteps;
+    uint32_t split_pc[kMaxSplit] = {};
+    uint32_t split_j[kMaxSplit] = {};
+    int depth = 0;
+
+    void push_item(uint32_t start, uint32_t stop, bool chunked, uint32_t chunk, i128 steps)
+    {
+        ItemDesc d{};
+        d.start_pc = start;
+        d.stop_pc = stop;
+        d.nsplit = (uint16_t)depth;
+        d.chunked = chunked ? 1 : 0;
+        d.chunk = chunk;
+        for (int l = 0; l < depth; l++) { d.split_pc[l] = split_pc[l]; d.j[l] = split_j[l]; }
+        items.push_back(d);
+        isteps.push_back((uint64_t)std::min<i128>(std::max<i128>(steps, 1), (i128)1 << 62));
+    }
+
+    void list(const Stmt &seq, i128 budget)
+    {
+        std::vector<const Stmt *> xs;
+        if (seq.op == SOp::Seq) for (auto &it : seq.items) xs.push_back(it.get());
+        else xs.push_back(&seq);
+        i128 total = 0;
+        for (const Stmt *x : xs) total = sat(total + an.work.at(x).steps);
+        int32_t run_b = -1, run_e = -1;
+        i128 run_steps = 0;
+        auto flush = [&] {
+            if (run_b >= 0 && run_e > run_b) push_item((uint32_t)run_b, (uint32_t)run_e, false, 1, run_steps);
+            run_b = -1; run_steps = 0;
+        };
+        for (const Stmt *x : xs) {
+            auto r = lw.range.at(x);
+            if (r.first == r.second) continue;                       // no code (skip)
+            i128 steps = an.work.at(x).steps;
+            i128 ks = total > 0 ? (budget * steps + total - 1) / total : 1;
+            bool loop = x->op == SOp::ForU || x->op == SOp::ForS;
+            const LoopInfo *li = loop ? &an.loops.at(x) : nullptr;
+            if (!loop || ks < 2 || depth >= kMaxSplit || li->trip_max < 1 || li->trip_max > (i128)UINT32_MAX) {
+                if (run_b < 0) run_b = r.first;
+                run_e = r.second;
+                run_steps = sat(run_steps + steps);
+                continue;
+            }
+            flush();
+            const i128 m = li->trip_max;
+            const uint32_t loop_pc = (uint32_t)r.first, end_pc = (uint32_t)r.second;   // ENDLOOP is end_pc - 1
+            split_pc[depth] = loop_pc;
+            if (ks <= m || depth + 1 >= kMaxSplit) {
+                i128 parts = std::min(ks, m);
+                i128 chunk = (m + parts - 1) / parts;
+                i128 nch = (m + chunk - 1) / chunk;
+                for (i128 c = 0; c < nch; c++) {
+                    split_j[depth] = (uint32_t)c;
+                    depth++;
+                    push_item(loop_pc + 1, end_pc, true, (uint32_t)chunk, mul_sat(chunk, li->body_steps));
+                    depth--;
+                }
+            } else {
+                i128 sub = (ks + m - 1) / m;
+                for (i128 j = 0; j < m; j++) {
+                    split_j[depth] = (uint32_t)j;
+                    depth++;
+                    list(*x->body, sub);
+                    depth--;
+                }
+            }
+        }
+        flush();
+    }
+};
+
+}  // namespace
+
+Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, const uint64_t *cells,
+              uint32_t nparams, const int64_t *params, const PrepareOpts &opts, Prepared &out)
+{
+    Protocol p;
+    Error err = decode_bytecode(bc, len, p);
+    if (!err.ok()) return err;
+    if (nlocs != p.narrays || nparams != p.nparams)
+        return Error::make(S_INVALID_ARG, "bounds give " + std::to_string(nlocs) + " arrays and " +
+                                              std::to_string(nparams) + " params; the protocol declares " +
+                                              std::to_string(p.narrays) + " and " + std::to_string(p.nparams));
+    if ((nlocs && !cells) || (nparams && !params)) return Error::make(S_INVALID_ARG, "null array sizes or params");
+    if (nthreads > (1u << 27)) return Error::make(S_LIMIT, "more than 2^27 threads");
+
+    out = Prepared{};
+    out.nthreads = nthreads;
+    out.narrays = nlocs;
+    out.cells.assign(cells, cells + nlocs);
+
+    Analyzer an(nthreads ? nthreads : 1, cells, params, p.nslots);
+    Work w = an.stmt(*p.body, nthreads > 0);
+    if (an.risk) return Error::make(S_OVERFLOW_RISK, "an intermediate value may leave the 64-bit range");
+    if (w.syncs >= ((i128)1 << 32)) return Error::make(S_LIMIT, "more than 2^32 syncs per thread");
+    if ((i128)nthreads * w.tuples > (i128)kMaxTupleBound)
+        return Error::make(S_LIMIT, "the protocol may make more than 2^36 accesses");
+    if ((i128)nthreads * w.steps > (i128)kMaxStepBound)
+        return Error::make(S_LIMIT, "the protocol may run more than 2^42 steps");
+    out.wide = an.wide;
+    out.max_syncs = (uint64_t)w.syncs;
+    out.max_tuples = (uint64_t)w.tuples;
+    out.max_steps = (uint64_t)w.steps;
+
+    Lowerer lw{params, an.ranges, an.count_eval};
+    lw.slot_reg.assign(p.nslots, 0);
+
+    lw.stmt(*p.body, 0);
+    if (lw.too_deep) return Error::make(S_LIMIT, "loops nested more than 16 deep");
+    if (lw.max_stack > kMaxStack) return Error::make(S_LIMIT, "expression needs more than 16 stack slots");
+    lw.emit(I_END);
+    if (lw.insns.size() > (1u << 24) || lw.xcode.size() > (1u << 26)) return Error::make(S_LIMIT, "protocol too large");
+
+    // --- work decomposition: how many items each thread is cut into
+    i128 total = std::max<i128>(1, w.steps);
+    uint64_t groups = nthreads ? (nthreads + 31) / 32 : 1;
+    i128 k_want = std::max<i128>(1, ((i128)opts.desired_warp_items + groups - 1) / groups);
+    i128 k_work = std::max<i128>(1, total / std::max<uint64_t>(1, opts.min_item_steps));
+    i128 K = std::min<i128>(std::min(k_want, k_work), opts.max_items);
+    if ((i128)K * nthreads > ((i128)1 << 27)) K = std::max<i128>(1, ((i128)1 << 27) / std::max<uint32_t>(1, nthreads));
+
+    std::vector<ItemDesc> items;
+    std::vector<uint64_t> isteps;
+    for (int attempt = 0; attempt < 16; attempt++) {
+        items.clear();
+        isteps.clear();
+        Splitter sp{an, lw, items, isteps};
+        sp.list(*p.body, K);
+        if (items.size() <= opts.max_items || K <= 1) break;
+        K = std::max<i128>(1, K / 2);                          // too fine: coarsen
+    }
+    if (items.empty()) {
+        ItemDesc d{};
+        items.push_back(d);                                    // nothing to run
+        isteps.push_back(1);
+    }
+    if ((i128)items.size() * nthreads > ((i128)1 << 28)) return Error::make(S_LIMIT, "too many work items");
+
+    out.insns = std::move(lw.insns);
+    out.xcode = std::move(lw.xcode);
+    out.items = std::move(items);
+    out.item_steps = std::move(isteps);
+    return Error{};
+}
+
+}  // namespace drf

@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA pipeline, called through the C ABI, against the
+oracle.  Everything here is integer work, so the bar is bit-exact equality of
+status, verdict, witness (phase, array, index, i, j, i_writes, j_writes),
+divergence fields, error tid and ordinal, tuple and phase counts."""
+import json
+import os
+import random
+
+import numpy as np
+import pytest
+
+from paper_2203_12878_b300 import drf, protogen
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+CELLS = 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = drf.drf_ctx_create(0)
+    yield c
+    drf.drf_ctx_destroy(c)
+
+
+def run(ctx, p):
+    bc = drf.drf_protocol_compile(p.text)
+    return drf.result_dict(drf.drf_check(ctx, bc, p.nthreads, p.cells, p.params))
+
+
+def want(oracle, p):
+    return oracle.check(p.text, p.nthreads, p.cells, p.params, CELLS)
+
+
+def same(got, exp):
+    exp = {k: v for k, v in exp.items() if k != "message"}
+    return got == exp
+
+
+def test_paper_examples(ctx):
+    with open(os.path.join(HERE, "golden", "paper_examples.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        p = protogen.Protocol(c["text"], c["nthreads"], c["cells"], c["params"])
+        try:
+            got = run(ctx, p)
+        except drf.DrfError as e:
+            got = {"status": e.name}
+        for k, v in c["expect"].items():
+            assert got[k] == v, (c["name"], k, got)
+
+
+@pytest.mark.parametrize("chunk", range(6))
+def test_random_small_sweep(ctx, oracle, chunk):
+    """600 tiny protocols per chunk over the whole syntax: conditionals,
+    thread-dependent bounds, min/max, floor division, Euclidean remainder,
+    parameters, syncs, evaluation errors, barrier divergence."""
+    mism = []
+    for seed in range(chunk * 600, (chunk + 1) * 600):
+        p = protogen.random_small(seed)
+        exp = want(oracle, p)
+        if exp["status"] == "OVERFLOW":
+            continue
+        got = run(ctx, p)
+        if not same(got, exp):
+            mism.append((seed, got, exp))
+    assert not mism, mism[:3]
+
+
+def _decode(keys, lay):
+    tb, ib, lb, pb = lay["tid_bits"], lay["idx_bits"], lay["loc_bits"], lay["phase_bits"]
+    k = keys.astype(np.uint64)
+    mode = k & np.uint64(1)
+    k = k >> np.uint64(1)
+    tid = k & np.uint64((1 << tb) - 1)
+    k = k >> np.uint64(tb)
+    idx = k & np.uint64((1 << ib) - 1)
+    k = k >> np.uint64(ib)
+    loc = k & np.uint64((1 << lb) - 1)
+    k = k >> np.uint64(lb)
+    phase = k & np.uint64((1 << pb) - 1)
+    return np.stack([phase, loc, idx, tid, mode], axis=1)
+
+
+def _rows_sorted(rows):
+    order = np.lexsort(rows.T[::-1])
+    return rows[order]
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: protogen.config1("drf"), lambda: protogen.config1("nosync"),
+    lambda: protogen.config2(2, target=3e5), lambda: protogen.config2(4, "constructed", target=3e5),
+    lambda: protogen.config4_one(random.Random(11), True),
+])
+def test_emitted_keys_are_the_access_multiset_and_sorted(ctx, oracle, maker):
+    """Stage check: the keys the emit kernel wrote are exactly the oracle's
+    dynamic accesses (as a multiset), and after the radix passes they are
+    ordered by (phase, array, index)."""
+    p = maker()
+    got = run(ctx, p)
+    assert got["status"] == "OK"
+    keys, lay = drf.drf_debug_sorted_keys(ctx)
+    rows = _decode(keys, lay)
+    seg = keys >> np.uint64(lay["tid_bits"] + 1)
+    assert np.all(seg[1:] >= seg[:-1])
+    ref = oracle.tuples(p.text, p.nthreads, p.cells, p.params)
+    assert len(ref) == len(rows) == got["tuples"]
+    assert np.array_equal(_rows_sorted(rows), _rows_sorted(ref.astype(np.uint64)))
+
+
+def test_random_small_keys(ctx, oracle):
+    for seed in range(200):
+        p = protogen.random_small(seed)
+        exp = want(oracle, p)
+        if exp["status"] != "OK" or exp["verdict"] == "BARRIER_DIVERGENCE":
+            continue
+        run(ctx, p)
+        keys, lay = drf.drf_debug_sorted_keys(ctx)
+        ref = oracle.tuples(p.text, p.nthreads, p.cells, p.params)
+        rows = _decode(keys, lay) if len(keys) else np.zeros((0, 5), np.uint64)
+        assert np.array_equal(_rows_sorted(rows), _rows_sorted(ref.astype(np.uint64))), p.text
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("mode", ["literal", "constructed"])
+def test_config2_shapes_small(ctx, oracle, seed, mode):
+    """The one-protocol workload's shape (1024 threads, two arrays of 2^20
+    cells, depth-3 nests, 1..6 syncs) at ~2x10^5 accesses: several sort tiles
+    and ragged tails."""
+    p = protogen.config2(seed, mode, target=2e5)
+    assert same(run(ctx, p), want(oracle, p))
+
+
+@pytest.mark.parametrize("seed,mode,plant", [(0, "literal", None), (3, "constructed", True),
+                                             (3, "constructed", False)])
+def test_config2_full_size(ctx, oracle, seed, mode, plant):
+    """The benchmarked workload at full size (~10^7 accesses), same launch
+    path as the benchmark: whole result against the oracle."""
+    p = protogen.config2(seed, mode, plant=plant)
+    assert same(run(ctx, p), want(oracle, p))
+
+
+def test_config2_full_size_plan_equals_check(ctx, oracle):
+    """The captured-graph path the benchmark times gives the same result as
+    the direct path and the oracle, launch after launch."""
+    p = protogen.config2(0)
+    bc = drf.drf_protocol_compile(p.text)
+    plan = drf.drf_plan_create(ctx, [bc], [(p.nthreads, p.cells, p.params)])
+    try:
+        exp = want(oracle, p)
+        for _ in range(3):
+            drf.drf_plan_launch(plan)
+            got = drf.result_dict(drf.drf_plan_results(plan)[0])
+            assert same(got, exp)
+        info = drf.drf_plan_info(plan)
+        assert info["tuples"] == exp["tuples"]
+    finally:
+        drf.drf_plan_destroy(plan)
+
+
+def test_batch_equals_alone_and_oracle(ctx, oracle):
+    ps = protogen.config4(master_seed=7, count=96)
+    ps += [protogen.random_small(s) for s in range(40)]
+    ps.append(protogen.config1("nosync"))
+    bcs = [drf.drf_protocol_compile(p.text) for p in ps]
+    res = drf.drf_check_batch(ctx, bcs, [(p.nthreads, p.cells, p.params) for p in ps])
+    for p, r in zip(ps, res):
+        exp = want(oracle, p)
+        if exp["status"] == "OVERFLOW":
+            continue
+        assert same(drf.result_dict(r), exp), p.text
+    for p, r in list(zip(ps, res))[::9]:
+        assert drf.result_dict(r) == run(ctx, p)
+
+
+@pytest.mark.parametrize("case", [
+    ("array A;\nwr A[tid];\n", 0, [4], []),                        # no threads
+    ("array A;\nwr A[0];\n", 1, [1], []),                          # one thread
+    ("", 5, [], []),                                               # empty protocol
+    ("array A;\nforS x in 0 .. 3 { sync; }\n", 64, [1], []),       # syncs only
+    ("array A;\nrd A[0];\n", 3, [0], []),                          # zero-size array
+    ("array A;\nwr A[tid % 7];\n", 1 << 20, [7], []),              # a million threads
+    ("array A;\nrd A[tid];\nwr A[tid * 2 % 1000003];\n", 200000, [1000003], []),
+    ("array A, B;\nwr B[tid];\nsync;\nwr A[tid % 2];\n", 33, [1, 64], []),
+    ("array A;\nforU x in 0 .. 70000 { wr A[x]; }\n", 2, [70000], []),      # one long item loop
+    ("array A;\nwr A[4294967295 + tid];\n", 2, [1 << 40], []),      # 40-bit index field
+])
+def test_edge_cases(ctx, oracle, case):
+    text, T, cells, params = case
+    p = protogen.Protocol(text, T, cells, params)
+    assert same(run(ctx, p), want(oracle, p))
+
+
+def test_key_too_wide_is_reported(ctx):
+    p = protogen.Protocol("array A;\nwr A[tid];\n", 1 << 27, [1 << 40], [])
+    got = run(ctx, p)
+    assert got["status"] == "KEY_TOO_WIDE"
+
+
+def test_server_results_equal_alone(ctx, oracle):
+    ps = protogen.config4(master_seed=3, count=60) + [protogen.config2(1, target=3e5)]
+    s = drf.drf_ctx_create(0)
+    try:
+        drf.drf_server_start(s, max_round_tuples=1 << 20)
+        tickets = [drf.drf_server_submit(s, drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
+                   for p in ps]
+        out = [drf.drf_server_poll(s, t, timeout_us=60_000_000) for t in tickets]
+        stats = drf.drf_server_stats(s)
+        drf.drf_server_stop(s)
+    finally:
+        drf.drf_ctx_destroy(s)
+    assert stats["completed"] == len(ps) and stats["rounds"] >= 2
+    for p, o in zip(ps, out):
+        assert o is not None
+        assert same(drf.result_dict(o[0]), want(oracle, p))

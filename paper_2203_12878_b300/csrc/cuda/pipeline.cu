@@ -22,6 +22,7 @@
 #include <cstdint>
 
 #include "pipeline.cuh"
+#include "radix.cuh"
 
 namespace drf {
 namespace {
@@ -139,6 +140,53 @@ struct EmitShared {
     unsigned int hist[kMaxPasses][kRadixBins];
 };
 
+// Adds one key per lane in `ok` to the shared digit histograms of every
+// radix pass.  When all lanes' digits agree (the usual case for the digits
+// above the index field) the lowest lane adds the whole warp's count at
+// once; otherwise every lane adds its own key.
+__device__ __forceinline__ void hist_add(EmitShared *sh, const KeyLayout &L, unsigned long long key, bool ok)
+{
+    const unsigned om = __ballot_sync(kFull, ok);
+    if (om == 0) return;
+    const int lead = __ffs(om) - 1;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t q = 0; q < L.passes; q++) {
+        uint32_t d = (uint32_t)(key >> (L.sort_lo + q * kRadixBits)) & (kRadixBins - 1);
+        uint32_t d0 = __shfl_sync(kFull, d, lead);
+        if (__all_sync(kFull, !ok || d == d0)) {
+            if ((int)lane == lead) atomicAdd(&sh->hist[q][d0], (unsigned)__popc(om));
+        } else if (ok) {
+            atomicAdd(&sh->hist[q][d], 1u);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long make_key(uint32_t p, uint32_t phase, uint32_t loc, unsigned long long idx,
+                                                      unsigned long long tidpart, uint32_t wbit, const KeyLayout &L)
+{
+    unsigned long long key = ((unsigned long long)p << L.phase_bits) | phase;
+    key = (key << L.loc_bits) | loc;
+    key = (key << L.idx_bits) | idx;
+    return (key << (L.tid_bits + 1)) | tidpart | wbit;
+}
+
+__device__ __forceinline__ unsigned long long key_or_zero(bool ok, uint32_t p, uint32_t phase, uint32_t loc,
+                                                         unsigned long long idx, unsigned long long tidpart,
+                                                         uint32_t flags, const KeyLayout &L)
+{
+    return ok ? make_key(p, phase, loc, idx, tidpart, flags & AF_WRITE, L) : 0ull;
+}
+
+// Post-operation of a fast-loop index on its linear value.
+template <typename V, typename U>
+__device__ __forceinline__ V fast_post(V v, uint32_t kind, U c)
+{
+    if (kind == FP_MASK) return (V)((U)v & c);
+    if (kind == FP_MOD) return euclid_mod<V, U>(v, (V)c);
+    if (kind == FP_DIV) return floor_div<V, U>(v, (V)c);
+    return v;
+}
+
 // Interprets one item for the 32 threads of a warp (threads 32g .. 32g+31).
 // All lanes fetch the instruction at the smallest pc among running lanes and
 // only lanes at that pc execute it, so lanes that diverge on a thread-
@@ -214,18 +262,11 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                 unsigned em = __ballot_sync(kFull, ok);
                 if (ok) {
                     unsigned long long pos = cursor + __popc(em & lanemask_lt());
-                    unsigned long long key = ((unsigned long long)p << L.phase_bits) | phase;
-                    key = (key << L.loc_bits) | in.b;
-                    key = (key << L.idx_bits) | (unsigned long long)(U)idx;
-                    key = (key << (L.tid_bits + 1)) | tidpart | (in.a & AF_WRITE);
-                    if (pos < wend && pos < a.nkeys) {
-                        a.keys[0][pos] = key;
-                        for (uint32_t q = 0; q < L.passes; q++)
-                            atomicAdd(&sh->hist[q][(key >> (L.sort_lo + q * kRadixBits)) & (kRadixBins - 1)], 1u);
-                    } else {
-                        atomicOr(&a.ctrl->flags, CF_EMIT_OVERFLOW);
-                    }
+                    unsigned long long key = make_key(p, phase, in.b, (unsigned long long)(U)idx, tidpart, in.a & AF_WRITE, L);
+                    if (pos < wend && pos < a.nkeys) a.keys[0][pos] = key;
+                    else atomicOr(&a.ctrl->flags, CF_EMIT_OVERFLOW);
                 }
+                hist_add(sh, L, key_or_zero(ok, p, phase, in.b, (unsigned long long)(U)idx, tidpart, in.a, L), ok);
                 cursor += __popc(em);
             } else if (ok) {
                 count++;
@@ -265,6 +306,69 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
         case I_JUMP:
             if (ex) pc = (uint32_t)in.c;
             break;
+        case I_FASTLOOP: {
+            V lo = 0, hi = 0;
+            bool okb = ex;
+            if (ex) {
+                if (it.chunked == 2 && mpc == it.split_pc[it.nsplit - 1]) {
+                    lo = vars[in.a]; hi = his[in.a];            // this item's chunk of the loop
+                } else if (!eval<V>(xc, in.c, tid, vars, lo) || !eval<V>(xc, in.d, tid, vars, hi)) {
+                    err = kErrDiv0; running = false; okb = false;
+                }
+            }
+            const uint64_t trip = (okb && lo < hi) ? (uint64_t)(U)((U)hi - (U)lo) : 0;
+            const uint32_t m = (uint32_t)in.e;
+            if (!EMIT) {
+                if (okb) { count += (uint32_t)(trip * m); syncs += (uint32_t)(trip * in.b); }
+            } else {
+                V rest[kFastMax];
+                U coef[kFastMax], pcon[kFastMax];
+                uint32_t meta[kFastMax];
+#pragma unroll
+                for (uint32_t j = 0; j < kFastMax; j++) {
+                    if (j < m) {
+                        const Insn A = load_insn(prog + mpc + 1 + j);
+                        rest[j] = 0;
+                        if (okb) eval<V>(xc, A.c, tid, vars, rest[j]);
+                        coef[j] = (U)__ldg(xc + A.d);
+                        pcon[j] = (U)__ldg(xc + A.d + 1);
+                        meta[j] = (uint32_t)A.a | ((uint32_t)A.b << 8);
+                        meta[j] |= (uint32_t)A.e << 24;          // phase offset: at most 255 syncs per iteration
+                    }
+                }
+                const uint32_t spi = in.b;
+                for (uint64_t t = 0;; t++) {
+                    const bool act = okb && t < trip;
+                    const unsigned am = __ballot_sync(kFull, act);
+                    if (am == 0) break;
+                    const V x = (V)((U)lo + (U)t);
+                    const uint32_t ph0 = phase + (uint32_t)(t * spi);
+                    const unsigned long long before = __popc(am & lanemask_lt());
+#pragma unroll
+                    for (uint32_t j = 0; j < kFastMax; j++) {
+                        if (j < m) {
+                            const uint32_t mt = meta[j];
+                            const V v = (V)((U)rest[j] + coef[j] * (U)x);
+                            const V idx = fast_post<V, U>(v, (mt >> 2) & 3, pcon[j]);
+                            const unsigned long long key =
+                                act ? make_key(p, ph0 + (mt >> 24), (mt >> 8) & 0xFFFF, (unsigned long long)(U)idx,
+                                               tidpart, mt & AF_WRITE, L)
+                                    : 0ull;
+                            if (act) {
+                                unsigned long long pos = cursor + before;
+                                if (pos < wend && pos < a.nkeys) a.keys[0][pos] = key;
+                                else atomicOr(&a.ctrl->flags, CF_EMIT_OVERFLOW);
+                            }
+                            hist_add(sh, L, key, act);
+                            cursor += __popc(am);
+                        }
+                    }
+                }
+                if (okb) phase += (uint32_t)(trip * spi);
+            }
+            if (okb) pc = mpc + 1 + m;
+            break;
+        }
         default:
             if (ex) running = false;
             break;
@@ -309,7 +413,9 @@ __global__ void k_init(BatchArgs a)
     if (i == 0) *a.epoch = *a.epoch + 1;
 }
 
-template <bool EMIT>
+// One kernel per arithmetic width (WIDE: 64-bit); each skips the warp-items
+// of protocols of the other width.
+template <bool EMIT, bool WIDE>
 __global__ void __launch_bounds__(256) k_interp(BatchArgs a)
 {
     __shared__ EmitShared sh;
@@ -321,6 +427,7 @@ __global__ void __launch_bounds__(256) k_interp(BatchArgs a)
     for (uint32_t w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < a.nwitems; w += warps) {
         const WarpItem wi = a.witems[w];
         const DevProto P = a.protos[wi.proto];
+        if ((P.wide != 0) != WIDE) continue;
         const ItemDesc it = a.items[P.item_off + wi.k];
         if (EMIT && wi.k == 0) {
             // barrier divergence: every thread must run as many syncs as thread 0
@@ -328,7 +435,7 @@ __global__ void __launch_bounds__(256) k_interp(BatchArgs a)
             if (tid < P.nthreads && a.totsyn[P.tid_off + tid] != a.totsyn[P.tid_off])
                 atomicMin(&a.div_tid[wi.proto], tid);
         }
-        if (P.wide) run_item<int64_t, EMIT>(a, wi.proto, P, it, wi.k, wi.g, w, &sh);
+        if (WIDE) run_item<int64_t, EMIT>(a, wi.proto, P, it, wi.k, wi.g, w, &sh);
         else run_item<int32_t, EMIT>(a, wi.proto, P, it, wi.k, wi.g, w, &sh);
     }
     if (EMIT) {
@@ -341,28 +448,55 @@ __global__ void __launch_bounds__(256) k_interp(BatchArgs a)
 }
 
 // Two roles.  Blocks [0, col_blocks): per-thread exclusive scan of syncs over
-// items.  The remaining blocks: exclusive scan of per-warp-item access counts
-// (4096 per block; the block's offset is the sum of the earlier blocks'
-// totals, accumulated by the count kernel).
+// items, 32 threads (columns) per block, each column's items split over the
+// block's 8 warps.  The remaining blocks: exclusive scan of per-warp-item
+// access counts (4096 per block; the block's offset is the sum of the earlier
+// blocks' totals, accumulated by the count kernel).
 __global__ void __launch_bounds__(kScanThreads) k_scan(BatchArgs a, uint32_t col_blocks)
 {
     if (blockIdx.x < col_blocks) {
-        uint64_t c = blockIdx.x * (uint64_t)kScanThreads + threadIdx.x;
-        if (c >= a.ncols) return;
-        uint32_t lo = 0, hi = a.nprotos - 1;               // protocol owning column c
-        while (lo < hi) {
-            uint32_t mid = (lo + hi + 1) / 2;
-            if (a.protos[mid].tid_off <= c) lo = mid; else hi = mid - 1;
+        __shared__ uint32_t s_part[kScanThreads / 32][32];
+        const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const uint64_t c = (uint64_t)blockIdx.x * 32 + lane;
+        const bool valid = c < a.ncols;
+        DevProto P{};
+        if (valid) {
+            uint32_t lo = 0, hi = a.nprotos - 1;           // protocol owning column c
+            while (lo < hi) {
+                uint32_t mid = (lo + hi + 1) / 2;
+                if (a.protos[mid].tid_off <= c) lo = mid; else hi = mid - 1;
+            }
+            P = a.protos[lo];
         }
-        const DevProto P = a.protos[lo];
-        uint32_t t = (uint32_t)(c - P.tid_off);
-        uint32_t run = 0;
-        for (uint32_t k = 0; k < P.nitems; k++) {
-            uint64_t li = P.lane_off + (uint64_t)k * P.nthreads + t;
-            a.phs[li] = run;
-            run += a.syn[li];
+        const uint32_t t = valid ? (uint32_t)(c - P.tid_off) : 0;
+        const uint32_t K = valid ? P.nitems : 0;
+        const uint32_t per = (K + kScanThreads / 32 - 1) / (kScanThreads / 32);
+        const uint32_t k0 = min(K, wid * per), k1 = min(K, k0 + per);
+        const uint32_t *syn = a.syn + P.lane_off + t;
+        uint32_t sum = 0;
+        uint32_t k = k0;
+        for (; k + 8 <= k1; k += 8) {                      // eight loads in flight
+            uint32_t v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) v[u] = syn[(uint64_t)(k + u) * P.nthreads];
+#pragma unroll
+            for (int u = 0; u < 8; u++) sum += v[u];
         }
-        a.totsyn[c] = run;
+        for (; k < k1; k++) sum += syn[(uint64_t)k * P.nthreads];
+        s_part[wid][lane] = sum;
+        __syncthreads();
+        uint32_t run = 0, total = 0;
+        for (uint32_t w = 0; w < kScanThreads / 32; w++) {
+            if (w < wid) run += s_part[w][lane];
+            total += s_part[w][lane];
+        }
+        uint32_t *phs = a.phs + P.lane_off + t;
+        for (k = k0; k < k1; k++) {
+            uint64_t off = (uint64_t)k * P.nthreads;
+            phs[off] = run;
+            run += syn[off];
+        }
+        if (valid && wid == 0) a.totsyn[c] = total;
         return;
     }
     const uint32_t b = blockIdx.x - col_blocks;
@@ -412,22 +546,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(BatchArgs a, uint32_t col
 }
 
 // ------------------------------------------------------------ radix pass
-// Look-back status word: flag (bits 62..63: 1 aggregate, 2 inclusive
-// prefix), launch tag (bits 40..61), count (bits 0..39).
-constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPrefix = 2ull << 62;
-constexpr unsigned long long kValueMask = (1ull << 40) - 1;
-constexpr int kTagShift = 40;
-constexpr unsigned long long kTagMask = (1ull << 22) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;   // ~ a second of waiting at most
-
-__device__ __forceinline__ unsigned long long ld_status(const unsigned long long *p)
-{
-    return *reinterpret_cast<const volatile unsigned long long *>(p);
-}
-__device__ __forceinline__ void st_status(unsigned long long *p, unsigned long long v)
-{
-    *reinterpret_cast<volatile unsigned long long *>(p) = v;
-}
 
 // Number of non-trivial passes (digit not constant over all keys) before
 // `pass`, and whether `pass` itself is non-trivial.  Uniform over the block.
@@ -439,144 +557,98 @@ __device__ int nontrivial_before(const BatchArgs &a, uint32_t pass, bool *self)
         if (q < pass) before += nz > 1;
         else *self = nz > 1;
     }
-    return before;
+    return before & 1 ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(kRadixThreads) k_radix(BatchArgs a, uint32_t pass)
+__global__ void __launch_bounds__(kRadixThreads, 3) k_radix(BatchArgs a, uint32_t pass)
 {
-    static_assert(kRadixThreads == kRadixBins, "one thread per digit");
-    __shared__ unsigned long long s_keys[kRadixTile];
-    __shared__ uint32_t s_whist[kRadixThreads / 32][kRadixBins];
-    __shared__ uint32_t s_tstart[kRadixBins];
-    __shared__ unsigned long long s_gofs[kRadixBins];
-    __shared__ unsigned long long s_scan[kRadixThreads / 32];
-    __shared__ uint32_t s_tile;
-
+    __shared__ radix::PassShared<kRadixThreads, kRadixItems> sh;
     bool self;
-    int before = nontrivial_before(a, pass, &self);
-    if (!self) return;
-    const unsigned long long *src = a.keys[before & 1];
-    unsigned long long *dst = a.keys[(before + 1) & 1];
-    const uint32_t t = threadIdx.x, lane = t & 31, wid = t / 32;
-    const uint32_t shift = a.L.sort_lo + pass * kRadixBits;
-    const uint32_t nbits = min((uint32_t)kRadixBits, a.L.sort_bits - pass * kRadixBits);
-    const uint32_t dmask = (1u << nbits) - 1;
-    const unsigned long long tag = (unsigned long long)(*a.epoch & kTagMask) << kTagShift;
-    unsigned long long *status = a.status + (uint64_t)pass * a.ntiles * kRadixBins;
-
-    for (int w = 0; w < kRadixThreads / 32; w++) s_whist[w][t] = 0;
-    if (t == 0) s_tile = (uint32_t)atomicAdd(&a.ctrl->tile_counter[pass], 1ull);
-    // global start of every digit: exclusive scan of this pass's histogram
-    unsigned long long h = a.hist[pass * kRadixBins + t];
-    unsigned long long incl = h;
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_scan[wid] = incl;
-    __syncthreads();
-    unsigned long long dbase = incl - h;
-    for (uint32_t i = 0; i < wid; i++) dbase += s_scan[i];
-    const uint32_t tile = s_tile;
-    const uint64_t base = (uint64_t)tile * kRadixTile;
-    const uint64_t n = a.nkeys;
-
-    // load: warp w owns keys [w*512, (w+1)*512) of the tile, 32 per round
-    unsigned long long key[kRadixItems];
-    uint32_t rank[kRadixItems];
-    const uint64_t wbase = base + wid * (32 * kRadixItems);
-#pragma unroll
-    for (int i = 0; i < kRadixItems; i++) {
-        uint64_t idx = wbase + i * 32 + lane;
-        key[i] = idx < n ? src[idx] : 0;
-    }
-    // rank within the warp, stable in (round, lane) order
-#pragma unroll
-    for (int i = 0; i < kRadixItems; i++) {
-        uint64_t idx = wbase + i * 32 + lane;
-        bool valid = idx < n;
-        uint32_t d = (uint32_t)(key[i] >> shift) & dmask;
-        unsigned peers = __ballot_sync(kFull, valid);
-        for (uint32_t b = 0; b < nbits; b++) {
-            unsigned bal = __ballot_sync(kFull, (d >> b) & 1);
-            peers &= ((d >> b) & 1) ? bal : ~bal;
-        }
-        uint32_t before_me = __popc(peers & lanemask_lt());
-        uint32_t prior = valid ? s_whist[wid][d] : 0;
-        __syncwarp();
-        if (valid && before_me == 0) s_whist[wid][d] = prior + __popc(peers);
-        __syncwarp();
-        rank[i] = prior + before_me;
-    }
-    __syncthreads();
-    // per digit: exclusive offsets of each warp, and the tile's count
-    uint32_t cnt = 0;
-    for (int w = 0; w < kRadixThreads / 32; w++) {
-        uint32_t c = s_whist[w][t];
-        s_whist[w][t] = cnt;
-        cnt += c;
-    }
-    // publish this tile's aggregate for digit t, then look back
-    unsigned long long *my = status + (uint64_t)tile * kRadixBins + t;
-    if (tile == 0) st_status(my, kFlagPrefix | tag | cnt);
-    else st_status(my, kFlagAgg | tag | cnt);
-    unsigned long long excl = 0;
-    if (tile > 0) {
-        int64_t j = (int64_t)tile - 1;
-        uint32_t spins = 0;
-        bool gave_up = false;
-        while (j >= 0) {
-            unsigned long long s = ld_status(status + (uint64_t)j * kRadixBins + t);
-            if ((s & (kTagMask << kTagShift)) != tag || (s >> 62) == 0) {
-                if (++spins > kSpinLimit) { gave_up = true; break; }
-                __nanosleep(spins < 64 ? 32 : 256);
-                continue;
-            }
-            excl += s & kValueMask;
-            if ((s >> 62) == 2) break;
-            j--;
-        }
-        if (gave_up) atomicOr(&a.ctrl->flags, CF_LOOKBACK_TIMEOUT);
-        st_status(my, kFlagPrefix | tag | ((excl + cnt) & kValueMask));
-    }
-    // tile-local start of every digit
-    uint32_t tincl = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, tincl, o);
-        if (lane >= o) tincl += y;
-    }
-    __syncthreads();
-    if (lane == 31) s_scan[wid] = tincl;
-    __syncthreads();
-    uint32_t tstart = tincl - cnt;
-    for (uint32_t i = 0; i < wid; i++) tstart += (uint32_t)s_scan[i];
-    s_tstart[t] = tstart;
-    s_gofs[t] = dbase + excl;
-    __syncthreads();
-    // scatter into tile order in shared memory, then stream out per digit run
-#pragma unroll
-    for (int i = 0; i < kRadixItems; i++) {
-        uint64_t idx = wbase + i * 32 + lane;
-        if (idx < n) {
-            uint32_t d = (uint32_t)(key[i] >> shift) & dmask;
-            s_keys[s_tstart[d] + s_whist[wid][d] + rank[i]] = key[i];
-        }
-    }
-    __syncthreads();
-    const uint32_t valid_n = (uint32_t)min((uint64_t)kRadixTile, n - base);
-    bool bad = false;
-    for (uint32_t j = t; j < valid_n; j += kRadixThreads) {
-        unsigned long long k = s_keys[j];
-        uint32_t d = (uint32_t)(k >> shift) & dmask;
-        unsigned long long pos = s_gofs[d] + (j - s_tstart[d]);
-        if (pos < n) dst[pos] = k;
-        else bad = true;              // histogram and keys disagree: never write past the buffer
-    }
-    if (bad) atomicOr(&a.ctrl->flags, CF_EMIT_OVERFLOW);
+    const int before = nontrivial_before(a, pass, &self);
+    if (!self) return;                       // constant digit: the pass would not move any key
+    radix::PassArgs A;
+    A.src = a.keys[before];
+    A.dst = a.keys[before ^ 1];
+    A.n = a.nkeys;
+    A.shift = a.L.sort_lo + pass * kRadixBits;
+    A.nbits = min((uint32_t)kRadixBits, a.L.sort_bits - pass * kRadixBits);
+    A.hist = a.hist + pass * kRadixBins;
+    A.status = a.status + (uint64_t)pass * a.ntiles * kRadixBins;
+    A.tile_counter = &a.ctrl->tile_counter[pass];
+    A.tag = (unsigned long long)(*a.epoch & radix::kTagMask) << radix::kTagShift;
+    A.flags = &a.ctrl->flags;
+    radix::pass<kRadixThreads, kRadixItems>(A, sh);
 }
 
 // ------------------------------------------------------------- detection
+// A segment (equal proto | phase | array | index) is racy iff it holds a
+// write and two distinct tids (Definition 1: a writer and a second,
+// different accessor).  Per contiguous piece of a segment the detector keeps
+// (min tid, max tid, any write, whether the piece holds the segment's first
+// key, that key's position): an associative summary, combined across keys
+// by a segmented scan (segment starts are the scan's reset flags).
 
+__device__ __forceinline__ Agg agg_empty() { return Agg{0xFFFFFFFFu, 0u, 0u, kNone}; }
+
+__device__ __forceinline__ Agg agg_key(unsigned long long k, uint32_t tid_mask, bool head, unsigned long long pos)
+{
+    uint32_t t = (uint32_t)(k >> 1) & tid_mask;
+    return Agg{t, t, (uint32_t)(k & 1) | (head ? 2u : 0u) | 4u, head ? pos : kNone};
+}
+
+// a is the left piece, b the right piece of the same segment
+__device__ __forceinline__ Agg agg_cat(const Agg &a, const Agg &b)
+{
+    if (!(a.bits & 4)) return b;
+    if (!(b.bits & 4)) return a;
+    return Agg{min(a.mint, b.mint), max(a.maxt, b.maxt), (a.bits | (b.bits & 1)), a.start};
+}
+
+__device__ __forceinline__ bool agg_racy(const Agg &a) { return (a.bits & 1) && a.mint != a.maxt; }
+
+struct SegVal {
+    uint32_t f;                 // a segment starts inside this range
+    Agg v;                      // summary of the range's last segment piece
+};
+
+__device__ __forceinline__ SegVal seg_op(const SegVal &l, const SegVal &r)
+{
+    return SegVal{l.f | r.f, r.f ? r.v : agg_cat(l.v, r.v)};
+}
+
+__device__ __forceinline__ SegVal seg_shfl_up(const SegVal &x, int o)
+{
+    SegVal y;
+    y.f = __shfl_up_sync(kFull, x.f, o);
+    y.v.mint = __shfl_up_sync(kFull, x.v.mint, o);
+    y.v.maxt = __shfl_up_sync(kFull, x.v.maxt, o);
+    y.v.bits = __shfl_up_sync(kFull, x.v.bits, o);
+    y.v.start = __shfl_up_sync(kFull, x.v.start, o);
+    return y;
+}
+
+// Exclusive segmented scan over the threads of a block (all threads call).
+// s_warp: shared scratch of blockDim/32 entries.
+__device__ SegVal block_seg_exclusive(SegVal x, SegVal *s_warp)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    SegVal inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        SegVal y = seg_shfl_up(inc, o);
+        if (lane >= o) inc = seg_op(y, inc);
+    }
+    SegVal exc = seg_shfl_up(inc, 1);
+    if (lane == 0) exc = SegVal{0, agg_empty()};
+    if (lane == 31) s_warp[wid] = inc;
+    __syncthreads();
+    SegVal pre{0, agg_empty()};
+    for (int w = 0; w < wid && w < nw; w++) pre = seg_op(pre, s_warp[w]);
+    __syncthreads();
+    return seg_op(pre, exc);
+}
+
+// Sorted-key buffer parity: passes whose digit was constant did not move
+// the keys.  Uniform over the block.
 __device__ __forceinline__ int sorted_parity(const BatchArgs &a)
 {
     int before = 0;
@@ -587,42 +659,141 @@ __device__ __forceinline__ int sorted_parity(const BatchArgs &a)
     return before & 1;
 }
 
+struct DetectShared {
+    unsigned long long keys[kDetectTile + kDetectTile / 16];   // one pad word per 16 keys
+    SegVal warp[kDetectThreads / 32];
+    unsigned long long best;
+};
+
+__device__ __forceinline__ uint32_t pad16(uint32_t i) { return i + (i >> 4); }
+
+// Records a complete racy segment of protocol `proto` starting at `pos`.
+__device__ __forceinline__ void note_racy(const BatchArgs &a, uint32_t proto, uint32_t tile_proto,
+                                          unsigned long long pos, unsigned long long &local_best)
+{
+    if (proto == tile_proto) local_best = min(local_best, pos);
+    else if (proto < a.nprotos) atomicMin(&a.best_pos[proto], pos);
+}
+
+// One 4096-key tile per block: complete segments inside the tile are judged
+// here; the pieces of segments that cross the tile's edges go to the tile
+// record for k_resolve.
 __global__ void __launch_bounds__(kDetectThreads) k_detect(BatchArgs a)
 {
-    __shared__ unsigned long long s_keys[kDetectTile + 1];
+    __shared__ DetectShared sh;
     const unsigned long long *keys = a.keys[sorted_parity(a)];
     const uint64_t n = a.nkeys;
     const uint32_t lo = a.L.sort_lo;
     const uint32_t proto_shift = a.L.sort_bits - a.L.proto_bits;
     const uint32_t tid_mask = a.L.tid_bits ? (1u << a.L.tid_bits) - 1 : 0;
-    for (uint64_t base = (uint64_t)blockIdx.x * kDetectTile; base < n; base += (uint64_t)gridDim.x * kDetectTile) {
-        const uint32_t valid = (uint32_t)min((uint64_t)kDetectTile, n - base);
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < valid; i += kDetectThreads) s_keys[i + 1] = keys[base + i];
-        if (threadIdx.x == 0) s_keys[0] = base ? keys[base - 1] : 0;
-        __syncthreads();
-        for (uint32_t r = 0; r < kDetectItems; r++) {
-            uint32_t i = threadIdx.x * kDetectItems + r;
-            if (i >= valid) break;
-            unsigned long long k = s_keys[i + 1];
-            unsigned long long seg = k >> lo;
-            if (base + i > 0 && (s_keys[i] >> lo) == seg) continue;     // not a segment start
-            // walk the segment: racy iff it has a write and two distinct tids
-            uint32_t first = (uint32_t)(k >> 1) & tid_mask;
-            bool writes = k & 1, two = false;
-            uint64_t j = base + i + 1;
-            while (j < n && !(writes && two)) {
-                unsigned long long x = (j - base < valid) ? s_keys[j - base + 1] : __ldg(keys + j);
-                if ((x >> lo) != seg) break;
-                writes |= x & 1;
-                two |= (((uint32_t)(x >> 1) & tid_mask) != first);
-                j++;
+    const uint64_t base = (uint64_t)blockIdx.x * kDetectTile;
+    const uint32_t valid = (uint32_t)min((uint64_t)kDetectTile, n - base);
+    for (uint32_t i = threadIdx.x; i < valid; i += kDetectThreads) sh.keys[pad16(i)] = keys[base + i];
+    if (threadIdx.x == 0) sh.best = kNone;
+    __syncthreads();
+    const unsigned long long prev_seg = base ? (keys[base - 1] >> lo) : ~0ull;
+    const bool has_next = base + valid < n;
+    const unsigned long long next_seg = has_next ? (keys[base + valid] >> lo) : ~0ull;
+    const unsigned long long first_seg = sh.keys[0] >> lo;
+    const uint32_t tile_proto = a.L.proto_bits ? (uint32_t)(first_seg >> proto_shift) : 0;
+
+    // this thread's keys: [i0, i1) of the tile
+    const uint32_t i0 = threadIdx.x * kDetectItems;
+    const uint32_t i1 = min(valid, i0 + kDetectItems);
+    // pass 1: the thread's summary for the scan
+    SegVal mine{0, agg_empty()};
+    unsigned long long pseg = i0 == 0 ? prev_seg : (i0 < valid ? sh.keys[pad16(i0 - 1)] >> lo : 0);
+    for (uint32_t i = i0; i < i1; i++) {
+        unsigned long long k = sh.keys[pad16(i)];
+        unsigned long long sg = k >> lo;
+        bool head = (base + i == 0) || sg != pseg;
+        SegVal e{head ? 1u : 0u, agg_key(k, tid_mask, head, base + i)};
+        mine = seg_op(mine, e);
+        pseg = sg;
+    }
+    SegVal carry = block_seg_exclusive(mine, sh.warp);
+    // pass 2: close every segment that ends inside the tile
+    unsigned long long local_best = kNone;
+    Agg run = carry.v;
+    unsigned long long run_seg = i0 == 0 ? prev_seg : (i0 < valid ? sh.keys[pad16(i0 - 1)] >> lo : 0);
+    TileRec *rec = a.trec + blockIdx.x;
+    for (uint32_t i = i0; i < i1; i++) {
+        unsigned long long k = sh.keys[pad16(i)];
+        unsigned long long sg = k >> lo;
+        bool head = (base + i == 0) || sg != run_seg;
+        if (head) {
+            if (run.bits & 4) {            // the piece before i is a whole segment or the tile's first one
+                if (run.bits & 2) {
+                    if (agg_racy(run))
+                        note_racy(a, a.L.proto_bits ? (uint32_t)(run_seg >> proto_shift) : 0, tile_proto,
+                                  run.start, local_best);
+                } else {
+                    rec->first = run;      // continues from the previous tile, ends here
+                }
             }
-            if (writes && two) {
-                uint32_t proto = a.L.proto_bits ? (uint32_t)(seg >> proto_shift) : 0;
-                if (proto < a.nprotos) atomicMin(&a.best_pos[proto], (unsigned long long)(base + i));
+            run = agg_key(k, tid_mask, true, base + i);
+        } else {
+            run = agg_cat(run, agg_key(k, tid_mask, false, base + i));
+        }
+        run_seg = sg;
+    }
+    if (i1 == valid && i0 < valid) {
+        // the thread holding the tile's last key settles the open segment
+        uint32_t flags = 0;
+        if (base && prev_seg == first_seg) flags |= TR_STARTS_CONT;
+        if (has_next && next_seg == run_seg) flags |= TR_ENDS_CONT;
+        if (flags & TR_ENDS_CONT) {
+            if (run.bits & 2) rec->last = run;
+            else { rec->first = run; flags |= TR_SINGLE; }
+        } else if (run.bits & 2) {
+            if (agg_racy(run))
+                note_racy(a, a.L.proto_bits ? (uint32_t)(run_seg >> proto_shift) : 0, tile_proto, run.start,
+                          local_best);
+        } else {
+            rec->first = run;              // the continuing segment ends at the tile's end
+        }
+        rec->first_seg = first_seg;
+        rec->last_seg = run_seg;
+        rec->flags = flags;
+    }
+    if (local_best != kNone) atomicMin(&sh.best, local_best);
+    __syncthreads();
+    if (threadIdx.x == 0 && sh.best != kNone && tile_proto < a.nprotos) atomicMin(&a.best_pos[tile_proto], sh.best);
+}
+
+// One block settles every segment that crosses tile edges: a segment opened
+// as the last piece of tile r (TR_ENDS_CONT without TR_SINGLE) runs through
+// single tiles and ends in the first piece of the next tile that is not
+// single.  Segmented scan over tiles, each thread a contiguous chunk.
+__global__ void __launch_bounds__(1024) k_resolve(BatchArgs a)
+{
+    __shared__ SegVal s_warp[32];
+    const uint32_t nt = a.ndtiles;
+    const uint32_t per = (nt + blockDim.x - 1) / blockDim.x;
+    const uint32_t r0 = min(nt, threadIdx.x * per), r1 = min(nt, r0 + per);
+    const uint32_t proto_shift = a.L.sort_bits - a.L.proto_bits;
+    auto element = [&](uint32_t r, const TileRec &t) {
+        bool single = t.flags & TR_SINGLE;
+        SegVal e;
+        e.f = single ? 0u : 1u;
+        e.v = single ? t.first : ((t.flags & TR_ENDS_CONT) ? t.last : agg_empty());
+        return e;
+    };
+    SegVal mine{0, agg_empty()};
+    for (uint32_t r = r0; r < r1; r++) mine = seg_op(mine, element(r, a.trec[r]));
+    SegVal carry = block_seg_exclusive(mine, s_warp);
+    Agg run = carry.v;
+    for (uint32_t r = r0; r < r1; r++) {
+        const TileRec t = a.trec[r];
+        if (t.flags & TR_SINGLE) { run = agg_cat(run, t.first); continue; }
+        if (t.flags & TR_STARTS_CONT) {
+            Agg whole = agg_cat(run, t.first);
+            if ((whole.bits & 2) && agg_racy(whole)) {
+                uint32_t proto = a.L.proto_bits ? (uint32_t)(t.first_seg >> proto_shift) : 0;
+                if (proto < a.nprotos) atomicMin(&a.best_pos[proto], whole.start);
             }
         }
+        run = (t.flags & TR_ENDS_CONT) ? t.last : agg_empty();
     }
 }
 
@@ -633,41 +804,79 @@ __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t 
     else if (x < s) s = x;
 }
 
-// Parity of the buffer holding the sorted keys, computed by one warp.
-__device__ __forceinline__ int sorted_parity_warp(const BatchArgs &a)
+// One block per protocol: evaluation error, else barrier divergence, else the
+// witness of the first racy segment.  The witness segment is found by binary
+// search for its end, then reduced by the whole block: the two smallest
+// distinct tids of all its accesses and of its writes.
+__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(BatchArgs a)
 {
-    const uint32_t lane = threadIdx.x & 31;
-    int before = 0;
-    for (uint32_t q = 0; q < a.L.passes; q++) {
-        int nz = 0;
-        for (uint32_t d = lane; d < kRadixBins; d += 32) nz += a.hist[q * kRadixBins + d] != 0;
-        nz = __reduce_add_sync(kFull, (unsigned)nz);
-        before += nz > 1;
-    }
-    return before & 1;
-}
-
-// One warp per protocol: evaluation error, else barrier divergence, else the
-// witness of the first racy segment (re-reduced here: the two smallest
-// distinct tids of all accesses and of the writes).
-__global__ void k_finalize(BatchArgs a)
-{
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (p == 0 && lane == 0 && a.ctrl->total != a.nkeys) atomicOr(&a.ctrl->flags, CF_COUNT_MISMATCH);
-    if (p >= a.nprotos) return;
+    __shared__ uint32_t s_red[4][kFinalizeThreads / 32];
+    __shared__ unsigned long long s_end;
+    const uint32_t p = blockIdx.x;
+    const uint32_t t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int parity = sorted_parity(a);
+    if (p == 0 && t == 0 && a.ctrl->total != a.nkeys) atomicOr(&a.ctrl->flags, CF_COUNT_MISMATCH);
     const DevProto P = a.protos[p];
     const KeyLayout L = a.L;
     DevResult r = {};
     r.verdict = -1;
     r.tuples = a.ptuples[p];
     const unsigned long long ek = a.err_key[p];
+    const unsigned long long bp = a.best_pos[p];
+    const uint32_t dt = a.div_tid[p];
+    if (ek == kNone && P.nthreads && dt == 0xFFFFFFFFu && bp != kNone) {
+        const unsigned long long *keys = a.keys[parity];
+        const uint32_t tid_mask = L.tid_bits ? (1u << L.tid_bits) - 1 : 0;
+        const unsigned long long seg = keys[bp] >> L.sort_lo;
+        if (t == 0) {               // first position after the segment
+            unsigned long long lo = bp + 1, hi = a.nkeys;
+            while (lo < hi) {
+                unsigned long long mid = lo + (hi - lo) / 2;
+                if ((keys[mid] >> L.sort_lo) == seg) lo = mid + 1; else hi = mid;
+            }
+            s_end = lo;
+        }
+        __syncthreads();
+        const unsigned long long end = s_end;
+        uint32_t t0 = 0xFFFFFFFFu, t1 = 0xFFFFFFFFu, w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
+        for (unsigned long long j = bp + t; j < end; j += kFinalizeThreads) {
+            unsigned long long x = keys[j];
+            uint32_t tid = (uint32_t)(x >> 1) & tid_mask;
+            two_smallest(t0, t1, tid);
+            if (x & 1) two_smallest(w0, w1, tid);
+        }
+        for (int o = 16; o; o >>= 1) {
+            uint32_t u0 = __shfl_xor_sync(kFull, t0, o), u1 = __shfl_xor_sync(kFull, t1, o);
+            uint32_t v0 = __shfl_xor_sync(kFull, w0, o), v1 = __shfl_xor_sync(kFull, w1, o);
+            two_smallest(t0, t1, u0); two_smallest(t0, t1, u1);
+            two_smallest(w0, w1, v0); two_smallest(w0, w1, v1);
+        }
+        if (lane == 0) { s_red[0][wid] = t0; s_red[1][wid] = t1; s_red[2][wid] = w0; s_red[3][wid] = w1; }
+        __syncthreads();
+        if (t == 0) {
+            for (int w = 1; w < kFinalizeThreads / 32; w++) {
+                two_smallest(t0, t1, s_red[0][w]); two_smallest(t0, t1, s_red[1][w]);
+                two_smallest(w0, w1, s_red[2][w]); two_smallest(w0, w1, s_red[3][w]);
+            }
+            r.verdict = 1;
+            r.phases = a.totsyn[P.tid_off] + 1;
+            r.sync_count_0 = a.totsyn[P.tid_off];
+            r.index = seg & (L.idx_bits ? (~0ull >> (64 - L.idx_bits)) : 0);
+            r.loc = (uint32_t)((seg >> L.idx_bits) & (L.loc_bits ? (~0ull >> (64 - L.loc_bits)) : 0));
+            r.phase = (uint32_t)((seg >> (L.idx_bits + L.loc_bits)) & (L.phase_bits ? (~0ull >> (64 - L.phase_bits)) : 0));
+            r.tid_i = t0;
+            if (w0 == t0) { r.tid_j = t1; r.i_writes = 1; r.j_writes = (w1 == t1); }
+            else { r.tid_j = w0; r.i_writes = 0; r.j_writes = 1; }
+            a.results[p] = r;
+        }
+        return;
+    }
+    if (t != 0) return;
     if (ek != kNone) {
         uint32_t tid = (uint32_t)(ek >> 32), k = (uint32_t)ek;
         unsigned long long e = a.erro[P.lane_off + (uint64_t)k * P.nthreads + tid];
         unsigned long long pre = 0;
-        for (uint32_t q = lane; q < k; q += 32) pre += a.cnt[P.lane_off + (uint64_t)q * P.nthreads + tid];
-        for (int o = 16; o; o >>= 1) pre += __shfl_xor_sync(kFull, pre, o);
+        for (uint32_t q = 0; q < k; q++) pre += a.cnt[P.lane_off + (uint64_t)q * P.nthreads + tid];
         r.status = (e & 0xff) == kErrOob ? -9 : -10;
         r.err_tid = tid;
         r.err_ordinal = pre + (e >> 8);
@@ -678,46 +887,15 @@ __global__ void k_finalize(BatchArgs a)
         const uint32_t s0 = a.totsyn[P.tid_off];
         r.phases = s0 + 1;
         r.sync_count_0 = s0;
-        const uint32_t dt = a.div_tid[p];
-        const unsigned long long bp = a.best_pos[p];
         if (dt != 0xFFFFFFFFu) {
             r.verdict = 2;
             r.div_tid = dt;
             r.sync_count_div = a.totsyn[P.tid_off + dt];
-        } else if (bp != kNone) {
-            const unsigned long long *keys = a.keys[sorted_parity_warp(a)];
-            const uint32_t tid_mask = L.tid_bits ? (1u << L.tid_bits) - 1 : 0;
-            const unsigned long long seg = keys[bp] >> L.sort_lo;
-            uint32_t t0 = 0xFFFFFFFFu, t1 = 0xFFFFFFFFu, w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
-            for (uint64_t b = bp;; b += 32) {
-                uint64_t j = b + lane;
-                unsigned long long x = j < a.nkeys ? keys[j] : 0;
-                bool in = j < a.nkeys && (x >> L.sort_lo) == seg;
-                if (in) {
-                    uint32_t tid = (uint32_t)(x >> 1) & tid_mask;
-                    two_smallest(t0, t1, tid);
-                    if (x & 1) two_smallest(w0, w1, tid);
-                }
-                if (__ballot_sync(kFull, !in)) break;
-            }
-            for (int o = 16; o; o >>= 1) {
-                uint32_t u0 = __shfl_xor_sync(kFull, t0, o), u1 = __shfl_xor_sync(kFull, t1, o);
-                uint32_t v0 = __shfl_xor_sync(kFull, w0, o), v1 = __shfl_xor_sync(kFull, w1, o);
-                two_smallest(t0, t1, u0); two_smallest(t0, t1, u1);
-                two_smallest(w0, w1, v0); two_smallest(w0, w1, v1);
-            }
-            r.verdict = 1;
-            r.index = seg & (L.idx_bits ? (~0ull >> (64 - L.idx_bits)) : 0);
-            r.loc = (uint32_t)((seg >> L.idx_bits) & (L.loc_bits ? (~0ull >> (64 - L.loc_bits)) : 0));
-            r.phase = (uint32_t)((seg >> (L.idx_bits + L.loc_bits)) & (L.phase_bits ? (~0ull >> (64 - L.phase_bits)) : 0));
-            r.tid_i = t0;
-            if (w0 == t0) { r.tid_j = t1; r.i_writes = 1; r.j_writes = (w1 == t1); }
-            else { r.tid_j = w0; r.i_writes = 0; r.j_writes = 1; }
         } else {
             r.verdict = 0;
         }
     }
-    if (lane == 0) a.results[p] = r;
+    a.results[p] = r;
 }
 
 }  // namespace
@@ -749,9 +927,10 @@ cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_
     mark(ev, nev, s);
     k_init<<<(unsigned)((init_n + 255) / 256), 256, 0, s>>>(a);
     mark(ev, nev, s);
-    k_interp<false><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+    if (a.has_narrow) k_interp<false, false><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+    if (a.has_wide) k_interp<false, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
     mark(ev, nev, s);
-    uint32_t col_blocks = (uint32_t)((a.ncols + kScanThreads - 1) / kScanThreads);
+    uint32_t col_blocks = (uint32_t)((a.ncols + 31) / 32);
     k_scan<<<col_blocks + a.nwblocks, kScanThreads, 0, s>>>(a, col_blocks);
     mark(ev, nev, s);
     return cudaGetLastError();
@@ -759,17 +938,19 @@ cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_
 
 cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev)
 {
-    k_interp<true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+    if (a.has_narrow) k_interp<true, false><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+    if (a.has_wide) k_interp<true, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
     mark(ev, nev, s);
     for (uint32_t q = 0; q < a.L.passes; q++) {
         if (a.ntiles) k_radix<<<a.ntiles, kRadixThreads, 0, s>>>(a, q);
         mark(ev, nev, s);
     }
-    uint64_t dt = (a.nkeys + kDetectTile - 1) / kDetectTile;
-    uint64_t cap = (uint64_t)sms * 8;
-    if (dt) k_detect<<<(unsigned)(dt < cap ? dt : cap), kDetectThreads, 0, s>>>(a);
+    if (a.ndtiles) {
+        k_detect<<<a.ndtiles, kDetectThreads, 0, s>>>(a);
+        k_resolve<<<1, 1024, 0, s>>>(a);
+    }
     mark(ev, nev, s);
-    k_finalize<<<(a.nprotos + 7) / 8, 256, 0, s>>>(a);
+    k_finalize<<<a.nprotos, kFinalizeThreads, 0, s>>>(a);
     mark(ev, nev, s);
     return cudaGetLastError();
 }

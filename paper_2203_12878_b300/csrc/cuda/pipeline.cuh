@@ -7,6 +7,28 @@
 
 namespace drf {
 
+// Summary of a contiguous piece of one segment of equal sort keys, and the
+// per-tile record of the pieces that touch a detection tile's edges.
+struct Agg {
+    uint32_t mint, maxt;
+    uint32_t bits;              // 1: any write, 2: holds the segment head, 4: non-empty
+    unsigned long long start;   // sorted position of the head (valid with bit 2)
+};
+
+struct TileRec {
+    unsigned long long first_seg, last_seg;   // sort keys of the tile's first and last key
+    Agg first;                                // in-tile piece of the segment continuing from the previous tile
+    Agg last;                                 // the tile's last segment piece, when it continues into the next tile
+    uint32_t flags;                           // TR_*
+    uint32_t pad;
+};
+
+enum : uint32_t {
+    TR_STARTS_CONT = 1,   // the tile's first key continues a segment of the previous tile
+    TR_ENDS_CONT = 2,     // the tile's last segment continues into the next tile
+    TR_SINGLE = 4,        // the tile lies inside one segment that crosses both edges
+};
+
 // Everything the kernels of one launch touch.  Device pointers unless noted.
 struct BatchArgs {
     // device programs of the batch
@@ -18,6 +40,7 @@ struct BatchArgs {
     const WarpItem *witems;
     uint32_t nwitems;
     uint32_t nprotos;
+    uint32_t has_narrow, has_wide;   // protocols with 32-bit / 64-bit arithmetic present
     uint64_t ncols;                  // sum of thread counts (per-thread arrays)
     // per (item, thread)
     uint32_t *cnt;                   // accesses
@@ -37,6 +60,8 @@ struct BatchArgs {
     unsigned long long *hist;        // [kMaxPasses][kRadixBins]
     unsigned long long *status;      // [passes][ntiles][kRadixBins] look-back words
     uint32_t ntiles;
+    TileRec *trec;                   // [ndtiles] detection tile records
+    uint32_t ndtiles;
     // per protocol
     unsigned long long *err_key;     // min (tid << 32 | item) with an evaluation error
     uint32_t *div_tid;               // min tid whose sync count differs from thread 0's
@@ -52,12 +77,14 @@ constexpr int kRadixThreads = 256;
 constexpr int kRadixItems = 16;
 constexpr int kRadixTile = kRadixThreads * kRadixItems;     // 4096 keys
 constexpr int kDetectThreads = 256;
-constexpr int kDetectItems = 8;
-constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 2048 keys
+constexpr int kDetectItems = 16;
+constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 4096 keys
+constexpr int kFinalizeThreads = 128;
 constexpr int kScanThreads = 256;
 constexpr int kWScanPerBlock = 4096;                        // warp-items per scan block
 
 inline uint32_t radix_tiles(uint64_t n) { return (uint32_t)((n + kRadixTile - 1) / kRadixTile); }
+inline uint32_t detect_tiles(uint64_t n) { return (uint32_t)((n + kDetectTile - 1) / kDetectTile); }
 
 // Stage launchers (all asynchronous on `s`).  Each returns cudaGetLastError().
 // When ev is non-null, an event is recorded before the first kernel of

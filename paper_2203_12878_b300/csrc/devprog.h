@@ -34,7 +34,21 @@ enum : uint8_t {
     I_ENDLOOP = 4,   // a: variable register, c: first pc of the body
     I_IF = 5,        // c: condition expression, d: pc to continue at when false
     I_JUMP = 6,      // c: target pc
+    // An innermost loop whose body holds only accesses and syncs, with every
+    // index an affine function of the loop variable (plus a constant
+    // remainder / division): a: variable register, b: syncs per iteration (< 256),
+    // c: lo expression, d: hi expression, e: number m of I_FASTACC entries
+    // that follow.  The count pass takes trip * m accesses in one step.
+    I_FASTLOOP = 7,
+    // a: AF_WRITE | post kind << 2 (FP_*), b: array, c: expression of the
+    // index without its loop-variable term, d: xcode offset of the words
+    // [coefficient of the loop variable, post-op constant], e: syncs before
+    // this access within one iteration
+    I_FASTACC = 8,
 };
+
+enum : uint8_t { FP_NONE = 0, FP_MASK = 1, FP_MOD = 2, FP_DIV = 3 };
+constexpr uint32_t kFastMax = 4;    // accesses per fast loop body
 
 enum : uint8_t {
     AF_WRITE = 1,         // access mode: write
@@ -75,7 +89,7 @@ struct ItemDesc {
     uint32_t start_pc;
     uint32_t stop_pc;
     uint16_t nsplit;
-    uint16_t chunked;
+    uint16_t chunked;               // 1: chunk of an I_LOOP, 2: chunk of an I_FASTLOOP (start_pc is the loop)
     uint32_t chunk;
     uint32_t split_pc[kMaxSplit];   // pcs of the split I_LOOP instructions
     uint32_t j[kMaxSplit];          // iteration index (or chunk index, innermost chunked level)

@@ -374,7 +374,10 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
     if (!plan) return DRF_E_INVALID_ARG;
     if (tuples) *tuples = plan->tuples;
     if (sort_passes) *sort_passes = plan->host.L.passes;
-    if (kernels_per_launch) *kernels_per_launch = 6 + plan->host.L.passes;
+    if (kernels_per_launch) {
+        uint32_t widths = plan->dev.args.has_narrow + plan->dev.args.has_wide;
+        *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes;   // init, 2x interp, scan, passes, detect, resolve, finalize
+    }
     if (sort_bits) *sort_bits = plan->host.L.sort_bits;
     return DRF_OK;
 }

@@ -94,7 +94,7 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
 DeviceBatch::~DeviceBatch()
 {
     DevBuf *all[] = {&insns, &xcode, &items, &protos, &cells, &witems, &cnt, &syn, &phs, &erro, &totsyn,
-                     &wcnt, &wbase, &blocksum, &keys0, &keys1, &hist, &status, &err_key, &div_tid,
+                     &wcnt, &wbase, &blocksum, &keys0, &keys1, &hist, &status, &trec, &err_key, &div_tid,
                      &best_pos, &ptuples, &results, &ctrl, &epoch};
     for (DevBuf *b : all) release(*b, &in_use);
 }
@@ -152,6 +152,8 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.witems = (const WarpItem *)witems.p;
     a.nwitems = (uint32_t)nw;
     a.nprotos = (uint32_t)np;
+    a.has_narrow = a.has_wide = 0;
+    for (const DevProto &d : b.protos) (d.wide ? a.has_wide : a.has_narrow) = 1;
     a.ncols = b.ncols;
     a.cnt = (uint32_t *)cnt.p;
     a.syn = (uint32_t *)syn.p;
@@ -185,8 +187,10 @@ Error DeviceBatch::size_keys(uint64_t n, cudaStream_t s)
     const size_t kb = std::max<uint64_t>(n, 1) * 8;
     const size_t sb = std::max<size_t>((size_t)args.L.passes * tiles * kRadixBins * 8, 16);
     size_t old_status = status.cap;
+    const uint32_t dtiles = detect_tiles(n);
     bool ok = ensure(keys0, kb, &in_use, limit) && ensure(keys1, kb, &in_use, limit) &&
-              ensure(status, sb, &in_use, limit);
+              ensure(status, sb, &in_use, limit) &&
+              ensure(trec, std::max<size_t>((size_t)dtiles * sizeof(TileRec), 16), &in_use, limit);
     if (!ok) {
         cudaGetLastError();
         return Error::make(S_NOMEM, "device allocation for " + std::to_string(n) + " access keys failed");
@@ -199,6 +203,8 @@ Error DeviceBatch::size_keys(uint64_t n, cudaStream_t s)
     }
     args.nkeys = n;
     args.ntiles = tiles;
+    args.ndtiles = dtiles;
+    args.trec = (TileRec *)trec.p;
     args.keys[0] = (unsigned long long *)keys0.p;
     args.keys[1] = (unsigned long long *)keys1.p;
     args.status = (unsigned long long *)status.p;

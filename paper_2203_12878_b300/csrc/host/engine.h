@@ -45,7 +45,7 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out);
 struct DeviceBatch {
     DevBuf insns, xcode, items, protos, cells, witems;
     DevBuf cnt, syn, phs, erro, totsyn, wcnt, wbase, blocksum;
-    DevBuf keys0, keys1, hist, status;
+    DevBuf keys0, keys1, hist, status, trec;
     DevBuf err_key, div_tid, best_pos, ptuples, results, ctrl, epoch;
     size_t in_use = 0;
     uint64_t limit = 0;

@@ -297,25 +297,27 @@ struct Lowerer {
     void word(uint8_t op, int64_t arg = 0) { xcode.push_back((uint64_t)op | ((uint64_t)arg << 8)); }
     void lit(int64_t v) { xcode.push_back((uint64_t)v); }
 
+    void emit_linear(const Lin &l)
+    {
+        std::vector<std::pair<uint32_t, i128>> terms;
+        for (auto &t : l.terms) if (t.second != 0) terms.push_back(t);
+        if (terms.empty()) { word(X_CONST); lit((int64_t)l.c0); return; }
+        if (terms.size() == 1 && terms[0].second == 1 && l.c0 == 0) {
+            if (terms[0].first == kAffTid) word(X_TID);
+            else word(X_VAR, terms[0].first);
+            return;
+        }
+        word(X_AFF, (int64_t)terms.size());
+        for (auto &t : terms) { lit(t.first); lit((int64_t)t.second); }
+        lit((int64_t)l.c0);
+    }
+
     // Emits code for e; depth is the stack height before it runs.
     void emit_expr(const Expr &e, int depth)
     {
         if (depth + 1 > max_stack) max_stack = depth + 1;
         Lin l = linear(e);
-        if (l.ok) {
-            std::vector<std::pair<uint32_t, i128>> terms;
-            for (auto &t : l.terms) if (t.second != 0) terms.push_back(t);
-            if (terms.empty()) { word(X_CONST); lit((int64_t)l.c0); return; }
-            if (terms.size() == 1 && terms[0].second == 1 && l.c0 == 0) {
-                if (terms[0].first == kAffTid) word(X_TID);
-                else word(X_VAR, terms[0].first);
-                return;
-            }
-            word(X_AFF, (int64_t)terms.size());
-            for (auto &t : terms) { lit(t.first); lit((int64_t)t.second); }
-            lit((int64_t)l.c0);
-            return;
-        }
+        if (l.ok) { emit_linear(l); return; }
         switch (e.op) {
         case EOp::Neg: emit_expr(*e.a, depth); word(X_NEG); return;
         case EOp::Div:
@@ -385,6 +387,67 @@ struct Lowerer {
     }
 
     std::unordered_map<const Stmt *, std::pair<int32_t, int32_t>> range;   // [begin, end) pcs
+    std::unordered_map<const Stmt *, bool> fast;                           // loops lowered to I_FASTLOOP
+
+    // An innermost loop whose body is only accesses (whose indices the count
+    // pass need not evaluate) and syncs, each index linear in the variables
+    // with at most a constant remainder or division on top, becomes one
+    // I_FASTLOOP followed by its accesses.
+    bool try_fast(const Stmt &s, int depth)
+    {
+        std::vector<const Stmt *> body;
+        if (s.body->op == SOp::Seq) for (auto &it : s.body->items) body.push_back(it.get());
+        else body.push_back(s.body.get());
+        struct Acc { const Stmt *st; Lin rest; i128 coef; uint8_t post; i128 pconst; uint32_t phase_off; };
+        std::vector<Acc> accs;
+        uint32_t syncs = 0;
+        const uint32_t reg = (uint32_t)depth;
+        for (const Stmt *b : body) {
+            if (b->op == SOp::Skip) continue;
+            if (b->op == SOp::Sync) { if (++syncs > 255) return false; continue; }
+            if (b->op != SOp::Access || count_eval.at(b)) return false;
+            const Expr *e = b->index.get();
+            uint8_t post = FP_NONE;
+            i128 pc = 0;
+            if (e->op == EOp::Mod || e->op == EOp::Div) {
+                Lin d = linear(*e->b);
+                if (!d.ok || !d.terms.empty() || d.c0 == 0) return false;
+                if (e->op == EOp::Mod) {
+                    if (d.c0 > 0 && (d.c0 & (d.c0 - 1)) == 0) { post = FP_MASK; pc = d.c0 - 1; }
+                    else { post = FP_MOD; pc = d.c0; }
+                } else {
+                    post = FP_DIV; pc = d.c0;
+                }
+                e = e->a.get();
+            }
+            Lin l = linear(*e);
+            if (!l.ok) return false;
+            Acc a{b, Lin{}, 0, post, pc, syncs};
+            a.rest.ok = true;
+            a.rest.c0 = l.c0;
+            for (auto &t : l.terms) {
+                if (t.first == reg) a.coef += t.second;
+                else a.rest.terms.push_back(t);
+            }
+            accs.push_back(a);
+        }
+        if (accs.empty() || accs.size() > kFastMax) return false;
+        int32_t lo = expr_code(*s.lo), hi = expr_code(*s.hi);
+        emit(I_FASTLOOP, (uint8_t)depth, (uint16_t)syncs, lo, hi, (int32_t)accs.size());
+        for (const Acc &a : accs) {
+            int32_t rest = (int32_t)xcode.size();
+            if (max_stack < 1) max_stack = 1;
+            emit_linear(a.rest);
+            word(X_RET);
+            int32_t consts = (int32_t)xcode.size();
+            lit((int64_t)a.coef);
+            lit((int64_t)a.pconst);
+            uint8_t flags = (uint8_t)((a.st->write ? AF_WRITE : 0) | (a.post << 2));
+            emit(I_FASTACC, flags, a.st->loc, rest, consts, (int32_t)a.phase_off);
+        }
+        fast[&s] = true;
+        return true;
+    }
 
     void stmt(const Stmt &s, int depth)
     {
@@ -425,6 +488,7 @@ struct Lowerer {
         case SOp::ForS: {
             if (depth >= kMaxVars) { too_deep = true; return; }
             slot_reg[s.slot] = depth;
+            if (try_fast(s, depth)) return;
             int32_t lo = expr_code(*s.lo), hi = expr_code(*s.hi);
             int32_t lp = emit(I_LOOP, (uint8_t)depth, 0, lo, hi);
             int32_t body = pc();
@@ -451,13 +515,16 @@ struct Splitter {
     uint32_t split_j[kMaxSplit] = {};
     int depth = 0;
 
-    void push_item(uint32_t start, uint32_t stop, bool chunked, uint32_t chunk, i128 steps)
+    i128 max_item_tuples = 0;
+
+    void push_item(uint32_t start, uint32_t stop, uint16_t chunked, uint32_t chunk, i128 steps, i128 tuples)
     {
+        max_item_tuples = std::max(max_item_tuples, tuples);
         ItemDesc d{};
         d.start_pc = start;
         d.stop_pc = stop;
         d.nsplit = (uint16_t)depth;
-        d.chunked = chunked ? 1 : 0;
+        d.chunked = chunked;
         d.chunk = chunk;
         for (int l = 0; l < depth; l++) { d.split_pc[l] = split_pc[l]; d.j[l] = split_j[l]; }
         items.push_back(d);
@@ -472,10 +539,10 @@ struct Splitter {
         i128 total = 0;
         for (const Stmt *x : xs) total = sat(total + an.work.at(x).steps);
         int32_t run_b = -1, run_e = -1;
-        i128 run_steps = 0;
+        i128 run_steps = 0, run_tuples = 0;
         auto flush = [&] {
-            if (run_b >= 0 && run_e > run_b) push_item((uint32_t)run_b, (uint32_t)run_e, false, 1, run_steps);
-            run_b = -1; run_steps = 0;
+            if (run_b >= 0 && run_e > run_b) push_item((uint32_t)run_b, (uint32_t)run_e, 0, 1, run_steps, run_tuples);
+            run_b = -1; run_steps = 0; run_tuples = 0;
         };
         for (const Stmt *x : xs) {
             auto r = lw.range.at(x);
@@ -488,20 +555,24 @@ struct Splitter {
                 if (run_b < 0) run_b = r.first;
                 run_e = r.second;
                 run_steps = sat(run_steps + steps);
+                run_tuples = sat(run_tuples + an.work.at(x).tuples);
                 continue;
             }
             flush();
             const i128 m = li->trip_max;
             const uint32_t loop_pc = (uint32_t)r.first, end_pc = (uint32_t)r.second;   // ENDLOOP is end_pc - 1
             split_pc[depth] = loop_pc;
-            if (ks <= m || depth + 1 >= kMaxSplit) {
+            const bool is_fast = lw.fast.count(x) != 0;
+            if (ks <= m || depth + 1 >= kMaxSplit || is_fast) {
+                // chunks of iterations (a fast loop starts at its own instruction)
                 i128 parts = std::min(ks, m);
                 i128 chunk = (m + parts - 1) / parts;
                 i128 nch = (m + chunk - 1) / chunk;
                 for (i128 c = 0; c < nch; c++) {
                     split_j[depth] = (uint32_t)c;
                     depth++;
-                    push_item(loop_pc + 1, end_pc, true, (uint32_t)chunk, mul_sat(chunk, li->body_steps));
+                    push_item(is_fast ? loop_pc : loop_pc + 1, end_pc, is_fast ? 2 : 1, (uint32_t)chunk,
+                              mul_sat(chunk, li->body_steps), mul_sat(chunk, li->body_tuples));
                     depth--;
                 }
             } else {
@@ -575,6 +646,8 @@ Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, 
         isteps.clear();
         Splitter sp{an, lw, items, isteps};
         sp.list(*p.body, K);
+        if (sp.max_item_tuples >= ((i128)1 << 32))
+            return Error::make(S_LIMIT, "a work item may make 2^32 accesses or more");
         if (items.size() <= opts.max_items || K <= 1) break;
         K = std::max<i128>(1, K / 2);                          // too fine: coarsen
     }

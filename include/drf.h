@@ -213,6 +213,38 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes,
  * (tuple count, control block, results). */
 int drf_ctx_transfer_bytes(const drf_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
 
+/* ---------------------------------------------------- allocation-free check */
+
+/* Size of the fixed device array that drf_check_noalloc works in. */
+#define DRF_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* drf_check without any device allocation, for callers that cannot call
+ * cudaMalloc when they need a check: a process whose device memory is
+ * already reserved by another component's allocator, code that may not
+ * allocate after start-up, or a path where an allocation's implicit
+ * synchronisation is not acceptable.  (The paper has no counterpart; this
+ * is a deployment variant of drf_check.)
+ *
+ * Every buffer of the pipeline is carved from one file-scope device array
+ * of DRF_NOALLOC_SCRATCH_BYTES, reserved when the library's device code is
+ * loaded on a GPU and held there until the process exits.  The call works
+ * on the current device and `stream` (NULL: the legacy default stream),
+ * needs no context, and never calls cudaMalloc, cudaFree or any allocating
+ * library routine.  Its result equals drf_check's.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device); make that first call before any stream capture.
+ *   - Protocols whose buffers do not fit the array (roughly 3.5 million
+ *     access tuples or fewer fit; the exact need depends on the thread
+ *     count and work items) are rejected with DRF_E_LIMIT in the return
+ *     value and in out->status.
+ *   - All calls share the one array (per device) and leave their data in
+ *     it; each call clears what it needs cleared.  Calls that overlap on the
+ *     GPU -- from two host threads, or on two streams -- race on the array:
+ *     serialise them.
+ * Blocks until the result is on the host; returns out->status. */
+int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_bounds *bounds, drf_result *out,
+                      void *stream);
+
 /* Diagnostics: copies the sorted access keys of the context's last
  * drf_check / drf_check_batch into keys (device -> host, at most cap) and
  * sets *n to their number.  layout[0..4] receive the key's field widths:

@@ -89,6 +89,8 @@ _SIGS = {
                                  ctypes.POINTER(drf_result), _P]),
     "drf_check_batch": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.POINTER(_U8P), ctypes.POINTER(ctypes.c_size_t),
                                        ctypes.POINTER(drf_bounds), ctypes.POINTER(drf_result), _P]),
+    "drf_check_noalloc": (ctypes.c_int, [_U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds),
+                                         ctypes.POINTER(drf_result), _P]),
     "drf_ctx_transfer_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "drf_debug_sorted_keys": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64,
                                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)]),
@@ -235,6 +237,16 @@ def drf_check(ctx, bytecode: bytes, nthreads: int, cells=(), params=(), stream=N
     st = lib().drf_check(ctx, p, n, ctypes.byref(b.c), ctypes.byref(r), _stream(stream))
     if st != 0 and r.status == 0:
         raise DrfError(st, drf_last_error(ctx))
+    return r
+
+
+def drf_check_noalloc(bytecode: bytes, nthreads: int, cells=(), params=(), stream=None) -> drf_result:
+    """drf_check on the current device with no device allocation (the
+    library's fixed scratch array); for callers that cannot allocate."""
+    _keep, p, n = _bytes(bytecode)
+    b = Bounds(nthreads, cells, params)
+    r = drf_result()
+    lib().drf_check_noalloc(p, n, ctypes.byref(b.c), ctypes.byref(r), _stream(stream))
     return r
 
 

@@ -103,7 +103,7 @@ class ClockSampler:
 def _pipeline_hash():
     h = hashlib.sha256()
     for rel in ("paper_2203_12878_b300/csrc/cuda/pipeline.cu", "paper_2203_12878_b300/csrc/cuda/pipeline.cuh",
-                "paper_2203_12878_b300/csrc/devprog.h"):
+                "paper_2203_12878_b300/csrc/cuda/radix.cuh", "paper_2203_12878_b300/csrc/devprog.h"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

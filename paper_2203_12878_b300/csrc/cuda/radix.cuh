@@ -22,6 +22,7 @@ constexpr int kTagShift = 40;
 constexpr unsigned long long kTagMask = (1ull << 22) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;   // ~ a second of waiting at most
 constexpr int kBins = 256;
+constexpr long long kNoWrite = -(1ll << 62);  // marks a digit whose run would leave the output
 
 struct PassArgs {
     const unsigned long long *src;
@@ -66,16 +67,26 @@ struct PassShared {
 
 // The pass body; BLOCK threads, BLOCK >= 256 (one thread per digit for the
 // digit-wise steps).
+// Digit of a key at bit `shift` (uniform over the launch): one funnel shift
+// of the key's two 32-bit halves.
+__device__ __forceinline__ uint32_t digit_of(unsigned long long k, uint32_t shift, uint32_t mask)
+{
+    const uint32_t lo = (uint32_t)k, hi = (uint32_t)(k >> 32);
+    const uint32_t v = shift < 32 ? __funnelshift_r(lo, hi, shift) : hi >> (shift - 32);
+    return v & mask;
+}
+
 template <int BLOCK, int ITEMS, int WINDOW = 4>
 __device__ __forceinline__ void pass(const PassArgs &A, PassShared<BLOCK, ITEMS> &sh)
 {
-    constexpr int kLookWindow = WINDOW;   // predecessor statuses read per look-back step
     static_assert(BLOCK >= kBins && BLOCK % 32 == 0, "one thread per digit");
+    constexpr int kLookWindow = WINDOW;   // predecessor statuses read per look-back step
     constexpr int kWarps = BLOCK / 32;
     constexpr int kTile = BLOCK * ITEMS;
     constexpr int kWarpKeys = 32 * ITEMS;
     const uint32_t t = threadIdx.x, lane = t & 31, wid = t / 32;
     const uint32_t dmask = (1u << A.nbits) - 1;
+    const uint32_t shift = A.shift;
 
     for (int i = t; i < kWarps * kBins; i += BLOCK) (&sh.whist[0][0])[i] = 0;
     if (t == 0) sh.tile = (uint32_t)atomicAdd(A.tile_counter, 1ull);
@@ -92,15 +103,17 @@ __device__ __forceinline__ void pass(const PassArgs &A, PassShared<BLOCK, ITEMS>
     const uint32_t tile = sh.tile;
     const uint64_t base = (uint64_t)tile * kTile;
     const uint64_t n = A.n;
+    const uint32_t valid_n = (uint32_t)min((uint64_t)kTile, n - base);
+    const unsigned long long *src = A.src + base;
 
     // load: warp w owns keys [w*32*ITEMS, (w+1)*32*ITEMS) of the tile, 32
     // consecutive keys per round, so that (round, lane) order is memory order
     unsigned long long key[ITEMS];
-    const uint64_t wbase = base + (uint64_t)wid * kWarpKeys;
+    const uint32_t wofs = wid * kWarpKeys + lane;
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-        const uint64_t idx = wbase + (uint64_t)i * 32 + lane;
-        key[i] = idx < n ? A.src[idx] : 0;
+        const uint32_t idx = wofs + i * 32;
+        key[i] = idx < valid_n ? src[idx] : 0;
     }
     // rank inside the warp, stable in memory order: lanes with equal digits
     // meet in one match; the lowest of them claims the run in the warp's
@@ -110,8 +123,8 @@ __device__ __forceinline__ void pass(const PassArgs &A, PassShared<BLOCK, ITEMS>
     const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-        const bool valid = wbase + (uint64_t)i * 32 + lane < n;
-        const uint32_t d = (uint32_t)(key[i] >> A.shift) & dmask;
+        const bool valid = wofs + i * 32 < valid_n;
+        const uint32_t d = digit_of(key[i], shift, dmask);
         if (i % 4 == 0) digs[i / 4] = 0;
         digs[i / 4] |= d << (8 * (i % 4));
         const unsigned peers = __match_any_sync(kFull, valid ? d : 0x100u + lane);
@@ -179,30 +192,29 @@ __device__ __forceinline__ void pass(const PassArgs &A, PassShared<BLOCK, ITEMS>
     uint32_t tstart = tincl - cnt;
     for (uint32_t i = 0; i < wid; i++) tstart += (uint32_t)sh.scan[i];
     if (t < kBins) {
-        sh.gdelta[t] = (long long)(dbase + excl) - (long long)tstart;
+        // this tile's run of digit t goes to [dbase + excl, + cnt): check it
+        // lies inside the output once per digit instead of once per key
+        const unsigned long long start = dbase + excl;
+        const bool inside = start + cnt <= n;
+        if (!inside && cnt) atomicOr(A.flags, 2u);   // histogram and keys disagree
+        sh.gdelta[t] = inside ? (long long)start - (long long)tstart : kNoWrite;
         for (int w = 0; w < kWarps; w++) sh.whist[w][t] += tstart;   // scatter base of (warp, digit)
     }
     __syncthreads();
     // scatter into tile order in shared memory, then stream each digit's run out
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-        const uint64_t idx = wbase + (uint64_t)i * 32 + lane;
-        if (idx < n) {
+        if (wofs + i * 32 < valid_n) {
             const uint32_t d = (digs[i / 4] >> (8 * (i % 4))) & 0xFF;
             sh.keys[sh.whist[wid][d] + rank[i]] = key[i];
         }
     }
     __syncthreads();
-    const uint32_t valid_n = (uint32_t)min((uint64_t)kTile, n - base);
-    bool bad = false;
     for (uint32_t j = t; j < valid_n; j += BLOCK) {
         const unsigned long long k = sh.keys[j];
-        const uint32_t d = (uint32_t)(k >> A.shift) & dmask;
-        const unsigned long long pos = (unsigned long long)(sh.gdelta[d] + (long long)j);
-        if (pos < n) A.dst[pos] = k;
-        else bad = true;            // histogram and keys disagree: never write past the buffer
+        const long long g = sh.gdelta[digit_of(k, shift, dmask)];
+        if (g != kNoWrite) A.dst[g + (long long)j] = k;
     }
-    if (bad) atomicOr(A.flags, 2u);
 }
 
 }  // namespace radix

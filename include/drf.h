@@ -167,6 +167,28 @@ const char *drf_last_error(const drf_ctx *ctx);
 int drf_protocol_compile(const char *text, uint8_t **bytecode, size_t *len,
                          char *err, size_t errlen);
 
+/* BabyCUDA front-end (Sec. 3, Fig. 3 syntax; typing rules of Fig. 4).
+ * Reads a BabyCUDA program --
+ *   stmt := "let" NAME "=" ARRAY "[" expr "]" ";"     (read; NAME holds the value)
+ *         | ARRAY "[" expr "]" ":=" expr ";"          (write of a payload)
+ *         | "if" "(" cond ")" "{" stmt* "}" ["else" "{" stmt* "}"]
+ *         | ("for" | "forS") NAME "in" expr ".." expr "{" stmt* "}"
+ *         | "sync" ";" | "skip" ";"
+ * with the same declarations and expressions as protocol text -- and infers
+ * its memory access protocol: a write A[n] := m types as wr A[n] (the payload
+ * is dropped, rule t-write), "let x = A[n]; b" as rd A[n]; b where x may
+ * appear in payloads only (rule t-read keeps x out of the typing
+ * environment, so an index, condition or loop bound that depends on data
+ * read from an array is rejected with DRF_E_UNBOUND_VAR -- the paper's
+ * eqn. illtyped).  "for" is the unsynchronized loop.  Output and errors as
+ * drf_protocol_compile.  Host only. */
+int drf_babycuda_infer(const char *text, uint8_t **bytecode, size_t *len, char *err, size_t errlen);
+
+/* MAP text of a bytecode (arrays A0.., parameters P0.., loop variables
+ * v<slot>); drf_protocol_compile reads it back to the same bytecode.
+ * *text is malloc'd (free with drf_free). */
+int drf_protocol_text(const uint8_t *bytecode, size_t len, char **text);
+
 /* Array and parameter counts a bytecode declares (validates it fully). */
 int drf_protocol_info(const uint8_t *bytecode, size_t len, uint32_t *nlocs, uint32_t *nparams);
 

@@ -128,6 +128,42 @@ int drf_protocol_compile(const char *text, uint8_t **bytecode, size_t *len, char
     return DRF_OK;
 }
 
+int drf_babycuda_infer(const char *text, uint8_t **bytecode, size_t *len, char *err, size_t errlen)
+{
+    if (err && errlen) err[0] = 0;
+    if (!text || !bytecode || !len) return DRF_E_INVALID_ARG;
+    *bytecode = nullptr;
+    *len = 0;
+    Protocol p;
+    Error e = parse_babycuda_text(text, p);
+    if (!e.ok()) {
+        if (err && errlen) { std::strncpy(err, e.message.c_str(), errlen - 1); err[errlen - 1] = 0; }
+        return e.status;
+    }
+    std::vector<uint8_t> bc = encode_bytecode(p);
+    uint8_t *buf = (uint8_t *)std::malloc(bc.size());
+    if (!buf) return DRF_E_NOMEM;
+    std::memcpy(buf, bc.data(), bc.size());
+    *bytecode = buf;
+    *len = bc.size();
+    return DRF_OK;
+}
+
+int drf_protocol_text(const uint8_t *bytecode, size_t len, char **text)
+{
+    if (!text) return DRF_E_INVALID_ARG;
+    *text = nullptr;
+    Protocol p;
+    Error e = decode_bytecode(bytecode, len, p);
+    if (!e.ok()) return e.status;
+    std::string t = protocol_text(p);
+    char *buf = (char *)std::malloc(t.size() + 1);
+    if (!buf) return DRF_E_NOMEM;
+    std::memcpy(buf, t.c_str(), t.size() + 1);
+    *text = buf;
+    return DRF_OK;
+}
+
 int drf_protocol_info(const uint8_t *bytecode, size_t len, uint32_t *nlocs, uint32_t *nparams)
 {
     Protocol p;

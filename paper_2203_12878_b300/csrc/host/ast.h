@@ -67,6 +67,12 @@ struct Error {
 
 // Front-end entry points.
 Error parse_text(const std::string &text, Protocol &out);
+// BabyCUDA text (Fig. 3 syntax: "let x = A[n];", "A[n] := m;", if, for,
+// forS, sync, skip) typed into its MAP by the rules of Fig. 4.
+Error parse_babycuda_text(const std::string &text, Protocol &out);
+// MAP text of a protocol (arrays named A0.., parameters P0.., loop
+// variables v<slot>); parse_text reads it back to the same protocol.
+std::string protocol_text(const Protocol &p);
 std::vector<uint8_t> encode_bytecode(const Protocol &p);
 Error decode_bytecode(const uint8_t *data, size_t len, Protocol &out);
 

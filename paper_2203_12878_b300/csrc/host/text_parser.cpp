@@ -67,7 +67,7 @@ std::vector<Token> tokenize(const std::string &src)
             for (const char *p : two)
                 if (src.compare(i, 2, p) == 0) { t.kind = Tk::Punct; t.text = p; i += 2; break; }
             if (t.kind == Tk::Bad) {
-                if (std::strchr(";,{}[]()+-*/%<>=!", c)) { t.kind = Tk::Punct; t.text = std::string(1, c); }
+                if (std::strchr(";,{}[]()+-*/%<>=!:", c)) { t.kind = Tk::Punct; t.text = std::string(1, c); }
                 else t.text = std::string(1, c);
                 i++;
             }
@@ -103,7 +103,9 @@ struct ParseFail {
 
 class Parser {
 public:
-    explicit Parser(const std::string &src) : toks_(tokenize(src)) {}
+    // baby: read BabyCUDA (Fig. 3) instead of MAP text and infer its MAP by
+    // the rules of Fig. 4 while parsing (see parse_babycuda_text)
+    explicit Parser(const std::string &src, bool baby = false) : toks_(tokenize(src)), baby_(baby) {}
 
     Error run(Protocol &out)
     {
@@ -127,6 +129,9 @@ private:
     std::vector<std::pair<std::string, uint16_t>> scope_;   // enclosing loop variables
     uint16_t nslots_ = 0;
     int depth_ = 0;
+    const bool baby_;
+    std::vector<std::string> data_;     // BabyCUDA: names bound by a read (values, not in V)
+    bool payload_ = false;              // BabyCUDA: parsing a write's payload
 
     const Token &cur() const { return toks_[pos_]; }
     void advance() { if (pos_ + 1 < toks_.size()) pos_++; }
@@ -215,6 +220,16 @@ private:
             if (!found)
                 for (size_t i = 0; i < params_.size(); i++)
                     if (params_[i] == t.text) { n->kind = PNode::Param; n->slot = (uint16_t)i; found = true; break; }
+            if (!found && baby_)
+                for (auto &d : data_)
+                    if (d == t.text) {
+                        // a value read from an array: allowed in a payload only (rule t-write
+                        // ignores the payload; rule t-read keeps the binder out of V)
+                        if (!payload_)
+                            fail(S_UNBOUND_VAR, "'" + t.text + "' holds data read from an array; an index, "
+                                                "condition or bound may not depend on it (rule t-read)");
+                        n->kind = PNode::Lit; found = true; break;
+                    }
             if (!found) fail(S_UNBOUND_VAR, "unbound variable '" + t.text + "'");
             advance();
         } else {
@@ -303,8 +318,65 @@ private:
     StmtP parse_block(bool synced)
     {
         expect("{");
+        const size_t data_mark = data_.size();          // reads bind until the end of their block
         StmtP s = parse_seq(synced, true);
+        data_.resize(data_mark);
         expect("}");
+        return s;
+    }
+
+    bool bound_anywhere(const std::string &name) const
+    {
+        for (auto &v : scope_) if (v.first == name) return true;
+        for (auto &p : params_) if (p == name) return true;
+        for (auto &d : data_) if (d == name) return true;
+        return false;
+    }
+
+    int array_index(const std::string &name)
+    {
+        for (size_t i = 0; i < arrays_.size(); i++) if (arrays_[i] == name) return (int)i;
+        fail(S_UNKNOWN_ARRAY, "unknown array '" + name + "'");
+    }
+
+    // BabyCUDA statements: "let x = A[n];" (rule t-read: rd A[n], x stays out
+    // of V for the rest of the block) and "A[n] := m;" (rule t-write: wr A[n]).
+    StmtP parse_baby_access()
+    {
+        StmtP s(new Stmt);
+        s->op = SOp::Access;
+        if (is_word("let")) {
+            advance();
+            if (cur().kind != Tk::Name || reserved(cur().text) || cur().text == "let" || cur().text == "for")
+                fail(S_PARSE, "expected a name");
+            std::string name = cur().text;
+            if (bound_anywhere(name)) fail(S_REBIND, "'" + name + "' is already bound");
+            advance();
+            expect("=");
+            if (cur().kind != Tk::Name) fail(S_PARSE, "expected an array name");
+            s->loc = (uint16_t)array_index(cur().text);
+            advance();
+            expect("[");
+            s->index = parse_expr();
+            expect("]");
+            expect(";");
+            s->write = false;
+            data_.push_back(name);
+            return s;
+        }
+        s->loc = (uint16_t)array_index(cur().text);
+        advance();
+        expect("[");
+        s->index = parse_expr();
+        expect("]");
+        if (!(is_punct(":") || (cur().kind == Tk::Bad && cur().text == ":"))) fail(S_PARSE, "expected ':='");
+        advance();
+        expect("=");
+        payload_ = true;
+        parse_expr();                                    // the payload is dropped by the MAP
+        payload_ = false;
+        expect(";");
+        s->write = true;
         return s;
     }
 
@@ -321,7 +393,12 @@ private:
     {
         if (++depth_ > kMaxStmtDepth) fail(S_LIMIT, "statements nested too deeply");
         StmtP s(new Stmt);
-        if (is_word("skip")) {
+        if (baby_ && (is_word("rd") || is_word("wr"))) fail(S_PARSE, "BabyCUDA has no rd / wr statements");
+        if (baby_ && (is_word("let") ||
+                      (cur().kind == Tk::Name && !reserved(cur().text) && cur().text != "for" &&
+                       toks_[pos_ + 1].kind == Tk::Punct && toks_[pos_ + 1].text == "["))) {
+            s = parse_baby_access();
+        } else if (is_word("skip")) {
             advance(); expect(";");
             s->op = SOp::Skip;
         } else if (is_word("sync")) {
@@ -351,7 +428,7 @@ private:
             s->then_s = parse_block(false);
             if (is_word("else")) { advance(); s->else_s = parse_block(false); }
             else { s->else_s.reset(new Stmt); s->else_s->op = SOp::Skip; }
-        } else if (is_word("forU") || is_word("forS")) {
+        } else if (is_word("forU") || is_word("forS") || (baby_ && is_word("for"))) {
             bool sync_loop = is_word("forS");
             if (sync_loop && !synced) fail(S_SYNC_IN_UNSYNC, "forS inside an unsynchronized fragment");
             s->op = sync_loop ? SOp::ForS : SOp::ForU;
@@ -384,6 +461,12 @@ private:
 Error parse_text(const std::string &text, Protocol &out)
 {
     Parser p(text);
+    return p.run(out);
+}
+
+Error parse_babycuda_text(const std::string &text, Protocol &out)
+{
+    Parser p(text, true);
     return p.run(out);
 }
 

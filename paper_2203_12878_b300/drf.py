@@ -80,6 +80,9 @@ _SIGS = {
     "drf_last_error": (ctypes.c_char_p, [_P]),
     "drf_protocol_compile": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_U8P), ctypes.POINTER(ctypes.c_size_t),
                                             ctypes.c_char_p, ctypes.c_size_t]),
+    "drf_babycuda_infer": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_U8P), ctypes.POINTER(ctypes.c_size_t),
+                                          ctypes.c_char_p, ctypes.c_size_t]),
+    "drf_protocol_text": (ctypes.c_int, [_U8P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
     "drf_protocol_info": (ctypes.c_int, [_U8P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint32),
                                          ctypes.POINTER(ctypes.c_uint32)]),
     "drf_protocol_analyze": (ctypes.c_int, [_U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds),
@@ -190,6 +193,34 @@ def drf_protocol_compile(text: str) -> bytes:
         raise DrfError(st, err.value.decode(errors="replace"))
     try:
         return ctypes.string_at(out, n.value)
+    finally:
+        lib().drf_free(out)
+
+
+def drf_babycuda_infer(text: str) -> bytes:
+    """BabyCUDA program -> bytecode of its inferred MAP; raises DrfError when
+    the program is ill-typed (e.g. data-dependent indexing)."""
+    out = _U8P()
+    n = ctypes.c_size_t()
+    err = ctypes.create_string_buffer(512)
+    st = lib().drf_babycuda_infer(text.encode(), ctypes.byref(out), ctypes.byref(n), err, len(err))
+    if st != 0:
+        raise DrfError(st, err.value.decode(errors="replace"))
+    try:
+        return ctypes.string_at(out, n.value)
+    finally:
+        lib().drf_free(out)
+
+
+def drf_protocol_text(bytecode: bytes) -> str:
+    """MAP text of a bytecode."""
+    _keep, p, n = _bytes(bytecode)
+    out = ctypes.c_void_p()
+    st = lib().drf_protocol_text(p, n, ctypes.byref(out))
+    if st != 0:
+        raise DrfError(st)
+    try:
+        return ctypes.string_at(out).decode()
     finally:
         lib().drf_free(out)
 

@@ -473,3 +473,78 @@ def config5_arrivals(rate: float, duration_s: float, seed: int = 1):
         if t >= duration_s:
             return out
         out.append((t, "batch" if r.random() < 0.9 else "single"))
+
+
+# ------------------------------------------------------------- BabyCUDA --
+
+def random_babycuda(seed: int, ill_typed: bool = False) -> Protocol:
+    """A small random BabyCUDA program (Fig. 3 syntax): reads bind data
+    variables ("let x = A[n];") that flow only into write payloads
+    ("A[n] := m;"), conditionals and loops over tid / loop variables /
+    parameters, forS and sync in the synchronized fragment.  With
+    ill_typed=True one index depends on a data variable (not typable)."""
+    r = random.Random(0xBABC ^ (seed * 2654435761))
+    narrays = r.randint(1, 2)
+    arrays = ["A", "B"][:narrays]
+    cells = [r.randint(1, 12) for _ in range(narrays)]
+    params = ["M"] if r.random() < 0.3 else []
+    pvals = [r.randint(0, 3) for _ in params]
+    counter = [0]
+    planted = [False]
+
+    def fresh(prefix):
+        counter[0] += 1
+        return f"{prefix}{counter[0]}"
+
+    def iexpr(names, depth=2):
+        if depth <= 0 or r.random() < 0.4:
+            return r.choice(names) if r.random() < 0.6 else str(r.randint(0, 5))
+        op = r.choice(["+", "-", "*", "+"])
+        return f"({iexpr(names, depth - 1)} {op} {iexpr(names, depth - 1)})"
+
+    def block(typable, data, synced, depth, budget):
+        out = []
+        for _ in range(r.randint(1, 3)):
+            if budget[0] <= 0:
+                break
+            budget[0] -= 1
+            k = r.random()
+            i = r.randrange(narrays)
+            if k < 0.3:
+                x = fresh("x")
+                ix = iexpr(typable)
+                if ill_typed and not planted[0] and data:
+                    ix = f"{r.choice(data)} + {ix}"          # the index depends on data
+                    planted[0] = True
+                out.append(f"let {x} = {arrays[i]}[({ix}) % {cells[i]}];")
+                data = data + [x]
+            elif k < 0.6:
+                payload = iexpr(typable + data)
+                ix = iexpr(typable)
+                if ill_typed and not planted[0] and data:
+                    ix = f"{r.choice(data)} + {ix}"          # the index depends on data
+                    planted[0] = True
+                out.append(f"{arrays[i]}[({ix}) % {cells[i]}] := {payload};")
+            elif k < 0.68 and synced:
+                out.append("sync;")
+            elif k < 0.72:
+                out.append("skip;")
+            elif k < 0.85 and depth > 0:
+                c = f"{iexpr(typable, 1)} {r.choice(['==', '!=', '<', '>=', '<='])} {iexpr(typable, 1)}"
+                th = block(typable, data, False, depth - 1, budget)
+                el = block(typable, data, False, depth - 1, budget)
+                out.append(f"if ({c}) {{ {' '.join(th)} }} else {{ {' '.join(el)} }}")
+            elif depth > 0:
+                kind = "forS" if synced and r.random() < 0.5 else "for"
+                v = fresh("v")
+                hi = r.choice([str(r.randint(0, 3)), "tid", "tid + 1"] + ([params[0]] if params else []))
+                body = block(typable + [v], data, kind == "forS", depth - 1, budget)
+                out.append(f"{kind} {v} in 0 .. {hi} {{ {' '.join(body)} }}")
+        return out
+
+    typable = ["tid"] + params
+    body = block(typable, [], True, 3, [10])
+    if ill_typed and not planted[0]:
+        body += [f"let xz = {arrays[0]}[0];", f"{arrays[0]}[xz % {cells[0]}] := 1;"]
+    decl = f"array {', '.join(arrays)};\n" + (f"param {', '.join(params)};\n" if params else "")
+    return Protocol(decl + "\n".join(body) + "\n", r.randint(1, 6), cells, pvals, {"seed": seed})

@@ -275,6 +275,14 @@ int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_bounds *bou
  * (mode 1 = write). */
 int drf_debug_sorted_keys(drf_ctx *ctx, uint64_t *keys, uint64_t cap, uint64_t *n, uint32_t layout[5]);
 
+/* A parameter swept over a range in one batched pass: checks the protocol
+ * for every value v in [lo, hi) of parameter `param` (the other bounds as
+ * given), as a batch of hi - lo protocols -- a bounded stand-in for a
+ * symbolic parameter such as M in the paper's Fig. 1.  out has hi - lo
+ * entries, out[k] for value lo + k; each equals drf_check at that value. */
+int drf_check_param_sweep(drf_ctx *ctx, const uint8_t *bytecode, size_t len, const drf_bounds *bounds,
+                          uint32_t param, int64_t lo, int64_t hi, drf_result *out, void *stream);
+
 /* ------------------------------------------------------------------- plans -- */
 
 /* Prepares a fixed batch for repeated checks: validates and lowers every

@@ -1162,6 +1162,57 @@ int64_t oracle_tuples(const char *text, uint32_t nthreads, uint32_t nlocs, const
     return n;
 }
 
+/* Every thread's accesses to one cell (phase, loc, index), without storing
+ * the others: the two smallest distinct accessor tids and the two smallest
+ * distinct writer tids (0xFFFFFFFF when absent), the number of accesses to
+ * the cell and the total number of accesses.  For checking a witness of a
+ * protocol too large to check whole. */
+typedef struct {
+    uint32_t t0, t1, w0, w1;
+    uint64_t cell_accesses;
+    uint64_t total;
+    int32_t status;
+    uint32_t pad;
+} oracle_cell_result;
+
+static void cell_visit(const Tuple *t, uint32_t phase, uint32_t loc, int64_t index, oracle_cell_result *r)
+{
+    if (t->phase != phase || t->loc != loc || t->index != index) return;
+    two_smallest(&r->t0, &r->t1, t->tid);
+    if (t->write) two_smallest(&r->w0, &r->w1, t->tid);
+    r->cell_accesses++;
+}
+
+int oracle_cell(const char *text, uint32_t nthreads, uint32_t nlocs, const uint64_t *cells, uint32_t nparams,
+                const int64_t *params, uint32_t phase, uint32_t loc, uint64_t index, oracle_cell_result *out,
+                char *msg, int msglen)
+{
+    memset(out, 0, sizeof *out);
+    out->t0 = out->t1 = out->w0 = out->w1 = NONE;
+    Program prog;
+    int st = parse_program(text, &prog, msg, msglen);
+    if (st) { program_free(&prog); out->status = st; return st; }
+    Bounds b = { nthreads, nlocs, nparams, cells, params };
+    st = check_bounds(&prog, &b, msg, msglen);
+    if (st) { program_free(&prog); out->status = st; return st; }
+    int64_t *vars = (int64_t *)calloc((size_t)(prog.nslots ? prog.nslots : 1), sizeof(int64_t));
+    TupleVec tv; memset(&tv, 0, sizeof tv);
+    if (!vars) { program_free(&prog); out->status = OR_E_NOMEM; return OR_E_NOMEM; }
+    for (uint32_t t = 0; t < nthreads && !out->status; t++) {   /* one thread at a time */
+        Thread th; memset(&th, 0, sizeof th);
+        th.prog = &prog; th.cells = cells; th.params = params; th.vars = vars;
+        th.tid = t; th.out = &tv;
+        tv.n = 0;
+        run_stmt(&th, prog.body);
+        if (tv.nomem) { out->status = OR_E_NOMEM; break; }
+        if (th.error) { out->status = th.error; break; }
+        for (size_t i = 0; i < tv.n; i++) cell_visit(&tv.v[i], phase, loc, (int64_t)index, out);
+        out->total += th.ordinal;
+    }
+    free(tv.v); free(vars); program_free(&prog);
+    return out->status;
+}
+
 /* Parse and validate only: 0 or the validation status, and the declared
  * array and param counts. */
 int oracle_validate(const char *text, int *narrays, int *nparams, char *msg, int msglen)

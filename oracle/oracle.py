@@ -51,6 +51,12 @@ class _Result(ctypes.Structure):
     ]
 
 
+class _Cell(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_uint32), ("t1", ctypes.c_uint32), ("w0", ctypes.c_uint32), ("w1", ctypes.c_uint32),
+                ("cell_accesses", ctypes.c_uint64), ("total", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("pad", ctypes.c_uint32)]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (plain gcc)."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -77,6 +83,11 @@ def _load():
                 ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
                 ctypes.c_uint32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64),
                 ctypes.c_int64, ctypes.c_char_p, ctypes.c_int]
+            lib.oracle_cell.restype = ctypes.c_int
+            lib.oracle_cell.argtypes = [
+                ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                ctypes.c_uint32, ctypes.POINTER(ctypes.c_int64), ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                ctypes.POINTER(_Cell), ctypes.c_char_p, ctypes.c_int]
             lib.oracle_validate.restype = ctypes.c_int
             lib.oracle_validate.argtypes = [
                 ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -139,6 +150,28 @@ def tuples(text: str, nthreads: int, cells=(), params=(), cap: int | None = None
     if n < 0:
         raise ValueError(f"oracle_tuples: {STATUS_NAMES.get(n, n)} {msg.value.decode()}")
     return rows[:min(n, cap)]
+
+
+def cell(text: str, nthreads: int, cells, params, phase: int, loc: int, index: int) -> dict:
+    """Accessors of one cell, computed one thread at a time: the witness that
+    Definition 1 (with the smallest-pair reading) gives for that cell, and the
+    protocol's total access count."""
+    lib = _load()
+    cells, params, ca, pa = _arrays(cells, params)
+    r = _Cell()
+    msg = ctypes.create_string_buffer(256)
+    lib.oracle_cell(text.encode(), nthreads, len(cells), ca, len(params), pa, phase, loc, index,
+                    ctypes.byref(r), msg, len(msg))
+    none = 0xFFFFFFFF
+    d = {"status": STATUS_NAMES.get(r.status, r.status), "accesses": r.cell_accesses, "total": r.total}
+    racy = r.w0 != none and r.t1 != none
+    d["racy"] = racy
+    if racy:
+        if r.w0 == r.t0:
+            d.update(tid_i=r.t0, tid_j=r.t1, i_writes=True, j_writes=(r.w1 == r.t1))
+        else:
+            d.update(tid_i=r.t0, tid_j=r.w0, i_writes=False, j_writes=True)
+    return d
 
 
 def validate(text: str):

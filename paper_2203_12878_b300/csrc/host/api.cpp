@@ -292,6 +292,27 @@ int drf_debug_sorted_keys(drf_ctx *ctx, uint64_t *keys, uint64_t cap, uint64_t *
     return DRF_OK;
 }
 
+int drf_check_param_sweep(drf_ctx *ctx, const uint8_t *bytecode, size_t len, const drf_bounds *bounds,
+                          uint32_t param, int64_t lo, int64_t hi, drf_result *out, void *stream)
+{
+    if (!ctx || !bytecode || !bounds || !out || hi < lo) return DRF_E_INVALID_ARG;
+    if (param >= bounds->nparams || !bounds->params) return DRF_E_INVALID_ARG;
+    if ((uint64_t)(hi - lo) > (1u << 20)) return fail(ctx, DRF_E_LIMIT, "more than 2^20 parameter values");
+    const uint32_t n = (uint32_t)(hi - lo);
+    if (n == 0) return DRF_OK;
+    std::vector<int64_t> values((size_t)n * bounds->nparams);
+    std::vector<drf_bounds> bs(n, *bounds);
+    std::vector<const uint8_t *> bcs(n, bytecode);
+    std::vector<size_t> lens(n, len);
+    for (uint32_t k = 0; k < n; k++) {
+        int64_t *v = &values[(size_t)k * bounds->nparams];
+        std::memcpy(v, bounds->params, sizeof(int64_t) * bounds->nparams);
+        v[param] = lo + (int64_t)k;
+        bs[k].params = v;
+    }
+    return drf_check_batch(ctx, n, bcs.data(), lens.data(), bs.data(), out, stream);
+}
+
 // ------------------------------------------------------------------- plans
 
 int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const size_t *lens,

@@ -97,6 +97,8 @@ _SIGS = {
     "drf_ctx_transfer_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "drf_debug_sorted_keys": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64,
                                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)]),
+    "drf_check_param_sweep": (ctypes.c_int, [_P, _U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds), ctypes.c_uint32,
+                                             ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(drf_result), _P]),
     "drf_plan_create": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.POINTER(_U8P), ctypes.POINTER(ctypes.c_size_t),
                                        ctypes.POINTER(drf_bounds), ctypes.POINTER(_P)]),
     "drf_plan_launch": (ctypes.c_int, [_P, _P]),
@@ -325,6 +327,18 @@ def drf_debug_sorted_keys(ctx):
         raise DrfError(st)
     layout = dict(zip(("tid_bits", "idx_bits", "loc_bits", "phase_bits", "proto_bits"), list(lay)))
     return keys[:n.value], layout
+
+
+def drf_check_param_sweep(ctx, bytecode: bytes, nthreads: int, cells, params, param: int, lo: int, hi: int,
+                          stream=None):
+    """Results for every value of parameter `param` in [lo, hi), one batched pass."""
+    _keep, p, n = _bytes(bytecode)
+    b = Bounds(nthreads, cells, params)
+    out = (drf_result * max(1, hi - lo))()
+    st = lib().drf_check_param_sweep(ctx, p, n, ctypes.byref(b.c), param, lo, hi, out, _stream(stream))
+    if st != 0:
+        raise DrfError(st, drf_last_error(ctx))
+    return list(out)[:max(0, hi - lo)]
 
 
 def drf_plan_create(ctx, bytecodes, bounds):

@@ -213,3 +213,42 @@ def test_server_results_equal_alone(ctx, oracle):
     for p, o in zip(ps, out):
         assert o is not None
         assert same(drf.result_dict(o[0]), want(oracle, p))
+
+
+def test_param_sweep_equals_per_value(ctx, oracle):
+    """Fig. 1's MAP with M swept over 0..9 in one batched pass: DRF for M = 0,
+    racy on cell 0 for every M >= 1; each entry equals the oracle at that M."""
+    text = "array A;\nparam M;\nforU x in 0 .. M { rd A[x]; wr A[x]; }\n"
+    bc = drf.drf_protocol_compile(text)
+    res = drf.drf_check_param_sweep(ctx, bc, 4, [16], [0], 0, 0, 10)
+    for m, r in enumerate(res):
+        assert same(drf.result_dict(r), oracle.check(text, 4, [16], [m], CELLS))
+    assert drf.result_dict(res[0])["verdict"] == "DRF"
+    assert all(drf.result_dict(r)["verdict"] == "RACY" for r in res[1:])
+    # a parameter that moves an index out of range in part of the sweep
+    text2 = "array A;\nparam K;\nwr A[tid + K];\n"
+    res2 = drf.drf_check_param_sweep(ctx, drf.drf_protocol_compile(text2), 4, [6], [0], 0, -1, 4)
+    for k, r in zip(range(-1, 4), res2):
+        assert same(drf.result_dict(r), oracle.check(text2, 4, [6], [k], CELLS))
+
+
+@pytest.mark.parametrize("racy", [False, True])
+def test_config3_full_size(ctx, oracle, racy):
+    """Grid-scale protocol (65,536 threads, 4 arrays of 2^24 cells, 8 phases,
+    ~2.2x10^8 accesses) at full size.  The race-free variant is race-free by
+    construction (every cell has one owner thread); the planted one has
+    exactly one racy cell, whose accessors the oracle recomputes one thread at
+    a time."""
+    p = protogen.config3(0, racy=racy)
+    got = run(ctx, p)
+    m = p.meta
+    assert got["status"] == "OK" and got["phases"] == 8
+    if not racy:
+        assert got["verdict"] == "DRF" and got["tuples"] == m["accesses"]
+        return
+    assert got["tuples"] == m["accesses"] + 2
+    assert (got["verdict"], got["phase"], got["loc"], got["index"]) == ("RACY", m["phase"], m["loc"], m["index"])
+    cell = oracle.cell(p.text, p.nthreads, p.cells, p.params, m["phase"], m["loc"], m["index"])
+    assert cell["total"] == got["tuples"] and cell["racy"]
+    assert {k: got[k] for k in ("tid_i", "tid_j", "i_writes", "j_writes")} == \
+           {k: cell[k] for k in ("tid_i", "tid_j", "i_writes", "j_writes")}

@@ -331,3 +331,20 @@ def test_pairs_equal_cells_config1(oracle):
     for v in ("drf", "rdwr", "nosync"):
         p = protogen.config1(v)
         assert oracle.check(p.text, 256, p.cells, [], PAIRS) == oracle.check(p.text, 256, p.cells, [], CELLS)
+
+
+def test_single_cell_helper_agrees_with_whole_check(oracle):
+    """oracle.cell (accessors of one cell, one thread at a time) gives the
+    same witness as the whole-protocol checkers on the witness cell."""
+    n = 0
+    for seed in range(400):
+        p = protogen.random_small(seed)
+        got = oracle.check(p.text, p.nthreads, p.cells, p.params, PAIRS)
+        if got["status"] != "OK" or got["verdict"] != "RACY":
+            continue
+        c = oracle.cell(p.text, p.nthreads, p.cells, p.params, got["phase"], got["loc"], got["index"])
+        assert c["racy"] and c["total"] == got["tuples"]
+        assert {k: c[k] for k in ("tid_i", "tid_j", "i_writes", "j_writes")} == \
+               {k: got[k] for k in ("tid_i", "tid_j", "i_writes", "j_writes")}
+        n += 1
+    assert n > 50

@@ -133,6 +133,7 @@ typedef struct {
 } drf_opts;
 
 #define DRF_OPT_PROFILE_STAGES 0x1u   /* record per-kernel CUDA events in plans */
+#define DRF_OPT_AUTOTUNE       0x2u   /* plans: time candidate launch configurations, keep the fastest */
 
 /* ------------------------------------------------------- library / errors -- */
 
@@ -310,6 +311,15 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
  * was created with DRF_OPT_PROFILE_STAGES: names[i] (static strings) and
  * ms[i] for i < *count (cap entries at most).  Waits for the launch. */
 int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap, int *count);
+
+/* The launch configuration a plan uses: the warp-items per SM its items
+ * were cut for (the item-to-warp schedule) and the keys per thread of its
+ * radix tiles.  With DRF_OPT_AUTOTUNE, drf_plan_create times every
+ * candidate (granularity 32 / 128 / 512 x tile 12 / 16 / 24 keys per
+ * thread) on the batch and keeps the fastest; the choice is cached per
+ * workload signature for the process and, when the environment variable
+ * DRF_TUNE_CACHE names a file, persisted there. */
+int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix_items);
 
 /* Releases the plan's device memory and graph. */
 void drf_plan_destroy(drf_plan *plan);

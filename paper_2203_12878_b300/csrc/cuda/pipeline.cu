@@ -560,9 +560,10 @@ __device__ int nontrivial_before(const BatchArgs &a, uint32_t pass, bool *self)
     return before & 1 ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(kRadixThreads, 3) k_radix(BatchArgs a, uint32_t pass)
+template <int ITEMS>
+__global__ void __launch_bounds__(kRadixThreads, ITEMS >= 24 ? 2 : 3) k_radix(BatchArgs a, uint32_t pass)
 {
-    __shared__ radix::PassShared<kRadixThreads, kRadixItems> sh;
+    __shared__ radix::PassShared<kRadixThreads, ITEMS> sh;
     bool self;
     const int before = nontrivial_before(a, pass, &self);
     if (!self) return;                       // constant digit: the pass would not move any key
@@ -577,7 +578,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix(BatchArgs a, uint32_
     A.tile_counter = &a.ctrl->tile_counter[pass];
     A.tag = (unsigned long long)(*a.epoch & radix::kTagMask) << radix::kTagShift;
     A.flags = &a.ctrl->flags;
-    radix::pass<kRadixThreads, kRadixItems>(A, sh);
+    radix::pass<kRadixThreads, ITEMS>(A, sh);
 }
 
 // ------------------------------------------------------------- detection
@@ -942,7 +943,12 @@ cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t
     if (a.has_wide) k_interp<true, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
     mark(ev, nev, s);
     for (uint32_t q = 0; q < a.L.passes; q++) {
-        if (a.ntiles) k_radix<<<a.ntiles, kRadixThreads, 0, s>>>(a, q);
+        if (a.ntiles) {
+            const uint32_t items = radix_items_or_default(a.radix_items);
+            if (items == 12) k_radix<12><<<a.ntiles, kRadixThreads, 0, s>>>(a, q);
+            else if (items == 24) k_radix<24><<<a.ntiles, kRadixThreads, 0, s>>>(a, q);
+            else k_radix<16><<<a.ntiles, kRadixThreads, 0, s>>>(a, q);
+        }
         mark(ev, nev, s);
     }
     if (a.ndtiles) {

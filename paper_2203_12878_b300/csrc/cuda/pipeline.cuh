@@ -60,6 +60,7 @@ struct BatchArgs {
     unsigned long long *hist;        // [kMaxPasses][kRadixBins]
     unsigned long long *status;      // [passes][ntiles][kRadixBins] look-back words
     uint32_t ntiles;
+    uint32_t radix_items;            // keys per thread of a radix tile (12, 16 or 24; 0 = 16)
     TileRec *trec;                   // [ndtiles] detection tile records
     uint32_t ndtiles;
     // per protocol
@@ -83,7 +84,13 @@ constexpr int kFinalizeThreads = 128;
 constexpr int kScanThreads = 256;
 constexpr int kWScanPerBlock = 4096;                        // warp-items per scan block
 
-inline uint32_t radix_tiles(uint64_t n) { return (uint32_t)((n + kRadixTile - 1) / kRadixTile); }
+// Keys per thread of a radix tile: a tuning choice among these (0 = 16).
+inline uint32_t radix_items_or_default(uint32_t items) { return items == 12 || items == 24 ? items : 16; }
+inline uint32_t radix_tiles(uint64_t n, uint32_t items = kRadixItems)
+{
+    const uint64_t tile = (uint64_t)kRadixThreads * radix_items_or_default(items);
+    return (uint32_t)((n + tile - 1) / tile);
+}
 inline uint32_t detect_tiles(uint64_t n) { return (uint32_t)((n + kDetectTile - 1) / kDetectTile); }
 
 // Stage launchers (all asynchronous on `s`).  Each returns cudaGetLastError().

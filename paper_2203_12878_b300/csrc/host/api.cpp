@@ -6,6 +6,7 @@
 
 #include "engine.h"
 #include "server.h"
+#include "tune.h"
 
 using namespace drf;
 
@@ -213,7 +214,7 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     if (ce != cudaSuccess) return cuda_fail(ctx, ce);
     ctx->last_error.clear();
     PrepareOpts po;
-    po.desired_warp_items = (uint64_t)ctx->sms * 128;
+    po.desired_warp_items = std::max<uint64_t>(1, (uint64_t)ctx->sms * 128 / std::max<uint32_t>(1, n));
     std::vector<Prepared> preps(n);
     std::vector<const Prepared *> valid;
     std::vector<uint32_t> where;
@@ -315,16 +316,20 @@ int drf_check_param_sweep(drf_ctx *ctx, const uint8_t *bytecode, size_t len, con
 
 // ------------------------------------------------------------------- plans
 
-int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const size_t *lens,
-                    const drf_bounds *bounds, drf_plan **out)
+}  // extern "C"
+
+namespace {
+
+// Prepares, packs and uploads a batch under one launch configuration and
+// does the sizing run (count pass, then the whole pipeline once so that
+// evaluation errors surface).  On failure returns the status and leaves
+// *out null.
+int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const size_t *lens,
+               const drf_bounds *bounds, const PlanConfig &cfg, drf_plan **out)
 {
-    if (!ctx || !out || !n || !bytecodes || !lens || !bounds) return DRF_E_INVALID_ARG;
     *out = nullptr;
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    cudaError_t ce = cudaSetDevice(ctx->device);
-    if (ce != cudaSuccess) return cuda_fail(ctx, ce);
     PrepareOpts po;
-    po.desired_warp_items = (uint64_t)ctx->sms * 128;
+    po.desired_warp_items = std::max<uint64_t>(1, (uint64_t)ctx->sms * cfg.granularity / n);
     std::vector<Prepared> preps(n);
     std::vector<const Prepared *> ptrs;
     for (uint32_t i = 0; i < n; i++) {
@@ -336,14 +341,16 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     if (!plan) return DRF_E_NOMEM;
     plan->ctx = ctx;
     plan->n = n;
+    plan->cfg = cfg;
     Error e = pack_batch(ptrs, plan->host);
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
     cudaStream_t s = ctx->stream;
     DeviceBatch &d = plan->dev;
     d.limit = ctx->opts.max_device_bytes;
+    d.radix_items = cfg.radix_items;
     e = d.load(plan->host, s);
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
-    // sizing run: the count pass gives the number of access keys
+    cudaError_t ce;
     if ((ce = launch_front(d.args, s, ctx->sms, nullptr, nullptr)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(ctx->pinned_ctrl, d.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
@@ -354,7 +361,6 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     e = d.size_keys(plan->tuples, s);
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
     d.status_launches++;
-    // complete the sizing run so evaluation errors surface now
     std::vector<DevResult> res(n);
     if ((ce = launch_back(d.args, s, ctx->sms, nullptr, nullptr)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(res.data(), d.args.results, n * sizeof(DevResult), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -364,7 +370,44 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     }
     for (uint32_t i = 0; i < n; i++)
         if (res[i].status) { delete plan; return fail(ctx, res[i].status, "protocol " + std::to_string(i) + " fails to evaluate"); }
-    // record the whole pipeline as a graph (with timing events when asked)
+    *out = plan;
+    return DRF_OK;
+}
+
+// Best of `reps` direct launches of the whole pipeline, in milliseconds.
+double time_plan(drf_plan *plan, int reps)
+{
+    drf_ctx *ctx = plan->ctx;
+    cudaStream_t s = ctx->stream;
+    DeviceBatch &d = plan->dev;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    double best = 1e30;
+    for (int r = 0; r < reps; r++) {
+        d.status_launches++;
+        cudaEventRecord(a, s);
+        launch_front(d.args, s, ctx->sms, nullptr, nullptr);
+        launch_back(d.args, s, ctx->sms, nullptr, nullptr);
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) { best = 1e30; break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        best = std::min(best, (double)ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaGetLastError();
+    return best;
+}
+
+// Records the plan's pipeline as one CUDA graph (timing events inside when
+// the context profiles stages).
+int capture_plan(drf_plan *plan)
+{
+    drf_ctx *ctx = plan->ctx;
+    cudaStream_t s = ctx->stream;
+    DeviceBatch &d = plan->dev;
     plan->profiled = (ctx->opts.flags & DRF_OPT_PROFILE_STAGES) != 0;
     if (plan->profiled) {
         plan->events.resize(4 + kMaxPasses + 3);
@@ -372,20 +415,78 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     }
     cudaEvent_t *evp = plan->profiled ? plan->events.data() : nullptr;
     int nev = 0;
-    if ((ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
-        drf_plan_destroy(plan);
-        return cuda_fail(ctx, ce);
-    }
+    cudaError_t ce;
+    if ((ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(ctx, ce);
     cudaError_t e1 = launch_front(d.args, s, ctx->sms, evp, &nev);
     cudaError_t e2 = launch_back(d.args, s, ctx->sms, evp, &nev);
     ce = cudaStreamEndCapture(s, &plan->graph);
     plan->nevents = nev;
     if (e1 != cudaSuccess || e2 != cudaSuccess || ce != cudaSuccess ||
-        (ce = cudaGraphInstantiate(&plan->exec, plan->graph, 0)) != cudaSuccess) {
-        drf_plan_destroy(plan);
+        (ce = cudaGraphInstantiate(&plan->exec, plan->graph, 0)) != cudaSuccess)
         return cuda_fail(ctx, ce != cudaSuccess ? ce : (e1 != cudaSuccess ? e1 : e2));
+    return DRF_OK;
+}
+
+std::string signature(drf_ctx *ctx, uint32_t n, const drf_plan *p)
+{
+    uint32_t maxt = 0;
+    for (const DevProto &d : p->host.protos) maxt = std::max(maxt, d.nthreads);
+    return "sms" + std::to_string(ctx->sms) + "_n" + std::to_string(bits_for(n)) + "_t" +
+           std::to_string(bits_for(p->tuples)) + "_s" + std::to_string(p->host.L.sort_bits) + "_T" +
+           std::to_string(bits_for(maxt));
+}
+
+}  // namespace
+
+extern "C" {
+
+int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const size_t *lens,
+                    const drf_bounds *bounds, drf_plan **out)
+{
+    if (!ctx || !out || !n || !bytecodes || !lens || !bounds) return DRF_E_INVALID_ARG;
+    *out = nullptr;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaError_t ce = cudaSetDevice(ctx->device);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce);
+    drf_plan *plan = nullptr;
+    int st = build_plan(ctx, n, bytecodes, lens, bounds, PlanConfig{}, &plan);
+    if (st) return st;
+    if (ctx->opts.flags & DRF_OPT_AUTOTUNE) {
+        // tune: time every candidate configuration, keep the fastest; a
+        // workload signature seen before reuses its choice
+        const std::string key = signature(ctx, n, plan);
+        PlanConfig best_cfg;
+        if (!tune_lookup(key, best_cfg)) {
+            double best = time_plan(plan, 3);
+            best_cfg = plan->cfg;
+            for (uint32_t g : kTuneGranularity)
+                for (uint32_t it : kTuneRadixItems) {
+                    PlanConfig c{g, it};
+                    if (c.granularity == plan->cfg.granularity && c.radix_items == plan->cfg.radix_items) continue;
+                    drf_plan *cand = nullptr;
+                    if (build_plan(ctx, n, bytecodes, lens, bounds, c, &cand)) continue;
+                    double ms = time_plan(cand, 3);
+                    drf_plan_destroy(cand);
+                    if (ms < best) { best = ms; best_cfg = c; }
+                }
+            tune_store(key, best_cfg, best);
+        }
+        if (best_cfg.granularity != plan->cfg.granularity || best_cfg.radix_items != plan->cfg.radix_items) {
+            drf_plan_destroy(plan);
+            plan = nullptr;
+            if ((st = build_plan(ctx, n, bytecodes, lens, bounds, best_cfg, &plan))) return st;
+        }
     }
+    if ((st = capture_plan(plan))) { drf_plan_destroy(plan); return st; }
     *out = plan;
+    return DRF_OK;
+}
+
+int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix_items)
+{
+    if (!plan) return DRF_E_INVALID_ARG;
+    if (granularity) *granularity = plan->cfg.granularity;
+    if (radix_items) *radix_items = plan->cfg.radix_items;
     return DRF_OK;
 }
 

@@ -173,6 +173,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.ctrl = (Control *)ctrl.p;
     a.epoch = (uint32_t *)epoch.p;
     a.L = b.L;
+    a.radix_items = radix_items;
     a.nkeys = 0;
     a.ntiles = 0;
     a.keys[0] = (unsigned long long *)keys0.p;
@@ -183,7 +184,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
 
 Error DeviceBatch::size_keys(uint64_t n, cudaStream_t s)
 {
-    const uint32_t tiles = radix_tiles(n);
+    const uint32_t tiles = radix_tiles(n, args.radix_items);
     const size_t kb = std::max<uint64_t>(n, 1) * 8;
     const size_t sb = std::max<size_t>((size_t)args.L.passes * tiles * kRadixBins * 8, 16);
     size_t old_status = status.cap;

@@ -11,6 +11,7 @@
 #include "../../../include/drf.h"
 #include "../cuda/pipeline.cuh"
 #include "prepare.h"
+#include "tune.h"
 
 namespace drf {
 
@@ -51,6 +52,7 @@ struct DeviceBatch {
     uint64_t limit = 0;
     uint64_t status_launches = 0;     // launches since the look-back words were cleared
     uint64_t h2d_bytes = 0, d2h_bytes = 0;   // copies of the last run
+    uint32_t radix_items = 16;                // radix tile shape (tuning choice)
     BatchArgs args{};
 
     ~DeviceBatch();
@@ -91,6 +93,7 @@ struct drf_plan {
     std::vector<cudaEvent_t> events;
     int nevents = 0;
     bool profiled = false;
+    drf::PlanConfig cfg;
 };
 
 namespace drf {

@@ -81,7 +81,7 @@ public:
         std::unique_ptr<Request> r(new Request);
         r->t_submit = Clock::now();
         PrepareOpts po;
-        po.desired_warp_items = (uint64_t)ctx_->sms * 128;
+        po.desired_warp_items = (uint64_t)ctx_->sms * 2;      // a request shares its round with others
         Error e = prepare(bc, len, b->nthreads, b->nlocs, b->loc_cells, b->nparams, b->params, po, r->prep);
         std::lock_guard<std::mutex> g(mu_);
         if (stopping_) return S_BUSY;

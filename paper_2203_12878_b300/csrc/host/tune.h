@@ -1,0 +1,25 @@
+// Autotuning of a plan's launch configuration and its cache.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+namespace drf {
+
+// A plan's tunable launch configuration.
+struct PlanConfig {
+    uint32_t granularity = 128;   // desired warp-items per SM for the whole batch (item-to-warp schedule)
+    uint32_t radix_items = 16;    // keys per thread of a radix tile (12, 16 or 24)
+};
+
+// Candidate configurations the tuner times.
+constexpr uint32_t kTuneGranularity[] = {32, 128, 512};
+constexpr uint32_t kTuneRadixItems[] = {12, 16, 24};
+
+// Process-wide cache of tuned configurations, keyed by a workload signature;
+// when DRF_TUNE_CACHE names a file the cache is loaded from it once and
+// every new entry is appended to it.
+bool tune_lookup(const std::string &key, PlanConfig &out);
+void tune_store(const std::string &key, const PlanConfig &cfg, double ms);
+
+}  // namespace drf

@@ -24,6 +24,7 @@ STATUS = {
 }
 VERDICTS = {-1: None, 0: "DRF", 1: "RACY", 2: "BARRIER_DIVERGENCE"}
 OPT_PROFILE_STAGES = 0x1
+OPT_AUTOTUNE = 0x2
 
 
 class DrfError(RuntimeError):
@@ -107,6 +108,7 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "drf_plan_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "drf_plan_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "drf_plan_destroy": (None, [_P]),
     "drf_server_start": (ctypes.c_int, [_P, ctypes.POINTER(drf_server_opts)]),
     "drf_server_submit": (ctypes.c_int, [_P, _U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds),
@@ -381,6 +383,14 @@ def drf_plan_stage_times(plan) -> list:
     if st != 0:
         raise DrfError(st)
     return [(names[i].decode(), ms[i]) for i in range(n.value)]
+
+
+def drf_plan_config(plan) -> dict:
+    g, it = ctypes.c_uint32(), ctypes.c_uint32()
+    st = lib().drf_plan_config(plan, ctypes.byref(g), ctypes.byref(it))
+    if st != 0:
+        raise DrfError(st)
+    return {"granularity": g.value, "radix_items": it.value}
 
 
 def drf_plan_destroy(plan) -> None:

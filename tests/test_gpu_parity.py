@@ -252,3 +252,23 @@ def test_config3_full_size(ctx, oracle, racy):
     assert cell["total"] == got["tuples"] and cell["racy"]
     assert {k: got[k] for k in ("tid_i", "tid_j", "i_writes", "j_writes")} == \
            {k: cell[k] for k in ("tid_i", "tid_j", "i_writes", "j_writes")}
+
+
+def test_autotuned_batched_plan(oracle):
+    """The batched workload's shape through an autotuned plan (every
+    candidate launch configuration is run while tuning): the chosen
+    configuration is a candidate and every result equals the oracle."""
+    c = drf.drf_ctx_create(0, flags=drf.OPT_AUTOTUNE)
+    try:
+        ps = protogen.config4(master_seed=11, count=64)
+        plan = drf.drf_plan_create(c, [drf.drf_protocol_compile(p.text) for p in ps],
+                                   [(p.nthreads, p.cells, p.params) for p in ps])
+        cfg = drf.drf_plan_config(plan)
+        assert cfg["granularity"] in (32, 128, 512) and cfg["radix_items"] in (12, 16, 24)
+        for _ in range(2):
+            drf.drf_plan_launch(plan)
+            for p, r in zip(ps, drf.drf_plan_results(plan)):
+                assert same(drf.result_dict(r), want(oracle, p))
+        drf.drf_plan_destroy(plan)
+    finally:
+        drf.drf_ctx_destroy(c)

@@ -152,6 +152,69 @@ def time_oracle(p, min_seconds):
 
 # ------------------------------------------------------------------ ours --
 
+def time_steps(plan, steps, warmup, stream, flush, clk_dev=None):
+    """Times `steps` graph launches of `plan` on `stream` (L2 flushed before
+    each, outside the events).  Returns per-step ms, per-stage launch lists
+    {kind: [(name, ms), ...]}, the clock summary and the wall time."""
+    import torch
+    from paper_2203_12878_b300 import drf
+
+    def step(evs):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            drf.drf_plan_launch(plan, stream)
+            e.record(stream)
+        if evs is not None:
+            evs.append((s, e))
+
+    for _ in range(warmup):
+        step(None)
+    torch.cuda.synchronize()
+    evs, kinds = [], {}
+    sampler = ClockSampler(clk_dev) if clk_dev is not None else None
+    if sampler:
+        sampler.__enter__()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step(evs)
+        stream.synchronize()
+        for name, t in drf.drf_plan_stage_times(plan):
+            kind = "radix" if name.startswith("radix") else name
+            kinds.setdefault(kind, []).append((name, t))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = None
+    if sampler:
+        sampler.__exit__(None, None, None)
+        clocks = sampler.summary()
+    return [s.elapsed_time(e) for s, e in evs], kinds, clocks, wall
+
+
+def roofline(kinds, steps, n, info):
+    """Roofline entry of the dominant kernel (largest device time per step)."""
+    totals = {k: sum(t for _, t in v) / steps for k, v in kinds.items()}
+    dominant = max(totals, key=totals.get)
+    peak, peak_kind = _peaks()
+    # algorithmic bytes per launch: radix pass = read + write every key (16 B);
+    # emit = write every key (8 B); detect = read every key (8 B)
+    bytes_per = {"radix": 16 * n, "emit": 8 * n, "detect": 8 * n}
+    radix_launches = [t for _, t in kinds.get("radix", []) if t > 0.002]
+    dom_ms = (statistics.mean(radix_launches) if dominant == "radix" and radix_launches
+              else totals[dominant] / max(1, len(kinds[dominant]) // steps))
+    if dominant in bytes_per:
+        achieved = bytes_per[dominant] / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"k_{dominant}", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": _profiled_traffic(dominant), "launch_ms": round(dom_ms, 4),
+                "algorithmic_bytes_per_launch": bytes_per[dominant]}
+    else:
+        roof = {"bound": "alu", "kernel": f"k_{dominant}", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "launch_ms": round(dom_ms, 4)}
+    return roof, {k: round(v, 4) for k, v in sorted(totals.items())}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2203_12878_b300 import drf
@@ -164,74 +227,52 @@ def run_ours(args, rank, world):
         from paper_2203_12878_b300 import protogen
         p = protogen.config2(rank, "literal")
     bc = drf.drf_protocol_compile(p.text)
-    ctx = drf.drf_ctx_create(dev, flags=drf.OPT_PROFILE_STAGES)
-    plan = drf.drf_plan_create(ctx, [bc], [(p.nthreads, p.cells, p.params)])
+    bounds = [(p.nthreads, p.cells, p.params)]
+    flags = drf.OPT_PROFILE_STAGES | {"auto": drf.OPT_AUTOTUNE, "sort": drf.OPT_PATH_SORT,
+                                      "table": drf.OPT_PATH_TABLE}[args.path]
+    ctx = drf.drf_ctx_create(dev, flags=flags)
+    t_plan = time.perf_counter()
+    plan = drf.drf_plan_create(ctx, [bc], bounds)
+    plan_s = time.perf_counter() - t_plan
     info = drf.drf_plan_info(plan)
+    path = drf.drf_plan_path(plan)
     n = info["tuples"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    stage_acc = {}
-    def step(timed, evs):
-        with torch.cuda.stream(stream):
-            flush.fill_(1)
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            drf.drf_plan_launch(plan, stream)
-            e.record(stream)
-        if timed:
-            evs.append((s, e))
-
-    for _ in range(args.warmup):
-        step(False, None)
+    drf.drf_plan_launch(plan, stream)
     torch.cuda.synchronize()
     res = drf.result_dict(drf.drf_plan_results(plan)[0])
-
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    evs, per_stage = [], []
     torch.cuda.synchronize()
-    with ClockSampler(dev) as clk:
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            step(True, evs)
-            stream.synchronize()
-            per_stage.append(drf.drf_plan_stage_times(plan))
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+    step_ms, kinds, clocks, wall = time_steps(plan, args.steps, args.warmup, stream, flush, clk_dev=dev)
     if world > 1:
         dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in evs]
     ms = statistics.mean(step_ms)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    roof, stages = roofline(kinds, args.steps, n, info)
 
-    # per-kernel device times (events inside the graph, on the launching stream)
-    kinds = {}
-    for st in per_stage:
-        for name, t in st:
-            kind = "radix" if name.startswith("radix") else name
-            kinds.setdefault(kind, []).append((name, t))
-    totals = {k: sum(t for _, t in v) / args.steps for k, v in kinds.items()}
-    dominant = max(totals, key=totals.get)
-    peak, peak_kind = _peaks()
-    # algorithmic bytes per launch: radix pass = read + write every key (16 B);
-    # emit = write every key (8 B); detect = read every key (8 B)
-    bytes_per = {"radix": 16 * n, "emit": 8 * n, "detect": 8 * n}
-    radix_launches = [t for _, t in kinds.get("radix", []) if t > 0.002]
-    dom_ms = (statistics.mean(radix_launches) if dominant == "radix" and radix_launches
-              else totals[dominant] / max(1, len(kinds[dominant]) // args.steps))
-    if dominant in bytes_per:
-        achieved = bytes_per[dominant] / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": f"k_{dominant}", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": _profiled_traffic(dominant), "launch_ms": round(dom_ms, 4),
-                "algorithmic_bytes_per_launch": bytes_per[dominant]}
-    else:
-        roof = {"bound": "alu", "kernel": f"k_{dominant}", "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None, "launch_ms": round(dom_ms, 4)}
+    # the other back end on the same protocol, for comparison
+    other = None
+    if rank == 0 and not args.quick and args.path == "auto":
+        octx = drf.drf_ctx_create(dev, flags=drf.OPT_PROFILE_STAGES |
+                                  (drf.OPT_PATH_SORT if path == "table" else drf.OPT_PATH_TABLE))
+        try:
+            oplan = drf.drf_plan_create(octx, [bc], bounds)
+            osteps = max(20, args.steps // 5)
+            oms, okinds, _, _ = time_steps(oplan, osteps, 3, stream, flush)
+            assert drf.result_dict(drf.drf_plan_results(oplan)[0]) == res
+            oroof, ostages = roofline(okinds, osteps, n, drf.drf_plan_info(oplan))
+            other = {"path": drf.drf_plan_path(oplan), "ms_per_step": statistics.mean(oms),
+                     "value": n / (statistics.mean(oms) * 1e-3), "stages_ms": ostages, "roofline": oroof}
+            drf.drf_plan_destroy(oplan)
+        except drf.DrfError as e:
+            other = {"unavailable": str(e)}
+        drf.drf_ctx_destroy(octx)
 
     # end to end through the public API: host bytecode in, host result out
     e2e_t = []
@@ -255,14 +296,17 @@ def run_ours(args, rank, world):
         out = {
             "metric": METRIC, "value": world * n / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys, int32/int64 index arithmetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": ("u32/u64 owner records" if path == "table" else "u64 keys") + ", int32/int64 index arithmetic",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "tuples_per_step": n, "sort_passes": info["sort_passes"],
-                       "sort_bits": info["sort_bits"], "verdict": res.get("verdict"),
+            "config": {"workload": WORKLOAD, "tuples_per_step": n, "path": path, "path_choice": args.path,
+                       "plan": {**drf.drf_plan_config(plan), "create_s": round(plan_s, 3)},
+                       "sort_passes": info["sort_passes"], "sort_bits": info["sort_bits"],
+                       "verdict": res.get("verdict"),
                        "l2": "flushed before every step (256 MiB write, outside the timed events)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
-            "stages_ms": {k: round(v, 4) for k, v in sorted(totals.items())},
+            "stages_ms": stages,
+            "other_path": other,
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"the same protocol with its first 128 of 1024 threads, "
                                        f"per-cell-record checker, {cpu_runs} runs in {cpu_el:.1f} s"},
@@ -270,7 +314,7 @@ def run_ours(args, rank, world):
                     "ms_per_step": e2e_s * 1e3,
                     "path": "drf_check: host bytecode -> validate/lower -> H2D -> all kernels -> D2H result"},
             "gpu_launches": info["kernels_per_launch"] * args.steps,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "wall_s_timed_region": wall,
         }
         out.update(extra)
@@ -392,6 +436,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--path", choices=("auto", "sort", "table"), default="auto",
+                    help="back end of the timed plan: chosen per batch (autotuned), or forced")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--rates", type=float, nargs="*", default=[1000, 5000, 20000, 50000],
                     help="served-workload arrival rates (requests/s)")

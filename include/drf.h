@@ -134,6 +134,27 @@ typedef struct {
 
 #define DRF_OPT_PROFILE_STAGES 0x1u   /* record per-kernel CUDA events in plans */
 #define DRF_OPT_AUTOTUNE       0x2u   /* plans: time candidate launch configurations, keep the fastest */
+/* Back end (at most one; neither = chosen per batch).  Both decide
+ * Definition 1 exactly and return identical results:
+ *   sort path   -- one 64-bit key per access (phase, array, index, tid, mode),
+ *                  radix-sorted on the cell fields, racy segments detected;
+ *   owner table -- one record per (phase, array, index) cell, rows up to the
+ *                  static bound on syncs; each access ORs (tid, ~tid, write)
+ *                  into its cell, a cell is racy iff written with two
+ *                  distinct accessors, and a second pass restricted to the
+ *                  first racy cell finds the witness threads.  It needs
+ *                  (sync bound + 1) x (sum of array sizes) x 4 bytes (8 when
+ *                  thread ids exceed 15 bits), at most 64 GiB, and thread
+ *                  ids below 2^31.
+ * The automatic choice takes the owner table when it fits and is at most
+ * max(256 MiB, 256 bytes per access tuple); otherwise, or when the table
+ * cannot be allocated, the sort path.  Forcing the owner table on a batch
+ * it cannot hold returns DRF_E_LIMIT (or DRF_E_NOMEM). */
+#define DRF_OPT_PATH_SORT      0x4u
+#define DRF_OPT_PATH_TABLE     0x8u
+
+#define DRF_PATH_SORT  1
+#define DRF_PATH_TABLE 2
 
 /* ------------------------------------------------------- library / errors -- */
 
@@ -273,7 +294,8 @@ int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_bounds *bou
  * sets *n to their number.  layout[0..4] receive the key's field widths:
  * tid, index, array, phase and protocol bits; a key is, from its most
  * significant field down, protocol | phase | array | index | tid | mode
- * (mode 1 = write). */
+ * (mode 1 = write).  DRF_E_NOT_FOUND when that check ran the owner-table
+ * path (which sorts nothing). */
 int drf_debug_sorted_keys(drf_ctx *ctx, uint64_t *keys, uint64_t cap, uint64_t *n, uint32_t layout[5]);
 
 /* A parameter swept over a range in one batched pass: checks the protocol
@@ -320,6 +342,11 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
  * workload signature for the process and, when the environment variable
  * DRF_TUNE_CACHE names a file, persisted there. */
 int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix_items);
+
+/* The back end a plan runs: DRF_PATH_SORT or DRF_PATH_TABLE (see
+ * DRF_OPT_PATH_*).  With DRF_OPT_AUTOTUNE the tuner times both back ends
+ * (the owner table once per granularity) when the owner table fits. */
+int drf_plan_path(const drf_plan *plan, uint32_t *path);
 
 /* Releases the plan's device memory and graph. */
 void drf_plan_destroy(drf_plan *plan);

@@ -5,6 +5,8 @@
 //   count     interpret every (item, thread): accesses, syncs, first error
 //   scan      per thread, exclusive scan of syncs over items -> phase at item
 //             start; exclusive scan of per-warp access counts -> key offsets
+//
+// Then one of two back ends.  Sort path:
 //   emit      interpret again, writing one 64-bit key per access
 //             (proto | phase | array | index | tid | mode), coalesced per
 //             warp; builds the digit histograms of every radix pass
@@ -15,9 +17,19 @@
 //   detect    segments of equal (proto, phase, array, index); a segment is
 //             racy iff it holds a write and two distinct tids; min-reduce the
 //             sorted position of the first racy segment per protocol
+// Owner-table path (no sort; one record per (proto, phase, array, index)):
+//   table     interpret again, OR-ing each access's owner record (tid, its
+//             complement, the write bit) into its cell and marking the
+//             cell's block as touched
+//   tscan     read the touched blocks: a cell is racy iff written and its
+//             accessors are not all one thread; min-reduce the first racy
+//             position per protocol; clear what was read
+//   witness   interpret the racy protocols once more, up to the witness
+//             cell's phase, collecting which threads access / write it
+// Both:
 //   finalize  per protocol: first evaluation error (smallest tid, then the
 //             number of accesses before it), else barrier divergence, else
-//             the witness of the first racy segment: i = smallest accessor,
+//             the witness of the first racy cell: i = smallest accessor,
 //             j = its smallest admissible partner
 #include <cstdint>
 
@@ -187,15 +199,105 @@ __device__ __forceinline__ V fast_post(V v, uint32_t kind, U c)
     return v;
 }
 
+// Interpretation modes of one item.
+enum : int {
+    M_COUNT = 0,   // accesses, syncs and the first error per (item, thread)
+    M_EMIT = 1,    // one sort key per access
+    M_TAB32 = 2,   // OR one 32-bit owner record per access into the table
+    M_TAB64 = 3,   // the same with 64-bit records
+    M_CELL = 4,    // which threads access / write one given cell
+};
+
+// Owner records.  Definition 1 asks, per cell, whether some access writes it
+// and whether two different threads access it.  An access contributes its
+// thread id, the id's complement and its write bit; OR-ing the contributions
+// of all accesses to a cell leaves OR(tid), the complement of AND(tid) and
+// "written".  The cell is racy iff it is written and AND(tid) != OR(tid),
+// i.e. the accessors are not all one thread.  32-bit records hold 15-bit
+// thread ids, 64-bit records 31-bit ones.
+__device__ __forceinline__ unsigned long long owner_rec32(uint32_t tid, uint32_t w)
+{
+    return (tid & 0x7FFFu) | ((~tid & 0x7FFFu) << 15) | (w << 31);
+}
+__device__ __forceinline__ unsigned long long owner_rec64(uint32_t tid, uint32_t w)
+{
+    return (unsigned long long)(tid & 0x7FFFFFFFu) | ((unsigned long long)(~tid & 0x7FFFFFFFu) << 31) |
+           ((unsigned long long)w << 63);
+}
+__device__ __forceinline__ bool owner_racy32(uint32_t r)
+{
+    return (r >> 31) && (r & 0x7FFFu) != (~(r >> 15) & 0x7FFFu);
+}
+__device__ __forceinline__ bool owner_racy64(unsigned long long r)
+{
+    return (r >> 63) && (r & 0x7FFFFFFFull) != (~(r >> 31) & 0x7FFFFFFFull);
+}
+
+// ORs each valid lane's record into the table and marks the record's block
+// as touched.  When every valid lane hits one cell (an index that does not
+// depend on tid), the warp combines its records and one lane writes.  A
+// lane first reads the record through L1 and skips the OR when the record
+// already holds all its bits: records only gain bits during a launch, so a
+// stale copy can only under-report and the skip never loses a bit -- but it
+// removes most same-address atomics on cells that many accesses share.
+// Each lane remembers the last block it marked.
+template <bool R64>
+__device__ __forceinline__ void table_put(const BatchArgs &a, bool ok, unsigned long long off,
+                                          unsigned long long rec, unsigned long long &last_bid)
+{
+    const unsigned m = __ballot_sync(kFull, ok);
+    if (m == 0) return;
+    const int lead = __ffs(m) - 1;
+    const unsigned long long off0 = __shfl_sync(kFull, off, lead);
+    bool mine = ok;
+    if (__all_sync(kFull, !ok || off == off0)) {
+        const unsigned long long r = ok ? rec : 0ull;
+        const uint32_t lo = __reduce_or_sync(kFull, (uint32_t)r);
+        const uint32_t hi = R64 ? __reduce_or_sync(kFull, (uint32_t)(r >> 32)) : 0u;
+        rec = ((unsigned long long)hi << 32) | lo;
+        mine = (int)(threadIdx.x & 31) == lead;
+    }
+    if (mine) {
+        if (R64) {
+            unsigned long long *cell = reinterpret_cast<unsigned long long *>(a.table) + off;
+            const unsigned long long cur = __ldca(cell);
+            if ((cur | rec) != cur) atomicOr(cell, rec);
+        } else {
+            uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
+            const uint32_t cur = __ldca(cell);
+            if ((cur | (uint32_t)rec) != cur) atomicOr(cell, (uint32_t)rec);
+        }
+        // touch bit: a few hot blocks share one bitmap word, so it is read
+        // through L1 first like the record (bits only get set in a launch)
+        const unsigned long long bid = off >> kTabBlockLog;
+        if (bid != last_bid) {
+            const uint32_t bit = 1u << (uint32_t)(bid & 31);
+            if (!(__ldca(&a.touch[bid >> 5]) & bit)) atomicOr(&a.touch[bid >> 5], bit);
+            last_bid = bid;
+        }
+    }
+}
+
+// The cell whose accessors the M_CELL pass collects.
+struct CellTarget {
+    uint32_t phase, loc;
+    unsigned long long idx;
+};
+
 // Interprets one item for the 32 threads of a warp (threads 32g .. 32g+31).
 // All lanes fetch the instruction at the smallest pc among running lanes and
 // only lanes at that pc execute it, so lanes that diverge on a thread-
 // dependent condition or trip count re-converge at the join point.
-template <typename V, bool EMIT>
+template <typename V, int MODE>
 __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, const ItemDesc &it, uint32_t k,
-                         uint32_t g, uint32_t w, EmitShared *sh)
+                         uint32_t g, uint32_t w, EmitShared *sh, const CellTarget &tg)
 {
     using U = typename Unsigned<V>::T;
+    constexpr bool EMIT = MODE == M_EMIT;
+    constexpr bool R64 = MODE == M_TAB64;
+    constexpr bool TAB = MODE == M_TAB32 || MODE == M_TAB64;
+    constexpr bool CELL = MODE == M_CELL;
+    constexpr bool PHASED = MODE != M_COUNT;      // knows the phase of every access
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t tid = g * 32 + lane;
     const bool alive = tid < P.nthreads;
@@ -234,14 +336,21 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
     if (running && pc == it.stop_pc) running = false;
 
     uint32_t phase = 0;
+    if (PHASED && alive) phase = a.phs[li];
+    if (CELL && phase > tg.phase) running = false;     // phases only grow: nothing here reaches the cell
     unsigned long long cursor = 0, wend = 0;
     if (EMIT) {
-        if (alive) phase = a.phs[li];
         cursor = a.wbase[w];
         wend = cursor + a.wcnt[w];
     }
     const KeyLayout L = a.L;
     const unsigned long long tidpart = (((unsigned long long)tid) << 1);
+    // owner-table state
+    const uint64_t *cb = a.cbase + P.cells_off;
+    unsigned long long last_bid = kNone;
+    const unsigned long long rec_rd = R64 ? owner_rec64(tid, 0) : owner_rec32(tid, 0);
+    const unsigned long long rec_wr = R64 ? owner_rec64(tid, 1) : owner_rec32(tid, 1);
+    uint32_t hit = 0;                                  // M_CELL: 1 accessed, 2 wrote
 
     while (true) {
         unsigned act = __ballot_sync(kFull, running);
@@ -253,7 +362,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
         case I_ACCESS: {
             bool ok = ex;
             V idx = 0;
-            if (ex && (EMIT || (in.a & AF_EVAL_IN_COUNT))) {
+            if (ex && (PHASED || (in.a & AF_EVAL_IN_COUNT))) {
                 if (!eval<V>(xc, in.c, tid, vars, idx)) { err = kErrDiv0; ok = false; }
                 else if (idx < 0 || (uint64_t)(U)idx >= __ldg(cells + in.b)) { err = kErrOob; ok = false; }
             }
@@ -268,6 +377,15 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                 }
                 hist_add(sh, L, key_or_zero(ok, p, phase, in.b, (unsigned long long)(U)idx, tidpart, in.a, L), ok);
                 cursor += __popc(em);
+            } else if (TAB) {
+                const bool put = ok && phase < P.tab_phases;
+                if (ok && !put) atomicOr(&a.ctrl->flags, CF_TABLE_RANGE);
+                const unsigned long long off =
+                    put ? P.tab_off + (uint64_t)phase * P.cells_sum + __ldg(cb + in.b) + (uint64_t)(U)idx : 0ull;
+                table_put<R64>(a, put, off, (in.a & AF_WRITE) ? rec_wr : rec_rd, last_bid);
+            } else if (CELL) {
+                if (ok && phase == tg.phase && in.b == tg.loc && (unsigned long long)(U)idx == tg.idx)
+                    hit |= 1u | ((in.a & AF_WRITE) << 1);
             } else if (ok) {
                 count++;
             }
@@ -275,7 +393,11 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             break;
         }
         case I_SYNC:
-            if (ex) { if (EMIT) phase++; else syncs++; pc++; }
+            if (ex) {
+                if (PHASED) phase++; else syncs++;
+                pc++;
+                if (CELL && phase > tg.phase) running = false;
+            }
             break;
         case I_LOOP:
             if (ex) {
@@ -318,12 +440,13 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             }
             const uint64_t trip = (okb && lo < hi) ? (uint64_t)(U)((U)hi - (U)lo) : 0;
             const uint32_t m = (uint32_t)in.e;
-            if (!EMIT) {
+            if (!PHASED) {
                 if (okb) { count += (uint32_t)(trip * m); syncs += (uint32_t)(trip * in.b); }
             } else {
                 V rest[kFastMax];
                 U coef[kFastMax], pcon[kFastMax];
                 uint32_t meta[kFastMax];
+                uint64_t lim[kFastMax];                          // owner table: array size
 #pragma unroll
                 for (uint32_t j = 0; j < kFastMax; j++) {
                     if (j < m) {
@@ -334,15 +457,16 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                         pcon[j] = (U)__ldg(xc + A.d + 1);
                         meta[j] = (uint32_t)A.a | ((uint32_t)A.b << 8);
                         meta[j] |= (uint32_t)A.e << 24;          // phase offset: at most 255 syncs per iteration
+                        if (TAB) lim[j] = __ldg(cells + A.b);
                     }
                 }
                 const uint32_t spi = in.b;
                 for (uint64_t t = 0;; t++) {
-                    const bool act = okb && t < trip;
+                    const uint32_t ph0 = phase + (uint32_t)(t * spi);
+                    const bool act = okb && t < trip && (!CELL || ph0 <= tg.phase);
                     const unsigned am = __ballot_sync(kFull, act);
                     if (am == 0) break;
                     const V x = (V)((U)lo + (U)t);
-                    const uint32_t ph0 = phase + (uint32_t)(t * spi);
                     const unsigned long long before = __popc(am & lanemask_lt());
 #pragma unroll
                     for (uint32_t j = 0; j < kFastMax; j++) {
@@ -350,21 +474,36 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                             const uint32_t mt = meta[j];
                             const V v = (V)((U)rest[j] + coef[j] * (U)x);
                             const V idx = fast_post<V, U>(v, (mt >> 2) & 3, pcon[j]);
-                            const unsigned long long key =
-                                act ? make_key(p, ph0 + (mt >> 24), (mt >> 8) & 0xFFFF, (unsigned long long)(U)idx,
-                                               tidpart, mt & AF_WRITE, L)
-                                    : 0ull;
-                            if (act) {
-                                unsigned long long pos = cursor + before;
-                                if (pos < wend && pos < a.nkeys) a.keys[0][pos] = key;
-                                else atomicOr(&a.ctrl->flags, CF_EMIT_OVERFLOW);
+                            const uint32_t ph = ph0 + (mt >> 24), loc = (mt >> 8) & 0xFFFF;
+                            if (EMIT) {
+                                const unsigned long long key =
+                                    act ? make_key(p, ph, loc, (unsigned long long)(U)idx, tidpart, mt & AF_WRITE, L)
+                                        : 0ull;
+                                if (act) {
+                                    unsigned long long pos = cursor + before;
+                                    if (pos < wend && pos < a.nkeys) a.keys[0][pos] = key;
+                                    else atomicOr(&a.ctrl->flags, CF_EMIT_OVERFLOW);
+                                }
+                                hist_add(sh, L, key, act);
+                                cursor += __popc(am);
+                            } else if (TAB) {
+                                // the lowering proved the index in range; the check keeps every
+                                // table write inside this protocol's rows regardless
+                                const bool put = act && ph < P.tab_phases && idx >= 0 && (uint64_t)(U)idx < lim[j];
+                                if (act && !put) atomicOr(&a.ctrl->flags, CF_TABLE_RANGE);
+                                const unsigned long long off =
+                                    put ? P.tab_off + (uint64_t)ph * P.cells_sum + __ldg(cb + loc) + (uint64_t)(U)idx
+                                        : 0ull;
+                                table_put<R64>(a, put, off, (mt & AF_WRITE) ? rec_wr : rec_rd, last_bid);
+                            } else if (CELL) {
+                                if (act && ph == tg.phase && loc == tg.loc && (unsigned long long)(U)idx == tg.idx)
+                                    hit |= 1u | ((mt & AF_WRITE) << 1);
                             }
-                            hist_add(sh, L, key, act);
-                            cursor += __popc(am);
                         }
                     }
                 }
                 if (okb) phase += (uint32_t)(trip * spi);
+                if (CELL && phase > tg.phase) running = false;
             }
             if (okb) pc = mpc + 1 + m;
             break;
@@ -376,7 +515,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
         if (ex && running && pc == it.stop_pc) running = false;
     }
 
-    if (!EMIT && alive) {
+    if (!PHASED && alive) {
         a.cnt[li] = count;
         a.syn[li] = syncs;
         if (err) {
@@ -384,7 +523,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             atomicMin(&a.err_key[p], ((unsigned long long)tid << 32) | k);
         }
     }
-    if (!EMIT) {
+    if (!PHASED) {
         uint32_t total = __reduce_add_sync(kFull, count);
         if (lane == 0) {
             a.wcnt[w] = total;
@@ -393,6 +532,11 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                 atomicAdd(&a.ptuples[p], (unsigned long long)total);
             }
         }
+    }
+    if (CELL && hit) {
+        const uint64_t b = P.tid_off + tid;
+        atomicOr(&a.hit_acc[b >> 5], 1u << (uint32_t)(b & 31));
+        if (hit & 2) atomicOr(&a.hit_wr[b >> 5], 1u << (uint32_t)(b & 31));
     }
 }
 
@@ -413,35 +557,70 @@ __global__ void k_init(BatchArgs a)
     if (i == 0) *a.epoch = *a.epoch + 1;
 }
 
+// The witness cell of protocol P from its first racy owner-table position.
+__device__ __forceinline__ CellTarget decode_cell(const BatchArgs &a, const DevProto &P, unsigned long long pos)
+{
+    const unsigned long long rel = pos - P.tab_off;
+    const unsigned long long row = rel / P.cells_sum;
+    const unsigned long long c = rel - row * P.cells_sum;
+    const uint64_t *cb = a.cbase + P.cells_off;
+    uint32_t l = 0;
+    while (l + 1 < P.nlocs && __ldg(cb + l + 1) <= c) l++;
+    return CellTarget{(uint32_t)row, l, c - __ldg(cb + l)};
+}
+
+template <int MODE> struct InterpShared { unsigned int unused; };
+template <> struct InterpShared<M_EMIT> { EmitShared e; };
+
 // One kernel per arithmetic width (WIDE: 64-bit); each skips the warp-items
 // of protocols of the other width.
-template <bool EMIT, bool WIDE>
+template <int MODE, bool WIDE>
 __global__ void __launch_bounds__(256) k_interp(BatchArgs a)
 {
-    __shared__ EmitShared sh;
-    if (EMIT) {
-        for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) (&sh.hist[0][0])[i] = 0;
+    constexpr bool EMIT = MODE == M_EMIT;
+    __shared__ InterpShared<MODE> shm;
+    EmitShared *sh = nullptr;
+    if constexpr (EMIT) {
+        sh = &shm.e;
+        for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) (&sh->hist[0][0])[i] = 0;
         __syncthreads();
     }
     const uint32_t warps = gridDim.x * (blockDim.x / 32);
+    CellTarget tg{};
+    uint32_t tg_proto = 0xFFFFFFFFu;     // M_CELL: protocol whose witness cell tg holds
+    bool tg_live = false;
     for (uint32_t w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < a.nwitems; w += warps) {
         const WarpItem wi = a.witems[w];
         const DevProto P = a.protos[wi.proto];
         if ((P.wide != 0) != WIDE) continue;
+        if (MODE == M_CELL) {
+            // only racy protocols whose verdict is not an error or a divergence
+            if (wi.proto != tg_proto) {
+                tg_proto = wi.proto;
+                const unsigned long long bp = a.best_pos[wi.proto];
+                tg_live = bp != kNone && a.err_key[wi.proto] == kNone && a.div_tid[wi.proto] == 0xFFFFFFFFu;
+                if (tg_live) tg = decode_cell(a, P, bp);
+            }
+            if (!tg_live) continue;
+            // nothing to do for an item that starts after the witness phase in every lane
+            const uint32_t tid = wi.g * 32 + (threadIdx.x & 31);
+            const bool reach = tid < P.nthreads && a.phs[P.lane_off + (uint64_t)wi.k * P.nthreads + tid] <= tg.phase;
+            if (!__any_sync(kFull, reach)) continue;
+        }
         const ItemDesc it = a.items[P.item_off + wi.k];
-        if (EMIT && wi.k == 0) {
+        if (MODE != M_COUNT && MODE != M_CELL && wi.k == 0) {
             // barrier divergence: every thread must run as many syncs as thread 0
             uint32_t tid = wi.g * 32 + (threadIdx.x & 31);
             if (tid < P.nthreads && a.totsyn[P.tid_off + tid] != a.totsyn[P.tid_off])
                 atomicMin(&a.div_tid[wi.proto], tid);
         }
-        if (WIDE) run_item<int64_t, EMIT>(a, wi.proto, P, it, wi.k, wi.g, w, &sh);
-        else run_item<int32_t, EMIT>(a, wi.proto, P, it, wi.k, wi.g, w, &sh);
+        if (WIDE) run_item<int64_t, MODE>(a, wi.proto, P, it, wi.k, wi.g, w, sh, tg);
+        else run_item<int32_t, MODE>(a, wi.proto, P, it, wi.k, wi.g, w, sh, tg);
     }
-    if (EMIT) {
+    if constexpr (EMIT) {
         __syncthreads();
         for (int i = threadIdx.x; i < (int)(a.L.passes * kRadixBins); i += blockDim.x) {
-            unsigned int v = (&sh.hist[0][0])[i];
+            unsigned int v = (&sh->hist[0][0])[i];
             if (v) atomicAdd(&a.hist[i], (unsigned long long)v);
         }
     }
@@ -798,6 +977,148 @@ __global__ void __launch_bounds__(1024) k_resolve(BatchArgs a)
     }
 }
 
+// ------------------------------------------------------------ owner table
+
+// Protocol whose table rows hold record `pos` (the last one starting at or
+// before it).
+__device__ uint32_t proto_of_record(const BatchArgs &a, unsigned long long pos)
+{
+    uint32_t lo = 0, hi = a.nprotos - 1;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi + 1) / 2;
+        if (__ldg(&a.protos[mid].tab_off) <= pos) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Reads every touched block of the owner table: records a protocol's first
+// racy cell (the smallest position: rows are phase-major, then array, then
+// index, the lexicographic order of the witness) and clears every record it
+// read and every touch word, so that table and bitmap are all zero again for
+// the next launch.  A warp takes 32 touch words at a time (one per lane) and
+// then their touched blocks, up to BLK in flight.  Also clears the witness
+// hit bits for the M_CELL pass that follows.
+template <bool R64>
+__global__ void __launch_bounds__(kTabScanThreads) k_tscan(BatchArgs a)
+{
+    constexpr int BLK = R64 ? 2 : 4;
+    constexpr int V4 = R64 ? 4 : 2;                     // uint4 loads per lane per block
+    constexpr int PER = kTabBlock / 32;                 // records per lane per block
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kTabScanThreads;
+    for (uint64_t i = blockIdx.x * (uint64_t)kTabScanThreads + threadIdx.x; i < a.nhit; i += gthreads) {
+        a.hit_acc[i] = 0;
+        a.hit_wr[i] = 0;
+    }
+    __shared__ uint32_t s_proto;
+    __shared__ unsigned long long s_best;
+    if (threadIdx.x == 0) { s_proto = 0xFFFFFFFFu; s_best = kNone; }
+    __syncthreads();
+    const uint64_t nwords = touch_words(a.tab_cells);
+    const uint64_t warps = gthreads / 32;
+    unsigned long long cand = kNone, cand_end = 0;
+    uint32_t cand_p = 0;
+    auto flush = [&]() {
+        if (cand != kNone && __ldcg(&a.best_pos[cand_p]) > cand) atomicMin(&a.best_pos[cand_p], cand);
+        cand = kNone;
+    };
+    // positions a lane sees only grow, so its first racy record per protocol is its smallest
+    auto note = [&](unsigned long long pos) {
+        if (cand != kNone && pos < cand_end) return;
+        flush();
+        cand_p = proto_of_record(a, pos);
+        const DevProto &P = a.protos[cand_p];
+        cand = pos;
+        cand_end = P.tab_off + (uint64_t)P.tab_phases * P.cells_sum;
+    };
+    // 32 touch words per warp step, one per lane, so that the bitmap is read
+    // with one round trip; then the warp works through the set words' blocks
+    const uint64_t nchunks = (nwords + 31) / 32;
+    for (uint64_t ch = (blockIdx.x * (uint64_t)kTabScanThreads + threadIdx.x) / 32; ch < nchunks; ch += warps) {
+        const uint64_t my = ch * 32 + lane;
+        uint32_t mine = my < nwords ? a.touch[my] : 0u;
+        if (mine) a.touch[my] = 0;
+        unsigned pend = __ballot_sync(kFull, mine != 0);
+        uint32_t bits = 0;
+        uint64_t wd = 0;
+        while (pend || bits) {
+            if (!bits) {                       // next set word of the chunk
+                const int src = __ffs(pend) - 1;
+                pend &= pend - 1;
+                bits = __shfl_sync(kFull, mine, src);
+                wd = ch * 32 + (uint32_t)src;
+            }
+            uint64_t blk[BLK];
+            int nb = 0;
+            for (; nb < BLK && bits; nb++) {
+                blk[nb] = wd * 32 + (uint32_t)(__ffs(bits) - 1);
+                bits &= bits - 1;
+            }
+            uint4 v[BLK][V4];
+#pragma unroll
+            for (int b = 0; b < BLK; b++) {
+                if (b < nb) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(a.table) + blk[b] * (kTabBlock / (R64 ? 2 : 4)) +
+                                       (uint64_t)lane * V4;
+#pragma unroll
+                    for (int q = 0; q < V4; q++) v[b][q] = src[q];
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < BLK; b++) {
+                if (b < nb) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(a.table) + blk[b] * (kTabBlock / (R64 ? 2 : 4)) +
+                                 (uint64_t)lane * V4;
+                    const unsigned long long pos0 = blk[b] * kTabBlock + (uint64_t)lane * PER;
+#pragma unroll
+                    for (int q = 0; q < V4; q++) {
+                        const uint4 x = v[b][q];
+                        if ((x.x | x.y | x.z | x.w) == 0) continue;
+                        if (R64) {
+                            const unsigned long long r0 = ((unsigned long long)x.y << 32) | x.x;
+                            const unsigned long long r1 = ((unsigned long long)x.w << 32) | x.z;
+                            if (owner_racy64(r0)) note(pos0 + q * 2);
+                            if (owner_racy64(r1)) note(pos0 + q * 2 + 1);
+                        } else {
+                            const uint32_t r[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                            for (int e = 0; e < 4; e++)
+                                if (owner_racy32(r[e])) note(pos0 + q * 4 + e);
+                        }
+                        dst[q] = make_uint4(0, 0, 0, 0);
+                    }
+                }
+            }
+        }
+    }
+    // final candidates: min over the warp, then over the block, when they
+    // belong to one protocol (the usual case); otherwise each lane's own
+    const unsigned has = __ballot_sync(kFull, cand != kNone);
+    if (has) {
+        const uint32_t p0 = __shfl_sync(kFull, cand_p, __ffs(has) - 1);
+        if (__all_sync(kFull, cand == kNone || cand_p == p0)) {
+            unsigned long long m = cand;
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(kFull, m, o);
+                m = y < m ? y : m;
+            }
+            cand = lane == 0 ? m : kNone;
+            cand_p = p0;
+            if (lane == 0) {
+                const uint32_t prev = atomicCAS(&s_proto, 0xFFFFFFFFu, p0);
+                if (prev == 0xFFFFFFFFu || prev == p0) { atomicMin(&s_best, m); cand = kNone; }
+            }
+        }
+    }
+    flush();
+    __syncthreads();
+    if (threadIdx.x == 0 && s_best != kNone) {
+        cand = s_best;
+        cand_p = s_proto;
+        flush();
+    }
+}
+
 __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t x)
 {
     if (x == f || x == s) return;
@@ -806,16 +1127,20 @@ __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t 
 }
 
 // One block per protocol: evaluation error, else barrier divergence, else the
-// witness of the first racy segment.  The witness segment is found by binary
-// search for its end, then reduced by the whole block: the two smallest
-// distinct tids of all its accesses and of its writes.
+// witness of the first racy cell.  Sorted keys (TABLE false): the witness
+// segment is found by binary search for its end, and the block reduces its
+// accesses.  Owner table (TABLE true): the cell is decoded from its table
+// position, and the block reduces the per-thread hit bits of the M_CELL
+// pass.  Either way the result is the two smallest distinct tids of all
+// accesses to the cell and of its writes.
+template <bool TABLE>
 __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(BatchArgs a)
 {
     __shared__ uint32_t s_red[4][kFinalizeThreads / 32];
     __shared__ unsigned long long s_end;
     const uint32_t p = blockIdx.x;
     const uint32_t t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int parity = sorted_parity(a);
+    const int parity = TABLE ? 0 : sorted_parity(a);
     if (p == 0 && t == 0 && a.ctrl->total != a.nkeys) atomicOr(&a.ctrl->flags, CF_COUNT_MISMATCH);
     const DevProto P = a.protos[p];
     const KeyLayout L = a.L;
@@ -826,25 +1151,48 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(BatchArgs a)
     const unsigned long long bp = a.best_pos[p];
     const uint32_t dt = a.div_tid[p];
     if (ek == kNone && P.nthreads && dt == 0xFFFFFFFFu && bp != kNone) {
-        const unsigned long long *keys = a.keys[parity];
-        const uint32_t tid_mask = L.tid_bits ? (1u << L.tid_bits) - 1 : 0;
-        const unsigned long long seg = keys[bp] >> L.sort_lo;
-        if (t == 0) {               // first position after the segment
-            unsigned long long lo = bp + 1, hi = a.nkeys;
-            while (lo < hi) {
-                unsigned long long mid = lo + (hi - lo) / 2;
-                if ((keys[mid] >> L.sort_lo) == seg) lo = mid + 1; else hi = mid;
-            }
-            s_end = lo;
-        }
-        __syncthreads();
-        const unsigned long long end = s_end;
         uint32_t t0 = 0xFFFFFFFFu, t1 = 0xFFFFFFFFu, w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
-        for (unsigned long long j = bp + t; j < end; j += kFinalizeThreads) {
-            unsigned long long x = keys[j];
-            uint32_t tid = (uint32_t)(x >> 1) & tid_mask;
-            two_smallest(t0, t1, tid);
-            if (x & 1) two_smallest(w0, w1, tid);
+        unsigned long long seg = 0;
+        if (TABLE) {
+            // this protocol's bits: [tid_off, tid_off + T) of the hit arrays
+            const uint64_t b0 = P.tid_off, b1 = P.tid_off + P.nthreads;
+            for (uint64_t wd = (b0 >> 5) + t; wd <= ((b1 - 1) >> 5); wd += kFinalizeThreads) {
+                uint32_t ma = a.hit_acc[wd], mw = a.hit_wr[wd];
+                const uint64_t lo = wd * 32;
+                if (lo < b0) { ma &= ~0u << (uint32_t)(b0 - lo); mw &= ~0u << (uint32_t)(b0 - lo); }
+                if (lo + 32 > b1) {
+                    const uint32_t keep = (1u << (uint32_t)(b1 - lo)) - 1;
+                    ma &= keep; mw &= keep;
+                }
+                for (int q = 0; q < 2 && ma; q++) {
+                    two_smallest(t0, t1, (uint32_t)(lo + (uint32_t)(__ffs(ma) - 1) - b0));
+                    ma &= ma - 1;
+                }
+                for (int q = 0; q < 2 && mw; q++) {
+                    two_smallest(w0, w1, (uint32_t)(lo + (uint32_t)(__ffs(mw) - 1) - b0));
+                    mw &= mw - 1;
+                }
+            }
+        } else {
+            const unsigned long long *keys = a.keys[parity];
+            const uint32_t tid_mask = L.tid_bits ? (1u << L.tid_bits) - 1 : 0;
+            seg = keys[bp] >> L.sort_lo;
+            if (t == 0) {               // first position after the segment
+                unsigned long long lo = bp + 1, hi = a.nkeys;
+                while (lo < hi) {
+                    unsigned long long mid = lo + (hi - lo) / 2;
+                    if ((keys[mid] >> L.sort_lo) == seg) lo = mid + 1; else hi = mid;
+                }
+                s_end = lo;
+            }
+            __syncthreads();
+            const unsigned long long end = s_end;
+            for (unsigned long long j = bp + t; j < end; j += kFinalizeThreads) {
+                unsigned long long x = keys[j];
+                uint32_t tid = (uint32_t)(x >> 1) & tid_mask;
+                two_smallest(t0, t1, tid);
+                if (x & 1) two_smallest(w0, w1, tid);
+            }
         }
         for (int o = 16; o; o >>= 1) {
             uint32_t u0 = __shfl_xor_sync(kFull, t0, o), u1 = __shfl_xor_sync(kFull, t1, o);
@@ -862,9 +1210,17 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(BatchArgs a)
             r.verdict = 1;
             r.phases = a.totsyn[P.tid_off] + 1;
             r.sync_count_0 = a.totsyn[P.tid_off];
-            r.index = seg & (L.idx_bits ? (~0ull >> (64 - L.idx_bits)) : 0);
-            r.loc = (uint32_t)((seg >> L.idx_bits) & (L.loc_bits ? (~0ull >> (64 - L.loc_bits)) : 0));
-            r.phase = (uint32_t)((seg >> (L.idx_bits + L.loc_bits)) & (L.phase_bits ? (~0ull >> (64 - L.phase_bits)) : 0));
+            if (TABLE) {
+                const CellTarget c = decode_cell(a, P, bp);
+                r.phase = c.phase;
+                r.loc = c.loc;
+                r.index = c.idx;
+            } else {
+                r.index = seg & (L.idx_bits ? (~0ull >> (64 - L.idx_bits)) : 0);
+                r.loc = (uint32_t)((seg >> L.idx_bits) & (L.loc_bits ? (~0ull >> (64 - L.loc_bits)) : 0));
+                r.phase = (uint32_t)((seg >> (L.idx_bits + L.loc_bits)) &
+                                     (L.phase_bits ? (~0ull >> (64 - L.phase_bits)) : 0));
+            }
             r.tid_i = t0;
             if (w0 == t0) { r.tid_j = t1; r.i_writes = 1; r.j_writes = (w1 == t1); }
             else { r.tid_j = w0; r.i_writes = 0; r.j_writes = 1; }
@@ -928,8 +1284,8 @@ cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_
     mark(ev, nev, s);
     k_init<<<(unsigned)((init_n + 255) / 256), 256, 0, s>>>(a);
     mark(ev, nev, s);
-    if (a.has_narrow) k_interp<false, false><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
-    if (a.has_wide) k_interp<false, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+    if (a.has_narrow) k_interp<M_COUNT, false><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+    if (a.has_wide) k_interp<M_COUNT, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
     mark(ev, nev, s);
     uint32_t col_blocks = (uint32_t)((a.ncols + 31) / 32);
     k_scan<<<col_blocks + a.nwblocks, kScanThreads, 0, s>>>(a, col_blocks);
@@ -937,10 +1293,37 @@ cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_
     return cudaGetLastError();
 }
 
+template <int MODE>
+static void launch_interp(const BatchArgs &a, cudaStream_t s, int sms)
+{
+    if (a.has_narrow) k_interp<MODE, false><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+    if (a.has_wide) k_interp<MODE, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+}
+
+static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev)
+{
+    if (a.rec64) launch_interp<M_TAB64>(a, s, sms);
+    else launch_interp<M_TAB32>(a, s, sms);
+    mark(ev, nev, s);
+    const uint64_t warps_needed = (touch_words(a.tab_cells) + 31) / 32;
+    uint64_t grid = (warps_needed + kTabScanThreads / 32 - 1) / (kTabScanThreads / 32);
+    const uint64_t cap = (uint64_t)sms * 8;
+    if (grid > cap) grid = cap;
+    if (grid == 0) grid = 1;
+    if (a.rec64) k_tscan<true><<<(unsigned)grid, kTabScanThreads, 0, s>>>(a);
+    else k_tscan<false><<<(unsigned)grid, kTabScanThreads, 0, s>>>(a);
+    mark(ev, nev, s);
+    launch_interp<M_CELL>(a, s, sms);
+    mark(ev, nev, s);
+    k_finalize<true><<<a.nprotos, kFinalizeThreads, 0, s>>>(a);
+    mark(ev, nev, s);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev)
 {
-    if (a.has_narrow) k_interp<true, false><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
-    if (a.has_wide) k_interp<true, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+    if (a.path == PATH_TABLE) return launch_back_table(a, s, sms, ev, nev);
+    launch_interp<M_EMIT>(a, s, sms);
     mark(ev, nev, s);
     for (uint32_t q = 0; q < a.L.passes; q++) {
         if (a.ntiles) {
@@ -956,20 +1339,26 @@ cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t
         k_resolve<<<1, 1024, 0, s>>>(a);
     }
     mark(ev, nev, s);
-    k_finalize<<<a.nprotos, kFinalizeThreads, 0, s>>>(a);
+    k_finalize<false><<<a.nprotos, kFinalizeThreads, 0, s>>>(a);
     mark(ev, nev, s);
     return cudaGetLastError();
 }
 
-int stage_names(const char **names, int cap, uint32_t passes)
+int stage_names(const char **names, int cap, uint32_t passes, uint32_t path)
 {
     static const char *radix[kMaxPasses] = {"radix0", "radix1", "radix2", "radix3",
                                             "radix4", "radix5", "radix6", "radix7"};
-    const char *all[4 + kMaxPasses + 2];
+    const char *all[kMaxStages];
     int n = 0;
-    all[n++] = "init"; all[n++] = "count"; all[n++] = "scan"; all[n++] = "emit";
-    for (uint32_t q = 0; q < passes && q < (uint32_t)kMaxPasses; q++) all[n++] = radix[q];
-    all[n++] = "detect"; all[n++] = "finalize";
+    all[n++] = "init"; all[n++] = "count"; all[n++] = "scan";
+    if (path == PATH_TABLE) {
+        all[n++] = "table"; all[n++] = "tscan"; all[n++] = "witness";
+    } else {
+        all[n++] = "emit";
+        for (uint32_t q = 0; q < passes && q < (uint32_t)kMaxPasses; q++) all[n++] = radix[q];
+        all[n++] = "detect";
+    }
+    all[n++] = "finalize";
     for (int i = 0; i < n && i < cap; i++) names[i] = all[i];
     return n;
 }

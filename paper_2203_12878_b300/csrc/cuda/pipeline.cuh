@@ -72,7 +72,19 @@ struct BatchArgs {
     Control *ctrl;
     uint32_t *epoch;                 // persists across launches
     KeyLayout L;
+    // owner table (the sort-free path): one record per (protocol, phase,
+    // array, index) cell, all zero between launches
+    uint32_t path;                   // PATH_SORT or PATH_TABLE
+    uint32_t rec64;                  // 64-bit records (thread ids above 15 bits)
+    void *table;                     // [tab_cells] records, padded to whole blocks
+    uint64_t tab_cells;
+    uint32_t *touch;                 // one bit per block of kTabBlock records written this launch
+    const uint64_t *cbase;           // per (protocol, array): first record of the array in a phase row
+    uint32_t *hit_acc, *hit_wr;      // per (protocol, thread) bit: accessed / wrote the witness cell
+    uint64_t nhit;                   // words of each hit array
 };
+
+enum : uint32_t { PATH_SORT = 0, PATH_TABLE = 1 };
 
 constexpr int kRadixThreads = 256;
 constexpr int kRadixItems = 16;
@@ -83,6 +95,9 @@ constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 4096 keys
 constexpr int kFinalizeThreads = 128;
 constexpr int kScanThreads = 256;
 constexpr int kWScanPerBlock = 4096;                        // warp-items per scan block
+constexpr int kTabBlockLog = 8;
+constexpr int kTabBlock = 1 << kTabBlockLog;                // owner-table records per touch bit
+constexpr int kTabScanThreads = 256;
 
 // Keys per thread of a radix tile: a tuning choice among these (0 = 16).
 inline uint32_t radix_items_or_default(uint32_t items) { return items == 12 || items == 24 ? items : 16; }
@@ -92,14 +107,24 @@ inline uint32_t radix_tiles(uint64_t n, uint32_t items = kRadixItems)
     return (uint32_t)((n + tile - 1) / tile);
 }
 inline uint32_t detect_tiles(uint64_t n) { return (uint32_t)((n + kDetectTile - 1) / kDetectTile); }
+// Owner-table blocks and touch-bitmap words for `cells` records.
+#ifdef __CUDACC__
+#define DRF_HOST_DEVICE __host__ __device__
+#else
+#define DRF_HOST_DEVICE
+#endif
+DRF_HOST_DEVICE inline uint64_t table_blocks(uint64_t cells) { return (cells + kTabBlock - 1) / kTabBlock; }
+DRF_HOST_DEVICE inline uint64_t touch_words(uint64_t cells) { return (table_blocks(cells) + 31) / 32; }
 
 // Stage launchers (all asynchronous on `s`).  Each returns cudaGetLastError().
 // When ev is non-null, an event is recorded before the first kernel of
 // launch_front and after every kernel; *nev counts the events recorded.
 cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev);  // init, count, scan
-cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev);   // emit, radix, detect, finalize
+// PATH_SORT: emit, radix, detect, finalize.  PATH_TABLE: table, tscan, witness, finalize.
+cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev);
 
 // Names of the stages whose boundaries launch_front / launch_back record.
-int stage_names(const char **names, int cap, uint32_t passes);
+int stage_names(const char **names, int cap, uint32_t passes, uint32_t path);
+constexpr int kMaxStages = 4 + kMaxPasses + 2;
 
 }  // namespace drf

@@ -108,6 +108,11 @@ struct DevProto {
     uint32_t cells_off;    // into the batch array-size array
     uint64_t lane_off;     // per-(item, thread) arrays: lane_off + k * T + t
     uint64_t tid_off;      // per-thread arrays: tid_off + t
+    // owner table: phase-major rows of cells_sum records, array after array
+    uint64_t tab_off;      // first record of this protocol
+    uint64_t cells_sum;    // records per phase row (sum of the array sizes)
+    uint32_t tab_phases;   // rows: the static bound on syncs per thread, plus one
+    uint32_t pad;
 };
 
 struct WarpItem {
@@ -142,6 +147,7 @@ enum : unsigned {
     CF_LOOKBACK_TIMEOUT = 1,   // a radix pass gave up waiting on a predecessor tile
     CF_EMIT_OVERFLOW = 2,      // emission disagreed with the count pass
     CF_COUNT_MISMATCH = 4,     // the launch's tuple total differs from the plan's
+    CF_TABLE_RANGE = 8,        // an access fell outside its protocol's owner-table rows
 };
 
 // Device-side result of one protocol (converted to drf_result on the host).

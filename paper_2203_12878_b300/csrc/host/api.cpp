@@ -271,6 +271,8 @@ int drf_debug_sorted_keys(drf_ctx *ctx, uint64_t *keys, uint64_t cap, uint64_t *
     cudaError_t ce = cudaSetDevice(ctx->device);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce);
     const BatchArgs &a = ctx->work.args;
+    if (a.path == PATH_TABLE)
+        return fail(ctx, DRF_E_NOT_FOUND, "the last check ran the owner-table path, which sorts no keys");
     *n = a.nkeys;
     if (layout) {
         layout[0] = a.L.tid_bits; layout[1] = a.L.idx_bits; layout[2] = a.L.loc_bits;
@@ -348,6 +350,7 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
     DeviceBatch &d = plan->dev;
     d.limit = ctx->opts.max_device_bytes;
     d.radix_items = cfg.radix_items;
+    d.path_pref = cfg.path ? (int)cfg.path : path_pref_of(ctx->opts);
     e = d.load(plan->host, s);
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
     cudaError_t ce;
@@ -358,8 +361,9 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
         return cuda_fail(ctx, ce);
     }
     plan->tuples = ctx->pinned_ctrl->total;
-    e = d.size_keys(plan->tuples, s);
+    e = d.choose_path(plan->host, plan->tuples, s);
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
+    plan->cfg.path = d.args.path == PATH_TABLE ? 2 : 1;
     d.status_launches++;
     std::vector<DevResult> res(n);
     if ((ce = launch_back(d.args, s, ctx->sms, nullptr, nullptr)) != cudaSuccess ||
@@ -410,7 +414,7 @@ int capture_plan(drf_plan *plan)
     DeviceBatch &d = plan->dev;
     plan->profiled = (ctx->opts.flags & DRF_OPT_PROFILE_STAGES) != 0;
     if (plan->profiled) {
-        plan->events.resize(4 + kMaxPasses + 3);
+        plan->events.resize(kMaxStages + 1);
         for (auto &ev : plan->events) cudaEventCreate(&ev);
     }
     cudaEvent_t *evp = plan->profiled ? plan->events.data() : nullptr;
@@ -433,7 +437,8 @@ std::string signature(drf_ctx *ctx, uint32_t n, const drf_plan *p)
     for (const DevProto &d : p->host.protos) maxt = std::max(maxt, d.nthreads);
     return "sms" + std::to_string(ctx->sms) + "_n" + std::to_string(bits_for(n)) + "_t" +
            std::to_string(bits_for(p->tuples)) + "_s" + std::to_string(p->host.L.sort_bits) + "_T" +
-           std::to_string(bits_for(maxt));
+           std::to_string(bits_for(maxt)) + "_b" + std::to_string(bits_for(p->host.table_bytes())) + "_p" +
+           std::to_string(path_pref_of(ctx->opts));
 }
 
 }  // namespace
@@ -459,19 +464,29 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
         if (!tune_lookup(key, best_cfg)) {
             double best = time_plan(plan, 3);
             best_cfg = plan->cfg;
-            for (uint32_t g : kTuneGranularity)
-                for (uint32_t it : kTuneRadixItems) {
-                    PlanConfig c{g, it};
-                    if (c.granularity == plan->cfg.granularity && c.radix_items == plan->cfg.radix_items) continue;
-                    drf_plan *cand = nullptr;
-                    if (build_plan(ctx, n, bytecodes, lens, bounds, c, &cand)) continue;
-                    double ms = time_plan(cand, 3);
-                    drf_plan_destroy(cand);
-                    if (ms < best) { best = ms; best_cfg = c; }
-                }
+            // candidates: the sort path under every granularity and tile
+            // shape, the owner table (no radix tiles) under every granularity
+            const int pref = path_pref_of(ctx->opts);
+            std::vector<PlanConfig> cands;
+            for (uint32_t g : kTuneGranularity) {
+                if (pref != 2)
+                    for (uint32_t it : kTuneRadixItems) cands.push_back(PlanConfig{g, it, 1});
+                if (pref != 1 && plan->host.table_ok) cands.push_back(PlanConfig{g, 16, 2});
+            }
+            for (const PlanConfig &c : cands) {
+                if (c.granularity == plan->cfg.granularity && c.path == plan->cfg.path &&
+                    (c.path == 2 || c.radix_items == plan->cfg.radix_items))
+                    continue;
+                drf_plan *cand = nullptr;
+                if (build_plan(ctx, n, bytecodes, lens, bounds, c, &cand)) continue;
+                double ms = time_plan(cand, 3);
+                drf_plan_destroy(cand);
+                if (ms < best) { best = ms; best_cfg = c; }
+            }
             tune_store(key, best_cfg, best);
         }
-        if (best_cfg.granularity != plan->cfg.granularity || best_cfg.radix_items != plan->cfg.radix_items) {
+        if (best_cfg.granularity != plan->cfg.granularity || best_cfg.radix_items != plan->cfg.radix_items ||
+            best_cfg.path != plan->cfg.path) {
             drf_plan_destroy(plan);
             plan = nullptr;
             if ((st = build_plan(ctx, n, bytecodes, lens, bounds, best_cfg, &plan))) return st;
@@ -490,6 +505,13 @@ int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix
     return DRF_OK;
 }
 
+int drf_plan_path(const drf_plan *plan, uint32_t *path)
+{
+    if (!plan || !path) return DRF_E_INVALID_ARG;
+    *path = plan->dev.args.path == PATH_TABLE ? DRF_PATH_TABLE : DRF_PATH_SORT;
+    return DRF_OK;
+}
+
 int drf_plan_launch(drf_plan *plan, void *stream)
 {
     if (!plan || !plan->exec) return DRF_E_INVALID_ARG;
@@ -497,7 +519,7 @@ int drf_plan_launch(drf_plan *plan, void *stream)
     cudaSetDevice(ctx->device);
     cudaStream_t s = pick(ctx, stream);
     DeviceBatch &d = plan->dev;
-    if (++d.status_launches >= (1ull << 21)) {
+    if (++d.status_launches >= (1ull << 21) && d.status.p) {
         if (cudaMemsetAsync(d.status.p, 0, d.status.cap, s) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError());
         d.status_launches = 0;
     }
@@ -530,11 +552,13 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
                   uint32_t *sort_bits)
 {
     if (!plan) return DRF_E_INVALID_ARG;
+    const bool table = plan->dev.args.path == PATH_TABLE;
     if (tuples) *tuples = plan->tuples;
-    if (sort_passes) *sort_passes = plan->host.L.passes;
+    if (sort_passes) *sort_passes = table ? 0 : plan->host.L.passes;
     if (kernels_per_launch) {
         uint32_t widths = plan->dev.args.has_narrow + plan->dev.args.has_wide;
-        *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes;   // init, 2x interp, scan, passes, detect, resolve, finalize
+        if (table) *kernels_per_launch = 3 * widths + 4;   // init, 3x interp, scan, tscan, finalize
+        else *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes;   // init, 2x interp, scan, passes, detect, resolve, finalize
     }
     if (sort_bits) *sort_bits = plan->host.L.sort_bits;
     return DRF_OK;
@@ -549,8 +573,8 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
     cudaStream_t s = plan->last_stream ? plan->last_stream : plan->ctx->stream;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(plan->ctx, e);
-    const char *all[4 + kMaxPasses + 2];
-    int nn = stage_names(all, 4 + kMaxPasses + 2, plan->host.L.passes);
+    const char *all[kMaxStages];
+    int nn = stage_names(all, kMaxStages, plan->host.L.passes, plan->dev.args.path);
     int n = std::min(nn, plan->nevents - 1);
     for (int i = 0; i < n && i < cap; i++) {
         float t = 0;

@@ -56,6 +56,7 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
 
     struct W { WarpItem wi; uint64_t steps; };
     std::vector<W> ws;
+    bool table_fits = true;
     for (uint32_t i = 0; i < n; i++) {
         const Prepared &p = *ps[i];
         DevProto d{};
@@ -69,6 +70,18 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
         d.cells_off = (uint32_t)out.cells.size();
         d.lane_off = out.lanes;
         d.tid_off = out.ncols;
+        // owner-table rows: one per phase the static sync bound allows
+        uint64_t row = 0;
+        for (uint64_t c : p.cells) {
+            out.cbase.push_back(row);
+            row = row + c < row ? ~0ull : row + c;
+        }
+        d.tab_off = out.table_cells;
+        d.cells_sum = row;
+        d.tab_phases = p.max_syncs < 0xFFFFFFFFull ? (uint32_t)(p.max_syncs + 1) : 0;
+        if (!d.tab_phases || (row && (unsigned __int128)row * d.tab_phases > kMaxTableBytes)) table_fits = false;
+        else out.table_cells += row * d.tab_phases;
+        if (out.table_cells > kMaxTableBytes) table_fits = false;
         out.insns.insert(out.insns.end(), p.insns.begin(), p.insns.end());
         out.xcode.insert(out.xcode.end(), p.xcode.begin(), p.xcode.end());
         out.items.insert(out.items.end(), p.items.begin(), p.items.end());
@@ -84,6 +97,9 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
     if (out.insns.size() >= (1ull << 31) || out.xcode.size() >= (1ull << 31) || out.items.size() >= (1ull << 31) ||
         ws.size() >= (1ull << 31) || out.lanes >= (1ull << 31))
         return Error::make(S_LIMIT, "batch too large");
+    out.rec64 = L.tid_bits > 15;
+    out.table_ok = table_fits && L.tid_bits <= 31 && out.table_bytes() <= kMaxTableBytes;
+    if (!out.table_ok) out.table_cells = 0;
     // longest items first, so that the grid-stride loops end together
     std::stable_sort(ws.begin(), ws.end(), [](const W &x, const W &y) { return x.steps > y.steps; });
     out.witems.reserve(ws.size());
@@ -95,7 +111,7 @@ DeviceBatch::~DeviceBatch()
 {
     DevBuf *all[] = {&insns, &xcode, &items, &protos, &cells, &witems, &cnt, &syn, &phs, &erro, &totsyn,
                      &wcnt, &wbase, &blocksum, &keys0, &keys1, &hist, &status, &trec, &err_key, &div_tid,
-                     &best_pos, &ptuples, &results, &ctrl, &epoch};
+                     &best_pos, &ptuples, &results, &ctrl, &epoch, &cbase, &table, &touch, &hit};
     for (DevBuf *b : all) release(*b, &in_use);
 }
 
@@ -124,7 +140,8 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     uint64_t *hb = &h2d_bytes;
     bool ok = upload(insns, b.insns, &in_use, limit, s, hb) && upload(xcode, b.xcode, &in_use, limit, s, hb) &&
               upload(items, b.items, &in_use, limit, s, hb) && upload(protos, b.protos, &in_use, limit, s, hb) &&
-              upload(cells, b.cells, &in_use, limit, s, hb) && upload(witems, b.witems, &in_use, limit, s, hb);
+              upload(cells, b.cells, &in_use, limit, s, hb) && upload(cbase, b.cbase, &in_use, limit, s, hb) &&
+              upload(witems, b.witems, &in_use, limit, s, hb);
     const size_t lanes = std::max<uint64_t>(b.lanes, 1);
     ok = ok && ensure(cnt, lanes * 4, &in_use, limit) && ensure(syn, lanes * 4, &in_use, limit) &&
          ensure(phs, lanes * 4, &in_use, limit) && ensure(erro, lanes * 8, &in_use, limit) &&
@@ -179,7 +196,75 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.keys[0] = (unsigned long long *)keys0.p;
     a.keys[1] = (unsigned long long *)keys1.p;
     a.status = (unsigned long long *)status.p;
+    a.cbase = (const uint64_t *)cbase.p;
+    a.path = PATH_SORT;
+    a.rec64 = b.rec64 ? 1 : 0;
+    a.table = nullptr;
+    a.tab_cells = 0;
+    a.touch = nullptr;
+    a.hit_acc = a.hit_wr = nullptr;
+    a.nhit = 0;
     return Error{};
+}
+
+Error DeviceBatch::size_table(const BatchHost &b, uint64_t n, cudaStream_t s)
+{
+    const uint64_t recs = table_blocks(b.table_cells) * kTabBlock;
+    const size_t tb = std::max<uint64_t>(recs * (b.rec64 ? 8 : 4), 16);
+    const size_t wb = std::max<uint64_t>(touch_words(b.table_cells) * 4, 16);
+    const uint64_t nhit = (b.ncols + 31) / 32 + 1;
+    void *old_table = table.p, *old_touch = touch.p;
+    if (!ensure(table, tb, &in_use, limit) || !ensure(touch, wb, &in_use, limit) ||
+        !ensure(hit, nhit * 8, &in_use, limit)) {
+        cudaGetLastError();
+        return Error::make(S_NOMEM, "device allocation of a " + std::to_string(tb) + "-byte owner table failed");
+    }
+    // the kernels keep the table and its touch bits all zero between
+    // launches; fresh memory (or a failed launch) needs one clear
+    if (table.p != old_table || touch.p != old_touch || table_dirty) {
+        if (cudaMemsetAsync(table.p, 0, table.cap, s) != cudaSuccess ||
+            cudaMemsetAsync(touch.p, 0, touch.cap, s) != cudaSuccess)
+            return Error::make(S_CUDA, "memset failed");
+        table_dirty = false;
+    }
+    BatchArgs &a = args;
+    a.path = PATH_TABLE;
+    a.rec64 = b.rec64 ? 1 : 0;
+    a.table = table.p;
+    a.tab_cells = b.table_cells;
+    a.touch = (uint32_t *)touch.p;
+    a.hit_acc = (uint32_t *)hit.p;
+    a.hit_wr = (uint32_t *)hit.p + nhit;
+    a.nhit = nhit;
+    a.nkeys = n;
+    a.ntiles = 0;
+    a.ndtiles = 0;
+    return Error{};
+}
+
+uint32_t auto_path(const BatchHost &b, uint64_t n)
+{
+    // The table path reads only the blocks the accesses touched, so its cost
+    // follows the tuples; the table's size costs memory and one clear.  Take
+    // it unless the table is far larger than the accesses that fill it.
+    if (!b.table_ok) return PATH_SORT;
+    const uint64_t bytes = b.table_bytes();
+    return bytes <= std::max<uint64_t>(256ull << 20, n * 256) ? PATH_TABLE : PATH_SORT;
+}
+
+Error DeviceBatch::choose_path(const BatchHost &b, uint64_t n, cudaStream_t s)
+{
+    uint32_t path = path_pref == 1 ? PATH_SORT : path_pref == 2 ? PATH_TABLE : auto_path(b, n);
+    if (path == PATH_TABLE) {
+        Error e = b.table_ok ? size_table(b, n, s)
+                             : Error::make(S_LIMIT, "the owner table of this batch would exceed " +
+                                                        std::to_string(kMaxTableBytes >> 30) +
+                                                        " GiB or thread ids exceed 31 bits");
+        if (e.ok()) return e;
+        if (path_pref == 2) return e;
+    }
+    args.path = PATH_SORT;
+    return size_keys(n, s);
 }
 
 Error DeviceBatch::size_keys(uint64_t n, cudaStream_t s)
@@ -231,7 +316,7 @@ int run_batch(DeviceBatch &w, Control *pinned, int sms, cudaStream_t s, const Ba
         return S_CUDA;
     }
     const uint64_t n = pinned->total;
-    e = w.size_keys(n, s);
+    e = w.choose_path(b, n, s);
     if (!e.ok()) { err = e.message; return e.status; }
     w.status_launches++;
     out.resize(b.protos.size());
@@ -240,6 +325,7 @@ int run_batch(DeviceBatch &w, Control *pinned, int sms, cudaStream_t s, const Ba
         cudaMemcpyAsync(pinned, w.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         err = cudaGetErrorString(cudaGetLastError());
+        w.table_dirty = true;
         return S_CUDA;
     }
     w.d2h_bytes = 2 * sizeof(Control) + out.size() * sizeof(DevResult);
@@ -248,9 +334,17 @@ int run_batch(DeviceBatch &w, Control *pinned, int sms, cudaStream_t s, const Ba
     return st;
 }
 
+int path_pref_of(const drf_opts &o)
+{
+    if (o.flags & DRF_OPT_PATH_SORT) return 1;
+    if (o.flags & DRF_OPT_PATH_TABLE) return 2;
+    return 0;
+}
+
 int run_batch(drf_ctx *ctx, const BatchHost &b, cudaStream_t s, std::vector<DevResult> &out)
 {
     ctx->work.limit = ctx->opts.max_device_bytes;
+    ctx->work.path_pref = path_pref_of(ctx->opts);
     return run_batch(ctx->work, ctx->pinned_ctrl, ctx->sms, s, b, out, ctx->last_error);
 }
 

@@ -31,12 +31,20 @@ struct BatchHost {
     std::vector<ItemDesc> items;
     std::vector<DevProto> protos;
     std::vector<uint64_t> cells;
+    std::vector<uint64_t> cbase;     // per (protocol, array): offset of the array within a table row
     std::vector<WarpItem> witems;
     uint64_t ncols = 0;
     uint64_t lanes = 0;
     uint64_t tuple_bound = 0;
     KeyLayout L{};
+    uint64_t table_cells = 0;        // owner-table records of the whole batch
+    bool table_ok = false;           // the owner-table path can run this batch
+    bool rec64 = false;              // owner records need 64 bits (thread ids above 15 bits)
+    uint64_t table_bytes() const { return table_cells * (rec64 ? 8 : 4); }
 };
+
+// Largest owner table (bytes) the library sets up for one batch.
+constexpr uint64_t kMaxTableBytes = 64ull << 30;
 
 // Packs prepared protocols (all valid) into a batch; fails with
 // S_KEY_TOO_WIDE when the combined key layout exceeds 64 bits.
@@ -48,20 +56,33 @@ struct DeviceBatch {
     DevBuf cnt, syn, phs, erro, totsyn, wcnt, wbase, blocksum;
     DevBuf keys0, keys1, hist, status, trec;
     DevBuf err_key, div_tid, best_pos, ptuples, results, ctrl, epoch;
+    DevBuf cbase, table, touch, hit;
     size_t in_use = 0;
     uint64_t limit = 0;
     uint64_t status_launches = 0;     // launches since the look-back words were cleared
     uint64_t h2d_bytes = 0, d2h_bytes = 0;   // copies of the last run
     uint32_t radix_items = 16;                // radix tile shape (tuning choice)
+    int path_pref = 0;                        // 0: choose per batch, 1: sort path, 2: owner-table path
+    bool table_dirty = false;                 // a failed launch may have left records behind
     BatchArgs args{};
 
     ~DeviceBatch();
     // Uploads the batch and sizes every buffer that does not depend on the
     // tuple count.
     Error load(const BatchHost &b, cudaStream_t s);
-    // Sizes the key and look-back buffers for n tuples.
+    // Sizes the key and look-back buffers for n tuples (sort path).
     Error size_keys(uint64_t n, cudaStream_t s);
+    // Sizes the owner table, its touch bits and the witness hit bits
+    // (owner-table path); a new or grown table is cleared once.
+    Error size_table(const BatchHost &b, uint64_t n, cudaStream_t s);
+    // Picks the back end for a batch of n tuples (after the count pass) and
+    // sizes its buffers.  Falls back to the sort path when the table
+    // cannot be allocated, unless the table path was asked for.
+    Error choose_path(const BatchHost &b, uint64_t n, cudaStream_t s);
 };
+
+// The back end the automatic choice takes for a batch of n tuples.
+uint32_t auto_path(const BatchHost &b, uint64_t n);
 
 struct Timing;
 
@@ -104,6 +125,9 @@ namespace drf {
 int run_batch(DeviceBatch &w, Control *pinned, int sms, cudaStream_t s, const BatchHost &b,
               std::vector<DevResult> &out, std::string &err);
 int run_batch(drf_ctx *ctx, const BatchHost &b, cudaStream_t s, std::vector<DevResult> &out);
+
+// Back-end preference of a context's options: 0 automatic, 1 sort, 2 owner table.
+int path_pref_of(const drf_opts &o);
 
 void to_public(const DevResult &d, drf_result *out);
 

@@ -48,6 +48,7 @@ public:
                 return S_CUDA;
             }
             l->dev.limit = ctx_->opts.max_device_bytes;
+            l->dev.path_pref = path_pref_of(ctx_->opts);
             lanes_.push_back(std::move(l));
         }
         for (int i = 0; i < kWorkers; i++) workers_.emplace_back([this, i] { work(i); });

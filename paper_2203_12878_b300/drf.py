@@ -25,6 +25,9 @@ STATUS = {
 VERDICTS = {-1: None, 0: "DRF", 1: "RACY", 2: "BARRIER_DIVERGENCE"}
 OPT_PROFILE_STAGES = 0x1
 OPT_AUTOTUNE = 0x2
+OPT_PATH_SORT = 0x4      # force the sort back end
+OPT_PATH_TABLE = 0x8     # force the owner-table back end
+PATHS = {1: "sort", 2: "table"}
 
 
 class DrfError(RuntimeError):
@@ -109,6 +112,7 @@ _SIGS = {
     "drf_plan_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "drf_plan_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
+    "drf_plan_path": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
     "drf_plan_destroy": (None, [_P]),
     "drf_server_start": (ctypes.c_int, [_P, ctypes.POINTER(drf_server_opts)]),
     "drf_server_submit": (ctypes.c_int, [_P, _U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds),
@@ -391,6 +395,15 @@ def drf_plan_config(plan) -> dict:
     if st != 0:
         raise DrfError(st)
     return {"granularity": g.value, "radix_items": it.value}
+
+
+def drf_plan_path(plan) -> str:
+    """'sort' or 'table': the back end the plan runs."""
+    v = ctypes.c_uint32()
+    st = lib().drf_plan_path(plan, ctypes.byref(v))
+    if st != 0:
+        raise DrfError(st)
+    return PATHS[v.value]
 
 
 def drf_plan_destroy(plan) -> None:

@@ -16,20 +16,49 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CELLS = 1
 
 
+PATH_FLAGS = {"sort": drf.OPT_PATH_SORT, "table": drf.OPT_PATH_TABLE}
+TABLE_LIMIT = 64 << 30           # bytes: the largest owner table the library sets up
+
+
+@pytest.fixture(scope="module", params=["sort", "table"])
+def ctx(request):
+    """A context forced onto one back end; every test using it runs on both."""
+    c = drf.drf_ctx_create(0, flags=PATH_FLAGS[request.param])
+    c.path = request.param
+    yield c
+    drf.drf_ctx_destroy(c)
+
+
 @pytest.fixture(scope="module")
-def ctx():
-    c = drf.drf_ctx_create(0)
+def sort_ctx():
+    c = drf.drf_ctx_create(0, flags=drf.OPT_PATH_SORT)
     yield c
     drf.drf_ctx_destroy(c)
 
 
 def run(ctx, p):
     bc = drf.drf_protocol_compile(p.text)
-    return drf.result_dict(drf.drf_check(ctx, bc, p.nthreads, p.cells, p.params))
+    try:
+        return drf.result_dict(drf.drf_check(ctx, bc, p.nthreads, p.cells, p.params))
+    except drf.DrfError as e:
+        return {"status": e.name}
 
 
-def want(oracle, p):
-    return oracle.check(p.text, p.nthreads, p.cells, p.params, CELLS)
+def table_fits(p):
+    """Whether the owner table of p is within the library's limit: one
+    record (4 bytes, 8 above 15-bit thread ids) per cell and phase row."""
+    st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
+    if st != "OK":
+        return True
+    rec = 8 if max(p.nthreads - 1, 0).bit_length() > 15 else 4
+    return (a["sync_bound"] + 1) * sum(p.cells) * rec <= TABLE_LIMIT
+
+
+def want(oracle, p, ctx=None):
+    exp = oracle.check(p.text, p.nthreads, p.cells, p.params, CELLS)
+    if ctx is not None and getattr(ctx, "path", "") == "table" and exp["status"] == "OK" and not table_fits(p):
+        return {"status": "LIMIT"}
+    return exp
 
 
 def same(got, exp):
@@ -58,7 +87,7 @@ def test_random_small_sweep(ctx, oracle, chunk):
     mism = []
     for seed in range(chunk * 600, (chunk + 1) * 600):
         p = protogen.random_small(seed)
-        exp = want(oracle, p)
+        exp = want(oracle, p, ctx)
         if exp["status"] == "OVERFLOW":
             continue
         got = run(ctx, p)
@@ -92,14 +121,14 @@ def _rows_sorted(rows):
     lambda: protogen.config2(2, target=3e5), lambda: protogen.config2(4, "constructed", target=3e5),
     lambda: protogen.config4_one(random.Random(11), True),
 ])
-def test_emitted_keys_are_the_access_multiset_and_sorted(ctx, oracle, maker):
+def test_emitted_keys_are_the_access_multiset_and_sorted(sort_ctx, oracle, maker):
     """Stage check: the keys the emit kernel wrote are exactly the oracle's
     dynamic accesses (as a multiset), and after the radix passes they are
     ordered by (phase, array, index)."""
     p = maker()
-    got = run(ctx, p)
+    got = run(sort_ctx, p)
     assert got["status"] == "OK"
-    keys, lay = drf.drf_debug_sorted_keys(ctx)
+    keys, lay = drf.drf_debug_sorted_keys(sort_ctx)
     rows = _decode(keys, lay)
     seg = keys >> np.uint64(lay["tid_bits"] + 1)
     assert np.all(seg[1:] >= seg[:-1])
@@ -108,14 +137,14 @@ def test_emitted_keys_are_the_access_multiset_and_sorted(ctx, oracle, maker):
     assert np.array_equal(_rows_sorted(rows), _rows_sorted(ref.astype(np.uint64)))
 
 
-def test_random_small_keys(ctx, oracle):
+def test_random_small_keys(sort_ctx, oracle):
     for seed in range(200):
         p = protogen.random_small(seed)
         exp = want(oracle, p)
         if exp["status"] != "OK" or exp["verdict"] == "BARRIER_DIVERGENCE":
             continue
-        run(ctx, p)
-        keys, lay = drf.drf_debug_sorted_keys(ctx)
+        run(sort_ctx, p)
+        keys, lay = drf.drf_debug_sorted_keys(sort_ctx)
         ref = oracle.tuples(p.text, p.nthreads, p.cells, p.params)
         rows = _decode(keys, lay) if len(keys) else np.zeros((0, 5), np.uint64)
         assert np.array_equal(_rows_sorted(rows), _rows_sorted(ref.astype(np.uint64))), p.text
@@ -128,7 +157,7 @@ def test_config2_shapes_small(ctx, oracle, seed, mode):
     cells, depth-3 nests, 1..6 syncs) at ~2x10^5 accesses: several sort tiles
     and ragged tails."""
     p = protogen.config2(seed, mode, target=2e5)
-    assert same(run(ctx, p), want(oracle, p))
+    assert same(run(ctx, p), want(oracle, p, ctx))
 
 
 @pytest.mark.parametrize("seed,mode,plant", [(0, "literal", None), (3, "constructed", True),
@@ -137,7 +166,7 @@ def test_config2_full_size(ctx, oracle, seed, mode, plant):
     """The benchmarked workload at full size (~10^7 accesses), same launch
     path as the benchmark: whole result against the oracle."""
     p = protogen.config2(seed, mode, plant=plant)
-    assert same(run(ctx, p), want(oracle, p))
+    assert same(run(ctx, p), want(oracle, p, ctx))
 
 
 def test_config2_full_size_plan_equals_check(ctx, oracle):
@@ -147,7 +176,7 @@ def test_config2_full_size_plan_equals_check(ctx, oracle):
     bc = drf.drf_protocol_compile(p.text)
     plan = drf.drf_plan_create(ctx, [bc], [(p.nthreads, p.cells, p.params)])
     try:
-        exp = want(oracle, p)
+        exp = want(oracle, p, ctx)
         for _ in range(3):
             drf.drf_plan_launch(plan)
             got = drf.result_dict(drf.drf_plan_results(plan)[0])
@@ -165,7 +194,7 @@ def test_batch_equals_alone_and_oracle(ctx, oracle):
     bcs = [drf.drf_protocol_compile(p.text) for p in ps]
     res = drf.drf_check_batch(ctx, bcs, [(p.nthreads, p.cells, p.params) for p in ps])
     for p, r in zip(ps, res):
-        exp = want(oracle, p)
+        exp = want(oracle, p, ctx)
         if exp["status"] == "OVERFLOW":
             continue
         assert same(drf.result_dict(r), exp), p.text
@@ -188,7 +217,7 @@ def test_batch_equals_alone_and_oracle(ctx, oracle):
 def test_edge_cases(ctx, oracle, case):
     text, T, cells, params = case
     p = protogen.Protocol(text, T, cells, params)
-    assert same(run(ctx, p), want(oracle, p))
+    assert same(run(ctx, p), want(oracle, p, ctx))
 
 
 def test_key_too_wide_is_reported(ctx):
@@ -199,7 +228,7 @@ def test_key_too_wide_is_reported(ctx):
 
 def test_server_results_equal_alone(ctx, oracle):
     ps = protogen.config4(master_seed=3, count=60) + [protogen.config2(1, target=3e5)]
-    s = drf.drf_ctx_create(0)
+    s = drf.drf_ctx_create(0, flags=PATH_FLAGS[ctx.path])
     try:
         drf.drf_server_start(s, max_round_tuples=1 << 20)
         tickets = [drf.drf_server_submit(s, drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
@@ -212,7 +241,7 @@ def test_server_results_equal_alone(ctx, oracle):
     assert stats["completed"] == len(ps) and stats["rounds"] >= 2
     for p, o in zip(ps, out):
         assert o is not None
-        assert same(drf.result_dict(o[0]), want(oracle, p))
+        assert same(drf.result_dict(o[0]), want(oracle, p, ctx))
 
 
 def test_param_sweep_equals_per_value(ctx, oracle):
@@ -265,10 +294,68 @@ def test_autotuned_batched_plan(oracle):
                                    [(p.nthreads, p.cells, p.params) for p in ps])
         cfg = drf.drf_plan_config(plan)
         assert cfg["granularity"] in (32, 128, 512) and cfg["radix_items"] in (12, 16, 24)
+        assert drf.drf_plan_path(plan) in ("sort", "table")
         for _ in range(2):
             drf.drf_plan_launch(plan)
             for p, r in zip(ps, drf.drf_plan_results(plan)):
                 assert same(drf.result_dict(r), want(oracle, p))
         drf.drf_plan_destroy(plan)
+    finally:
+        drf.drf_ctx_destroy(c)
+
+
+# ------------------------------------------------------------ owner table
+
+@pytest.mark.parametrize("T", [2, 32767, 32768, 32769, 65536])
+def test_owner_record_width_boundary(ctx, oracle, T):
+    """Thread ids up to 15 bits take 32-bit owner records, wider ones 64-bit
+    records: the first and the last thread collide on one cell, and only
+    they do."""
+    text = "array A;\nwr A[tid % (NT - 1)];\n".replace("NT", str(T))
+    p = protogen.Protocol(text, T, [T], [])
+    got = run(ctx, p)
+    assert same(got, want(oracle, p, ctx))
+    assert (got["verdict"], got["index"], got["tid_i"], got["tid_j"]) == ("RACY", 0, 0, T - 1)
+
+
+def test_table_is_clean_between_checks(ctx, oracle):
+    """A racy check followed by race-free checks of the same shape on one
+    context: records of the first must not leak into the next (the table
+    scan clears what it reads)."""
+    racy = protogen.config2(3, "constructed", target=3e5, plant=True)
+    clean = protogen.config2(3, "constructed", target=3e5, plant=False)
+    for p in (racy, clean, racy, clean, clean):
+        assert same(run(ctx, p), want(oracle, p, ctx))
+
+
+def test_table_plan_replays(oracle):
+    """Graph replays of an owner-table plan: the witness is found launch after
+    launch (each launch leaves the table zero for the next)."""
+    c = drf.drf_ctx_create(0, flags=drf.OPT_PATH_TABLE)
+    try:
+        ps = [protogen.config2(3, "constructed", target=3e5, plant=True), protogen.config1("nosync"),
+              protogen.config1("drf"), protogen.random_small(5)]
+        plan = drf.drf_plan_create(c, [drf.drf_protocol_compile(p.text) for p in ps],
+                                   [(p.nthreads, p.cells, p.params) for p in ps])
+        assert drf.drf_plan_path(plan) == "table"
+        info = drf.drf_plan_info(plan)
+        assert info["sort_passes"] == 0
+        for _ in range(4):
+            drf.drf_plan_launch(plan)
+            for p, r in zip(ps, drf.drf_plan_results(plan)):
+                assert same(drf.result_dict(r), want(oracle, p))
+        drf.drf_plan_destroy(plan)
+    finally:
+        drf.drf_ctx_destroy(c)
+
+
+def test_automatic_path_choice(oracle):
+    """Without a forced back end the library picks one per batch; results are
+    the same either way."""
+    c = drf.drf_ctx_create(0)
+    try:
+        for p in (protogen.config1("nosync"), protogen.config2(0, target=3e5),
+                  protogen.Protocol("array A;\nwr A[4294967295 + tid];\n", 2, [1 << 40], [])):
+            assert same(run(c, p), want(oracle, p))
     finally:
         drf.drf_ctx_destroy(c)

@@ -21,8 +21,9 @@
 //   table     interpret again, OR-ing each access's owner record (tid, its
 //             complement, the write bit) into its cell and marking the
 //             cell's block as touched
-//   tscan     read the touched blocks: a cell is racy iff written and its
-//             accessors are not all one thread; min-reduce the first racy
+//   tscan     list the touched blocks (compaction of the touch bitmap), then
+//             read them, one warp per block: a cell is racy iff written and
+//             its accessors are not all one thread; min-reduce the first racy
 //             position per protocol; clear what was read
 //   witness   interpret the racy protocols once more, up to the witness
 //             cell's phase, collecting which threads access / write it
@@ -991,104 +992,105 @@ __device__ uint32_t proto_of_record(const BatchArgs &a, unsigned long long pos)
     return lo;
 }
 
-// Reads every touched block of the owner table: records a protocol's first
-// racy cell (the smallest position: rows are phase-major, then array, then
-// index, the lexicographic order of the witness) and clears every record it
-// read and every touch word, so that table and bitmap are all zero again for
-// the next launch.  A warp takes 32 touch words at a time (one per lane) and
-// then their touched blocks, up to BLK in flight.  Also clears the witness
-// hit bits for the M_CELL pass that follows.
-template <bool R64>
-__global__ void __launch_bounds__(kTabScanThreads) k_tscan(BatchArgs a)
+// Lists the touched blocks of the owner table: one thread per touch word,
+// one atomicAdd per warp for its words' share of the list; clears the words
+// it read and the witness hit bits for the M_CELL pass.
+__global__ void __launch_bounds__(kTabScanThreads) k_tlist(BatchArgs a)
 {
-    constexpr int BLK = R64 ? 2 : 4;
-    constexpr int V4 = R64 ? 4 : 2;                     // uint4 loads per lane per block
-    constexpr int PER = kTabBlock / 32;                 // records per lane per block
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t gthreads = (uint64_t)gridDim.x * kTabScanThreads;
     for (uint64_t i = blockIdx.x * (uint64_t)kTabScanThreads + threadIdx.x; i < a.nhit; i += gthreads) {
         a.hit_acc[i] = 0;
         a.hit_wr[i] = 0;
     }
+    const uint64_t nwords = touch_words(a.tab_cells);
+    const uint64_t cap = table_blocks(a.tab_cells);
+    const uint64_t first = (blockIdx.x * (uint64_t)kTabScanThreads) & ~31ull;
+    for (uint64_t base = first + (threadIdx.x & ~31u); base < nwords; base += gthreads) {
+        const uint64_t wd = base + lane;
+        const uint32_t bits = wd < nwords ? a.touch[wd] : 0u;
+        if (bits) a.touch[wd] = 0;
+        const uint32_t cnt = (uint32_t)__popc(bits);
+        uint32_t incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if ((int)lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        if (total == 0) continue;
+        unsigned long long at = 0;
+        if (lane == 31) at = atomicAdd(&a.ctrl->touched, (unsigned long long)total);
+        at = __shfl_sync(kFull, at, 31) + (incl - cnt);
+        for (uint32_t b = bits; b; b &= b - 1, at++) {
+            if (at < cap) a.tlist[at] = (uint32_t)(wd * 32 + (uint32_t)(__ffs(b) - 1));
+            else atomicOr(&a.ctrl->flags, CF_TABLE_RANGE);
+        }
+    }
+}
+
+// Reads every listed block of the owner table: records each protocol's first
+// racy cell -- the smallest position, since rows are phase-major, then array,
+// then index, the lexicographic order of the witness -- and clears every
+// record it read, so that the table is all zero again for the next launch
+// (k_tlist cleared the touch words).  One warp per listed block.
+template <bool R64>
+__global__ void __launch_bounds__(kTabScanThreads) k_tscan(BatchArgs a)
+{
+    constexpr int V4 = R64 ? 4 : 2;                     // uint4 loads per lane per block
+    constexpr int PER = kTabBlock / 32;                 // records per lane per block
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kTabScanThreads;
     __shared__ uint32_t s_proto;
     __shared__ unsigned long long s_best;
     if (threadIdx.x == 0) { s_proto = 0xFFFFFFFFu; s_best = kNone; }
     __syncthreads();
-    const uint64_t nwords = touch_words(a.tab_cells);
+    unsigned long long listed = a.ctrl->touched;
+    if (listed > table_blocks(a.tab_cells)) listed = table_blocks(a.tab_cells);
     const uint64_t warps = gthreads / 32;
-    unsigned long long cand = kNone, cand_end = 0;
+    // a lane's smallest racy position, per protocol ([cand_lo, cand_hi) its records)
+    unsigned long long cand = kNone, cand_lo = 0, cand_hi = 0;
     uint32_t cand_p = 0;
     auto flush = [&]() {
         if (cand != kNone && __ldcg(&a.best_pos[cand_p]) > cand) atomicMin(&a.best_pos[cand_p], cand);
         cand = kNone;
     };
-    // positions a lane sees only grow, so its first racy record per protocol is its smallest
     auto note = [&](unsigned long long pos) {
-        if (cand != kNone && pos < cand_end) return;
+        if (cand != kNone && pos >= cand_lo && pos < cand_hi) {
+            cand = pos < cand ? pos : cand;
+            return;
+        }
         flush();
         cand_p = proto_of_record(a, pos);
         const DevProto &P = a.protos[cand_p];
         cand = pos;
-        cand_end = P.tab_off + (uint64_t)P.tab_phases * P.cells_sum;
+        cand_lo = P.tab_off;
+        cand_hi = P.tab_off + (uint64_t)P.tab_phases * P.cells_sum;
     };
-    // 32 touch words per warp step, one per lane, so that the bitmap is read
-    // with one round trip; then the warp works through the set words' blocks
-    const uint64_t nchunks = (nwords + 31) / 32;
-    for (uint64_t ch = (blockIdx.x * (uint64_t)kTabScanThreads + threadIdx.x) / 32; ch < nchunks; ch += warps) {
-        const uint64_t my = ch * 32 + lane;
-        uint32_t mine = my < nwords ? a.touch[my] : 0u;
-        if (mine) a.touch[my] = 0;
-        unsigned pend = __ballot_sync(kFull, mine != 0);
-        uint32_t bits = 0;
-        uint64_t wd = 0;
-        while (pend || bits) {
-            if (!bits) {                       // next set word of the chunk
-                const int src = __ffs(pend) - 1;
-                pend &= pend - 1;
-                bits = __shfl_sync(kFull, mine, src);
-                wd = ch * 32 + (uint32_t)src;
+    for (uint64_t e = (blockIdx.x * (uint64_t)kTabScanThreads + threadIdx.x) / 32; e < listed; e += warps) {
+        const uint64_t blk = a.tlist[e];
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.table) + blk * (kTabBlock / (R64 ? 2 : 4)) +
+                           (uint64_t)lane * V4;
+        uint4 v[V4];
+#pragma unroll
+        for (int q = 0; q < V4; q++) v[q] = src[q];
+        uint4 *dst = reinterpret_cast<uint4 *>(a.table) + blk * (kTabBlock / (R64 ? 2 : 4)) + (uint64_t)lane * V4;
+        const unsigned long long pos0 = blk * kTabBlock + (uint64_t)lane * PER;
+#pragma unroll
+        for (int q = 0; q < V4; q++) {
+            const uint4 x = v[q];
+            if ((x.x | x.y | x.z | x.w) == 0) continue;
+            if (R64) {
+                const unsigned long long r0 = ((unsigned long long)x.y << 32) | x.x;
+                const unsigned long long r1 = ((unsigned long long)x.w << 32) | x.z;
+                if (owner_racy64(r0)) note(pos0 + q * 2);
+                if (owner_racy64(r1)) note(pos0 + q * 2 + 1);
+            } else {
+                const uint32_t r[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (owner_racy32(r[k])) note(pos0 + q * 4 + k);
             }
-            uint64_t blk[BLK];
-            int nb = 0;
-            for (; nb < BLK && bits; nb++) {
-                blk[nb] = wd * 32 + (uint32_t)(__ffs(bits) - 1);
-                bits &= bits - 1;
-            }
-            uint4 v[BLK][V4];
-#pragma unroll
-            for (int b = 0; b < BLK; b++) {
-                if (b < nb) {
-                    const uint4 *src = reinterpret_cast<const uint4 *>(a.table) + blk[b] * (kTabBlock / (R64 ? 2 : 4)) +
-                                       (uint64_t)lane * V4;
-#pragma unroll
-                    for (int q = 0; q < V4; q++) v[b][q] = src[q];
-                }
-            }
-#pragma unroll
-            for (int b = 0; b < BLK; b++) {
-                if (b < nb) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(a.table) + blk[b] * (kTabBlock / (R64 ? 2 : 4)) +
-                                 (uint64_t)lane * V4;
-                    const unsigned long long pos0 = blk[b] * kTabBlock + (uint64_t)lane * PER;
-#pragma unroll
-                    for (int q = 0; q < V4; q++) {
-                        const uint4 x = v[b][q];
-                        if ((x.x | x.y | x.z | x.w) == 0) continue;
-                        if (R64) {
-                            const unsigned long long r0 = ((unsigned long long)x.y << 32) | x.x;
-                            const unsigned long long r1 = ((unsigned long long)x.w << 32) | x.z;
-                            if (owner_racy64(r0)) note(pos0 + q * 2);
-                            if (owner_racy64(r1)) note(pos0 + q * 2 + 1);
-                        } else {
-                            const uint32_t r[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-                            for (int e = 0; e < 4; e++)
-                                if (owner_racy32(r[e])) note(pos0 + q * 4 + e);
-                        }
-                        dst[q] = make_uint4(0, 0, 0, 0);
-                    }
-                }
-            }
+            dst[q] = make_uint4(0, 0, 0, 0);
         }
     }
     // final candidates: min over the warp, then over the block, when they
@@ -1305,9 +1307,12 @@ static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms
     if (a.rec64) launch_interp<M_TAB64>(a, s, sms);
     else launch_interp<M_TAB32>(a, s, sms);
     mark(ev, nev, s);
-    const uint64_t warps_needed = (touch_words(a.tab_cells) + 31) / 32;
-    uint64_t grid = (warps_needed + kTabScanThreads / 32 - 1) / (kTabScanThreads / 32);
     const uint64_t cap = (uint64_t)sms * 8;
+    uint64_t lgrid = (touch_words(a.tab_cells) + kTabScanThreads - 1) / kTabScanThreads;
+    if (lgrid > cap) lgrid = cap;
+    if (lgrid == 0) lgrid = 1;
+    k_tlist<<<(unsigned)lgrid, kTabScanThreads, 0, s>>>(a);
+    uint64_t grid = (table_blocks(a.tab_cells) + kTabScanThreads / 32 - 1) / (kTabScanThreads / 32);
     if (grid > cap) grid = cap;
     if (grid == 0) grid = 1;
     if (a.rec64) k_tscan<true><<<(unsigned)grid, kTabScanThreads, 0, s>>>(a);

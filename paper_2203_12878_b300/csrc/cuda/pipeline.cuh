@@ -79,6 +79,7 @@ struct BatchArgs {
     void *table;                     // [tab_cells] records, padded to whole blocks
     uint64_t tab_cells;
     uint32_t *touch;                 // one bit per block of kTabBlock records written this launch
+    uint32_t *tlist;                 // [table blocks] the touched blocks, in the order first touched
     const uint64_t *cbase;           // per (protocol, array): first record of the array in a phase row
     uint32_t *hit_acc, *hit_wr;      // per (protocol, thread) bit: accessed / wrote the witness cell
     uint64_t nhit;                   // words of each hit array

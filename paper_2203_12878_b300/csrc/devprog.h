@@ -140,7 +140,7 @@ struct Control {
     unsigned long long total;          // access tuples of the launch
     unsigned int detect_tiles;
     unsigned int flags;                // CF_* internal failures
-    unsigned int pad[2];
+    unsigned long long touched;        // owner-table blocks listed this launch
 };
 
 enum : unsigned {

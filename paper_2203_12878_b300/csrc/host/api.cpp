@@ -557,7 +557,7 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
     if (sort_passes) *sort_passes = table ? 0 : plan->host.L.passes;
     if (kernels_per_launch) {
         uint32_t widths = plan->dev.args.has_narrow + plan->dev.args.has_wide;
-        if (table) *kernels_per_launch = 3 * widths + 4;   // init, 3x interp, scan, tscan, finalize
+        if (table) *kernels_per_launch = 3 * widths + 5;   // init, 3x interp, scan, tlist, tscan, finalize
         else *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes;   // init, 2x interp, scan, passes, detect, resolve, finalize
     }
     if (sort_bits) *sort_bits = plan->host.L.sort_bits;

@@ -111,7 +111,7 @@ DeviceBatch::~DeviceBatch()
 {
     DevBuf *all[] = {&insns, &xcode, &items, &protos, &cells, &witems, &cnt, &syn, &phs, &erro, &totsyn,
                      &wcnt, &wbase, &blocksum, &keys0, &keys1, &hist, &status, &trec, &err_key, &div_tid,
-                     &best_pos, &ptuples, &results, &ctrl, &epoch, &cbase, &table, &touch, &hit};
+                     &best_pos, &ptuples, &results, &ctrl, &epoch, &cbase, &table, &touch, &tlist, &hit};
     for (DevBuf *b : all) release(*b, &in_use);
 }
 
@@ -202,6 +202,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.table = nullptr;
     a.tab_cells = 0;
     a.touch = nullptr;
+    a.tlist = nullptr;
     a.hit_acc = a.hit_wr = nullptr;
     a.nhit = 0;
     return Error{};
@@ -214,8 +215,9 @@ Error DeviceBatch::size_table(const BatchHost &b, uint64_t n, cudaStream_t s)
     const size_t wb = std::max<uint64_t>(touch_words(b.table_cells) * 4, 16);
     const uint64_t nhit = (b.ncols + 31) / 32 + 1;
     void *old_table = table.p, *old_touch = touch.p;
+    const size_t lb = std::max<uint64_t>(table_blocks(b.table_cells) * 4, 16);
     if (!ensure(table, tb, &in_use, limit) || !ensure(touch, wb, &in_use, limit) ||
-        !ensure(hit, nhit * 8, &in_use, limit)) {
+        !ensure(tlist, lb, &in_use, limit) || !ensure(hit, nhit * 8, &in_use, limit)) {
         cudaGetLastError();
         return Error::make(S_NOMEM, "device allocation of a " + std::to_string(tb) + "-byte owner table failed");
     }
@@ -233,6 +235,7 @@ Error DeviceBatch::size_table(const BatchHost &b, uint64_t n, cudaStream_t s)
     a.table = table.p;
     a.tab_cells = b.table_cells;
     a.touch = (uint32_t *)touch.p;
+    a.tlist = (uint32_t *)tlist.p;
     a.hit_acc = (uint32_t *)hit.p;
     a.hit_wr = (uint32_t *)hit.p + nhit;
     a.nhit = nhit;

@@ -56,7 +56,7 @@ struct DeviceBatch {
     DevBuf cnt, syn, phs, erro, totsyn, wcnt, wbase, blocksum;
     DevBuf keys0, keys1, hist, status, trec;
     DevBuf err_key, div_tid, best_pos, ptuples, results, ctrl, epoch;
-    DevBuf cbase, table, touch, hit;
+    DevBuf cbase, table, touch, tlist, hit;
     size_t in_use = 0;
     uint64_t limit = 0;
     uint64_t status_launches = 0;     // launches since the look-back words were cleared

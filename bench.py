@@ -228,14 +228,16 @@ def run_ours(args, rank, world):
         p = protogen.config2(rank, "literal")
     bc = drf.drf_protocol_compile(p.text)
     bounds = [(p.nthreads, p.cells, p.params)]
-    flags = drf.OPT_PROFILE_STAGES | {"auto": drf.OPT_AUTOTUNE, "sort": drf.OPT_PATH_SORT,
-                                      "table": drf.OPT_PATH_TABLE}[args.path]
+    flags = drf.OPT_PROFILE_STAGES | {"auto": drf.OPT_AUTOTUNE | drf.OPT_SPECIALIZE, "sort": drf.OPT_PATH_SORT,
+                                      "table": drf.OPT_PATH_TABLE,
+                                      "specialized": drf.OPT_PATH_TABLE | drf.OPT_SPECIALIZE}[args.path]
     ctx = drf.drf_ctx_create(dev, flags=flags)
     t_plan = time.perf_counter()
     plan = drf.drf_plan_create(ctx, [bc], bounds)
     plan_s = time.perf_counter() - t_plan
     info = drf.drf_plan_info(plan)
     path = drf.drf_plan_path(plan)
+    specialized, _ = drf.drf_plan_specialized(plan)
     n = info["tuples"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -256,23 +258,24 @@ def run_ours(args, rank, world):
         ms = float(t.item())
     roof, stages = roofline(kinds, args.steps, n, info)
 
-    # the other back end on the same protocol, for comparison
-    other = None
+    # the interpreted back ends on the same protocol, for comparison
+    others = []
     if rank == 0 and not args.quick and args.path == "auto":
-        octx = drf.drf_ctx_create(dev, flags=drf.OPT_PROFILE_STAGES |
-                                  (drf.OPT_PATH_SORT if path == "table" else drf.OPT_PATH_TABLE))
-        try:
-            oplan = drf.drf_plan_create(octx, [bc], bounds)
-            osteps = max(20, args.steps // 5)
-            oms, okinds, _, _ = time_steps(oplan, osteps, 3, stream, flush)
-            assert drf.result_dict(drf.drf_plan_results(oplan)[0]) == res
-            oroof, ostages = roofline(okinds, osteps, n, drf.drf_plan_info(oplan))
-            other = {"path": drf.drf_plan_path(oplan), "ms_per_step": statistics.mean(oms),
-                     "value": n / (statistics.mean(oms) * 1e-3), "stages_ms": ostages, "roofline": oroof}
-            drf.drf_plan_destroy(oplan)
-        except drf.DrfError as e:
-            other = {"unavailable": str(e)}
-        drf.drf_ctx_destroy(octx)
+        for oflags in (drf.OPT_PATH_SORT, drf.OPT_PATH_TABLE):
+            octx = drf.drf_ctx_create(dev, flags=drf.OPT_PROFILE_STAGES | oflags)
+            try:
+                oplan = drf.drf_plan_create(octx, [bc], bounds)
+                osteps = max(20, args.steps // 5)
+                oms, okinds, _, _ = time_steps(oplan, osteps, 3, stream, flush)
+                assert drf.result_dict(drf.drf_plan_results(oplan)[0]) == res
+                oroof, ostages = roofline(okinds, osteps, n, drf.drf_plan_info(oplan))
+                others.append({"path": drf.drf_plan_path(oplan), "specialized": False,
+                               "ms_per_step": statistics.mean(oms), "value": n / (statistics.mean(oms) * 1e-3),
+                               "stages_ms": ostages, "roofline": oroof})
+                drf.drf_plan_destroy(oplan)
+            except drf.DrfError as e:
+                others.append({"flags": oflags, "unavailable": str(e)})
+            drf.drf_ctx_destroy(octx)
 
     # end to end through the public API: host bytecode in, host result out
     e2e_t = []
@@ -298,7 +301,8 @@ def run_ours(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": ("u32/u64 owner records" if path == "table" else "u64 keys") + ", int32/int64 index arithmetic",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "tuples_per_step": n, "path": path, "path_choice": args.path,
+            "config": {"workload": WORKLOAD, "tuples_per_step": n, "path": path, "specialized": specialized,
+                       "path_choice": args.path,
                        "plan": {**drf.drf_plan_config(plan), "create_s": round(plan_s, 3)},
                        "sort_passes": info["sort_passes"], "sort_bits": info["sort_bits"],
                        "verdict": res.get("verdict"),
@@ -306,7 +310,7 @@ def run_ours(args, rank, world):
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "stages_ms": stages,
-            "other_path": other,
+            "alternatives": others,
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"the same protocol with its first 128 of 1024 threads, "
                                        f"per-cell-record checker, {cpu_runs} runs in {cpu_el:.1f} s"},
@@ -436,8 +440,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the batched and served measurements")
-    ap.add_argument("--path", choices=("auto", "sort", "table"), default="auto",
-                    help="back end of the timed plan: chosen per batch (autotuned), or forced")
+    ap.add_argument("--path", choices=("auto", "sort", "table", "specialized"), default="auto",
+                    help="back end of the timed plan: autotuned (specialized kernels allowed), or forced")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--rates", type=float, nargs="*", default=[1000, 5000, 20000, 50000],
                     help="served-workload arrival rates (requests/s)")

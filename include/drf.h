@@ -138,20 +138,28 @@ typedef struct {
  * Definition 1 exactly and return identical results:
  *   sort path   -- one 64-bit key per access (phase, array, index, tid, mode),
  *                  radix-sorted on the cell fields, racy segments detected;
- *   owner table -- one record per (phase, array, index) cell, rows up to the
- *                  static bound on syncs; each access ORs (tid, ~tid, write)
- *                  into its cell, a cell is racy iff written with two
- *                  distinct accessors, and a second pass restricted to the
- *                  first racy cell finds the witness threads.  It needs
- *                  (sync bound + 1) x (sum of array sizes) x 4 bytes (8 when
- *                  thread ids exceed 15 bits), at most 64 GiB, and thread
- *                  ids below 2^31.
+ *   owner table -- one 32-bit record per (phase, array, index) cell, rows
+ *                  up to the static bound on syncs: the first accessor, "a
+ *                  second thread accessed it", "it was written"; a cell is
+ *                  racy iff written with a second thread, and a further pass
+ *                  restricted to the first racy cell finds the witness
+ *                  threads.  It needs (sync bound + 1) x (sum of array
+ *                  sizes) x 4 bytes, at most 64 GiB.
  * The automatic choice takes the owner table when it fits and is at most
  * max(256 MiB, 256 bytes per access tuple); otherwise, or when the table
  * cannot be allocated, the sort path.  Forcing the owner table on a batch
  * it cannot hold returns DRF_E_LIMIT (or DRF_E_NOMEM). */
 #define DRF_OPT_PATH_SORT      0x4u
 #define DRF_OPT_PATH_TABLE     0x8u
+/* Plans over a single protocol may run kernels specialized to it: its
+ * count, owner-table and witness passes translated to CUDA C (loops as
+ * loops, every coefficient, array size and table stride a constant) and
+ * compiled for sm_103a with NVRTC at plan creation (about 0.1 - 1 s); the
+ * results are those of the interpreter.  Without DRF_OPT_AUTOTUNE such a
+ * plan uses them whenever they compile; with it the tuner times them
+ * against the interpreted configurations.  Plans keep the interpreter when
+ * NVRTC is unavailable or the protocol has no owner table. */
+#define DRF_OPT_SPECIALIZE     0x10u
 
 #define DRF_PATH_SORT  1
 #define DRF_PATH_TABLE 2
@@ -306,6 +314,18 @@ int drf_debug_sorted_keys(drf_ctx *ctx, uint64_t *keys, uint64_t cap, uint64_t *
 int drf_check_param_sweep(drf_ctx *ctx, const uint8_t *bytecode, size_t len, const drf_bounds *bounds,
                           uint32_t param, int64_t lo, int64_t hi, drf_result *out, void *stream);
 
+/* Run-time specialization diagnostics.  Generates the CUDA source of the
+ * per-protocol kernels (count, owner-table and witness passes) that a plan
+ * over this one protocol compiles with DRF_OPT_SPECIALIZE, and, when
+ * `compile` is nonzero, compiles it for sm_103a with NVRTC (no GPU needed).
+ * *source receives the text (free with drf_free); log, when not NULL,
+ * receives the compiler's log (truncated to loglen).  Returns DRF_E_LIMIT
+ * when the protocol cannot be specialized (its owner table does not fit, or
+ * more than 64 item shapes), DRF_E_NOT_FOUND when NVRTC cannot be loaded,
+ * DRF_E_INTERNAL when NVRTC rejects the source. */
+int drf_protocol_specialize(const uint8_t *bytecode, size_t len, const drf_bounds *bounds, int compile,
+                            char **source, char *log, size_t loglen);
+
 /* ------------------------------------------------------------------- plans -- */
 
 /* Prepares a fixed batch for repeated checks: validates and lowers every
@@ -342,6 +362,11 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
  * workload signature for the process and, when the environment variable
  * DRF_TUNE_CACHE names a file, persisted there. */
 int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix_items);
+
+/* Whether a plan runs kernels specialized to its protocol
+ * (DRF_OPT_SPECIALIZE); when specialization was asked for but not used,
+ * log (may be NULL) receives why. */
+int drf_plan_specialized(const drf_plan *plan, uint32_t *specialized, char *log, size_t loglen);
 
 /* The back end a plan runs: DRF_PATH_SORT or DRF_PATH_TABLE (see
  * DRF_OPT_PATH_*).  With DRF_OPT_AUTOTUNE the tuner times both back ends

@@ -32,6 +32,34 @@ def _headers():
     return hs
 
 
+# Headers the per-protocol kernels compiled at run time inline as text.
+JIT_HEADERS = (("kJitDevprogH", "devprog.h"), ("kJitBatchArgsH", "batch_args.h"),
+               ("kJitIntmathCuh", os.path.join("cuda", "intmath.cuh")),
+               ("kJitOwnerCuh", os.path.join("cuda", "owner.cuh")))
+GEN = os.path.join(BUILD, "gen")
+
+
+def _gen_jit_headers():
+    """Writes _build/gen/jit_headers.inc (the headers as C++ raw strings)
+    when it is missing or older than one of them."""
+    os.makedirs(GEN, exist_ok=True)
+    out = os.path.join(GEN, "jit_headers.inc")
+    srcs = [os.path.join(CSRC, rel) for _, rel in JIT_HEADERS]
+    if os.path.exists(out) and os.path.getmtime(out) >= max(os.path.getmtime(x) for x in srcs):
+        return out
+    parts = ["// Generated by build.py from the shared headers; do not edit.\n"]
+    for (name, _), path in zip(JIT_HEADERS, srcs):
+        text = open(path).read()
+        if ")DRFH\"" in text:
+            raise RuntimeError(f"{path} contains the raw-string delimiter")
+        parts.append(f'static const char {name}[] = R"DRFH({text})DRFH";\n')
+    tmp = out + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        f.write("".join(parts))
+    os.replace(tmp, out)
+    return out
+
+
 def _run(cmd, verbose):
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
@@ -42,7 +70,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     """Compiles what is out of date and links the library; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     cu, cpp = _sources()
-    newest_header = max((os.path.getmtime(h) for h in _headers()), default=0)
+    gen = _gen_jit_headers()
+    newest_header = max([os.path.getmtime(h) for h in _headers()] + [os.path.getmtime(gen)])
     objs = []
     for src in cu + cpp:
         rel = os.path.relpath(src, CSRC).replace(os.sep, "_")
@@ -55,12 +84,12 @@ def build(verbose: bool = False, force: bool = False) -> str:
                    "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
         else:
             cmd = ["g++", *CXXFLAGS, "-I", "/usr/local/cuda/include", "-I", os.path.join(ROOT, "include"),
-                   "-c", src, "-o", obj]
+                   "-I", GEN, "-c", src, "-o", obj]
         _run(cmd, verbose)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
         _run([NVCC, "-shared", *ARCH, "-Xcompiler", "-fPIC", "-o", tmp, *objs,
-              "-cudart", "static", "-lpthread"], verbose)
+              "-cudart", "static", "-lpthread", "-ldl"], verbose)
         os.replace(tmp, LIB)
     return LIB
 

@@ -1,0 +1,111 @@
+// Argument block of the device pipeline and the layout constants its
+// kernels share.  Plain data only: included by the host code, the CUDA
+// sources and, as text, by the per-protocol kernels compiled at run time.
+#pragma once
+
+#include "devprog.h"
+
+namespace drf {
+
+// Summary of a contiguous piece of one segment of equal sort keys, and the
+// per-tile record of the pieces that touch a detection tile's edges.
+struct Agg {
+    uint32_t mint, maxt;
+    uint32_t bits;              // 1: any write, 2: holds the segment head, 4: non-empty
+    unsigned long long start;   // sorted position of the head (valid with bit 2)
+};
+
+struct TileRec {
+    unsigned long long first_seg, last_seg;   // sort keys of the tile's first and last key
+    Agg first;                                // in-tile piece of the segment continuing from the previous tile
+    Agg last;                                 // the tile's last segment piece, when it continues into the next tile
+    uint32_t flags;                           // TR_*
+    uint32_t pad;
+};
+
+enum : uint32_t {
+    TR_STARTS_CONT = 1,   // the tile's first key continues a segment of the previous tile
+    TR_ENDS_CONT = 2,     // the tile's last segment continues into the next tile
+    TR_SINGLE = 4,        // the tile lies inside one segment that crosses both edges
+};
+
+// Everything the kernels of one launch touch.  Device pointers unless noted.
+struct BatchArgs {
+    // device programs of the batch
+    const Insn *insns;
+    const uint64_t *xcode;
+    const ItemDesc *items;
+    const DevProto *protos;
+    const uint64_t *cells;
+    const WarpItem *witems;
+    uint32_t nwitems;
+    uint32_t nprotos;
+    uint32_t has_narrow, has_wide;   // protocols with 32-bit / 64-bit arithmetic present
+    uint64_t ncols;                  // sum of thread counts (per-thread arrays)
+    // per (item, thread)
+    uint32_t *cnt;                   // accesses
+    uint32_t *syn;                   // syncs
+    uint32_t *phs;                   // phase at item start (exclusive scan of syn)
+    unsigned long long *erro;        // (local ordinal << 8) | error code
+    // per (protocol, thread)
+    uint32_t *totsyn;
+    // per warp-item
+    uint32_t *wcnt;
+    unsigned long long *wbase;
+    unsigned long long *blocksum;    // per 4096 warp-items
+    uint32_t nwblocks;
+    // keys
+    unsigned long long *keys[2];
+    uint64_t nkeys;                  // tuples this launch must produce (plan size)
+    unsigned long long *hist;        // [kMaxPasses][kRadixBins]
+    unsigned long long *status;      // [passes][ntiles][kRadixBins] look-back words
+    uint32_t ntiles;
+    uint32_t radix_items;            // keys per thread of a radix tile (12, 16 or 24; 0 = 16)
+    TileRec *trec;                   // [ndtiles] detection tile records
+    uint32_t ndtiles;
+    // per protocol
+    unsigned long long *err_key;     // min (tid << 32 | item) with an evaluation error
+    uint32_t *div_tid;               // min tid whose sync count differs from thread 0's
+    unsigned long long *best_pos;    // min sorted position of a racy segment
+    unsigned long long *ptuples;
+    DevResult *results;
+    Control *ctrl;
+    uint32_t *epoch;                 // persists across launches
+    KeyLayout L;
+    // owner table (the sort-free path): one record per (protocol, phase,
+    // array, index) cell, all zero between launches
+    uint32_t path;                   // PATH_SORT or PATH_TABLE
+    void *table;                     // [tab_cells] 32-bit owner records, padded to whole blocks
+    uint64_t tab_cells;
+    uint32_t *touch;                 // one bit per block of kTabBlock records written this launch
+    uint32_t *tlist;                 // [table blocks] the touched blocks, in the order first touched
+    const uint64_t *cbase;           // per (protocol, array): first record of the array in a phase row
+    uint32_t *hit_acc, *hit_wr;      // per (protocol, thread) bit: accessed / wrote the witness cell
+    uint64_t nhit;                   // words of each hit array
+};
+
+enum : uint32_t { PATH_SORT = 0, PATH_TABLE = 1 };
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;     // 4096 keys
+constexpr int kDetectThreads = 256;
+constexpr int kDetectItems = 16;
+constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 4096 keys
+constexpr int kFinalizeThreads = 128;
+constexpr int kScanThreads = 256;
+constexpr int kWScanPerBlock = 4096;                        // warp-items per scan block
+constexpr int kTabBlockLog = 8;
+constexpr int kTabBlock = 1 << kTabBlockLog;                // owner-table records per touch bit
+constexpr int kTabScanThreads = 256;
+
+// Owner-table blocks and touch-bitmap words for `cells` records.
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
+#define DRF_HOST_DEVICE __host__ __device__
+#else
+#define DRF_HOST_DEVICE
+#endif
+DRF_HOST_DEVICE inline uint64_t table_blocks(uint64_t cells) { return (cells + kTabBlock - 1) / kTabBlock; }
+DRF_HOST_DEVICE inline uint64_t touch_words(uint64_t cells) { return (table_blocks(cells) + 31) / 32; }
+
+}  // namespace drf

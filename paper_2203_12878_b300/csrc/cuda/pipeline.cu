@@ -18,12 +18,12 @@
 //             racy iff it holds a write and two distinct tids; min-reduce the
 //             sorted position of the first racy segment per protocol
 // Owner-table path (no sort; one record per (proto, phase, array, index)):
-//   table     interpret again, OR-ing each access's owner record (tid, its
-//             complement, the write bit) into its cell and marking the
-//             cell's block as touched
+//   table     interpret again, updating each access's owner record (first
+//             accessor, "a second thread", "written"; owner.cuh) and marking
+//             the cell's block as touched
 //   tscan     list the touched blocks (compaction of the touch bitmap), then
 //             read them, one warp per block: a cell is racy iff written and
-//             its accessors are not all one thread; min-reduce the first racy
+//             accessed by a second thread; min-reduce the first racy
 //             position per protocol; clear what was read
 //   witness   interpret the racy protocols once more, up to the witness
 //             cell's phase, collecting which threads access / write it
@@ -34,6 +34,8 @@
 //             j = its smallest admissible partner
 #include <cstdint>
 
+#include "intmath.cuh"
+#include "owner.cuh"
 #include "pipeline.cuh"
 #include "radix.cuh"
 
@@ -63,30 +65,6 @@ __device__ __forceinline__ unsigned lanemask_lt()
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
-
-// ------------------------------------------------------- integer semantics
-// Floor division and Euclidean remainder.  The host's interval analysis
-// guarantees b != 0 where no check is made and that no result overflows.
-template <typename V, typename U>
-__device__ __forceinline__ V floor_div(V a, V b)
-{
-    V q = a / b;
-    V r = (V)((U)a - (U)q * (U)b);
-    if (r != 0 && ((r < 0) != (b < 0))) q -= 1;
-    return q;
-}
-
-template <typename V, typename U>
-__device__ __forceinline__ V euclid_mod(V a, V b)
-{
-    V r = a % b;
-    if (r < 0) r = (V)(b > 0 ? (U)r + (U)b : (U)r - (U)b);
-    return r;
-}
-
-template <typename V> struct Unsigned;
-template <> struct Unsigned<int32_t> { using T = uint32_t; };
-template <> struct Unsigned<int64_t> { using T = uint64_t; };
 
 // Stack machine over the expression code (see devprog.h).  Returns false on
 // a division or remainder by zero.
@@ -204,47 +182,17 @@ __device__ __forceinline__ V fast_post(V v, uint32_t kind, U c)
 enum : int {
     M_COUNT = 0,   // accesses, syncs and the first error per (item, thread)
     M_EMIT = 1,    // one sort key per access
-    M_TAB32 = 2,   // OR one 32-bit owner record per access into the table
-    M_TAB64 = 3,   // the same with 64-bit records
-    M_CELL = 4,    // which threads access / write one given cell
+    M_TABLE = 2,   // one owner-record update per access
+    M_CELL = 3,    // which threads access / write one given cell
 };
 
-// Owner records.  Definition 1 asks, per cell, whether some access writes it
-// and whether two different threads access it.  An access contributes its
-// thread id, the id's complement and its write bit; OR-ing the contributions
-// of all accesses to a cell leaves OR(tid), the complement of AND(tid) and
-// "written".  The cell is racy iff it is written and AND(tid) != OR(tid),
-// i.e. the accessors are not all one thread.  32-bit records hold 15-bit
-// thread ids, 64-bit records 31-bit ones.
-__device__ __forceinline__ unsigned long long owner_rec32(uint32_t tid, uint32_t w)
-{
-    return (tid & 0x7FFFu) | ((~tid & 0x7FFFu) << 15) | (w << 31);
-}
-__device__ __forceinline__ unsigned long long owner_rec64(uint32_t tid, uint32_t w)
-{
-    return (unsigned long long)(tid & 0x7FFFFFFFu) | ((unsigned long long)(~tid & 0x7FFFFFFFu) << 31) |
-           ((unsigned long long)w << 63);
-}
-__device__ __forceinline__ bool owner_racy32(uint32_t r)
-{
-    return (r >> 31) && (r & 0x7FFFu) != (~(r >> 15) & 0x7FFFu);
-}
-__device__ __forceinline__ bool owner_racy64(unsigned long long r)
-{
-    return (r >> 63) && (r & 0x7FFFFFFFull) != (~(r >> 31) & 0x7FFFFFFFull);
-}
-
-// ORs each valid lane's record into the table and marks the record's block
-// as touched.  When every valid lane hits one cell (an index that does not
-// depend on tid), the warp combines its records and one lane writes.  A
-// lane first reads the record through L1 and skips the OR when the record
-// already holds all its bits: records only gain bits during a launch, so a
-// stale copy can only under-report and the skip never loses a bit -- but it
-// removes most same-address atomics on cells that many accesses share.
-// Each lane remembers the last block it marked.
-template <bool R64>
-__device__ __forceinline__ void table_put(const BatchArgs &a, bool ok, unsigned long long off,
-                                          unsigned long long rec, unsigned long long &last_bid)
+// Applies each valid lane's access to its owner record (owner.cuh) and marks
+// the record's block as touched.  When every valid lane hits one cell (an
+// index that does not depend on tid), one lane updates the record for the
+// warp.  The record is read through L1 first; the update is skipped when the
+// copy already implies it.  Each lane remembers the last block it marked.
+__device__ __forceinline__ void table_put(const BatchArgs &a, bool ok, unsigned long long off, uint32_t tid,
+                                          uint32_t w, unsigned long long &last_bid)
 {
     const unsigned m = __ballot_sync(kFull, ok);
     if (m == 0) return;
@@ -252,22 +200,20 @@ __device__ __forceinline__ void table_put(const BatchArgs &a, bool ok, unsigned 
     const unsigned long long off0 = __shfl_sync(kFull, off, lead);
     bool mine = ok;
     if (__all_sync(kFull, !ok || off == off0)) {
-        const unsigned long long r = ok ? rec : 0ull;
-        const uint32_t lo = __reduce_or_sync(kFull, (uint32_t)r);
-        const uint32_t hi = R64 ? __reduce_or_sync(kFull, (uint32_t)(r >> 32)) : 0u;
-        rec = ((unsigned long long)hi << 32) | lo;
+        const unsigned wm = __ballot_sync(kFull, ok && w);
         mine = (int)(threadIdx.x & 31) == lead;
+        if (mine && __popc(m) >= 2) {
+            uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
+            owner_put_many(cell, __ldca(cell), wm != 0);
+        } else if (mine) {
+            uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
+            owner_put(cell, __ldca(cell), tid, w);
+        }
+    } else if (ok) {
+        uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
+        owner_put(cell, __ldca(cell), tid, w);
     }
     if (mine) {
-        if (R64) {
-            unsigned long long *cell = reinterpret_cast<unsigned long long *>(a.table) + off;
-            const unsigned long long cur = __ldca(cell);
-            if ((cur | rec) != cur) atomicOr(cell, rec);
-        } else {
-            uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
-            const uint32_t cur = __ldca(cell);
-            if ((cur | (uint32_t)rec) != cur) atomicOr(cell, (uint32_t)rec);
-        }
         // touch bit: a few hot blocks share one bitmap word, so it is read
         // through L1 first like the record (bits only get set in a launch)
         const unsigned long long bid = off >> kTabBlockLog;
@@ -295,8 +241,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
 {
     using U = typename Unsigned<V>::T;
     constexpr bool EMIT = MODE == M_EMIT;
-    constexpr bool R64 = MODE == M_TAB64;
-    constexpr bool TAB = MODE == M_TAB32 || MODE == M_TAB64;
+    constexpr bool TAB = MODE == M_TABLE;
     constexpr bool CELL = MODE == M_CELL;
     constexpr bool PHASED = MODE != M_COUNT;      // knows the phase of every access
     const uint32_t lane = threadIdx.x & 31;
@@ -349,8 +294,6 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
     // owner-table state
     const uint64_t *cb = a.cbase + P.cells_off;
     unsigned long long last_bid = kNone;
-    const unsigned long long rec_rd = R64 ? owner_rec64(tid, 0) : owner_rec32(tid, 0);
-    const unsigned long long rec_wr = R64 ? owner_rec64(tid, 1) : owner_rec32(tid, 1);
     uint32_t hit = 0;                                  // M_CELL: 1 accessed, 2 wrote
 
     while (true) {
@@ -383,7 +326,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                 if (ok && !put) atomicOr(&a.ctrl->flags, CF_TABLE_RANGE);
                 const unsigned long long off =
                     put ? P.tab_off + (uint64_t)phase * P.cells_sum + __ldg(cb + in.b) + (uint64_t)(U)idx : 0ull;
-                table_put<R64>(a, put, off, (in.a & AF_WRITE) ? rec_wr : rec_rd, last_bid);
+                table_put(a, put, off, tid, in.a & AF_WRITE, last_bid);
             } else if (CELL) {
                 if (ok && phase == tg.phase && in.b == tg.loc && (unsigned long long)(U)idx == tg.idx)
                     hit |= 1u | ((in.a & AF_WRITE) << 1);
@@ -495,7 +438,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                                 const unsigned long long off =
                                     put ? P.tab_off + (uint64_t)ph * P.cells_sum + __ldg(cb + loc) + (uint64_t)(U)idx
                                         : 0ull;
-                                table_put<R64>(a, put, off, (mt & AF_WRITE) ? rec_wr : rec_rd, last_bid);
+                                table_put(a, put, off, tid, mt & AF_WRITE, last_bid);
                             } else if (CELL) {
                                 if (act && ph == tg.phase && loc == tg.loc && (unsigned long long)(U)idx == tg.idx)
                                     hit |= 1u | ((mt & AF_WRITE) << 1);
@@ -1033,10 +976,9 @@ __global__ void __launch_bounds__(kTabScanThreads) k_tlist(BatchArgs a)
 // then index, the lexicographic order of the witness -- and clears every
 // record it read, so that the table is all zero again for the next launch
 // (k_tlist cleared the touch words).  One warp per listed block.
-template <bool R64>
 __global__ void __launch_bounds__(kTabScanThreads) k_tscan(BatchArgs a)
 {
-    constexpr int V4 = R64 ? 4 : 2;                     // uint4 loads per lane per block
+    constexpr int V4 = 2;                               // uint4 loads per lane per block
     constexpr int PER = kTabBlock / 32;                 // records per lane per block
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t gthreads = (uint64_t)gridDim.x * kTabScanThreads;
@@ -1068,28 +1010,20 @@ __global__ void __launch_bounds__(kTabScanThreads) k_tscan(BatchArgs a)
     };
     for (uint64_t e = (blockIdx.x * (uint64_t)kTabScanThreads + threadIdx.x) / 32; e < listed; e += warps) {
         const uint64_t blk = a.tlist[e];
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.table) + blk * (kTabBlock / (R64 ? 2 : 4)) +
-                           (uint64_t)lane * V4;
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.table) + blk * (kTabBlock / 4) + (uint64_t)lane * V4;
         uint4 v[V4];
 #pragma unroll
         for (int q = 0; q < V4; q++) v[q] = src[q];
-        uint4 *dst = reinterpret_cast<uint4 *>(a.table) + blk * (kTabBlock / (R64 ? 2 : 4)) + (uint64_t)lane * V4;
+        uint4 *dst = reinterpret_cast<uint4 *>(a.table) + blk * (kTabBlock / 4) + (uint64_t)lane * V4;
         const unsigned long long pos0 = blk * kTabBlock + (uint64_t)lane * PER;
 #pragma unroll
         for (int q = 0; q < V4; q++) {
             const uint4 x = v[q];
             if ((x.x | x.y | x.z | x.w) == 0) continue;
-            if (R64) {
-                const unsigned long long r0 = ((unsigned long long)x.y << 32) | x.x;
-                const unsigned long long r1 = ((unsigned long long)x.w << 32) | x.z;
-                if (owner_racy64(r0)) note(pos0 + q * 2);
-                if (owner_racy64(r1)) note(pos0 + q * 2 + 1);
-            } else {
-                const uint32_t r[4] = {x.x, x.y, x.z, x.w};
+            const uint32_t r[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-                for (int k = 0; k < 4; k++)
-                    if (owner_racy32(r[k])) note(pos0 + q * 4 + k);
-            }
+            for (int k = 0; k < 4; k++)
+                if (owner_racy(r[k])) note(pos0 + q * 4 + k);
             dst[q] = make_uint4(0, 0, 0, 0);
         }
     }
@@ -1278,7 +1212,16 @@ static void mark(cudaEvent_t *ev, int *nev, cudaStream_t s)
     else cudaEventRecord(ev[(*nev)++], s);
 }
 
-cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev)
+// One launch of a specialized kernel (a cudaKernel_t) over the warp-items.
+static void launch_jit(const void *k, const BatchArgs &a, const JitLaunch *j, cudaStream_t s, int sms)
+{
+    BatchArgs args = a;
+    const uint16_t *shape = j->shape;
+    void *params[] = {&args, &shape};
+    cudaLaunchKernel(k, dim3((unsigned)interp_grid(a.nwitems, sms)), dim3(256), params, 0, s);
+}
+
+cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev, const JitLaunch *j)
 {
     uint64_t init_n = a.nprotos;
     if (init_n < (uint64_t)kMaxPasses * kRadixBins) init_n = (uint64_t)kMaxPasses * kRadixBins;
@@ -1286,8 +1229,12 @@ cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_
     mark(ev, nev, s);
     k_init<<<(unsigned)((init_n + 255) / 256), 256, 0, s>>>(a);
     mark(ev, nev, s);
-    if (a.has_narrow) k_interp<M_COUNT, false><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
-    if (a.has_wide) k_interp<M_COUNT, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+    if (j && j->count) {
+        launch_jit(j->count, a, j, s, sms);
+    } else {
+        if (a.has_narrow) k_interp<M_COUNT, false><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+        if (a.has_wide) k_interp<M_COUNT, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+    }
     mark(ev, nev, s);
     uint32_t col_blocks = (uint32_t)((a.ncols + 31) / 32);
     k_scan<<<col_blocks + a.nwblocks, kScanThreads, 0, s>>>(a, col_blocks);
@@ -1302,10 +1249,11 @@ static void launch_interp(const BatchArgs &a, cudaStream_t s, int sms)
     if (a.has_wide) k_interp<MODE, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
 }
 
-static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev)
+static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev,
+                                     const JitLaunch *j)
 {
-    if (a.rec64) launch_interp<M_TAB64>(a, s, sms);
-    else launch_interp<M_TAB32>(a, s, sms);
+    if (j && j->table) launch_jit(j->table, a, j, s, sms);
+    else launch_interp<M_TABLE>(a, s, sms);
     mark(ev, nev, s);
     const uint64_t cap = (uint64_t)sms * 8;
     uint64_t lgrid = (touch_words(a.tab_cells) + kTabScanThreads - 1) / kTabScanThreads;
@@ -1315,19 +1263,19 @@ static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms
     uint64_t grid = (table_blocks(a.tab_cells) + kTabScanThreads / 32 - 1) / (kTabScanThreads / 32);
     if (grid > cap) grid = cap;
     if (grid == 0) grid = 1;
-    if (a.rec64) k_tscan<true><<<(unsigned)grid, kTabScanThreads, 0, s>>>(a);
-    else k_tscan<false><<<(unsigned)grid, kTabScanThreads, 0, s>>>(a);
+    k_tscan<<<(unsigned)grid, kTabScanThreads, 0, s>>>(a);
     mark(ev, nev, s);
-    launch_interp<M_CELL>(a, s, sms);
+    if (j && j->cell) launch_jit(j->cell, a, j, s, sms);
+    else launch_interp<M_CELL>(a, s, sms);
     mark(ev, nev, s);
     k_finalize<true><<<a.nprotos, kFinalizeThreads, 0, s>>>(a);
     mark(ev, nev, s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev)
+cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev, const JitLaunch *j)
 {
-    if (a.path == PATH_TABLE) return launch_back_table(a, s, sms, ev, nev);
+    if (a.path == PATH_TABLE) return launch_back_table(a, s, sms, ev, nev, j);
     launch_interp<M_EMIT>(a, s, sms);
     mark(ev, nev, s);
     for (uint32_t q = 0; q < a.L.passes; q++) {

@@ -3,102 +3,9 @@
 
 #include <cuda_runtime.h>
 
-#include "../devprog.h"
+#include "../batch_args.h"
 
 namespace drf {
-
-// Summary of a contiguous piece of one segment of equal sort keys, and the
-// per-tile record of the pieces that touch a detection tile's edges.
-struct Agg {
-    uint32_t mint, maxt;
-    uint32_t bits;              // 1: any write, 2: holds the segment head, 4: non-empty
-    unsigned long long start;   // sorted position of the head (valid with bit 2)
-};
-
-struct TileRec {
-    unsigned long long first_seg, last_seg;   // sort keys of the tile's first and last key
-    Agg first;                                // in-tile piece of the segment continuing from the previous tile
-    Agg last;                                 // the tile's last segment piece, when it continues into the next tile
-    uint32_t flags;                           // TR_*
-    uint32_t pad;
-};
-
-enum : uint32_t {
-    TR_STARTS_CONT = 1,   // the tile's first key continues a segment of the previous tile
-    TR_ENDS_CONT = 2,     // the tile's last segment continues into the next tile
-    TR_SINGLE = 4,        // the tile lies inside one segment that crosses both edges
-};
-
-// Everything the kernels of one launch touch.  Device pointers unless noted.
-struct BatchArgs {
-    // device programs of the batch
-    const Insn *insns;
-    const uint64_t *xcode;
-    const ItemDesc *items;
-    const DevProto *protos;
-    const uint64_t *cells;
-    const WarpItem *witems;
-    uint32_t nwitems;
-    uint32_t nprotos;
-    uint32_t has_narrow, has_wide;   // protocols with 32-bit / 64-bit arithmetic present
-    uint64_t ncols;                  // sum of thread counts (per-thread arrays)
-    // per (item, thread)
-    uint32_t *cnt;                   // accesses
-    uint32_t *syn;                   // syncs
-    uint32_t *phs;                   // phase at item start (exclusive scan of syn)
-    unsigned long long *erro;        // (local ordinal << 8) | error code
-    // per (protocol, thread)
-    uint32_t *totsyn;
-    // per warp-item
-    uint32_t *wcnt;
-    unsigned long long *wbase;
-    unsigned long long *blocksum;    // per 4096 warp-items
-    uint32_t nwblocks;
-    // keys
-    unsigned long long *keys[2];
-    uint64_t nkeys;                  // tuples this launch must produce (plan size)
-    unsigned long long *hist;        // [kMaxPasses][kRadixBins]
-    unsigned long long *status;      // [passes][ntiles][kRadixBins] look-back words
-    uint32_t ntiles;
-    uint32_t radix_items;            // keys per thread of a radix tile (12, 16 or 24; 0 = 16)
-    TileRec *trec;                   // [ndtiles] detection tile records
-    uint32_t ndtiles;
-    // per protocol
-    unsigned long long *err_key;     // min (tid << 32 | item) with an evaluation error
-    uint32_t *div_tid;               // min tid whose sync count differs from thread 0's
-    unsigned long long *best_pos;    // min sorted position of a racy segment
-    unsigned long long *ptuples;
-    DevResult *results;
-    Control *ctrl;
-    uint32_t *epoch;                 // persists across launches
-    KeyLayout L;
-    // owner table (the sort-free path): one record per (protocol, phase,
-    // array, index) cell, all zero between launches
-    uint32_t path;                   // PATH_SORT or PATH_TABLE
-    uint32_t rec64;                  // 64-bit records (thread ids above 15 bits)
-    void *table;                     // [tab_cells] records, padded to whole blocks
-    uint64_t tab_cells;
-    uint32_t *touch;                 // one bit per block of kTabBlock records written this launch
-    uint32_t *tlist;                 // [table blocks] the touched blocks, in the order first touched
-    const uint64_t *cbase;           // per (protocol, array): first record of the array in a phase row
-    uint32_t *hit_acc, *hit_wr;      // per (protocol, thread) bit: accessed / wrote the witness cell
-    uint64_t nhit;                   // words of each hit array
-};
-
-enum : uint32_t { PATH_SORT = 0, PATH_TABLE = 1 };
-
-constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 16;
-constexpr int kRadixTile = kRadixThreads * kRadixItems;     // 4096 keys
-constexpr int kDetectThreads = 256;
-constexpr int kDetectItems = 16;
-constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 4096 keys
-constexpr int kFinalizeThreads = 128;
-constexpr int kScanThreads = 256;
-constexpr int kWScanPerBlock = 4096;                        // warp-items per scan block
-constexpr int kTabBlockLog = 8;
-constexpr int kTabBlock = 1 << kTabBlockLog;                // owner-table records per touch bit
-constexpr int kTabScanThreads = 256;
 
 // Keys per thread of a radix tile: a tuning choice among these (0 = 16).
 inline uint32_t radix_items_or_default(uint32_t items) { return items == 12 || items == 24 ? items : 16; }
@@ -108,21 +15,23 @@ inline uint32_t radix_tiles(uint64_t n, uint32_t items = kRadixItems)
     return (uint32_t)((n + tile - 1) / tile);
 }
 inline uint32_t detect_tiles(uint64_t n) { return (uint32_t)((n + kDetectTile - 1) / kDetectTile); }
-// Owner-table blocks and touch-bitmap words for `cells` records.
-#ifdef __CUDACC__
-#define DRF_HOST_DEVICE __host__ __device__
-#else
-#define DRF_HOST_DEVICE
-#endif
-DRF_HOST_DEVICE inline uint64_t table_blocks(uint64_t cells) { return (cells + kTabBlock - 1) / kTabBlock; }
-DRF_HOST_DEVICE inline uint64_t touch_words(uint64_t cells) { return (table_blocks(cells) + 31) / 32; }
+
+// Kernels specialized to one protocol at run time (host/jit.h), launched in
+// place of the interpreter's count, table and witness passes when set; all
+// take (BatchArgs, const uint16_t *item_shape).
+struct JitLaunch {
+    const void *count = nullptr, *table = nullptr, *cell = nullptr;
+    const uint16_t *shape = nullptr;   // device: per item, its code shape
+};
 
 // Stage launchers (all asynchronous on `s`).  Each returns cudaGetLastError().
 // When ev is non-null, an event is recorded before the first kernel of
 // launch_front and after every kernel; *nev counts the events recorded.
-cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev);  // init, count, scan
+cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev,
+                         const JitLaunch *j = nullptr);   // init, count, scan
 // PATH_SORT: emit, radix, detect, finalize.  PATH_TABLE: table, tscan, witness, finalize.
-cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev);
+cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev,
+                        const JitLaunch *j = nullptr);
 
 // Names of the stages whose boundaries launch_front / launch_back record.
 int stage_names(const char **names, int cap, uint32_t passes, uint32_t path);

@@ -15,7 +15,9 @@
 // syncs each item executes gives the phase every item starts in.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 namespace drf {
 

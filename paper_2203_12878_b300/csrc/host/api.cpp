@@ -5,6 +5,7 @@
 #include <new>
 
 #include "engine.h"
+#include "jit.h"
 #include "server.h"
 #include "tune.h"
 
@@ -316,6 +317,36 @@ int drf_check_param_sweep(drf_ctx *ctx, const uint8_t *bytecode, size_t len, con
     return drf_check_batch(ctx, n, bcs.data(), lens.data(), bs.data(), out, stream);
 }
 
+int drf_protocol_specialize(const uint8_t *bytecode, size_t len, const drf_bounds *bounds, int compile,
+                            char **source, char *log, size_t loglen)
+{
+    if (log && loglen) log[0] = 0;
+    if (!source) return DRF_E_INVALID_ARG;
+    *source = nullptr;
+    Prepared p;
+    Error e = prepare_one(bytecode, len, bounds, PrepareOpts{}, p);
+    if (!e.ok()) return e.status;
+    BatchHost bh;
+    e = pack_batch({&p}, bh);
+    if (!e.ok()) return e.status;
+    std::string src, clog;
+    std::vector<uint16_t> shapes;
+    e = jit_source(p, bh, src, shapes);
+    if (!e.ok()) clog = e.message;
+    if (e.ok()) {
+        char *buf = (char *)std::malloc(src.size() + 1);
+        if (!buf) return DRF_E_NOMEM;
+        std::memcpy(buf, src.c_str(), src.size() + 1);
+        *source = buf;
+        if (compile) {
+            std::vector<char> cubin;
+            e = jit_compile(src, cubin, clog);
+        }
+    }
+    if (log && loglen) { std::strncpy(log, clog.c_str(), loglen - 1); log[loglen - 1] = 0; }
+    return e.status;
+}
+
 // ------------------------------------------------------------------- plans
 
 }  // extern "C"
@@ -351,10 +382,37 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
     d.limit = ctx->opts.max_device_bytes;
     d.radix_items = cfg.radix_items;
     d.path_pref = cfg.path ? (int)cfg.path : path_pref_of(ctx->opts);
+    if (cfg.jit) d.path_pref = 2;                  // specialized kernels run the owner-table back end
     e = d.load(plan->host, s);
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
+    if (cfg.jit) {
+        // kernels specialized to the protocol: generate, compile (NVRTC), load
+        std::string src;
+        std::vector<uint16_t> shapes;
+        std::vector<char> cubin;
+        auto mod = std::make_unique<JitModule>();
+        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes)
+                   : Error::make(S_INVALID_ARG, "specialization takes a plan of one protocol");
+        if (e.ok()) e = jit_compile(src, cubin, plan->jit_log);
+        if (e.ok()) e = jit_load(cubin, *mod);
+        if (e.ok() && (!ensure(d.ishape, std::max<size_t>(shapes.size() * 2, 16), &d.in_use, d.limit) ||
+                       cudaMemcpyAsync(d.ishape.p, shapes.data(), shapes.size() * 2, cudaMemcpyHostToDevice, s) !=
+                           cudaSuccess))
+            e = Error::make(S_NOMEM, "device allocation failed");
+        if (!e.ok()) {
+            cudaGetLastError();
+            const std::string why = e.message + (plan->jit_log.empty() ? "" : "\n" + plan->jit_log);
+            delete plan;
+            return fail(ctx, e.status, "specialization: " + why);
+        }
+        plan->jit = std::move(mod);
+        d.jit.count = (const void *)plan->jit->count;
+        d.jit.table = (const void *)plan->jit->table;
+        d.jit.cell = (const void *)plan->jit->cell;
+        d.jit.shape = (const uint16_t *)d.ishape.p;
+    }
     cudaError_t ce;
-    if ((ce = launch_front(d.args, s, ctx->sms, nullptr, nullptr)) != cudaSuccess ||
+    if ((ce = launch_front(d.args, s, ctx->sms, nullptr, nullptr, &d.jit)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(ctx->pinned_ctrl, d.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
         delete plan;
@@ -364,9 +422,10 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
     e = d.choose_path(plan->host, plan->tuples, s);
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
     plan->cfg.path = d.args.path == PATH_TABLE ? 2 : 1;
+    if (cfg.jit && d.args.path != PATH_TABLE) { delete plan; return fail(ctx, DRF_E_LIMIT, "specialization needs the owner table"); }
     d.status_launches++;
     std::vector<DevResult> res(n);
-    if ((ce = launch_back(d.args, s, ctx->sms, nullptr, nullptr)) != cudaSuccess ||
+    if ((ce = launch_back(d.args, s, ctx->sms, nullptr, nullptr, &d.jit)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(res.data(), d.args.results, n * sizeof(DevResult), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
         delete plan;
@@ -391,8 +450,8 @@ double time_plan(drf_plan *plan, int reps)
     for (int r = 0; r < reps; r++) {
         d.status_launches++;
         cudaEventRecord(a, s);
-        launch_front(d.args, s, ctx->sms, nullptr, nullptr);
-        launch_back(d.args, s, ctx->sms, nullptr, nullptr);
+        launch_front(d.args, s, ctx->sms, nullptr, nullptr, &d.jit);
+        launch_back(d.args, s, ctx->sms, nullptr, nullptr, &d.jit);
         cudaEventRecord(b, s);
         if (cudaEventSynchronize(b) != cudaSuccess) { best = 1e30; break; }
         float ms = 0;
@@ -421,8 +480,8 @@ int capture_plan(drf_plan *plan)
     int nev = 0;
     cudaError_t ce;
     if ((ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(ctx, ce);
-    cudaError_t e1 = launch_front(d.args, s, ctx->sms, evp, &nev);
-    cudaError_t e2 = launch_back(d.args, s, ctx->sms, evp, &nev);
+    cudaError_t e1 = launch_front(d.args, s, ctx->sms, evp, &nev, &d.jit);
+    cudaError_t e2 = launch_back(d.args, s, ctx->sms, evp, &nev, &d.jit);
     ce = cudaStreamEndCapture(s, &plan->graph);
     plan->nevents = nev;
     if (e1 != cudaSuccess || e2 != cudaSuccess || ce != cudaSuccess ||
@@ -454,8 +513,20 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     cudaError_t ce = cudaSetDevice(ctx->device);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce);
     drf_plan *plan = nullptr;
-    int st = build_plan(ctx, n, bytecodes, lens, bounds, PlanConfig{}, &plan);
+    PlanConfig first;
+    const bool specialize = (ctx->opts.flags & DRF_OPT_SPECIALIZE) && n == 1 && path_pref_of(ctx->opts) != 1;
+    std::string jit_why;
+    if (specialize && !(ctx->opts.flags & DRF_OPT_AUTOTUNE)) {
+        first.jit = 1;
+        if (build_plan(ctx, n, bytecodes, lens, bounds, first, &plan)) {
+            jit_why = ctx->last_error;        // not specializable here: keep the interpreter
+            first.jit = 0;
+            plan = nullptr;
+        }
+    }
+    int st = plan ? 0 : build_plan(ctx, n, bytecodes, lens, bounds, first, &plan);
     if (st) return st;
+    if (!jit_why.empty()) plan->jit_log = jit_why;
     if (ctx->opts.flags & DRF_OPT_AUTOTUNE) {
         // tune: time every candidate configuration, keep the fastest; a
         // workload signature seen before reuses its choice
@@ -470,11 +541,12 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
             std::vector<PlanConfig> cands;
             for (uint32_t g : kTuneGranularity) {
                 if (pref != 2)
-                    for (uint32_t it : kTuneRadixItems) cands.push_back(PlanConfig{g, it, 1});
-                if (pref != 1 && plan->host.table_ok) cands.push_back(PlanConfig{g, 16, 2});
+                    for (uint32_t it : kTuneRadixItems) cands.push_back(PlanConfig{g, it, 1, 0});
+                if (pref != 1 && plan->host.table_ok) cands.push_back(PlanConfig{g, 16, 2, 0});
+                if (specialize && plan->host.table_ok) cands.push_back(PlanConfig{g, 16, 2, 1});
             }
             for (const PlanConfig &c : cands) {
-                if (c.granularity == plan->cfg.granularity && c.path == plan->cfg.path &&
+                if (c.granularity == plan->cfg.granularity && c.path == plan->cfg.path && c.jit == plan->cfg.jit &&
                     (c.path == 2 || c.radix_items == plan->cfg.radix_items))
                     continue;
                 drf_plan *cand = nullptr;
@@ -486,7 +558,7 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
             tune_store(key, best_cfg, best);
         }
         if (best_cfg.granularity != plan->cfg.granularity || best_cfg.radix_items != plan->cfg.radix_items ||
-            best_cfg.path != plan->cfg.path) {
+            best_cfg.path != plan->cfg.path || best_cfg.jit != plan->cfg.jit) {
             drf_plan_destroy(plan);
             plan = nullptr;
             if ((st = build_plan(ctx, n, bytecodes, lens, bounds, best_cfg, &plan))) return st;
@@ -502,6 +574,17 @@ int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix
     if (!plan) return DRF_E_INVALID_ARG;
     if (granularity) *granularity = plan->cfg.granularity;
     if (radix_items) *radix_items = plan->cfg.radix_items;
+    return DRF_OK;
+}
+
+int drf_plan_specialized(const drf_plan *plan, uint32_t *specialized, char *log, size_t loglen)
+{
+    if (!plan || !specialized) return DRF_E_INVALID_ARG;
+    *specialized = plan->jit ? 1 : 0;
+    if (log && loglen) {
+        std::strncpy(log, plan->jit_log.c_str(), loglen - 1);
+        log[loglen - 1] = 0;
+    }
     return DRF_OK;
 }
 

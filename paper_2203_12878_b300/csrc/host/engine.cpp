@@ -97,8 +97,7 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
     if (out.insns.size() >= (1ull << 31) || out.xcode.size() >= (1ull << 31) || out.items.size() >= (1ull << 31) ||
         ws.size() >= (1ull << 31) || out.lanes >= (1ull << 31))
         return Error::make(S_LIMIT, "batch too large");
-    out.rec64 = L.tid_bits > 15;
-    out.table_ok = table_fits && L.tid_bits <= 31 && out.table_bytes() <= kMaxTableBytes;
+    out.table_ok = table_fits && out.table_bytes() <= kMaxTableBytes;
     if (!out.table_ok) out.table_cells = 0;
     // longest items first, so that the grid-stride loops end together
     std::stable_sort(ws.begin(), ws.end(), [](const W &x, const W &y) { return x.steps > y.steps; });
@@ -111,7 +110,7 @@ DeviceBatch::~DeviceBatch()
 {
     DevBuf *all[] = {&insns, &xcode, &items, &protos, &cells, &witems, &cnt, &syn, &phs, &erro, &totsyn,
                      &wcnt, &wbase, &blocksum, &keys0, &keys1, &hist, &status, &trec, &err_key, &div_tid,
-                     &best_pos, &ptuples, &results, &ctrl, &epoch, &cbase, &table, &touch, &tlist, &hit};
+                     &best_pos, &ptuples, &results, &ctrl, &epoch, &cbase, &table, &touch, &tlist, &hit, &ishape};
     for (DevBuf *b : all) release(*b, &in_use);
 }
 
@@ -198,7 +197,6 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.status = (unsigned long long *)status.p;
     a.cbase = (const uint64_t *)cbase.p;
     a.path = PATH_SORT;
-    a.rec64 = b.rec64 ? 1 : 0;
     a.table = nullptr;
     a.tab_cells = 0;
     a.touch = nullptr;
@@ -211,7 +209,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
 Error DeviceBatch::size_table(const BatchHost &b, uint64_t n, cudaStream_t s)
 {
     const uint64_t recs = table_blocks(b.table_cells) * kTabBlock;
-    const size_t tb = std::max<uint64_t>(recs * (b.rec64 ? 8 : 4), 16);
+    const size_t tb = std::max<uint64_t>(recs * 4, 16);
     const size_t wb = std::max<uint64_t>(touch_words(b.table_cells) * 4, 16);
     const uint64_t nhit = (b.ncols + 31) / 32 + 1;
     void *old_table = table.p, *old_touch = touch.p;
@@ -231,7 +229,6 @@ Error DeviceBatch::size_table(const BatchHost &b, uint64_t n, cudaStream_t s)
     }
     BatchArgs &a = args;
     a.path = PATH_TABLE;
-    a.rec64 = b.rec64 ? 1 : 0;
     a.table = table.p;
     a.tab_cells = b.table_cells;
     a.touch = (uint32_t *)touch.p;
@@ -261,8 +258,7 @@ Error DeviceBatch::choose_path(const BatchHost &b, uint64_t n, cudaStream_t s)
     if (path == PATH_TABLE) {
         Error e = b.table_ok ? size_table(b, n, s)
                              : Error::make(S_LIMIT, "the owner table of this batch would exceed " +
-                                                        std::to_string(kMaxTableBytes >> 30) +
-                                                        " GiB or thread ids exceed 31 bits");
+                                                        std::to_string(kMaxTableBytes >> 30) + " GiB");
         if (e.ok()) return e;
         if (path_pref == 2) return e;
     }

@@ -4,12 +4,14 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../../include/drf.h"
 #include "../cuda/pipeline.cuh"
+#include "jit.h"
 #include "prepare.h"
 #include "tune.h"
 
@@ -39,8 +41,7 @@ struct BatchHost {
     KeyLayout L{};
     uint64_t table_cells = 0;        // owner-table records of the whole batch
     bool table_ok = false;           // the owner-table path can run this batch
-    bool rec64 = false;              // owner records need 64 bits (thread ids above 15 bits)
-    uint64_t table_bytes() const { return table_cells * (rec64 ? 8 : 4); }
+    uint64_t table_bytes() const { return table_cells * 4; }   // one 32-bit owner record per cell
 };
 
 // Largest owner table (bytes) the library sets up for one batch.
@@ -56,7 +57,7 @@ struct DeviceBatch {
     DevBuf cnt, syn, phs, erro, totsyn, wcnt, wbase, blocksum;
     DevBuf keys0, keys1, hist, status, trec;
     DevBuf err_key, div_tid, best_pos, ptuples, results, ctrl, epoch;
-    DevBuf cbase, table, touch, tlist, hit;
+    DevBuf cbase, table, touch, tlist, hit, ishape;
     size_t in_use = 0;
     uint64_t limit = 0;
     uint64_t status_launches = 0;     // launches since the look-back words were cleared
@@ -64,6 +65,7 @@ struct DeviceBatch {
     uint32_t radix_items = 16;                // radix tile shape (tuning choice)
     int path_pref = 0;                        // 0: choose per batch, 1: sort path, 2: owner-table path
     bool table_dirty = false;                 // a failed launch may have left records behind
+    JitLaunch jit{};                          // specialized kernels (plans over one protocol)
     BatchArgs args{};
 
     ~DeviceBatch();
@@ -115,6 +117,8 @@ struct drf_plan {
     int nevents = 0;
     bool profiled = false;
     drf::PlanConfig cfg;
+    std::unique_ptr<drf::JitModule> jit;   // specialized kernels, when the plan uses them
+    std::string jit_log;                   // why specialization was not used, when asked for
 };
 
 namespace drf {

@@ -1,5 +1,5 @@
 // Tuning cache (see tune.h).  File format, one entry per line:
-//   <signature> <granularity> <radix_items> <path> <milliseconds>
+//   <signature> <granularity> <radix_items> <path> <specialized> <milliseconds>
 #include "tune.h"
 
 #include <cstdio>
@@ -35,7 +35,7 @@ void load_locked()
         std::string key, extra;
         PlanConfig c;
         double ms;
-        if ((in >> key >> c.granularity >> c.radix_items >> c.path >> ms) && !(in >> extra)) g_cache[key] = c;
+        if ((in >> key >> c.granularity >> c.radix_items >> c.path >> c.jit >> ms) && !(in >> extra)) g_cache[key] = c;
     }
 }
 
@@ -59,7 +59,7 @@ void tune_store(const std::string &key, const PlanConfig &cfg, double ms)
     const char *path = cache_path();
     if (!path) return;
     if (FILE *f = std::fopen(path, "a")) {
-        std::fprintf(f, "%s %u %u %u %.4f\n", key.c_str(), cfg.granularity, cfg.radix_items, cfg.path, ms);
+        std::fprintf(f, "%s %u %u %u %u %.4f\n", key.c_str(), cfg.granularity, cfg.radix_items, cfg.path, cfg.jit, ms);
         std::fclose(f);
     }
 }

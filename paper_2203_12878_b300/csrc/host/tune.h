@@ -11,6 +11,7 @@ struct PlanConfig {
     uint32_t granularity = 128;   // desired warp-items per SM for the whole batch (item-to-warp schedule)
     uint32_t radix_items = 16;    // keys per thread of a radix tile (12, 16 or 24)
     uint32_t path = 0;            // back end: 0 the context's choice, 1 sort, 2 owner table
+    uint32_t jit = 0;             // 1: kernels specialized to the (single) protocol
 };
 
 // Candidate configurations the tuner times.

@@ -27,6 +27,7 @@ OPT_PROFILE_STAGES = 0x1
 OPT_AUTOTUNE = 0x2
 OPT_PATH_SORT = 0x4      # force the sort back end
 OPT_PATH_TABLE = 0x8     # force the owner-table back end
+OPT_SPECIALIZE = 0x10    # plans over one protocol may compile kernels specialized to it
 PATHS = {1: "sort", 2: "table"}
 
 
@@ -113,6 +114,10 @@ _SIGS = {
                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "drf_plan_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "drf_plan_path": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
+    "drf_plan_specialized": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32), ctypes.c_char_p, ctypes.c_size_t]),
+    "drf_protocol_specialize": (ctypes.c_int, [_U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds),
+                                               ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p,
+                                               ctypes.c_size_t]),
     "drf_plan_destroy": (None, [_P]),
     "drf_server_start": (ctypes.c_int, [_P, ctypes.POINTER(drf_server_opts)]),
     "drf_server_submit": (ctypes.c_int, [_P, _U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds),
@@ -249,6 +254,21 @@ def drf_protocol_analyze(bytecode: bytes, nthreads: int, cells=(), params=()):
     a = drf_analysis()
     st = lib().drf_protocol_analyze(p, n, ctypes.byref(b.c), ctypes.byref(a))
     return STATUS.get(st, st), {f: getattr(a, f) for f, _ in drf_analysis._fields_}
+
+
+def drf_protocol_specialize(bytecode: bytes, nthreads: int, cells=(), params=(), compile: bool = True):
+    """(status name, generated CUDA source or None, compiler log) -- host only;
+    compiling needs NVRTC but no GPU."""
+    _keep, p, n = _bytes(bytecode)
+    b = Bounds(nthreads, cells, params)
+    src = ctypes.c_void_p()
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib().drf_protocol_specialize(p, n, ctypes.byref(b.c), 1 if compile else 0, ctypes.byref(src), log, len(log))
+    text = None
+    if src.value:
+        text = ctypes.string_at(src.value).decode()
+        lib().drf_free(src)
+    return STATUS.get(st, st), text, log.value.decode(errors="replace")
 
 
 def drf_ctx_create(device: int = 0, radix_bits: int = 0, flags: int = 0, max_device_bytes: int = 0):
@@ -395,6 +415,16 @@ def drf_plan_config(plan) -> dict:
     if st != 0:
         raise DrfError(st)
     return {"granularity": g.value, "radix_items": it.value}
+
+
+def drf_plan_specialized(plan):
+    """(whether the plan runs specialized kernels, why not when asked for)."""
+    v = ctypes.c_uint32()
+    log = ctypes.create_string_buffer(4096)
+    st = lib().drf_plan_specialized(plan, ctypes.byref(v), log, len(log))
+    if st != 0:
+        raise DrfError(st)
+    return bool(v.value), log.value.decode(errors="replace")
 
 
 def drf_plan_path(plan) -> str:

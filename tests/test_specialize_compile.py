@@ -1,0 +1,58 @@
+"""Run-time specialization, host side: the generated CUDA source of a
+protocol's count, owner-table and witness kernels compiles with NVRTC for
+sm_103a (no GPU needed), for protocols across the whole syntax."""
+import ctypes.util
+import random
+
+import pytest
+
+from paper_2203_12878_b300 import drf, protogen
+
+
+def _nvrtc():
+    try:
+        ctypes.CDLL("libnvrtc.so.13")
+        return True
+    except OSError:
+        return False
+
+
+pytestmark = pytest.mark.skipif(not _nvrtc(), reason="NVRTC not installed")
+
+
+def _protocols():
+    ps = [protogen.config1("drf"), protogen.config1("nosync"), protogen.config2(0),
+          protogen.config2(3, "constructed", target=3e5, plant=True),
+          protogen.config4_one(random.Random(5), True), protogen.config4_one(random.Random(9), False)]
+    ps += [protogen.random_small(s) for s in range(0, 400, 10)]
+    return ps
+
+
+@pytest.mark.parametrize("i", range(46))
+def test_specialized_source_compiles(i):
+    p = _protocols()[i]
+    bc = drf.drf_protocol_compile(p.text)
+    st, src, log = drf.drf_protocol_specialize(bc, p.nthreads, p.cells, p.params)
+    if st == "LIMIT":            # no owner table (or too many shapes): the plan keeps the interpreter
+        assert src is None
+        return
+    assert st == "OK", log
+    for k in ("drf_count", "drf_table", "drf_cell"):
+        assert f'extern "C" __global__ void __launch_bounds__(256) {k}(' in src
+
+
+def test_wide_protocol_specializes_with_64bit_arithmetic():
+    p = protogen.Protocol("array A;\nwr A[4294967295 + tid];\n", 2, [1 << 33], [])
+    st, src, log = drf.drf_protocol_specialize(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
+    assert st in ("OK", "LIMIT"), log
+    if st == "OK":
+        assert "int64_t v[" in src
+
+
+def test_constants_are_baked_in():
+    """Array sizes and table strides appear as literals in the source."""
+    p = protogen.config1("drf")
+    st, src, _ = drf.drf_protocol_specialize(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params,
+                                             compile=False)
+    assert st == "OK"
+    assert "2048ull" in src      # the array's size bounds every index check

@@ -100,10 +100,16 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+KERNEL_SOURCES = ("paper_2203_12878_b300/csrc/cuda/pipeline.cu", "paper_2203_12878_b300/csrc/cuda/pipeline.cuh",
+                  "paper_2203_12878_b300/csrc/cuda/radix.cuh", "paper_2203_12878_b300/csrc/cuda/owner.cuh",
+                  "paper_2203_12878_b300/csrc/cuda/intmath.cuh", "paper_2203_12878_b300/csrc/batch_args.h",
+                  "paper_2203_12878_b300/csrc/devprog.h", "paper_2203_12878_b300/csrc/host/jit.cpp")
+
+
 def _pipeline_hash():
+    """Hash of every source the device kernels are built or generated from."""
     h = hashlib.sha256()
-    for rel in ("paper_2203_12878_b300/csrc/cuda/pipeline.cu", "paper_2203_12878_b300/csrc/cuda/pipeline.cuh",
-                "paper_2203_12878_b300/csrc/cuda/radix.cuh", "paper_2203_12878_b300/csrc/devprog.h"):
+    for rel in KERNEL_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -192,6 +198,9 @@ def time_steps(plan, steps, warmup, stream, flush, clk_dev=None):
     return [s.elapsed_time(e) for s, e in evs], kinds, clocks, wall
 
 
+TABLE_OPS_PER_TUPLE = 8
+
+
 def roofline(kinds, steps, n, info):
     """Roofline entry of the dominant kernel (largest device time per step)."""
     totals = {k: sum(t for _, t in v) / steps for k, v in kinds.items()}
@@ -209,6 +218,20 @@ def roofline(kinds, steps, n, info):
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                 "traffic": _profiled_traffic(dominant), "launch_ms": round(dom_ms, 4),
                 "algorithmic_bytes_per_launch": bytes_per[dominant]}
+    elif dominant in ("table", "emit", "count", "witness"):
+        # integer interpretation/update kernels: ALU roofline.  Algorithmic
+        # work per access tuple: index update, post-op, phase, range test,
+        # 64-bit record offset (2), record read, saturation test = 8 int ops.
+        # Peak: 148 SMs x 128 INT32 lanes x the maximum SM clock (2032 MHz).
+        ops = TABLE_OPS_PER_TUPLE * n
+        achieved = ops / (dom_ms * 1e-3) / 1e12
+        peak_ops = 148 * 128 * 2.032e9 / 1e12
+        kernel = "drf_table (specialized)" if info.get("specialized") else f"k_interp<{dominant}>"
+        roof = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3), "peak": round(peak_ops, 2),
+                "unit": "Tops/s", "frac": round(achieved / peak_ops, 4),
+                "peak_source": "derived: 148 SMs x 128 INT32 lanes x 2032 MHz",
+                "traffic": _profiled_traffic(dominant), "launch_ms": round(dom_ms, 4),
+                "algorithmic_ops_per_launch": ops}
     else:
         roof = {"bound": "alu", "kernel": f"k_{dominant}", "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None, "launch_ms": round(dom_ms, 4)}
@@ -256,7 +279,7 @@ def run_ours(args, rank, world):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    roof, stages = roofline(kinds, args.steps, n, info)
+    roof, stages = roofline(kinds, args.steps, n, {**info, "specialized": specialized})
 
     # the interpreted back ends on the same protocol, for comparison
     others = []
@@ -436,16 +459,21 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--sources-hash", action="store_true",
+                    help="print the hash of the kernel sources (the key of profiles/ncu_config2_traffic.txt) and exit")
     ap.add_argument("--path", choices=("auto", "sort", "table", "specialized"), default="auto",
                     help="back end of the timed plan: autotuned (specialized kernels allowed), or forced")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--rates", type=float, nargs="*", default=[1000, 5000, 20000, 50000],
                     help="served-workload arrival rates (requests/s)")
     args = ap.parse_args()
+    if args.sources_hash:
+        print(_pipeline_hash())
+        return
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

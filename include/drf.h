@@ -358,7 +358,8 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
  * were cut for (the item-to-warp schedule) and the keys per thread of its
  * radix tiles.  With DRF_OPT_AUTOTUNE, drf_plan_create times every
  * candidate (granularity 32 / 128 / 512 x tile 12 / 16 / 24 keys per
- * thread) on the batch and keeps the fastest; the choice is cached per
+ * thread) on the batch -- each launch after overwriting 256 MiB of scratch,
+ * so that it starts with a cold L2 -- and keeps the fastest; the choice is cached per
  * workload signature for the process and, when the environment variable
  * DRF_TUNE_CACHE names a file, persisted there. */
 int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix_items);

@@ -438,7 +438,10 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
 }
 
 // Best of `reps` direct launches of the whole pipeline, in milliseconds.
-double time_plan(drf_plan *plan, int reps)
+// Before each launch `flush` (when not null) is overwritten, outside the
+// timed events, so that every launch starts with a cold L2 as a check of a
+// new batch does.
+double time_plan(drf_plan *plan, int reps, void *flush, size_t flush_bytes)
 {
     drf_ctx *ctx = plan->ctx;
     cudaStream_t s = ctx->stream;
@@ -449,6 +452,7 @@ double time_plan(drf_plan *plan, int reps)
     double best = 1e30;
     for (int r = 0; r < reps; r++) {
         d.status_launches++;
+        if (flush) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
         cudaEventRecord(a, s);
         launch_front(d.args, s, ctx->sms, nullptr, nullptr, &d.jit);
         launch_back(d.args, s, ctx->sms, nullptr, nullptr, &d.jit);
@@ -533,7 +537,11 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
         const std::string key = signature(ctx, n, plan);
         PlanConfig best_cfg;
         if (!tune_lookup(key, best_cfg)) {
-            double best = time_plan(plan, 3);
+            // scratch larger than L2, overwritten before each timed launch
+            const size_t flush_bytes = 256ull << 20;
+            void *flush = nullptr;
+            if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) { cudaGetLastError(); flush = nullptr; }
+            double best = time_plan(plan, 5, flush, flush_bytes);
             best_cfg = plan->cfg;
             // candidates: the sort path under every granularity and tile
             // shape, the owner table (no radix tiles) under every granularity
@@ -551,10 +559,11 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
                     continue;
                 drf_plan *cand = nullptr;
                 if (build_plan(ctx, n, bytecodes, lens, bounds, c, &cand)) continue;
-                double ms = time_plan(cand, 3);
+                double ms = time_plan(cand, 5, flush, flush_bytes);
                 drf_plan_destroy(cand);
                 if (ms < best) { best = ms; best_cfg = c; }
             }
+            if (flush) cudaFree(flush);
             tune_store(key, best_cfg, best);
         }
         if (best_cfg.granularity != plan->cfg.granularity || best_cfg.radix_items != plan->cfg.radix_items ||

@@ -337,24 +337,65 @@ class Gen {
                 rest[j] = expr(A.c);
                 if (!error.empty()) return false;
             }
-            body_ << "        for (uint64_t t = 0; t < trip; t++) {\n";
+            // index of fast access j at loop value `x` (a C expression)
+            auto idx_of = [&](uint32_t j, const std::string &x) {
+                const Insn &A = p_.insns.at(pc + 1 + j);
+                const uint64_t coef = p_.xcode.at((size_t)A.d), pcon = p_.xcode.at((size_t)A.d + 1);
+                const uint32_t post = (A.a >> 2) & 3;
+                std::string v = cast(u(rest[j]) + " + " + u("(" + ulit(coef) + ")") + " * " + u(x));
+                if (post == FP_MASK) return cast(u(v) + " & " + u("(" + ulit(pcon) + ")"));
+                if (post == FP_MOD)
+                    return std::string("drf::euclid_mod<") + V_ + ", " + U_ + ">(" + v + ", " + cast(lit64((int64_t)pcon)) + ")";
+                if (post == FP_DIV)
+                    return std::string("drf::floor_div<") + V_ + ", " + U_ + ">(" + v + ", " + cast(lit64((int64_t)pcon)) + ")";
+                return v;
+            };
+            std::string tail_start = "0";
+            if (mode_ == GM_TABLE) {
+                // unrolled by UF: all record copies of UF iterations are read
+                // before any update, so the reads overlap (a copy older than an
+                // update of the same cell is still a valid filter: records
+                // only gain bits)
+                const uint32_t UF = m == 1 ? 8 : m == 2 ? 4 : 2;
+                body_ << "        const uint64_t tmain = trip - trip % " << UF << "u;\n";
+                body_ << "        for (uint64_t t = 0; t < tmain; t += " << UF << "u) {\n";
+                for (uint32_t q = 0; q < UF; q++) {
+                    body_ << "        const " << V_ << " x" << q << " = (" << V_ << ")((" << U_ << ")flo + (" << U_
+                          << ")(t + " << q << "u));\n";
+                    body_ << "        const uint32_t p" << q << " = phase + (uint32_t)((t + " << q << "u) * " << spi << "u);\n";
+                    for (uint32_t j = 0; j < m; j++) {
+                        const Insn &A = p_.insns.at(pc + 1 + j);
+                        const std::string sfx = std::to_string(q) + "_" + std::to_string(j);
+                        body_ << "        const " << V_ << " i" << sfx << " = " << idx_of(j, "x" + std::to_string(q)) << ";\n";
+                        body_ << "        const uint32_t h" << sfx << " = p" << q << " + " << (uint32_t)A.e << "u;\n";
+                        body_ << "        const bool k" << sfx << " = h" << sfx << " < " << d_.tab_phases << "u && i" << sfx
+                              << " >= 0 && (uint64_t)(" << U_ << ")i" << sfx << " < " << ulit(p_.cells.at(A.b)) << ";\n";
+                        body_ << "        const unsigned long long o" << sfx << " = k" << sfx << " ? (unsigned long long)h" << sfx
+                              << " * " << ulit(d_.cells_sum) << " + " << ulit(d_.tab_off + cbase_.at(A.b))
+                              << " + (unsigned long long)(" << U_ << ")i" << sfx << " : 0ull;\n";
+                        body_ << "        const uint32_t c" << sfx << " = k" << sfx
+                              << " ? __ldca(reinterpret_cast<const uint32_t *>(a.table) + o" << sfx << ") : 0u;\n";
+                    }
+                }
+                for (uint32_t q = 0; q < UF; q++)
+                    for (uint32_t j = 0; j < m; j++) {
+                        const Insn &A = p_.insns.at(pc + 1 + j);
+                        const std::string sfx = std::to_string(q) + "_" + std::to_string(j);
+                        body_ << "        if (k" << sfx << ") put_cur(a, o" << sfx << ", c" << sfx << ", tid, "
+                              << ((A.a & AF_WRITE) ? 1 : 0) << "u, last_bid);\n"
+                              << "        else atomicOr(&a.ctrl->flags, (unsigned)drf::CF_TABLE_RANGE);\n";
+                    }
+                body_ << "        }\n";
+                tail_start = "tmain";
+            }
+            body_ << "        for (uint64_t t = " << tail_start << "; t < trip; t++) {\n";
             body_ << "        const " << V_ << " x = (" << V_ << ")((" << U_ << ")flo + (" << U_ << ")t);\n";
             body_ << "        const uint32_t ph0 = phase + (uint32_t)(t * " << spi << "u);\n";
             if (mode_ == GM_CELL) body_ << "        if (ph0 > tg.phase) break;\n";
             for (uint32_t j = 0; j < m; j++) {
                 const Insn &A = p_.insns.at(pc + 1 + j);
-                const uint64_t coef = p_.xcode.at((size_t)A.d), pcon = p_.xcode.at((size_t)A.d + 1);
-                const uint32_t post = (A.a >> 2) & 3;
-                std::string v = cast(u(rest[j]) + " + " + u("(" + ulit(coef) + ")") + " * " + u("x"));
-                std::string idx;
-                if (post == FP_MASK) idx = cast(u(v) + " & " + u("(" + ulit(pcon) + ")"));
-                else if (post == FP_MOD)
-                    idx = std::string("drf::euclid_mod<") + V_ + ", " + U_ + ">(" + v + ", " + cast(lit64((int64_t)pcon)) + ")";
-                else if (post == FP_DIV)
-                    idx = std::string("drf::floor_div<") + V_ + ", " + U_ + ">(" + v + ", " + cast(lit64((int64_t)pcon)) + ")";
-                else idx = v;
                 body_ << "        {\n";
-                body_ << "        const " << V_ << " fi = " << idx << ";\n";
+                body_ << "        const " << V_ << " fi = " << idx_of(j, "x") << ";\n";
                 body_ << "        const uint32_t fph = ph0 + " << (uint32_t)A.e << "u;\n";
                 access("fph", A.b, "fi", (A.a & AF_WRITE) != 0);
                 body_ << "        }\n";
@@ -386,19 +427,26 @@ typedef unsigned long long uint64_t;
 const char *kHelpers = R"DRF(
 struct CellTarget { uint32_t phase, loc; unsigned long long idx; };
 
-// Apply an access to its cell's owner record (drf::owner_put reads the L1
-// copy first) and mark the cell's block as touched (same filter).
-static __device__ __forceinline__ void put(const drf::BatchArgs &a, unsigned long long off, uint32_t tid, uint32_t w,
-                                           unsigned long long &last_bid)
+// Apply an access to its cell's owner record given a copy `cur` of it read
+// through L1 (drf::owner_put), and mark the cell's block as touched (the
+// bitmap word is read through L1 first too).
+static __device__ __forceinline__ void put_cur(const drf::BatchArgs &a, unsigned long long off, uint32_t cur,
+                                               uint32_t tid, uint32_t w, unsigned long long &last_bid)
 {
     uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
-    drf::owner_put(cell, __ldca(cell), tid, w);
+    drf::owner_put(cell, cur, tid, w);
     const unsigned long long bid = off >> drf::kTabBlockLog;
     if (bid != last_bid) {
         const uint32_t bit = 1u << (uint32_t)(bid & 31);
         if (!(__ldca(&a.touch[bid >> 5]) & bit)) atomicOr(&a.touch[bid >> 5], bit);
         last_bid = bid;
     }
+}
+
+static __device__ __forceinline__ void put(const drf::BatchArgs &a, unsigned long long off, uint32_t tid, uint32_t w,
+                                           unsigned long long &last_bid)
+{
+    put_cur(a, off, __ldca(reinterpret_cast<const uint32_t *>(a.table) + off), tid, w, last_bid);
 }
 )DRF";
 

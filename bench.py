@@ -46,7 +46,11 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons.  Started before the
+    warm-up so that the sampler runs steadily when the timed region opens;
+    mark() brackets the timed region and summary() keeps the samples inside
+    it (plus the one just before and just after, so that a timed region
+    shorter than the sampling period still has its clock)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -56,6 +60,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.window = None
 
     def __enter__(self):
         try:
@@ -72,6 +77,14 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout=5.0):
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+
+    def mark(self):
+        return len(self.lines)
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -80,10 +93,14 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, window=None):
+        lines = self.lines
+        if window is not None:
+            lo, hi = window
+            lines = lines[max(0, lo - 1):min(len(lines), hi + 1)]
         sm, mx, reasons = [], None, set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in self.lines:
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 7:
                 continue
@@ -158,10 +175,16 @@ def time_oracle(p, min_seconds):
 
 # ------------------------------------------------------------------ ours --
 
-def time_steps(plan, steps, warmup, stream, flush, clk_dev=None):
+WARMUP_MIN_S = 1.5   # the GPU leaves its idle clocks only after some sustained work
+
+
+def time_steps(plan, steps, warmup, stream, flush, clk_dev=None, stages=False):
     """Times `steps` graph launches of `plan` on `stream` (L2 flushed before
-    each, outside the events).  Returns per-step ms, per-stage launch lists
-    {kind: [(name, ms), ...]}, the clock summary and the wall time."""
+    each, outside the events), after at least `warmup` untimed steps and at
+    least WARMUP_MIN_S seconds of them.  Returns per-step ms, per-stage
+    launch lists {kind: [(name, ms), ...]} (when `stages`: the plan's graph
+    then holds an event node between its kernels), the clock summary of the
+    timed region, the wall time and the warm-up actually done (steps, seconds)."""
     import torch
     from paper_2203_12878_b300 import drf
 
@@ -175,27 +198,40 @@ def time_steps(plan, steps, warmup, stream, flush, clk_dev=None):
         if evs is not None:
             evs.append((s, e))
 
-    for _ in range(warmup):
-        step(None)
-    torch.cuda.synchronize()
-    evs, kinds = [], {}
     sampler = ClockSampler(clk_dev) if clk_dev is not None else None
     if sampler:
         sampler.__enter__()
+    w0, done = time.perf_counter(), 0
+    while done < warmup or time.perf_counter() - w0 < WARMUP_MIN_S:
+        for _ in range(8):
+            step(None)
+            done += 1
+        stream.synchronize()
+    if sampler:
+        sampler.wait_first()
+    warm_s = time.perf_counter() - w0
+    torch.cuda.synchronize()
+    evs, kinds = [], {}
+    mark0 = sampler.mark() if sampler else 0
     t0 = time.perf_counter()
     for _ in range(steps):
         step(evs)
-        stream.synchronize()
-        for name, t in drf.drf_plan_stage_times(plan):
-            kind = "radix" if name.startswith("radix") else name
-            kinds.setdefault(kind, []).append((name, t))
+        if stages:
+            stream.synchronize()
+            for name, t in drf.drf_plan_stage_times(plan):
+                kind = "radix" if name.startswith("radix") else name
+                kinds.setdefault(kind, []).append((name, t))
+    stream.synchronize()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clocks = None
     if sampler:
+        if wall < 0.1:
+            time.sleep(0.06)      # let the sample after the region arrive
+        mark1 = sampler.mark()
         sampler.__exit__(None, None, None)
-        clocks = sampler.summary()
-    return [s.elapsed_time(e) for s, e in evs], kinds, clocks, wall
+        clocks = sampler.summary((mark0, mark1))
+    return [s.elapsed_time(e) for s, e in evs], kinds, clocks, wall, (done, warm_s)
 
 
 TABLE_OPS_PER_TUPLE = 8
@@ -238,6 +274,17 @@ def roofline(kinds, steps, n, info):
     return roof, {k: round(v, 4) for k, v in sorted(totals.items())}
 
 
+def hbm_equivalent(tuples_per_s, sort_bits):
+    peak, kind = _peaks()
+    passes = (sort_bits + 7) // 8
+    per_tuple = 8 + 16 * passes + 8
+    return {"peak_gbs": peak, "peak_source": kind,
+            "sort_pipeline_bytes_per_tuple": per_tuple,
+            "sort_pipeline_frac": round(tuples_per_s * per_tuple / 1e9 / peak, 3),
+            "materialize_floor_bytes_per_tuple": 16,
+            "materialize_floor_frac": round(tuples_per_s * 16 / 1e9 / peak, 3)}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2203_12878_b300 import drf
@@ -251,9 +298,8 @@ def run_ours(args, rank, world):
         p = protogen.config2(rank, "literal")
     bc = drf.drf_protocol_compile(p.text)
     bounds = [(p.nthreads, p.cells, p.params)]
-    flags = drf.OPT_PROFILE_STAGES | {"auto": drf.OPT_AUTOTUNE | drf.OPT_SPECIALIZE, "sort": drf.OPT_PATH_SORT,
-                                      "table": drf.OPT_PATH_TABLE,
-                                      "specialized": drf.OPT_PATH_TABLE | drf.OPT_SPECIALIZE}[args.path]
+    flags = {"auto": drf.OPT_AUTOTUNE | drf.OPT_SPECIALIZE, "sort": drf.OPT_PATH_SORT,
+             "table": drf.OPT_PATH_TABLE, "specialized": drf.OPT_PATH_TABLE | drf.OPT_SPECIALIZE}[args.path]
     ctx = drf.drf_ctx_create(dev, flags=flags)
     t_plan = time.perf_counter()
     plan = drf.drf_plan_create(ctx, [bc], bounds)
@@ -271,7 +317,7 @@ def run_ours(args, rank, world):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, kinds, clocks, wall = time_steps(plan, args.steps, args.warmup, stream, flush, clk_dev=dev)
+    step_ms, _, clocks, wall, warm = time_steps(plan, args.steps, args.warmup, stream, flush, clk_dev=dev)
     if world > 1:
         dist.barrier()
     ms = statistics.mean(step_ms)
@@ -279,26 +325,43 @@ def run_ours(args, rank, world):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    roof, stages = roofline(kinds, args.steps, n, {**info, "specialized": specialized})
+    # per-stage times: the same configuration (the tuning cache returns the
+    # timed plan's choice) recorded with an event node between its kernels;
+    # those nodes cost time of their own, so the step above is timed without
+    prof_steps = max(20, min(args.steps, 300))
+    pctx = drf.drf_ctx_create(dev, flags=flags | drf.OPT_PROFILE_STAGES)
+    pplan = drf.drf_plan_create(pctx, [bc], bounds)
+    assert (drf.drf_plan_config(pplan), drf.drf_plan_path(pplan), drf.drf_plan_specialized(pplan)[0]) == \
+        (drf.drf_plan_config(plan), path, specialized)
+    pms, kinds, _, _, _ = time_steps(pplan, prof_steps, 3, stream, flush, stages=True)
+    assert drf.result_dict(drf.drf_plan_results(pplan)[0]) == res
+    drf.drf_plan_destroy(pplan)
+    drf.drf_ctx_destroy(pctx)
+    roof, stages = roofline(kinds, prof_steps, n, {**info, "specialized": specialized})
 
     # the interpreted back ends on the same protocol, for comparison
     others = []
     if rank == 0 and not args.quick and args.path == "auto":
         for oflags in (drf.OPT_PATH_SORT, drf.OPT_PATH_TABLE):
-            octx = drf.drf_ctx_create(dev, flags=drf.OPT_PROFILE_STAGES | oflags)
             try:
+                osteps = max(20, min(args.steps // 5, 300))
+                octx = drf.drf_ctx_create(dev, flags=oflags)
                 oplan = drf.drf_plan_create(octx, [bc], bounds)
-                osteps = max(20, args.steps // 5)
-                oms, okinds, _, _ = time_steps(oplan, osteps, 3, stream, flush)
+                oms, _, _, _, _ = time_steps(oplan, osteps, 3, stream, flush)
                 assert drf.result_dict(drf.drf_plan_results(oplan)[0]) == res
+                drf.drf_plan_destroy(oplan)
+                drf.drf_ctx_destroy(octx)
+                octx = drf.drf_ctx_create(dev, flags=drf.OPT_PROFILE_STAGES | oflags)
+                oplan = drf.drf_plan_create(octx, [bc], bounds)
+                _, okinds, _, _, _ = time_steps(oplan, osteps, 3, stream, flush, stages=True)
                 oroof, ostages = roofline(okinds, osteps, n, drf.drf_plan_info(oplan))
                 others.append({"path": drf.drf_plan_path(oplan), "specialized": False,
                                "ms_per_step": statistics.mean(oms), "value": n / (statistics.mean(oms) * 1e-3),
                                "stages_ms": ostages, "roofline": oroof})
                 drf.drf_plan_destroy(oplan)
+                drf.drf_ctx_destroy(octx)
             except drf.DrfError as e:
                 others.append({"flags": oflags, "unavailable": str(e)})
-            drf.drf_ctx_destroy(octx)
 
     # end to end through the public API: host bytecode in, host result out
     e2e_t = []
@@ -332,7 +395,15 @@ def run_ours(args, rank, world):
                        "l2": "flushed before every step (256 MiB write, outside the timed events)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
+            # the whole step against HBM: the bytes a sort-based check must move
+            # per access tuple (emit 8 + P radix passes x 16 + detect 8, P for
+            # 8-bit digits) and the 16 B/tuple floor of any design that writes
+            # and re-reads one key per access, at this step's tuples/s
+            "hbm_equivalent": hbm_equivalent(n / (ms * 1e-3), info["sort_bits"]),
             "stages_ms": stages,
+            "stages_note": (f"per-stage device times from {prof_steps} further steps of the same configuration "
+                            f"with an event node between kernels (mean {statistics.mean(pms):.4f} ms per step "
+                            f"with those nodes); value and ms_per_step come from the graph without them"),
             "alternatives": others,
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"the same protocol with its first 128 of 1024 threads, "
@@ -343,6 +414,7 @@ def run_ours(args, rank, world):
             "gpu_launches": info["kernels_per_launch"] * args.steps,
             "clocks": clocks,
             "wall_s_timed_region": wall,
+            "warmup_done": {"steps": warm[0], "seconds": round(warm[1], 3)},
         }
         out.update(extra)
     drf.drf_plan_destroy(plan)

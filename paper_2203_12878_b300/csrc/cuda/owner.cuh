@@ -23,28 +23,53 @@ constexpr uint32_t kOwnerWritten = 1u << 31;
 
 __device__ __forceinline__ bool owner_racy(uint32_t r) { return (r & kOwnerMulti) && (r & kOwnerWritten); }
 
-// One access by thread `tid` (w: it writes).  `cur` is a copy of the record
-// read through L1 (it may be stale; the record itself only gains bits).
-__device__ __forceinline__ void owner_put(uint32_t *cell, uint32_t cur, uint32_t tid, uint32_t w)
+// The bits an access by thread `tid` (w: it writes) adds to a non-empty
+// record `cur`: multi-owner when the record's first accessor is another
+// thread, written when it writes.  Zero when `cur` already implies the access.
+__device__ __forceinline__ uint32_t owner_need(uint32_t cur, uint32_t tid, uint32_t w)
 {
-    const uint32_t me = tid + 1;
+    uint32_t need = 0;
+    if (!(cur & kOwnerMulti) && (cur & kOwnerRep) != tid + 1) need |= kOwnerMulti;
+    if (w && !(cur & kOwnerWritten)) need |= kOwnerWritten;
+    return need;
+}
+
+// One access by thread `tid` (w: it writes).  `cur` is a copy of the record
+// read through L1 (it may be stale; the record itself only gains bits).  An
+// empty copy claims the record (first accessor) by compare-and-swap.
+// Returns true when this call turned the record from zero into non-zero.
+__device__ __forceinline__ bool owner_put(uint32_t *cell, uint32_t cur, uint32_t tid, uint32_t w)
+{
     if (cur == 0) {
-        const uint32_t old = atomicCAS(cell, 0u, me | (w << 31));
-        if (old == 0) return;
+        const uint32_t old = atomicCAS(cell, 0u, (tid + 1) | (w << 31));
+        if (old == 0) return true;
         cur = old;
     }
-    uint32_t need = 0;
-    if (!(cur & kOwnerMulti) && (cur & kOwnerRep) != me) need |= kOwnerMulti;
-    if (w && !(cur & kOwnerWritten)) need |= kOwnerWritten;
+    const uint32_t need = owner_need(cur, tid, w);
     if (need) atomicOr(cell, need);
+    return false;
 }
 
 // Accesses of two or more different threads to one cell at once (a warp
-// whose lanes agree on the cell): the cell is multi-owner.
-__device__ __forceinline__ void owner_put_many(uint32_t *cell, uint32_t cur, uint32_t any_write)
+// whose lanes agree on the cell): the cell is multi-owner.  Returns true when
+// the copy was zero (this call may have turned the record non-zero).
+__device__ __forceinline__ bool owner_put_many(uint32_t *cell, uint32_t cur, uint32_t any_write)
 {
     const uint32_t need = kOwnerMulti | (any_write ? kOwnerWritten : 0u);
     if ((cur & need) != need) atomicOr(cell, need);
+    return cur == 0;
+}
+
+// Marks the block of record `off` in the touch bitmap (one bit per
+// 2^block_log records).  A record turns non-zero exactly once per launch,
+// through an update whose copy was zero, and only that update marks its
+// block: every block holding a non-zero record is marked, and the scan that
+// clears the table reads exactly the marked blocks.  A plain reduction:
+// reading the word first would put a dependent load on the claiming path.
+__device__ __forceinline__ void owner_touch(uint32_t *touch, unsigned long long off, int block_log)
+{
+    const unsigned long long bid = off >> block_log;
+    atomicOr(touch + (bid >> 5), 1u << (uint32_t)(bid & 31));
 }
 
 }  // namespace drf

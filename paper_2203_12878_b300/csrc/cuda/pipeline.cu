@@ -186,43 +186,29 @@ enum : int {
     M_CELL = 3,    // which threads access / write one given cell
 };
 
-// Applies each valid lane's access to its owner record (owner.cuh) and marks
-// the record's block as touched.  When every valid lane hits one cell (an
-// index that does not depend on tid), one lane updates the record for the
-// warp.  The record is read through L1 first; the update is skipped when the
-// copy already implies it.  Each lane remembers the last block it marked.
+// Applies each valid lane's access to its owner record (owner.cuh); the
+// update that creates a record marks its block as touched.  When every valid
+// lane hits one cell (an index that does not depend on tid), one lane
+// updates the record for the warp.  The record is read through L1 first; the
+// update is skipped when the copy already implies it.
 __device__ __forceinline__ void table_put(const BatchArgs &a, bool ok, unsigned long long off, uint32_t tid,
-                                          uint32_t w, unsigned long long &last_bid)
+                                          uint32_t w)
 {
     const unsigned m = __ballot_sync(kFull, ok);
     if (m == 0) return;
     const int lead = __ffs(m) - 1;
     const unsigned long long off0 = __shfl_sync(kFull, off, lead);
-    bool mine = ok;
+    uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
+    bool created = false;
     if (__all_sync(kFull, !ok || off == off0)) {
         const unsigned wm = __ballot_sync(kFull, ok && w);
-        mine = (int)(threadIdx.x & 31) == lead;
-        if (mine && __popc(m) >= 2) {
-            uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
-            owner_put_many(cell, __ldca(cell), wm != 0);
-        } else if (mine) {
-            uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
-            owner_put(cell, __ldca(cell), tid, w);
-        }
+        if ((int)(threadIdx.x & 31) == lead)
+            created = __popc(m) >= 2 ? owner_put_many(cell, __ldca(cell), wm != 0)
+                                     : owner_put(cell, __ldca(cell), tid, w);
     } else if (ok) {
-        uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
-        owner_put(cell, __ldca(cell), tid, w);
+        created = owner_put(cell, __ldca(cell), tid, w);
     }
-    if (mine) {
-        // touch bit: a few hot blocks share one bitmap word, so it is read
-        // through L1 first like the record (bits only get set in a launch)
-        const unsigned long long bid = off >> kTabBlockLog;
-        if (bid != last_bid) {
-            const uint32_t bit = 1u << (uint32_t)(bid & 31);
-            if (!(__ldca(&a.touch[bid >> 5]) & bit)) atomicOr(&a.touch[bid >> 5], bit);
-            last_bid = bid;
-        }
-    }
+    if (created) owner_touch(a.touch, off, kTabBlockLog);
 }
 
 // The cell whose accessors the M_CELL pass collects.
@@ -293,7 +279,6 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
     const unsigned long long tidpart = (((unsigned long long)tid) << 1);
     // owner-table state
     const uint64_t *cb = a.cbase + P.cells_off;
-    unsigned long long last_bid = kNone;
     uint32_t hit = 0;                                  // M_CELL: 1 accessed, 2 wrote
 
     while (true) {
@@ -326,7 +311,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                 if (ok && !put) atomicOr(&a.ctrl->flags, CF_TABLE_RANGE);
                 const unsigned long long off =
                     put ? P.tab_off + (uint64_t)phase * P.cells_sum + __ldg(cb + in.b) + (uint64_t)(U)idx : 0ull;
-                table_put(a, put, off, tid, in.a & AF_WRITE, last_bid);
+                table_put(a, put, off, tid, in.a & AF_WRITE);
             } else if (CELL) {
                 if (ok && phase == tg.phase && in.b == tg.loc && (unsigned long long)(U)idx == tg.idx)
                     hit |= 1u | ((in.a & AF_WRITE) << 1);
@@ -438,7 +423,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                                 const unsigned long long off =
                                     put ? P.tab_off + (uint64_t)ph * P.cells_sum + __ldg(cb + loc) + (uint64_t)(U)idx
                                         : 0ull;
-                                table_put(a, put, off, tid, mt & AF_WRITE, last_bid);
+                                table_put(a, put, off, tid, mt & AF_WRITE);
                             } else if (CELL) {
                                 if (act && ph == tg.phase && loc == tg.loc && (unsigned long long)(U)idx == tg.idx)
                                     hit |= 1u | ((mt & AF_WRITE) << 1);

@@ -4,8 +4,10 @@
 #include <dlfcn.h>
 #include <nvrtc.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <set>
 #include <mutex>
 #include <sstream>
 
@@ -52,9 +54,13 @@ class Gen {
   public:
     Gen(const Prepared &p, const DevProto &d, const std::vector<uint64_t> &cbase)
         : p_(p), d_(d), cbase_(cbase), V_(p.wide ? "int64_t" : "int32_t"),
-          U_(p.wide ? "uint64_t" : "uint32_t")
+          U_(p.wide ? "uint64_t" : "uint32_t"),
+          narrow_(d.tab_off + (uint64_t)d.tab_phases * d.cells_sum <= (1ull << 32))
     {
     }
+
+    // Record offsets fit 32 bits when the protocol's rows end below 2^32.
+    bool narrow() const { return narrow_; }
 
     std::string error;
 
@@ -66,14 +72,21 @@ class Gen {
         tmp_ = 0;
         const char *name[] = {"count", "table", "cell"};
         o << "static __device__ __forceinline__ void s" << id << "_" << name[m] << "(";
-        if (m == GM_COUNT) o << "const drf::ItemDesc &it, uint32_t tid, uint32_t &count, uint32_t &syncs, uint32_t &err)";
+        if (m == GM_COUNT) o << "const IJ &it, uint32_t tid, uint32_t &count, uint32_t &syncs, uint32_t &err)";
         if (m == GM_TABLE)
-            o << "const drf::BatchArgs &a, const drf::ItemDesc &it, uint32_t tid, uint32_t phase, "
-                 "unsigned long long &last_bid)";
-        if (m == GM_CELL) o << "const drf::ItemDesc &it, uint32_t tid, uint32_t phase, const CellTarget &tg, uint32_t &hit)";
+            o << "const drf::BatchArgs &a, const IJ &it, uint32_t tid, uint32_t phase)";
+        if (m == GM_CELL) o << "const IJ &it, uint32_t tid, uint32_t phase, const CellTarget &tg, uint32_t &hit)";
         o << "\n{\n";
         o << "    " << V_ << " v[" << kMaxVars << "], h[" << kMaxVars << "];\n";
         o << "    (void)tid; (void)it;\n";
+        if (m == GM_TABLE) o << "    uint32_t *const tab = reinterpret_cast<uint32_t *>(a.table);\n    (void)tab;\n";
+        jump_targets_.clear();
+        for (uint32_t pc = k.start; pc < k.stop && pc < p_.insns.size(); pc++) {
+            const Insn &in = p_.insns[pc];
+            if (in.op == I_LOOP) jump_targets_.insert((uint32_t)in.e + 1);
+            if (in.op == I_ENDLOOP || in.op == I_JUMP) jump_targets_.insert((uint32_t)in.c);
+            if (in.op == I_IF) jump_targets_.insert((uint32_t)in.d);
+        }
         // prologue: the split loops at this item's iterations
         for (uint32_t l = 0; l < k.nsplit; l++) {
             const Insn &L = p_.insns.at(k.split_pc[l]);
@@ -121,11 +134,53 @@ class Gen {
     const DevProto &d_;
     const std::vector<uint64_t> &cbase_;
     const char *V_, *U_;
+    const bool narrow_;
     Mode mode_ = GM_COUNT;
     std::ostringstream body_;
     int tmp_ = 0;
     std::vector<uint32_t> targets_;
     std::map<uint32_t, bool> labels_skip_;
+    std::set<uint32_t> jump_targets_;      // every jump target of the item being generated
+    int slot_ = 0;                         // names of batched-update temporaries
+
+    // One access of a batch of owner-table updates: the access applies when
+    // `k` holds; `o` is its record offset and `c` a copy of its record.
+    struct Slot { std::string k, o, c; bool write, uniform; };
+
+    // The updates of a batch whose record copies are already read
+    // (owner.cuh's rule, split in three rounds so that one warp waits for at
+    // most one round trip of claims): first every claim of a cell whose copy
+    // is empty (compare-and-swap), then the bits the non-empty copies ask
+    // for, then the outcome of the claims -- a won claim marks the cell's
+    // block as touched, a lost one adds the bits the winner's record asks
+    // for.  Accesses whose index does not read tid go through put_warp_cur.
+    void updates(const std::vector<Slot> &S)
+    {
+        std::vector<std::string> n(S.size());
+        for (size_t i = 0; i < S.size(); i++) {
+            if (S[i].uniform) continue;
+            n[i] = "n" + std::to_string(slot_++);
+            body_ << "        uint32_t " << n[i] << " = 1u;\n";
+            body_ << "        if (" << S[i].k << " && " << S[i].c << " == 0u) " << n[i] << " = atomicCAS(tab + " << S[i].o
+                  << ", 0u, (tid + 1u)" << (S[i].write ? " | 0x80000000u" : "") << ");\n";
+        }
+        for (size_t i = 0; i < S.size(); i++) {
+            if (S[i].uniform) continue;
+            body_ << "        if (" << S[i].k << " && " << S[i].c << " != 0u) { const uint32_t nd = drf::owner_need(" << S[i].c
+                  << ", tid, " << (S[i].write ? 1 : 0) << "u); if (nd) atomicOr(tab + " << S[i].o << ", nd); }\n";
+        }
+        for (size_t i = 0; i < S.size(); i++) {
+            if (S[i].uniform) continue;
+            body_ << "        if (" << S[i].k << " && " << S[i].c << " == 0u) { if (" << n[i]
+                  << " == 0u) drf::owner_touch(a.touch, " << S[i].o << ", drf::kTabBlockLog); else { const uint32_t nd = "
+                  << "drf::owner_need(" << n[i] << ", tid, " << (S[i].write ? 1 : 0) << "u); if (nd) atomicOr(tab + "
+                  << S[i].o << ", nd); } }\n";
+        }
+        for (size_t i = 0; i < S.size(); i++)
+            if (S[i].uniform)
+                body_ << "        if (" << S[i].k << ") put_warp_cur(tab, a.touch, " << S[i].o << ", " << S[i].c << ", tid, "
+                      << (S[i].write ? 1 : 0) << "u);\n";
+    }
 
     bool fail(const std::string &m)
     {
@@ -232,20 +287,81 @@ class Gen {
         return "0";
     }
 
-    // The access's effect in the current mode.  `ph`, `idx` are C expressions.
+    // Whether the expression code at `off` reads tid (directly or as an
+    // affine term).  Loop variables do not count: lanes at the same point of
+    // the same iteration agree on them.
+    bool uses_tid(int32_t off) const
+    {
+        size_t i = (size_t)off;
+        for (int guard = 0; guard < 1 << 16 && i < p_.xcode.size(); guard++) {
+            const uint64_t w = p_.xcode[i++];
+            switch ((uint32_t)(w & 0xff)) {
+            case X_RET: return false;
+            case X_TID: return true;
+            case X_CONST: case X_DIVC: case X_MODC: case X_MASK: i++; break;
+            case X_AFF: {
+                const uint32_t n = (uint32_t)(w >> 8);
+                for (uint32_t t = 0; t < n; t++, i += 2)
+                    if ((uint32_t)p_.xcode.at(i) == kAffTid && p_.xcode.at(i + 1) != 0) return true;
+                i++;
+                break;
+            }
+            default: break;
+            }
+        }
+        return true;
+    }
+
+    // Record offset of (phase `ph`, array `loc`, index `idx`) -- C expressions
+    // known to be in range -- in the offset type of the generated source.
+    std::string offset(const std::string &ph, uint32_t loc, const std::string &idx) const
+    {
+        if (narrow_)
+            return "(toff_t)((uint32_t)" + ph + " * " + std::to_string((uint32_t)d_.cells_sum) + "u + " +
+                   std::to_string((uint32_t)(d_.tab_off + cbase_.at(loc))) + "u + (uint32_t)(" + U_ + ")" + idx + ")";
+        return "(toff_t)((unsigned long long)" + ph + " * " + ulit(d_.cells_sum) + " + " +
+               ulit(d_.tab_off + cbase_.at(loc)) + " + (unsigned long long)(" + U_ + ")" + idx + ")";
+    }
+
+    // The access's effect in the witness pass.  `ph`, `idx` are C expressions.
     void access(const std::string &ph, uint32_t loc, const std::string &idx, bool write)
     {
-        if (mode_ == GM_TABLE) {
-            body_ << "        if (" << ph << " < " << d_.tab_phases << "u && " << idx << " >= 0 && (uint64_t)(" << U_
-                  << ")" << idx << " < " << ulit(p_.cells.at(loc)) << ") "
-                  << "put(a, (unsigned long long)" << ph << " * " << ulit(d_.cells_sum) << " + "
-                  << ulit(d_.tab_off + cbase_.at(loc)) << " + (unsigned long long)(" << U_ << ")" << idx << ", tid, "
-                  << (write ? 1 : 0) << "u, last_bid);\n"
-                  << "        else atomicOr(&a.ctrl->flags, (unsigned)drf::CF_TABLE_RANGE);\n";
-        } else if (mode_ == GM_CELL) {
-            body_ << "        if (" << ph << " == tg.phase && tg.loc == " << loc << "u && (unsigned long long)(" << U_
-                  << ")" << idx << " == tg.idx) hit |= " << (write ? 3 : 1) << "u;\n";
+        if (mode_ == GM_CELL)
+            body_ << "        if (" << ph << " == tg.phase && tg.loc == " << loc << "u && (unsigned long long)(" << U_ << ")"
+                  << idx << " == tg.idx) hit |= " << (write ? 3 : 1) << "u;\n";
+    }
+
+    // A run of consecutive accesses (no jump lands inside it) in the table
+    // pass: every index first (an evaluation error ends the thread's item;
+    // the check then reports the error and no verdict, so the run's updates
+    // do not matter), then every record copy, then the batch's updates.
+    bool access_run(const ShapeKey &k, uint32_t pc, uint32_t &next)
+    {
+        uint32_t end = pc + 1;
+        while (end < k.stop && end - pc < 8 && p_.insns.at(end).op == I_ACCESS && !jump_targets_.count(end)) end++;
+        next = end;
+        body_ << "    {\n";
+        std::vector<std::string> idx;
+        for (uint32_t q = pc; q < end; q++) {
+            const Insn &A = p_.insns.at(q);
+            idx.push_back(expr(A.c));
+            if (!error.empty()) return false;
+            body_ << "        if (" << idx.back() << " < 0 || (uint64_t)(" << U_ << ")" << idx.back() << " >= "
+                  << ulit(p_.cells.at(A.b)) << ") goto done;\n";
         }
+        body_ << "        const bool kr = phase < " << d_.tab_phases << "u;\n";
+        body_ << "        if (!kr) atomicOr(&a.ctrl->flags, (unsigned)drf::CF_TABLE_RANGE);\n";
+        std::vector<Slot> S;
+        for (uint32_t q = pc; q < end; q++) {
+            const Insn &A = p_.insns.at(q);
+            const std::string sfx = std::to_string(slot_++);
+            body_ << "        const toff_t o" << sfx << " = kr ? " << offset("phase", A.b, idx[q - pc]) << " : (toff_t)0;\n";
+            body_ << "        const uint32_t c" << sfx << " = kr ? __ldca(tab + o" << sfx << ") : 0u;\n";
+            S.push_back(Slot{"kr", "o" + sfx, "c" + sfx, (A.a & AF_WRITE) != 0, !uses_tid(A.c)});
+        }
+        updates(S);
+        body_ << "    }\n";
+        return true;
     }
 
     bool insn(const ShapeKey &k, uint32_t pc, const Insn &in, uint32_t &next)
@@ -255,6 +371,7 @@ class Gen {
             body_ << "    goto done;\n";
             return true;
         case I_ACCESS: {
+            if (mode_ == GM_TABLE) return access_run(k, pc, next);
             const bool write = (in.a & AF_WRITE) != 0;
             body_ << "    {\n";
             if (mode_ == GM_COUNT && !(in.a & AF_EVAL_IN_COUNT)) {
@@ -350,44 +467,55 @@ class Gen {
                     return std::string("drf::floor_div<") + V_ + ", " + U_ + ">(" + v + ", " + cast(lit64((int64_t)pcon)) + ")";
                 return v;
             };
-            std::string tail_start = "0";
             if (mode_ == GM_TABLE) {
-                // unrolled by UF: all record copies of UF iterations are read
-                // before any update, so the reads overlap (a copy older than an
-                // update of the same cell is still a valid filter: records
-                // only gain bits)
+                // groups of UF iterations: every record copy of a group is
+                // read before any update (a copy older than an update of the
+                // same cell is still a valid filter: records only gain bits),
+                // the last group predicated on the trip count
                 const uint32_t UF = m == 1 ? 8 : m == 2 ? 4 : 2;
-                body_ << "        const uint64_t tmain = trip - trip % " << UF << "u;\n";
-                body_ << "        for (uint64_t t = 0; t < tmain; t += " << UF << "u) {\n";
+                body_ << "        for (uint64_t t = 0; t < trip; t += " << UF << "u) {\n";
+                std::vector<Slot> S;
+                std::vector<std::string> acts, ks;
                 for (uint32_t q = 0; q < UF; q++) {
-                    body_ << "        const " << V_ << " x" << q << " = (" << V_ << ")((" << U_ << ")flo + (" << U_
+                    const std::string qs = std::to_string(q);
+                    body_ << "        const bool a" << qs << " = t + " << q << "u < trip;\n";
+                    body_ << "        const " << V_ << " x" << qs << " = (" << V_ << ")((" << U_ << ")flo + (" << U_
                           << ")(t + " << q << "u));\n";
-                    body_ << "        const uint32_t p" << q << " = phase + (uint32_t)((t + " << q << "u) * " << spi << "u);\n";
+                    body_ << "        const uint32_t p" << qs << " = phase + (uint32_t)((t + " << q << "u) * " << spi << "u);\n";
                     for (uint32_t j = 0; j < m; j++) {
                         const Insn &A = p_.insns.at(pc + 1 + j);
-                        const std::string sfx = std::to_string(q) + "_" + std::to_string(j);
-                        body_ << "        const " << V_ << " i" << sfx << " = " << idx_of(j, "x" + std::to_string(q)) << ";\n";
-                        body_ << "        const uint32_t h" << sfx << " = p" << q << " + " << (uint32_t)A.e << "u;\n";
-                        body_ << "        const bool k" << sfx << " = h" << sfx << " < " << d_.tab_phases << "u && i" << sfx
-                              << " >= 0 && (uint64_t)(" << U_ << ")i" << sfx << " < " << ulit(p_.cells.at(A.b)) << ";\n";
-                        body_ << "        const unsigned long long o" << sfx << " = k" << sfx << " ? (unsigned long long)h" << sfx
-                              << " * " << ulit(d_.cells_sum) << " + " << ulit(d_.tab_off + cbase_.at(A.b))
-                              << " + (unsigned long long)(" << U_ << ")i" << sfx << " : 0ull;\n";
-                        body_ << "        const uint32_t c" << sfx << " = k" << sfx
-                              << " ? __ldca(reinterpret_cast<const uint32_t *>(a.table) + o" << sfx << ") : 0u;\n";
+                        const std::string sfx = qs + "_" + std::to_string(j);
+                        body_ << "        const " << V_ << " i" << sfx << " = " << idx_of(j, "x" + qs) << ";\n";
+                        body_ << "        const uint32_t h" << sfx << " = p" << qs << " + " << (uint32_t)A.e << "u;\n";
+                        // the post-operation may already confine the index to the array
+                        const uint32_t post = (A.a >> 2) & 3;
+                        const int64_t pk = (int64_t)p_.xcode.at((size_t)A.d + 1);
+                        const uint64_t ncell = p_.cells.at(A.b);
+                        const bool in_range = (post == FP_MASK && (uint64_t)pk < ncell) ||
+                                              (post == FP_MOD && pk != 0 && pk != INT64_MIN &&
+                                               (uint64_t)(pk < 0 ? -pk : pk) <= ncell);
+                        body_ << "        const bool k" << sfx << " = a" << qs << " && h" << sfx << " < " << d_.tab_phases << "u";
+                        if (!in_range)
+                            body_ << " && i" << sfx << " >= 0 && (uint64_t)(" << U_ << ")i" << sfx << " < " << ulit(ncell);
+                        body_ << ";\n";
+                        body_ << "        const toff_t o" << sfx << " = k" << sfx << " ? "
+                              << offset("h" + sfx, A.b, "i" + sfx) << " : (toff_t)0;\n";
+                        body_ << "        const uint32_t c" << sfx << " = k" << sfx << " ? __ldca(tab + o" << sfx << ") : 0u;\n";
+                        S.push_back(Slot{"k" + sfx, "o" + sfx, "c" + sfx, (A.a & AF_WRITE) != 0, !uses_tid(A.c)});
+                        acts.push_back("a" + qs);
+                        ks.push_back("k" + sfx);
                     }
                 }
-                for (uint32_t q = 0; q < UF; q++)
-                    for (uint32_t j = 0; j < m; j++) {
-                        const Insn &A = p_.insns.at(pc + 1 + j);
-                        const std::string sfx = std::to_string(q) + "_" + std::to_string(j);
-                        body_ << "        if (k" << sfx << ") put_cur(a, o" << sfx << ", c" << sfx << ", tid, "
-                              << ((A.a & AF_WRITE) ? 1 : 0) << "u, last_bid);\n"
-                              << "        else atomicOr(&a.ctrl->flags, (unsigned)drf::CF_TABLE_RANGE);\n";
-                    }
+                updates(S);
+                for (size_t i = 0; i < ks.size(); i++)
+                    body_ << "        if (" << acts[i] << " && !" << ks[i]
+                          << ") atomicOr(&a.ctrl->flags, (unsigned)drf::CF_TABLE_RANGE);\n";
                 body_ << "        }\n";
-                tail_start = "tmain";
+                if (spi) body_ << "        phase += (uint32_t)(trip * " << spi << "u);\n";
+                body_ << "        }\n    }\n";
+                return true;
             }
+            std::string tail_start = "0";
             body_ << "        for (uint64_t t = " << tail_start << "; t < trip; t++) {\n";
             body_ << "        const " << V_ << " x = (" << V_ << ")((" << U_ << ")flo + (" << U_ << ")t);\n";
             body_ << "        const uint32_t ph0 = phase + (uint32_t)(t * " << spi << "u);\n";
@@ -427,28 +555,42 @@ typedef unsigned long long uint64_t;
 const char *kHelpers = R"DRF(
 struct CellTarget { uint32_t phase, loc; unsigned long long idx; };
 
+// The split-loop positions of one item (its ItemDesc's j and chunk).
+struct IJ { uint32_t j[4]; uint32_t chunk; };
+
 // Apply an access to its cell's owner record given a copy `cur` of it read
-// through L1 (drf::owner_put), and mark the cell's block as touched (the
-// bitmap word is read through L1 first too).
-static __device__ __forceinline__ void put_cur(const drf::BatchArgs &a, unsigned long long off, uint32_t cur,
-                                               uint32_t tid, uint32_t w, unsigned long long &last_bid)
+// through L1 (drf::owner_put); the update that creates the record marks its
+// block as touched.
+static __device__ __forceinline__ void put_cur(uint32_t *table, uint32_t *touch, toff_t off, uint32_t cur, uint32_t tid,
+                                               uint32_t w)
 {
-    uint32_t *cell = reinterpret_cast<uint32_t *>(a.table) + off;
-    drf::owner_put(cell, cur, tid, w);
-    const unsigned long long bid = off >> drf::kTabBlockLog;
-    if (bid != last_bid) {
-        const uint32_t bit = 1u << (uint32_t)(bid & 31);
-        if (!(__ldca(&a.touch[bid >> 5]) & bit)) atomicOr(&a.touch[bid >> 5], bit);
-        last_bid = bid;
+    if (drf::owner_put(table + off, cur, tid, w)) drf::owner_touch(touch, off, drf::kTabBlockLog);
+}
+
+// An access whose index does not read tid: the lanes running together
+// usually hit one cell, and then the lowest of them updates it for all (two
+// or more lanes are two or more threads).  Lanes that disagree update their
+// own cells.
+static __device__ __forceinline__ void put_warp_cur(uint32_t *table, uint32_t *touch, toff_t off, uint32_t cur,
+                                                    uint32_t tid, uint32_t w)
+{
+    const unsigned am = __activemask();
+    const int lead = __ffs(am) - 1;
+    const toff_t off0 = __shfl_sync(am, off, lead);
+    if (__all_sync(am, off == off0)) {
+        if ((int)(threadIdx.x & 31) == lead) {
+            const bool created = __popc(am) >= 2 ? drf::owner_put_many(table + off, cur, w)
+                                                 : drf::owner_put(table + off, cur, tid, w);
+            if (created) drf::owner_touch(touch, off, drf::kTabBlockLog);
+        }
+    } else {
+        put_cur(table, touch, off, cur, tid, w);
     }
 }
 
-static __device__ __forceinline__ void put(const drf::BatchArgs &a, unsigned long long off, uint32_t tid, uint32_t w,
-                                           unsigned long long &last_bid)
-{
-    put_cur(a, off, __ldca(reinterpret_cast<const uint32_t *>(a.table) + off), tid, w, last_bid);
-}
 )DRF";
+
+constexpr size_t kMaxConstItems = 1024;  // items whose schedule and positions are compiled in
 
 }  // namespace
 
@@ -479,8 +621,34 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
     o << kPrelude;
     o << header_text(kJitDevprogH) << header_text(kJitBatchArgsH) << header_text(kJitIntmathCuh)
       << header_text(kJitOwnerCuh);
-    o << kHelpers;
     Gen g(p, d, b.cbase);
+    o << "typedef " << (g.narrow() ? "uint32_t" : "unsigned long long") << " toff_t;   // owner-record offset\n";
+    o << kHelpers;
+
+    // The schedule (warp-item w -> item, thread group) compiled in: items
+    // longest first, the 32-thread groups of one item consecutive, as the
+    // batch's warp-item array holds it; else that array is read.
+    const uint32_t K = (uint32_t)p.items.size(), G = (d.nthreads + 31) / 32;
+    bool csched = K <= kMaxConstItems && K < (1u << 16) && (uint64_t)K * G == b.witems.size();
+    std::vector<uint32_t> order(K);
+    for (uint32_t pos = 0; csched && pos < K; pos++) {
+        order[pos] = b.witems[(size_t)pos * G].k;
+        for (uint32_t gg = 0; gg < G && csched; gg++) {
+            const WarpItem &wi = b.witems[(size_t)pos * G + gg];
+            if (wi.proto != 0 || wi.k != order[pos] || wi.g != gg || wi.k >= K) csched = false;
+        }
+    }
+    if (csched) {
+        o << "__constant__ uint32_t c_ord[" << K << "] = {";   // item | shape << 16, in schedule order
+        for (uint32_t pos = 0; pos < K; pos++) o << (pos ? "," : "") << (order[pos] | ((uint32_t)item_shape[order[pos]] << 16)) << "u";
+        o << "};\n__constant__ IJ c_it[" << K << "] = {";
+        for (uint32_t k = 0; k < K; k++) {
+            const ItemDesc &it = p.items[k];
+            o << (k ? "," : "") << "{{" << it.j[0] << "u," << it.j[1] << "u," << it.j[2] << "u," << it.j[3] << "u},"
+              << it.chunk << "u}";
+        }
+        o << "};\n";
+    }
     const Mode modes[] = {GM_COUNT, GM_TABLE, GM_CELL};
     for (Mode m : modes)
         for (size_t s = 0; s < keys.size(); s++)
@@ -488,7 +656,7 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
                 return Error::make(S_LIMIT, "cannot specialize: " + g.error);
     auto dispatch = [&](const char *call) {
         std::ostringstream c;
-        c << "            switch (shape[P.item_off + wi.k]) {\n";
+        c << "            switch (shp) {\n";
         for (size_t s = 0; s < keys.size(); s++) {
             std::string fn = call;
             fn.replace(fn.find('#'), 1, std::to_string(s));
@@ -497,19 +665,37 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
         c << "            default: break;\n            }\n";
         return c.str();
     };
-    const char *loop_head = R"DRF(    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t warps = gridDim.x * (blockDim.x / 32);
-    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < a.nwitems; w += warps) {
-        const drf::WarpItem wi = a.witems[w];
-        const drf::DevProto P = a.protos[wi.proto];
-        const drf::ItemDesc it = a.items[P.item_off + wi.k];
-        const uint32_t tid = wi.g * 32 + lane;
-        const bool alive = tid < P.nthreads;
-        const uint64_t li = P.lane_off + (uint64_t)wi.k * P.nthreads + tid;
-)DRF";
+    // the loop over warp-items: k (item), g (thread group), shp (its code
+    // shape), it (its split-loop positions), tid, alive, li (its per-(item,
+    // thread) slot); the protocol's descriptor fields are literals
+    const std::string T = std::to_string(d.nthreads) + "u", LANE_OFF = ulit(d.lane_off), TID_OFF = ulit(d.tid_off);
+    std::ostringstream lh;
+    lh << "    const uint32_t lane = threadIdx.x & 31;\n"
+          "    const uint32_t warps = gridDim.x * (blockDim.x / 32);\n";
+    if (csched) {
+        lh << "    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < " << (uint64_t)K * G
+           << "u; w += warps) {\n"
+           << "        const uint32_t pos = w / " << G << "u;\n"
+           << "        const uint32_t ord = c_ord[pos];\n"
+           << "        const uint32_t k = ord & 0xFFFFu, shp = ord >> 16, g = w - pos * " << G << "u;\n"
+           << "        const IJ &it = c_it[k];\n";
+    } else {
+        lh << "    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < a.nwitems; w += warps) {\n"
+           << "        const drf::WarpItem wi = a.witems[w];\n"
+           << "        const uint32_t k = wi.k, g = wi.g, shp = shape[" << d.item_off << "u + k];\n"
+           << "        const drf::ItemDesc &itd = a.items[" << d.item_off << "u + k];\n"
+           << "        IJ it;\n"
+           << "        for (int l = 0; l < 4; l++) it.j[l] = itd.j[l];\n"
+           << "        it.chunk = itd.chunk;\n";
+    }
+    lh << "        const uint32_t tid = g * 32 + lane;\n"
+       << "        const bool alive = tid < " << T << ";\n"
+       << "        const uint64_t li = " << LANE_OFF << " + (uint64_t)k * " << T << " + tid;\n"
+       << "        (void)shp; (void)li;\n";
+    const std::string loop_head = lh.str();
+    const char *sig = "(drf::BatchArgs a, const uint16_t *__restrict__ shape)\n{\n    (void)shape;\n";
     // count pass: the interpreter's M_COUNT outputs
-    o << "extern \"C\" __global__ void __launch_bounds__(256) drf_count(drf::BatchArgs a, const uint16_t *__restrict__ shape)\n{\n"
-      << loop_head
+    o << "extern \"C\" __global__ void __launch_bounds__(256) drf_count" << sig << loop_head
       << "        uint32_t count = 0, syncs = 0, err = 0;\n"
       << "        if (alive) {\n" << dispatch("s#_count(it, tid, count, syncs, err)") << "        }\n"
       << R"DRF(        if (alive) {
@@ -517,7 +703,7 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
             a.syn[li] = syncs;
             if (err) {
                 a.erro[li] = ((unsigned long long)count << 8) | err;
-                atomicMin(&a.err_key[wi.proto], ((unsigned long long)tid << 32) | wi.k);
+                atomicMin(&a.err_key[0], ((unsigned long long)tid << 32) | k);
             }
         }
         const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, count);
@@ -525,40 +711,35 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
             a.wcnt[w] = total;
             if (total) {
                 atomicAdd(&a.blocksum[w / drf::kWScanPerBlock], (unsigned long long)total);
-                atomicAdd(&a.ptuples[wi.proto], (unsigned long long)total);
+                atomicAdd(&a.ptuples[0], (unsigned long long)total);
             }
         }
     }
 }
 )DRF";
     // table pass: owner records, plus the barrier-divergence check
-    o << "extern \"C\" __global__ void __launch_bounds__(256) drf_table(drf::BatchArgs a, const uint16_t *__restrict__ shape)\n{\n"
-      << loop_head
-      << R"DRF(        if (wi.k == 0 && alive && a.totsyn[P.tid_off + tid] != a.totsyn[P.tid_off])
-            atomicMin(&a.div_tid[wi.proto], tid);
-        if (!alive) continue;
-        const uint32_t phase = a.phs[li];
-        unsigned long long last_bid = ~0ull;
-)DRF"
-      << dispatch("s#_table(a, it, tid, phase, last_bid)") << "    }\n}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(256) drf_table" << sig;
+    o << loop_head
+      << "        if (k == 0 && alive && a.totsyn[" << TID_OFF << " + tid] != a.totsyn[" << TID_OFF << "])\n"
+      << "            atomicMin(&a.div_tid[0], tid);\n"
+      << "        if (!alive) continue;\n"
+      << "        const uint32_t phase = a.phs[li];\n";
+    o << dispatch("s#_table(a, it, tid, phase)");
+    o << "    }\n}\n";
     // witness pass: which threads access / write the first racy cell
-    o << "extern \"C\" __global__ void __launch_bounds__(256) drf_cell(drf::BatchArgs a, const uint16_t *__restrict__ shape)\n{\n"
-      << R"DRF(    const unsigned long long bp = a.best_pos[0];
-    if (bp == ~0ull || a.err_key[0] != ~0ull || a.div_tid[0] != 0xFFFFFFFFu) return;
-    CellTarget tg;
-    {
-        const drf::DevProto P0 = a.protos[0];
-        const unsigned long long rel = bp - P0.tab_off;
-        const unsigned long long row = rel / P0.cells_sum;
-        const unsigned long long c = rel - row * P0.cells_sum;
-        const uint64_t *cb = a.cbase + P0.cells_off;
-        uint32_t l = 0;
-        while (l + 1 < P0.nlocs && cb[l + 1] <= c) l++;
-        tg.phase = (uint32_t)row;
-        tg.loc = l;
-        tg.idx = c - cb[l];
-    }
-)DRF"
+    o << "extern \"C\" __global__ void __launch_bounds__(256) drf_cell" << sig
+      << "    const unsigned long long bp = a.best_pos[0];\n"
+      << "    if (bp == ~0ull || a.err_key[0] != ~0ull || a.div_tid[0] != 0xFFFFFFFFu) return;\n"
+      << "    CellTarget tg;\n    {\n"
+      << "        const unsigned long long rel = bp - " << ulit(d.tab_off) << ";\n"
+      << "        const unsigned long long row = rel / " << ulit(d.cells_sum ? d.cells_sum : 1) << ";\n"
+      << "        const unsigned long long c = rel - row * " << ulit(d.cells_sum) << ";\n"
+      << "        uint32_t l = 0;\n";
+    for (uint32_t l = 1; l < d.nlocs; l++) o << "        if (c >= " << ulit(b.cbase.at(l)) << ") l = " << l << "u;\n";
+    o << "        static const unsigned long long cb[" << std::max<uint32_t>(1, d.nlocs) << "] = {";
+    for (uint32_t l = 0; l < std::max<uint32_t>(1, d.nlocs); l++) o << (l ? "," : "") << ulit(l < d.nlocs ? b.cbase.at(l) : 0);
+    o << "};\n"
+      << "        tg.phase = (uint32_t)row;\n        tg.loc = l;\n        tg.idx = c - cb[l];\n    }\n"
       << loop_head
       << R"DRF(        if (!alive) continue;
         const uint32_t phase = a.phs[li];
@@ -566,9 +747,9 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
         uint32_t hit = 0;
 )DRF"
       << dispatch("s#_cell(it, tid, phase, tg, hit)")
-      << R"DRF(        if (hit) {
-            const uint64_t bb = P.tid_off + tid;
-            atomicOr(&a.hit_acc[bb >> 5], 1u << (uint32_t)(bb & 31));
+      << "        if (hit) {\n"
+      << "            const uint64_t bb = " << TID_OFF << " + tid;\n"
+      << R"DRF(            atomicOr(&a.hit_acc[bb >> 5], 1u << (uint32_t)(bb & 31));
             if (hit & 2) atomicOr(&a.hit_wr[bb >> 5], 1u << (uint32_t)(bb & 31));
         }
     }

@@ -365,8 +365,12 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
 int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix_items);
 
 /* Whether a plan runs kernels specialized to its protocol
- * (DRF_OPT_SPECIALIZE); when specialization was asked for but not used,
- * log (may be NULL) receives why. */
+ * (DRF_OPT_SPECIALIZE): *specialized = 0 (no), 1 (yes), or 2 (yes, and the
+ * protocol's sync structure is the same for every thread and no evaluation
+ * can fail, so each item's phase is compiled in and a launch runs neither
+ * the count nor the scan pass; the owner-table pass counts the tuples).
+ * When specialization was asked for but not used, log (may be NULL)
+ * receives why. */
 int drf_plan_specialized(const drf_plan *plan, uint32_t *specialized, char *log, size_t loglen);
 
 /* The back end a plan runs: DRF_PATH_SORT or DRF_PATH_TABLE (see

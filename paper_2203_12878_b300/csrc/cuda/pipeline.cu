@@ -1214,6 +1214,7 @@ cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_
     mark(ev, nev, s);
     k_init<<<(unsigned)((init_n + 255) / 256), 256, 0, s>>>(a);
     mark(ev, nev, s);
+    if (j && j->static_phases) return cudaGetLastError();   // nothing to count or scan
     if (j && j->count) {
         launch_jit(j->count, a, j, s, sms);
     } else {
@@ -1282,13 +1283,14 @@ cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t
     return cudaGetLastError();
 }
 
-int stage_names(const char **names, int cap, uint32_t passes, uint32_t path)
+int stage_names(const char **names, int cap, uint32_t passes, uint32_t path, bool static_phases)
 {
     static const char *radix[kMaxPasses] = {"radix0", "radix1", "radix2", "radix3",
                                             "radix4", "radix5", "radix6", "radix7"};
     const char *all[kMaxStages];
     int n = 0;
-    all[n++] = "init"; all[n++] = "count"; all[n++] = "scan";
+    all[n++] = "init";
+    if (!static_phases) { all[n++] = "count"; all[n++] = "scan"; }
     if (path == PATH_TABLE) {
         all[n++] = "table"; all[n++] = "tscan"; all[n++] = "witness";
     } else {

@@ -22,6 +22,9 @@ inline uint32_t detect_tiles(uint64_t n) { return (uint32_t)((n + kDetectTile - 
 struct JitLaunch {
     const void *count = nullptr, *table = nullptr, *cell = nullptr;
     const uint16_t *shape = nullptr;   // device: per item, its code shape
+    // The kernels take every item's phase as a constant and the table pass
+    // counts the tuples: the count and scan passes are left out.
+    bool static_phases = false;
 };
 
 // Stage launchers (all asynchronous on `s`).  Each returns cudaGetLastError().
@@ -34,7 +37,8 @@ cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t
                         const JitLaunch *j = nullptr);
 
 // Names of the stages whose boundaries launch_front / launch_back record.
-int stage_names(const char **names, int cap, uint32_t passes, uint32_t path);
+// static_phases: the launch leaves the count and scan passes out (JitLaunch).
+int stage_names(const char **names, int cap, uint32_t passes, uint32_t path, bool static_phases = false);
 constexpr int kMaxStages = 4 + kMaxPasses + 2;
 
 }  // namespace drf

@@ -391,8 +391,10 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
         std::vector<uint16_t> shapes;
         std::vector<char> cubin;
         auto mod = std::make_unique<JitModule>();
-        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes)
+        bool stat = false;
+        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes, &stat)
                    : Error::make(S_INVALID_ARG, "specialization takes a plan of one protocol");
+        d.jit.static_phases = stat;
         if (e.ok()) e = jit_compile(src, cubin, plan->jit_log);
         if (e.ok()) e = jit_load(cubin, *mod);
         if (e.ok() && (!ensure(d.ishape, std::max<size_t>(shapes.size() * 2, 16), &d.in_use, d.limit) ||
@@ -412,7 +414,11 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
         d.jit.shape = (const uint16_t *)d.ishape.p;
     }
     cudaError_t ce;
-    if ((ce = launch_front(d.args, s, ctx->sms, nullptr, nullptr, &d.jit)) != cudaSuccess ||
+    // the sizing run counts with the count and scan passes even when the
+    // plan's launches leave them out
+    JitLaunch sizing = d.jit;
+    sizing.static_phases = false;
+    if ((ce = launch_front(d.args, s, ctx->sms, nullptr, nullptr, &sizing)) != cudaSuccess ||
         (ce = cudaMemcpyAsync(ctx->pinned_ctrl, d.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
         delete plan;
@@ -589,7 +595,7 @@ int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix
 int drf_plan_specialized(const drf_plan *plan, uint32_t *specialized, char *log, size_t loglen)
 {
     if (!plan || !specialized) return DRF_E_INVALID_ARG;
-    *specialized = plan->jit ? 1 : 0;
+    *specialized = plan->jit ? (plan->dev.jit.static_phases ? 2 : 1) : 0;
     if (log && loglen) {
         std::strncpy(log, plan->jit_log.c_str(), loglen - 1);
         log[loglen - 1] = 0;
@@ -649,7 +655,8 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
     if (sort_passes) *sort_passes = table ? 0 : plan->host.L.passes;
     if (kernels_per_launch) {
         uint32_t widths = plan->dev.args.has_narrow + plan->dev.args.has_wide;
-        if (table) *kernels_per_launch = 3 * widths + 5;   // init, 3x interp, scan, tlist, tscan, finalize
+        if (table && plan->dev.jit.static_phases) *kernels_per_launch = 6;   // init, table, tlist, tscan, witness, finalize
+        else if (table) *kernels_per_launch = 3 * widths + 5;   // init, 3x interp, scan, tlist, tscan, finalize
         else *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes;   // init, 2x interp, scan, passes, detect, resolve, finalize
     }
     if (sort_bits) *sort_bits = plan->host.L.sort_bits;
@@ -666,7 +673,7 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(plan->ctx, e);
     const char *all[kMaxStages];
-    int nn = stage_names(all, kMaxStages, plan->host.L.passes, plan->dev.args.path);
+    int nn = stage_names(all, kMaxStages, plan->host.L.passes, plan->dev.args.path, plan->dev.jit.static_phases);
     int n = std::min(nn, plan->nevents - 1);
     for (int i = 0; i < n && i < cap; i++) {
         float t = 0;

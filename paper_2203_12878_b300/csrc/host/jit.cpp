@@ -74,7 +74,7 @@ class Gen {
         o << "static __device__ __forceinline__ void s" << id << "_" << name[m] << "(";
         if (m == GM_COUNT) o << "const IJ &it, uint32_t tid, uint32_t &count, uint32_t &syncs, uint32_t &err)";
         if (m == GM_TABLE)
-            o << "const drf::BatchArgs &a, const IJ &it, uint32_t tid, uint32_t phase)";
+            o << "const drf::BatchArgs &a, const IJ &it, uint32_t tid, uint32_t phase, uint32_t &nacc)";
         if (m == GM_CELL) o << "const IJ &it, uint32_t tid, uint32_t phase, const CellTarget &tg, uint32_t &hit)";
         o << "\n{\n";
         o << "    " << V_ << " v[" << kMaxVars << "], h[" << kMaxVars << "];\n";
@@ -349,6 +349,7 @@ class Gen {
             body_ << "        if (" << idx.back() << " < 0 || (uint64_t)(" << U_ << ")" << idx.back() << " >= "
                   << ulit(p_.cells.at(A.b)) << ") goto done;\n";
         }
+        body_ << "        nacc += " << (end - pc) << "u;\n";
         body_ << "        const bool kr = phase < " << d_.tab_phases << "u;\n";
         body_ << "        if (!kr) atomicOr(&a.ctrl->flags, (unsigned)drf::CF_TABLE_RANGE);\n";
         std::vector<Slot> S;
@@ -473,6 +474,7 @@ class Gen {
                 // same cell is still a valid filter: records only gain bits),
                 // the last group predicated on the trip count
                 const uint32_t UF = m == 1 ? 8 : m == 2 ? 4 : 2;
+                body_ << "        nacc += (uint32_t)(trip * " << m << "u);\n";
                 body_ << "        for (uint64_t t = 0; t < trip; t += " << UF << "u) {\n";
                 std::vector<Slot> S;
                 std::vector<std::string> acts, ks;
@@ -555,8 +557,9 @@ typedef unsigned long long uint64_t;
 const char *kHelpers = R"DRF(
 struct CellTarget { uint32_t phase, loc; unsigned long long idx; };
 
-// The split-loop positions of one item (its ItemDesc's j and chunk).
-struct IJ { uint32_t j[4]; uint32_t chunk; };
+// The split-loop positions of one item (its ItemDesc's j and chunk), and
+// with static phases the phases at the item's start and end.
+struct IJ { uint32_t j[4]; uint32_t chunk; uint32_t phase, phase_end; };
 
 // Apply an access to its cell's owner record given a copy `cur` of it read
 // through L1 (drf::owner_put); the update that creates the record marks its
@@ -594,8 +597,10 @@ constexpr size_t kMaxConstItems = 1024;  // items whose schedule and positions a
 
 }  // namespace
 
-Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::vector<uint16_t> &item_shape)
+Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::vector<uint16_t> &item_shape,
+                 bool *static_phases)
 {
+    if (static_phases) *static_phases = false;
     if (b.protos.size() != 1) return Error::make(S_INVALID_ARG, "specialization takes a batch of one protocol");
     if (!b.table_ok) return Error::make(S_LIMIT, "the protocol has no owner table");
     const DevProto &d = b.protos[0];
@@ -638,6 +643,10 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
             if (wi.proto != 0 || wi.k != order[pos] || wi.g != gg || wi.k >= K) csched = false;
         }
     }
+    // static phases (see Prepared): the phase of every item is compiled in,
+    // and the table pass counts the tuples the count pass would have
+    const bool stat = csched && p.static_phases && p.item_phase.size() == K;
+    if (static_phases) *static_phases = stat;
     if (csched) {
         o << "__constant__ uint32_t c_ord[" << K << "] = {";   // item | shape << 16, in schedule order
         for (uint32_t pos = 0; pos < K; pos++) o << (pos ? "," : "") << (order[pos] | ((uint32_t)item_shape[order[pos]] << 16)) << "u";
@@ -645,7 +654,8 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
         for (uint32_t k = 0; k < K; k++) {
             const ItemDesc &it = p.items[k];
             o << (k ? "," : "") << "{{" << it.j[0] << "u," << it.j[1] << "u," << it.j[2] << "u," << it.j[3] << "u},"
-              << it.chunk << "u}";
+              << it.chunk << "u," << (stat ? p.item_phase[k] : 0u) << "u,"
+              << (stat ? (k + 1 < K ? p.item_phase[k + 1] : (uint32_t)p.max_syncs) : 0u) << "u}";
         }
         o << "};\n";
     }
@@ -686,7 +696,9 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
            << "        const drf::ItemDesc &itd = a.items[" << d.item_off << "u + k];\n"
            << "        IJ it;\n"
            << "        for (int l = 0; l < 4; l++) it.j[l] = itd.j[l];\n"
-           << "        it.chunk = itd.chunk;\n";
+           << "        it.chunk = itd.chunk;\n"
+           << "        it.phase = 0;\n"
+           << "        it.phase_end = 0;\n";
     }
     lh << "        const uint32_t tid = g * 32 + lane;\n"
        << "        const bool alive = tid < " << T << ";\n"
@@ -719,13 +731,35 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
 )DRF";
     // table pass: owner records, plus the barrier-divergence check
     o << "extern \"C\" __global__ void __launch_bounds__(256) drf_table" << sig;
-    o << loop_head
-      << "        if (k == 0 && alive && a.totsyn[" << TID_OFF << " + tid] != a.totsyn[" << TID_OFF << "])\n"
-      << "            atomicMin(&a.div_tid[0], tid);\n"
-      << "        if (!alive) continue;\n"
-      << "        const uint32_t phase = a.phs[li];\n";
-    o << dispatch("s#_table(a, it, tid, phase)");
-    o << "    }\n}\n";
+    if (stat) {
+        // phases compiled in; tuples counted here (one shared-memory sum per
+        // block, one global add per block)
+        o << "    __shared__ unsigned long long s_tuples;\n"
+          << "    if (threadIdx.x == 0) s_tuples = 0;\n    __syncthreads();\n"
+          << loop_head
+          << "        uint32_t nacc = 0;\n"
+          << "        if (alive) {\n"
+          << "            const uint32_t phase = it.phase;\n"
+          << dispatch("s#_table(a, it, tid, phase, nacc)")
+          << "        }\n"
+          << "        const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, nacc);\n"
+          << "        if (lane == 0 && tot) atomicAdd(&s_tuples, (unsigned long long)tot);\n"
+          << "    }\n"
+          << "    __syncthreads();\n"
+          << "    if (threadIdx.x == 0 && s_tuples) {\n"
+          << "        atomicAdd(&a.ptuples[0], s_tuples);\n"
+          << "        atomicAdd(&a.ctrl->total, s_tuples);\n"
+          << "    }\n}\n";
+    } else {
+        o << loop_head
+          << "        if (k == 0 && alive && a.totsyn[" << TID_OFF << " + tid] != a.totsyn[" << TID_OFF << "])\n"
+          << "            atomicMin(&a.div_tid[0], tid);\n"
+          << "        if (!alive) continue;\n"
+          << "        const uint32_t phase = a.phs[li];\n"
+          << "        uint32_t nacc = 0;\n"
+          << dispatch("s#_table(a, it, tid, phase, nacc)")
+          << "    }\n}\n";
+    }
     // witness pass: which threads access / write the first racy cell
     o << "extern \"C\" __global__ void __launch_bounds__(256) drf_cell" << sig
       << "    const unsigned long long bp = a.best_pos[0];\n"
@@ -741,10 +775,10 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
     o << "};\n"
       << "        tg.phase = (uint32_t)row;\n        tg.loc = l;\n        tg.idx = c - cb[l];\n    }\n"
       << loop_head
-      << R"DRF(        if (!alive) continue;
-        const uint32_t phase = a.phs[li];
-        if (phase > tg.phase) continue;
-        uint32_t hit = 0;
+      << (stat ? "        if (it.phase > tg.phase || it.phase_end < tg.phase || !alive) continue;\n"
+                 "        const uint32_t phase = it.phase;\n"
+               : "        if (!alive) continue;\n        const uint32_t phase = a.phs[li];\n        if (phase > tg.phase) continue;\n")
+      << R"DRF(        uint32_t hit = 0;
 )DRF"
       << dispatch("s#_cell(it, tid, phase, tg, hit)")
       << "        if (hit) {\n"

@@ -26,8 +26,12 @@ struct BatchHost;
 
 // CUDA source of the specialized kernels of protocol 0 of `b` (a batch of
 // one protocol prepared as `p`); item_shape receives, per item, the index
-// of the code shape its kernels dispatch on.
-Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::vector<uint16_t> &item_shape);
+// of the code shape its kernels dispatch on.  *static_phases (when not null)
+// is set when the kernels take every item's phase as a constant
+// (Prepared::static_phases): the table pass then needs neither the count
+// nor the scan pass, and counts the tuples itself.
+Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::vector<uint16_t> &item_shape,
+                 bool *static_phases = nullptr);
 
 // Compiles `src` for sm_103a with NVRTC.  On failure, `log` holds the
 // compiler's log (or why NVRTC is unavailable).

@@ -63,6 +63,7 @@ public:
 
     bool risk = false;
     bool wide = false;
+    bool maybe_div0 = false;                               // some division's divisor may be zero
     std::unordered_map<const Stmt *, LoopInfo> loops;
     std::unordered_map<const Stmt *, bool> count_eval;   // access -> evaluate index in the count pass
     std::unordered_map<const Expr *, Iv> ranges;
@@ -194,7 +195,7 @@ private:
         case EOp::Max: return Iv{std::max(a.lo, b.lo), std::max(a.hi, b.hi)};
         case EOp::Div:
         case EOp::Mod: {
-            if (b.lo <= 0 && b.hi >= 0) div0 = true;
+            if (b.lo <= 0 && b.hi >= 0) div0 = maybe_div0 = true;
             Iv parts[2] = {Iv{b.lo, std::min(b.hi, (i128)-1)}, Iv{std::max(b.lo, (i128)1), b.hi}};
             Iv r;
             bool any = false;
@@ -516,9 +517,18 @@ struct Splitter {
     int depth = 0;
 
     i128 max_item_tuples = 0;
+    // With a constant sync structure (every forS bound the same for all
+    // threads and iterations), the syncs a thread has executed when an item
+    // starts -- the phase at the item's start -- is the same for every
+    // thread: `phase` tracks it along the traversal, item_phase gets it per
+    // item.  Meaningful only when the caller established that structure.
+    i128 phase = 0;
+    std::vector<uint64_t> item_phase;
 
-    void push_item(uint32_t start, uint32_t stop, uint16_t chunked, uint32_t chunk, i128 steps, i128 tuples)
+    void push_item(uint32_t start, uint32_t stop, uint16_t chunked, uint32_t chunk, i128 steps, i128 tuples,
+                   i128 at_phase)
     {
+        item_phase.push_back((uint64_t)std::min<i128>(std::max<i128>(at_phase, 0), (i128)1 << 62));
         max_item_tuples = std::max(max_item_tuples, tuples);
         ItemDesc d{};
         d.start_pc = start;
@@ -539,20 +549,23 @@ struct Splitter {
         i128 total = 0;
         for (const Stmt *x : xs) total = sat(total + an.work.at(x).steps);
         int32_t run_b = -1, run_e = -1;
-        i128 run_steps = 0, run_tuples = 0;
+        i128 run_steps = 0, run_tuples = 0, run_phase = 0;
         auto flush = [&] {
-            if (run_b >= 0 && run_e > run_b) push_item((uint32_t)run_b, (uint32_t)run_e, 0, 1, run_steps, run_tuples);
+            if (run_b >= 0 && run_e > run_b)
+                push_item((uint32_t)run_b, (uint32_t)run_e, 0, 1, run_steps, run_tuples, run_phase);
             run_b = -1; run_steps = 0; run_tuples = 0;
         };
         for (const Stmt *x : xs) {
             auto r = lw.range.at(x);
+            const i128 x_phase = phase, x_syncs = an.work.at(x).syncs;
+            phase = sat(phase + x_syncs);                            // the phase after x
             if (r.first == r.second) continue;                       // no code (skip)
             i128 steps = an.work.at(x).steps;
             i128 ks = total > 0 ? (budget * steps + total - 1) / total : 1;
             bool loop = x->op == SOp::ForU || x->op == SOp::ForS;
             const LoopInfo *li = loop ? &an.loops.at(x) : nullptr;
             if (!loop || ks < 2 || depth >= kMaxSplit || li->trip_max < 1 || li->trip_max > (i128)UINT32_MAX) {
-                if (run_b < 0) run_b = r.first;
+                if (run_b < 0) { run_b = r.first; run_phase = x_phase; }
                 run_e = r.second;
                 run_steps = sat(run_steps + steps);
                 run_tuples = sat(run_tuples + an.work.at(x).tuples);
@@ -563,6 +576,7 @@ struct Splitter {
             const uint32_t loop_pc = (uint32_t)r.first, end_pc = (uint32_t)r.second;   // ENDLOOP is end_pc - 1
             split_pc[depth] = loop_pc;
             const bool is_fast = lw.fast.count(x) != 0;
+            const i128 body_syncs = an.work.at(x->body.get()).syncs;
             if (ks <= m || depth + 1 >= kMaxSplit || is_fast) {
                 // chunks of iterations (a fast loop starts at its own instruction)
                 i128 parts = std::min(ks, m);
@@ -572,17 +586,21 @@ struct Splitter {
                     split_j[depth] = (uint32_t)c;
                     depth++;
                     push_item(is_fast ? loop_pc : loop_pc + 1, end_pc, is_fast ? 2 : 1, (uint32_t)chunk,
-                              mul_sat(chunk, li->body_steps), mul_sat(chunk, li->body_tuples));
+                              mul_sat(chunk, li->body_steps), mul_sat(chunk, li->body_tuples),
+                              sat(x_phase + mul_sat(mul_sat(c, chunk), body_syncs)));
                     depth--;
                 }
             } else {
                 i128 sub = (ks + m - 1) / m;
+                const i128 after = phase;
                 for (i128 j = 0; j < m; j++) {
                     split_j[depth] = (uint32_t)j;
                     depth++;
+                    phase = sat(x_phase + mul_sat(j, body_syncs));
                     list(*x->body, sub);
                     depth--;
                 }
+                phase = after;
             }
         }
         flush();
@@ -640,12 +658,13 @@ Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, 
     if ((i128)K * nthreads > ((i128)1 << 27)) K = std::max<i128>(1, ((i128)1 << 27) / std::max<uint32_t>(1, nthreads));
 
     std::vector<ItemDesc> items;
-    std::vector<uint64_t> isteps;
+    std::vector<uint64_t> isteps, iphase;
     for (int attempt = 0; attempt < 16; attempt++) {
         items.clear();
         isteps.clear();
         Splitter sp{an, lw, items, isteps};
         sp.list(*p.body, K);
+        iphase = sp.item_phase;
         if (sp.max_item_tuples >= ((i128)1 << 32))
             return Error::make(S_LIMIT, "a work item may make 2^32 accesses or more");
         if (items.size() <= opts.max_items || K <= 1) break;
@@ -655,8 +674,37 @@ Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, 
         ItemDesc d{};
         items.push_back(d);                                    // nothing to run
         isteps.push_back(1);
+        iphase.assign(1, 0);
     }
     if ((i128)items.size() * nthreads > ((i128)1 << 28)) return Error::make(S_LIMIT, "too many work items");
+
+    // Static phases: every forS bound is one value for all threads and
+    // iterations (the analysis's range of each is a single point), so the
+    // sync structure, and with it the phase at each item's start, is the
+    // same for every thread; and no evaluation can fail (every index is
+    // proven in range, no divisor may be zero).  Then the per-thread sync
+    // counts all agree (no barrier divergence) and the count and scan passes
+    // have nothing to add: the specialized kernels take the phases as
+    // constants.
+    bool constant_syncs = true;
+    std::vector<const Stmt *> todo{p.body.get()};
+    while (!todo.empty() && constant_syncs) {
+        const Stmt *t = todo.back();
+        todo.pop_back();
+        if (t->op == SOp::ForS) {
+            const Iv &lo = an.ranges.at(t->lo.get()), &hi = an.ranges.at(t->hi.get());
+            if (lo.empty() || hi.empty() || lo.lo != lo.hi || hi.lo != hi.hi) constant_syncs = false;
+        }
+        for (auto &it : t->items) todo.push_back(it.get());
+        if (t->body) todo.push_back(t->body.get());
+        if (t->then_s) todo.push_back(t->then_s.get());
+        if (t->else_s) todo.push_back(t->else_s.get());
+    }
+    bool may_fail = an.maybe_div0;
+    for (auto &kv : an.count_eval) may_fail = may_fail || kv.second;
+    out.static_phases = constant_syncs && !may_fail && iphase.size() == items.size();
+    for (uint64_t ph : iphase) if (ph > w.syncs) out.static_phases = false;
+    if (out.static_phases) out.item_phase.assign(iphase.begin(), iphase.end());
 
     out.insns = std::move(lw.insns);
     out.xcode = std::move(lw.xcode);

@@ -32,6 +32,10 @@ struct Prepared {
     std::vector<uint64_t> xcode;
     std::vector<ItemDesc> items;
     std::vector<uint64_t> item_steps; // per item, upper bound of steps per lane
+    // Set when every thread runs the same sync structure and no evaluation
+    // can fail; item_phase then holds, per item, the phase at its start.
+    bool static_phases = false;
+    std::vector<uint32_t> item_phase;
 
     uint64_t tuple_bound() const { return (uint64_t)nthreads * max_tuples; }
 };

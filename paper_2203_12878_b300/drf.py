@@ -418,13 +418,14 @@ def drf_plan_config(plan) -> dict:
 
 
 def drf_plan_specialized(plan):
-    """(whether the plan runs specialized kernels, why not when asked for)."""
+    """(0: interpreted, 1: specialized kernels, 2: specialized with static
+    phases -- no count or scan pass; why not specialized when asked for)."""
     v = ctypes.c_uint32()
     log = ctypes.create_string_buffer(4096)
     st = lib().drf_plan_specialized(plan, ctypes.byref(v), log, len(log))
     if st != 0:
         raise DrfError(st)
-    return bool(v.value), log.value.decode(errors="replace")
+    return int(v.value), log.value.decode(errors="replace")
 
 
 def drf_plan_path(plan) -> str:

@@ -46,14 +46,17 @@ def plan_result(ctx, p, launches=2):
 
 
 def check(ctx, oracle, p, need_spec=True):
+    """Compares the plan's result with the oracle's; returns how the plan
+    ran (0 interpreted, 1 specialized, 2 specialized with static phases)."""
     exp = {k: v for k, v in want(oracle, p).items() if k != "message"}
     got, spec = plan_result(ctx, p)
     if exp["status"] != "OK":
         assert got["status"] == exp["status"], (p.text, got, exp)
-        return
+        return spec
     assert got == exp, (p.text, got, exp)
     if need_spec:
         assert spec, p.text
+    return spec
 
 
 def test_paper_examples(sctx, oracle):
@@ -70,11 +73,34 @@ def test_paper_examples(sctx, oracle):
 def test_random_small(sctx, oracle, chunk):
     """Conditionals, thread-dependent bounds, min/max, floor division,
     Euclidean remainder, parameters, syncs, barrier divergence."""
+    kinds = []
     for seed in range(chunk * 40, (chunk + 1) * 40):
         p = protogen.random_small(seed)
         if want(oracle, p)["status"] == "OVERFLOW":
             continue
-        check(sctx, oracle, p, need_spec=False)
+        kinds.append(check(sctx, oracle, p, need_spec=False))
+    # both forms of the specialized kernels are exercised
+    assert kinds.count(2) >= 5 and kinds.count(1) >= 1, kinds
+
+
+def late_phase_race(T, rows, racy_row, writer):
+    """Row x is written in phase x and read (shifted by one thread) in phase
+    x + 1; after the sync of iteration racy_row - 1 (phase racy_row, the
+    phase that row racy_row is written in) thread `writer` also writes cell 1
+    of row racy_row: a race unless the writer is that cell's own thread 1."""
+    text = (f"array A;\nforS x in 0 .. {rows} {{\n  wr A[tid + {T} * x];\n  sync;\n"
+            f"  rd A[(tid + 1) % {T} + {T} * x];\n"
+            f"  if (tid == {writer} && x == {racy_row - 1}) {{ wr A[{T} * {racy_row} + 1]; }}\n}}\n")
+    return protogen.Protocol(text, T, [T * (rows + 1)], [])
+
+
+@pytest.mark.parametrize("T,rows,racy_row,writer", [(8, 6, 3, 5), (64, 9, 8, 0), (96, 4, 1, 1), (40, 7, 6, 39)])
+def test_static_phases_late_race(sctx, oracle, T, rows, racy_row, writer):
+    """Phases compiled into the kernels: a race planted in a late phase is
+    reported with the oracle's phase and threads (writer 1 owns the cell
+    itself in one case: then the protocol is race-free)."""
+    p = late_phase_race(T, rows, racy_row, writer)
+    assert check(sctx, oracle, p) == 2
 
 
 @pytest.mark.parametrize("maker", [
@@ -94,8 +120,10 @@ def test_record_width_boundary(sctx, oracle):
 
 
 def test_config2_full_size(sctx, oracle):
-    """The benchmarked protocol at full size, launch after launch."""
-    check(sctx, oracle, protogen.config2(0))
+    """The benchmarked protocol at full size, launch after launch; its sync
+    structure is the same for every thread, so the plan runs with static
+    phases."""
+    assert check(sctx, oracle, protogen.config2(0)) == 2
 
 
 def test_config3_full_size_racy(sctx, oracle):

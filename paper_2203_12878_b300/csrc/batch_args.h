@@ -86,6 +86,10 @@ struct BatchArgs {
 
 enum : uint32_t { PATH_SORT = 0, PATH_TABLE = 1 };
 
+// BatchArgs::nkeys of a launch whose tuple count is not known in advance
+// (no sizing run); the finalize kernel then skips its count check.
+constexpr unsigned long long kUncounted = ~0ull;
+
 constexpr int kRadixThreads = 256;
 constexpr int kRadixItems = 16;
 constexpr int kRadixTile = kRadixThreads * kRadixItems;     // 4096 keys

@@ -1062,7 +1062,8 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(BatchArgs a)
     const uint32_t p = blockIdx.x;
     const uint32_t t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int parity = TABLE ? 0 : sorted_parity(a);
-    if (p == 0 && t == 0 && a.ctrl->total != a.nkeys) atomicOr(&a.ctrl->flags, CF_COUNT_MISMATCH);
+    if (p == 0 && t == 0 && a.nkeys != kUncounted && a.ctrl->total != a.nkeys)
+        atomicOr(&a.ctrl->flags, CF_COUNT_MISMATCH);
     const DevProto P = a.protos[p];
     const KeyLayout L = a.L;
     DevResult r = {};

@@ -33,6 +33,52 @@ Error prepare_one(const uint8_t *bc, size_t len, const drf_bounds *b, const Prep
     return prepare(bc, len, b->nthreads, b->nlocs, b->loc_cells, b->nparams, b->params, po, out);
 }
 
+// The specialized kernels of one protocol under its bounds, from the
+// context's cache, compiled and loaded on a miss (a protocol that cannot be
+// specialized is remembered as such).  The key is the bytecode and the
+// bounds themselves: the kernels depend on nothing else (the preparation
+// options of drf_check are fixed per context).
+const JitEntry *jit_entry(drf_ctx *ctx, const uint8_t *bc, size_t len, const drf_bounds *b, const Prepared &p,
+                          const BatchHost &bh)
+{
+    std::string key;
+    auto put = [&key](const void *x, size_t n) { key.append((const char *)x, n); };
+    put(&len, sizeof len);
+    put(bc, len);
+    put(&b->nthreads, sizeof b->nthreads);
+    put(&b->nlocs, sizeof b->nlocs);
+    if (b->nlocs) put(b->loc_cells, b->nlocs * sizeof(uint64_t));
+    put(&b->nparams, sizeof b->nparams);
+    if (b->nparams) put(b->params, b->nparams * sizeof(int64_t));
+    auto found = ctx->jit_cache.find(key);
+    if (found != ctx->jit_cache.end()) return found->second.get();
+    if (ctx->jit_cache.size() >= kJitCacheEntries) ctx->jit_cache.clear();
+    auto je = std::make_unique<JitEntry>();
+    std::string src, log;
+    std::vector<uint16_t> shapes;
+    std::vector<char> cubin;
+    bool stat = false;
+    auto mod = std::make_unique<JitModule>();
+    Error e = jit_source(p, bh, src, shapes, &stat);
+    if (e.ok()) e = jit_compile(src, cubin, log);
+    if (e.ok()) e = jit_load(cubin, *mod);
+    if (e.ok() && (cudaMalloc(&je->shape, std::max<size_t>(shapes.size() * 2, 16)) != cudaSuccess ||
+                   cudaMemcpy(je->shape, shapes.data(), shapes.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess))
+        e = Error::make(S_NOMEM, "device allocation failed");
+    cudaGetLastError();
+    if (e.ok()) {
+        je->launch.count = (const void *)mod->count;
+        je->launch.table = (const void *)mod->table;
+        je->launch.cell = (const void *)mod->cell;
+        je->launch.shape = (const uint16_t *)je->shape;
+        je->launch.static_phases = stat;
+        je->mod = std::move(mod);
+    }
+    const JitEntry *out = je.get();
+    ctx->jit_cache[key] = std::move(je);
+    return out;
+}
+
 void error_result(int status, drf_result *out)
 {
     std::memset(out, 0, sizeof *out);
@@ -251,6 +297,23 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
         return DRF_OK;
     }
     std::vector<DevResult> r;
+    // one protocol with DRF_OPT_SPECIALIZE: the kernels compiled for it (the
+    // first check of a protocol under given bounds compiles them), when its
+    // owner table is of a size the automatic choice would take
+    if (valid.size() == 1 && (ctx->opts.flags & DRF_OPT_SPECIALIZE) && path_pref_of(ctx->opts) != 1 && bh.table_ok &&
+        auto_path(bh, bh.tuple_bound) == PATH_TABLE) {
+        const uint32_t i = where[0];
+        const JitEntry *je = jit_entry(ctx, bytecodes[i], lens[i], &bounds[i], *valid[0], bh);
+        if (je && je->mod) {
+            int st = run_batch_jit(ctx, bh, je->launch, s, r);
+            if (st == S_OK) {
+                to_public(r[0], &out[i]);
+                return DRF_OK;
+            }
+            if (st == S_CUDA) return st;
+            ctx->last_error.clear();                // no room for the table: interpret
+        }
+    }
     int st = run_batch(ctx, bh, s, r);
     if (st) return st;
     for (size_t j = 0; j < where.size(); j++) to_public(r[j], &out[where[j]]);

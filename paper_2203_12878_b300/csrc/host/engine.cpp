@@ -54,8 +54,10 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
     L.passes = (L.sort_bits + kRadixBits - 1) / kRadixBits;
     out.L = L;
 
-    struct W { WarpItem wi; uint64_t steps; };
+    // one entry per (protocol, item); its thread groups follow it in order
+    struct W { uint32_t proto, k, groups; uint64_t steps; };
     std::vector<W> ws;
+    uint64_t nwitems = 0;
     bool table_fits = true;
     for (uint32_t i = 0; i < n; i++) {
         const Prepared &p = *ps[i];
@@ -91,18 +93,21 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
         out.ncols += p.nthreads;
         out.tuple_bound += p.tuple_bound();
         uint32_t groups = (p.nthreads + 31) / 32;
-        for (uint32_t k = 0; k < d.nitems; k++)
-            for (uint32_t g = 0; g < groups; g++) ws.push_back(W{WarpItem{i, k, g}, p.item_steps[k]});
+        for (uint32_t k = 0; k < d.nitems; k++) ws.push_back(W{i, k, groups, p.item_steps[k]});
+        nwitems += (uint64_t)d.nitems * groups;
     }
     if (out.insns.size() >= (1ull << 31) || out.xcode.size() >= (1ull << 31) || out.items.size() >= (1ull << 31) ||
-        ws.size() >= (1ull << 31) || out.lanes >= (1ull << 31))
+        nwitems >= (1ull << 31) || out.lanes >= (1ull << 31))
         return Error::make(S_LIMIT, "batch too large");
     out.table_ok = table_fits && out.table_bytes() <= kMaxTableBytes;
     if (!out.table_ok) out.table_cells = 0;
-    // longest items first, so that the grid-stride loops end together
+    // longest items first, so that the grid-stride loops end together (a
+    // stable order: equal items keep protocol and item order, and the
+    // groups of one item stay consecutive)
     std::stable_sort(ws.begin(), ws.end(), [](const W &x, const W &y) { return x.steps > y.steps; });
-    out.witems.reserve(ws.size());
-    for (auto &w : ws) out.witems.push_back(w.wi);
+    out.witems.reserve(nwitems);
+    for (auto &w : ws)
+        for (uint32_t g = 0; g < w.groups; g++) out.witems.push_back(WarpItem{w.proto, w.k, g});
     return Error{};
 }
 
@@ -330,6 +335,41 @@ int run_batch(DeviceBatch &w, Control *pinned, int sms, cudaStream_t s, const Ba
     w.d2h_bytes = 2 * sizeof(Control) + out.size() * sizeof(DevResult);
     int st = flags_status(pinned->flags);
     if (st) err = "device pipeline consistency check failed (flags " + std::to_string(pinned->flags) + ")";
+    return st;
+}
+
+JitEntry::~JitEntry()
+{
+    if (shape) cudaFree(shape);
+}
+
+int run_batch_jit(drf_ctx *ctx, const BatchHost &b, const JitLaunch &j, cudaStream_t s, std::vector<DevResult> &out)
+{
+    DeviceBatch &w = ctx->work;
+    w.limit = ctx->opts.max_device_bytes;
+    w.path_pref = 2;                               // specialized kernels run the owner-table back end
+    Error e = w.load(b, s);
+    if (e.ok()) e = w.choose_path(b, b.tuple_bound, s);
+    if (!e.ok() || w.args.path != PATH_TABLE) {
+        ctx->last_error = e.message;
+        return e.ok() ? S_LIMIT : e.status;
+    }
+    w.args.nkeys = kUncounted;                     // no sizing run: the count is known only afterwards
+    w.status_launches++;
+    out.resize(b.protos.size());
+    Control *pinned = ctx->pinned_ctrl;
+    if (launch_front(w.args, s, ctx->sms, nullptr, nullptr, &j) != cudaSuccess ||
+        launch_back(w.args, s, ctx->sms, nullptr, nullptr, &j) != cudaSuccess ||
+        cudaMemcpyAsync(out.data(), w.args.results, out.size() * sizeof(DevResult), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(pinned, w.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        ctx->last_error = cudaGetErrorString(cudaGetLastError());
+        w.table_dirty = true;
+        return S_CUDA;
+    }
+    w.d2h_bytes = sizeof(Control) + out.size() * sizeof(DevResult);
+    int st = flags_status(pinned->flags);
+    if (st) ctx->last_error = "device pipeline consistency check failed (flags " + std::to_string(pinned->flags) + ")";
     return st;
 }
 

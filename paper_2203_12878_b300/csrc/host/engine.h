@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -86,6 +87,18 @@ struct DeviceBatch {
 // The back end the automatic choice takes for a batch of n tuples.
 uint32_t auto_path(const BatchHost &b, uint64_t n);
 
+// Kernels specialized to one protocol under one set of bounds, kept by a
+// context for its later checks of the same protocol (DRF_OPT_SPECIALIZE).
+struct JitEntry {
+    std::unique_ptr<JitModule> mod;   // null: the protocol could not be specialized
+    JitLaunch launch{};
+    void *shape = nullptr;            // device: per item, its code shape
+    JitEntry() = default;
+    JitEntry(const JitEntry &) = delete;
+    JitEntry &operator=(const JitEntry &) = delete;
+    ~JitEntry();
+};
+
 struct Timing;
 
 }  // namespace drf
@@ -102,6 +115,9 @@ struct drf_ctx {
     drf::Control *pinned_ctrl = nullptr;
     void *server = nullptr;           // drf::Server when running
     std::mutex mu;                    // guards `work` between the caller and the server thread
+    // specialized kernels of protocols checked before, keyed by bytecode and
+    // bounds (DRF_OPT_SPECIALIZE; at most kJitCacheEntries, then cleared)
+    std::map<std::string, std::unique_ptr<drf::JitEntry>> jit_cache;
 };
 
 struct drf_plan {
@@ -129,6 +145,14 @@ namespace drf {
 int run_batch(DeviceBatch &w, Control *pinned, int sms, cudaStream_t s, const BatchHost &b,
               std::vector<DevResult> &out, std::string &err);
 int run_batch(drf_ctx *ctx, const BatchHost &b, cudaStream_t s, std::vector<DevResult> &out);
+
+// One protocol on the context's buffers with kernels specialized to it:
+// the owner-table path, front and back in one go (one wait).  A non-zero
+// return other than a CUDA failure means the caller may run the
+// interpreter instead.
+int run_batch_jit(drf_ctx *ctx, const BatchHost &b, const JitLaunch &j, cudaStream_t s, std::vector<DevResult> &out);
+
+constexpr size_t kJitCacheEntries = 32;
 
 // Back-end preference of a context's options: 0 automatic, 1 sort, 2 owner table.
 int path_pref_of(const drf_opts &o);

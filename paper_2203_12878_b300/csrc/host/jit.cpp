@@ -735,7 +735,11 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
         // phases compiled in; tuples counted here (one shared-memory sum per
         // block, one global add per block)
         o << "    __shared__ unsigned long long s_tuples;\n"
-          << "    if (threadIdx.x == 0) s_tuples = 0;\n    __syncthreads();\n"
+          << "    if (threadIdx.x == 0) s_tuples = 0;\n"
+          // every thread executes the same syncs: thread 0's count, which the
+          // finalize pass reports, is the protocol's static count
+          << "    if (blockIdx.x == 0 && threadIdx.x == 0) a.totsyn[" << TID_OFF << "] = " << (uint32_t)p.max_syncs << "u;\n"
+          << "    __syncthreads();\n"
           << loop_head
           << "        uint32_t nacc = 0;\n"
           << "        if (alive) {\n"

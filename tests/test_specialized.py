@@ -149,3 +149,28 @@ def test_autotuned_specialized_plan(oracle):
         assert got == {k: v for k, v in want(oracle, p).items() if k != "message"}
     finally:
         drf.drf_ctx_destroy(c)
+
+
+def test_drf_check_with_specialized_kernels(oracle):
+    """drf_check on a context with DRF_OPT_SPECIALIZE: the first check of a
+    protocol under its bounds compiles kernels for it and later checks reuse
+    them; results equal the oracle's whether the protocol has static phases,
+    thread-dependent syncs, evaluation errors or barrier divergence, with
+    checks of different protocols interleaved on the context's buffers."""
+    c = drf.drf_ctx_create(0, flags=drf.OPT_SPECIALIZE)
+    try:
+        ps = [protogen.config1("drf"), protogen.config1("nosync"), late_phase_race(64, 9, 8, 0),
+              protogen.config2(1, target=3e5), protogen.config2(2, "constructed", target=3e5, plant=True)]
+        ps += [protogen.random_small(s) for s in range(40)]
+        for rnd in range(2):
+            for p in ps:
+                exp = {k: v for k, v in want(oracle, p).items() if k != "message"}
+                if exp["status"] == "OVERFLOW":
+                    continue
+                got = drf.result_dict(drf.drf_check(c, drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params))
+                if exp["status"] != "OK":
+                    assert got["status"] == exp["status"], (rnd, p.text, got, exp)
+                else:
+                    assert got == exp, (rnd, p.text, got, exp)
+    finally:
+        drf.drf_ctx_destroy(c)

@@ -520,20 +520,103 @@ class Gen {
                 body_ << "        }\n    }\n";
                 return true;
             }
-            std::string tail_start = "0";
-            body_ << "        for (uint64_t t = " << tail_start << "; t < trip; t++) {\n";
-            body_ << "        const " << V_ << " x = (" << V_ << ")((" << U_ << ")flo + (" << U_ << ")t);\n";
-            body_ << "        const uint32_t ph0 = phase + (uint32_t)(t * " << spi << "u);\n";
-            if (mode_ == GM_CELL) body_ << "        if (ph0 > tg.phase) break;\n";
-            for (uint32_t j = 0; j < m; j++) {
+            // witness pass: whether the thread's accesses of the loop hit the
+            // witness cell.  With syncs in the body at most one iteration lies
+            // in the witness phase, and it is evaluated alone.  Without, an
+            // access whose index is (rest + coef * x) mod n (a mask or a
+            // Euclidean remainder, n < 2^31) hits target on the loop's range
+            // iff coef * x == target - rest (mod n) has a solution x there: with
+            // g = gcd(coef mod n, n) that needs g | (target - rest), and the
+            // solutions are x0 + i * (n / g), x0 from the inverse of coef / g
+            // modulo n / g -- constants of the access, computed here.  Other
+            // accesses iterate the loop.
+            std::vector<bool> solved(m, false);
+            for (uint32_t j = 0; j < m && spi == 0; j++) {
                 const Insn &A = p_.insns.at(pc + 1 + j);
-                body_ << "        {\n";
-                body_ << "        const " << V_ << " fi = " << idx_of(j, "x") << ";\n";
-                body_ << "        const uint32_t fph = ph0 + " << (uint32_t)A.e << "u;\n";
-                access("fph", A.b, "fi", (A.a & AF_WRITE) != 0);
+                const uint32_t post = (A.a >> 2) & 3;
+                const int64_t pk = (int64_t)p_.xcode.at((size_t)A.d + 1);
+                const int64_t coef = (int64_t)p_.xcode.at((size_t)A.d);
+                __int128 n = 0;
+                if (post == FP_MASK) n = (__int128)(uint64_t)pk + 1;
+                if (post == FP_MOD && pk != 0 && pk != INT64_MIN) n = pk < 0 ? -(__int128)pk : (__int128)pk;
+                if (n < 2 || n >= ((__int128)1 << 31)) continue;
+                // coef as the lowered arithmetic sees it (the U word, read as V)
+                const __int128 cv = p_.wide ? (__int128)coef : (__int128)(int32_t)(uint32_t)(uint64_t)coef;
+                __int128 ca = cv % n;
+                if (ca < 0) ca += n;
+                __int128 g = ca, r2 = n;
+                while (r2 != 0) { const __int128 t = g % r2; g = r2; r2 = t; }
+                if (ca == 0) g = n;
+                const __int128 mm = n / g;
+                __int128 inv = 0;
+                if (ca != 0 && mm > 1) {                   // (ca / g) * inv == 1 (mod mm), extended Euclid
+                    __int128 r0 = (ca / g) % mm, r1 = mm, s0 = 1, s1 = 0;
+                    while (r1 != 0) {
+                        const __int128 q = r0 / r1;
+                        __int128 t = r0 - q * r1; r0 = r1; r1 = t;
+                        t = s0 - q * s1; s0 = s1; s1 = t;
+                    }
+                    inv = s0 % mm;
+                    if (inv < 0) inv += mm;
+                }
+                const std::string N = ulit((uint64_t)n), G = ulit((uint64_t)g), M = ulit((uint64_t)mm), I = ulit((uint64_t)inv);
+                const char *hitbits = (A.a & AF_WRITE) ? "3u" : "1u";
+                body_ << "        if (phase + " << (uint32_t)A.e << "u == tg.phase && tg.loc == " << A.b << "u && tg.idx < " << N
+                      << ") {\n";
+                if (post == FP_MASK)
+                    body_ << "        const unsigned long long rm = (unsigned long long)(" << U_ << ")" << rest[j] << " & "
+                          << ulit((uint64_t)pk) << ";\n";
+                else
+                    body_ << "        const long long rq = (long long)" << rest[j] << " % (long long)" << N << ";\n"
+                          << "        const unsigned long long rm = rq < 0 ? (unsigned long long)(rq + (long long)" << N
+                          << ") : (unsigned long long)rq;\n";
+                body_ << "        const unsigned long long cc = tg.idx >= rm ? tg.idx - rm : tg.idx + " << N << " - rm;\n";
+                if (ca == 0) {
+                    body_ << "        if (cc == 0) hit |= " << hitbits << ";\n";
+                } else if (mm == 1) {
+                    body_ << "        if (cc % " << G << " == 0) hit |= " << hitbits << ";\n";
+                } else {
+                    body_ << "        if (cc % " << G << " == 0) {\n"
+                          << "        const unsigned long long x0 = (cc / " << G << ") * " << I << " % " << M << ";\n"
+                          << "        const long long lq = (long long)flo % (long long)" << M << ";\n"
+                          << "        const unsigned long long lm = lq < 0 ? (unsigned long long)(lq + (long long)" << M
+                          << ") : (unsigned long long)lq;\n"
+                          << "        if ((x0 >= lm ? x0 - lm : x0 + " << M << " - lm) < trip) hit |= " << hitbits << ";\n"
+                          << "        }\n";
+                }
+                body_ << "        }\n";
+                solved[j] = true;
+            }
+            bool all_solved = true;
+            for (uint32_t j = 0; j < m; j++) all_solved = all_solved && solved[j];
+            if (spi) {
+                for (uint32_t j = 0; j < m; j++) {
+                    const Insn &A = p_.insns.at(pc + 1 + j);
+                    body_ << "        {\n"
+                          << "        const long long dt = (long long)tg.phase - (long long)phase - " << (uint32_t)A.e << "ll;\n"
+                          << "        if (dt >= 0 && dt % " << spi << "ll == 0 && (unsigned long long)(dt / " << spi
+                          << "ll) < trip && tg.loc == " << A.b << "u) {\n"
+                          << "        const " << V_ << " x = (" << V_ << ")((" << U_ << ")flo + (" << U_ << ")(dt / " << spi
+                          << "ll));\n"
+                          << "        const " << V_ << " fi = " << idx_of(j, "x") << ";\n"
+                          << "        if ((unsigned long long)(" << U_ << ")fi == tg.idx) hit |= "
+                          << ((A.a & AF_WRITE) ? "3u" : "1u") << ";\n"
+                          << "        }\n        }\n";
+                }
+            } else if (!all_solved) {
+                body_ << "        if (phase == tg.phase)\n";
+                body_ << "        for (uint64_t t = 0; t < trip; t++) {\n";
+                body_ << "        const " << V_ << " x = (" << V_ << ")((" << U_ << ")flo + (" << U_ << ")t);\n";
+                for (uint32_t j = 0; j < m; j++) {
+                    if (solved[j]) continue;
+                    const Insn &A = p_.insns.at(pc + 1 + j);
+                    body_ << "        {\n";
+                    body_ << "        const " << V_ << " fi = " << idx_of(j, "x") << ";\n";
+                    access("phase", A.b, "fi", (A.a & AF_WRITE) != 0);
+                    body_ << "        }\n";
+                }
                 body_ << "        }\n";
             }
-            body_ << "        }\n";
             if (spi) body_ << "        phase += (uint32_t)(trip * " << spi << "u);\n";
             body_ << "        }\n    }\n";
             if (mode_ == GM_CELL) body_ << "    if (phase > tg.phase) goto done;\n";

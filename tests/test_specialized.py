@@ -174,3 +174,57 @@ def test_drf_check_with_specialized_kernels(oracle):
                     assert got == exp, (rnd, p.text, got, exp)
     finally:
         drf.drf_ctx_destroy(c)
+
+
+def affine_case(seed):
+    """A fast loop whose index takes each post-operation (none, mask,
+    Euclidean remainder with positive or negative modulus, floor division by
+    a positive or negative divisor), some with 64-bit intermediates, some
+    with a sync in the body; most are racy."""
+    r = random.Random(0xAFF1 ^ (seed * 7919))
+    T = r.choice([8, 32, 40, 64])
+    post = seed % 4
+    a, b = r.randint(-3, 3), r.randint(-5, 5)
+    lo = r.randint(0, 4)
+    hi = lo + r.randint(1, 13)
+    syncs = seed % 3 == 2
+    wide = seed % 7 == 3
+    big = 4000000000 if wide else 0
+    if post == 0:
+        c = abs(a) * T + abs(b) * hi + r.randint(0, 9)
+        N = 2 * c + 1
+        idx = f"{a} * tid + {b} * x + {c}"
+    elif post == 1:
+        N = r.choice([16, 64, 256])
+        idx = f"({a} * tid + {b} * x + {r.randint(0, 50) + big}) % {N}"
+    elif post == 2:
+        N = r.choice([12, 48, 100, -36])
+        idx = f"({a} * tid + {b} * x + {r.randint(0, 50) + big}) % {N}"
+        N = abs(N)
+    else:
+        d = r.choice([2, 3, 5, -2, -3])
+        c = abs(a) * T + abs(b) * hi + r.randint(0, 9)
+        idx = f"({a} * tid + {b} * x + {c}) / {d}" if d > 0 else f"({a} * tid + {b} * x - {c}) / {d}"
+        N = 2 * c + 2
+    mode = r.choice(["wr", "rd"])
+    body = f"  {mode} A[{idx}];\n  wr A[{idx}];\n" if r.random() < 0.5 else f"  wr A[{idx}];\n"
+    if syncs:
+        text = f"array A;\nforS x in {lo} .. {hi} {{\n{body}  sync;\n  rd A[({a} * tid + {b} * x + 7) % {N}];\n}}\n"
+    else:
+        text = f"array A;\nforU x in {lo} .. {hi} {{\n{body}}}\n"
+    return text, T, [N]
+
+
+@pytest.mark.parametrize("chunk", range(3))
+def test_witness_hits_solved_per_loop(sctx, oracle, chunk):
+    """The witness pass decides whether a thread's fast loop hits the witness
+    cell by solving the index equation (affine.cuh) rather than iterating:
+    the witness threads (the two smallest accessors of the first racy cell)
+    must be the oracle's."""
+    wide = 0
+    for seed in range(chunk * 16, (chunk + 1) * 16):
+        text, T, cells = affine_case(seed)
+        p = protogen.Protocol(text, T, cells, [])
+        wide += drf.drf_protocol_analyze(drf.drf_protocol_compile(text), T, cells, [])[1]["wide_arithmetic"]
+        assert check(sctx, oracle, p) == 2
+    assert wide >= 1

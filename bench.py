@@ -120,7 +120,8 @@ class ClockSampler:
 KERNEL_SOURCES = ("paper_2203_12878_b300/csrc/cuda/pipeline.cu", "paper_2203_12878_b300/csrc/cuda/pipeline.cuh",
                   "paper_2203_12878_b300/csrc/cuda/radix.cuh", "paper_2203_12878_b300/csrc/cuda/owner.cuh",
                   "paper_2203_12878_b300/csrc/cuda/intmath.cuh", "paper_2203_12878_b300/csrc/batch_args.h",
-                  "paper_2203_12878_b300/csrc/devprog.h", "paper_2203_12878_b300/csrc/host/jit.cpp")
+                  "paper_2203_12878_b300/csrc/devprog.h", "paper_2203_12878_b300/csrc/host/jit.cpp",
+                  "paper_2203_12878_b300/csrc/host/prepare.cpp")
 
 
 def _pipeline_hash():
@@ -175,10 +176,10 @@ def time_oracle(p, min_seconds):
 
 # ------------------------------------------------------------------ ours --
 
-WARMUP_MIN_S = 1.5   # the GPU leaves its idle clocks only after some sustained work
+WARMUP_MIN_S = 1.5   # default: the GPU leaves its idle clocks only after some sustained work
 
 
-def time_steps(plan, steps, warmup, stream, flush, clk_dev=None, stages=False):
+def time_steps(plan, steps, warmup, stream, flush, clk_dev=None, stages=False, warm_s=None):
     """Times `steps` graph launches of `plan` on `stream` (L2 flushed before
     each, outside the events), after at least `warmup` untimed steps and at
     least WARMUP_MIN_S seconds of them.  Returns per-step ms, per-stage
@@ -201,8 +202,9 @@ def time_steps(plan, steps, warmup, stream, flush, clk_dev=None, stages=False):
     sampler = ClockSampler(clk_dev) if clk_dev is not None else None
     if sampler:
         sampler.__enter__()
+    warm_s = WARMUP_MIN_S if warm_s is None else warm_s
     w0, done = time.perf_counter(), 0
-    while done < warmup or time.perf_counter() - w0 < WARMUP_MIN_S:
+    while done < warmup or time.perf_counter() - w0 < warm_s:
         for _ in range(8):
             step(None)
             done += 1
@@ -317,7 +319,8 @@ def run_ours(args, rank, world):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, _, clocks, wall, warm = time_steps(plan, args.steps, args.warmup, stream, flush, clk_dev=dev)
+    step_ms, _, clocks, wall, warm = time_steps(plan, args.steps, args.warmup, stream, flush, clk_dev=dev,
+                                                warm_s=args.warmup_seconds)
     if world > 1:
         dist.barrier()
     ms = statistics.mean(step_ms)
@@ -333,7 +336,7 @@ def run_ours(args, rank, world):
     pplan = drf.drf_plan_create(pctx, [bc], bounds)
     assert (drf.drf_plan_config(pplan), drf.drf_plan_path(pplan), drf.drf_plan_specialized(pplan)[0]) == \
         (drf.drf_plan_config(plan), path, specialized)
-    pms, kinds, _, _, _ = time_steps(pplan, prof_steps, 3, stream, flush, stages=True)
+    pms, kinds, _, _, _ = time_steps(pplan, prof_steps, 3, stream, flush, stages=True, warm_s=args.warmup_seconds)
     assert drf.result_dict(drf.drf_plan_results(pplan)[0]) == res
     drf.drf_plan_destroy(pplan)
     drf.drf_ctx_destroy(pctx)
@@ -347,13 +350,13 @@ def run_ours(args, rank, world):
                 osteps = max(20, min(args.steps // 5, 300))
                 octx = drf.drf_ctx_create(dev, flags=oflags)
                 oplan = drf.drf_plan_create(octx, [bc], bounds)
-                oms, _, _, _, _ = time_steps(oplan, osteps, 3, stream, flush)
+                oms, _, _, _, _ = time_steps(oplan, osteps, 3, stream, flush, warm_s=args.warmup_seconds)
                 assert drf.result_dict(drf.drf_plan_results(oplan)[0]) == res
                 drf.drf_plan_destroy(oplan)
                 drf.drf_ctx_destroy(octx)
                 octx = drf.drf_ctx_create(dev, flags=drf.OPT_PROFILE_STAGES | oflags)
                 oplan = drf.drf_plan_create(octx, [bc], bounds)
-                _, okinds, _, _, _ = time_steps(oplan, osteps, 3, stream, flush, stages=True)
+                _, okinds, _, _, _ = time_steps(oplan, osteps, 3, stream, flush, stages=True, warm_s=args.warmup_seconds)
                 oroof, ostages = roofline(okinds, osteps, n, drf.drf_plan_info(oplan))
                 others.append({"path": drf.drf_plan_path(oplan), "specialized": False,
                                "ms_per_step": statistics.mean(oms), "value": n / (statistics.mean(oms) * 1e-3),
@@ -550,6 +553,8 @@ def main():
     ap.add_argument("--path", choices=("auto", "sort", "table", "specialized"), default="auto",
                     help="back end of the timed plan: autotuned (specialized kernels allowed), or forced")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--warmup-seconds", type=float, default=WARMUP_MIN_S,
+                    help="least wall time of untimed steps before each timed region (besides --warmup steps)")
     ap.add_argument("--rates", type=float, nargs="*", default=[1000, 5000, 20000, 50000],
                     help="served-workload arrival rates (requests/s)")
     args = ap.parse_args()

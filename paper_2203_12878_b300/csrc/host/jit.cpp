@@ -645,7 +645,7 @@ struct CellTarget { uint32_t phase, loc; unsigned long long idx; };
 
 // The split-loop positions of one item (its ItemDesc's j and chunk), and
 // with static phases the phases at the item's start and end.
-struct IJ { uint32_t j[4]; uint32_t chunk; uint32_t phase, phase_end; };
+struct __align__(16) IJ { uint32_t j[4]; uint32_t chunk, phase, phase_end, pad; };
 
 // Apply an access to its cell's owner record given a copy `cur` of it read
 // through L1 (drf::owner_put); the update that creates the record marks its
@@ -734,14 +734,17 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
     const bool stat = csched && p.static_phases && p.item_phase.size() == K;
     if (static_phases) *static_phases = stat;
     if (csched) {
-        o << "__constant__ uint32_t c_ord[" << K << "] = {";   // item | shape << 16, in schedule order
+        // read-only global data, not __constant__: warps index it by their
+        // work item, and a per-item table of kilobytes outgrows the constant
+        // cache while L1 keeps it after the first reads
+        o << "static __device__ const uint32_t c_ord[" << K << "] = {";   // item | shape << 16, in schedule order
         for (uint32_t pos = 0; pos < K; pos++) o << (pos ? "," : "") << (order[pos] | ((uint32_t)item_shape[order[pos]] << 16)) << "u";
-        o << "};\n__constant__ IJ c_it[" << K << "] = {";
+        o << "};\nstatic __device__ const IJ c_it[" << K << "] = {";
         for (uint32_t k = 0; k < K; k++) {
             const ItemDesc &it = p.items[k];
             o << (k ? "," : "") << "{{" << it.j[0] << "u," << it.j[1] << "u," << it.j[2] << "u," << it.j[3] << "u},"
               << it.chunk << "u," << (stat ? p.item_phase[k] : 0u) << "u,"
-              << (stat ? (k + 1 < K ? p.item_phase[k + 1] : (uint32_t)p.max_syncs) : 0u) << "u}";
+              << (stat ? (k + 1 < K ? p.item_phase[k + 1] : (uint32_t)p.max_syncs) : 0u) << "u,0u}";
         }
         o << "};\n";
     }
@@ -772,9 +775,15 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
         lh << "    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < " << (uint64_t)K * G
            << "u; w += warps) {\n"
            << "        const uint32_t pos = w / " << G << "u;\n"
-           << "        const uint32_t ord = c_ord[pos];\n"
+           << "        const uint32_t ord = __ldg(&c_ord[pos]);\n"
            << "        const uint32_t k = ord & 0xFFFFu, shp = ord >> 16, g = w - pos * " << G << "u;\n"
-           << "        const IJ &it = c_it[k];\n";
+           << "        IJ it;\n"
+           << "        {\n"
+           << "            const uint4 w0 = __ldg(reinterpret_cast<const uint4 *>(&c_it[k]));\n"
+           << "            const uint4 w1 = __ldg(reinterpret_cast<const uint4 *>(&c_it[k]) + 1);\n"
+           << "            it.j[0] = w0.x; it.j[1] = w0.y; it.j[2] = w0.z; it.j[3] = w0.w;\n"
+           << "            it.chunk = w1.x; it.phase = w1.y; it.phase_end = w1.z; it.pad = 0;\n"
+           << "        }\n";
     } else {
         lh << "    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < a.nwitems; w += warps) {\n"
            << "        const drf::WarpItem wi = a.witems[w];\n"

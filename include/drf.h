@@ -160,13 +160,15 @@ typedef struct {
  * against the interpreted configurations.  Plans keep the interpreter when
  * NVRTC is unavailable or the protocol has no owner table.
  * drf_check / drf_check_batch of a single protocol on such a context use
- * kernels specialized to it too, kept per context and keyed by the bytecode
- * and bounds (at most 32 protocols, then the cache starts over): the first
- * check of a protocol under given bounds compiles them (that call takes the
- * compile time), later ones reuse them; every check still validates,
- * lowers and uploads the protocol and runs every pass.  Protocols the
- * automatic choice would not give the owner table, and forced sort-path
- * contexts, keep the interpreter. */
+ * kernels specialized to it too when the protocol may make 2^21 accesses or
+ * more (smaller checks run faster interpreted than the compile would take),
+ * kept per context and keyed by the bytecode and bounds (at most 32
+ * protocols, then the cache starts over): the first check of a protocol
+ * under given bounds compiles them (that call takes the compile time), later
+ * ones reuse them; every check still validates, lowers and uploads the
+ * protocol and runs every pass.  Protocols the automatic choice would not
+ * give the owner table, and forced sort-path contexts, keep the
+ * interpreter. */
 #define DRF_OPT_SPECIALIZE     0x10u
 
 #define DRF_PATH_SORT  1

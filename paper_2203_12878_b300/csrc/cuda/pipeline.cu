@@ -471,8 +471,22 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
 
 // ------------------------------------------------------------------ kernels
 
+// Programmatic dependent launch: the kernels after init are launched with
+// programmatic stream serialization, so a kernel's blocks may start while
+// the previous kernel drains.  Each first lets its own successor launch
+// (every block of it is resident by then, so the successor's waiting blocks
+// cannot keep any of it from running), then waits until the previous kernel
+// has completed and its writes are visible.  Under a plain launch both are
+// no-ops.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __global__ void k_init(BatchArgs a)
 {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (i < a.nprotos) {
         a.err_key[i] = kNone;
@@ -506,6 +520,7 @@ template <> struct InterpShared<M_EMIT> { EmitShared e; };
 template <int MODE, bool WIDE>
 __global__ void __launch_bounds__(256) k_interp(BatchArgs a)
 {
+    pdl_begin();
     constexpr bool EMIT = MODE == M_EMIT;
     __shared__ InterpShared<MODE> shm;
     EmitShared *sh = nullptr;
@@ -562,6 +577,7 @@ __global__ void __launch_bounds__(256) k_interp(BatchArgs a)
 // blocks' totals, accumulated by the count kernel).
 __global__ void __launch_bounds__(kScanThreads) k_scan(BatchArgs a, uint32_t col_blocks)
 {
+    pdl_begin();
     if (blockIdx.x < col_blocks) {
         __shared__ uint32_t s_part[kScanThreads / 32][32];
         const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -925,6 +941,7 @@ __device__ uint32_t proto_of_record(const BatchArgs &a, unsigned long long pos)
 // it read and the witness hit bits for the M_CELL pass.
 __global__ void __launch_bounds__(kTabScanThreads) k_tlist(BatchArgs a)
 {
+    pdl_begin();
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t gthreads = (uint64_t)gridDim.x * kTabScanThreads;
     for (uint64_t i = blockIdx.x * (uint64_t)kTabScanThreads + threadIdx.x; i < a.nhit; i += gthreads) {
@@ -963,6 +980,7 @@ __global__ void __launch_bounds__(kTabScanThreads) k_tlist(BatchArgs a)
 // (k_tlist cleared the touch words).  One warp per listed block.
 __global__ void __launch_bounds__(kTabScanThreads) k_tscan(BatchArgs a)
 {
+    pdl_begin();
     constexpr int V4 = 2;                               // uint4 loads per lane per block
     constexpr int PER = kTabBlock / 32;                 // records per lane per block
     const uint32_t lane = threadIdx.x & 31;
@@ -1057,6 +1075,7 @@ __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t 
 template <bool TABLE>
 __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(BatchArgs a)
 {
+    pdl_begin();
     __shared__ uint32_t s_red[4][kFinalizeThreads / 32];
     __shared__ unsigned long long s_end;
     const uint32_t p = blockIdx.x;
@@ -1198,13 +1217,40 @@ static void mark(cudaEvent_t *ev, int *nev, cudaStream_t s)
     else cudaEventRecord(ev[(*nev)++], s);
 }
 
-// One launch of a specialized kernel (a cudaKernel_t) over the warp-items.
+// Launch configuration with programmatic stream serialization (pdl_begin).
+struct PdlConfig {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    PdlConfig(dim3 grid, dim3 block, cudaStream_t s)
+    {
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+};
+
+template <typename... P>
+static void launch_pdl(void (*k)(BatchArgs, P...), dim3 grid, dim3 block, cudaStream_t s, const BatchArgs &a, P... p)
+{
+    PdlConfig c(grid, block, s);
+    cudaLaunchKernelEx(&c.cfg, k, a, p...);
+}
+
+// One launch of a specialized kernel (a cudaKernel_t) over the warp-items,
+// with programmatic stream serialization (the generated kernels begin as
+// pdl_begin does).
 static void launch_jit(const void *k, const BatchArgs &a, const JitLaunch *j, cudaStream_t s, int sms)
 {
     BatchArgs args = a;
     const uint16_t *shape = j->shape;
     void *params[] = {&args, &shape};
-    cudaLaunchKernel(k, dim3((unsigned)interp_grid(a.nwitems, sms)), dim3(256), params, 0, s);
+    PdlConfig c(dim3((unsigned)interp_grid(a.nwitems, sms)), dim3(256), s);
+    cudaLaunchKernelExC(&c.cfg, k, params);
 }
 
 cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev, const JitLaunch *j)
@@ -1219,12 +1265,12 @@ cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_
     if (j && j->count) {
         launch_jit(j->count, a, j, s, sms);
     } else {
-        if (a.has_narrow) k_interp<M_COUNT, false><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
-        if (a.has_wide) k_interp<M_COUNT, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
+        if (a.has_narrow) launch_pdl(k_interp<M_COUNT, false>, dim3(interp_grid(a.nwitems, sms)), dim3(256), s, a);
+        if (a.has_wide) launch_pdl(k_interp<M_COUNT, true>, dim3(interp_grid(a.nwitems, sms)), dim3(256), s, a);
     }
     mark(ev, nev, s);
     uint32_t col_blocks = (uint32_t)((a.ncols + 31) / 32);
-    k_scan<<<col_blocks + a.nwblocks, kScanThreads, 0, s>>>(a, col_blocks);
+    launch_pdl(k_scan, dim3(col_blocks + a.nwblocks), dim3(kScanThreads), s, a, col_blocks);
     mark(ev, nev, s);
     return cudaGetLastError();
 }
@@ -1236,26 +1282,33 @@ static void launch_interp(const BatchArgs &a, cudaStream_t s, int sms)
     if (a.has_wide) k_interp<MODE, true><<<interp_grid(a.nwitems, sms), 256, 0, s>>>(a);
 }
 
+template <int MODE>
+static void launch_interp_pdl(const BatchArgs &a, cudaStream_t s, int sms)
+{
+    if (a.has_narrow) launch_pdl(k_interp<MODE, false>, dim3(interp_grid(a.nwitems, sms)), dim3(256), s, a);
+    if (a.has_wide) launch_pdl(k_interp<MODE, true>, dim3(interp_grid(a.nwitems, sms)), dim3(256), s, a);
+}
+
 static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev,
                                      const JitLaunch *j)
 {
     if (j && j->table) launch_jit(j->table, a, j, s, sms);
-    else launch_interp<M_TABLE>(a, s, sms);
+    else launch_interp_pdl<M_TABLE>(a, s, sms);
     mark(ev, nev, s);
     const uint64_t cap = (uint64_t)sms * 8;
     uint64_t lgrid = (touch_words(a.tab_cells) + kTabScanThreads - 1) / kTabScanThreads;
     if (lgrid > cap) lgrid = cap;
     if (lgrid == 0) lgrid = 1;
-    k_tlist<<<(unsigned)lgrid, kTabScanThreads, 0, s>>>(a);
+    launch_pdl(k_tlist, dim3((unsigned)lgrid), dim3(kTabScanThreads), s, a);
     uint64_t grid = (table_blocks(a.tab_cells) + kTabScanThreads / 32 - 1) / (kTabScanThreads / 32);
     if (grid > cap) grid = cap;
     if (grid == 0) grid = 1;
-    k_tscan<<<(unsigned)grid, kTabScanThreads, 0, s>>>(a);
+    launch_pdl(k_tscan, dim3((unsigned)grid), dim3(kTabScanThreads), s, a);
     mark(ev, nev, s);
     if (j && j->cell) launch_jit(j->cell, a, j, s, sms);
-    else launch_interp<M_CELL>(a, s, sms);
+    else launch_interp_pdl<M_CELL>(a, s, sms);
     mark(ev, nev, s);
-    k_finalize<true><<<a.nprotos, kFinalizeThreads, 0, s>>>(a);
+    launch_pdl(k_finalize<true>, dim3(a.nprotos), dim3(kFinalizeThreads), s, a);
     mark(ev, nev, s);
     return cudaGetLastError();
 }

@@ -301,7 +301,7 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     // first check of a protocol under given bounds compiles them), when its
     // owner table is of a size the automatic choice would take
     if (valid.size() == 1 && (ctx->opts.flags & DRF_OPT_SPECIALIZE) && path_pref_of(ctx->opts) != 1 && bh.table_ok &&
-        auto_path(bh, bh.tuple_bound) == PATH_TABLE) {
+        bh.tuple_bound >= kJitMinTuples && auto_path(bh, bh.tuple_bound) == PATH_TABLE) {
         const uint32_t i = where[0];
         const JitEntry *je = jit_entry(ctx, bytecodes[i], lens[i], &bounds[i], *valid[0], bh);
         if (je && je->mod) {

@@ -153,6 +153,10 @@ int run_batch(drf_ctx *ctx, const BatchHost &b, cudaStream_t s, std::vector<DevR
 int run_batch_jit(drf_ctx *ctx, const BatchHost &b, const JitLaunch &j, cudaStream_t s, std::vector<DevResult> &out);
 
 constexpr size_t kJitCacheEntries = 32;
+// drf_check specializes only protocols that may make this many accesses: a
+// smaller check takes well under a millisecond interpreted, far less than
+// the compile (0.1 - 1 s) would cost it the first time.
+constexpr uint64_t kJitMinTuples = 1ull << 21;
 
 // Back-end preference of a context's options: 0 automatic, 1 sort, 2 owner table.
 int path_pref_of(const drf_opts &o);

@@ -800,7 +800,11 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
        << "        const uint64_t li = " << LANE_OFF << " + (uint64_t)k * " << T << " + tid;\n"
        << "        (void)shp; (void)li;\n";
     const std::string loop_head = lh.str();
-    const char *sig = "(drf::BatchArgs a, const uint16_t *__restrict__ shape)\n{\n    (void)shape;\n";
+    // every kernel lets its successor launch, then waits for its predecessor
+    // (programmatic dependent launch; no-ops under a plain launch)
+    const char *sig = "(drf::BatchArgs a, const uint16_t *__restrict__ shape)\n{\n    (void)shape;\n"
+                      "    asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n"
+                      "    asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n";
     // count pass: the interpreter's M_COUNT outputs
     o << "extern \"C\" __global__ void __launch_bounds__(256) drf_count" << sig << loop_head
       << "        uint32_t count = 0, syncs = 0, err = 0;\n"

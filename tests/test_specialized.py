@@ -152,18 +152,25 @@ def test_autotuned_specialized_plan(oracle):
 
 
 def test_drf_check_with_specialized_kernels(oracle):
-    """drf_check on a context with DRF_OPT_SPECIALIZE: the first check of a
-    protocol under its bounds compiles kernels for it and later checks reuse
-    them; results equal the oracle's whether the protocol has static phases,
-    thread-dependent syncs, evaluation errors or barrier divergence, with
+    """drf_check on a context with DRF_OPT_SPECIALIZE: a protocol that may
+    make 2^21 accesses or more gets kernels compiled for it on its first
+    check, reused by later checks; smaller ones are interpreted.  Results
+    equal the oracle's either way, with static and thread-dependent phases,
     checks of different protocols interleaved on the context's buffers."""
     c = drf.drf_ctx_create(0, flags=drf.OPT_SPECIALIZE)
     try:
-        ps = [protogen.config1("drf"), protogen.config1("nosync"), late_phase_race(64, 9, 8, 0),
-              protogen.config2(1, target=3e5), protogen.config2(2, "constructed", target=3e5, plant=True)]
-        ps += [protogen.random_small(s) for s in range(40)]
+        # the last one's index is never negative, but the analysis cannot
+        # prove it: its phases are thread-dependent (count and scan run)
+        big = [protogen.config2(0), protogen.config2(4), protogen.config2(2, "constructed", plant=True),
+               protogen.config2(6, "constructed", plant=False), late_phase_race(4096, 600, 500, 7),
+               protogen.Protocol("array A;\nforS x in 0 .. 300 {\n  wr A[tid - (tid % 2) + 4096 * x];\n  sync;\n"
+                                 "  rd A[(tid + 1) % 4096 + 4096 * x];\n}\n", 4096, [4096 * 300], [])]
+        small = [protogen.config1("nosync"), protogen.random_small(3), protogen.random_small(11)]
+        for p in big:
+            assert drf.drf_protocol_analyze(drf.drf_protocol_compile(p.text), p.nthreads, p.cells,
+                                            p.params)[1]["tuple_bound"] >= 1 << 21
         for rnd in range(2):
-            for p in ps:
+            for p in big + small:
                 exp = {k: v for k, v in want(oracle, p).items() if k != "message"}
                 if exp["status"] == "OVERFLOW":
                     continue

@@ -382,6 +382,7 @@ def run_ours(args, rank, world):
 
     extra = {}
     if not args.quick and rank == 0:
+        extra["grid_scale"] = bench_grid_scale(stream, flush, args)
         extra["batched"] = bench_batched(ctx, args)
         extra["served"] = [bench_served(args, rate=r, seconds=1.5) for r in args.rates]
 
@@ -427,6 +428,30 @@ def run_ours(args, rank, world):
     drf.drf_plan_destroy(plan)
     drf.drf_ctx_destroy(ctx)
     return out
+
+
+def bench_grid_scale(stream, flush, args):
+    """The grid-scale workload: one protocol of 65,536 threads, 4 arrays of
+    2^24 cells, 8 phases, ~2.2x10^8 access tuples (seed 0, one planted race),
+    as an autotuned plan; device time per check, L2 flushed before each."""
+    import torch
+    from paper_2203_12878_b300 import drf, protogen
+    p = protogen.config3(0, racy=True)
+    bc = drf.drf_protocol_compile(p.text)
+    ctx = drf.drf_ctx_create(0, flags=drf.OPT_AUTOTUNE | drf.OPT_SPECIALIZE)
+    try:
+        plan = drf.drf_plan_create(ctx, [bc], [(p.nthreads, p.cells, p.params)])
+        n = drf.drf_plan_info(plan)["tuples"]
+        ms, _, _, _, _ = time_steps(plan, 20, 3, stream, flush, warm_s=0.5)
+        r = drf.result_dict(drf.drf_plan_results(plan)[0])
+        assert (r["verdict"], r["phase"], r["loc"], r["index"]) == ("RACY", p.meta["phase"], p.meta["loc"], p.meta["index"])
+        out = {"workload": "65,536 threads, 4 arrays x 2^24 cells, 8 phases, one planted race (seed 0)",
+               "tuples": n, "path": drf.drf_plan_path(plan), "specialized": drf.drf_plan_specialized(plan)[0],
+               "ms_per_check": statistics.mean(ms), "tuples_per_s": n / (statistics.mean(ms) * 1e-3)}
+        drf.drf_plan_destroy(plan)
+        return out
+    finally:
+        drf.drf_ctx_destroy(ctx)
 
 
 def bench_batched(ctx, args):

@@ -383,6 +383,7 @@ def run_ours(args, rank, world):
     extra = {}
     if not args.quick and rank == 0:
         extra["grid_scale"] = bench_grid_scale(stream, flush, args)
+        extra["small_latency"] = bench_small_latency(stream)
         extra["batched"] = bench_batched(ctx, args)
         extra["served"] = [bench_served(args, rate=r, seconds=1.5) for r in args.rates]
 
@@ -427,6 +428,43 @@ def run_ours(args, rank, world):
         out.update(extra)
     drf.drf_plan_destroy(plan)
     drf.drf_ctx_destroy(ctx)
+    return out
+
+
+def bench_small_latency(stream, calls=200):
+    """The small workload (256 threads, one array of 2048 cells, 4096
+    accesses: latency-bound): wall time of one drf_check (host bytecode in,
+    result out) and of one plan launch with its results read back."""
+    import torch
+    from paper_2203_12878_b300 import drf, protogen
+    out = {}
+    ctx = drf.drf_ctx_create(0)
+    try:
+        for v in ("drf", "nosync"):
+            p = protogen.config1(v)
+            bc = drf.drf_protocol_compile(p.text)
+            for _ in range(20):
+                drf.drf_check(ctx, bc, p.nthreads, p.cells, p.params, stream)
+            ts = []
+            for _ in range(calls):
+                t0 = time.perf_counter()
+                r = drf.drf_check(ctx, bc, p.nthreads, p.cells, p.params, stream)
+                ts.append(time.perf_counter() - t0)
+            plan = drf.drf_plan_create(ctx, [bc], [(p.nthreads, p.cells, p.params)])
+            tp = []
+            for i in range(calls + 20):
+                t0 = time.perf_counter()
+                drf.drf_plan_launch(plan, stream)
+                drf.drf_plan_results(plan)
+                if i >= 20:
+                    tp.append(time.perf_counter() - t0)
+            drf.drf_plan_destroy(plan)
+            ts.sort(); tp.sort()
+            out[v] = {"verdict": drf.result_dict(r)["verdict"], "tuples": p.meta.get("accesses", 4096),
+                      "drf_check_us_p50": round(ts[len(ts) // 2] * 1e6, 1), "drf_check_us_p99": round(ts[int(len(ts) * 0.99)] * 1e6, 1),
+                      "plan_launch_us_p50": round(tp[len(tp) // 2] * 1e6, 1), "plan_launch_us_p99": round(tp[int(len(tp) * 0.99)] * 1e6, 1)}
+    finally:
+        drf.drf_ctx_destroy(ctx)
     return out
 
 

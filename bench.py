@@ -120,16 +120,23 @@ class ClockSampler:
 KERNEL_SOURCES = ("paper_2203_12878_b300/csrc/cuda/pipeline.cu", "paper_2203_12878_b300/csrc/cuda/pipeline.cuh",
                   "paper_2203_12878_b300/csrc/cuda/radix.cuh", "paper_2203_12878_b300/csrc/cuda/owner.cuh",
                   "paper_2203_12878_b300/csrc/cuda/intmath.cuh", "paper_2203_12878_b300/csrc/batch_args.h",
-                  "paper_2203_12878_b300/csrc/devprog.h", "paper_2203_12878_b300/csrc/host/jit.cpp",
-                  "paper_2203_12878_b300/csrc/host/prepare.cpp")
+                  "paper_2203_12878_b300/csrc/devprog.h", "paper_2203_12878_b300/csrc/host/jit.cpp")
 
 
 def _pipeline_hash():
-    """Hash of every source the device kernels are built or generated from."""
+    """Hash of what the measured kernels are built from: the device sources,
+    the code generator (its compile options included) and the CUDA source it
+    generates for the benchmark protocol (which also fingerprints the host's
+    lowering of that protocol, the program the interpreter runs)."""
+    from paper_2203_12878_b300 import drf
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
+    p = workload()
+    st, src, _ = drf.drf_protocol_specialize(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params,
+                                             compile=False)
+    h.update((src or st).encode())
     return h.hexdigest()[:16]
 
 

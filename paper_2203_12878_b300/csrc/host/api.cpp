@@ -131,10 +131,8 @@ int drf_ctx_create(int device, const drf_opts *opts, drf_ctx **out)
     if (opts) ctx->opts = *opts;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0) ctx->sms = sms;
-    if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaMallocHost((void **)&ctx->pinned_ctrl, sizeof(Control))) != cudaSuccess) {
+    if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess) {
         cudaGetLastError();
-        if (ctx->stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
         return DRF_E_CUDA;
     }
@@ -148,7 +146,6 @@ void drf_ctx_destroy(drf_ctx *ctx)
     if (ctx->server) drf_server_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    cudaFreeHost(ctx->pinned_ctrl);
     cudaStreamDestroy(ctx->stream);
     delete ctx;                       // frees the workspace's device buffers
 }
@@ -277,7 +274,7 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     }
     if (valid.empty()) return DRF_OK;
     cudaStream_t s = pick(ctx, stream);
-    BatchHost bh;
+    BatchHost &bh = ctx->host;
     Error e = pack_batch(valid, bh);
     if (e.status == S_KEY_TOO_WIDE && valid.size() > 1) {
         // the combined key does not fit: check the protocols one by one
@@ -482,12 +479,11 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
     JitLaunch sizing = d.jit;
     sizing.static_phases = false;
     if ((ce = launch_front(d.args, s, ctx->sms, nullptr, nullptr, &sizing)) != cudaSuccess ||
-        (ce = cudaMemcpyAsync(ctx->pinned_ctrl, d.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
+        (ce = d.fetch(s, true)) != cudaSuccess || (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
         delete plan;
         return cuda_fail(ctx, ce);
     }
-    plan->tuples = ctx->pinned_ctrl->total;
+    plan->tuples = d.host_ctrl()->total;
     e = d.choose_path(plan->host, plan->tuples, s);
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
     plan->cfg.path = d.args.path == PATH_TABLE ? 2 : 1;
@@ -696,15 +692,14 @@ int drf_plan_results(drf_plan *plan, drf_result *out)
     drf_ctx *ctx = plan->ctx;
     cudaSetDevice(ctx->device);
     cudaStream_t s = plan->last_stream ? plan->last_stream : ctx->stream;
-    std::vector<DevResult> res(plan->n);
-    Control c{};
+    DeviceBatch &d = plan->dev;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(res.data(), plan->dev.args.results, plan->n * sizeof(DevResult), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(&c, plan->dev.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    if ((e = d.fetch(s, false)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(ctx, e);
-    if (c.flags & CF_LOOKBACK_TIMEOUT) return fail(ctx, DRF_E_TIMEOUT, "radix look-back gave up waiting");
-    if (c.flags) return fail(ctx, DRF_E_INTERNAL, "device consistency flags " + std::to_string(c.flags));
+    const unsigned flags = d.host_ctrl()->flags;
+    if (flags & CF_LOOKBACK_TIMEOUT) return fail(ctx, DRF_E_TIMEOUT, "radix look-back gave up waiting");
+    if (flags) return fail(ctx, DRF_E_INTERNAL, "device consistency flags " + std::to_string(flags));
+    const DevResult *res = d.host_results();
     for (uint32_t i = 0; i < plan->n; i++) to_public(res[i], &out[i]);
     return DRF_OK;
 }

@@ -36,7 +36,17 @@ void release(DevBuf &b, size_t *in_use)
 
 Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
 {
-    out = BatchHost{};
+    // cleared, not reassigned: a reused image keeps its vectors' capacity
+    out.insns.clear();
+    out.xcode.clear();
+    out.items.clear();
+    out.protos.clear();
+    out.cells.clear();
+    out.cbase.clear();
+    out.witems.clear();
+    out.ncols = out.lanes = out.tuple_bound = out.table_cells = 0;
+    out.L = KeyLayout{};
+    out.table_ok = false;
     KeyLayout L{};
     const uint32_t n = (uint32_t)ps.size();
     L.proto_bits = n > 1 ? bits_for(n - 1) : 0;
@@ -105,31 +115,46 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
     // stable order: equal items keep protocol and item order, and the
     // groups of one item stay consecutive)
     std::stable_sort(ws.begin(), ws.end(), [](const W &x, const W &y) { return x.steps > y.steps; });
-    out.witems.reserve(nwitems);
+    out.witems.resize(nwitems);
+    WarpItem *wi = out.witems.data();
     for (auto &w : ws)
-        for (uint32_t g = 0; g < w.groups; g++) out.witems.push_back(WarpItem{w.proto, w.k, g});
+        for (uint32_t g = 0; g < w.groups; g++) *wi++ = WarpItem{w.proto, w.k, g};
     return Error{};
 }
 
 DeviceBatch::~DeviceBatch()
 {
-    DevBuf *all[] = {&insns, &xcode, &items, &protos, &cells, &witems, &cnt, &syn, &phs, &erro, &totsyn,
-                     &wcnt, &wbase, &blocksum, &keys0, &keys1, &hist, &status, &trec, &err_key, &div_tid,
-                     &best_pos, &ptuples, &results, &ctrl, &epoch, &cbase, &table, &touch, &tlist, &hit, &ishape};
+    DevBuf *all[] = {&image, &cnt, &syn, &phs, &erro, &totsyn, &wcnt, &wbase, &blocksum, &keys0, &keys1, &hist,
+                     &status, &trec, &err_key, &div_tid, &best_pos, &ptuples, &out, &epoch, &table,
+                     &touch, &tlist, &hit, &ishape};
     for (DevBuf *b : all) release(*b, &in_use);
+    if (staged) cudaEventDestroy(staged);
+    if (stage) cudaFreeHost(stage);
+    if (out_host) cudaFreeHost(out_host);
+}
+
+cudaError_t DeviceBatch::fetch(cudaStream_t s, bool ctrl_only)
+{
+    const size_t bytes = ctrl_only ? sizeof(Control) : kOutResults + (size_t)args.nprotos * sizeof(DevResult);
+    d2h_bytes += bytes;
+    return cudaMemcpyAsync(out_host, out.p, bytes, cudaMemcpyDeviceToHost, s);
 }
 
 namespace {
 
+// One section of the batch image: its bytes start at a 256-byte boundary.
+struct Section {
+    const void *src;
+    size_t bytes;
+    size_t off;
+};
+
 template <typename T>
-bool upload(DevBuf &b, const std::vector<T> &v, size_t *in_use, uint64_t limit, cudaStream_t s, uint64_t *bytes_out)
+Section section(const std::vector<T> &v, size_t &end)
 {
-    *bytes_out += v.size() * sizeof(T);
-    size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
-    if (!ensure(b, bytes, in_use, limit)) return false;
-    if (!v.empty() && cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return false;
-    return true;
+    Section x{v.data(), v.size() * sizeof(T), end};
+    end += (x.bytes + 255) & ~(size_t)255;
+    return x;
 }
 
 }  // namespace
@@ -141,11 +166,34 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     const uint32_t nwblocks = (uint32_t)std::max<uint64_t>(1, (nw + kWScanPerBlock - 1) / kWScanPerBlock);
     h2d_bytes = 0;
     d2h_bytes = 0;
-    uint64_t *hb = &h2d_bytes;
-    bool ok = upload(insns, b.insns, &in_use, limit, s, hb) && upload(xcode, b.xcode, &in_use, limit, s, hb) &&
-              upload(items, b.items, &in_use, limit, s, hb) && upload(protos, b.protos, &in_use, limit, s, hb) &&
-              upload(cells, b.cells, &in_use, limit, s, hb) && upload(cbase, b.cbase, &in_use, limit, s, hb) &&
-              upload(witems, b.witems, &in_use, limit, s, hb);
+    // the image: every host section packed into pinned memory, then one copy
+    size_t end = 0;
+    const Section sec[] = {section(b.insns, end), section(b.xcode, end), section(b.items, end),
+                           section(b.protos, end), section(b.cells, end), section(b.cbase, end),
+                           section(b.witems, end)};
+    const size_t total = std::max<size_t>(end, 256);
+    bool ok = ensure(image, total, &in_use, limit);
+    // the previous copy out of the stage must be done before it is rewritten
+    if (ok && staged_pending) ok = cudaEventSynchronize(staged) == cudaSuccess;
+    staged_pending = false;
+    if (ok && stage_cap < total) {
+        const size_t want = std::max(total, stage_cap + stage_cap / 4);
+        if (stage) cudaFreeHost(stage);
+        stage = nullptr;
+        stage_cap = 0;
+        ok = cudaHostAlloc(&stage, want, cudaHostAllocDefault) == cudaSuccess;
+        if (ok) stage_cap = want;
+        else stage = nullptr;
+    }
+    if (ok && !staged) ok = cudaEventCreateWithFlags(&staged, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+        for (const Section &x : sec)
+            if (x.bytes) std::memcpy((char *)stage + x.off, x.src, x.bytes);
+        ok = cudaMemcpyAsync(image.p, stage, end ? end : 16, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+             cudaEventRecord(staged, s) == cudaSuccess;
+        staged_pending = ok;
+        h2d_bytes = end;
+    }
     const size_t lanes = std::max<uint64_t>(b.lanes, 1);
     ok = ok && ensure(cnt, lanes * 4, &in_use, limit) && ensure(syn, lanes * 4, &in_use, limit) &&
          ensure(phs, lanes * 4, &in_use, limit) && ensure(erro, lanes * 8, &in_use, limit) &&
@@ -156,7 +204,17 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
          ensure(hist, (size_t)kMaxPasses * kRadixBins * 8, &in_use, limit) &&
          ensure(err_key, np * 8, &in_use, limit) && ensure(div_tid, np * 4, &in_use, limit) &&
          ensure(best_pos, np * 8, &in_use, limit) && ensure(ptuples, np * 8, &in_use, limit) &&
-         ensure(results, np * sizeof(DevResult), &in_use, limit) && ensure(ctrl, sizeof(Control), &in_use, limit);
+         ensure(out, kOutResults + np * sizeof(DevResult), &in_use, limit);
+    if (ok && out_host_cap < kOutResults + np * sizeof(DevResult)) {
+        // every reader of the mirror waits for its copy before the next load
+        const size_t want = std::max(kOutResults + np * sizeof(DevResult), out_host_cap + out_host_cap / 4);
+        if (out_host) cudaFreeHost(out_host);
+        out_host = nullptr;
+        out_host_cap = 0;
+        ok = cudaHostAlloc(&out_host, want, cudaHostAllocDefault) == cudaSuccess;
+        if (ok) out_host_cap = want;
+        else out_host = nullptr;
+    }
     if (ok && !epoch.p) {
         ok = ensure(epoch, 16, &in_use, limit) && cudaMemsetAsync(epoch.p, 0, 16, s) == cudaSuccess;
     }
@@ -165,12 +223,14 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
         return Error::make(S_NOMEM, "device allocation failed");
     }
     BatchArgs &a = args;
-    a.insns = (const Insn *)insns.p;
-    a.xcode = (const uint64_t *)xcode.p;
-    a.items = (const ItemDesc *)items.p;
-    a.protos = (const DevProto *)protos.p;
-    a.cells = (const uint64_t *)cells.p;
-    a.witems = (const WarpItem *)witems.p;
+    char *img = (char *)image.p;
+    a.insns = (const Insn *)(img + sec[0].off);
+    a.xcode = (const uint64_t *)(img + sec[1].off);
+    a.items = (const ItemDesc *)(img + sec[2].off);
+    a.protos = (const DevProto *)(img + sec[3].off);
+    a.cells = (const uint64_t *)(img + sec[4].off);
+    a.cbase = (const uint64_t *)(img + sec[5].off);
+    a.witems = (const WarpItem *)(img + sec[6].off);
     a.nwitems = (uint32_t)nw;
     a.nprotos = (uint32_t)np;
     a.has_narrow = a.has_wide = 0;
@@ -190,8 +250,8 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.div_tid = (uint32_t *)div_tid.p;
     a.best_pos = (unsigned long long *)best_pos.p;
     a.ptuples = (unsigned long long *)ptuples.p;
-    a.results = (DevResult *)results.p;
-    a.ctrl = (Control *)ctrl.p;
+    a.ctrl = (Control *)out.p;
+    a.results = (DevResult *)((char *)out.p + kOutResults);
     a.epoch = (uint32_t *)epoch.p;
     a.L = b.L;
     a.radix_items = radix_items;
@@ -200,7 +260,6 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.keys[0] = (unsigned long long *)keys0.p;
     a.keys[1] = (unsigned long long *)keys1.p;
     a.status = (unsigned long long *)status.p;
-    a.cbase = (const uint64_t *)cbase.p;
     a.path = PATH_SORT;
     a.table = nullptr;
     a.tab_cells = 0;
@@ -308,34 +367,56 @@ static int flags_status(unsigned flags)
     return S_OK;
 }
 
-int run_batch(DeviceBatch &w, Control *pinned, int sms, cudaStream_t s, const BatchHost &b,
-              std::vector<DevResult> &out, std::string &err)
+// Copies the mirrored results into `out` and checks the control flags.
+static int collect(const DeviceBatch &w, std::vector<DevResult> &out, std::string &err)
+{
+    out.assign(w.host_results(), w.host_results() + w.args.nprotos);
+    const unsigned flags = w.host_ctrl()->flags;
+    int st = flags_status(flags);
+    if (st) err = "device pipeline consistency check failed (flags " + std::to_string(flags) + ")";
+    return st;
+}
+
+int run_batch(DeviceBatch &w, int sms, cudaStream_t s, const BatchHost &b, std::vector<DevResult> &out,
+              std::string &err)
 {
     Error e = w.load(b, s);
     if (!e.ok()) { err = e.message; return e.status; }
-    if (launch_front(w.args, s, sms, nullptr, nullptr) != cudaSuccess ||
-        cudaMemcpyAsync(pinned, w.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    // When the tuple bound already selects the owner table (the automatic
+    // choice made on the bound, or the table asked for), nothing the host
+    // does depends on the count: front and back run in one go, one wait.
+    if (b.table_ok && w.path_pref != 1 && (w.path_pref == 2 || auto_path(b, b.tuple_bound) == PATH_TABLE)) {
+        e = w.size_table(b, kUncounted, s);
+        if (e.ok()) {
+            w.status_launches++;
+            if (launch_front(w.args, s, sms, nullptr, nullptr) != cudaSuccess ||
+                launch_back(w.args, s, sms, nullptr, nullptr) != cudaSuccess || w.fetch(s, false) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                err = cudaGetErrorString(cudaGetLastError());
+                w.table_dirty = true;
+                return S_CUDA;
+            }
+            return collect(w, out, err);
+        }
+        if (w.path_pref == 2) { err = e.message; return e.status; }
+        cudaGetLastError();                          // no room for the table: count, then choose
+    }
+    if (launch_front(w.args, s, sms, nullptr, nullptr) != cudaSuccess || w.fetch(s, true) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         err = cudaGetErrorString(cudaGetLastError());
         return S_CUDA;
     }
-    const uint64_t n = pinned->total;
+    const uint64_t n = w.host_ctrl()->total;
     e = w.choose_path(b, n, s);
     if (!e.ok()) { err = e.message; return e.status; }
     w.status_launches++;
-    out.resize(b.protos.size());
-    if (launch_back(w.args, s, sms, nullptr, nullptr) != cudaSuccess ||
-        cudaMemcpyAsync(out.data(), w.args.results, out.size() * sizeof(DevResult), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(pinned, w.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (launch_back(w.args, s, sms, nullptr, nullptr) != cudaSuccess || w.fetch(s, false) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         err = cudaGetErrorString(cudaGetLastError());
         w.table_dirty = true;
         return S_CUDA;
     }
-    w.d2h_bytes = 2 * sizeof(Control) + out.size() * sizeof(DevResult);
-    int st = flags_status(pinned->flags);
-    if (st) err = "device pipeline consistency check failed (flags " + std::to_string(pinned->flags) + ")";
-    return st;
+    return collect(w, out, err);
 }
 
 JitEntry::~JitEntry()
@@ -356,21 +437,14 @@ int run_batch_jit(drf_ctx *ctx, const BatchHost &b, const JitLaunch &j, cudaStre
     }
     w.args.nkeys = kUncounted;                     // no sizing run: the count is known only afterwards
     w.status_launches++;
-    out.resize(b.protos.size());
-    Control *pinned = ctx->pinned_ctrl;
     if (launch_front(w.args, s, ctx->sms, nullptr, nullptr, &j) != cudaSuccess ||
-        launch_back(w.args, s, ctx->sms, nullptr, nullptr, &j) != cudaSuccess ||
-        cudaMemcpyAsync(out.data(), w.args.results, out.size() * sizeof(DevResult), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(pinned, w.args.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        launch_back(w.args, s, ctx->sms, nullptr, nullptr, &j) != cudaSuccess || w.fetch(s, false) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         ctx->last_error = cudaGetErrorString(cudaGetLastError());
         w.table_dirty = true;
         return S_CUDA;
     }
-    w.d2h_bytes = sizeof(Control) + out.size() * sizeof(DevResult);
-    int st = flags_status(pinned->flags);
-    if (st) ctx->last_error = "device pipeline consistency check failed (flags " + std::to_string(pinned->flags) + ")";
-    return st;
+    return collect(w, out, ctx->last_error);
 }
 
 int path_pref_of(const drf_opts &o)
@@ -384,7 +458,7 @@ int run_batch(drf_ctx *ctx, const BatchHost &b, cudaStream_t s, std::vector<DevR
 {
     ctx->work.limit = ctx->opts.max_device_bytes;
     ctx->work.path_pref = path_pref_of(ctx->opts);
-    return run_batch(ctx->work, ctx->pinned_ctrl, ctx->sms, s, b, out, ctx->last_error);
+    return run_batch(ctx->work, ctx->sms, s, b, out, ctx->last_error);
 }
 
 void to_public(const DevResult &d, drf_result *o)

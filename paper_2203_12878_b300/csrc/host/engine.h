@@ -52,13 +52,28 @@ constexpr uint64_t kMaxTableBytes = 64ull << 30;
 // S_KEY_TOO_WIDE when the combined key layout exceeds 64 bits.
 Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out);
 
+// Offset of the results after the control block in a batch's report.
+constexpr size_t kOutResults = 128;
+static_assert(sizeof(Control) <= kOutResults, "control block fits before the results");
+
 // Device buffers of one batch (a plan owns one; a context reuses one).
 struct DeviceBatch {
-    DevBuf insns, xcode, items, protos, cells, witems;
+    // the batch's host image (program, items, protocols, array sizes, table
+    // bases, warp items): one device arena, filled by one copy from `stage`
+    DevBuf image;
+    void *stage = nullptr;            // pinned host staging buffer of the image
+    size_t stage_cap = 0;
+    cudaEvent_t staged = nullptr;     // recorded after the copy out of `stage`
+    bool staged_pending = false;
     DevBuf cnt, syn, phs, erro, totsyn, wcnt, wbase, blocksum;
     DevBuf keys0, keys1, hist, status, trec;
-    DevBuf err_key, div_tid, best_pos, ptuples, results, ctrl, epoch;
-    DevBuf cbase, table, touch, tlist, hit, ishape;
+    DevBuf err_key, div_tid, best_pos, ptuples, epoch;
+    DevBuf table, touch, tlist, hit, ishape;
+    // what a launch reports: the control block, then one result per
+    // protocol, read back by one copy into a pinned mirror
+    DevBuf out;
+    void *out_host = nullptr;
+    size_t out_host_cap = 0;
     size_t in_use = 0;
     uint64_t limit = 0;
     uint64_t status_launches = 0;     // launches since the look-back words were cleared
@@ -70,6 +85,11 @@ struct DeviceBatch {
     BatchArgs args{};
 
     ~DeviceBatch();
+    Control *host_ctrl() const { return (Control *)out_host; }
+    const DevResult *host_results() const { return (const DevResult *)((const char *)out_host + kOutResults); }
+    // Queues the copy of the control block (ctrl_only) or of the control
+    // block and every result into the pinned mirror.
+    cudaError_t fetch(cudaStream_t s, bool ctrl_only);
     // Uploads the batch and sizes every buffer that does not depend on the
     // tuple count.
     Error load(const BatchHost &b, cudaStream_t s);
@@ -110,9 +130,7 @@ struct drf_ctx {
     drf_opts opts{};
     std::string last_error;
     drf::DeviceBatch work;            // reused by drf_check / drf_check_batch
-    std::vector<drf::DevResult> host_results;
-    drf::Control host_ctrl{};
-    drf::Control *pinned_ctrl = nullptr;
+    drf::BatchHost host;              // host image of the last batch (its vectors keep their capacity)
     void *server = nullptr;           // drf::Server when running
     std::mutex mu;                    // guards `work` between the caller and the server thread
     // specialized kernels of protocols checked before, keyed by bytecode and
@@ -140,10 +158,10 @@ struct drf_plan {
 namespace drf {
 
 // Runs one batch on the buffers `w`: front, size, back; results into `out`
-// (one per packed protocol).  `pinned` is a host-pinned Control used to read
-// the tuple count back.  Returns a batch-level status; `err` gets a message.
-int run_batch(DeviceBatch &w, Control *pinned, int sms, cudaStream_t s, const BatchHost &b,
-              std::vector<DevResult> &out, std::string &err);
+// (one per packed protocol).  Returns a batch-level status; `err` gets a
+// message.
+int run_batch(DeviceBatch &w, int sms, cudaStream_t s, const BatchHost &b, std::vector<DevResult> &out,
+              std::string &err);
 int run_batch(drf_ctx *ctx, const BatchHost &b, cudaStream_t s, std::vector<DevResult> &out);
 
 // One protocol on the context's buffers with kernels specialized to it:

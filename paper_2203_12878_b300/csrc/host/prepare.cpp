@@ -13,7 +13,7 @@
 // width), accesses and interpreter steps per thread.
 #include <algorithm>
 #include <cstring>
-#include <unordered_map>
+#include <stdexcept>
 
 #include "prepare.h"
 
@@ -46,6 +46,55 @@ i128 floor_div(i128 a, i128 b)
     return q;
 }
 
+// Map from AST nodes to their analysis results: open addressing over one
+// array (the analyses store a value for nearly every node, so per-entry
+// allocations would dominate their cost).  References returned by at() stay
+// valid until the next insertion.
+template <typename K, typename V>
+class NodeMap {
+public:
+    V &operator[](const K *k)
+    {
+        if ((n_ + 1) * 2 > slots_.size()) rehash(std::max<size_t>(64, slots_.size() * 2));
+        Slot &x = slots_[probe(k)];
+        if (!x.key) {
+            x.key = k;
+            x.val = V{};
+            n_++;
+        }
+        return x.val;
+    }
+    const V &at(const K *k) const
+    {
+        if (slots_.empty() || slots_[probe(k)].key != k) throw std::out_of_range("node without an analysis result");
+        return slots_[probe(k)].val;
+    }
+    size_t count(const K *k) const { return !slots_.empty() && slots_[probe(k)].key == k; }
+
+private:
+    struct Slot {
+        const K *key = nullptr;
+        V val{};
+    };
+    std::vector<Slot> slots_;
+    size_t n_ = 0;
+
+    size_t probe(const K *k) const
+    {
+        const size_t mask = slots_.size() - 1;
+        size_t i = (size_t)(((uintptr_t)k >> 4) * 0x9E3779B97F4A7C15ull >> 20) & mask;
+        while (slots_[i].key && slots_[i].key != k) i = (i + 1) & mask;
+        return i;
+    }
+    void rehash(size_t cap)
+    {
+        std::vector<Slot> old(cap);
+        old.swap(slots_);
+        for (const Slot &x : old)
+            if (x.key) slots_[probe(x.key)] = x;
+    }
+};
+
 struct LoopInfo {
     i128 trip_max = 0;       // over all threads and outer iterations
     i128 body_steps = 0;     // steps per iteration, upper bound
@@ -64,11 +113,12 @@ public:
     bool risk = false;
     bool wide = false;
     bool maybe_div0 = false;                               // some division's divisor may be zero
-    std::unordered_map<const Stmt *, LoopInfo> loops;
-    std::unordered_map<const Stmt *, bool> count_eval;   // access -> evaluate index in the count pass
-    std::unordered_map<const Expr *, Iv> ranges;
+    NodeMap<Stmt, LoopInfo> loops;
+    NodeMap<Stmt, bool> count_eval;                      // access -> evaluate index in the count pass
+    bool any_count_eval = false;                         // some access must be evaluated in the count pass
+    NodeMap<Expr, Iv> ranges;
 
-    std::unordered_map<const Stmt *, Work> work;          // per statement, upper bounds per thread
+    NodeMap<Stmt, Work> work;                            // per statement, upper bounds per thread
 
     Work stmt(const Stmt &s, bool reachable)
     {
@@ -91,6 +141,7 @@ public:
             Iv ix = expr(*s.index, div0, reachable);
             bool in_range = !ix.empty() && ix.lo >= 0 && ix.hi < (i128)cells_[s.loc];
             count_eval[&s] = !(in_range && !div0);
+            if (!(in_range && !div0)) any_count_eval = true;
             w.tuples = 1; w.steps = 1;
             return w;
         }
@@ -228,20 +279,47 @@ private:
 
 struct Lowerer {
     const int64_t *params;
-    const std::unordered_map<const Expr *, Iv> &ranges;
-    const std::unordered_map<const Stmt *, bool> &count_eval;
+    const NodeMap<Expr, Iv> &ranges;
+    const NodeMap<Stmt, bool> &count_eval;
     std::vector<Insn> insns;
     std::vector<uint64_t> xcode;
     std::vector<int> slot_reg;        // AST slot -> device register (nesting depth)
     int max_stack = 0;
     bool too_deep = false;
 
+    // (register or kAffTid, coefficient) pairs of a linear form: at most one
+    // per register and one for tid, kept inline (no allocation per node).
+    struct Term {
+        uint32_t first;               // register or kAffTid
+        i128 second;                  // coefficient
+    };
+    struct Terms {
+        uint32_t n = 0;
+        Term v[kMaxVars + 1];         // the first n are set
+        Terms() {}
+        Terms(const Terms &o) : n(o.n) { std::copy(o.v, o.v + o.n, v); }
+        Terms &operator=(const Terms &o) { n = o.n; std::copy(o.v, o.v + o.n, v); return *this; }
+        Term *begin() { return v; }
+        Term *end() { return v + n; }
+        const Term *begin() const { return v; }
+        const Term *end() const { return v + n; }
+        bool empty() const { return n == 0; }
+        size_t size() const { return n; }
+        const Term &operator[](size_t i) const { return v[i]; }
+        void push_back(const Term &t)
+        {
+            if (n > kMaxVars) throw std::length_error("linear form with too many terms");
+            v[n++] = t;
+        }
+        void emplace_back(uint32_t reg, i128 c) { push_back(Term{reg, c}); }
+    };
+
     // Folded form of an expression: a constant, or a linear combination of
     // tid / registers, or neither.
     struct Lin {
         bool ok = false;
         i128 c0 = 0;
-        std::vector<std::pair<uint32_t, i128>> terms;   // (register or kAffTid, coefficient)
+        Terms terms;
     };
 
     static void add_term(Lin &l, uint32_t reg, i128 c)
@@ -300,7 +378,7 @@ struct Lowerer {
 
     void emit_linear(const Lin &l)
     {
-        std::vector<std::pair<uint32_t, i128>> terms;
+        Terms terms;
         for (auto &t : l.terms) if (t.second != 0) terms.push_back(t);
         if (terms.empty()) { word(X_CONST); lit((int64_t)l.c0); return; }
         if (terms.size() == 1 && terms[0].second == 1 && l.c0 == 0) {
@@ -387,8 +465,8 @@ struct Lowerer {
         return pc() - 1;
     }
 
-    std::unordered_map<const Stmt *, std::pair<int32_t, int32_t>> range;   // [begin, end) pcs
-    std::unordered_map<const Stmt *, bool> fast;                           // loops lowered to I_FASTLOOP
+    NodeMap<Stmt, std::pair<int32_t, int32_t>> range;   // [begin, end) pcs
+    NodeMap<Stmt, bool> fast;                           // loops lowered to I_FASTLOOP
 
     // An innermost loop whose body is only accesses (whose indices the count
     // pass need not evaluate) and syncs, each index linear in the variables
@@ -543,9 +621,19 @@ struct Splitter {
 
     void list(const Stmt &seq, i128 budget)
     {
-        std::vector<const Stmt *> xs;
-        if (seq.op == SOp::Seq) for (auto &it : seq.items) xs.push_back(it.get());
-        else xs.push_back(&seq);
+        // the statements of the list (a sequence's items, else the statement itself)
+        struct Stmts {
+            const Stmt &s;
+            struct It {
+                const Stmt &s;
+                size_t i;
+                const Stmt *operator*() const { return s.op == SOp::Seq ? s.items[i].get() : &s; }
+                It &operator++() { i++; return *this; }
+                bool operator!=(const It &o) const { return i != o.i; }
+            };
+            It begin() const { return It{s, 0}; }
+            It end() const { return It{s, s.op == SOp::Seq ? s.items.size() : 1}; }
+        } xs{seq};
         i128 total = 0;
         for (const Stmt *x : xs) total = sat(total + an.work.at(x).steps);
         int32_t run_b = -1, run_e = -1;
@@ -701,7 +789,7 @@ Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, 
         if (t->else_s) todo.push_back(t->else_s.get());
     }
     bool may_fail = an.maybe_div0;
-    for (auto &kv : an.count_eval) may_fail = may_fail || kv.second;
+    may_fail = may_fail || an.any_count_eval;
     out.static_phases = constant_syncs && !may_fail && iphase.size() == items.size();
     for (uint64_t ph : iphase) if (ph > w.syncs) out.static_phases = false;
     if (out.static_phases) out.item_phase.assign(iphase.begin(), iphase.end());

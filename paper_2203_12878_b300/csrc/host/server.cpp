@@ -42,8 +42,7 @@ public:
     {
         for (int i = 0; i < kWorkers; i++) {
             std::unique_ptr<Lane> l(new Lane);
-            if (cudaStreamCreateWithFlags(&l->s, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaMallocHost((void **)&l->pinned, sizeof(Control)) != cudaSuccess) {
+            if (cudaStreamCreateWithFlags(&l->s, cudaStreamNonBlocking) != cudaSuccess) {
                 cudaGetLastError();
                 return S_CUDA;
             }
@@ -61,7 +60,6 @@ public:
         cudaSetDevice(ctx_->device);
         for (auto &l : lanes_) {
             if (l->s) { cudaStreamSynchronize(l->s); cudaStreamDestroy(l->s); }
-            if (l->pinned) cudaFreeHost(l->pinned);
         }
     }
 
@@ -142,7 +140,6 @@ private:
     struct Lane {
         DeviceBatch dev;
         cudaStream_t s = nullptr;
-        Control *pinned = nullptr;
     };
 
     drf_ctx *ctx_;
@@ -211,7 +208,7 @@ private:
         Error e = pack_batch(ps, bh);
         std::vector<DevResult> dr;
         if (e.ok()) {
-            int st = run_batch(lane.dev, lane.pinned, ctx_->sms, lane.s, bh, dr, err);
+            int st = run_batch(lane.dev, ctx_->sms, lane.s, bh, dr, err);
             if (st == S_OK) {
                 for (size_t i = 0; i < round.size(); i++) to_public(dr[i], &res[i]);
                 return;
@@ -223,7 +220,7 @@ private:
         for (size_t i = 0; i < round.size(); i++) {
             Error ei = pack_batch({ps[i]}, bh);
             int st = ei.status;
-            if (ei.ok()) st = run_batch(lane.dev, lane.pinned, ctx_->sms, lane.s, bh, dr, err);
+            if (ei.ok()) st = run_batch(lane.dev, ctx_->sms, lane.s, bh, dr, err);
             if (st == S_OK) to_public(dr[0], &res[i]);
             else { res[i] = drf_result{}; res[i].status = st; res[i].verdict = -1; }
         }

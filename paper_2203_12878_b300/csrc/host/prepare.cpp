@@ -742,7 +742,13 @@ Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, 
     uint64_t groups = nthreads ? (nthreads + 31) / 32 : 1;
     i128 k_want = std::max<i128>(1, ((i128)opts.desired_warp_items + groups - 1) / groups);
     i128 k_work = std::max<i128>(1, total / std::max<uint64_t>(1, opts.min_item_steps));
-    i128 K = std::min<i128>(std::min(k_want, k_work), opts.max_items);
+    // a small protocol is still cut into enough items for about a sixteenth
+    // of the desired warp items (one wave of warps for a lone check), even
+    // when that makes its items short: its time is the chain of dependent
+    // steps one lane runs, not the steps' total
+    const i128 k_floor = std::min<i128>(((i128)opts.desired_warp_items / 16 + groups - 1) / groups,
+                                        total / std::max<uint64_t>(1, opts.min_short_item_steps));
+    i128 K = std::min<i128>(std::min(k_want, std::max(k_work, k_floor)), opts.max_items);
     if ((i128)K * nthreads > ((i128)1 << 27)) K = std::max<i128>(1, ((i128)1 << 27) / std::max<uint32_t>(1, nthreads));
 
     std::vector<ItemDesc> items;

@@ -17,6 +17,7 @@ struct PrepareOpts {
     // interpreter steps per lane an item should carry
     uint64_t desired_warp_items = 148 * 128;
     uint64_t min_item_steps = 64;
+    uint64_t min_short_item_steps = 4;   // items of a small protocol (cut for parallelism)
     uint32_t max_items = 1u << 14;
 };
 

@@ -13,6 +13,7 @@
 // alone.
 #include "server.h"
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -79,8 +80,17 @@ public:
         if (!bc || !b || !ticket) return S_INVALID_ARG;
         std::unique_ptr<Request> r(new Request);
         r->t_submit = Clock::now();
+        // cut a request for its share of a round: alone (no backlog) as finely
+        // as a lone check, whose latency is its longest lane; behind a backlog
+        // it will share its round with the requests ahead of it, and coarser
+        // items keep preparation (on the caller's thread) cheap
+        size_t backlog;
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            backlog = pending_.size();
+        }
         PrepareOpts po;
-        po.desired_warp_items = (uint64_t)ctx_->sms * 2;      // a request shares its round with others
+        po.desired_warp_items = std::max<uint64_t>((uint64_t)ctx_->sms * 2, (uint64_t)ctx_->sms * 128 / (1 + backlog));
         Error e = prepare(bc, len, b->nthreads, b->nlocs, b->loc_cells, b->nparams, b->params, po, r->prep);
         std::lock_guard<std::mutex> g(mu_);
         if (stopping_) return S_BUSY;

@@ -462,10 +462,18 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             }
         }
     }
-    if (CELL && hit) {
+    if (CELL) {
+        // the warp's lanes that share a hit word set their bits with one
+        // update (a race's cell is usually hit by many threads)
         const uint64_t b = P.tid_off + tid;
-        atomicOr(&a.hit_acc[b >> 5], 1u << (uint32_t)(b & 31));
-        if (hit & 2) atomicOr(&a.hit_wr[b >> 5], 1u << (uint32_t)(b & 31));
+        const unsigned grp = __match_any_sync(kFull, b >> 5);
+        const uint32_t bit = 1u << (uint32_t)(b & 31);
+        const uint32_t acc = __reduce_or_sync(grp, (hit & 1u) ? bit : 0u);
+        const uint32_t wr = __reduce_or_sync(grp, (hit & 2u) ? bit : 0u);
+        if (lane == (uint32_t)(__ffs(grp) - 1)) {
+            if (acc) atomicOr(&a.hit_acc[b >> 5], acc);
+            if (wr) atomicOr(&a.hit_wr[b >> 5], wr);
+        }
     }
 }
 

@@ -680,6 +680,7 @@ static __device__ __forceinline__ void put_warp_cur(uint32_t *table, uint32_t *t
 )DRF";
 
 constexpr size_t kMaxConstItems = 1024;  // items whose schedule and positions are compiled in
+constexpr uint64_t kMaxPhaseRanges = 1u << 16;   // phases whose item ranges are compiled in
 
 }  // namespace
 
@@ -739,13 +740,38 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
         // cache while L1 keeps it after the first reads
         o << "static __device__ const uint32_t c_ord[" << K << "] = {";   // item | shape << 16, in schedule order
         for (uint32_t pos = 0; pos < K; pos++) o << (pos ? "," : "") << (order[pos] | ((uint32_t)item_shape[order[pos]] << 16)) << "u";
-        o << "};\nstatic __device__ const IJ c_it[" << K << "] = {";
+        o << "};\nstatic __device__ const IJ c_it[" << K << "] = {";   // per item; pad: its shape
         for (uint32_t k = 0; k < K; k++) {
             const ItemDesc &it = p.items[k];
             o << (k ? "," : "") << "{{" << it.j[0] << "u," << it.j[1] << "u," << it.j[2] << "u," << it.j[3] << "u},"
               << it.chunk << "u," << (stat ? p.item_phase[k] : 0u) << "u,"
-              << (stat ? (k + 1 < K ? p.item_phase[k + 1] : (uint32_t)p.max_syncs) : 0u) << "u,0u}";
+              << (stat ? (k + 1 < K ? p.item_phase[k + 1] : (uint32_t)p.max_syncs) : 0u) << "u,"
+              << item_shape[k] << "u}";
         }
+        o << "};\n";
+    }
+    // With static phases, items in program order start (and end) in
+    // non-decreasing phases, so the items that run any part of phase P are
+    // one range [c_plo[P], c_phi[P]): the witness pass visits only the
+    // range of the witness cell's phase.
+    const uint64_t nph = (uint64_t)p.max_syncs + 1;
+    const bool ranged = stat && nph <= kMaxPhaseRanges;
+    if (ranged) {
+        // item k runs phases [item_phase[k], end_phase(k)]
+        auto end_phase = [&](uint32_t k) -> uint64_t { return k + 1 < K ? p.item_phase[k + 1] : p.max_syncs; };
+        std::vector<uint32_t> plo(nph), phi(nph);
+        uint32_t lo = 0, hi = 0;
+        for (uint64_t ph = 0; ph < nph; ph++) {
+            while (lo < K && end_phase(lo) < ph) lo++;
+            if (hi < lo) hi = lo;
+            while (hi < K && p.item_phase[hi] <= ph) hi++;
+            plo[ph] = lo;
+            phi[ph] = hi;
+        }
+        o << "static __device__ const uint32_t c_plo[" << nph << "] = {";
+        for (uint64_t ph = 0; ph < nph; ph++) o << (ph ? "," : "") << plo[ph] << "u";
+        o << "};\nstatic __device__ const uint32_t c_phi[" << nph << "] = {";
+        for (uint64_t ph = 0; ph < nph; ph++) o << (ph ? "," : "") << phi[ph] << "u";
         o << "};\n";
     }
     const Mode modes[] = {GM_COUNT, GM_TABLE, GM_CELL};
@@ -876,18 +902,47 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
     o << "        static const unsigned long long cb[" << std::max<uint32_t>(1, d.nlocs) << "] = {";
     for (uint32_t l = 0; l < std::max<uint32_t>(1, d.nlocs); l++) o << (l ? "," : "") << ulit(l < d.nlocs ? b.cbase.at(l) : 0);
     o << "};\n"
-      << "        tg.phase = (uint32_t)row;\n        tg.loc = l;\n        tg.idx = c - cb[l];\n    }\n"
-      << loop_head
-      << (stat ? "        if (it.phase > tg.phase || it.phase_end < tg.phase || !alive) continue;\n"
-                 "        const uint32_t phase = it.phase;\n"
-               : "        if (!alive) continue;\n        const uint32_t phase = a.phs[li];\n        if (phase > tg.phase) continue;\n")
-      << R"DRF(        uint32_t hit = 0;
+      << "        tg.phase = (uint32_t)row;\n        tg.loc = l;\n        tg.idx = c - cb[l];\n    }\n";
+    if (ranged) {
+        // the items of the witness phase only, their thread groups consecutive
+        o << "    if (tg.phase >= " << nph << "u) return;\n"
+          << "    const uint32_t klo = __ldg(&c_plo[tg.phase]), nw = (__ldg(&c_phi[tg.phase]) - klo) * " << G << "u;\n"
+          << "    const uint32_t lane = threadIdx.x & 31;\n"
+          << "    const uint32_t warps = gridDim.x * (blockDim.x / 32);\n"
+          << "    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nw; w += warps) {\n"
+          << "        const uint32_t kk = w / " << G << "u, k = klo + kk, g = w - kk * " << G << "u;\n"
+          << "        IJ it;\n"
+          << "        uint32_t shp;\n"
+          << "        {\n"
+          << "            const uint4 w0 = __ldg(reinterpret_cast<const uint4 *>(&c_it[k]));\n"
+          << "            const uint4 w1 = __ldg(reinterpret_cast<const uint4 *>(&c_it[k]) + 1);\n"
+          << "            it.j[0] = w0.x; it.j[1] = w0.y; it.j[2] = w0.z; it.j[3] = w0.w;\n"
+          << "            it.chunk = w1.x; it.phase = w1.y; it.phase_end = w1.z; it.pad = 0;\n"
+          << "            shp = w1.w;\n"
+          << "        }\n"
+          << "        const uint32_t tid = g * 32 + lane;\n"
+          << "        if (tid >= " << T << ") continue;\n"
+          << "        const uint32_t phase = it.phase;\n";
+    } else {
+        o << loop_head
+          << (stat ? "        if (it.phase > tg.phase || it.phase_end < tg.phase || !alive) continue;\n"
+                     "        const uint32_t phase = it.phase;\n"
+                   : "        if (!alive) continue;\n        const uint32_t phase = a.phs[li];\n        if (phase > tg.phase) continue;\n");
+    }
+    o << R"DRF(        uint32_t hit = 0;
 )DRF"
       << dispatch("s#_cell(it, tid, phase, tg, hit)")
-      << "        if (hit) {\n"
-      << "            const uint64_t bb = " << TID_OFF << " + tid;\n"
-      << R"DRF(            atomicOr(&a.hit_acc[bb >> 5], 1u << (uint32_t)(bb & 31));
-            if (hit & 2) atomicOr(&a.hit_wr[bb >> 5], 1u << (uint32_t)(bb & 31));
+      << "        const uint64_t bb = " << TID_OFF << " + tid;\n"
+      << R"DRF(        // the lanes running together that share a hit word set their bits
+        // with one update (a race's cell is usually hit by many threads)
+        const unsigned am = __activemask();
+        const unsigned grp = __match_any_sync(am, bb >> 5);
+        const uint32_t bit = 1u << (uint32_t)(bb & 31);
+        const uint32_t acc = __reduce_or_sync(grp, (hit & 1u) ? bit : 0u);
+        const uint32_t wr = __reduce_or_sync(grp, (hit & 2u) ? bit : 0u);
+        if ((threadIdx.x & 31) == (uint32_t)(__ffs(grp) - 1)) {
+            if (acc) atomicOr(&a.hit_acc[bb >> 5], acc);
+            if (wr) atomicOr(&a.hit_wr[bb >> 5], wr);
         }
     }
 }

@@ -1316,8 +1316,12 @@ static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms
     if (j && j->cell) launch_jit(j->cell, a, j, s, sms);
     else launch_interp_pdl<M_CELL>(a, s, sms);
     mark(ev, nev, s);
-    launch_pdl(k_finalize<true>, dim3(a.nprotos), dim3(kFinalizeThreads), s, a);
-    mark(ev, nev, s);
+    // specialized kernels with static phases write the result from the
+    // witness pass's last block
+    if (!(j && j->cell && j->static_phases)) {
+        launch_pdl(k_finalize<true>, dim3(a.nprotos), dim3(kFinalizeThreads), s, a);
+        mark(ev, nev, s);
+    }
     return cudaGetLastError();
 }
 
@@ -1354,13 +1358,14 @@ int stage_names(const char **names, int cap, uint32_t passes, uint32_t path, boo
     all[n++] = "init";
     if (!static_phases) { all[n++] = "count"; all[n++] = "scan"; }
     if (path == PATH_TABLE) {
-        all[n++] = "table"; all[n++] = "tscan"; all[n++] = "witness";
+        all[n++] = "table"; all[n++] = "tscan";
+        all[n++] = static_phases ? "witness+finalize" : "witness";
     } else {
         all[n++] = "emit";
         for (uint32_t q = 0; q < passes && q < (uint32_t)kMaxPasses; q++) all[n++] = radix[q];
         all[n++] = "detect";
     }
-    all[n++] = "finalize";
+    if (!(static_phases && path == PATH_TABLE)) all[n++] = "finalize";
     for (int i = 0; i < n && i < cap; i++) names[i] = all[i];
     return n;
 }

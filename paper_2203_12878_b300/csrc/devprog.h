@@ -143,6 +143,8 @@ struct Control {
     unsigned int detect_tiles;
     unsigned int flags;                // CF_* internal failures
     unsigned long long touched;        // owner-table blocks listed this launch
+    unsigned int blocks_done;          // blocks of the witness pass that have finished
+    unsigned int pad;
 };
 
 enum : unsigned {

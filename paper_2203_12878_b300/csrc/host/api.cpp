@@ -713,7 +713,7 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
     if (sort_passes) *sort_passes = table ? 0 : plan->host.L.passes;
     if (kernels_per_launch) {
         uint32_t widths = plan->dev.args.has_narrow + plan->dev.args.has_wide;
-        if (table && plan->dev.jit.static_phases) *kernels_per_launch = 6;   // init, table, tlist, tscan, witness, finalize
+        if (table && plan->dev.jit.static_phases) *kernels_per_launch = 5;   // init, table, tlist, tscan, witness + finalize
         else if (table) *kernels_per_launch = 3 * widths + 5;   // init, 3x interp, scan, tlist, tscan, finalize
         else *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes;   // init, 2x interp, scan, passes, detect, resolve, finalize
     }

@@ -171,10 +171,11 @@ class Gen {
         }
         for (size_t i = 0; i < S.size(); i++) {
             if (S[i].uniform) continue;
-            body_ << "        if (" << S[i].k << " && " << S[i].c << " == 0u) { if (" << n[i]
-                  << " == 0u) drf::owner_touch(a.touch, " << S[i].o << ", drf::kTabBlockLog); else { const uint32_t nd = "
+            body_ << "        if (" << S[i].k << " && " << S[i].c << " == 0u && " << n[i] << " != 0u) { const uint32_t nd = "
                   << "drf::owner_need(" << n[i] << ", tid, " << (S[i].write ? 1 : 0) << "u); if (nd) atomicOr(tab + "
-                  << S[i].o << ", nd); } }\n";
+                  << S[i].o << ", nd); }\n";
+            body_ << "        touch_created(a.touch, " << S[i].o << ", " << S[i].k << " && " << S[i].c << " == 0u && " << n[i]
+                  << " == 0u);\n";
         }
         for (size_t i = 0; i < S.size(); i++)
             if (S[i].uniform)
@@ -656,6 +657,27 @@ static __device__ __forceinline__ void put_cur(uint32_t *table, uint32_t *touch,
     if (drf::owner_put(table + off, cur, tid, w)) drf::owner_touch(touch, off, drf::kTabBlockLog);
 }
 
+// Keeps the two smallest distinct values seen in f < s.
+static __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t x)
+{
+    if (x == f || x == s) return;
+    if (x < f) { s = f; f = x; }
+    else if (x < s) s = x;
+}
+
+// Marks the blocks of the records that the lanes running together created
+// (`created`): lanes whose blocks share a touch word set their bits with one
+// update -- a warp's new records usually lie in one word's blocks.
+static __device__ __forceinline__ void touch_created(uint32_t *touch, toff_t off, bool created)
+{
+    const unsigned am = __activemask();
+    if (!__any_sync(am, created)) return;
+    const uint32_t bid = (uint32_t)(off >> drf::kTabBlockLog);
+    const unsigned grp = __match_any_sync(am, bid >> 5);
+    const uint32_t bits = __reduce_or_sync(grp, created ? 1u << (bid & 31) : 0u);
+    if ((threadIdx.x & 31) == (uint32_t)(__ffs(grp) - 1) && bits) atomicOr(touch + (bid >> 5), bits);
+}
+
 // An access whose index does not read tid: the lanes running together
 // usually hit one cell, and then the lowest of them updates it for all (two
 // or more lanes are two or more threads).  Lanes that disagree update their
@@ -889,11 +911,16 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
           << dispatch("s#_table(a, it, tid, phase, nacc)")
           << "    }\n}\n";
     }
-    // witness pass: which threads access / write the first racy cell
+    // witness pass: which threads access / write the first racy cell; with
+    // static phases its last block to finish also writes the result (the
+    // finalize pass of the interpreted pipeline), so the launch needs no
+    // further kernel
     o << "extern \"C\" __global__ void __launch_bounds__(256) drf_cell" << sig
       << "    const unsigned long long bp = a.best_pos[0];\n"
-      << "    if (bp == ~0ull || a.err_key[0] != ~0ull || a.div_tid[0] != 0xFFFFFFFFu) return;\n"
-      << "    CellTarget tg;\n    {\n"
+      << "    const bool live = !(bp == ~0ull || a.err_key[0] != ~0ull || a.div_tid[0] != 0xFFFFFFFFu);\n"
+      << "    CellTarget tg{};\n"
+      << "    if (live) {\n"
+      << "    {\n"
       << "        const unsigned long long rel = bp - " << ulit(d.tab_off) << ";\n"
       << "        const unsigned long long row = rel / " << ulit(d.cells_sum ? d.cells_sum : 1) << ";\n"
       << "        const unsigned long long c = rel - row * " << ulit(d.cells_sum) << ";\n"
@@ -905,8 +932,8 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
       << "        tg.phase = (uint32_t)row;\n        tg.loc = l;\n        tg.idx = c - cb[l];\n    }\n";
     if (ranged) {
         // the items of the witness phase only, their thread groups consecutive
-        o << "    if (tg.phase >= " << nph << "u) return;\n"
-          << "    const uint32_t klo = __ldg(&c_plo[tg.phase]), nw = (__ldg(&c_phi[tg.phase]) - klo) * " << G << "u;\n"
+        o << "    const uint32_t klo = tg.phase < " << nph << "u ? __ldg(&c_plo[tg.phase]) : 0u;\n"
+          << "    const uint32_t nw = tg.phase < " << nph << "u ? (__ldg(&c_phi[tg.phase]) - klo) * " << G << "u : 0u;\n"
           << "    const uint32_t lane = threadIdx.x & 31;\n"
           << "    const uint32_t warps = gridDim.x * (blockDim.x / 32);\n"
           << "    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nw; w += warps) {\n"
@@ -945,8 +972,74 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
             if (wr) atomicOr(&a.hit_wr[bb >> 5], wr);
         }
     }
-}
+    }
 )DRF";
+    if (stat) {
+        // the last block: the two smallest accessors and writers of the cell
+        // from the hit bits (static phases: no evaluation error or barrier
+        // divergence can occur), then the protocol's result
+        const uint64_t b0 = d.tid_off, b1 = d.tid_off + d.nthreads;
+        o << "    __shared__ unsigned int s_last;\n"
+          << "    __shared__ uint32_t s_red[4][8];\n"
+          << "    __syncthreads();\n"
+          << "    if (threadIdx.x == 0) {\n"
+          << "        __threadfence();\n"
+          << "        s_last = atomicAdd(&a.ctrl->blocks_done, 1u) == gridDim.x - 1 ? 1u : 0u;\n"
+          << "    }\n"
+          << "    __syncthreads();\n"
+          << "    if (!s_last) return;\n"
+          << "    __threadfence();\n"
+          << "    if (threadIdx.x == 0 && a.nkeys != drf::kUncounted && __ldcg(&a.ctrl->total) != a.nkeys)\n"
+          << "        atomicOr(&a.ctrl->flags, drf::CF_COUNT_MISMATCH);\n"
+          << "    drf::DevResult r = {};\n"
+          << "    r.tuples = __ldcg(&a.ptuples[0]);\n"
+          << "    r.phases = " << (uint32_t)p.max_syncs << "u + 1u;\n"
+          << "    r.sync_count_0 = " << (uint32_t)p.max_syncs << "u;\n"
+          << "    if (!live) {\n"
+          << "        r.verdict = 0;\n"
+          << "        if (threadIdx.x == 0) a.results[0] = r;\n"
+          << "        return;\n"
+          << "    }\n"
+          << "    uint32_t t0 = 0xFFFFFFFFu, t1 = 0xFFFFFFFFu, w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;\n"
+          // (a protocol without threads has no racy cell: the loop is for T >= 1)
+          << "    for (uint64_t wd = " << ulit(b0 >> 5) << " + threadIdx.x; wd <= " << ulit(b1 > b0 ? (b1 - 1) >> 5 : 0)
+          << " && " << (b1 > b0 ? "true" : "false") << "; wd += blockDim.x) {\n"
+          << "        uint32_t ma = __ldcg(&a.hit_acc[wd]), mw = __ldcg(&a.hit_wr[wd]);\n"
+          << "        const uint64_t lo = wd * 32;\n"
+          << "        if (lo < " << ulit(b0) << ") { ma &= ~0u << (uint32_t)(" << ulit(b0) << " - lo); mw &= ~0u << (uint32_t)("
+          << ulit(b0) << " - lo); }\n"
+          << "        if (lo + 32 > " << ulit(b1) << ") { const uint32_t keep = (1u << (uint32_t)(" << ulit(b1)
+          << " - lo)) - 1; ma &= keep; mw &= keep; }\n"
+          << "        for (int q = 0; q < 2 && ma; q++) { two_smallest(t0, t1, (uint32_t)(lo + (uint32_t)(__ffs(ma) - 1) - "
+          << ulit(b0) << ")); ma &= ma - 1; }\n"
+          << "        for (int q = 0; q < 2 && mw; q++) { two_smallest(w0, w1, (uint32_t)(lo + (uint32_t)(__ffs(mw) - 1) - "
+          << ulit(b0) << ")); mw &= mw - 1; }\n"
+          << "    }\n"
+          << R"DRF(    for (int o = 16; o; o >>= 1) {
+        const uint32_t u0 = __shfl_xor_sync(0xFFFFFFFFu, t0, o), u1 = __shfl_xor_sync(0xFFFFFFFFu, t1, o);
+        const uint32_t v0 = __shfl_xor_sync(0xFFFFFFFFu, w0, o), v1 = __shfl_xor_sync(0xFFFFFFFFu, w1, o);
+        two_smallest(t0, t1, u0); two_smallest(t0, t1, u1);
+        two_smallest(w0, w1, v0); two_smallest(w0, w1, v1);
+    }
+    const uint32_t wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_red[0][wid] = t0; s_red[1][wid] = t1; s_red[2][wid] = w0; s_red[3][wid] = w1; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (uint32_t q = 1; q < blockDim.x / 32; q++) {
+        two_smallest(t0, t1, s_red[0][q]); two_smallest(t0, t1, s_red[1][q]);
+        two_smallest(w0, w1, s_red[2][q]); two_smallest(w0, w1, s_red[3][q]);
+    }
+    r.verdict = 1;
+    r.phase = tg.phase;
+    r.loc = tg.loc;
+    r.index = tg.idx;
+    r.tid_i = t0;
+    if (w0 == t0) { r.tid_j = t1; r.i_writes = 1; r.j_writes = (w1 == t1); }
+    else { r.tid_j = w0; r.i_writes = 0; r.j_writes = 1; }
+    a.results[0] = r;
+)DRF";
+    }
+    o << "}\n";
     src = o.str();
     if (src.size() > kMaxSourceBytes) return Error::make(S_LIMIT, "specialized source too large");
     return Error{};

@@ -72,17 +72,26 @@ template <typename V>
 __device__ bool eval(const uint64_t *__restrict__ xc, int32_t off, uint32_t tid, const V *vars, V &out)
 {
     using U = typename Unsigned<V>::T;
+    // the top of the stack lives in a register and the entries below it in
+    // st (st[d - 2] is the one under the top): the usual index -- one affine
+    // form, then a remainder or mask -- never touches st
     V st[kMaxStack];
-    int sp = 0;
+    V top = 0;
+    int d = 0;                                   // stack depth
+    auto push = [&](V x) {
+        if (d) st[d - 1] = top;
+        top = x;
+        d++;
+    };
     const uint64_t *p = xc + off;
     while (true) {
         uint64_t w = __ldg(p++);
         uint32_t op = (uint32_t)(w & 0xff);
         switch (op) {
-        case X_RET: out = st[0]; return true;
-        case X_CONST: st[sp++] = (V)(int64_t)__ldg(p++); break;
-        case X_TID: st[sp++] = (V)tid; break;
-        case X_VAR: st[sp++] = vars[(uint32_t)(w >> 8)]; break;
+        case X_RET: out = top; return true;
+        case X_CONST: push((V)(int64_t)__ldg(p++)); break;
+        case X_TID: push((V)tid); break;
+        case X_VAR: push(vars[(uint32_t)(w >> 8)]); break;
         case X_AFF: {
             uint32_t n = (uint32_t)(w >> 8);
             U acc = 0;
@@ -93,34 +102,44 @@ __device__ bool eval(const uint64_t *__restrict__ xc, int32_t off, uint32_t tid,
                 acc += coef * v;
             }
             acc += (U)__ldg(p++);
-            st[sp++] = (V)acc;
+            push((V)acc);
             break;
         }
-        case X_ADD: sp--; st[sp - 1] = (V)((U)st[sp - 1] + (U)st[sp]); break;
-        case X_SUB: sp--; st[sp - 1] = (V)((U)st[sp - 1] - (U)st[sp]); break;
-        case X_MUL: sp--; st[sp - 1] = (V)((U)st[sp - 1] * (U)st[sp]); break;
-        case X_MIN: sp--; st[sp - 1] = st[sp] < st[sp - 1] ? st[sp] : st[sp - 1]; break;
-        case X_MAX: sp--; st[sp - 1] = st[sp] > st[sp - 1] ? st[sp] : st[sp - 1]; break;
-        case X_NEG: st[sp - 1] = (V)(0 - (U)st[sp - 1]); break;
-        case X_DIV:
-        case X_MOD: {
-            V b = st[--sp];
-            if (b == 0) return false;
-            st[sp - 1] = op == X_DIV ? floor_div<V, U>(st[sp - 1], b) : euclid_mod<V, U>(st[sp - 1], b);
+        case X_NEG: top = (V)(0 - (U)top); break;
+        case X_DIVC: top = floor_div<V, U>(top, (V)(int64_t)__ldg(p++)); break;
+        case X_MODC: top = euclid_mod<V, U>(top, (V)(int64_t)__ldg(p++)); break;
+        case X_MASK: top = (V)((U)top & (U)__ldg(p++)); break;
+        case X_NOT: top = top == 0; break;
+        case X_ADD: case X_SUB: case X_MUL: case X_MIN: case X_MAX: case X_DIV: case X_MOD:
+        case X_EQ: case X_NE: case X_LT: case X_LE: case X_GT: case X_GE: case X_AND: case X_OR: {
+            // binary: a (under the top) op b (the top)
+            const V a = st[d - 2], b = top;
+            d--;
+            switch (op) {
+            case X_ADD: top = (V)((U)a + (U)b); break;
+            case X_SUB: top = (V)((U)a - (U)b); break;
+            case X_MUL: top = (V)((U)a * (U)b); break;
+            case X_MIN: top = b < a ? b : a; break;
+            case X_MAX: top = b > a ? b : a; break;
+            case X_DIV:
+                if (b == 0) return false;
+                top = floor_div<V, U>(a, b);
+                break;
+            case X_MOD:
+                if (b == 0) return false;
+                top = euclid_mod<V, U>(a, b);
+                break;
+            case X_EQ: top = a == b; break;
+            case X_NE: top = a != b; break;
+            case X_LT: top = a < b; break;
+            case X_LE: top = a <= b; break;
+            case X_GT: top = a > b; break;
+            case X_GE: top = a >= b; break;
+            case X_AND: top = (a != 0) & (b != 0); break;
+            case X_OR: top = (a != 0) | (b != 0); break;
+            }
             break;
         }
-        case X_DIVC: st[sp - 1] = floor_div<V, U>(st[sp - 1], (V)(int64_t)__ldg(p++)); break;
-        case X_MODC: st[sp - 1] = euclid_mod<V, U>(st[sp - 1], (V)(int64_t)__ldg(p++)); break;
-        case X_MASK: st[sp - 1] = (V)((U)st[sp - 1] & (U)__ldg(p++)); break;
-        case X_EQ: sp--; st[sp - 1] = st[sp - 1] == st[sp]; break;
-        case X_NE: sp--; st[sp - 1] = st[sp - 1] != st[sp]; break;
-        case X_LT: sp--; st[sp - 1] = st[sp - 1] < st[sp]; break;
-        case X_LE: sp--; st[sp - 1] = st[sp - 1] <= st[sp]; break;
-        case X_GT: sp--; st[sp - 1] = st[sp - 1] > st[sp]; break;
-        case X_GE: sp--; st[sp - 1] = st[sp - 1] >= st[sp]; break;
-        case X_AND: sp--; st[sp - 1] = (st[sp - 1] != 0) & (st[sp] != 0); break;
-        case X_OR: sp--; st[sp - 1] = (st[sp - 1] != 0) | (st[sp] != 0); break;
-        case X_NOT: st[sp - 1] = st[sp - 1] == 0; break;
         default: return false;   // not produced by the lowering
         }
     }
@@ -291,7 +310,11 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
         case I_ACCESS: {
             bool ok = ex;
             V idx = 0;
-            if (ex && (PHASED || (in.a & AF_EVAL_IN_COUNT))) {
+            // the witness pass runs only protocols none of whose accesses
+            // fails, and needs the index only of accesses in the cell's phase
+            // and array
+            const bool need = CELL ? (phase == tg.phase && in.b == tg.loc) : (PHASED || (in.a & AF_EVAL_IN_COUNT));
+            if (ex && need) {
                 if (!eval<V>(xc, in.c, tid, vars, idx)) { err = kErrDiv0; ok = false; }
                 else if (idx < 0 || (uint64_t)(U)idx >= __ldg(cells + in.b)) { err = kErrOob; ok = false; }
             }
@@ -554,9 +577,12 @@ __global__ void __launch_bounds__(256) k_interp(BatchArgs a)
                 if (tg_live) tg = decode_cell(a, P, bp);
             }
             if (!tg_live) continue;
-            // nothing to do for an item that starts after the witness phase in every lane
+            // nothing to do for an item that starts after the witness phase,
+            // or ends before it (the next item starts before it), in every lane
             const uint32_t tid = wi.g * 32 + (threadIdx.x & 31);
-            const bool reach = tid < P.nthreads && a.phs[P.lane_off + (uint64_t)wi.k * P.nthreads + tid] <= tg.phase;
+            const uint64_t lk = P.lane_off + (uint64_t)wi.k * P.nthreads + tid;
+            const bool reach = tid < P.nthreads && a.phs[lk] <= tg.phase &&
+                               (wi.k + 1 == P.nitems || a.phs[lk + P.nthreads] >= tg.phase);
             if (!__any_sync(kFull, reach)) continue;
         }
         const ItemDesc it = a.items[P.item_off + wi.k];

@@ -1287,8 +1287,16 @@ static void launch_jit(const void *k, const BatchArgs &a, const JitLaunch *j, cu
     cudaLaunchKernelExC(&c.cfg, k, params);
 }
 
+// The interpreter, and specialized kernels without a compiled-in schedule,
+// read the batch's warp-item array: a batch loaded without it cannot run them.
+static bool schedule_missing(const BatchArgs &a, const JitLaunch *j)
+{
+    return a.nwitems && !a.witems && !(j && j->csched);
+}
+
 cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev, const JitLaunch *j)
 {
+    if (schedule_missing(a, j)) return cudaErrorInvalidValue;
     uint64_t init_n = a.nprotos;
     if (init_n < (uint64_t)kMaxPasses * kRadixBins) init_n = (uint64_t)kMaxPasses * kRadixBins;
     if (init_n < a.nwblocks) init_n = a.nwblocks;
@@ -1353,6 +1361,7 @@ static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms
 
 cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev, const JitLaunch *j)
 {
+    if (schedule_missing(a, j)) return cudaErrorInvalidValue;
     if (a.path == PATH_TABLE) return launch_back_table(a, s, sms, ev, nev, j);
     launch_interp<M_EMIT>(a, s, sms);
     mark(ev, nev, s);

@@ -25,6 +25,9 @@ struct JitLaunch {
     // The kernels take every item's phase as a constant and the table pass
     // counts the tuples: the count and scan passes are left out.
     bool static_phases = false;
+    // The warp-item schedule is compiled in: the kernels do not read the
+    // batch's warp-item array.
+    bool csched = false;
 };
 
 // Stage launchers (all asynchronous on `s`).  Each returns cudaGetLastError().

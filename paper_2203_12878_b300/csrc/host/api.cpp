@@ -39,7 +39,7 @@ Error prepare_one(const uint8_t *bc, size_t len, const drf_bounds *b, const Prep
 // bounds themselves: the kernels depend on nothing else (the preparation
 // options of drf_check are fixed per context).
 const JitEntry *jit_entry(drf_ctx *ctx, const uint8_t *bc, size_t len, const drf_bounds *b, const Prepared &p,
-                          const BatchHost &bh)
+                          BatchHost &bh)
 {
     std::string key;
     auto put = [&key](const void *x, size_t n) { key.append((const char *)x, n); };
@@ -57,9 +57,10 @@ const JitEntry *jit_entry(drf_ctx *ctx, const uint8_t *bc, size_t len, const drf
     std::string src, log;
     std::vector<uint16_t> shapes;
     std::vector<char> cubin;
-    bool stat = false;
+    bool stat = false, csched = false;
     auto mod = std::make_unique<JitModule>();
-    Error e = jit_source(p, bh, src, shapes, &stat);
+    bh.expand_witems();                            // the generator reads the schedule
+    Error e = jit_source(p, bh, src, shapes, &stat, &csched);
     if (e.ok()) e = jit_compile(src, cubin, log);
     if (e.ok()) e = jit_load(cubin, *mod);
     if (e.ok() && (cudaMalloc(&je->shape, std::max<size_t>(shapes.size() * 2, 16)) != cudaSuccess ||
@@ -72,6 +73,7 @@ const JitEntry *jit_entry(drf_ctx *ctx, const uint8_t *bc, size_t len, const drf
         je->launch.cell = (const void *)mod->cell;
         je->launch.shape = (const uint16_t *)je->shape;
         je->launch.static_phases = stat;
+        je->launch.csched = csched;
         je->mod = std::move(mod);
     }
     const JitEntry *out = je.get();
@@ -275,7 +277,11 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     if (valid.empty()) return DRF_OK;
     cudaStream_t s = pick(ctx, stream);
     BatchHost &bh = ctx->host;
-    Error e = pack_batch(valid, bh);
+    // one protocol that may run specialized kernels: the warp-item schedule
+    // is expanded only if the kernels that run read it (compiled-in
+    // schedules do not)
+    const bool jit_try = valid.size() == 1 && (ctx->opts.flags & DRF_OPT_SPECIALIZE) && path_pref_of(ctx->opts) != 1;
+    Error e = pack_batch(valid, bh, !jit_try);
     if (e.status == S_KEY_TOO_WIDE && valid.size() > 1) {
         // the combined key does not fit: check the protocols one by one
         for (size_t j = 0; j < valid.size(); j++) {
@@ -297,11 +303,11 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     // one protocol with DRF_OPT_SPECIALIZE: the kernels compiled for it (the
     // first check of a protocol under given bounds compiles them), when its
     // owner table is of a size the automatic choice would take
-    if (valid.size() == 1 && (ctx->opts.flags & DRF_OPT_SPECIALIZE) && path_pref_of(ctx->opts) != 1 && bh.table_ok &&
-        bh.tuple_bound >= kJitMinTuples && auto_path(bh, bh.tuple_bound) == PATH_TABLE) {
+    if (jit_try && bh.table_ok && bh.tuple_bound >= kJitMinTuples && auto_path(bh, bh.tuple_bound) == PATH_TABLE) {
         const uint32_t i = where[0];
         const JitEntry *je = jit_entry(ctx, bytecodes[i], lens[i], &bounds[i], *valid[0], bh);
         if (je && je->mod) {
+            if (!je->launch.csched) bh.expand_witems();
             int st = run_batch_jit(ctx, bh, je->launch, s, r);
             if (st == S_OK) {
                 to_public(r[0], &out[i]);
@@ -311,6 +317,7 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
             ctx->last_error.clear();                // no room for the table: interpret
         }
     }
+    bh.expand_witems();                            // the interpreter reads the schedule
     int st = run_batch(ctx, bh, s, r);
     if (st) return st;
     for (size_t j = 0; j < where.size(); j++) to_public(r[j], &out[where[j]]);
@@ -451,10 +458,11 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
         std::vector<uint16_t> shapes;
         std::vector<char> cubin;
         auto mod = std::make_unique<JitModule>();
-        bool stat = false;
-        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes, &stat)
+        bool stat = false, csched = false;
+        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes, &stat, &csched)
                    : Error::make(S_INVALID_ARG, "specialization takes a plan of one protocol");
         d.jit.static_phases = stat;
+        d.jit.csched = csched;
         if (e.ok()) e = jit_compile(src, cubin, plan->jit_log);
         if (e.ok()) e = jit_load(cubin, *mod);
         if (e.ok() && (!ensure(d.ishape, std::max<size_t>(shapes.size() * 2, 16), &d.in_use, d.limit) ||

@@ -34,7 +34,16 @@ void release(DevBuf &b, size_t *in_use)
     b.cap = 0;
 }
 
-Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
+void BatchHost::expand_witems()
+{
+    if (expanded()) return;
+    witems.resize(nwitems);
+    WarpItem *wi = witems.data();
+    for (const Run &r : runs)
+        for (uint32_t g = 0; g < r.groups; g++) *wi++ = WarpItem{r.proto, r.k, g};
+}
+
+Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool expand)
 {
     // cleared, not reassigned: a reused image keeps its vectors' capacity
     out.insns.clear();
@@ -44,6 +53,8 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
     out.cells.clear();
     out.cbase.clear();
     out.witems.clear();
+    out.runs.clear();
+    out.nwitems = 0;
     out.ncols = out.lanes = out.tuple_bound = out.table_cells = 0;
     out.L = KeyLayout{};
     out.table_ok = false;
@@ -115,10 +126,10 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out)
     // stable order: equal items keep protocol and item order, and the
     // groups of one item stay consecutive)
     std::stable_sort(ws.begin(), ws.end(), [](const W &x, const W &y) { return x.steps > y.steps; });
-    out.witems.resize(nwitems);
-    WarpItem *wi = out.witems.data();
-    for (auto &w : ws)
-        for (uint32_t g = 0; g < w.groups; g++) *wi++ = WarpItem{w.proto, w.k, g};
+    out.runs.reserve(ws.size());
+    for (auto &w : ws) out.runs.push_back(BatchHost::Run{w.proto, w.k, w.groups});
+    out.nwitems = nwitems;
+    if (expand) out.expand_witems();
     return Error{};
 }
 
@@ -162,7 +173,7 @@ Section section(const std::vector<T> &v, size_t &end)
 Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
 {
     const uint64_t np = b.protos.size();
-    const uint64_t nw = b.witems.size();
+    const uint64_t nw = b.nwitems;
     const uint32_t nwblocks = (uint32_t)std::max<uint64_t>(1, (nw + kWScanPerBlock - 1) / kWScanPerBlock);
     h2d_bytes = 0;
     d2h_bytes = 0;
@@ -230,7 +241,8 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.protos = (const DevProto *)(img + sec[3].off);
     a.cells = (const uint64_t *)(img + sec[4].off);
     a.cbase = (const uint64_t *)(img + sec[5].off);
-    a.witems = (const WarpItem *)(img + sec[6].off);
+    // without its expansion, kernels that read the schedule refuse to launch
+    a.witems = b.expanded() ? (const WarpItem *)(img + sec[6].off) : nullptr;
     a.nwitems = (uint32_t)nw;
     a.nprotos = (uint32_t)np;
     a.has_narrow = a.has_wide = 0;

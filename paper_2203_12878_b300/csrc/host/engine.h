@@ -35,7 +35,15 @@ struct BatchHost {
     std::vector<DevProto> protos;
     std::vector<uint64_t> cells;
     std::vector<uint64_t> cbase;     // per (protocol, array): offset of the array within a table row
+    // the warp-item schedule: runs of (protocol, item, its thread groups),
+    // longest items first; `witems` is its expansion into one entry per
+    // warp item, made only when a kernel reads it (expand_witems)
+    struct Run { uint32_t proto, k, groups; };
+    std::vector<Run> runs;
+    uint64_t nwitems = 0;
     std::vector<WarpItem> witems;
+    bool expanded() const { return witems.size() == nwitems; }
+    void expand_witems();
     uint64_t ncols = 0;
     uint64_t lanes = 0;
     uint64_t tuple_bound = 0;
@@ -50,7 +58,7 @@ constexpr uint64_t kMaxTableBytes = 64ull << 30;
 
 // Packs prepared protocols (all valid) into a batch; fails with
 // S_KEY_TOO_WIDE when the combined key layout exceeds 64 bits.
-Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out);
+Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool expand = true);
 
 // Offset of the results after the control block in a batch's report.
 constexpr size_t kOutResults = 128;

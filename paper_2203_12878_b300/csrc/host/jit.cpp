@@ -707,9 +707,10 @@ constexpr uint64_t kMaxPhaseRanges = 1u << 16;   // phases whose item ranges are
 }  // namespace
 
 Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::vector<uint16_t> &item_shape,
-                 bool *static_phases)
+                 bool *static_phases, bool *compiled_schedule)
 {
     if (static_phases) *static_phases = false;
+    if (compiled_schedule) *compiled_schedule = false;
     if (b.protos.size() != 1) return Error::make(S_INVALID_ARG, "specialization takes a batch of one protocol");
     if (!b.table_ok) return Error::make(S_LIMIT, "the protocol has no owner table");
     const DevProto &d = b.protos[0];
@@ -756,6 +757,7 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
     // and the table pass counts the tuples the count pass would have
     const bool stat = csched && p.static_phases && p.item_phase.size() == K;
     if (static_phases) *static_phases = stat;
+    if (compiled_schedule) *compiled_schedule = csched;
     if (csched) {
         // read-only global data, not __constant__: warps index it by their
         // work item, and a per-item table of kilobytes outgrows the constant

@@ -29,9 +29,12 @@ struct BatchHost;
 // of the code shape its kernels dispatch on.  *static_phases (when not null)
 // is set when the kernels take every item's phase as a constant
 // (Prepared::static_phases): the table pass then needs neither the count
-// nor the scan pass, and counts the tuples itself.
+// nor the scan pass, and counts the tuples itself.  *compiled_schedule (when
+// not null) is set when the warp-item schedule is compiled in: the kernels
+// then read neither the batch's warp-item array nor its item descriptors.
+// `b` must hold its expanded warp-item array.
 Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::vector<uint16_t> &item_shape,
-                 bool *static_phases = nullptr);
+                 bool *static_phases = nullptr, bool *compiled_schedule = nullptr);
 
 // Compiles `src` for sm_103a with NVRTC.  On failure, `log` holds the
 // compiler's log (or why NVRTC is unavailable).

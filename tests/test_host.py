@@ -178,3 +178,18 @@ def test_key_layout_for_workloads():
     p = protogen.config3(0)
     st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile(p.text), p.nthreads, p.cells)
     assert st == "OK" and a["key_bits"] <= 64 and a["tuple_bound"] == p.meta["accesses"]
+
+
+def test_work_items_follow_protocol_size():
+    """A lone check cuts a small protocol into short items, so that its
+    threads' chains of dependent steps spread over about a wave of warps
+    (config 1: one item per iteration of its forS loop), and a large one into
+    items of at least 64 interpreter steps (config 2: 354 items)."""
+    def items(p):
+        st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
+        assert st == "OK"
+        return a["items"]
+    assert items(protogen.config1("drf")) == 8
+    assert items(protogen.config2(0)) == 354
+    # a protocol of a handful of steps per thread is not cut below 4 steps per item
+    assert items(protogen.Protocol("array A;\nwr A[tid];\nrd A[tid];\n", 32, [32], [])) == 1

@@ -164,11 +164,17 @@ def test_drf_check_with_specialized_kernels(oracle):
         big = [protogen.config2(0), protogen.config2(4), protogen.config2(2, "constructed", plant=True),
                protogen.config2(6, "constructed", plant=False), late_phase_race(4096, 600, 500, 7),
                protogen.Protocol("array A;\nforS x in 0 .. 300 {\n  wr A[tid - (tid % 2) + 4096 * x];\n  sync;\n"
-                                 "  rd A[(tid + 1) % 4096 + 4096 * x];\n}\n", 4096, [4096 * 300], [])]
+                                 "  rd A[(tid + 1) % 4096 + 4096 * x];\n}\n", 4096, [4096 * 300], []),
+               # more items than the generator compiles a schedule for: its
+               # kernels read the batch's warp-item array
+               protogen.Protocol("array A;\nforU x in 0 .. 4000 {\n  forU y in 0 .. 20 {\n"
+                                 "    wr A[tid + 64 * ((20 * x + y) % 1000)];\n  }\n}\nsync;\nrd A[(tid + 1) % 64];\n"
+                                 "wr A[tid];\n", 64, [64000], [])]
         small = [protogen.config1("nosync"), protogen.random_small(3), protogen.random_small(11)]
         for p in big:
             assert drf.drf_protocol_analyze(drf.drf_protocol_compile(p.text), p.nthreads, p.cells,
                                             p.params)[1]["tuple_bound"] >= 1 << 21
+        assert drf.drf_protocol_analyze(drf.drf_protocol_compile(big[-1].text), 64, [64000], [])[1]["items"] > 1024
         for rnd in range(2):
             for p in big + small:
                 exp = {k: v for k, v in want(oracle, p).items() if k != "message"}

@@ -545,6 +545,9 @@ def bench_batched(ctx, args):
             "path": "one plan (CUDA graph) over all 4096 protocols; plain = drf_check per protocol"}
 
 
+SERVER_POLL_US = 2000
+
+
 def bench_served(args, rate=5000.0, seconds=2.0, warm_seconds=0.5):
     """Continuous-batching server under a Poisson stream: 90% batched-family
     protocols, 10% one-protocol-family (scaled to 3x10^5 accesses).  The
@@ -560,7 +563,8 @@ def bench_served(args, rate=5000.0, seconds=2.0, warm_seconds=0.5):
     singles = [protogen.config2(s, target=3e5) for s in range(4)]
     pool_s = [(drf.drf_protocol_compile(p.text), p) for p in singles]
     ctx = drf.drf_ctx_create(0)
-    drf.drf_server_start(ctx)
+    # idle workers poll the queue for 2 ms before sleeping (low-latency mode)
+    drf.drf_server_start(ctx, poll_us=SERVER_POLL_US)
     tickets = []
     t0 = time.perf_counter()
     for t, fam in arr:
@@ -587,7 +591,7 @@ def bench_served(args, rate=5000.0, seconds=2.0, warm_seconds=0.5):
     lat.sort()
     return {"rate_req_s": rate, "requests": len(lat), "warmup_s": warm_seconds, "p50_ms": lat[len(lat) // 2],
             "p99_ms": lat[min(len(lat) - 1, int(len(lat) * 0.99))], "throughput_req_s": len(lat) / wall,
-            "rounds": stats["rounds"], "max_round": stats["max_round"]}
+            "rounds": stats["rounds"], "max_round": stats["max_round"], "worker_poll_us": SERVER_POLL_US}
 
 
 # ------------------------------------------------------------- reference --

@@ -401,6 +401,10 @@ typedef struct {
     uint64_t max_round_tuples;   /* tuple budget of one round; 0 = default */
     uint32_t max_round_protocols;/* protocols per round; 0 = default */
     uint32_t max_queue;          /* pending requests before submit returns BUSY; 0 = default */
+    uint32_t poll_us;            /* an idle worker polls the queue this long (keeping its core
+                                    busy) before sleeping: lower latency under moderate load at
+                                    the cost of CPU time; at most 10^6; 0 = sleep at once (default) */
+    uint32_t reserved;           /* must be 0 */
 } drf_server_opts;
 
 int drf_server_start(drf_ctx *ctx, const drf_server_opts *opts);

@@ -14,6 +14,7 @@
 #include "server.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -28,6 +29,14 @@ namespace drf {
 
 namespace {
 using Clock = std::chrono::steady_clock;
+}
+
+// A spin-wait hint to the core.
+inline void cpu_relax()
+{
+#if defined(__x86_64__) || defined(__i386__)
+    __builtin_ia32_pause();
+#endif
 }
 
 class Server {
@@ -107,6 +116,7 @@ public:
         }
         pending_.insert(r->ticket);
         queue_.push_back(std::move(r));
+        queued_.store(queue_.size(), std::memory_order_release);
         cv_work_.notify_one();
         return S_OK;
     }
@@ -149,6 +159,7 @@ private:
     };
     struct Lane {
         DeviceBatch dev;
+        BatchHost host;               // host image of the lane's last round (keeps its capacity)
         cudaStream_t s = nullptr;
     };
 
@@ -163,6 +174,7 @@ private:
     bool stopping_ = false;
     std::vector<std::thread> workers_;
     std::vector<std::unique_ptr<Lane>> lanes_;
+    std::atomic<size_t> queued_{0};   // queue_.size(), for polling workers (written under mu_)
     uint64_t rounds_ = 0, completed_ = 0;
     uint32_t max_round_ = 0;
 
@@ -189,7 +201,21 @@ private:
             std::vector<std::unique_ptr<Request>> round;
             {
                 std::unique_lock<std::mutex> g(mu_);
-                cv_work_.wait(g, [&] { return stopping_ || !queue_.empty(); });
+                // an idle worker first polls the queue for opts_.poll_us (its
+                // core stays awake: a request arriving meanwhile starts at once),
+                // then sleeps until notified
+                bool polled = opts_.poll_us == 0;
+                while (!stopping_ && queue_.empty()) {
+                    if (!polled) {
+                        g.unlock();
+                        const auto until = Clock::now() + std::chrono::microseconds(opts_.poll_us);
+                        while (queued_.load(std::memory_order_acquire) == 0 && Clock::now() < until) cpu_relax();
+                        g.lock();
+                        polled = true;
+                        continue;
+                    }
+                    cv_work_.wait(g);
+                }
                 if (queue_.empty()) return;                 // stopping and drained
                 uint64_t budget = 0;
                 while (!queue_.empty() && round.size() < opts_.max_round_protocols) {
@@ -198,6 +224,7 @@ private:
                     budget += tb;
                     round.push_back(std::move(queue_.front()));
                     queue_.pop_front();
+                    queued_.store(queue_.size(), std::memory_order_release);
                 }
                 rounds_++;
                 if (round.size() > max_round_) max_round_ = (uint32_t)round.size();
@@ -213,7 +240,7 @@ private:
     {
         std::vector<const Prepared *> ps;
         for (auto &r : round) ps.push_back(&r->prep);
-        BatchHost bh;
+        BatchHost &bh = lane.host;
         std::string err;
         Error e = pack_batch(ps, bh);
         std::vector<DevResult> dr;
@@ -250,6 +277,7 @@ int drf_server_start(drf_ctx *ctx, const drf_server_opts *opts)
     if (cudaSetDevice(ctx->device) != cudaSuccess) { cudaGetLastError(); return DRF_E_CUDA; }
     drf_server_opts o{};
     if (opts) o = *opts;
+    if (o.reserved || o.poll_us > 1000000u) return DRF_E_INVALID_ARG;   // polls of at most a second
     Server *s = new Server(ctx, o);
     int st = s->start();
     if (st) { delete s; return st; }

@@ -69,7 +69,7 @@ class drf_analysis(ctypes.Structure):
 
 class drf_server_opts(ctypes.Structure):
     _fields_ = [("max_round_tuples", ctypes.c_uint64), ("max_round_protocols", ctypes.c_uint32),
-                ("max_queue", ctypes.c_uint32)]
+                ("max_queue", ctypes.c_uint32), ("poll_us", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 _lib = None
@@ -441,8 +441,8 @@ def drf_plan_destroy(plan) -> None:
     lib().drf_plan_destroy(plan)
 
 
-def drf_server_start(ctx, max_round_tuples=0, max_round_protocols=0, max_queue=0) -> None:
-    o = drf_server_opts(max_round_tuples, max_round_protocols, max_queue)
+def drf_server_start(ctx, max_round_tuples=0, max_round_protocols=0, max_queue=0, poll_us=0) -> None:
+    o = drf_server_opts(max_round_tuples, max_round_protocols, max_queue, poll_us, 0)
     st = lib().drf_server_start(ctx, ctypes.byref(o))
     if st != 0:
         raise DrfError(st)

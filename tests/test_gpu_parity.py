@@ -226,11 +226,12 @@ def test_key_too_wide_is_reported(ctx):
     assert got["status"] == "KEY_TOO_WIDE"
 
 
-def test_server_results_equal_alone(ctx, oracle):
+@pytest.mark.parametrize("poll_us", [0, 500])
+def test_server_results_equal_alone(ctx, oracle, poll_us):
     ps = protogen.config4(master_seed=3, count=60) + [protogen.config2(1, target=3e5)]
     s = drf.drf_ctx_create(0, flags=PATH_FLAGS[ctx.path])
     try:
-        drf.drf_server_start(s, max_round_tuples=1 << 20)
+        drf.drf_server_start(s, max_round_tuples=1 << 20, poll_us=poll_us)
         tickets = [drf.drf_server_submit(s, drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
                    for p in ps]
         out = [drf.drf_server_poll(s, t, timeout_us=60_000_000) for t in tickets]
@@ -242,6 +243,16 @@ def test_server_results_equal_alone(ctx, oracle):
     for p, o in zip(ps, out):
         assert o is not None
         assert same(drf.result_dict(o[0]), want(oracle, p, ctx))
+
+
+def test_server_rejects_bad_options():
+    s = drf.drf_ctx_create(0)
+    try:
+        with pytest.raises(drf.DrfError) as e:
+            drf.drf_server_start(s, poll_us=2_000_000)     # polls of more than a second
+        assert e.value.name == "INVALID_ARG"
+    finally:
+        drf.drf_ctx_destroy(s)
 
 
 def test_param_sweep_equals_per_value(ctx, oracle):

@@ -35,8 +35,22 @@ i128 sat(i128 v) { return v > kHuge ? kHuge : v; }
 i128 mul_sat(i128 a, i128 b)
 {
     if (a == 0 || b == 0) return 0;
+    if (a > 0 && b > 0) {
+        // counts: no 128-bit division on the common path
+        i128 r;
+        if (__builtin_mul_overflow(a, b, &r)) return kHuge;
+        return sat(r);
+    }
     if (a > kHuge / b) return kHuge;
     return sat(a * b);
+}
+
+// ceil(a / b) for a >= 0, b > 0, in 64-bit arithmetic when both fit.
+i128 div_ceil(i128 a, i128 b)
+{
+    if (a < ((i128)1 << 62) && b < ((i128)1 << 62))
+        return (i128)(((uint64_t)a + (uint64_t)b - 1) / (uint64_t)b);
+    return (a + b - 1) / b;
 }
 
 i128 floor_div(i128 a, i128 b)
@@ -649,7 +663,7 @@ struct Splitter {
             phase = sat(phase + x_syncs);                            // the phase after x
             if (r.first == r.second) continue;                       // no code (skip)
             i128 steps = an.work.at(x).steps;
-            i128 ks = total > 0 ? (budget * steps + total - 1) / total : 1;
+            i128 ks = total > 0 ? div_ceil(budget * steps, total) : 1;
             bool loop = x->op == SOp::ForU || x->op == SOp::ForS;
             const LoopInfo *li = loop ? &an.loops.at(x) : nullptr;
             if (!loop || ks < 2 || depth >= kMaxSplit || li->trip_max < 1 || li->trip_max > (i128)UINT32_MAX) {
@@ -668,8 +682,8 @@ struct Splitter {
             if (ks <= m || depth + 1 >= kMaxSplit || is_fast) {
                 // chunks of iterations (a fast loop starts at its own instruction)
                 i128 parts = std::min(ks, m);
-                i128 chunk = (m + parts - 1) / parts;
-                i128 nch = (m + chunk - 1) / chunk;
+                i128 chunk = div_ceil(m, parts);
+                i128 nch = div_ceil(m, chunk);
                 for (i128 c = 0; c < nch; c++) {
                     split_j[depth] = (uint32_t)c;
                     depth++;
@@ -679,7 +693,7 @@ struct Splitter {
                     depth--;
                 }
             } else {
-                i128 sub = (ks + m - 1) / m;
+                i128 sub = div_ceil(ks, m);
                 const i128 after = phase;
                 for (i128 j = 0; j < m; j++) {
                     split_j[depth] = (uint32_t)j;

@@ -514,31 +514,41 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
 // Before each launch `flush` (when not null) is overwritten, outside the
 // timed events, so that every launch starts with a cold L2 as a check of a
 // new batch does.
-double time_plan(drf_plan *plan, int reps, void *flush, size_t flush_bytes)
+// Device time of one launch of the plan's pipeline: the median of `reps`
+// launches, each after a write of `flush_bytes` (a cold L2), following
+// `warm` untimed launches.  The launches are queued back to back, as a
+// plan's user runs them, so that the GPU stays at its working clocks (the
+// first launches of freshly loaded kernels, and launches after an idle gap,
+// run slower than that steady state).
+double time_plan(drf_plan *plan, int reps, void *flush, size_t flush_bytes, int warm = 3)
 {
     drf_ctx *ctx = plan->ctx;
     cudaStream_t s = ctx->stream;
     DeviceBatch &d = plan->dev;
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    double best = 1e30;
-    for (int r = 0; r < reps; r++) {
+    const int n = warm + reps;
+    std::vector<cudaEvent_t> ev(2 * n, nullptr);
+    bool ok = true;
+    for (auto &e : ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    for (int r = 0; ok && r < n; r++) {
         d.status_launches++;
         if (flush) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
-        cudaEventRecord(a, s);
+        cudaEventRecord(ev[2 * r], s);
         launch_front(d.args, s, ctx->sms, nullptr, nullptr, &d.jit);
         launch_back(d.args, s, ctx->sms, nullptr, nullptr, &d.jit);
-        cudaEventRecord(b, s);
-        if (cudaEventSynchronize(b) != cudaSuccess) { best = 1e30; break; }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, a, b);
-        best = std::min(best, (double)ms);
+        cudaEventRecord(ev[2 * r + 1], s);
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    std::vector<double> ms_all;
+    if (ok && cudaStreamSynchronize(s) == cudaSuccess) {
+        for (int r = warm; r < n; r++) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]) == cudaSuccess) ms_all.push_back(ms);
+        }
+    }
+    for (auto &e : ev) if (e) cudaEventDestroy(e);
     cudaGetLastError();
-    return best;
+    if (ms_all.empty()) return 1e30;
+    std::sort(ms_all.begin(), ms_all.end());
+    return ms_all[ms_all.size() / 2];
 }
 
 // Records the plan's pipeline as one CUDA graph (timing events inside when
@@ -609,12 +619,13 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
         // workload signature seen before reuses its choice
         const std::string key = signature(ctx, n, plan);
         PlanConfig best_cfg;
+        bool kept = false;                    // `plan` is the fastest candidate as measured
         if (!tune_lookup(key, best_cfg)) {
             // scratch larger than L2, overwritten before each timed launch
             const size_t flush_bytes = 256ull << 20;
             void *flush = nullptr;
             if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) { cudaGetLastError(); flush = nullptr; }
-            double best = time_plan(plan, 5, flush, flush_bytes);
+            double best = time_plan(plan, kTuneReps, flush, flush_bytes);
             best_cfg = plan->cfg;
             // candidates: the sort path under every granularity and tile
             // shape, the owner table (no radix tiles) under every granularity
@@ -626,21 +637,30 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
                 if (pref != 1 && plan->host.table_ok) cands.push_back(PlanConfig{g, 16, 2, 0});
                 if (specialize && plan->host.table_ok) cands.push_back(PlanConfig{g, 16, 2, 1});
             }
+            const PlanConfig timed = plan->cfg;   // the first plan's configuration, timed above
             for (const PlanConfig &c : cands) {
-                if (c.granularity == plan->cfg.granularity && c.path == plan->cfg.path && c.jit == plan->cfg.jit &&
-                    (c.path == 2 || c.radix_items == plan->cfg.radix_items))
+                if (c.granularity == timed.granularity && c.path == timed.path && c.jit == timed.jit &&
+                    (c.path == 2 || c.radix_items == timed.radix_items))
                     continue;
                 drf_plan *cand = nullptr;
                 if (build_plan(ctx, n, bytecodes, lens, bounds, c, &cand)) continue;
-                double ms = time_plan(cand, 5, flush, flush_bytes);
+                double ms = time_plan(cand, kTuneReps, flush, flush_bytes);
+                // the winner is kept as built: its timing covers its own
+                // buffers (the same configuration in other device memory --
+                // an owner table elsewhere -- can run measurably slower)
+                if (ms < best) {
+                    best = ms;
+                    best_cfg = c;
+                    std::swap(plan, cand);
+                }
                 drf_plan_destroy(cand);
-                if (ms < best) { best = ms; best_cfg = c; }
             }
             if (flush) cudaFree(flush);
             tune_store(key, best_cfg, best);
+            kept = true;
         }
-        if (best_cfg.granularity != plan->cfg.granularity || best_cfg.radix_items != plan->cfg.radix_items ||
-            best_cfg.path != plan->cfg.path || best_cfg.jit != plan->cfg.jit) {
+        if (!kept && (best_cfg.granularity != plan->cfg.granularity || best_cfg.radix_items != plan->cfg.radix_items ||
+                      best_cfg.path != plan->cfg.path || best_cfg.jit != plan->cfg.jit)) {
             drf_plan_destroy(plan);
             plan = nullptr;
             if ((st = build_plan(ctx, n, bytecodes, lens, bounds, best_cfg, &plan))) return st;

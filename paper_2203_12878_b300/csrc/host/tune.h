@@ -17,6 +17,7 @@ struct PlanConfig {
 // Candidate configurations the tuner times.
 constexpr uint32_t kTuneGranularity[] = {32, 128, 512};
 constexpr uint32_t kTuneRadixItems[] = {12, 16, 24};
+constexpr int kTuneReps = 15;                 // timed launches per candidate (median)
 
 // Process-wide cache of tuned configurations, keyed by a workload signature;
 // when DRF_TUNE_CACHE names a file the cache is loaded from it once and

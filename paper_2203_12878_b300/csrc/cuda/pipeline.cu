@@ -1105,10 +1105,13 @@ __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t 
 // accesses.  Owner table (TABLE true): the cell is decoded from its table
 // position, and the block reduces the per-thread hit bits of the M_CELL
 // pass.  Either way the result is the two smallest distinct tids of all
-// accesses to the cell and of its writes.
-template <bool TABLE>
-__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(BatchArgs a)
+// accesses to the cell and of its writes.  THREADS per block: on sorted keys
+// a batch of a few protocols gets wide blocks (a race's segment can hold
+// tens of thousands of keys).
+template <bool TABLE, int THREADS = kFinalizeThreads>
+__global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
 {
+    constexpr int kFinalizeThreads = THREADS;
     pdl_begin();
     __shared__ uint32_t s_red[4][kFinalizeThreads / 32];
     __shared__ unsigned long long s_end;
@@ -1379,7 +1382,10 @@ cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t
         k_resolve<<<1, 1024, 0, s>>>(a);
     }
     mark(ev, nev, s);
-    k_finalize<false><<<a.nprotos, kFinalizeThreads, 0, s>>>(a);
+    if (a.nprotos <= kFinalizeWideProtos)
+        k_finalize<false, kFinalizeWideThreads><<<a.nprotos, kFinalizeWideThreads, 0, s>>>(a);
+    else
+        k_finalize<false><<<a.nprotos, kFinalizeThreads, 0, s>>>(a);
     mark(ev, nev, s);
     return cudaGetLastError();
 }

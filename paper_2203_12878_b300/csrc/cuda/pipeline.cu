@@ -987,7 +987,10 @@ __global__ void __launch_bounds__(kTabScanThreads) k_tlist(BatchArgs a)
     const uint64_t first = (blockIdx.x * (uint64_t)kTabScanThreads) & ~31ull;
     for (uint64_t base = first + (threadIdx.x & ~31u); base < nwords; base += gthreads) {
         const uint64_t wd = base + lane;
-        const uint32_t bits = wd < nwords ? a.touch[wd] : 0u;
+        // through L2: the table pass's blocks may have left lines of this
+        // launch's data in this SM's L1, and a dependent launch that starts
+        // early gets no fresh L1 (the same holds for the scan's reads below)
+        const uint32_t bits = wd < nwords ? __ldcg(a.touch + wd) : 0u;
         if (bits) a.touch[wd] = 0;
         const uint32_t cnt = (uint32_t)__popc(bits);
         uint32_t incl = cnt;
@@ -1023,7 +1026,7 @@ __global__ void __launch_bounds__(kTabScanThreads) k_tscan(BatchArgs a)
     __shared__ unsigned long long s_best;
     if (threadIdx.x == 0) { s_proto = 0xFFFFFFFFu; s_best = kNone; }
     __syncthreads();
-    unsigned long long listed = a.ctrl->touched;
+    unsigned long long listed = __ldcg(&a.ctrl->touched);
     if (listed > table_blocks(a.tab_cells)) listed = table_blocks(a.tab_cells);
     const uint64_t warps = gthreads / 32;
     // a lane's smallest racy position, per protocol ([cand_lo, cand_hi) its records)
@@ -1046,11 +1049,14 @@ __global__ void __launch_bounds__(kTabScanThreads) k_tscan(BatchArgs a)
         cand_hi = P.tab_off + (uint64_t)P.tab_phases * P.cells_sum;
     };
     for (uint64_t e = (blockIdx.x * (uint64_t)kTabScanThreads + threadIdx.x) / 32; e < listed; e += warps) {
-        const uint64_t blk = a.tlist[e];
+        const uint64_t blk = __ldcg(a.tlist + e);
         const uint4 *src = reinterpret_cast<const uint4 *>(a.table) + blk * (kTabBlock / 4) + (uint64_t)lane * V4;
         uint4 v[V4];
+        // through L2: this SM's L1 may hold copies of these records that the
+        // table pass read before other SMs updated them -- a stale zero would
+        // leave its record uncleared for the next launch
 #pragma unroll
-        for (int q = 0; q < V4; q++) v[q] = src[q];
+        for (int q = 0; q < V4; q++) v[q] = __ldcg(src + q);
         uint4 *dst = reinterpret_cast<uint4 *>(a.table) + blk * (kTabBlock / 4) + (uint64_t)lane * V4;
         const unsigned long long pos0 = blk * kTabBlock + (uint64_t)lane * PER;
 #pragma unroll
@@ -1135,7 +1141,7 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
             // this protocol's bits: [tid_off, tid_off + T) of the hit arrays
             const uint64_t b0 = P.tid_off, b1 = P.tid_off + P.nthreads;
             for (uint64_t wd = (b0 >> 5) + t; wd <= ((b1 - 1) >> 5); wd += kFinalizeThreads) {
-                uint32_t ma = a.hit_acc[wd], mw = a.hit_wr[wd];
+                uint32_t ma = __ldcg(a.hit_acc + wd), mw = __ldcg(a.hit_wr + wd);
                 const uint64_t lo = wd * 32;
                 if (lo < b0) { ma &= ~0u << (uint32_t)(b0 - lo); mw &= ~0u << (uint32_t)(b0 - lo); }
                 if (lo + 32 > b1) {

@@ -151,9 +151,11 @@ class Gen {
     // (owner.cuh's rule, split in three rounds so that one warp waits for at
     // most one round trip of claims): first every claim of a cell whose copy
     // is empty (compare-and-swap), then the bits the non-empty copies ask
-    // for, then the outcome of the claims -- a won claim marks the cell's
-    // block as touched, a lost one adds the bits the winner's record asks
-    // for.  Accesses whose index does not read tid go through put_warp_cur.
+    // for, then the outcome of the claims -- a lost claim adds the bits the
+    // winner's record asks for, and the won claims of the lanes running
+    // together mark their blocks as touched with one reduction per touch
+    // word (touch_created).  Accesses whose index does not read tid go
+    // through put_warp_cur.
     void updates(const std::vector<Slot> &S)
     {
         std::vector<std::string> n(S.size());

@@ -339,6 +339,27 @@ def test_table_is_clean_between_checks(ctx, oracle):
         assert same(run(ctx, p), want(oracle, p, ctx))
 
 
+def test_table_reuse_across_many_batches(oracle):
+    """Ninety protocols in small batches, one after another on one owner-table
+    context, three times in different groupings: every record a
+    launch creates must be cleared before the next (a record left behind
+    would surface as a false race wherever a later batch's rows land)."""
+    ps = protogen.config4(master_seed=11, count=90)
+    exp = [want(oracle, p) for p in ps]            # small tables: no size limit applies
+    bcs = [drf.drf_protocol_compile(p.text) for p in ps]
+    c = drf.drf_ctx_create(0, flags=drf.OPT_PATH_TABLE)
+    try:
+        for size, shift in ((3, 0), (2, 1), (5, 2)):
+            idx = list(range(shift, len(ps))) + list(range(shift))
+            for g in range(0, len(idx), size):
+                grp = idx[g:g + size]
+                res = drf.drf_check_batch(c, [bcs[i] for i in grp], [(ps[i].nthreads, ps[i].cells, ps[i].params) for i in grp])
+                for i, r in zip(grp, res):
+                    assert same(drf.result_dict(r), exp[i]), (size, shift, i, ps[i].text)
+    finally:
+        drf.drf_ctx_destroy(c)
+
+
 def test_table_plan_replays(oracle):
     """Graph replays of an owner-table plan: the witness is found launch after
     launch (each launch leaves the table zero for the next)."""

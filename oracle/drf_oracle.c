@@ -1224,3 +1224,251 @@ int oracle_validate(const char *text, int *narrays, int *nparams, char *msg, int
     program_free(&prog);
     return st;
 }
+
+/* ------------------------------------------- method B on several cores -- */
+
+/* A driver that runs the same steps as oracle_check's method B on several
+ * host threads, for the CPU baseline and for protocols with hundreds of
+ * millions of accesses.  It changes nothing in what is computed:
+ *   1. rule par: each worker runs run_stmt for a contiguous range of thread
+ *      ids (the threads are independent by that rule), keeping its own
+ *      accesses, sync counts and first error;
+ *   2. the evaluation error of the smallest failing tid wins, then barrier
+ *      divergence against thread 0, exactly as in oracle_check;
+ *   3. the accesses are grouped into shards of consecutive cells in the
+ *      lexicographic order (phase, array, index) -- per (phase, array), the
+ *      index range cut into equal chunks -- and each shard is checked like
+ *      check_cells does (sort by cell, per-cell two smallest accessors and
+ *      writers).  Cells never span two shards, so every cell's verdict is
+ *      the one method B gives it, and the first racy cell of the first shard
+ *      that has one is the lexicographically smallest racy cell.
+ * Needs POSIX threads. */
+#include <pthread.h>
+
+typedef struct {
+    const Program *prog;
+    const Bounds *b;
+    uint32_t t_lo, t_hi;
+    uint32_t *syncs;           /* shared, indexed by tid */
+    TupleVec tv;
+    int error;                 /* first error of the smallest failing tid of the range */
+    uint32_t err_tid;
+    uint64_t err_ordinal;
+    uint64_t total;
+    int status;                /* OR_E_NOMEM */
+} EvalJob;
+
+static void *eval_worker(void *arg)
+{
+    EvalJob *j = (EvalJob *)arg;
+    int64_t *vars = (int64_t *)calloc((size_t)(j->prog->nslots ? j->prog->nslots : 1), sizeof(int64_t));
+    if (!vars) { j->status = OR_E_NOMEM; return NULL; }
+    for (uint32_t t = j->t_lo; t < j->t_hi; t++) {
+        Thread th; memset(&th, 0, sizeof th);
+        th.prog = j->prog; th.cells = j->b->cells; th.params = j->b->params; th.vars = vars;
+        th.tid = t; th.out = &j->tv;
+        run_stmt(&th, j->prog->body);
+        if (j->tv.nomem) { j->status = OR_E_NOMEM; break; }
+        j->syncs[t] = th.phase;
+        j->total += th.ordinal;
+        if (th.error && !j->error) { j->error = th.error; j->err_tid = t; j->err_ordinal = th.err_ordinal; }
+    }
+    free(vars);
+    return NULL;
+}
+
+typedef struct {
+    uint32_t nlocs;
+    uint64_t chunk[64];        /* index range of one shard, per array */
+    uint32_t per_loc[64];      /* shards per (phase, array) */
+    uint32_t base[64];         /* first shard of an array within a phase */
+    uint32_t per_phase;        /* shards per phase */
+} ShardMap;
+
+static uint32_t shard_of(const ShardMap *m, const Tuple *t)
+{
+    return t->phase * m->per_phase + m->base[t->loc] + (uint32_t)((uint64_t)t->index / m->chunk[t->loc]);
+}
+
+typedef struct {
+    EvalJob *jobs; int njobs;
+    const ShardMap *map;
+    uint64_t *offs;            /* [job][shard]: where this job's tuples of the shard go */
+    uint32_t nshards;
+    Tuple *all;
+    int w;                     /* this worker */
+    /* shard checking */
+    uint64_t *start;           /* [nshards + 1] */
+    uint32_t *next;            /* shared shard counter */
+    pthread_mutex_t *mu;
+    oracle_result *shard_res;  /* one per shard; verdict -1 = not racy */
+} CellJob;
+
+static void *count_worker(void *arg)
+{
+    CellJob *c = (CellJob *)arg;
+    const EvalJob *j = &c->jobs[c->w];
+    uint64_t *cnt = c->offs + (size_t)c->w * c->nshards;
+    for (size_t i = 0; i < j->tv.n; i++) cnt[shard_of(c->map, &j->tv.v[i])]++;
+    return NULL;
+}
+
+static void *scatter_worker(void *arg)
+{
+    CellJob *c = (CellJob *)arg;
+    EvalJob *j = &c->jobs[c->w];
+    uint64_t *off = c->offs + (size_t)c->w * c->nshards;
+    for (size_t i = 0; i < j->tv.n; i++) c->all[off[shard_of(c->map, &j->tv.v[i])]++] = j->tv.v[i];
+    return NULL;
+}
+
+static void *shard_worker(void *arg)
+{
+    CellJob *c = (CellJob *)arg;
+    for (;;) {
+        pthread_mutex_lock(c->mu);
+        uint32_t s = (*c->next)++;
+        pthread_mutex_unlock(c->mu);
+        if (s >= c->nshards) return NULL;
+        History h; memset(&h, 0, sizeof h);
+        h.tv.v = c->all + c->start[s];
+        h.tv.n = (size_t)(c->start[s + 1] - c->start[s]);
+        oracle_result r; memset(&r, 0, sizeof r);
+        check_cells(&h, &r);             /* sorts the shard in place */
+        if (r.verdict != V_RACY) r.verdict = -1;
+        c->shard_res[s] = r;
+    }
+}
+
+/* Method B on `workers` host threads (0: one).  Same result as
+ * oracle_check(..., method 1, ...). */
+int oracle_check_mt(const char *text, uint32_t nthreads, uint32_t nlocs, const uint64_t *cells,
+                    uint32_t nparams, const int64_t *params, int workers, oracle_result *out,
+                    char *msg, int msglen)
+{
+    if (!text || !out) return OR_E_INVALID_ARG;
+    memset(out, 0, sizeof *out);
+    out->verdict = -1;
+    if (workers < 1) workers = 1;
+    if (workers > 1024) workers = 1024;
+    if ((uint32_t)workers > nthreads && nthreads) workers = (int)nthreads;
+    Program prog;
+    int st = parse_program(text, &prog, msg, msglen);
+    if (st) { program_free(&prog); out->status = st; return st; }
+    Bounds b = { nthreads, nlocs, nparams, cells, params };
+    st = check_bounds(&prog, &b, msg, msglen);
+    if (!st && nlocs > 64) st = OR_E_INVALID_ARG;
+    if (st) { program_free(&prog); out->status = st; return st; }
+
+    uint32_t *syncs = (uint32_t *)calloc(nthreads ? nthreads : 1, sizeof(uint32_t));
+    EvalJob *jobs = (EvalJob *)calloc((size_t)workers, sizeof(EvalJob));
+    pthread_t *th = (pthread_t *)calloc((size_t)workers, sizeof(pthread_t));
+    if (!syncs || !jobs || !th) { free(syncs); free(jobs); free(th); program_free(&prog); return out->status = OR_E_NOMEM; }
+    /* 1. rule par over contiguous tid ranges */
+    for (int w = 0; w < workers; w++) {
+        jobs[w].prog = &prog; jobs[w].b = &b; jobs[w].syncs = syncs;
+        jobs[w].t_lo = (uint32_t)((uint64_t)nthreads * (uint64_t)w / (uint64_t)workers);
+        jobs[w].t_hi = (uint32_t)((uint64_t)nthreads * (uint64_t)(w + 1) / (uint64_t)workers);
+        pthread_create(&th[w], NULL, eval_worker, &jobs[w]);
+    }
+    for (int w = 0; w < workers; w++) pthread_join(th[w], NULL);
+    uint64_t total = 0, n = 0;
+    int error = 0; uint32_t err_tid = 0; uint64_t err_ord = 0;
+    for (int w = 0; w < workers; w++) {
+        if (jobs[w].status) st = jobs[w].status;
+        total += jobs[w].total;
+        n += jobs[w].tv.n;
+        if (jobs[w].error && !error) { error = jobs[w].error; err_tid = jobs[w].err_tid; err_ord = jobs[w].err_ordinal; }
+    }
+    Tuple *all = NULL;
+    uint64_t *offs = NULL, *start = NULL;
+    oracle_result *shard_res = NULL;
+    if (st) goto done;
+    out->tuples = total;
+    /* 2. evaluation error, then barrier divergence */
+    if (error) {
+        out->status = error; out->err_tid = err_tid; out->err_ordinal = err_ord;
+        st = error;
+        goto done;
+    }
+    out->phases = nthreads ? syncs[0] + 1 : 0;
+    for (uint32_t t = 0; t < nthreads; t++) {
+        if (syncs[t] != syncs[0]) {
+            out->verdict = V_DIVERGENCE;
+            out->div_tid = t; out->sync_count_0 = syncs[0]; out->sync_count_div = syncs[t];
+            goto done;
+        }
+    }
+    out->sync_count_0 = nthreads ? syncs[0] : 0;
+    out->verdict = V_DRF;
+    if (n == 0) goto done;
+    {
+        /* 3. shards of consecutive cells, (phase, array, index) order */
+        ShardMap m; memset(&m, 0, sizeof m);
+        m.nlocs = nlocs;
+        uint64_t cells_total = 0;
+        for (uint32_t l = 0; l < nlocs; l++) cells_total += cells[l];
+        const uint32_t phases = syncs[0] + 1;
+        /* every (phase, array) cut into chunks: the accesses of one phase
+           may all fall into a single array, so each phase alone gets enough
+           shards to keep every worker busy */
+        const uint64_t per_phase_want = (uint64_t)workers * 16;
+        for (uint32_t l = 0; l < nlocs; l++) {
+            uint64_t k = cells_total ? (per_phase_want * cells[l] + cells_total - 1) / cells_total : 1;
+            if (k < 1) k = 1;
+            if (k > 4096) k = 4096;
+            m.chunk[l] = (cells[l] + k - 1) / k;
+            if (m.chunk[l] == 0) m.chunk[l] = 1;
+            m.per_loc[l] = (uint32_t)((cells[l] + m.chunk[l] - 1) / m.chunk[l]);
+            if (m.per_loc[l] == 0) m.per_loc[l] = 1;
+            m.base[l] = m.per_phase;
+            m.per_phase += m.per_loc[l];
+        }
+        const uint32_t nshards = phases * m.per_phase;
+        all = (Tuple *)malloc(sizeof(Tuple) * (size_t)n);
+        offs = (uint64_t *)calloc((size_t)workers * nshards, sizeof(uint64_t));
+        start = (uint64_t *)calloc((size_t)nshards + 1, sizeof(uint64_t));
+        shard_res = (oracle_result *)calloc(nshards, sizeof(oracle_result));
+        if (!all || !offs || !start || !shard_res) { st = OR_E_NOMEM; goto done; }
+        CellJob *cj = (CellJob *)calloc((size_t)workers, sizeof(CellJob));
+        if (!cj) { st = OR_E_NOMEM; goto done; }
+        pthread_mutex_t mu = PTHREAD_MUTEX_INITIALIZER;
+        uint32_t next = 0;
+        for (int w = 0; w < workers; w++) {
+            cj[w] = (CellJob){ jobs, workers, &m, offs, nshards, all, w, start, &next, &mu, shard_res };
+            pthread_create(&th[w], NULL, count_worker, &cj[w]);
+        }
+        for (int w = 0; w < workers; w++) pthread_join(th[w], NULL);
+        uint64_t run = 0;
+        for (uint32_t s = 0; s < nshards; s++) {
+            start[s] = run;
+            for (int w = 0; w < workers; w++) {
+                uint64_t c = offs[(size_t)w * nshards + s];
+                offs[(size_t)w * nshards + s] = run;
+                run += c;
+            }
+        }
+        start[nshards] = run;
+        for (int w = 0; w < workers; w++) pthread_create(&th[w], NULL, scatter_worker, &cj[w]);
+        for (int w = 0; w < workers; w++) pthread_join(th[w], NULL);
+        for (int w = 0; w < workers; w++) { free(jobs[w].tv.v); jobs[w].tv.v = NULL; jobs[w].tv.n = 0; }
+        for (int w = 0; w < workers; w++) pthread_create(&th[w], NULL, shard_worker, &cj[w]);
+        for (int w = 0; w < workers; w++) pthread_join(th[w], NULL);
+        free(cj);
+        for (uint32_t s = 0; s < nshards; s++) {
+            const oracle_result *r = &shard_res[s];
+            if (r->verdict != V_RACY) continue;
+            out->verdict = V_RACY;
+            out->phase = r->phase; out->loc = r->loc; out->index = r->index;
+            out->tid_i = r->tid_i; out->tid_j = r->tid_j;
+            out->i_writes = r->i_writes; out->j_writes = r->j_writes;
+            break;
+        }
+    }
+done:
+    if (st == OR_E_NOMEM) { out->status = st; out->verdict = -1; }
+    for (int w = 0; w < workers; w++) free(jobs[w].tv.v);
+    free(jobs); free(th); free(syncs); free(all); free(offs); free(start); free(shard_res);
+    program_free(&prog);
+    return st;
+}

@@ -62,7 +62,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-Wall", "-shared", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-Wall", "-shared", "-fPIC", "-pthread",
                                "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
@@ -75,6 +75,11 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.oracle_check.restype = ctypes.c_int
             lib.oracle_check.argtypes = [
+                ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                ctypes.c_uint32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                ctypes.POINTER(_Result), ctypes.c_char_p, ctypes.c_int]
+            lib.oracle_check_mt.restype = ctypes.c_int
+            lib.oracle_check_mt.argtypes = [
                 ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
                 ctypes.c_uint32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                 ctypes.POINTER(_Result), ctypes.c_char_p, ctypes.c_int]
@@ -127,6 +132,30 @@ def check(text: str, nthreads: int, cells=(), params=(), method: int = METHOD_CE
     msg = ctypes.create_string_buffer(512)
     lib.oracle_check(text.encode(), nthreads, len(cells), ca, len(params), pa, method,
                      ctypes.byref(r), msg, len(msg))
+    d = result_dict(r)
+    if r.status != 0 and msg.value:
+        d["message"] = msg.value.decode(errors="replace")
+    return d
+
+
+def host_cores() -> int:
+    """Host threads the multithreaded checker uses by default: the cores
+    this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def check_mt(text: str, nthreads: int, cells=(), params=(), workers: int | None = None) -> dict:
+    """Method B (per-cell records) run on ``workers`` host threads (default:
+    every core); the same result as ``check(..., METHOD_CELLS)``."""
+    lib = _load()
+    cells, params, ca, pa = _arrays(cells, params)
+    r = _Result()
+    msg = ctypes.create_string_buffer(512)
+    lib.oracle_check_mt(text.encode(), nthreads, len(cells), ca, len(params), pa,
+                        host_cores() if workers is None else int(workers), ctypes.byref(r), msg, len(msg))
     d = result_dict(r)
     if r.status != 0 and msg.value:
         d["message"] = msg.value.decode(errors="replace")

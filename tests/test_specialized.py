@@ -126,17 +126,27 @@ def test_config2_full_size(sctx, oracle):
     assert check(sctx, oracle, protogen.config2(0)) == 2
 
 
-def test_config3_full_size_racy(sctx, oracle):
-    """Grid scale (65,536 threads: 64-bit owner records), one planted race;
-    the witness threads come from the oracle's one-cell recomputation."""
-    p = protogen.config3(0, racy=True)
-    got, spec = plan_result(sctx, p, launches=1)
-    m = p.meta
-    assert spec and got["status"] == "OK" and got["tuples"] == m["accesses"] + 2
-    assert (got["verdict"], got["phase"], got["loc"], got["index"]) == ("RACY", m["phase"], m["loc"], m["index"])
-    cell = oracle.cell(p.text, p.nthreads, p.cells, p.params, m["phase"], m["loc"], m["index"])
-    assert {k: got[k] for k in ("tid_i", "tid_j", "i_writes", "j_writes")} == \
-           {k: cell[k] for k in ("tid_i", "tid_j", "i_writes", "j_writes")}
+@pytest.mark.parametrize("seed,racy", [(0, True), (0, False), (1, True), (1, False)])
+def test_config3_full_size(sctx, grid_expected, seed, racy):
+    """Grid scale (65,536 threads, ~2.2x10^8 accesses) through specialized
+    kernels with static phases, launch after launch: every result field
+    against the oracle's method B over the whole protocol."""
+    p = protogen.config3(seed, racy=racy)
+    got, spec = plan_result(sctx, p, launches=3)
+    assert spec == 2
+    assert got == grid_expected(seed, racy)
+
+
+def test_config3_benchmark_launch_configuration(grid_expected):
+    """The benchmark's launch configuration on its workload: an autotuned
+    plan with specialization allowed, launched repeatedly, equals the
+    oracle over the whole protocol."""
+    c = drf.drf_ctx_create(0, flags=drf.OPT_SPECIALIZE | drf.OPT_AUTOTUNE)
+    try:
+        got, _ = plan_result(c, protogen.config3(0, racy=True), launches=4)
+        assert got == grid_expected(0, True)
+    finally:
+        drf.drf_ctx_destroy(c)
 
 
 def test_autotuned_specialized_plan(oracle):
@@ -231,7 +241,8 @@ def affine_case(seed):
 @pytest.mark.parametrize("chunk", range(3))
 def test_witness_hits_solved_per_loop(sctx, oracle, chunk):
     """The witness pass decides whether a thread's fast loop hits the witness
-    cell by solving the index equation (affine.cuh) rather than iterating:
+    cell by solving the index equation (a linear congruence whose constants
+    the code generator computes) rather than iterating:
     the witness threads (the two smallest accessors of the first racy cell)
     must be the oracle's."""
     wide = 0

@@ -24,7 +24,7 @@ def _cases():
     return cs
 
 
-def test_no_alloc_matches_drf_check_twice_in_a_row():
+def test_no_alloc_matches_drf_check_twice_in_a_row(oracle):
     import torch
     torch.cuda.set_device(0)
     ctx = drf.drf_ctx_create(0)
@@ -36,6 +36,12 @@ def test_no_alloc_matches_drf_check_twice_in_a_row():
             second = drf.result_dict(drf.drf_check_noalloc(bc, p.nthreads, p.cells, p.params))
             assert first == want, p.text
             assert second == want, p.text
+            # and directly against the oracle (this entry point always runs
+            # the sort path, drf_check on a default context may not)
+            exp = oracle.check(p.text, p.nthreads, p.cells, p.params, oracle.METHOD_CELLS)
+            exp.pop("message", None)
+            if exp["status"] != "OVERFLOW":
+                assert first == exp, p.text
     finally:
         drf.drf_ctx_destroy(ctx)
 

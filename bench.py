@@ -316,15 +316,21 @@ def roofline(kinds, steps, n, info, dev, clocks):
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                 "traffic": traffic, "launch_ms": round(dom_ms, 4),
                 "algorithmic_bytes_per_launch": bytes_per[dominant]}
-    elif dominant in ("table", "emit", "count", "witness"):
-        ops = TABLE_OPS_PER_TUPLE * n
+    elif dominant in ("table", "emit", "count", "witness", "range"):
+        # the range pass applies its share of the tuples (counted on the
+        # device); the table pass then applies the rest
+        units = n
+        if info.get("range_tuples") is not None:
+            units = info["range_tuples"] if dominant == "range" else n - info["range_tuples"]
+        ops = TABLE_OPS_PER_TUPLE * units
         achieved = ops / (dom_ms * 1e-3) / 1e12
         peak_ops, src = alu_peak(dev, clocks)
-        kernel = "drf_table (specialized)" if info.get("specialized") else f"k_interp<{dominant}>"
+        kernel = (f"drf_{dominant} (specialized)" if info.get("specialized") and dominant in ("table", "range")
+                  else f"k_interp<{dominant}>")
         roof = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3), "peak": round(peak_ops / 1e12, 2),
                 "unit": "Tops/s", "frac": round(achieved * 1e12 / peak_ops, 4), "peak_source": f"derived: {src}",
                 "traffic": traffic, "launch_ms": round(dom_ms, 4),
-                "algorithmic_ops_per_launch": ops, "ops_per_tuple": TABLE_OPS_PER_TUPLE}
+                "algorithmic_ops_per_launch": ops, "ops_per_tuple": TABLE_OPS_PER_TUPLE, "tuples_per_launch": units}
         if traffic:
             # the same kernel against HBM: its measured DRAM bytes per launch
             roof["dram_gbs"] = round(traffic / (dom_ms * 1e-3) / 1e9, 1)
@@ -344,6 +350,8 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream()
     # each rank checks its own seeded protocol of the same shape
     p = workload(seed=rank)
+    if args.threads:            # a smaller case of the same protocol (profiling captures)
+        p = thread_sample(p, min(args.threads, p.nthreads))
     bc = drf.drf_protocol_compile(p.text)
     bounds = [(p.nthreads, p.cells, p.params)]
     flags = {"auto": drf.OPT_AUTOTUNE | drf.OPT_SPECIALIZE, "sort": drf.OPT_PATH_SORT,
@@ -386,7 +394,9 @@ def run_ours(args, rank, world):
     assert drf.result_dict(drf.drf_plan_results(pplan)[0]) == res
     drf.drf_plan_destroy(pplan)
     drf.drf_ctx_destroy(pctx)
-    roof, stages = roofline(kinds, prof_steps, n, {**info, "specialized": specialized}, dev, clocks)
+    range_tuples = drf.drf_plan_range_tuples(plan) if specialized == 3 else None
+    roof, stages = roofline(kinds, prof_steps, n, {**info, "specialized": specialized, "range_tuples": range_tuples},
+                            dev, clocks)
 
     # the interpreted back ends on the same protocol, for comparison
     others = []
@@ -448,7 +458,10 @@ def run_ours(args, rank, world):
             "scaling": "weak", "vs_baseline": None,
             "dtype": ("u32 owner records" if path == "table" else "u64 keys") + ", int32/int64 index arithmetic",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "tuples_per_step": n, "path": path, "specialized": specialized,
+            "config": {"workload": WORKLOAD if not args.threads else
+                       f"{WORKLOAD}; restricted to its first {p.nthreads} threads",
+                       "tuples_per_step": n, "path": path, "specialized": specialized,
+                       "range_pass_tuples_per_step": range_tuples,
                        "path_choice": args.path,
                        "plan": {**drf.drf_plan_config(plan), "create_s": round(plan_s, 3)},
                        "sort_passes": info["sort_passes"], "sort_bits": info["sort_bits"],
@@ -694,6 +707,9 @@ def main():
                     help="back end of the timed plan: autotuned (specialized kernels allowed), or forced")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="least wall time of the oracle's all-core timing (the one-core sample gets half)")
+    ap.add_argument("--threads", type=int, default=0,
+                    help="check the workload restricted to its first THREADS threads (a smaller case for "
+                         "profiling captures; the JSON line's config says so); 0 = all 65,536")
     ap.add_argument("--cpu-one-core-threads", type=int, default=4096,
                     help="threads of the thread-prefix sample timed on one host core")
     ap.add_argument("--warmup-seconds", type=float, default=WARMUP_MIN_S,

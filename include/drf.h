@@ -127,7 +127,8 @@ typedef struct {
 
 /* Context options (all zero = defaults). */
 typedef struct {
-    uint32_t radix_bits;         /* radix digit width 4..8; 0 = autotuned */
+    uint32_t radix_bits;         /* sort path's radix digit width 4..8; 0 = 8, or tuned by plans
+                                    with DRF_OPT_AUTOTUNE (drf_plan_config) */
     uint32_t flags;              /* DRF_OPT_* */
     uint64_t max_device_bytes;   /* cap on the context's device workspace; 0 = none */
 } drf_opts;
@@ -255,9 +256,13 @@ void drf_free(void *p);
 /* ------------------------------------------------------------------ checks -- */
 
 /* Checks one protocol (bytecode of `len` bytes) under `bounds` and writes
- * the result to *out.  Runs the whole device pipeline on `stream` -- count,
- * scan, key emission, radix sort, segmented detection, witness -- and blocks
- * until the result is on the host.  Returns out->status. */
+ * the result to *out.  Runs the whole device pipeline on `stream` and blocks
+ * until the result is on the host: the front (count the accesses per thread
+ * and work item, scan them into phases and offsets), then the back end the
+ * context's options select (DRF_OPT_PATH_*; by default the owner table when
+ * it fits, see below): either key emission, radix sort and segmented
+ * detection, or the owner-table pass, its scan and the witness pass; then
+ * the result.  Returns out->status. */
 int drf_check(drf_ctx *ctx, const uint8_t *bytecode, size_t len,
               const drf_bounds *bounds, drf_result *out, void *stream);
 
@@ -293,19 +298,62 @@ int drf_ctx_transfer_bytes(const drf_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
  * on the current device and `stream` (NULL: the legacy default stream),
  * needs no context, and never calls cudaMalloc, cudaFree or any allocating
  * library routine.  Its result equals drf_check's.
- *   - The first call on a device looks up the array's device address (once
- *     per device); make that first call before any stream capture.
+ *   - Every call looks up the array's device address in the current context
+ *     (a lookup, no allocation); the first call on a device also loads the
+ *     library's device code there, so make that first call before any
+ *     stream capture.
  *   - Protocols whose buffers do not fit the array (roughly 3.5 million
  *     access tuples or fewer fit; the exact need depends on the thread
  *     count and work items) are rejected with DRF_E_LIMIT in the return
  *     value and in out->status.
- *   - All calls share the one array (per device) and leave their data in
- *     it; each call clears what it needs cleared.  Calls that overlap on the
- *     GPU -- from two host threads, or on two streams -- race on the array:
- *     serialise them.
+ *   - All calls on a device share the one array and leave their data in it;
+ *     each call clears what it needs cleared.  Calls that overlapped on the
+ *     GPU would race on the array; the library rules that out within a
+ *     process: a per-device lock is held for the whole call, and a call
+ *     waits for its own GPU work before it returns, so calls from several
+ *     host threads (on any streams) run one after another.  Calls on
+ *     different devices use different arrays and run in parallel.
  * Blocks until the result is on the host; returns out->status. */
 int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_bounds *bounds, drf_result *out,
                       void *stream);
+
+/* ------------------------------------------------------ one protocol, sharded */
+
+/* A protocol's cells split over several checkers (several GPUs, or several
+ * calls).  Definition 1 (Sec. 3) decides each (phase, array, index) cell on
+ * its own -- a race needs two threads on the same cell in the same phase --
+ * so the cells can be partitioned and checked independently; only the
+ * results are combined.  Cells are numbered in the witness's lexicographic
+ * order, position = phase * (sum of the array sizes) + (the array's offset
+ * among them, declaration order) + index, over the phases 0 .. S where S is
+ * the static bound on syncs per thread (drf_analysis.sync_bound).  Shard k
+ * of n takes positions [k * total / n, (k + 1) * total / n).
+ *
+ * drf_shard_range: the window [*lo, *hi) of shard `shard` of `nshards` and,
+ * when `positions` is not NULL, the total.  Host only (no GPU needed). */
+int drf_shard_range(const uint8_t *bytecode, size_t len, const drf_bounds *bounds, uint32_t shard, uint32_t nshards,
+                    uint64_t *lo, uint64_t *hi, uint64_t *positions);
+
+/* Checks shard `shard` of `nshards` of one protocol on the context's GPU:
+ * every thread is evaluated (evaluation errors, sync counts, barrier
+ * divergence and the tuple count are facts of the whole protocol, identical
+ * in every shard), but only the shard's cells are recorded in the owner
+ * table, so *out reports RACY iff the shard holds a racy cell, with the
+ * lexicographically smallest one and its witness threads (computed from all
+ * threads' accesses to that cell).  Always the owner-table back end
+ * (interpreted); DRF_E_LIMIT when the protocol's table does not fit. */
+int drf_check_shard(drf_ctx *ctx, const uint8_t *bytecode, size_t len, const drf_bounds *bounds, uint32_t shard,
+                    uint32_t nshards, drf_result *out, void *stream);
+
+/* Combines the n shard results of one protocol (any order) into the result
+ * drf_check gives for it: the shards must agree on every fact of the whole
+ * protocol (status, error thread and ordinal, tuples, phases, sync counts,
+ * divergence) -- else DRF_E_INTERNAL; an error or a divergence is then the
+ * result; otherwise the racy shard result with the smallest (phase, array,
+ * index), or DRF if none is racy.  Host only: a min-reduction over records
+ * of a few dozen bytes, the one exchange between the checkers of a
+ * protocol's shards. */
+int drf_merge_shards(const drf_result *parts, uint32_t n, drf_result *out);
 
 /* Diagnostics: copies the sorted access keys of the context's last
  * drf_check / drf_check_batch into keys (device -> host, at most cap) and
@@ -315,6 +363,15 @@ int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_bounds *bou
  * (mode 1 = write).  DRF_E_NOT_FOUND when that check ran the owner-table
  * path (which sorts nothing). */
 int drf_debug_sorted_keys(drf_ctx *ctx, uint64_t *keys, uint64_t cap, uint64_t *n, uint32_t layout[5]);
+
+/* Test hook for the bounded waits of the radix sort's look-back: the
+ * context's next `launches` checks that run the sort path leave tile 0's
+ * look-back status unpublished in every radix pass and let each waiting
+ * digit give up after 64 waits instead of about a second's worth.  Those
+ * checks return DRF_E_TIMEOUT (no verdict) without any GPU fault -- the
+ * waits end, every store stays inside the key buffers -- and the context
+ * works normally afterwards.  Owner-table launches are not affected. */
+int drf_debug_stall_lookback(drf_ctx *ctx, uint32_t launches);
 
 /* A parameter swept over a range in one batched pass: checks the protocol
  * for every value v in [lo, hi) of parameter `param` (the other bounds as
@@ -365,28 +422,47 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
 int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap, int *count);
 
 /* The launch configuration a plan uses: the warp-items per SM its items
- * were cut for (the item-to-warp schedule) and the keys per thread of its
- * radix tiles.  With DRF_OPT_AUTOTUNE, drf_plan_create times every
- * candidate (granularity 32 / 128 / 512 x tile 12 / 16 / 24 keys per
- * thread) on the batch -- each launch after overwriting 256 MiB of scratch,
- * so that it starts with a cold L2 -- and keeps the fastest; the choice is cached per
- * workload signature for the process and, when the environment variable
- * DRF_TUNE_CACHE names a file, persisted there. */
-int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix_items);
+ * were cut for (the item-to-warp schedule), the keys per thread of its
+ * radix tiles and the radix digit width of its sort (bits per pass; the
+ * sort makes ceil(sorted key bits / width) passes).  With DRF_OPT_AUTOTUNE,
+ * drf_plan_create times every candidate (granularity 32 / 128 / 512 x tile
+ * 12 / 16 / 24 keys per thread, 8-bit digits, on the sort path; granularity
+ * x interpreted / specialized on the owner table) on the batch -- each
+ * launch after overwriting 256 MiB of scratch, so that it starts with a
+ * cold L2 -- then, when a sort-path configuration wins and the context's
+ * drf_opts.radix_bits is 0, the same configuration with 6- and 7-bit
+ * digits, and keeps the fastest; the choice is cached per workload
+ * signature for the process and, when the environment variable
+ * DRF_TUNE_CACHE names a file, persisted there.  A nonzero
+ * drf_opts.radix_bits fixes the digit width of every sort (it is widened
+ * where the key would need more than 8 passes). */
+int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix_items, uint32_t *radix_bits);
 
 /* Whether a plan runs kernels specialized to its protocol
- * (DRF_OPT_SPECIALIZE): *specialized = 0 (no), 1 (yes), or 2 (yes, and the
+ * (DRF_OPT_SPECIALIZE): *specialized = 0 (no), 1 (yes), 2 (yes, and the
  * protocol's sync structure is the same for every thread and no evaluation
  * can fail, so each item's phase is compiled in and a launch runs neither
- * the count nor the scan pass; the owner-table pass counts the tuples).
- * When specialization was asked for but not used, log (may be NULL)
- * receives why. */
+ * the count nor the scan pass; the owner-table pass counts the tuples), or
+ * 3 (as 2, and the launch runs the range pass: accesses whose index is +tid
+ * or -tid plus a function of the loop variables -- possibly under a
+ * remainder -- in loops and conditions that do not read tid are applied
+ * cell range by cell range in shared memory, the threads reaching a range
+ * found as one or two tid intervals per loop iteration; the owner-table
+ * pass applies the other accesses and the range pass merges their records,
+ * then finds the first racy cell).  When specialization was asked for but
+ * not used, log (may be NULL) receives why. */
 int drf_plan_specialized(const drf_plan *plan, uint32_t *specialized, char *log, size_t loglen);
 
 /* The back end a plan runs: DRF_PATH_SORT or DRF_PATH_TABLE (see
  * DRF_OPT_PATH_*).  With DRF_OPT_AUTOTUNE the tuner times both back ends
  * (the owner table once per granularity) when the owner table fits. */
 int drf_plan_path(const drf_plan *plan, uint32_t *path);
+
+/* Access tuples the last launch applied in its range pass (drf_plan_specialized
+ * reports 3; 0 otherwise): the accesses at +-tid plus a function of the loop
+ * variables, applied task by task in shared memory; the owner-table pass
+ * applied the others.  Waits for the launch. */
+int drf_plan_range_tuples(drf_plan *plan, uint64_t *tuples);
 
 /* Releases the plan's device memory and graph. */
 void drf_plan_destroy(drf_plan *plan);

@@ -38,6 +38,7 @@ struct BatchArgs {
     const DevProto *protos;
     const uint64_t *cells;
     const WarpItem *witems;
+    const uint32_t *iphase;          // per item (item_off + k): its start phase when the protocol is DP_STATIC
     uint32_t nwitems;
     uint32_t nprotos;
     uint32_t has_narrow, has_wide;   // protocols with 32-bit / 64-bit arithmetic present
@@ -61,6 +62,7 @@ struct BatchArgs {
     unsigned long long *status;      // [passes][ntiles][kRadixBins] look-back words
     uint32_t ntiles;
     uint32_t radix_items;            // keys per thread of a radix tile (12, 16 or 24; 0 = 16)
+    uint32_t stall_lookback;         // test hook: radix passes leave tile 0's status out and wait briefly
     TileRec *trec;                   // [ndtiles] detection tile records
     uint32_t ndtiles;
     // per protocol
@@ -75,6 +77,15 @@ struct BatchArgs {
     // owner table (the sort-free path): one record per (protocol, phase,
     // array, index) cell, all zero between launches
     uint32_t path;                   // PATH_SORT or PATH_TABLE
+    // Owner-table launches of a batch whose protocols are all DP_STATIC: no
+    // count or scan pass; the interpreted passes take item phases from
+    // `iphase`, the table pass counts the tuples and writes thread 0's sync
+    // total, and nothing checks barrier divergence (none is possible).
+    uint32_t count_free;
+    // Shard of a one-protocol check (drf_check_shard): the table pass
+    // updates only the records at positions [shard_lo, shard_hi); [0, ~0)
+    // otherwise.
+    unsigned long long shard_lo, shard_hi;
     void *table;                     // [tab_cells] 32-bit owner records, padded to whole blocks
     uint64_t tab_cells;
     uint32_t *touch;                 // one bit per block of kTabBlock records written this launch

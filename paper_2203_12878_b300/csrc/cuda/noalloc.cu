@@ -24,12 +24,17 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = DRF_NOALLOC_SCRATCH_BYTES;
 
 // The scratch array.  In host code its name is only a host-side stand-in:
-// its device address comes from cudaGetSymbolAddress (once per device).
+// its device address comes from cudaGetSymbolAddress, looked up on every
+// call (a lookup allocates nothing), so that a device whose context was torn
+// down and made again (cudaDeviceReset) gets the address of the array in its
+// new context, never a stale one.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char *g_base[kMaxDevices];            // device address of the array, per device
+// One lock per device (the array is per device): held for a whole call, so
+// that calls on one device from several host threads run one after another;
+// calls on different devices proceed in parallel.
+std::mutex g_mu[kMaxDevices];
 
 struct Carver {
     unsigned char *base;
@@ -75,16 +80,18 @@ extern "C" int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_
         fail_result(DRF_E_CUDA, out);
         return DRF_E_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_base[dev]) {
-        // set-up on this device's first call: the array's device address
+    std::lock_guard<std::mutex> lock(g_mu[dev]);
+    // the array's device address in the current context (on a device's first
+    // call this also loads the library's device code there)
+    unsigned char *base = nullptr;
+    {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             fail_result(DRF_E_CUDA, out);
             return DRF_E_CUDA;
         }
-        g_base[dev] = static_cast<unsigned char *>(p);
+        base = static_cast<unsigned char *>(p);
     }
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -101,7 +108,7 @@ extern "C" int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_
     if (!e.ok()) { fail_result(e.status, out); return e.status; }
 
     // carve the fixed buffers; the launch epoch sits first so it survives calls
-    Carver c{g_base[dev]};
+    Carver c{base};
     uint32_t *epoch = c.take<uint32_t>(4);
     BatchArgs a{};
     const uint64_t nw = bh.witems.size();
@@ -112,6 +119,7 @@ extern "C" int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_
     DevProto *protos = c.take<DevProto>(bh.protos.size());
     uint64_t *cells = c.take<uint64_t>(bh.cells.size());
     WarpItem *witems = c.take<WarpItem>(nw);
+    uint32_t *iphase = c.take<uint32_t>(bh.iphase.size());
     a.cnt = c.take<uint32_t>(bh.lanes);
     a.syn = c.take<uint32_t>(bh.lanes);
     a.phs = c.take<uint32_t>(bh.lanes);
@@ -129,6 +137,10 @@ extern "C" int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_
     a.ctrl = c.take<Control>(1);
     if (!c.ok) { fail_result(DRF_E_LIMIT, out); return DRF_E_LIMIT; }
     a.insns = insns; a.xcode = xcode; a.items = items; a.protos = protos; a.cells = cells; a.witems = witems;
+    a.iphase = iphase;
+    a.count_free = 0;
+    a.shard_lo = 0;
+    a.shard_hi = ~0ull;
     a.nwitems = (uint32_t)nw;
     a.nprotos = 1;
     a.ncols = bh.ncols;
@@ -137,7 +149,8 @@ extern "C" int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_
     a.L = bh.L;
     for (const DevProto &d : bh.protos) (d.wide ? a.has_wide : a.has_narrow) = 1;
     if (!put(insns, bh.insns, s) || !put(xcode, bh.xcode, s) || !put(items, bh.items, s) ||
-        !put(protos, bh.protos, s) || !put(cells, bh.cells, s) || !put(witems, bh.witems, s)) {
+        !put(protos, bh.protos, s) || !put(cells, bh.cells, s) || !put(witems, bh.witems, s) ||
+        !put(iphase, bh.iphase, s)) {
         cudaGetLastError();
         fail_result(DRF_E_CUDA, out);
         return DRF_E_CUDA;

@@ -161,7 +161,7 @@ __device__ __forceinline__ void hist_add(EmitShared *sh, const KeyLayout &L, uns
     const int lead = __ffs(om) - 1;
     const uint32_t lane = threadIdx.x & 31;
     for (uint32_t q = 0; q < L.passes; q++) {
-        uint32_t d = (uint32_t)(key >> (L.sort_lo + q * kRadixBits)) & (kRadixBins - 1);
+        uint32_t d = (uint32_t)(key >> (L.sort_lo + q * L.digit_bits)) & ((1u << L.digit_bits) - 1);
         uint32_t d0 = __shfl_sync(kFull, d, lead);
         if (__all_sync(kFull, !ok || d == d0)) {
             if ((int)lane == lead) atomicAdd(&sh->hist[q][d0], (unsigned)__popc(om));
@@ -287,7 +287,9 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
     if (running && pc == it.stop_pc) running = false;
 
     uint32_t phase = 0;
-    if (PHASED && alive) phase = a.phs[li];
+    // count-free launches: every protocol has static phases, and the item's
+    // start phase comes from the host instead of the scan
+    if (PHASED && alive) phase = a.count_free ? __ldg(a.iphase + P.item_off + k) : a.phs[li];
     if (CELL && phase > tg.phase) running = false;     // phases only grow: nothing here reaches the cell
     unsigned long long cursor = 0, wend = 0;
     if (EMIT) {
@@ -334,13 +336,14 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                 if (ok && !put) atomicOr(&a.ctrl->flags, CF_TABLE_RANGE);
                 const unsigned long long off =
                     put ? P.tab_off + (uint64_t)phase * P.cells_sum + __ldg(cb + in.b) + (uint64_t)(U)idx : 0ull;
-                table_put(a, put, off, tid, in.a & AF_WRITE);
+                table_put(a, put && off >= a.shard_lo && off < a.shard_hi, off, tid, in.a & AF_WRITE);
             } else if (CELL) {
                 if (ok && phase == tg.phase && in.b == tg.loc && (unsigned long long)(U)idx == tg.idx)
                     hit |= 1u | ((in.a & AF_WRITE) << 1);
             } else if (ok) {
                 count++;
             }
+            if (TAB && ok) count++;
             if (ok) pc++;
             break;
         }
@@ -446,7 +449,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                                 const unsigned long long off =
                                     put ? P.tab_off + (uint64_t)ph * P.cells_sum + __ldg(cb + loc) + (uint64_t)(U)idx
                                         : 0ull;
-                                table_put(a, put, off, tid, mt & AF_WRITE);
+                                table_put(a, put && off >= a.shard_lo && off < a.shard_hi, off, tid, mt & AF_WRITE);
                             } else if (CELL) {
                                 if (act && ph == tg.phase && loc == tg.loc && (unsigned long long)(U)idx == tg.idx)
                                     hit |= 1u | ((mt & AF_WRITE) << 1);
@@ -455,6 +458,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                     }
                 }
                 if (okb) phase += (uint32_t)(trip * spi);
+                if (TAB && okb) count += (uint32_t)(trip * m);
                 if (CELL && phase > tg.phase) running = false;
             }
             if (okb) pc = mpc + 1 + m;
@@ -485,6 +489,14 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             }
         }
     }
+    if (TAB && a.count_free) {
+        // no count pass ran: the table pass counts the tuples
+        const uint32_t total = __reduce_add_sync(kFull, count);
+        if (lane == 0 && total) {
+            atomicAdd(&a.ptuples[p], (unsigned long long)total);
+            atomicAdd(&a.ctrl->total, (unsigned long long)total);
+        }
+    }
     if (CELL) {
         // the warp's lanes that share a hit word set their bits with one
         // update (a race's cell is usually hit by many threads)
@@ -509,10 +521,23 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
 // cannot keep any of it from running), then waits until the previous kernel
 // has completed and its writes are visible.  Under a plain launch both are
 // no-ops.
+//
+// Then a device-scope acquire fence.  Without it a kernel that follows init
+// directly (no count or scan pass in between) was seen reading, through its
+// SM's L1, owner-record lines that an earlier launch's table pass had
+// loaded before the scan cleared them: a stale non-zero copy made the
+// update skip its claim and OR bits into an empty record (no touch mark, so
+// the record also outlived the launch) -- a false race, in the server test
+// after the suite's earlier work, in three of four runs.  The fence orders
+// every later load of the thread after all writes that happened before the
+// wait returned; with it (and, separately, with record reads through L2)
+// the same runs found no such case.  Every load after it that goes through
+// L1 therefore returns data of this launch or later.
 __device__ __forceinline__ void pdl_begin()
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 __global__ void k_init(BatchArgs a)
@@ -572,8 +597,10 @@ __global__ void __launch_bounds__(256) k_interp(BatchArgs a)
             // only racy protocols whose verdict is not an error or a divergence
             if (wi.proto != tg_proto) {
                 tg_proto = wi.proto;
-                const unsigned long long bp = a.best_pos[wi.proto];
-                tg_live = bp != kNone && a.err_key[wi.proto] == kNone && a.div_tid[wi.proto] == 0xFFFFFFFFu;
+                // the reductions of earlier kernels of this launch, read through L2
+                const unsigned long long bp = __ldcg(a.best_pos + wi.proto);
+                tg_live = bp != kNone && __ldcg(a.err_key + wi.proto) == kNone &&
+                          __ldcg(a.div_tid + wi.proto) == 0xFFFFFFFFu;
                 if (tg_live) tg = decode_cell(a, P, bp);
             }
             if (!tg_live) continue;
@@ -581,16 +608,27 @@ __global__ void __launch_bounds__(256) k_interp(BatchArgs a)
             // or ends before it (the next item starts before it), in every lane
             const uint32_t tid = wi.g * 32 + (threadIdx.x & 31);
             const uint64_t lk = P.lane_off + (uint64_t)wi.k * P.nthreads + tid;
-            const bool reach = tid < P.nthreads && a.phs[lk] <= tg.phase &&
-                               (wi.k + 1 == P.nitems || a.phs[lk + P.nthreads] >= tg.phase);
+            bool reach;
+            if (a.count_free)          // static phases: the same for every thread
+                reach = tid < P.nthreads && __ldg(a.iphase + P.item_off + wi.k) <= tg.phase &&
+                        (wi.k + 1 == P.nitems || __ldg(a.iphase + P.item_off + wi.k + 1) >= tg.phase);
+            else
+                reach = tid < P.nthreads && a.phs[lk] <= tg.phase &&
+                        (wi.k + 1 == P.nitems || a.phs[lk + P.nthreads] >= tg.phase);
             if (!__any_sync(kFull, reach)) continue;
         }
         const ItemDesc it = a.items[P.item_off + wi.k];
         if (MODE != M_COUNT && MODE != M_CELL && wi.k == 0) {
-            // barrier divergence: every thread must run as many syncs as thread 0
             uint32_t tid = wi.g * 32 + (threadIdx.x & 31);
-            if (tid < P.nthreads && a.totsyn[P.tid_off + tid] != a.totsyn[P.tid_off])
+            if (a.count_free) {
+                // static phases: no divergence is possible, and no scan
+                // wrote the sync totals -- thread 0's, which the result
+                // reports, is the protocol's static count
+                if (tid == 0) a.totsyn[P.tid_off] = P.tab_phases - 1;
+            } else if (tid < P.nthreads && a.totsyn[P.tid_off + tid] != a.totsyn[P.tid_off]) {
+                // barrier divergence: every thread must run as many syncs as thread 0
                 atomicMin(&a.div_tid[wi.proto], tid);
+            }
         }
         if (WIDE) run_item<int64_t, MODE>(a, wi.proto, P, it, wi.k, wi.g, w, sh, tg);
         else run_item<int32_t, MODE>(a, wi.proto, P, it, wi.k, wi.g, w, sh, tg);
@@ -729,13 +767,16 @@ __global__ void __launch_bounds__(kRadixThreads, ITEMS >= 24 ? 2 : 3) k_radix(Ba
     A.src = a.keys[before];
     A.dst = a.keys[before ^ 1];
     A.n = a.nkeys;
-    A.shift = a.L.sort_lo + pass * kRadixBits;
-    A.nbits = min((uint32_t)kRadixBits, a.L.sort_bits - pass * kRadixBits);
+    A.shift = a.L.sort_lo + pass * a.L.digit_bits;
+    A.nbits = min(a.L.digit_bits, a.L.sort_bits - pass * a.L.digit_bits);
     A.hist = a.hist + pass * kRadixBins;
     A.status = a.status + (uint64_t)pass * a.ntiles * kRadixBins;
     A.tile_counter = &a.ctrl->tile_counter[pass];
     A.tag = (unsigned long long)(*a.epoch & radix::kTagMask) << radix::kTagShift;
     A.flags = &a.ctrl->flags;
+    // the test hook stalls the look-back and gives each wait 64 spins
+    A.spin_limit = a.stall_lookback ? 64u : radix::kSpinLimit;
+    A.stall_first = a.stall_lookback;
     radix::pass<kRadixThreads, ITEMS>(A, sh);
 }
 
@@ -1130,10 +1171,11 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
     const KeyLayout L = a.L;
     DevResult r = {};
     r.verdict = -1;
-    r.tuples = a.ptuples[p];
-    const unsigned long long ek = a.err_key[p];
-    const unsigned long long bp = a.best_pos[p];
-    const uint32_t dt = a.div_tid[p];
+    // the reductions of earlier kernels of this launch, read through L2
+    r.tuples = __ldcg(a.ptuples + p);
+    const unsigned long long ek = __ldcg(a.err_key + p);
+    const unsigned long long bp = __ldcg(a.best_pos + p);
+    const uint32_t dt = __ldcg(a.div_tid + p);
     if (ek == kNone && P.nthreads && dt == 0xFFFFFFFFu && bp != kNone) {
         uint32_t t0 = 0xFFFFFFFFu, t1 = 0xFFFFFFFFu, w0 = 0xFFFFFFFFu, w1 = 0xFFFFFFFFu;
         unsigned long long seg = 0;
@@ -1192,8 +1234,8 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
                 two_smallest(w0, w1, s_red[2][w]); two_smallest(w0, w1, s_red[3][w]);
             }
             r.verdict = 1;
-            r.phases = a.totsyn[P.tid_off] + 1;
-            r.sync_count_0 = a.totsyn[P.tid_off];
+            r.phases = __ldcg(a.totsyn + P.tid_off) + 1;
+            r.sync_count_0 = __ldcg(a.totsyn + P.tid_off);
             if (TABLE) {
                 const CellTarget c = decode_cell(a, P, bp);
                 r.phase = c.phase;
@@ -1225,13 +1267,13 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
         r.verdict = 0;
         r.phases = 0;
     } else {
-        const uint32_t s0 = a.totsyn[P.tid_off];
+        const uint32_t s0 = __ldcg(a.totsyn + P.tid_off);
         r.phases = s0 + 1;
         r.sync_count_0 = s0;
         if (dt != 0xFFFFFFFFu) {
             r.verdict = 2;
             r.div_tid = dt;
-            r.sync_count_div = a.totsyn[P.tid_off + dt];
+            r.sync_count_div = __ldcg(a.totsyn + P.tid_off + dt);
         } else {
             r.verdict = 0;
         }
@@ -1296,6 +1338,18 @@ static void launch_jit(const void *k, const BatchArgs &a, const JitLaunch *j, cu
     cudaLaunchKernelExC(&c.cfg, k, params);
 }
 
+// The specialized range pass: kJitRangeBlocksPerSm blocks per SM, each
+// holding one task's records in dynamic shared memory.
+static void launch_range(const BatchArgs &a, const JitLaunch *j, cudaStream_t s, int sms)
+{
+    BatchArgs args = a;
+    const uint16_t *shape = j->shape;
+    void *params[] = {&args, &shape};
+    PdlConfig c(dim3((unsigned)sms * kJitRangeBlocksPerSm), dim3(kJitRangeThreads), s);
+    c.cfg.dynamicSmemBytes = kJitRangeSmem;
+    cudaLaunchKernelExC(&c.cfg, j->range, params);
+}
+
 // The interpreter, and specialized kernels without a compiled-in schedule,
 // read the batch's warp-item array: a batch loaded without it cannot run them.
 static bool schedule_missing(const BatchArgs &a, const JitLaunch *j)
@@ -1312,7 +1366,9 @@ cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_
     mark(ev, nev, s);
     k_init<<<(unsigned)((init_n + 255) / 256), 256, 0, s>>>(a);
     mark(ev, nev, s);
-    if (j && j->static_phases) return cudaGetLastError();   // nothing to count or scan
+    // nothing to count or scan: specialized kernels with the phases compiled
+    // in, or interpreted owner-table launches of a batch with static phases
+    if ((j && j->static_phases) || (a.count_free && a.path == PATH_TABLE)) return cudaGetLastError();
     if (j && j->count) {
         launch_jit(j->count, a, j, s, sms);
     } else {
@@ -1346,6 +1402,13 @@ static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms
     if (j && j->table) launch_jit(j->table, a, j, s, sms);
     else launch_interp_pdl<M_TABLE>(a, s, sms);
     mark(ev, nev, s);
+    if (j && j->range) {
+        launch_range(a, j, s, sms);
+        mark(ev, nev, s);
+        launch_jit(j->cell, a, j, s, sms);
+        mark(ev, nev, s);
+        return cudaGetLastError();          // specialized with static phases: the witness pass writes the result
+    }
     const uint64_t cap = (uint64_t)sms * 8;
     uint64_t lgrid = (touch_words(a.tab_cells) + kTabScanThreads - 1) / kTabScanThreads;
     if (lgrid > cap) lgrid = cap;
@@ -1396,16 +1459,17 @@ cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t
     return cudaGetLastError();
 }
 
-int stage_names(const char **names, int cap, uint32_t passes, uint32_t path, bool static_phases)
+int stage_names(const char **names, int cap, uint32_t passes, uint32_t path, bool static_phases, bool count_free,
+                bool range)
 {
     static const char *radix[kMaxPasses] = {"radix0", "radix1", "radix2", "radix3",
                                             "radix4", "radix5", "radix6", "radix7"};
     const char *all[kMaxStages];
     int n = 0;
     all[n++] = "init";
-    if (!static_phases) { all[n++] = "count"; all[n++] = "scan"; }
+    if (!static_phases && !(count_free && path == PATH_TABLE)) { all[n++] = "count"; all[n++] = "scan"; }
     if (path == PATH_TABLE) {
-        all[n++] = "table"; all[n++] = "tscan";
+        all[n++] = "table"; all[n++] = range ? "range" : "tscan";
         all[n++] = static_phases ? "witness+finalize" : "witness";
     } else {
         all[n++] = "emit";

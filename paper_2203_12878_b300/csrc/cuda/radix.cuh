@@ -35,6 +35,10 @@ struct PassArgs {
     unsigned long long *tile_counter;
     unsigned long long tag;          // launch tag, already shifted into place
     unsigned int *flags;             // bit 1: look-back timeout, bit 2: out-of-range scatter
+    uint32_t spin_limit;             // look-back waits per digit before giving up (kSpinLimit normally)
+    // test hook: tile 0 publishes no status, so that the waits of the tiles
+    // after it run out (and the pass reports a look-back timeout)
+    uint32_t stall_first;
 };
 
 __device__ __forceinline__ unsigned lanemask_lt()
@@ -148,7 +152,7 @@ __device__ __forceinline__ void pass(const PassArgs &A, PassShared<BLOCK, ITEMS>
     unsigned long long excl = 0;
     if (t < kBins) {
         unsigned long long *my = A.status + (uint64_t)tile * kBins + t;
-        st_volatile(my, (tile == 0 ? kFlagPrefix : kFlagAgg) | A.tag | cnt);
+        if (!(A.stall_first && tile == 0)) st_volatile(my, (tile == 0 ? kFlagPrefix : kFlagAgg) | A.tag | cnt);
         if (tile > 0) {
             int64_t j = (int64_t)tile - 1;
             uint32_t spins = 0;
@@ -172,7 +176,7 @@ __device__ __forceinline__ void pass(const PassArgs &A, PassShared<BLOCK, ITEMS>
                 if (stop) break;
                 j -= used;
                 if (wait) {
-                    if (++spins > kSpinLimit) { gave_up = true; break; }
+                    if (++spins > A.spin_limit) { gave_up = true; break; }
                     __nanosleep(spins < 64 ? 32 : 256);
                 }
             }

@@ -24,7 +24,7 @@ namespace drf {
 constexpr int kMaxVars = 16;        // loop-variable registers (one per nesting depth)
 constexpr int kMaxStack = 16;       // expression evaluation stack
 constexpr int kMaxPasses = 8;       // radix passes (64 key bits / 8)
-constexpr int kRadixBits = 8;
+constexpr int kRadixBits = 8;       // the widest radix digit (a launch may use narrower ones: KeyLayout::digit_bits)
 constexpr int kRadixBins = 1 << kRadixBits;
 
 // ---------------------------------------------------------------- instructions
@@ -114,7 +114,14 @@ struct DevProto {
     uint64_t tab_off;      // first record of this protocol
     uint64_t cells_sum;    // records per phase row (sum of the array sizes)
     uint32_t tab_phases;   // rows: the static bound on syncs per thread, plus one
-    uint32_t pad;
+    uint32_t flags;        // DP_* below
+};
+
+enum : uint32_t {
+    // every thread runs the same syncs (tab_phases - 1 of them) and no
+    // evaluation can fail; the batch's item-phase array holds, per item, the
+    // phase at its start
+    DP_STATIC = 1,
 };
 
 struct WarpItem {
@@ -133,7 +140,8 @@ struct KeyLayout {
     uint32_t proto_bits;
     uint32_t sort_lo;      // first sort bit = tid_bits + 1
     uint32_t sort_bits;    // idx + loc + phase + proto bits
-    uint32_t passes;       // ceil(sort_bits / kRadixBits)
+    uint32_t passes;       // ceil(sort_bits / digit_bits), at most kMaxPasses
+    uint32_t digit_bits;   // radix digit width, 4..kRadixBits
 };
 
 // Per-launch control block (cleared by the init kernel).
@@ -145,6 +153,7 @@ struct Control {
     unsigned long long touched;        // owner-table blocks listed this launch
     unsigned int blocks_done;          // blocks of the witness pass that have finished
     unsigned int pad;
+    unsigned long long range_tuples;   // access tuples the range pass applied
 };
 
 enum : unsigned {

@@ -57,12 +57,12 @@ const JitEntry *jit_entry(drf_ctx *ctx, const uint8_t *bc, size_t len, const drf
     std::string src, log;
     std::vector<uint16_t> shapes;
     std::vector<char> cubin;
-    bool stat = false, csched = false;
+    bool stat = false, csched = false, range = false;
     auto mod = std::make_unique<JitModule>();
     bh.expand_witems();                            // the generator reads the schedule
-    Error e = jit_source(p, bh, src, shapes, &stat, &csched);
+    Error e = jit_source(p, bh, src, shapes, &stat, &csched, &range);
     if (e.ok()) e = jit_compile(src, cubin, log);
-    if (e.ok()) e = jit_load(cubin, *mod);
+    if (e.ok()) e = jit_load(cubin, *mod, range);
     if (e.ok() && (cudaMalloc(&je->shape, std::max<size_t>(shapes.size() * 2, 16)) != cudaSuccess ||
                    cudaMemcpy(je->shape, shapes.data(), shapes.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess))
         e = Error::make(S_NOMEM, "device allocation failed");
@@ -71,6 +71,7 @@ const JitEntry *jit_entry(drf_ctx *ctx, const uint8_t *bc, size_t len, const drf
         je->launch.count = (const void *)mod->count;
         je->launch.table = (const void *)mod->table;
         je->launch.cell = (const void *)mod->cell;
+        je->launch.range = (const void *)mod->range;
         je->launch.shape = (const uint16_t *)je->shape;
         je->launch.static_phases = stat;
         je->launch.csched = csched;
@@ -261,17 +262,20 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     ctx->last_error.clear();
     PrepareOpts po;
     po.desired_warp_items = std::max<uint64_t>(1, (uint64_t)ctx->sms * 128 / std::max<uint32_t>(1, n));
-    std::vector<Prepared> preps(n);
+    // prepared programs come from the context's cache when the same
+    // protocol was checked before under the same bounds
+    std::vector<std::shared_ptr<const Prepared>> preps(n);
     std::vector<const Prepared *> valid;
     std::vector<uint32_t> where;
     for (uint32_t i = 0; i < n; i++) {
-        Error e = prepare_one(bytecodes[i], lens[i], &bounds[i], po, preps[i]);
+        Error e;
+        preps[i] = ctx->prep_cache.get(bytecodes[i], lens[i], &bounds[i], po, e);
         if (!e.ok()) {
             error_result(e.status, &out[i]);
             if (n == 1) ctx->last_error = e.message;
             continue;
         }
-        valid.push_back(&preps[i]);
+        valid.push_back(preps[i].get());
         where.push_back(i);
     }
     if (valid.empty()) return DRF_OK;
@@ -281,11 +285,11 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     // is expanded only if the kernels that run read it (compiled-in
     // schedules do not)
     const bool jit_try = valid.size() == 1 && (ctx->opts.flags & DRF_OPT_SPECIALIZE) && path_pref_of(ctx->opts) != 1;
-    Error e = pack_batch(valid, bh, !jit_try);
+    Error e = pack_batch(valid, bh, !jit_try, ctx->opts.radix_bits);
     if (e.status == S_KEY_TOO_WIDE && valid.size() > 1) {
         // the combined key does not fit: check the protocols one by one
         for (size_t j = 0; j < valid.size(); j++) {
-            Error ej = pack_batch({valid[j]}, bh);
+            Error ej = pack_batch({valid[j]}, bh, true, ctx->opts.radix_bits);
             if (!ej.ok()) { error_result(ej.status, &out[where[j]]); continue; }
             std::vector<DevResult> r;
             int st = run_batch(ctx, bh, s, r);
@@ -360,6 +364,121 @@ int drf_debug_sorted_keys(drf_ctx *ctx, uint64_t *keys, uint64_t cap, uint64_t *
     uint64_t m = std::min<uint64_t>(cap, a.nkeys);
     if ((ce = cudaMemcpy(keys, a.keys[passes & 1], m * 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(ctx, ce);
+    return DRF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Owner-table positions [lo, hi) of shard k of n of a prepared protocol:
+// the positions phase * (sum of array sizes) + (the array's offset) + index
+// over the phases the static sync bound allows, cut into n equal parts.
+Error shard_window(const Prepared &p, uint32_t shard, uint32_t nshards, uint64_t &lo, uint64_t &hi, uint64_t &total)
+{
+    if (nshards == 0 || shard >= nshards) return Error::make(S_INVALID_ARG, "shard index out of range");
+    unsigned __int128 row = 0;
+    for (uint64_t c : p.cells) row += c;
+    const unsigned __int128 t = row * ((unsigned __int128)p.max_syncs + 1);
+    if (t >= ((unsigned __int128)1 << 63)) return Error::make(S_LIMIT, "more than 2^63 cell positions");
+    total = (uint64_t)t;
+    lo = (uint64_t)(t * shard / nshards);
+    hi = (uint64_t)(t * (shard + 1) / nshards);
+    return Error{};
+}
+
+bool same_facts(const drf_result &a, const drf_result &b)
+{
+    if (a.status != b.status || a.tuples != b.tuples) return false;
+    if (a.status != DRF_OK) return a.err_tid == b.err_tid && a.err_ordinal == b.err_ordinal;
+    if (a.phases != b.phases || a.sync_count_0 != b.sync_count_0) return false;
+    const bool ad = a.verdict == DRF_VERDICT_BARRIER_DIVERGENCE, bd = b.verdict == DRF_VERDICT_BARRIER_DIVERGENCE;
+    if (ad != bd) return false;
+    return !ad || (a.div_tid == b.div_tid && a.sync_count_div == b.sync_count_div);
+}
+
+}  // namespace
+
+extern "C" {
+
+int drf_shard_range(const uint8_t *bytecode, size_t len, const drf_bounds *bounds, uint32_t shard, uint32_t nshards,
+                    uint64_t *lo, uint64_t *hi, uint64_t *positions)
+{
+    if (!lo || !hi) return DRF_E_INVALID_ARG;
+    Prepared p;
+    Error e = prepare_one(bytecode, len, bounds, PrepareOpts{}, p);
+    uint64_t total = 0;
+    if (e.ok()) e = shard_window(p, shard, nshards, *lo, *hi, total);
+    if (e.ok() && positions) *positions = total;
+    return e.status;
+}
+
+int drf_check_shard(drf_ctx *ctx, const uint8_t *bytecode, size_t len, const drf_bounds *bounds, uint32_t shard,
+                    uint32_t nshards, drf_result *out, void *stream)
+{
+    if (!ctx || !out) return DRF_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaError_t ce = cudaSetDevice(ctx->device);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce);
+    ctx->last_error.clear();
+    PrepareOpts po;
+    po.desired_warp_items = (uint64_t)ctx->sms * 128;
+    Prepared p;
+    Error e = prepare_one(bytecode, len, bounds, po, p);
+    uint64_t lo = 0, hi = 0, total = 0;
+    if (e.ok()) e = shard_window(p, shard, nshards, lo, hi, total);
+    if (e.ok()) e = pack_batch({&p}, ctx->host);
+    if (e.ok() && !ctx->host.table_ok) e = Error::make(S_LIMIT, "the protocol's owner table does not fit");
+    if (!e.ok()) {
+        error_result(e.status, out);
+        return fail(ctx, e.status, e.message);
+    }
+    DeviceBatch &w = ctx->work;
+    w.limit = ctx->opts.max_device_bytes;
+    w.path_pref = 2;                          // the shard is a window of the owner table
+    w.shard_lo = lo;
+    w.shard_hi = hi;
+    std::vector<DevResult> r;
+    int st = run_batch(w, ctx->sms, pick(ctx, stream), ctx->host, r, ctx->last_error);
+    w.shard_lo = 0;
+    w.shard_hi = ~0ull;
+    if (st) return st;
+    to_public(r[0], out);
+    return out->status;
+}
+
+int drf_merge_shards(const drf_result *parts, uint32_t n, drf_result *out)
+{
+    if (!parts || !out || n == 0) return DRF_E_INVALID_ARG;
+    for (uint32_t i = 1; i < n; i++)
+        if (!same_facts(parts[0], parts[i])) return DRF_E_INTERNAL;   // the shards disagree on a global fact
+    *out = parts[0];
+    if (out->status != DRF_OK || out->verdict == DRF_VERDICT_BARRIER_DIVERGENCE) return out->status;
+    // the lexicographically smallest racy cell over the shards, with its witness
+    const drf_result *best = nullptr;
+    for (uint32_t i = 0; i < n; i++) {
+        const drf_result &x = parts[i];
+        if (x.verdict != DRF_VERDICT_RACY) continue;
+        if (!best || x.phase < best->phase || (x.phase == best->phase && x.loc < best->loc) ||
+            (x.phase == best->phase && x.loc == best->loc && x.index < best->index))
+            best = &x;
+    }
+    if (best) {
+        *out = *best;
+    } else {
+        out->verdict = DRF_VERDICT_DRF;
+        out->phase = out->loc = 0;
+        out->index = 0;
+        out->tid_i = out->tid_j = out->i_writes = out->j_writes = 0;
+    }
+    return DRF_OK;
+}
+
+int drf_debug_stall_lookback(drf_ctx *ctx, uint32_t launches)
+{
+    if (!ctx) return DRF_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->work.stall_lookback = launches;
     return DRF_OK;
 }
 
@@ -442,7 +561,7 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
     plan->ctx = ctx;
     plan->n = n;
     plan->cfg = cfg;
-    Error e = pack_batch(ptrs, plan->host);
+    Error e = pack_batch(ptrs, plan->host, true, cfg.radix_bits ? cfg.radix_bits : ctx->opts.radix_bits);
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
     cudaStream_t s = ctx->stream;
     DeviceBatch &d = plan->dev;
@@ -458,13 +577,13 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
         std::vector<uint16_t> shapes;
         std::vector<char> cubin;
         auto mod = std::make_unique<JitModule>();
-        bool stat = false, csched = false;
-        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes, &stat, &csched)
+        bool stat = false, csched = false, range = false;
+        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes, &stat, &csched, &range)
                    : Error::make(S_INVALID_ARG, "specialization takes a plan of one protocol");
         d.jit.static_phases = stat;
         d.jit.csched = csched;
         if (e.ok()) e = jit_compile(src, cubin, plan->jit_log);
-        if (e.ok()) e = jit_load(cubin, *mod);
+        if (e.ok()) e = jit_load(cubin, *mod, range);
         if (e.ok() && (!ensure(d.ishape, std::max<size_t>(shapes.size() * 2, 16), &d.in_use, d.limit) ||
                        cudaMemcpyAsync(d.ishape.p, shapes.data(), shapes.size() * 2, cudaMemcpyHostToDevice, s) !=
                            cudaSuccess))
@@ -479,6 +598,7 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
         d.jit.count = (const void *)plan->jit->count;
         d.jit.table = (const void *)plan->jit->table;
         d.jit.cell = (const void *)plan->jit->cell;
+        d.jit.range = (const void *)plan->jit->range;
         d.jit.shape = (const uint16_t *)d.ishape.p;
     }
     cudaError_t ce;
@@ -486,6 +606,7 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
     // plan's launches leave them out
     JitLaunch sizing = d.jit;
     sizing.static_phases = false;
+    sizing.range = nullptr;
     if ((ce = launch_front(d.args, s, ctx->sms, nullptr, nullptr, &sizing)) != cudaSuccess ||
         (ce = d.fetch(s, true)) != cudaSuccess || (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
         delete plan;
@@ -506,6 +627,9 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
     }
     for (uint32_t i = 0; i < n; i++)
         if (res[i].status) { delete plan; return fail(ctx, res[i].status, "protocol " + std::to_string(i) + " fails to evaluate"); }
+    // the plan's own launches: interpreted owner-table launches of a batch
+    // whose protocols all have static phases need no count or scan pass
+    d.args.count_free = (!cfg.jit && d.args.path == PATH_TABLE && plan->host.all_static) ? 1u : 0u;
     *out = plan;
     return DRF_OK;
 }
@@ -655,12 +779,30 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
                 }
                 drf_plan_destroy(cand);
             }
+            // the radix digit width, on the fastest sort-path configuration
+            // (unless the context fixes it)
+            if (best_cfg.path == 1 && ctx->opts.radix_bits == 0) {
+                for (uint32_t bits : kTuneRadixBits) {
+                    PlanConfig c = best_cfg;
+                    c.radix_bits = bits;
+                    drf_plan *cand = nullptr;
+                    if (build_plan(ctx, n, bytecodes, lens, bounds, c, &cand)) continue;
+                    double ms = time_plan(cand, kTuneReps, flush, flush_bytes);
+                    if (ms < best) {
+                        best = ms;
+                        best_cfg = c;
+                        std::swap(plan, cand);
+                    }
+                    drf_plan_destroy(cand);
+                }
+            }
             if (flush) cudaFree(flush);
             tune_store(key, best_cfg, best);
             kept = true;
         }
         if (!kept && (best_cfg.granularity != plan->cfg.granularity || best_cfg.radix_items != plan->cfg.radix_items ||
-                      best_cfg.path != plan->cfg.path || best_cfg.jit != plan->cfg.jit)) {
+                      best_cfg.path != plan->cfg.path || best_cfg.jit != plan->cfg.jit ||
+                      best_cfg.radix_bits != plan->cfg.radix_bits)) {
             drf_plan_destroy(plan);
             plan = nullptr;
             if ((st = build_plan(ctx, n, bytecodes, lens, bounds, best_cfg, &plan))) return st;
@@ -671,18 +813,19 @@ int drf_plan_create(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     return DRF_OK;
 }
 
-int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix_items)
+int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix_items, uint32_t *radix_bits)
 {
     if (!plan) return DRF_E_INVALID_ARG;
     if (granularity) *granularity = plan->cfg.granularity;
     if (radix_items) *radix_items = plan->cfg.radix_items;
+    if (radix_bits) *radix_bits = plan->host.L.digit_bits;
     return DRF_OK;
 }
 
 int drf_plan_specialized(const drf_plan *plan, uint32_t *specialized, char *log, size_t loglen)
 {
     if (!plan || !specialized) return DRF_E_INVALID_ARG;
-    *specialized = plan->jit ? (plan->dev.jit.static_phases ? 2 : 1) : 0;
+    *specialized = plan->jit ? (plan->dev.jit.range ? 3 : plan->dev.jit.static_phases ? 2 : 1) : 0;
     if (log && loglen) {
         std::strncpy(log, plan->jit_log.c_str(), loglen - 1);
         log[loglen - 1] = 0;
@@ -741,7 +884,9 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
     if (sort_passes) *sort_passes = table ? 0 : plan->host.L.passes;
     if (kernels_per_launch) {
         uint32_t widths = plan->dev.args.has_narrow + plan->dev.args.has_wide;
-        if (table && plan->dev.jit.static_phases) *kernels_per_launch = 5;   // init, table, tlist, tscan, witness + finalize
+        if (table && plan->dev.jit.range) *kernels_per_launch = 4;   // init, table, range, witness + finalize
+        else if (table && plan->dev.jit.static_phases) *kernels_per_launch = 5;   // init, table, tlist, tscan, witness + finalize
+        else if (table && plan->dev.args.count_free) *kernels_per_launch = 2 * widths + 4;   // init, 2x interp, tlist, tscan, finalize
         else if (table) *kernels_per_launch = 3 * widths + 5;   // init, 3x interp, scan, tlist, tscan, finalize
         else *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes;   // init, 2x interp, scan, passes, detect, resolve, finalize
     }
@@ -759,7 +904,8 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(plan->ctx, e);
     const char *all[kMaxStages];
-    int nn = stage_names(all, kMaxStages, plan->host.L.passes, plan->dev.args.path, plan->dev.jit.static_phases);
+    int nn = stage_names(all, kMaxStages, plan->host.L.passes, plan->dev.args.path, plan->dev.jit.static_phases,
+                         plan->dev.args.count_free != 0, plan->dev.jit.range != nullptr);
     int n = std::min(nn, plan->nevents - 1);
     for (int i = 0; i < n && i < cap; i++) {
         float t = 0;
@@ -768,6 +914,19 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
         if (ms) ms[i] = t;
         (*count)++;
     }
+    return DRF_OK;
+}
+
+int drf_plan_range_tuples(drf_plan *plan, uint64_t *tuples)
+{
+    if (!plan || !tuples) return DRF_E_INVALID_ARG;
+    drf_ctx *ctx = plan->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = plan->last_stream ? plan->last_stream : ctx->stream;
+    cudaError_t e;
+    if ((e = plan->dev.fetch(s, true)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(ctx, e);
+    *tuples = plan->dev.host_ctrl()->range_tuples;
     return DRF_OK;
 }
 

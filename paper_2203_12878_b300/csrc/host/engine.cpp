@@ -43,7 +43,7 @@ void BatchHost::expand_witems()
         for (uint32_t g = 0; g < r.groups; g++) *wi++ = WarpItem{r.proto, r.k, g};
 }
 
-Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool expand)
+Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool expand, uint32_t digit_bits)
 {
     // cleared, not reassigned: a reused image keeps its vectors' capacity
     out.insns.clear();
@@ -53,11 +53,13 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
     out.cells.clear();
     out.cbase.clear();
     out.witems.clear();
+    out.iphase.clear();
     out.runs.clear();
     out.nwitems = 0;
     out.ncols = out.lanes = out.tuple_bound = out.table_cells = 0;
     out.L = KeyLayout{};
     out.table_ok = false;
+    out.all_static = !ps.empty();
     KeyLayout L{};
     const uint32_t n = (uint32_t)ps.size();
     L.proto_bits = n > 1 ? bits_for(n - 1) : 0;
@@ -72,7 +74,12 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
     if (L.sort_lo + L.sort_bits > 64)
         return Error::make(S_KEY_TOO_WIDE, "phase, array, index and thread fields need " +
                                                std::to_string(L.sort_lo + L.sort_bits) + " bits");
-    L.passes = (L.sort_bits + kRadixBits - 1) / kRadixBits;
+    // the digit width asked for (4..8), widened when the sort key would need
+    // more than kMaxPasses passes of it
+    L.digit_bits = std::min<uint32_t>(kRadixBits, std::max<uint32_t>(4, digit_bits ? digit_bits : kRadixBits));
+    if ((L.sort_bits + L.digit_bits - 1) / L.digit_bits > (uint32_t)kMaxPasses)
+        L.digit_bits = (L.sort_bits + kMaxPasses - 1) / kMaxPasses;
+    L.passes = L.sort_bits ? (L.sort_bits + L.digit_bits - 1) / L.digit_bits : 0;
     out.L = L;
 
     // one entry per (protocol, item); its thread groups follow it in order
@@ -102,6 +109,10 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
         d.tab_off = out.table_cells;
         d.cells_sum = row;
         d.tab_phases = p.max_syncs < 0xFFFFFFFFull ? (uint32_t)(p.max_syncs + 1) : 0;
+        const bool stat = p.static_phases && p.item_phase.size() == p.items.size() && d.tab_phases;
+        d.flags = stat ? DP_STATIC : 0;
+        out.all_static = out.all_static && stat;
+        for (size_t k = 0; k < p.items.size(); k++) out.iphase.push_back(stat ? p.item_phase[k] : 0u);
         if (!d.tab_phases || (row && (unsigned __int128)row * d.tab_phases > kMaxTableBytes)) table_fits = false;
         else out.table_cells += row * d.tab_phases;
         if (out.table_cells > kMaxTableBytes) table_fits = false;
@@ -181,7 +192,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     size_t end = 0;
     const Section sec[] = {section(b.insns, end), section(b.xcode, end), section(b.items, end),
                            section(b.protos, end), section(b.cells, end), section(b.cbase, end),
-                           section(b.witems, end)};
+                           section(b.witems, end), section(b.iphase, end)};
     const size_t total = std::max<size_t>(end, 256);
     bool ok = ensure(image, total, &in_use, limit);
     // the previous copy out of the stage must be done before it is rewritten
@@ -243,6 +254,8 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.cbase = (const uint64_t *)(img + sec[5].off);
     // without its expansion, kernels that read the schedule refuse to launch
     a.witems = b.expanded() ? (const WarpItem *)(img + sec[6].off) : nullptr;
+    a.iphase = (const uint32_t *)(img + sec[7].off);
+    a.count_free = 0;
     a.nwitems = (uint32_t)nw;
     a.nprotos = (uint32_t)np;
     a.has_narrow = a.has_wide = 0;
@@ -267,6 +280,9 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.epoch = (uint32_t *)epoch.p;
     a.L = b.L;
     a.radix_items = radix_items;
+    a.stall_lookback = 0;
+    a.shard_lo = shard_lo;
+    a.shard_hi = shard_hi;
     a.nkeys = 0;
     a.ntiles = 0;
     a.keys[0] = (unsigned long long *)keys0.p;
@@ -293,6 +309,9 @@ Error DeviceBatch::size_table(const BatchHost &b, uint64_t n, cudaStream_t s)
     if (!ensure(table, tb, &in_use, limit) || !ensure(touch, wb, &in_use, limit) ||
         !ensure(tlist, lb, &in_use, limit) || !ensure(hit, nhit * 8, &in_use, limit)) {
         cudaGetLastError();
+        // the table or its touch bits may have moved to fresh memory that was
+        // not cleared: clear them when the next launch sizes them
+        if (table.p != old_table || touch.p != old_touch) table_dirty = true;
         return Error::make(S_NOMEM, "device allocation of a " + std::to_string(tb) + "-byte owner table failed");
     }
     // the kernels keep the table and its touch bits all zero between
@@ -400,6 +419,7 @@ int run_batch(DeviceBatch &w, int sms, cudaStream_t s, const BatchHost &b, std::
     if (b.table_ok && w.path_pref != 1 && (w.path_pref == 2 || auto_path(b, b.tuple_bound) == PATH_TABLE)) {
         e = w.size_table(b, kUncounted, s);
         if (e.ok()) {
+            w.args.count_free = b.all_static ? 1u : 0u;   // nothing to count first: no count or scan pass
             w.status_launches++;
             if (launch_front(w.args, s, sms, nullptr, nullptr) != cudaSuccess ||
                 launch_back(w.args, s, sms, nullptr, nullptr) != cudaSuccess || w.fetch(s, false) != cudaSuccess ||
@@ -419,8 +439,14 @@ int run_batch(DeviceBatch &w, int sms, cudaStream_t s, const BatchHost &b, std::
         return S_CUDA;
     }
     const uint64_t n = w.host_ctrl()->total;
+    w.args.count_free = 0;                           // the count pass ran
     e = w.choose_path(b, n, s);
     if (!e.ok()) { err = e.message; return e.status; }
+    w.args.stall_lookback = 0;
+    if (w.stall_lookback && w.args.path == PATH_SORT) {
+        w.args.stall_lookback = 1;
+        w.stall_lookback--;
+    }
     w.status_launches++;
     if (launch_back(w.args, s, sms, nullptr, nullptr) != cudaSuccess || w.fetch(s, false) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -457,6 +483,43 @@ int run_batch_jit(drf_ctx *ctx, const BatchHost &b, const JitLaunch &j, cudaStre
         return S_CUDA;
     }
     return collect(w, out, ctx->last_error);
+}
+
+std::shared_ptr<const Prepared> PrepCache::get(const uint8_t *bc, size_t len, const drf_bounds *b,
+                                               const PrepareOpts &po, Error &err)
+{
+    err = Error{};
+    if (!bc || !b) {
+        err = Error::make(S_INVALID_ARG, "null bytecode or bounds");
+        return nullptr;
+    }
+    if ((b->nlocs && !b->loc_cells) || (b->nparams && !b->params)) {
+        err = Error::make(S_INVALID_ARG, "null array sizes or params");
+        return nullptr;
+    }
+    std::string key;
+    key.reserve(len + 64 + 8 * (b->nlocs + b->nparams));
+    auto put = [&key](const void *x, size_t n) { key.append((const char *)x, n); };
+    put(&po, sizeof po);
+    put(&b->nthreads, sizeof b->nthreads);
+    put(&b->nlocs, sizeof b->nlocs);
+    if (b->nlocs) put(b->loc_cells, b->nlocs * sizeof(uint64_t));
+    put(&b->nparams, sizeof b->nparams);
+    if (b->nparams) put(b->params, b->nparams * sizeof(int64_t));
+    put(&len, sizeof len);
+    put(bc, len);
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        auto it = map_.find(key);
+        if (it != map_.end()) return it->second;
+    }
+    auto p = std::make_shared<Prepared>();
+    err = prepare(bc, len, b->nthreads, b->nlocs, b->loc_cells, b->nparams, b->params, po, *p);
+    if (!err.ok()) return nullptr;
+    std::lock_guard<std::mutex> g(mu_);
+    if (map_.size() >= kCap) map_.clear();
+    map_.emplace(std::move(key), p);
+    return p;
 }
 
 int path_pref_of(const drf_opts &o)

@@ -8,6 +8,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../../include/drf.h"
@@ -50,6 +51,11 @@ struct BatchHost {
     KeyLayout L{};
     uint64_t table_cells = 0;        // owner-table records of the whole batch
     bool table_ok = false;           // the owner-table path can run this batch
+    // per item (batch order): its start phase for DP_STATIC protocols, else 0
+    std::vector<uint32_t> iphase;
+    // every protocol is DP_STATIC: owner-table launches may leave the count
+    // and scan passes out (BatchArgs::count_free)
+    bool all_static = false;
     uint64_t table_bytes() const { return table_cells * 4; }   // one 32-bit owner record per cell
 };
 
@@ -57,8 +63,10 @@ struct BatchHost {
 constexpr uint64_t kMaxTableBytes = 64ull << 30;
 
 // Packs prepared protocols (all valid) into a batch; fails with
-// S_KEY_TOO_WIDE when the combined key layout exceeds 64 bits.
-Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool expand = true);
+// S_KEY_TOO_WIDE when the combined key layout exceeds 64 bits.  digit_bits:
+// the sort path's radix digit width (4..8; 0 = 8).
+Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool expand = true,
+                 uint32_t digit_bits = 0);
 
 // Offset of the results after the control block in a batch's report.
 constexpr size_t kOutResults = 128;
@@ -89,6 +97,9 @@ struct DeviceBatch {
     uint32_t radix_items = 16;                // radix tile shape (tuning choice)
     int path_pref = 0;                        // 0: choose per batch, 1: sort path, 2: owner-table path
     bool table_dirty = false;                 // a failed launch may have left records behind
+    uint32_t stall_lookback = 0;              // test hook: launches left whose radix look-back stalls
+    // drf_check_shard: the owner-table positions the launches update
+    unsigned long long shard_lo = 0, shard_hi = ~0ull;
     JitLaunch jit{};                          // specialized kernels (plans over one protocol)
     BatchArgs args{};
 
@@ -127,6 +138,21 @@ struct JitEntry {
     ~JitEntry();
 };
 
+// Prepared protocols of earlier checks, keyed by the bytecode, the bounds
+// and the preparation options (a check of a protocol seen before skips
+// validation, interval analysis, lowering and the item cut).  Thread-safe;
+// at most kCap entries, then it starts over.
+class PrepCache {
+public:
+    std::shared_ptr<const Prepared> get(const uint8_t *bc, size_t len, const drf_bounds *b, const PrepareOpts &po,
+                                        Error &err);
+
+private:
+    static constexpr size_t kCap = 4096;
+    std::mutex mu_;
+    std::unordered_map<std::string, std::shared_ptr<const Prepared>> map_;
+};
+
 struct Timing;
 
 }  // namespace drf
@@ -144,6 +170,7 @@ struct drf_ctx {
     // specialized kernels of protocols checked before, keyed by bytecode and
     // bounds (DRF_OPT_SPECIALIZE; at most kJitCacheEntries, then cleared)
     std::map<std::string, std::unique_ptr<drf::JitEntry>> jit_cache;
+    drf::PrepCache prep_cache;        // prepared protocols of earlier checks and server requests
 };
 
 struct drf_plan {

@@ -64,6 +64,118 @@ class Gen {
 
     std::string error;
 
+    // Accesses whose records the range pass makes (RangeAccess): the table
+    // pass counts them and leaves their records alone.
+    void set_range_skip(const std::set<uint32_t> &pcs) { skip_ = pcs; }
+
+    // The range pass's code for access `r` (number k), inside its task loop
+    // (see kRangeHelpers): for every iteration of the access's loops one
+    // thread finds the tids whose index lands in the task's records
+    // [r0, r1) -- at most two intervals -- and the block applies them to
+    // the records in shared memory.  `sb`: the first record of the access's
+    // (phase, array) segment; `ncells`: the array's size.
+    bool range_code(const RangeAccess &r, uint32_t k, uint64_t sb, uint64_t ncells, uint32_t T, uint32_t RT,
+                    std::ostringstream &o)
+    {
+        mode_ = GM_CELL;
+        body_.str("");
+        tmp_ = 0;
+        fail_label_ = "rskip" + std::to_string(k);
+        const std::string K = std::to_string(k), TL = std::to_string(T) + "ll";
+        body_ << "    {   // access at pc " << r.pc << ": phase " << r.phase << ", array " << r.loc
+              << (r.write ? ", write" : ", read") << "\n";
+        body_ << "    const unsigned long long sb = " << ulit(sb) << ", se = " << ulit(sb + ncells) << ";\n";
+        body_ << "    if (sb < r1 && se > r0) {\n";
+        body_ << "    const long long lo_c = (long long)((r0 > sb ? r0 : sb) - sb);\n";
+        body_ << "    const long long hi_c = (long long)((r1 < se ? r1 : se) - sb);\n";
+        body_ << "    const long long loc0 = (long long)sb - (long long)r0;\n";
+        body_ << "    for (unsigned long long f0 = 0; f0 < " << ulit(r.iters) << "; f0 += " << RT << "u) {\n";
+        body_ << "    const unsigned long long f = f0 + threadIdx.x;\n";
+        body_ << "    long long ta = 0, na = 0, la = 0, tb = 0, nb = 0, lb = 0;\n";
+        body_ << "    if (f < " << ulit(r.iters) << ") {\n";
+        body_ << "        " << V_ << " v[" << kMaxVars << "];\n        (void)v;\n";
+        body_ << "        unsigned long long q = f;\n";
+        const size_t nl = r.loops.size();
+        for (size_t i = nl; i-- > 0;) {
+            body_ << "        const unsigned long long d" << i << " = "
+                  << (i ? "q % " + ulit(r.loops[i].trip_max) : std::string("q")) << ";\n";
+            if (i) body_ << "        q /= " << ulit(r.loops[i].trip_max) << ";\n";
+        }
+        for (size_t i = 0; i < nl; i++) {
+            const RangeLoop &L = r.loops[i];
+            body_ << "        {\n";
+            std::string lo = expr(L.lo), hi = expr(L.hi);
+            if (!error.empty()) return false;
+            const std::string va = "v[" + std::to_string(L.reg) + "]";
+            body_ << "        " << va << " = (" << V_ << ")((" << U_ << ")" << lo << " + (" << U_ << ")d" << i << ");\n";
+            body_ << "        if (!(" << va << " < " << hi << ")) goto " << fail_label_ << ";\n";
+            body_ << "        }\n";
+        }
+        for (const auto &g : r.guards) {
+            body_ << "        {\n";
+            std::string c = expr(g.first);
+            if (!error.empty()) return false;
+            body_ << "        if (" << (g.second ? "!" : "") << "(" << c << ")) goto " << fail_label_ << ";\n";
+            body_ << "        }\n";
+        }
+        std::string c = expr(r.cexpr);
+        if (!error.empty()) return false;
+        body_ << "        const long long c = (long long)" << c << ";\n";
+        body_ << "        long long te;\n";
+        if (r.modn == 0 && r.sigma == 1) {
+            body_ << "        ta = lo_c - c; if (ta < 0) ta = 0; te = hi_c - c; if (te > " << TL << ") te = " << TL << ";\n"
+                  << "        na = te - ta; la = ta + c + loc0;\n";
+        } else if (r.modn == 0) {
+            body_ << "        ta = c - hi_c + 1; if (ta < 0) ta = 0; te = c - lo_c + 1; if (te > " << TL << ") te = " << TL << ";\n"
+                  << "        na = te - ta; la = c - ta + loc0;\n";
+        } else {
+            const std::string N = std::to_string(r.modn) + "ll";
+            body_ << "        long long cm = c % " << N << "; if (cm < 0) cm += " << N << ";\n";
+            if (r.sigma == 1) {
+                // tids below N - cm do not wrap around N; the others do
+                body_ << "        ta = lo_c - cm; if (ta < 0) ta = 0; te = hi_c - cm;\n"
+                      << "        { const long long lim = " << N << " - cm < " << TL << " ? " << N << " - cm : " << TL
+                      << "; if (te > lim) te = lim; }\n"
+                      << "        na = te - ta; la = ta + cm + loc0;\n"
+                      << "        tb = lo_c - cm + " << N << "; if (tb < " << N << " - cm) tb = " << N << " - cm;\n"
+                      << "        te = hi_c - cm + " << N << "; if (te > " << TL << ") te = " << TL << ";\n"
+                      << "        nb = te - tb; lb = tb + cm - " << N << " + loc0;\n";
+            } else {
+                // tids up to cm do not wrap below 0; the others do
+                body_ << "        ta = cm - hi_c + 1; if (ta < 0) ta = 0; te = cm - lo_c + 1;\n"
+                      << "        { const long long lim = cm + 1 < " << TL << " ? cm + 1 : " << TL << "; if (te > lim) te = lim; }\n"
+                      << "        na = te - ta; la = cm - ta + loc0;\n"
+                      << "        tb = cm + " << N << " - hi_c + 1; if (tb < cm + 1) tb = cm + 1;\n"
+                      << "        te = cm + " << N << " - lo_c + 1; if (te > " << TL << ") te = " << TL << ";\n"
+                      << "        nb = te - tb; lb = cm + " << N << " - tb + loc0;\n";
+            }
+        }
+        body_ << "    }\n";
+        body_ << fail_label_ << ":;\n";
+        // the block applies the intervals: one record update per (tid, interval)
+        body_ << "    if (__syncthreads_or(na > 0 || nb > 0)) {\n"
+              << "        if (na > 0) { const uint32_t e = atomicAdd(&s_n, 1u); s_ent[e] = REnt{(uint32_t)ta, (uint32_t)na, (int32_t)la}; }\n"
+              << "        if (nb > 0) { const uint32_t e = atomicAdd(&s_n, 1u); s_ent[e] = REnt{(uint32_t)tb, (uint32_t)nb, (int32_t)lb}; }\n"
+              << "        if (!live) range_zero(rec);\n"
+              << "        __syncthreads();\n"
+              << "        live = true;\n"
+              << "        const uint32_t n = s_n;\n"
+              << "        if (threadIdx.x == 0) for (uint32_t e = 0; e < n; e++) rtuples += s_ent[e].len;\n"
+              << "        for (uint32_t e = 0; e < n; e++) {\n"
+              << "            const REnt x = s_ent[e];\n"
+              << "            for (uint32_t o = threadIdx.x; o < x.len; o += " << RT << "u)\n"
+              << "                range_put(rec + (x.l0 " << (r.sigma == 1 ? "+" : "-") << " (int32_t)o), x.t0 + o, "
+              << (r.write ? 1 : 0) << "u);\n"
+              << "        }\n"
+              << "        __syncthreads();\n"
+              << "        if (threadIdx.x == 0) s_n = 0;\n"
+              << "    }\n";
+        body_ << "    }\n    }\n    }\n";
+        fail_label_ = "done";
+        o << body_.str();
+        return error.empty();
+    }
+
     // One device function per (shape, mode).
     bool shape_fn(const ShapeKey &k, uint32_t id, Mode m, std::ostringstream &o)
     {
@@ -142,6 +254,8 @@ class Gen {
     std::map<uint32_t, bool> labels_skip_;
     std::set<uint32_t> jump_targets_;      // every jump target of the item being generated
     int slot_ = 0;                         // names of batched-update temporaries
+    std::set<uint32_t> skip_;              // accesses the range pass applies
+    std::string fail_label_ = "done";      // where a division by zero jumps (not count pass)
 
     // One access of a batch of owner-table updates: the access applies when
     // `k` holds; `o` is its record offset and `c` a copy of its record.
@@ -191,7 +305,7 @@ class Gen {
         return false;
     }
 
-    std::string fail_div0() const { return mode_ == GM_COUNT ? "{ err = 2u; goto done; }" : "goto done;"; }
+    std::string fail_div0() const { return mode_ == GM_COUNT ? "{ err = 2u; goto done; }" : "goto " + fail_label_ + ";"; }
 
     std::string temp(const std::string &e)
     {
@@ -347,6 +461,7 @@ class Gen {
         std::vector<std::string> idx;
         for (uint32_t q = pc; q < end; q++) {
             const Insn &A = p_.insns.at(q);
+            if (skip_.count(q)) { idx.emplace_back(); continue; }     // the range pass applies it
             idx.push_back(expr(A.c));
             if (!error.empty()) return false;
             body_ << "        if (" << idx.back() << " < 0 || (uint64_t)(" << U_ << ")" << idx.back() << " >= "
@@ -358,6 +473,7 @@ class Gen {
         std::vector<Slot> S;
         for (uint32_t q = pc; q < end; q++) {
             const Insn &A = p_.insns.at(q);
+            if (skip_.count(q)) continue;
             const std::string sfx = std::to_string(slot_++);
             body_ << "        const toff_t o" << sfx << " = kr ? " << offset("phase", A.b, idx[q - pc]) << " : (toff_t)0;\n";
             body_ << "        const uint32_t c" << sfx << " = kr ? __ldca(tab + o" << sfx << ") : 0u;\n";
@@ -471,6 +587,15 @@ class Gen {
                     return std::string("drf::floor_div<") + V_ + ", " + U_ + ">(" + v + ", " + cast(lit64((int64_t)pcon)) + ")";
                 return v;
             };
+            uint32_t kept = 0;
+            for (uint32_t j = 0; j < m; j++) kept += skip_.count(pc + 1 + j) ? 0 : 1;
+            if (mode_ == GM_TABLE && kept == 0) {
+                // every access of the loop is the range pass's: count them
+                body_ << "        nacc += (uint32_t)(trip * " << m << "u);\n";
+                if (spi) body_ << "        phase += (uint32_t)(trip * " << spi << "u);\n";
+                body_ << "        }\n    }\n";
+                return true;
+            }
             if (mode_ == GM_TABLE) {
                 // groups of UF iterations: every record copy of a group is
                 // read before any update (a copy older than an update of the
@@ -492,6 +617,7 @@ class Gen {
                     body_ << "        const uint32_t p" << qs << " = phase + (uint32_t)((t + " << q << "u) * " << spi << "u);\n";
                     for (uint32_t j = 0; j < m; j++) {
                         const Insn &A = p_.insns.at(pc + 1 + j);
+                        if (skip_.count(pc + 1 + j)) continue;        // the range pass applies it
                         const std::string sfx = qs + "_" + std::to_string(j);
                         body_ << "        const " << V_ << " i" << sfx << " = " << idx_of(j, "x" + qs) << ";\n";
                         body_ << "        const uint32_t h" << sfx << " = p" << qs << " + " << (uint32_t)A.e << "u;\n";
@@ -703,16 +829,52 @@ static __device__ __forceinline__ void put_warp_cur(uint32_t *table, uint32_t *t
 
 )DRF";
 
+// The range pass: one block per task of kRangeRecs consecutive owner
+// records, held in shared memory while the accesses that land there are
+// applied.  kRangeRecs is a multiple of the records one touch word covers
+// (32 blocks of 256), so that every task owns its touch words.
+constexpr uint64_t kRangeRecs = 16384;
+constexpr uint32_t kRangeThreads = 512;
+
+const char *kRangeHelpers = R"DRF(
+#define RANGE_RECS 16384u
+#define RANGE_THREADS 512u
+// tids [t0, t0 + len) of one iteration of one access, and the record (in the
+// task's shared copy) that tid t0 updates; the others follow at +-1
+struct REnt { uint32_t t0, len; int32_t l0; };
+
+// drf::owner_put on a record in shared memory (no touch marks: the range
+// pass scans the whole task)
+static __device__ __forceinline__ void range_put(uint32_t *r, uint32_t tid, uint32_t w)
+{
+    uint32_t cur = *reinterpret_cast<volatile uint32_t *>(r);
+    if (cur == 0u) {
+        const uint32_t old = atomicCAS(r, 0u, (tid + 1u) | (w << 31));
+        if (old == 0u) return;
+        cur = old;
+    }
+    const uint32_t need = drf::owner_need(cur, tid, w);
+    if (need) atomicOr(r, need);
+}
+
+static __device__ __forceinline__ void range_zero(uint32_t *rec)
+{
+    uint4 *v = reinterpret_cast<uint4 *>(rec);
+    for (uint32_t i = threadIdx.x; i < RANGE_RECS / 4u; i += RANGE_THREADS) v[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+)DRF";
+
 constexpr size_t kMaxConstItems = 1024;  // items whose schedule and positions are compiled in
 constexpr uint64_t kMaxPhaseRanges = 1u << 16;   // phases whose item ranges are compiled in
 
 }  // namespace
 
 Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::vector<uint16_t> &item_shape,
-                 bool *static_phases, bool *compiled_schedule)
+                 bool *static_phases, bool *compiled_schedule, bool *range_pass)
 {
     if (static_phases) *static_phases = false;
     if (compiled_schedule) *compiled_schedule = false;
+    if (range_pass) *range_pass = false;
     if (b.protos.size() != 1) return Error::make(S_INVALID_ARG, "specialization takes a batch of one protocol");
     if (!b.table_ok) return Error::make(S_LIMIT, "the protocol has no owner table");
     const DevProto &d = b.protos[0];
@@ -800,6 +962,32 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
         for (uint64_t ph = 0; ph < nph; ph++) o << (ph ? "," : "") << phi[ph] << "u";
         o << "};\n";
     }
+    // The range pass (with static phases, one protocol at the table's
+    // start): the accesses it can take (RangeAccess) when visiting their
+    // iterations once per task of their segment costs no more than visiting
+    // them once per thread would, and they make a quarter of the tuples or
+    // more.
+    std::vector<const RangeAccess *> racc;
+    const uint64_t tab_end = d.tab_off + (uint64_t)d.tab_phases * d.cells_sum;
+    if (stat && d.tab_off == 0 && tab_end > 0 && d.nthreads > 0 && (tab_end + kRangeRecs - 1) / kRangeRecs <= (1ull << 24)) {
+        unsigned __int128 rt = 0;
+        for (const RangeAccess &r : p.range_access) {
+            if (r.iters == 0 || r.iters > (1ull << 24) || r.phase >= d.tab_phases || r.loc >= d.nlocs) continue;
+            const uint64_t seg_tasks = p.cells.at(r.loc) / kRangeRecs + 2;
+            const uint64_t rounds = (r.iters + kRangeThreads - 1) / kRangeThreads;
+            if ((unsigned __int128)seg_tasks * rounds * kRangeThreads > (unsigned __int128)d.nthreads * r.iters) continue;
+            racc.push_back(&r);
+            rt += (unsigned __int128)d.nthreads * r.iters;
+        }
+        if (racc.size() > 256 || rt * 4 < (unsigned __int128)p.tuple_bound()) racc.clear();
+    }
+    const bool range = !racc.empty();
+    if (range_pass) *range_pass = range;
+    if (range) {
+        std::set<uint32_t> pcs;
+        for (const RangeAccess *r : racc) pcs.insert(r->pc);
+        g.set_range_skip(pcs);
+    }
     const Mode modes[] = {GM_COUNT, GM_TABLE, GM_CELL};
     for (Mode m : modes)
         for (size_t s = 0; s < keys.size(); s++)
@@ -853,10 +1041,14 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
        << "        (void)shp; (void)li;\n";
     const std::string loop_head = lh.str();
     // every kernel lets its successor launch, then waits for its predecessor
-    // (programmatic dependent launch; no-ops under a plain launch)
+    // (programmatic dependent launch; no-ops under a plain launch), then
+    // issues a device-scope acquire fence so that none of its loads through
+    // L1 returns data older than what the wait made visible (the pipeline's
+    // pdl_begin says why)
     const char *sig = "(drf::BatchArgs a, const uint16_t *__restrict__ shape)\n{\n    (void)shape;\n"
                       "    asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n"
-                      "    asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n";
+                      "    asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
+                      "    asm volatile(\"fence.acq_rel.gpu;\" ::: \"memory\");\n";
     // count pass: the interpreter's M_COUNT outputs
     o << "extern \"C\" __global__ void __launch_bounds__(256) drf_count" << sig << loop_head
       << "        uint32_t count = 0, syncs = 0, err = 0;\n"
@@ -920,8 +1112,8 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
     // finalize pass of the interpreted pipeline), so the launch needs no
     // further kernel
     o << "extern \"C\" __global__ void __launch_bounds__(256) drf_cell" << sig
-      << "    const unsigned long long bp = a.best_pos[0];\n"
-      << "    const bool live = !(bp == ~0ull || a.err_key[0] != ~0ull || a.div_tid[0] != 0xFFFFFFFFu);\n"
+      << "    const unsigned long long bp = __ldcg(&a.best_pos[0]);\n"
+      << "    const bool live = !(bp == ~0ull || __ldcg(&a.err_key[0]) != ~0ull || __ldcg(&a.div_tid[0]) != 0xFFFFFFFFu);\n"
       << "    CellTarget tg{};\n"
       << "    if (live) {\n"
       << "    {\n"
@@ -1044,6 +1236,79 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
 )DRF";
     }
     o << "}\n";
+    if (range) {
+        // the range pass: in place of the touch listing and table scan
+        const uint64_t ntasks = (tab_end - d.tab_off + kRangeRecs - 1) / kRangeRecs;
+        o << kRangeHelpers;
+        o << "extern \"C\" __global__ void __launch_bounds__(" << kRangeThreads << ") drf_range" << sig
+          << R"DRF(    extern __shared__ uint4 r_dyn[];
+    uint32_t *const rec = reinterpret_cast<uint32_t *>(r_dyn);
+    __shared__ REnt s_ent[2 * RANGE_THREADS];
+    __shared__ uint32_t s_n, s_bits[RANGE_RECS / 8192u];
+    __shared__ unsigned int s_best;
+    // the witness pass's hit bits, which the touch listing clears otherwise
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.nhit; i += (uint64_t)gridDim.x * blockDim.x) {
+        a.hit_acc[i] = 0u;
+        a.hit_wr[i] = 0u;
+    }
+    uint32_t *const tab = reinterpret_cast<uint32_t *>(a.table);
+    if (threadIdx.x == 0) s_n = 0;
+    unsigned long long rtuples = 0;        // thread 0: the tuples this block applied
+)DRF";
+        o << "    for (unsigned long long task = blockIdx.x; task < " << ulit(ntasks) << "; task += gridDim.x) {\n"
+          << "    const unsigned long long r0 = " << ulit(d.tab_off) << " + task * RANGE_RECS;\n"
+          << "    const unsigned long long r1 = r0 + RANGE_RECS < " << ulit(tab_end) << " ? r0 + RANGE_RECS : " << ulit(tab_end)
+          << ";\n"
+          << R"DRF(    const uint32_t nrec = (uint32_t)(r1 - r0);
+    const uint32_t nwords = (nrec + 8191u) >> 13;
+    __syncthreads();                       // the previous task is done with rec and s_bits
+    uint32_t tb_bits = 0;
+    if (threadIdx.x < nwords) {
+        // through L2: this SM's L1 may hold lines the table pass read
+        tb_bits = __ldcg(a.touch + (r0 >> 13) + threadIdx.x);
+        s_bits[threadIdx.x] = tb_bits;
+        if (tb_bits) a.touch[(r0 >> 13) + threadIdx.x] = 0u;
+    }
+    bool live = __syncthreads_or(tb_bits != 0u) != 0;
+    if (live) {
+        // the records the table pass made in touched blocks of the task:
+        // merged into the shared copy, and cleared (the table is all zero
+        // between launches)
+        range_zero(rec);
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nrec; i += RANGE_THREADS) {
+            const uint32_t blk = i >> 8;
+            if ((s_bits[blk >> 5] >> (blk & 31u)) & 1u) {
+                const uint32_t v = __ldcg(tab + r0 + i);
+                if (v) { rec[i] = v; tab[r0 + i] = 0u; }
+            }
+        }
+        __syncthreads();
+    }
+)DRF";
+        for (size_t k = 0; k < racc.size(); k++) {
+            const RangeAccess &r = *racc[k];
+            const uint64_t sb = d.tab_off + (uint64_t)r.phase * d.cells_sum + b.cbase.at(d.cells_off + r.loc);
+            if (!g.range_code(r, (uint32_t)k, sb, p.cells.at(r.loc), d.nthreads, kRangeThreads, o))
+                return Error::make(S_LIMIT, "cannot specialize the range pass: " + g.error);
+        }
+        o << R"DRF(    if (live) {
+        // the task's first racy record (rows are phase-major, then array,
+        // then index: the lexicographic order of the witness)
+        uint32_t best = 0xFFFFFFFFu;
+        for (uint32_t i = threadIdx.x; i < nrec; i += RANGE_THREADS)
+            if (drf::owner_racy(rec[i])) { best = i; break; }
+        if (threadIdx.x == 0) s_best = 0xFFFFFFFFu;
+        __syncthreads();
+        if (best != 0xFFFFFFFFu) atomicMin(&s_best, best);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_best != 0xFFFFFFFFu) atomicMin(&a.best_pos[0], r0 + s_best);
+    }
+    }
+    if (threadIdx.x == 0 && rtuples) atomicAdd(&a.ctrl->range_tuples, rtuples);
+}
+)DRF";
+    }
     src = o.str();
     if (src.size() > kMaxSourceBytes) return Error::make(S_LIMIT, "specialized source too large");
     return Error{};
@@ -1115,8 +1380,9 @@ Error jit_compile(const std::string &src, std::vector<char> &cubin, std::string 
     return e;
 }
 
-Error jit_load(const std::vector<char> &cubin, JitModule &m)
+Error jit_load(const std::vector<char> &cubin, JitModule &m, bool want_range)
 {
+    static_assert(kJitRangeSmem == kRangeRecs * 4, "the range pass holds its task's records in shared memory");
     cudaError_t ce = cudaLibraryLoadData(&m.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&m.count, m.lib, "drf_count");
     if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&m.table, m.lib, "drf_table");
@@ -1124,6 +1390,17 @@ Error jit_load(const std::vector<char> &cubin, JitModule &m)
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return Error::make(S_CUDA, std::string("loading the specialized kernels: ") + cudaGetErrorString(ce));
+    }
+    if (want_range) {
+        int dev = 0;
+        ce = cudaLibraryGetKernel(&m.range, m.lib, "drf_range");
+        if (ce == cudaSuccess) ce = cudaGetDevice(&dev);
+        if (ce == cudaSuccess)
+            ce = cudaKernelSetAttributeForDevice(m.range, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJitRangeSmem, dev);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return Error::make(S_CUDA, std::string("loading the range pass: ") + cudaGetErrorString(ce));
+        }
     }
     return Error{};
 }

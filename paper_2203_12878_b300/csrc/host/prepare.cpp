@@ -709,6 +709,154 @@ struct Splitter {
     }
 };
 
+// Finds the accesses of a protocol with static phases that the range pass
+// can apply (RangeAccess): walks the statements in program order keeping the
+// phase (the syncs every thread has run), the enclosing loops and the
+// enclosing conditions.
+struct RangeFinder {
+    const Analyzer &an;
+    Lowerer &lw;
+    uint32_t T;
+    std::vector<RangeLoop> loops;
+    std::vector<std::pair<int32_t, bool>> guards;
+    std::vector<RangeAccess> out;
+
+    static bool has_tid(const Expr &e)
+    {
+        if (e.op == EOp::Tid) return true;
+        return (e.a && has_tid(*e.a)) || (e.b && has_tid(*e.b));
+    }
+
+    static bool cond_has_tid(const Cond &c)
+    {
+        if ((c.a && has_tid(*c.a)) || (c.b && has_tid(*c.b))) return true;
+        return (c.l && cond_has_tid(*c.l)) || (c.r && cond_has_tid(*c.r));
+    }
+
+    // The coefficient of tid when e is tid times it plus a part without tid
+    // (tid only under sums, differences, negations and products by
+    // constants); false otherwise.
+    bool tid_coef(const Expr &e, i128 &k)
+    {
+        if (!has_tid(e)) { k = 0; return true; }
+        switch (e.op) {
+        case EOp::Tid: k = 1; return true;
+        case EOp::Neg: if (!tid_coef(*e.a, k)) return false; k = -k; return true;
+        case EOp::Add: case EOp::Sub: {
+            i128 a, b;
+            if (!tid_coef(*e.a, a) || !tid_coef(*e.b, b)) return false;
+            k = e.op == EOp::Add ? a + b : a - b;
+            return k < ((i128)1 << 62) && k > -((i128)1 << 62);
+        }
+        case EOp::Mul: {
+            const bool ta = has_tid(*e.a);
+            Lowerer::Lin c = lw.linear(ta ? *e.b : *e.a);
+            if (!c.ok || !c.terms.empty()) return false;
+            i128 x;
+            if (!tid_coef(ta ? *e.a : *e.b, x)) return false;
+            k = x * c.c0;
+            return k < ((i128)1 << 62) && k > -((i128)1 << 62);
+        }
+        default: return false;
+        }
+    }
+
+    // A copy of e with tid replaced by 0.
+    static ExprP at_tid_zero(const Expr &e)
+    {
+        auto r = std::make_unique<Expr>();
+        if (e.op == EOp::Tid) { r->op = EOp::Const; r->value = 0; return r; }
+        r->op = e.op;
+        r->value = e.value;
+        r->slot = e.slot;
+        if (e.a) r->a = at_tid_zero(*e.a);
+        if (e.b) r->b = at_tid_zero(*e.b);
+        return r;
+    }
+
+    void access(const Stmt &s, uint32_t pc, i128 phase)
+    {
+        if (guards.size() > 8 || loops.size() > 8 || phase >= ((i128)1 << 31)) return;
+        const Expr *e = s.index.get();
+        uint64_t modn = 0;
+        if (e->op == EOp::Mod) {
+            Lowerer::Lin d = lw.linear(*e->b);
+            if (!d.ok || !d.terms.empty() || d.c0 <= 0 || d.c0 >= ((i128)1 << 62)) return;
+            modn = (uint64_t)d.c0;
+            if (T > modn) return;             // at most two tid intervals per cell range
+            e = e->a.get();
+        }
+        i128 k = 0;
+        if (!tid_coef(*e, k) || (k != 1 && k != -1)) return;
+        RangeAccess r;
+        r.pc = pc;
+        r.phase = (uint32_t)phase;
+        r.loc = s.loc;
+        r.write = s.write;
+        r.sigma = (int32_t)k;
+        r.modn = modn;
+        ExprP c0 = at_tid_zero(*e);
+        r.cexpr = lw.expr_code(*c0);
+        r.loops = loops;
+        r.guards = guards;
+        i128 it = 1;
+        for (const RangeLoop &l : loops) it = mul_sat(it, (i128)l.trip_max);
+        r.iters = it > ((i128)1 << 62) ? (1ull << 62) : (uint64_t)it;
+        out.push_back(std::move(r));
+    }
+
+    // Returns the phase after s; `ok`: s's accesses may still qualify.
+    i128 walk(const Stmt &s, i128 phase, bool ok)
+    {
+        switch (s.op) {
+        case SOp::Skip: return phase;
+        case SOp::Sync: return phase + 1;
+        case SOp::Access:
+            if (ok) access(s, (uint32_t)lw.range.at(&s).first, phase);
+            return phase;
+        case SOp::Seq:
+            for (auto &it : s.items) phase = walk(*it, phase, ok);
+            return phase;
+        case SOp::If: {
+            const int32_t c = lw.insns.at((size_t)lw.range.at(&s).first).c;
+            const bool gok = ok && !cond_has_tid(*s.cond);
+            guards.emplace_back(c, true);
+            walk(*s.then_s, phase, gok);
+            guards.back().second = false;
+            walk(*s.else_s, phase, gok);
+            guards.pop_back();
+            return phase + an.work.at(&s).syncs;    // (no sync inside an if)
+        }
+        case SOp::ForU:
+        case SOp::ForS: {
+            const i128 after = phase + an.work.at(&s).syncs;
+            const bool in_one_phase = an.work.at(s.body.get()).syncs == 0;
+            const bool bok = ok && in_one_phase && !has_tid(*s.lo) && !has_tid(*s.hi) && an.loops.at(&s).trip_max > 0;
+            const uint32_t lpc = (uint32_t)lw.range.at(&s).first;
+            const Insn &L = lw.insns.at(lpc);
+            loops.push_back(RangeLoop{L.a, L.c, L.d, (uint64_t)std::min<i128>(an.loops.at(&s).trip_max, (i128)1 << 40)});
+            if (lw.fast.count(&s)) {
+                // a fast loop: its accesses follow its instruction in body order
+                uint32_t j = 0;
+                std::vector<const Stmt *> body;
+                if (s.body->op == SOp::Seq) for (auto &it : s.body->items) body.push_back(it.get());
+                else body.push_back(s.body.get());
+                for (const Stmt *b : body)
+                    if (b->op == SOp::Access) {
+                        if (bok) access(*b, lpc + 1 + j, phase);
+                        j++;
+                    }
+            } else {
+                walk(*s.body, phase, bok);
+            }
+            loops.pop_back();
+            return after;
+        }
+        }
+        return phase;
+    }
+};
+
 }  // namespace
 
 Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, const uint64_t *cells,
@@ -813,6 +961,12 @@ Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, 
     out.static_phases = constant_syncs && !may_fail && iphase.size() == items.size();
     for (uint64_t ph : iphase) if (ph > w.syncs) out.static_phases = false;
     if (out.static_phases) out.item_phase.assign(iphase.begin(), iphase.end());
+    if (out.static_phases && nthreads > 0) {
+        RangeFinder rf{an, lw, nthreads};
+        rf.walk(*p.body, 0, true);
+        out.range_access = std::move(rf.out);
+        if (lw.xcode.size() > (1u << 26)) return Error::make(S_LIMIT, "protocol too large");
+    }
 
     out.insns = std::move(lw.insns);
     out.xcode = std::move(lw.xcode);

@@ -21,6 +21,30 @@ struct PrepareOpts {
     uint32_t max_items = 1u << 14;
 };
 
+// An access the owner table's range pass can apply cell by cell: it runs in
+// one phase (no enclosing loop holds a sync), its enclosing loops' bounds
+// and conditions do not read tid, and its index is (sigma * tid + c) or
+// (sigma * tid + c) mod modn with sigma = +1 or -1 and c a function of the
+// loop variables alone.  The threads that reach a given range of cells in
+// one iteration are then one or two intervals of tids, found without
+// visiting the others.
+struct RangeLoop {
+    uint32_t reg;                 // the loop variable's register
+    int32_t lo, hi;               // expression code of the bounds
+    uint64_t trip_max;            // trip count bound over all outer iterations
+};
+struct RangeAccess {
+    uint32_t pc;                  // its I_ACCESS or I_FASTACC instruction
+    uint32_t phase, loc;
+    bool write;
+    int32_t sigma;                // +1 or -1
+    uint64_t modn;                // 0: no remainder; else the index is a Euclidean remainder by modn
+    int32_t cexpr;                // expression code of the index before the remainder, at tid = 0
+    std::vector<RangeLoop> loops; // enclosing loops, outermost first
+    std::vector<std::pair<int32_t, bool>> guards;   // enclosing conditions' code and the branch taken
+    uint64_t iters;               // product of the loops' trip bounds (saturated)
+};
+
 struct Prepared {
     uint32_t nthreads = 0;
     uint32_t narrays = 0;
@@ -37,6 +61,8 @@ struct Prepared {
     // can fail; item_phase then holds, per item, the phase at its start.
     bool static_phases = false;
     std::vector<uint32_t> item_phase;
+    // With static phases: the accesses the range pass can take (see RangeAccess)
+    std::vector<RangeAccess> range_access;
 
     uint64_t tuple_bound() const { return (uint64_t)nthreads * max_tuples; }
 };

@@ -98,9 +98,15 @@ public:
             std::lock_guard<std::mutex> g(mu_);
             backlog = pending_.size();
         }
+        // (the desired warp items are rounded down to a power of two, so that
+        // a protocol seen before reuses its prepared program from the
+        // context's cache at most backlog levels)
         PrepareOpts po;
-        po.desired_warp_items = std::max<uint64_t>((uint64_t)ctx_->sms * 2, (uint64_t)ctx_->sms * 128 / (1 + backlog));
-        Error e = prepare(bc, len, b->nthreads, b->nlocs, b->loc_cells, b->nparams, b->params, po, r->prep);
+        uint64_t want = std::max<uint64_t>((uint64_t)ctx_->sms * 2, (uint64_t)ctx_->sms * 128 / (1 + backlog));
+        while (want & (want - 1)) want &= want - 1;
+        po.desired_warp_items = want;
+        Error e;
+        r->prep = ctx_->prep_cache.get(bc, len, b, po, e);
         std::lock_guard<std::mutex> g(mu_);
         if (stopping_) return S_BUSY;
         if (queue_.size() >= opts_.max_queue) return S_BUSY;
@@ -150,7 +156,7 @@ private:
 
     struct Request {
         uint64_t ticket = 0;
-        Prepared prep;
+        std::shared_ptr<const Prepared> prep;
         Clock::time_point t_submit;
     };
     struct Done {
@@ -219,7 +225,7 @@ private:
                 if (queue_.empty()) return;                 // stopping and drained
                 uint64_t budget = 0;
                 while (!queue_.empty() && round.size() < opts_.max_round_protocols) {
-                    uint64_t tb = queue_.front()->prep.tuple_bound();
+                    uint64_t tb = queue_.front()->prep->tuple_bound();
                     if (!round.empty() && budget + tb > opts_.max_round_tuples) break;
                     budget += tb;
                     round.push_back(std::move(queue_.front()));
@@ -236,31 +242,40 @@ private:
         }
     }
 
+    // A round's protocols [lo, hi) as one batch.  A batch that fails as a
+    // whole for want of room -- its combined key wider than 64 bits, its
+    // buffers beyond the context's device-memory cap, its owner table beyond
+    // the limit -- is run again in halves, down to single protocols, so that
+    // every request gets the result it would get alone, whatever it was
+    // mixed with.
+    void run_group(Lane &lane, const std::vector<const Prepared *> &ps, size_t lo, size_t hi,
+                   std::vector<drf_result> &res)
+    {
+        BatchHost &bh = lane.host;
+        std::string err;
+        std::vector<DevResult> dr;
+        std::vector<const Prepared *> part(ps.begin() + (long)lo, ps.begin() + (long)hi);
+        Error e = pack_batch(part, bh, true, ctx_->opts.radix_bits);
+        int st = e.status;
+        if (e.ok()) st = run_batch(lane.dev, ctx_->sms, lane.s, bh, dr, err);
+        if (st == S_OK) {
+            for (size_t i = lo; i < hi; i++) to_public(dr[i - lo], &res[i]);
+            return;
+        }
+        if (hi - lo > 1 && (st == S_KEY_TOO_WIDE || st == S_NOMEM || st == S_LIMIT)) {
+            const size_t mid = lo + (hi - lo) / 2;
+            run_group(lane, ps, lo, mid, res);
+            run_group(lane, ps, mid, hi, res);
+            return;
+        }
+        for (size_t i = lo; i < hi; i++) { res[i] = drf_result{}; res[i].status = st; res[i].verdict = -1; }
+    }
+
     void run_round(Lane &lane, const std::vector<std::unique_ptr<Request>> &round, std::vector<drf_result> &res)
     {
         std::vector<const Prepared *> ps;
-        for (auto &r : round) ps.push_back(&r->prep);
-        BatchHost &bh = lane.host;
-        std::string err;
-        Error e = pack_batch(ps, bh);
-        std::vector<DevResult> dr;
-        if (e.ok()) {
-            int st = run_batch(lane.dev, ctx_->sms, lane.s, bh, dr, err);
-            if (st == S_OK) {
-                for (size_t i = 0; i < round.size(); i++) to_public(dr[i], &res[i]);
-                return;
-            }
-            for (auto &r : res) { r = drf_result{}; r.status = st; r.verdict = -1; }
-            return;
-        }
-        // the combined key is too wide: one protocol per pass
-        for (size_t i = 0; i < round.size(); i++) {
-            Error ei = pack_batch({ps[i]}, bh);
-            int st = ei.status;
-            if (ei.ok()) st = run_batch(lane.dev, ctx_->sms, lane.s, bh, dr, err);
-            if (st == S_OK) to_public(dr[0], &res[i]);
-            else { res[i] = drf_result{}; res[i].status = st; res[i].verdict = -1; }
-        }
+        for (auto &r : round) ps.push_back(r->prep.get());
+        run_group(lane, ps, 0, ps.size(), res);
     }
 };
 

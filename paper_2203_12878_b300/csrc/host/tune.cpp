@@ -1,5 +1,6 @@
 // Tuning cache (see tune.h).  File format, one entry per line:
-//   <signature> <granularity> <radix_items> <path> <specialized> <milliseconds>
+//   <signature> <granularity> <radix_items> <path> <specialized> <radix_bits> <milliseconds>
+// (lines without the digit width, from earlier files, read as width 0)
 #include "tune.h"
 
 #include <cstdio>
@@ -8,6 +9,8 @@
 #include <map>
 #include <mutex>
 #include <sstream>
+#include <stdexcept>
+#include <vector>
 
 namespace drf {
 namespace {
@@ -32,10 +35,20 @@ void load_locked()
     std::string line;
     while (std::getline(f, line)) {
         std::istringstream in(line);
-        std::string key, extra;
-        PlanConfig c;
-        double ms;
-        if ((in >> key >> c.granularity >> c.radix_items >> c.path >> c.jit >> ms) && !(in >> extra)) g_cache[key] = c;
+        std::vector<std::string> tok;
+        std::string t;
+        while (in >> t) tok.push_back(t);
+        if (tok.size() != 6 && tok.size() != 7) continue;
+        try {
+            PlanConfig c;
+            c.granularity = (uint32_t)std::stoul(tok[1]);
+            c.radix_items = (uint32_t)std::stoul(tok[2]);
+            c.path = (uint32_t)std::stoul(tok[3]);
+            c.jit = (uint32_t)std::stoul(tok[4]);
+            if (tok.size() == 7) c.radix_bits = (uint32_t)std::stoul(tok[5]);
+            g_cache[tok[0]] = c;
+        } catch (const std::exception &) {
+        }
     }
 }
 
@@ -59,7 +72,8 @@ void tune_store(const std::string &key, const PlanConfig &cfg, double ms)
     const char *path = cache_path();
     if (!path) return;
     if (FILE *f = std::fopen(path, "a")) {
-        std::fprintf(f, "%s %u %u %u %u %.4f\n", key.c_str(), cfg.granularity, cfg.radix_items, cfg.path, cfg.jit, ms);
+        std::fprintf(f, "%s %u %u %u %u %u %.4f\n", key.c_str(), cfg.granularity, cfg.radix_items, cfg.path, cfg.jit,
+                     cfg.radix_bits, ms);
         std::fclose(f);
     }
 }

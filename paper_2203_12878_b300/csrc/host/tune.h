@@ -12,7 +12,11 @@ struct PlanConfig {
     uint32_t radix_items = 16;    // keys per thread of a radix tile (12, 16 or 24)
     uint32_t path = 0;            // back end: 0 the context's choice, 1 sort, 2 owner table
     uint32_t jit = 0;             // 1: kernels specialized to the (single) protocol
+    uint32_t radix_bits = 0;      // sort path: radix digit width (4..8); 0 = the context's choice
 };
+
+// Digit widths the tuner tries on the fastest sort-path configuration.
+constexpr uint32_t kTuneRadixBits[] = {6, 7};
 
 // Candidate configurations the tuner times.
 constexpr uint32_t kTuneGranularity[] = {32, 128, 512};

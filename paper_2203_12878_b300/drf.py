@@ -102,6 +102,13 @@ _SIGS = {
     "drf_ctx_transfer_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "drf_debug_sorted_keys": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64,
                                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)]),
+    "drf_debug_stall_lookback": (ctypes.c_int, [_P, ctypes.c_uint32]),
+    "drf_shard_range": (ctypes.c_int, [_U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds), ctypes.c_uint32,
+                                       ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "drf_check_shard": (ctypes.c_int, [_P, _U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds), ctypes.c_uint32,
+                                       ctypes.c_uint32, ctypes.POINTER(drf_result), _P]),
+    "drf_merge_shards": (ctypes.c_int, [ctypes.POINTER(drf_result), ctypes.c_uint32, ctypes.POINTER(drf_result)]),
     "drf_check_param_sweep": (ctypes.c_int, [_P, _U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds), ctypes.c_uint32,
                                              ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(drf_result), _P]),
     "drf_plan_create": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.POINTER(_U8P), ctypes.POINTER(ctypes.c_size_t),
@@ -112,12 +119,14 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "drf_plan_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
-    "drf_plan_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
+    "drf_plan_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(ctypes.c_uint32)]),
     "drf_plan_path": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
     "drf_plan_specialized": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32), ctypes.c_char_p, ctypes.c_size_t]),
     "drf_protocol_specialize": (ctypes.c_int, [_U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds),
                                                ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p,
                                                ctypes.c_size_t]),
+    "drf_plan_range_tuples": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "drf_plan_destroy": (None, [_P]),
     "drf_server_start": (ctypes.c_int, [_P, ctypes.POINTER(drf_server_opts)]),
     "drf_server_submit": (ctypes.c_int, [_P, _U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds),
@@ -338,6 +347,48 @@ def drf_ctx_transfer_bytes(ctx):
     return h.value, d.value
 
 
+def drf_shard_range(bytecode: bytes, nthreads: int, cells, params, shard: int, nshards: int):
+    """(lo, hi, total) cell positions of shard `shard` of `nshards` (host only)."""
+    _keep, p, n = _bytes(bytecode)
+    b = Bounds(nthreads, cells, params)
+    lo, hi, tot = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    st = lib().drf_shard_range(p, n, ctypes.byref(b.c), shard, nshards, ctypes.byref(lo), ctypes.byref(hi),
+                               ctypes.byref(tot))
+    if st != 0:
+        raise DrfError(st)
+    return lo.value, hi.value, tot.value
+
+
+def drf_check_shard(ctx, bytecode: bytes, nthreads: int, cells, params, shard: int, nshards: int,
+                    stream=None) -> drf_result:
+    """The result of shard `shard` of `nshards` of one protocol (see drf.h)."""
+    _keep, p, n = _bytes(bytecode)
+    b = Bounds(nthreads, cells, params)
+    r = drf_result()
+    st = lib().drf_check_shard(ctx, p, n, ctypes.byref(b.c), shard, nshards, ctypes.byref(r), _stream(stream))
+    if st != 0 and r.status == 0:
+        raise DrfError(st, drf_last_error(ctx))
+    return r
+
+
+def drf_merge_shards(parts) -> drf_result:
+    """One protocol's result from its shards' results (host only)."""
+    arr = (drf_result * max(1, len(parts)))(*parts)
+    out = drf_result()
+    st = lib().drf_merge_shards(arr, len(parts), ctypes.byref(out))
+    if st != 0 and out.status == 0:
+        raise DrfError(st)
+    return out
+
+
+def drf_debug_stall_lookback(ctx, launches: int = 1) -> None:
+    """Test hook: the context's next `launches` sort-path checks stall their
+    radix look-back briefly and report DRF_E_TIMEOUT."""
+    st = lib().drf_debug_stall_lookback(ctx, launches)
+    if st != 0:
+        raise DrfError(st)
+
+
 def drf_debug_sorted_keys(ctx):
     """(sorted keys as a numpy uint64 array, layout dict) of the last check."""
     import numpy as np
@@ -410,16 +461,26 @@ def drf_plan_stage_times(plan) -> list:
 
 
 def drf_plan_config(plan) -> dict:
-    g, it = ctypes.c_uint32(), ctypes.c_uint32()
-    st = lib().drf_plan_config(plan, ctypes.byref(g), ctypes.byref(it))
+    g, it, rb = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    st = lib().drf_plan_config(plan, ctypes.byref(g), ctypes.byref(it), ctypes.byref(rb))
     if st != 0:
         raise DrfError(st)
-    return {"granularity": g.value, "radix_items": it.value}
+    return {"granularity": g.value, "radix_items": it.value, "radix_bits": rb.value}
+
+
+def drf_plan_range_tuples(plan) -> int:
+    """Access tuples the plan's last launch applied in its range pass."""
+    n = ctypes.c_uint64()
+    st = lib().drf_plan_range_tuples(plan, ctypes.byref(n))
+    if st != 0:
+        raise DrfError(st)
+    return n.value
 
 
 def drf_plan_specialized(plan):
     """(0: interpreted, 1: specialized kernels, 2: specialized with static
-    phases -- no count or scan pass; why not specialized when asked for)."""
+    phases -- no count or scan pass, 3: the same with the range pass; why
+    not specialized when asked for)."""
     v = ctypes.c_uint32()
     log = ctypes.create_string_buffer(4096)
     st = lib().drf_plan_specialized(plan, ctypes.byref(v), log, len(log))

@@ -30,6 +30,12 @@ Workload families (all seeded with ``random.Random``):
 * ``config4``     -- a batch of protocols with log-uniform thread counts in
                      32..1024, depth <= 2, trip counts 1..32, 1..4 phases,
                      1..3 arrays of 2^12..2^18 cells, 20% with a planted race.
+* ``shifted_small``-- mid-sized protocols (hundreds to thousands of threads,
+                     arrays of odd sizes up to ~40,000 cells, 1..3 phases)
+                     whose indices are mostly +-tid plus a function of the
+                     loop variables (with or without a remainder), mixed with
+                     accesses of other tid coefficients and conditions on the
+                     loop variables; races arise where such ranges overlap.
 """
 from __future__ import annotations
 
@@ -391,6 +397,72 @@ def _nest_protocol(r, top, narrays, cells, nthreads, mode, plant):
     decl = f"array {', '.join('ABCD'[i] for i in range(narrays))};\n"
     text = decl + "\n".join(_render(top)) + "\n"
     return text, meta
+
+
+# ---------------------------------------------------------- shifted_small --
+
+def shifted_small(seed: int) -> Protocol:
+    """A protocol of the shape described in the module header
+    (``shifted_small``): every index provably inside its array, the same
+    sync structure for every thread."""
+    r = random.Random(0x5F17 ^ (seed * 2246822519))
+    nthreads = r.choice([r.randint(100, 700), r.randint(700, 4100)])
+    narrays = r.randint(1, 3)
+    names = "ABC"[:narrays]
+    cells = [r.randint(nthreads + 1, 41000) for _ in range(narrays)]
+    lines = [f"array {', '.join(names)};"]
+    nphases = r.randint(1, 3)
+    # quiet seeds: in each phase one array is written, only at cells
+    # tid + T * (its iteration), and only the other arrays are read -- race-free
+    quiet = r.random() < 0.4
+    if quiet:
+        cells = [max(c, nthreads * 40) for c in cells]
+    for ph in range(nphases):
+        if ph:
+            lines.append("sync;")
+        for _ in range(r.randint(1, 3)):
+            depth = r.randint(1, 2)
+            vs = ["x", "y"][:depth]
+            trips = [r.randint(1, 6) for _ in vs]
+            body = []
+            for _ in range(r.randint(1, 3)):
+                a = r.randrange(narrays)
+                n = cells[a]
+                if quiet:
+                    w = ph % narrays
+                    if a == w:
+                        body.append(f"wr {names[a]}[tid + {nthreads} * (({' + '.join(vs)}) % 40)];")
+                    elif narrays > 1:
+                        body.append(f"rd {names[a]}[({r.choice(['', '-1 * '])}tid + {r.randint(0, 999)} * {vs[0]}) % {n}];")
+                    continue
+                mode = r.choice(["rd", "wr", "wr"])
+                kind = r.random()
+                if kind < 0.4:              # (+-tid + f(x, y)) mod m, m <= the array, m >= threads
+                    m = r.randint(nthreads, n)
+                    sgn = r.choice(["", "-1 * "])
+                    f = " + ".join(f"{r.randint(0, 9000)} * {v}" for v in vs)
+                    body.append(f"{mode} {names[a]}[({sgn}tid + {f} + {r.randint(-5000, 5000)}) % {m}];")
+                elif kind < 0.65:           # tid + g(x, y) with no remainder, kept in range
+                    span = n - nthreads
+                    g = f"(({' + '.join(f'{r.randint(1, 5)} * {v}' for v in vs)}) % {max(1, span // 8)})"
+                    body.append(f"{mode} {names[a]}[tid + {g} * {r.randint(0, 8)}];")
+                elif kind < 0.75:           # -tid + c, no remainder
+                    body.append(f"{mode} {names[a]}[{nthreads - 1} - tid + {r.randint(0, n - nthreads)}];")
+                elif kind < 0.9:            # another tid coefficient (mostly read)
+                    body.append(f"{r.choice(['rd', 'rd', mode])} {names[a]}[({r.choice([2, 3, -2, 0])} * tid + {vs[-1]}) % {n}];")
+                else:                       # a condition on a loop variable
+                    body.append(f"if ({vs[0]} < {r.randint(1, 4)}) {{ {mode} {names[a]}[(tid + 7 * {vs[0]}) % {n}]; }}")
+            if not body:
+                body.append("skip;")
+            text = "\n".join(body)
+            kws, synced = [], True        # forS only inside forS (Fig. 1)
+            for _ in vs:
+                kws.append("forS" if synced and r.random() < 0.3 else "forU")
+                synced = kws[-1] == "forS"
+            for v, t, kw in reversed(list(zip(vs, trips, kws))):
+                text = f"{kw} {v} in 0 .. {t} {{\n{text}\n}}"
+            lines.append(text)
+    return Protocol("\n".join(lines) + "\n", nthreads, cells, [], {"seed": seed})
 
 
 # --------------------------------------------------------------- config 2 --

@@ -382,3 +382,130 @@ def test_automatic_path_choice(oracle):
             assert same(run(c, p), want(oracle, p))
     finally:
         drf.drf_ctx_destroy(c)
+
+
+def test_lookback_wait_runs_out_and_context_recovers(oracle):
+    """The radix look-back's bounded wait, made to run out: with the test
+    hook, tile 0 of every radix pass publishes nothing and the tiles after
+    it give up after 64 waits.  The check returns DRF_E_TIMEOUT (nothing
+    faults: the waits end and every store stays in the key buffers), and
+    the next checks on the same context equal the oracle."""
+    c = drf.drf_ctx_create(0, flags=drf.OPT_PATH_SORT)
+    try:
+        p = protogen.config2(2, target=2e5)           # ~50 radix tiles per pass
+        bc = drf.drf_protocol_compile(p.text)
+        exp = want(oracle, p)
+        assert same(run(c, p), exp)
+        drf.drf_debug_stall_lookback(c, 1)
+        with pytest.raises(drf.DrfError) as e:
+            drf.drf_check(c, bc, p.nthreads, p.cells, p.params)
+        assert e.value.name == "TIMEOUT"
+        for _ in range(2):
+            assert same(run(c, p), exp)
+        q = protogen.config1("nosync")
+        assert same(run(c, q), want(oracle, q))
+    finally:
+        drf.drf_ctx_destroy(c)
+
+
+@pytest.mark.parametrize("nshards", [1, 2, 3, 5])
+def test_one_protocol_split_by_cells(oracle, nshards):
+    """drf_check_shard over every shard of a protocol, merged by
+    drf_merge_shards, equals the oracle on the whole protocol -- every
+    field, races in one shard or several, errors and divergence (facts of
+    the whole protocol that every shard reports alike)."""
+    c = drf.drf_ctx_create(0)
+    try:
+        ps = [protogen.shifted_small(s) for s in range(8)]
+        ps += protogen.config4(master_seed=13, count=10)
+        ps += [protogen.random_small(s) for s in range(60, 100)]
+        ps += [protogen.config1(v) for v in ("drf", "nosync")]
+        for p in ps:
+            exp = want(oracle, p)
+            if exp["status"] == "OVERFLOW":
+                continue
+            bc = drf.drf_protocol_compile(p.text)
+            parts = [drf.drf_check_shard(c, bc, p.nthreads, p.cells, p.params, k, nshards) for k in range(nshards)]
+            assert same(drf.result_dict(drf.drf_merge_shards(parts)), exp), p.text
+    finally:
+        drf.drf_ctx_destroy(c)
+
+
+def test_grid_scale_split_by_cells(grid_expected):
+    """The grid-scale protocol (65,536 threads, 2.2e8 accesses) in four
+    shards: each shard records only its quarter of the cells; the merged
+    result equals the oracle over the whole protocol."""
+    c = drf.drf_ctx_create(0)
+    try:
+        p = protogen.config3(0, racy=True)
+        bc = drf.drf_protocol_compile(p.text)
+        parts = [drf.drf_check_shard(c, bc, p.nthreads, p.cells, p.params, k, 4) for k in range(4)]
+        assert sum(drf.result_dict(x)["verdict"] == "RACY" for x in parts) == 1
+        assert drf.result_dict(drf.drf_merge_shards(parts)) == grid_expected(0, True)
+    finally:
+        drf.drf_ctx_destroy(c)
+
+
+@pytest.mark.parametrize("bits", [4, 5, 6, 7, 8])
+def test_radix_digit_width(oracle, bits):
+    """The sort path with every radix digit width the context may fix: the
+    pass count follows the width (widened when the key would need more than
+    eight passes) and every result equals the oracle."""
+    c = drf.drf_ctx_create(0, radix_bits=bits, flags=drf.OPT_PATH_SORT)
+    try:
+        ps = [protogen.config2(1, target=2e5), protogen.config2(3, "constructed", target=2e5, plant=True)]
+        ps += [protogen.random_small(s) for s in range(200, 230)]
+        for p in ps:
+            assert same(run(c, p), want(oracle, p)), p.text
+        batch = protogen.config4(master_seed=17, count=24)
+        plan = drf.drf_plan_create(c, [drf.drf_protocol_compile(p.text) for p in batch],
+                                   [(p.nthreads, p.cells, p.params) for p in batch])
+        try:
+            info, cfg = drf.drf_plan_info(plan), drf.drf_plan_config(plan)
+            width = max(bits, -(-info["sort_bits"] // 8))
+            assert cfg["radix_bits"] == width and info["sort_passes"] == -(-info["sort_bits"] // width)
+            drf.drf_plan_launch(plan)
+            for p, r in zip(batch, drf.drf_plan_results(plan)):
+                assert same(drf.result_dict(r), want(oracle, p))
+        finally:
+            drf.drf_plan_destroy(plan)
+    finally:
+        drf.drf_ctx_destroy(c)
+
+
+def test_autotuned_radix_width(oracle):
+    """The tuner picks the digit width of a sort-path plan among 6, 7 and 8
+    bits; the plan it keeps gives the oracle's results."""
+    c = drf.drf_ctx_create(0, flags=drf.OPT_AUTOTUNE | drf.OPT_PATH_SORT)
+    try:
+        ps = protogen.config4(master_seed=19, count=48)
+        plan = drf.drf_plan_create(c, [drf.drf_protocol_compile(p.text) for p in ps],
+                                   [(p.nthreads, p.cells, p.params) for p in ps])
+        try:
+            assert drf.drf_plan_config(plan)["radix_bits"] in (6, 7, 8)
+            drf.drf_plan_launch(plan)
+            for p, r in zip(ps, drf.drf_plan_results(plan)):
+                assert same(drf.result_dict(r), want(oracle, p))
+        finally:
+            drf.drf_plan_destroy(plan)
+    finally:
+        drf.drf_ctx_destroy(c)
+
+
+def test_server_splits_a_round_that_does_not_fit(oracle):
+    """Requests whose owner tables fit the context's device-memory cap one at
+    a time, but not two in one round: the server runs such a round again in
+    halves, so every request gets the result it gets alone."""
+    n = 1 << 23                                   # a 32 MiB table per request
+    texts = [f"array A;\nwr A[(tid + {k}) % {n}];\n" for k in range(5)] + ["array A;\nwr A[tid % 3];\n"]
+    c = drf.drf_ctx_create(0, flags=drf.OPT_PATH_TABLE, max_device_bytes=48 << 20)
+    try:
+        drf.drf_server_start(c)
+        tickets = [drf.drf_server_submit(c, drf.drf_protocol_compile(t), 1024, [n], []) for t in texts]
+        got = [drf.result_dict(drf.drf_server_poll(c, tk, timeout_us=60_000_000)[0]) for tk in tickets]
+        drf.drf_server_stop(c)
+    finally:
+        drf.drf_ctx_destroy(c)
+    for t, g in zip(texts, got):
+        assert same(g, oracle.check(t, 1024, [n], [], CELLS)), t
+    assert got[-1]["verdict"] == "RACY"

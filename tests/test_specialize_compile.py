@@ -56,3 +56,21 @@ def test_constants_are_baked_in():
                                              compile=False)
     assert st == "OK"
     assert "2048ull" in src      # the array's size bounds every index check
+
+
+@pytest.mark.parametrize("seed", range(0, 60, 6))
+def test_range_pass_source_compiles(seed):
+    """Protocols whose accesses are mostly +-tid plus loop terms get the
+    range pass (drf_range) beside the other kernels, and it compiles."""
+    p = protogen.shifted_small(seed)
+    st, src, log = drf.drf_protocol_specialize(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
+    assert st == "OK", log
+
+
+def test_grid_scale_protocol_gets_the_range_pass():
+    p = protogen.config3(0, racy=True)
+    st, src, log = drf.drf_protocol_specialize(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
+    assert st == "OK", log
+    assert 'extern "C" __global__ void __launch_bounds__(512) drf_range(' in src
+    # every owned write (tid + 65536 * g(x, y) + d) mod 2^24 is the range pass's
+    assert src.count("// access at pc") >= 15

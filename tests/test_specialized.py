@@ -47,7 +47,8 @@ def plan_result(ctx, p, launches=2):
 
 def check(ctx, oracle, p, need_spec=True):
     """Compares the plan's result with the oracle's; returns how the plan
-    ran (0 interpreted, 1 specialized, 2 specialized with static phases)."""
+    ran (0 interpreted, 1 specialized, 2 specialized with static phases, 3
+    the same with the range pass)."""
     exp = {k: v for k, v in want(oracle, p).items() if k != "message"}
     got, spec = plan_result(ctx, p)
     if exp["status"] != "OK":
@@ -129,12 +130,13 @@ def test_config2_full_size(sctx, oracle):
 @pytest.mark.parametrize("seed,racy", [(0, True), (0, False), (1, True), (1, False)])
 def test_config3_full_size(sctx, grid_expected, seed, racy):
     """Grid scale (65,536 threads, ~2.2x10^8 accesses) through specialized
-    kernels with static phases, launch after launch: every result field
-    against the oracle's method B over the whole protocol."""
+    kernels with static phases and the range pass, launch after launch:
+    every result field against the oracle's method B over the whole
+    protocol."""
     p = protogen.config3(seed, racy=racy)
     got, spec = plan_result(sctx, p, launches=3)
-    assert spec == 2
     assert got == grid_expected(seed, racy)
+    assert spec == 3
 
 
 def test_config3_benchmark_launch_configuration(grid_expected):
@@ -252,3 +254,27 @@ def test_witness_hits_solved_per_loop(sctx, oracle, chunk):
         wide += drf.drf_protocol_analyze(drf.drf_protocol_compile(text), T, cells, [])[1]["wide_arithmetic"]
         assert check(sctx, oracle, p) == 2
     assert wide >= 1
+
+
+@pytest.mark.parametrize("chunk", range(4))
+def test_range_pass_against_oracle(sctx, oracle, chunk):
+    """Accesses at +-tid plus a function of the loop variables (with and
+    without a remainder, arrays of odd sizes across several 16384-record
+    tasks, conditions on loop variables) go through the range pass, mixed
+    with accesses of other tid coefficients that the table pass applies and
+    the range pass merges: every result field equals the oracle's, launch
+    after launch."""
+    kinds = []
+    for seed in range(chunk * 20, (chunk + 1) * 20):
+        kinds.append(check(sctx, oracle, protogen.shifted_small(seed)))
+    assert kinds.count(3) >= 10, kinds
+
+
+def test_config3_runs_the_range_pass(sctx):
+    p = protogen.config3(0, racy=True)
+    plan = drf.drf_plan_create(sctx, [drf.drf_protocol_compile(p.text)], [(p.nthreads, p.cells, p.params)])
+    try:
+        assert drf.drf_plan_specialized(plan)[0] == 3
+        assert drf.drf_plan_info(plan)["kernels_per_launch"] == 4
+    finally:
+        drf.drf_plan_destroy(plan)

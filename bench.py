@@ -394,7 +394,7 @@ def run_ours(args, rank, world):
     assert drf.result_dict(drf.drf_plan_results(pplan)[0]) == res
     drf.drf_plan_destroy(pplan)
     drf.drf_ctx_destroy(pctx)
-    range_tuples = drf.drf_plan_range_tuples(plan) if specialized == 3 else None
+    range_tuples, range_updates = drf.drf_plan_range_tuples(plan) if specialized == 3 else (None, None)
     roof, stages = roofline(kinds, prof_steps, n, {**info, "specialized": specialized, "range_tuples": range_tuples},
                             dev, clocks)
 
@@ -461,7 +461,7 @@ def run_ours(args, rank, world):
             "config": {"workload": WORKLOAD if not args.threads else
                        f"{WORKLOAD}; restricted to its first {p.nthreads} threads",
                        "tuples_per_step": n, "path": path, "specialized": specialized,
-                       "range_pass_tuples_per_step": range_tuples,
+                       "range_pass_tuples_per_step": range_tuples, "range_pass_record_updates_per_step": range_updates,
                        "path_choice": args.path,
                        "plan": {**drf.drf_plan_config(plan), "create_s": round(plan_s, 3)},
                        "sort_passes": info["sort_passes"], "sort_bits": info["sort_bits"],

@@ -458,11 +458,13 @@ int drf_plan_specialized(const drf_plan *plan, uint32_t *specialized, char *log,
  * (the owner table once per granularity) when the owner table fits. */
 int drf_plan_path(const drf_plan *plan, uint32_t *path);
 
-/* Access tuples the last launch applied in its range pass (drf_plan_specialized
- * reports 3; 0 otherwise): the accesses at +-tid plus a function of the loop
- * variables, applied task by task in shared memory; the owner-table pass
- * applied the others.  Waits for the launch. */
-int drf_plan_range_tuples(drf_plan *plan, uint64_t *tuples);
+/* The range pass of a plan (drf_plan_specialized reports 3; zeros
+ * otherwise): *tuples, the access tuples its accesses make in one launch
+ * (every thread, every iteration; the owner-table pass applies the other
+ * tuples); *updates (may be NULL), the record updates its last launch made
+ * -- fewer, since the iterations of an access that share an offset apply
+ * the same accesses and are applied once (waits for the launch). */
+int drf_plan_range_tuples(const drf_plan *plan, uint64_t *tuples, uint64_t *updates);
 
 /* Releases the plan's device memory and graph. */
 void drf_plan_destroy(drf_plan *plan);

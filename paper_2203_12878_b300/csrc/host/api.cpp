@@ -578,7 +578,7 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
         std::vector<char> cubin;
         auto mod = std::make_unique<JitModule>();
         bool stat = false, csched = false, range = false;
-        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes, &stat, &csched, &range)
+        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes, &stat, &csched, &range, &plan->range_tuples)
                    : Error::make(S_INVALID_ARG, "specialization takes a plan of one protocol");
         d.jit.static_phases = stat;
         d.jit.csched = csched;
@@ -917,16 +917,23 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
     return DRF_OK;
 }
 
-int drf_plan_range_tuples(drf_plan *plan, uint64_t *tuples)
+int drf_plan_range_tuples(const drf_plan *plan, uint64_t *tuples, uint64_t *updates)
 {
     if (!plan || !tuples) return DRF_E_INVALID_ARG;
-    drf_ctx *ctx = plan->ctx;
-    cudaSetDevice(ctx->device);
-    cudaStream_t s = plan->last_stream ? plan->last_stream : ctx->stream;
-    cudaError_t e;
-    if ((e = plan->dev.fetch(s, true)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
-        return cuda_fail(ctx, e);
-    *tuples = plan->dev.host_ctrl()->range_tuples;
+    *tuples = plan->dev.jit.range ? plan->range_tuples : 0;
+    if (updates) {
+        *updates = 0;
+        if (plan->dev.jit.range) {
+            drf_ctx *ctx = plan->ctx;
+            cudaSetDevice(ctx->device);
+            cudaStream_t s = plan->last_stream ? plan->last_stream : ctx->stream;
+            DeviceBatch &d = const_cast<drf_plan *>(plan)->dev;
+            cudaError_t e;
+            if ((e = d.fetch(s, true)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
+                return cuda_fail(ctx, e);
+            *updates = d.host_ctrl()->range_tuples;
+        }
+    }
     return DRF_OK;
 }
 

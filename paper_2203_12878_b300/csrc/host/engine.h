@@ -188,6 +188,7 @@ struct drf_plan {
     drf::PlanConfig cfg;
     std::unique_ptr<drf::JitModule> jit;   // specialized kernels, when the plan uses them
     std::string jit_log;                   // why specialization was not used, when asked for
+    uint64_t range_tuples = 0;             // access tuples of the range pass's accesses (jit_source)
 };
 
 namespace drf {

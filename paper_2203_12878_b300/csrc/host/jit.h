@@ -39,9 +39,13 @@ struct BatchHost;
 // consecutive owner records, in shared memory -- the table pass only counts
 // them -- and the range pass takes the place of the touch listing and table
 // scan: it merges and clears the table pass's records and finds the first
-// racy cell.
+// racy cell.  The accesses' distinct offsets are found here, by evaluating
+// their loops, and compiled in as per-task lists.
+// *range_pass_tuples: the access tuples the range accesses make (all threads,
+// every iteration; duplicates of an offset are applied once).
 Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::vector<uint16_t> &item_shape,
-                 bool *static_phases = nullptr, bool *compiled_schedule = nullptr, bool *range_pass = nullptr);
+                 bool *static_phases = nullptr, bool *compiled_schedule = nullptr, bool *range_pass = nullptr,
+                 uint64_t *range_pass_tuples = nullptr);
 
 // Compiles `src` for sm_103a with NVRTC.  On failure, `log` holds the
 // compiler's log (or why NVRTC is unavailable).

@@ -13,6 +13,7 @@
 // width), accesses and interpreter steps per thread.
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <stdexcept>
 
 #include "prepare.h"
@@ -859,6 +860,164 @@ struct RangeFinder {
 
 }  // namespace
 
+// Evaluates expression code (devprog.h's stack machine) on the host, with
+// tid and the loop variables `vars`, on mathematical integers: false on a
+// division or remainder by zero, a value outside int64 or malformed code.
+bool host_eval(const std::vector<uint64_t> &xc, int32_t off, int64_t tid, const int64_t *vars, int64_t &out)
+{
+    using i128 = __int128;
+    i128 st[kMaxStack + 2];
+    int d = 0;
+    auto fits = [](i128 v) { return v >= (i128)INT64_MIN && v <= (i128)INT64_MAX; };
+    auto fdiv = [](i128 a, i128 b) { i128 q = a / b; if ((a % b != 0) && ((a < 0) != (b < 0))) q -= 1; return q; };
+    auto emod = [](i128 a, i128 b) { i128 r = a % b; if (r < 0) r += b < 0 ? -b : b; return r; };
+    size_t i = (size_t)off;
+    for (int guard = 0; guard < 1 << 16; guard++) {
+        if (i >= xc.size()) return false;
+        const uint64_t w = xc[i++];
+        const uint32_t op = (uint32_t)(w & 0xff);
+        if (op != X_RET && d >= kMaxStack + 1) return false;
+        switch (op) {
+        case X_RET:
+            if (d != 1 || !fits(st[0])) return false;
+            out = (int64_t)st[0];
+            return true;
+        case X_CONST: if (i >= xc.size()) return false; st[d++] = (int64_t)xc[i++]; break;
+        case X_TID: st[d++] = tid; break;
+        case X_VAR: if ((w >> 8) >= (uint64_t)kMaxVars) return false; st[d++] = vars[w >> 8]; break;
+        case X_AFF: {
+            const uint32_t n = (uint32_t)(w >> 8);
+            i128 acc = 0;
+            for (uint32_t t = 0; t < n; t++) {
+                if (i + 1 >= xc.size()) return false;
+                const uint32_t reg = (uint32_t)xc[i++];
+                const int64_t coef = (int64_t)xc[i++];
+                if (reg != kAffTid && reg >= (uint32_t)kMaxVars) return false;
+                acc += (i128)coef * (reg == kAffTid ? tid : vars[reg]);
+                if (!fits(acc)) return false;
+            }
+            if (i >= xc.size()) return false;
+            acc += (int64_t)xc[i++];
+            st[d++] = acc;
+            break;
+        }
+        case X_NEG: if (d < 1) return false; st[d - 1] = -st[d - 1]; break;
+        case X_NOT: if (d < 1) return false; st[d - 1] = st[d - 1] == 0; break;
+        case X_DIVC: case X_MODC: case X_MASK: {
+            if (d < 1 || i >= xc.size()) return false;
+            const int64_t c = (int64_t)xc[i++];
+            if (op == X_MASK) st[d - 1] = (i128)(int64_t)((uint64_t)(int64_t)st[d - 1] & (uint64_t)c);
+            else if (c == 0) return false;
+            else st[d - 1] = op == X_DIVC ? fdiv(st[d - 1], c) : emod(st[d - 1], c);
+            break;
+        }
+        default: {
+            if (d < 2) return false;
+            const i128 a = st[d - 2], b = st[d - 1];
+            i128 r = 0;
+            switch (op) {
+            case X_ADD: r = a + b; break;
+            case X_SUB: r = a - b; break;
+            case X_MUL: if (!fits(a) || !fits(b)) return false; r = a * b; break;
+            case X_MIN: r = b < a ? b : a; break;
+            case X_MAX: r = b > a ? b : a; break;
+            case X_DIV: if (b == 0) return false; r = fdiv(a, b); break;
+            case X_MOD: if (b == 0) return false; r = emod(a, b); break;
+            case X_EQ: r = a == b; break;
+            case X_NE: r = a != b; break;
+            case X_LT: r = a < b; break;
+            case X_LE: r = a <= b; break;
+            case X_GT: r = a > b; break;
+            case X_GE: r = a >= b; break;
+            case X_AND: r = (a != 0) & (b != 0); break;
+            case X_OR: r = (a != 0) | (b != 0); break;
+            default: return false;
+            }
+            if (!fits(r)) return false;
+            d--;
+            st[d - 1] = r;
+        }
+        }
+    }
+    return false;
+}
+
+// The distinct offsets c of a range access over its loops' iterations (the
+// conditions applied), and how many iterations it runs; false when an
+// evaluation fails or more than `cap` iterations would be visited.
+bool range_offsets(const std::vector<uint64_t> &xcode, const RangeAccess &r, uint64_t cap, std::vector<int64_t> &cs,
+                   uint64_t &iters)
+{
+    int64_t vars[kMaxVars] = {};
+    uint64_t visited = 0;
+    iters = 0;
+    cs.clear();
+    bool ok = true;
+    std::function<void(size_t)> rec = [&](size_t l) {
+        if (!ok) return;
+        if (l == r.loops.size()) {
+            for (const auto &g : r.guards) {
+                int64_t c = 0;
+                if (!host_eval(xcode, g.first, 0, vars, c)) { ok = false; return; }
+                if ((c != 0) != g.second) return;
+            }
+            int64_t c = 0;
+            if (!host_eval(xcode, r.cexpr, 0, vars, c)) { ok = false; return; }
+            if (r.modn) {
+                c %= (int64_t)r.modn;
+                if (c < 0) c += (int64_t)r.modn;
+            }
+            cs.push_back(c);
+            iters++;
+            return;
+        }
+        const RangeLoop &L = r.loops[l];
+        int64_t lo = 0, hi = 0;
+        if (L.reg >= (uint32_t)kMaxVars || !host_eval(xcode, L.lo, 0, vars, lo) || !host_eval(xcode, L.hi, 0, vars, hi)) {
+            ok = false;
+            return;
+        }
+        for (int64_t x = lo; x < hi && ok; x++) {
+            if (++visited > cap) { ok = false; return; }
+            vars[L.reg] = x;
+            rec(l + 1);
+        }
+    };
+    rec(0);
+    if (!ok) return false;
+    std::sort(cs.begin(), cs.end());
+    cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+    return true;
+}
+
+// Index intervals [lo, hi) of the cells access `r` (array of ncells) reaches
+// over threads [0, T) at offset c (already reduced when the index has a
+// remainder).
+void range_image(const RangeAccess &r, int64_t c, uint64_t ncells, uint32_t T, std::vector<std::pair<int64_t, int64_t>> &out)
+{
+    out.clear();
+    const int64_t t = (int64_t)T, n = (int64_t)ncells;
+    auto add = [&](int64_t lo, int64_t hi) {
+        lo = std::max<int64_t>(lo, 0);
+        hi = std::min<int64_t>(hi, n);
+        if (lo < hi) out.emplace_back(lo, hi);
+    };
+    if (!r.modn) {
+        if (r.sigma == 1) add(c, c + t);
+        else add(c - t + 1, c + 1);
+        return;
+    }
+    const int64_t N = (int64_t)r.modn;
+    if (r.sigma == 1) {
+        add(c, std::min(c + t, N));
+        if (c + t > N) add(0, c + t - N);
+    } else {
+        add(c - std::min(t - 1, c), c + 1);
+        if (t - 1 > c) add(N - (t - 1 - c), N);
+    }
+}
+
+
 Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, const uint64_t *cells,
               uint32_t nparams, const int64_t *params, const PrepareOpts &opts, Prepared &out)
 {
@@ -964,8 +1123,18 @@ Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, 
     if (out.static_phases && nthreads > 0) {
         RangeFinder rf{an, lw, nthreads};
         rf.walk(*p.body, 0, true);
-        out.range_access = std::move(rf.out);
         if (lw.xcode.size() > (1u << 26)) return Error::make(S_LIMIT, "protocol too large");
+        // the distinct offsets of each, by evaluating its loops (at most
+        // kRangeIterCap iterations over all of them; the rest are left to
+        // the table pass)
+        uint64_t budget = kRangeIterCap;
+        for (RangeAccess &r : rf.out) {
+            uint64_t iters = 0;
+            if (!range_offsets(lw.xcode, r, budget, r.offsets, iters) || iters == 0) continue;
+            budget -= std::min<uint64_t>(budget, iters);
+            r.run_iters = iters;
+            out.range_access.push_back(std::move(r));
+        }
     }
 
     out.insns = std::move(lw.insns);

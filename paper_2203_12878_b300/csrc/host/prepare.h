@@ -43,7 +43,29 @@ struct RangeAccess {
     std::vector<RangeLoop> loops; // enclosing loops, outermost first
     std::vector<std::pair<int32_t, bool>> guards;   // enclosing conditions' code and the branch taken
     uint64_t iters;               // product of the loops' trip bounds (saturated)
+    // found by evaluating the loops at preparation: the distinct offsets c
+    // (reduced mod modn when there is a remainder) and the iterations run
+    std::vector<int64_t> offsets;
+    uint64_t run_iters = 0;
 };
+
+// Loop iterations preparation evaluates to find range accesses' offsets,
+// over all of one protocol's range accesses.
+constexpr uint64_t kRangeIterCap = 1ull << 22;
+
+// Expression code (devprog.h's stack machine) evaluated on the host over
+// mathematical integers; false on a division by zero, a value outside int64
+// or malformed code.
+bool host_eval(const std::vector<uint64_t> &xc, int32_t off, int64_t tid, const int64_t *vars, int64_t &out);
+// The distinct offsets of a range access over its loops' iterations (its
+// conditions applied) and the iterations it runs; false when an evaluation
+// fails or more than `cap` iterations would be visited.
+bool range_offsets(const std::vector<uint64_t> &xcode, const RangeAccess &r, uint64_t cap, std::vector<int64_t> &cs,
+                   uint64_t &iters);
+// Index intervals [lo, hi) of the cells a range access (array of ncells)
+// reaches over threads [0, T) at offset c.
+void range_image(const RangeAccess &r, int64_t c, uint64_t ncells, uint32_t T,
+                 std::vector<std::pair<int64_t, int64_t>> &out);
 
 struct Prepared {
     uint32_t nthreads = 0;

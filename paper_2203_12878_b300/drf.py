@@ -126,7 +126,7 @@ _SIGS = {
     "drf_protocol_specialize": (ctypes.c_int, [_U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds),
                                                ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p,
                                                ctypes.c_size_t]),
-    "drf_plan_range_tuples": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "drf_plan_range_tuples": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "drf_plan_destroy": (None, [_P]),
     "drf_server_start": (ctypes.c_int, [_P, ctypes.POINTER(drf_server_opts)]),
     "drf_server_submit": (ctypes.c_int, [_P, _U8P, ctypes.c_size_t, ctypes.POINTER(drf_bounds),
@@ -468,13 +468,14 @@ def drf_plan_config(plan) -> dict:
     return {"granularity": g.value, "radix_items": it.value, "radix_bits": rb.value}
 
 
-def drf_plan_range_tuples(plan) -> int:
-    """Access tuples the plan's last launch applied in its range pass."""
-    n = ctypes.c_uint64()
-    st = lib().drf_plan_range_tuples(plan, ctypes.byref(n))
+def drf_plan_range_tuples(plan):
+    """(access tuples of the range pass's accesses per launch, record updates
+    its last launch made)."""
+    n, u = ctypes.c_uint64(), ctypes.c_uint64()
+    st = lib().drf_plan_range_tuples(plan, ctypes.byref(n), ctypes.byref(u))
     if st != 0:
         raise DrfError(st)
-    return n.value
+    return n.value, u.value
 
 
 def drf_plan_specialized(plan):

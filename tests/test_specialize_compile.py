@@ -73,4 +73,5 @@ def test_grid_scale_protocol_gets_the_range_pass():
     assert st == "OK", log
     assert 'extern "C" __global__ void __launch_bounds__(512) drf_range(' in src
     # every owned write (tid + 65536 * g(x, y) + d) mod 2^24 is the range pass's
-    assert src.count("// access at pc") >= 15
+    import re
+    assert int(re.search(r"const RAcc r_acc\[(\d+)\]", src).group(1)) >= 15

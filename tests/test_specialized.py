@@ -252,7 +252,7 @@ def test_witness_hits_solved_per_loop(sctx, oracle, chunk):
         text, T, cells = affine_case(seed)
         p = protogen.Protocol(text, T, cells, [])
         wide += drf.drf_protocol_analyze(drf.drf_protocol_compile(text), T, cells, [])[1]["wide_arithmetic"]
-        assert check(sctx, oracle, p) == 2
+        assert check(sctx, oracle, p) in (2, 3)
     assert wide >= 1
 
 

@@ -171,6 +171,12 @@ typedef struct {
  * give the owner table, and forced sort-path contexts, keep the
  * interpreter. */
 #define DRF_OPT_SPECIALIZE     0x10u
+/* The owner table's range pass (drf_plan_specialized) for batches of any
+ * size.  By default a batch takes it only when its range accesses make 2^22
+ * access tuples or more: below that, planning its work lists, uploading them
+ * and the extra kernel cost more than the table pass they relieve.  Results
+ * are the same either way. */
+#define DRF_OPT_RANGE_ANY      0x20u
 
 #define DRF_PATH_SORT  1
 #define DRF_PATH_TABLE 2
@@ -246,6 +252,13 @@ typedef struct {
     uint32_t wide_arithmetic;
     uint32_t sort_bits;
     uint32_t key_bits;
+    /* access tuples the owner table's range pass takes when the protocol is
+     * checked alone on the owner-table path: its accesses at +-tid plus a
+     * function of the loop variables, applied cell range by cell range in
+     * shared memory (0 when it has none or they make under a quarter of its
+     * tuples); counted at any size (see DRF_OPT_RANGE_ANY for when checks
+     * take the pass) */
+    uint64_t range_tuples;
 } drf_analysis;
 
 int drf_protocol_analyze(const uint8_t *bytecode, size_t len, const drf_bounds *bounds, drf_analysis *out);

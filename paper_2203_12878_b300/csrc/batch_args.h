@@ -29,6 +29,24 @@ enum : uint32_t {
     TR_SINGLE = 4,        // the tile lies inside one segment that crosses both edges
 };
 
+// One range access of a batch (the range pass): the first owner record of
+// its (phase, array) segment, its array's size, the remainder's modulus (0:
+// none), the sign of tid in its index, whether it writes, and its
+// protocol's thread count.
+struct RAcc {
+    unsigned long long sb, ncells, modn;
+    int sigma;
+    unsigned int w, T, pad;
+};
+
+// Owner records per task of the range pass: a multiple of the 8,192 records
+// one touch word covers, so that every task owns its touch words.
+constexpr uint32_t kRangeRecs = 16384;
+constexpr uint32_t kRangeThreads = 512;
+constexpr uint32_t kRangeChunk = 256;                       // entries turned into intervals per round
+constexpr uint32_t kRangeSmem = kRangeRecs * 4;             // dynamic shared memory of a range block
+constexpr uint32_t kRangeBlocksPerSm = 3;
+
 // Everything the kernels of one launch touch.  Device pointers unless noted.
 struct BatchArgs {
     // device programs of the batch
@@ -82,10 +100,21 @@ struct BatchArgs {
     // `iphase`, the table pass counts the tuples and writes thread 0's sync
     // total, and nothing checks barrier divergence (none is possible).
     uint32_t count_free;
-    // Shard of a one-protocol check (drf_check_shard): the table pass
-    // updates only the records at positions [shard_lo, shard_hi); [0, ~0)
-    // otherwise.
+    // Shard of a one-protocol check (drf_check_shard): the table and range
+    // passes update only the records at positions [shard_lo, shard_hi);
+    // [0, ~0) otherwise.
     unsigned long long shard_lo, shard_hi;
+    // The range pass (owner-table launches): tasks of kRangeRecs records
+    // that range accesses reach (rlive, ascending), each with its entries
+    // [rfirst[i], rfirst[i + 1]) of (access rk, offset rc); the table pass
+    // leaves accesses marked AF_RANGE alone when range_on is set.
+    const RAcc *racc;
+    const uint32_t *rk;
+    const long long *rc;
+    const uint32_t *rlive;
+    const uint32_t *rfirst;
+    uint32_t nlive;
+    uint32_t range_on;
     void *table;                     // [tab_cells] 32-bit owner records, padded to whole blocks
     uint64_t tab_cells;
     uint32_t *touch;                 // one bit per block of kTabBlock records written this launch

@@ -315,7 +315,9 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             // the witness pass runs only protocols none of whose accesses
             // fails, and needs the index only of accesses in the cell's phase
             // and array
-            const bool need = CELL ? (phase == tg.phase && in.b == tg.loc) : (PHASED || (in.a & AF_EVAL_IN_COUNT));
+            // (nor does the table pass the index of an access the range pass applies)
+            const bool need = CELL ? (phase == tg.phase && in.b == tg.loc)
+                                   : TAB ? !(a.range_on && (in.a & AF_RANGE)) : (PHASED || (in.a & AF_EVAL_IN_COUNT));
             if (ex && need) {
                 if (!eval<V>(xc, in.c, tid, vars, idx)) { err = kErrDiv0; ok = false; }
                 else if (idx < 0 || (uint64_t)(U)idx >= __ldg(cells + in.b)) { err = kErrOob; ok = false; }
@@ -336,7 +338,9 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                 if (ok && !put) atomicOr(&a.ctrl->flags, CF_TABLE_RANGE);
                 const unsigned long long off =
                     put ? P.tab_off + (uint64_t)phase * P.cells_sum + __ldg(cb + in.b) + (uint64_t)(U)idx : 0ull;
-                table_put(a, put && off >= a.shard_lo && off < a.shard_hi, off, tid, in.a & AF_WRITE);
+                // an access the range pass applies is only counted here
+                const bool mine = !(a.range_on && (in.a & AF_RANGE));
+                table_put(a, mine && put && off >= a.shard_lo && off < a.shard_hi, off, tid, in.a & AF_WRITE);
             } else if (CELL) {
                 if (ok && phase == tg.phase && in.b == tg.loc && (unsigned long long)(U)idx == tg.idx)
                     hit |= 1u | ((in.a & AF_WRITE) << 1);
@@ -395,8 +399,14 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             }
             const uint64_t trip = (okb && lo < hi) ? (uint64_t)(U)((U)hi - (U)lo) : 0;
             const uint32_t m = (uint32_t)in.e;
+            // the table pass takes a loop whose accesses the range pass all
+            // applies in one step: it only counts them
+            bool skip = TAB && a.range_on;
+            for (uint32_t j = 0; j < m && skip; j++) skip = (load_insn(prog + mpc + 1 + j).a & AF_RANGE) != 0;
             if (!PHASED) {
                 if (okb) { count += (uint32_t)(trip * m); syncs += (uint32_t)(trip * in.b); }
+            } else if (skip) {
+                if (okb) { count += (uint32_t)(trip * m); phase += (uint32_t)(trip * in.b); }
             } else {
                 V rest[kFastMax];
                 U coef[kFastMax], pcon[kFastMax];
@@ -449,7 +459,9 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                                 const unsigned long long off =
                                     put ? P.tab_off + (uint64_t)ph * P.cells_sum + __ldg(cb + loc) + (uint64_t)(U)idx
                                         : 0ull;
-                                table_put(a, put && off >= a.shard_lo && off < a.shard_hi, off, tid, mt & AF_WRITE);
+                                const bool mine = !(a.range_on && (mt & AF_RANGE));
+                                table_put(a, mine && put && off >= a.shard_lo && off < a.shard_hi, off, tid,
+                                          mt & AF_WRITE);
                             } else if (CELL) {
                                 if (act && ph == tg.phase && loc == tg.loc && (unsigned long long)(U)idx == tg.idx)
                                     hit |= 1u | ((mt & AF_WRITE) << 1);
@@ -1139,6 +1151,238 @@ __global__ void __launch_bounds__(kTabScanThreads) k_tscan(BatchArgs a)
     }
 }
 
+// ------------------------------------------------------------- range pass
+// Accesses whose index is (sigma * tid + c) mod m or sigma * tid + c
+// (sigma = +-1, c a function of the loop variables), in loops and
+// conditions that do not read tid and hold no sync: at one offset c, the
+// threads whose index falls into a range of cells are one interval of tids
+// (two when the remainder wraps).  The host lists, per task of kRangeRecs
+// consecutive owner records, the (access, offset) pairs that reach it; one
+// block per listed task holds the task's records in shared memory, merges
+// the table pass's records there, applies the intervals, and finds the
+// task's first racy record per protocol.  The table scan that follows reads
+// the table pass's records elsewhere.
+
+// tids [t0, t0 + len) of one offset of one access, the record (in the
+// task's shared copy) tid t0 updates -- the others follow at +1, or -1 with
+// bit 31 of lenf set -- and whether they write (bit 30 of lenf)
+struct REnt {
+    uint32_t t0, lenf;
+    int32_t l0;
+};
+constexpr uint32_t kRDown = 1u << 31, kRWrite = 1u << 30, kRLen = (1u << 30) - 1;
+
+struct RangeShared {
+    REnt ent[2 * kRangeChunk];
+    uint32_t pre[2 * kRangeChunk];
+    uint32_t n, tot, plain, bits[kRangeRecs / 8192];
+    unsigned long long best;
+    unsigned long long updates;                   // record updates the block made
+};
+
+// The one or two tid intervals of access A at offset c (reduced mod the
+// modulus when there is one) whose records lie in [w0, w1), within the task
+// starting at record r0.
+__device__ __forceinline__ void range_pieces(const RAcc &A, long long c, unsigned long long r0, unsigned long long w0,
+                                             unsigned long long w1, RangeShared &sh)
+{
+    const unsigned long long sb = A.sb, se = A.sb + A.ncells;
+    if (!(sb < w1 && se > w0)) return;
+    const long long T = (long long)A.T;
+    const long long lo_c = (long long)((w0 > sb ? w0 : sb) - sb);
+    const long long hi_c = (long long)((w1 < se ? w1 : se) - sb);
+    const long long loc0 = (long long)sb - (long long)r0;
+    long long ta = 0, na = 0, la = 0, tb = 0, nb = 0, lb = 0, te;
+    if (A.modn == 0 && A.sigma == 1) {
+        ta = lo_c - c; if (ta < 0) ta = 0; te = hi_c - c; if (te > T) te = T;
+        na = te - ta; la = ta + c + loc0;
+    } else if (A.modn == 0) {
+        ta = c - hi_c + 1; if (ta < 0) ta = 0; te = c - lo_c + 1; if (te > T) te = T;
+        na = te - ta; la = c - ta + loc0;
+    } else {
+        const long long N = (long long)A.modn, cm = c;
+        if (A.sigma == 1) {                         // tids below N - cm do not wrap around N
+            ta = lo_c - cm; if (ta < 0) ta = 0; te = hi_c - cm;
+            { const long long lim = N - cm < T ? N - cm : T; if (te > lim) te = lim; }
+            na = te - ta; la = ta + cm + loc0;
+            tb = lo_c - cm + N; if (tb < N - cm) tb = N - cm;
+            te = hi_c - cm + N; if (te > T) te = T;
+            nb = te - tb; lb = tb + cm - N + loc0;
+        } else {                                    // tids up to cm do not wrap below 0
+            ta = cm - hi_c + 1; if (ta < 0) ta = 0; te = cm - lo_c + 1;
+            { const long long lim = cm + 1 < T ? cm + 1 : T; if (te > lim) te = lim; }
+            na = te - ta; la = cm - ta + loc0;
+            tb = cm + N - hi_c + 1; if (tb < cm + 1) tb = cm + 1;
+            te = cm + N - lo_c + 1; if (te > T) te = T;
+            nb = te - tb; lb = cm + N - tb + loc0;
+        }
+    }
+    const uint32_t f = (A.sigma < 0 ? kRDown : 0u) | (A.w ? kRWrite : 0u);
+    if (na > 0) { const uint32_t e = atomicAdd(&sh.n, 1u); sh.ent[e] = REnt{(uint32_t)ta, (uint32_t)na | f, (int32_t)la}; }
+    if (nb > 0) { const uint32_t e = atomicAdd(&sh.n, 1u); sh.ent[e] = REnt{(uint32_t)tb, (uint32_t)nb | f, (int32_t)lb}; }
+}
+
+__device__ __forceinline__ void range_span(const REnt &x, int32_t &lo, int32_t &hi)
+{
+    const int32_t len = (int32_t)(x.lenf & kRLen);
+    if (x.lenf & kRDown) { lo = x.l0 - len + 1; hi = x.l0 + 1; }
+    else { lo = x.l0; hi = x.l0 + len; }
+}
+
+// Applies the round's intervals (sh.ent[0 .. sh.n)) to the task's records:
+// every (interval, offset) pair spread over the block.  Within one interval
+// every record has one tid; when no two intervals share a record (checked
+// for rounds of up to 64), no two threads update one record and each update
+// is a plain read and write of the record (owner.cuh's rule), four records
+// read before any is written; otherwise the updates are atomic.  Leaves
+// sh.n at 0.
+__device__ void range_apply(uint32_t *rec, RangeShared &sh)
+{
+    const uint32_t n = sh.n;
+    if (threadIdx.x < 32) {
+        bool clash = n > 64;
+        for (uint32_t e = threadIdx.x; e < n && !clash; e += 32) {
+            int32_t a0, a1;
+            range_span(sh.ent[e], a0, a1);
+            for (uint32_t f = e + 1; f < n; f++) {
+                int32_t b0, b1;
+                range_span(sh.ent[f], b0, b1);
+                if (a0 < b1 && b0 < a1) { clash = true; break; }
+            }
+        }
+        clash = __any_sync(kFull, clash);
+        // exclusive prefix of the lengths
+        uint32_t carry = 0;
+        for (uint32_t b = 0; b < n; b += 32) {
+            const uint32_t e = b + threadIdx.x;
+            const uint32_t v = e < n ? (sh.ent[e].lenf & kRLen) : 0u;
+            uint32_t inc = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, inc, o);
+                if ((int)threadIdx.x >= o) inc += y;
+            }
+            if (e < n) sh.pre[e] = carry + inc - v;
+            carry += __shfl_sync(kFull, inc, 31);
+        }
+        if (threadIdx.x == 0) { sh.tot = carry; sh.plain = clash ? 0u : 1u; sh.updates += carry; }
+    }
+    __syncthreads();
+    const uint32_t total = sh.tot;
+    const bool plain = sh.plain != 0;
+    uint32_t e = 0;
+    for (uint32_t q0 = threadIdx.x; q0 < total; q0 += 4u * kRangeThreads) {
+        uint32_t *rp[4];
+        uint32_t tq[4], wq[4], old[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t q = q0 + (uint32_t)k * kRangeThreads;
+            rp[k] = nullptr;
+            if (q < total) {
+                while (e + 1 < n && sh.pre[e + 1] <= q) e++;
+                const REnt x = sh.ent[e];
+                const uint32_t o = q - sh.pre[e];
+                tq[k] = x.t0 + o;
+                wq[k] = (x.lenf & kRWrite) ? 1u : 0u;
+                rp[k] = rec + (x.l0 + ((x.lenf & kRDown) ? -(int32_t)o : (int32_t)o));
+            }
+        }
+        if (plain) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) old[k] = rp[k] ? *rp[k] : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (!rp[k]) continue;
+                if (old[k] == 0u) *rp[k] = (tq[k] + 1u) | (wq[k] << 31);
+                else if (const uint32_t need = owner_need(old[k], tq[k], wq[k])) *rp[k] = old[k] | need;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) old[k] = rp[k] ? atomicCAS(rp[k], 0u, (tq[k] + 1u) | (wq[k] << 31)) : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (!rp[k] || old[k] == 0u) continue;
+                if (const uint32_t need = owner_need(old[k], tq[k], wq[k])) atomicOr(rp[k], need);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sh.n = 0;
+}
+
+__global__ void __launch_bounds__(kRangeThreads) k_range(BatchArgs a)
+{
+    pdl_begin();
+    extern __shared__ uint4 r_dyn[];
+    uint32_t *const rec = reinterpret_cast<uint32_t *>(r_dyn);
+    __shared__ RangeShared sh;
+    if (threadIdx.x == 0) { sh.n = 0; sh.updates = 0; }
+    uint32_t *const tab = reinterpret_cast<uint32_t *>(a.table);
+    for (uint32_t li = blockIdx.x; li < a.nlive; li += gridDim.x) {
+        const unsigned long long r0 = (unsigned long long)__ldg(a.rlive + li) * kRangeRecs;
+        const unsigned long long r1 = r0 + kRangeRecs < a.tab_cells ? r0 + kRangeRecs : a.tab_cells;
+        // the window this launch may record (a shard), within the task
+        const unsigned long long w0 = r0 > a.shard_lo ? r0 : a.shard_lo;
+        const unsigned long long w1 = r1 < a.shard_hi ? r1 : a.shard_hi;
+        const uint32_t nrec = (uint32_t)(r1 - r0);
+        __syncthreads();                                  // the previous task is done with rec and sh
+        uint4 *r4 = reinterpret_cast<uint4 *>(rec);
+        for (uint32_t i = threadIdx.x; i < kRangeRecs / 4; i += kRangeThreads) r4[i] = make_uint4(0u, 0u, 0u, 0u);
+        // the blocks the table pass touched in the task: merged into the
+        // shared copy and cleared in the table (through L2: this SM's L1 may
+        // hold lines the table pass read), their touch words cleared
+        const uint32_t nwords = (nrec + 8191u) >> 13;
+        uint32_t tb = 0;
+        if (threadIdx.x < nwords) {
+            tb = __ldcg(a.touch + (r0 >> 13) + threadIdx.x);
+            sh.bits[threadIdx.x] = tb;
+            if (tb) a.touch[(r0 >> 13) + threadIdx.x] = 0u;
+        }
+        if (__syncthreads_or(tb != 0u)) {
+            for (uint32_t i = threadIdx.x; i < nrec; i += kRangeThreads) {
+                const uint32_t blk = i >> 8;
+                if ((sh.bits[blk >> 5] >> (blk & 31u)) & 1u) {
+                    const uint32_t v = __ldcg(tab + r0 + i);
+                    if (v) { rec[i] = v; tab[r0 + i] = 0u; }
+                }
+            }
+            __syncthreads();
+        }
+        const uint32_t e1 = __ldg(a.rfirst + li + 1);
+        for (uint32_t e0 = __ldg(a.rfirst + li); e0 < e1 && w0 < w1; e0 += kRangeChunk) {
+            const uint32_t e = e0 + threadIdx.x;
+            if (threadIdx.x < kRangeChunk && e < e1) {
+                const RAcc A = a.racc[__ldg(a.rk + e)];
+                range_pieces(A, __ldg(a.rc + e), r0, w0, w1, sh);
+            }
+            __syncthreads();
+            range_apply(rec, sh);
+        }
+        // the first racy record of each protocol whose rows meet the task
+        // (rows are phase-major, then array, then index: the lexicographic
+        // order of the witness)
+        uint32_t p = proto_of_record(a, r0);
+        while (true) {
+            const DevProto P = a.protos[p];
+            const unsigned long long pe = P.tab_off + (unsigned long long)P.tab_phases * P.cells_sum;
+            const unsigned long long s0 = P.tab_off > r0 ? P.tab_off : r0, s1 = pe < r1 ? pe : r1;
+            if (s0 < s1) {
+                uint32_t best = 0xFFFFFFFFu;
+                for (uint32_t i = (uint32_t)(s0 - r0) + threadIdx.x; i < (uint32_t)(s1 - r0); i += kRangeThreads)
+                    if (owner_racy(rec[i])) { best = i; break; }
+                if (threadIdx.x == 0) sh.best = ~0ull;
+                __syncthreads();
+                if (best != 0xFFFFFFFFu) atomicMin(&sh.best, r0 + best);
+                __syncthreads();
+                if (threadIdx.x == 0 && sh.best != ~0ull) atomicMin(&a.best_pos[p], sh.best);
+            }
+            if (p + 1 >= a.nprotos || __ldg(&a.protos[p + 1].tab_off) >= r1) break;
+            p++;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && sh.updates) atomicAdd(&a.ctrl->range_tuples, sh.updates);
+}
+
 __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t x)
 {
     if (x == f || x == s) return;
@@ -1338,16 +1582,25 @@ static void launch_jit(const void *k, const BatchArgs &a, const JitLaunch *j, cu
     cudaLaunchKernelExC(&c.cfg, k, params);
 }
 
-// The specialized range pass: kJitRangeBlocksPerSm blocks per SM, each
-// holding one task's records in dynamic shared memory.
-static void launch_range(const BatchArgs &a, const JitLaunch *j, cudaStream_t s, int sms)
+// The range pass: kRangeBlocksPerSm blocks per SM, each holding one task's
+// records in dynamic shared memory (the kernel's attributes set once per
+// device: that much dynamic shared memory, and all of the SM's unified L1 /
+// shared memory as shared memory so that the blocks fit).
+static void launch_range(const BatchArgs &a, cudaStream_t s, int sms)
 {
-    BatchArgs args = a;
-    const uint16_t *shape = j->shape;
-    void *params[] = {&args, &shape};
-    PdlConfig c(dim3((unsigned)sms * kJitRangeBlocksPerSm), dim3(kJitRangeThreads), s);
-    c.cfg.dynamicSmemBytes = kJitRangeSmem;
-    cudaLaunchKernelExC(&c.cfg, j->range, params);
+    static bool ready[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !ready[dev]) {
+        cudaFuncSetAttribute((const void *)k_range, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRangeSmem);
+        cudaFuncSetAttribute((const void *)k_range, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        ready[dev] = true;
+    }
+    const uint32_t want = (uint32_t)sms * kRangeBlocksPerSm;
+    PdlConfig c(dim3(a.nlive < want ? (a.nlive ? a.nlive : 1) : want), dim3(kRangeThreads), s);
+    c.cfg.dynamicSmemBytes = kRangeSmem;
+    cudaLaunchKernelEx(&c.cfg, k_range, a);
 }
 
 // The interpreter, and specialized kernels without a compiled-in schedule,
@@ -1399,15 +1652,13 @@ static void launch_interp_pdl(const BatchArgs &a, cudaStream_t s, int sms)
 static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev,
                                      const JitLaunch *j)
 {
+    if (j && j->table && j->range && !a.range_on) return cudaErrorInvalidValue;   // its range accesses would be lost
     if (j && j->table) launch_jit(j->table, a, j, s, sms);
     else launch_interp_pdl<M_TABLE>(a, s, sms);
     mark(ev, nev, s);
-    if (j && j->range) {
-        launch_range(a, j, s, sms);
+    if (a.range_on) {
+        launch_range(a, s, sms);
         mark(ev, nev, s);
-        launch_jit(j->cell, a, j, s, sms);
-        mark(ev, nev, s);
-        return cudaGetLastError();          // specialized with static phases: the witness pass writes the result
     }
     const uint64_t cap = (uint64_t)sms * 8;
     uint64_t lgrid = (touch_words(a.tab_cells) + kTabScanThreads - 1) / kTabScanThreads;
@@ -1469,7 +1720,9 @@ int stage_names(const char **names, int cap, uint32_t passes, uint32_t path, boo
     all[n++] = "init";
     if (!static_phases && !(count_free && path == PATH_TABLE)) { all[n++] = "count"; all[n++] = "scan"; }
     if (path == PATH_TABLE) {
-        all[n++] = "table"; all[n++] = range ? "range" : "tscan";
+        all[n++] = "table";
+        if (range) all[n++] = "range";
+        all[n++] = "tscan";
         all[n++] = static_phases ? "witness+finalize" : "witness";
     } else {
         all[n++] = "emit";

@@ -19,16 +19,8 @@ inline uint32_t detect_tiles(uint64_t n) { return (uint32_t)((n + kDetectTile - 
 // Kernels specialized to one protocol at run time (host/jit.h), launched in
 // place of the interpreter's count, table and witness passes when set; all
 // take (BatchArgs, const uint16_t *item_shape).
-// Dynamic shared memory of a specialized range pass (its task's records).
-constexpr uint32_t kJitRangeSmem = 16384 * 4;
-constexpr uint32_t kJitRangeThreads = 512;
-constexpr uint32_t kJitRangeBlocksPerSm = 2;
-
 struct JitLaunch {
     const void *count = nullptr, *table = nullptr, *cell = nullptr;
-    // the range pass (host/jit.h): launched in place of the touch listing
-    // and the table scan when set
-    const void *range = nullptr;
     const uint16_t *shape = nullptr;   // device: per item, its code shape
     // The kernels take every item's phase as a constant and the table pass
     // counts the tuples: the count and scan passes are left out.
@@ -36,6 +28,9 @@ struct JitLaunch {
     // The warp-item schedule is compiled in: the kernels do not read the
     // batch's warp-item array.
     bool csched = false;
+    // The table kernel leaves the batch's range accesses to the range pass:
+    // launches need BatchArgs::range_on.
+    bool range = false;
 };
 
 // Stage launchers (all asynchronous on `s`).  Each returns cudaGetLastError().
@@ -50,7 +45,7 @@ cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t
 // Names of the stages whose boundaries launch_front / launch_back record.
 // static_phases: the launch leaves the count and scan passes out (JitLaunch).
 // count_free: an interpreted owner-table launch without them (BatchArgs::count_free).
-// range: the launch runs the range pass in place of the table scan.
+// range: the launch runs the range pass (before the table scan).
 int stage_names(const char **names, int cap, uint32_t passes, uint32_t path, bool static_phases = false,
                 bool count_free = false, bool range = false);
 constexpr int kMaxStages = 4 + kMaxPasses + 2;

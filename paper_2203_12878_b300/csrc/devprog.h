@@ -55,6 +55,7 @@ constexpr uint32_t kFastMax = 4;    // accesses per fast loop body
 enum : uint8_t {
     AF_WRITE = 1,         // access mode: write
     AF_EVAL_IN_COUNT = 2, // the count pass must evaluate the index (it may fail)
+    AF_RANGE = 16,        // the range pass applies it (owner-table launches with BatchArgs::range_on)
 };
 
 struct Insn {

@@ -62,7 +62,7 @@ const JitEntry *jit_entry(drf_ctx *ctx, const uint8_t *bc, size_t len, const drf
     bh.expand_witems();                            // the generator reads the schedule
     Error e = jit_source(p, bh, src, shapes, &stat, &csched, &range);
     if (e.ok()) e = jit_compile(src, cubin, log);
-    if (e.ok()) e = jit_load(cubin, *mod, range);
+    if (e.ok()) e = jit_load(cubin, *mod);
     if (e.ok() && (cudaMalloc(&je->shape, std::max<size_t>(shapes.size() * 2, 16)) != cudaSuccess ||
                    cudaMemcpy(je->shape, shapes.data(), shapes.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess))
         e = Error::make(S_NOMEM, "device allocation failed");
@@ -71,7 +71,7 @@ const JitEntry *jit_entry(drf_ctx *ctx, const uint8_t *bc, size_t len, const drf
         je->launch.count = (const void *)mod->count;
         je->launch.table = (const void *)mod->table;
         je->launch.cell = (const void *)mod->cell;
-        je->launch.range = (const void *)mod->range;
+        je->launch.range = range;
         je->launch.shape = (const uint16_t *)je->shape;
         je->launch.static_phases = stat;
         je->launch.csched = csched;
@@ -230,13 +230,14 @@ int drf_protocol_analyze(const uint8_t *bytecode, size_t len, const drf_bounds *
     Error e = prepare_one(bytecode, len, bounds, PrepareOpts{}, p);
     if (!e.ok()) return e.status;
     BatchHost bh;
-    e = pack_batch({&p}, bh);
+    e = pack_batch({&p}, bh, true, 0, 0);
     out->tuple_bound = p.tuple_bound();
     out->sync_bound = p.max_syncs;
     out->items = (uint32_t)p.items.size();
     out->wide_arithmetic = p.wide ? 1 : 0;
     out->sort_bits = bh.L.sort_bits;
     out->key_bits = bh.L.sort_lo + bh.L.sort_bits;
+    out->range_tuples = bh.rlive.empty() ? 0 : bh.range_tuples;
     return e.status;
 }
 
@@ -285,11 +286,23 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     // is expanded only if the kernels that run read it (compiled-in
     // schedules do not)
     const bool jit_try = valid.size() == 1 && (ctx->opts.flags & DRF_OPT_SPECIALIZE) && path_pref_of(ctx->opts) != 1;
-    Error e = pack_batch(valid, bh, !jit_try, ctx->opts.radix_bits);
+    // a check of the one protocol packed last time reuses that pack (the
+    // host image; it is still uploaded with every check)
+    Error e;
+    const bool same_pack = valid.size() == 1 && ctx->host_of && ctx->host_of.get() == valid[0] &&
+                           ctx->host_digit_bits == ctx->opts.radix_bits && (bh.expanded() || jit_try);
+    if (!same_pack) {
+        ctx->host_of.reset();
+        e = pack_batch(valid, bh, !jit_try, ctx->opts.radix_bits, range_min_of(ctx->opts));
+        if (e.ok() && valid.size() == 1) {
+            ctx->host_of = preps[where[0]];
+            ctx->host_digit_bits = ctx->opts.radix_bits;
+        }
+    }
     if (e.status == S_KEY_TOO_WIDE && valid.size() > 1) {
         // the combined key does not fit: check the protocols one by one
         for (size_t j = 0; j < valid.size(); j++) {
-            Error ej = pack_batch({valid[j]}, bh, true, ctx->opts.radix_bits);
+            Error ej = pack_batch({valid[j]}, bh, true, ctx->opts.radix_bits, range_min_of(ctx->opts));
             if (!ej.ok()) { error_result(ej.status, &out[where[j]]); continue; }
             std::vector<DevResult> r;
             int st = run_batch(ctx, bh, s, r);
@@ -427,7 +440,8 @@ int drf_check_shard(drf_ctx *ctx, const uint8_t *bytecode, size_t len, const drf
     Error e = prepare_one(bytecode, len, bounds, po, p);
     uint64_t lo = 0, hi = 0, total = 0;
     if (e.ok()) e = shard_window(p, shard, nshards, lo, hi, total);
-    if (e.ok()) e = pack_batch({&p}, ctx->host);
+    ctx->host_of.reset();
+    if (e.ok()) e = pack_batch({&p}, ctx->host, true, ctx->opts.radix_bits, range_min_of(ctx->opts));
     if (e.ok() && !ctx->host.table_ok) e = Error::make(S_LIMIT, "the protocol's owner table does not fit");
     if (!e.ok()) {
         error_result(e.status, out);
@@ -561,7 +575,8 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
     plan->ctx = ctx;
     plan->n = n;
     plan->cfg = cfg;
-    Error e = pack_batch(ptrs, plan->host, true, cfg.radix_bits ? cfg.radix_bits : ctx->opts.radix_bits);
+    Error e = pack_batch(ptrs, plan->host, true, cfg.radix_bits ? cfg.radix_bits : ctx->opts.radix_bits,
+                         range_min_of(ctx->opts));
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
     cudaStream_t s = ctx->stream;
     DeviceBatch &d = plan->dev;
@@ -578,12 +593,12 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
         std::vector<char> cubin;
         auto mod = std::make_unique<JitModule>();
         bool stat = false, csched = false, range = false;
-        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes, &stat, &csched, &range, &plan->range_tuples)
+        e = n == 1 ? jit_source(preps[0], plan->host, src, shapes, &stat, &csched, &range)
                    : Error::make(S_INVALID_ARG, "specialization takes a plan of one protocol");
         d.jit.static_phases = stat;
         d.jit.csched = csched;
         if (e.ok()) e = jit_compile(src, cubin, plan->jit_log);
-        if (e.ok()) e = jit_load(cubin, *mod, range);
+        if (e.ok()) e = jit_load(cubin, *mod);
         if (e.ok() && (!ensure(d.ishape, std::max<size_t>(shapes.size() * 2, 16), &d.in_use, d.limit) ||
                        cudaMemcpyAsync(d.ishape.p, shapes.data(), shapes.size() * 2, cudaMemcpyHostToDevice, s) !=
                            cudaSuccess))
@@ -598,7 +613,7 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
         d.jit.count = (const void *)plan->jit->count;
         d.jit.table = (const void *)plan->jit->table;
         d.jit.cell = (const void *)plan->jit->cell;
-        d.jit.range = (const void *)plan->jit->range;
+        d.jit.range = range;
         d.jit.shape = (const uint16_t *)d.ishape.p;
     }
     cudaError_t ce;
@@ -606,7 +621,7 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
     // plan's launches leave them out
     JitLaunch sizing = d.jit;
     sizing.static_phases = false;
-    sizing.range = nullptr;
+    sizing.range = false;
     if ((ce = launch_front(d.args, s, ctx->sms, nullptr, nullptr, &sizing)) != cudaSuccess ||
         (ce = d.fetch(s, true)) != cudaSuccess || (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
         delete plan;
@@ -825,7 +840,7 @@ int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix
 int drf_plan_specialized(const drf_plan *plan, uint32_t *specialized, char *log, size_t loglen)
 {
     if (!plan || !specialized) return DRF_E_INVALID_ARG;
-    *specialized = plan->jit ? (plan->dev.jit.range ? 3 : plan->dev.jit.static_phases ? 2 : 1) : 0;
+    *specialized = plan->jit ? (plan->dev.jit.static_phases ? (plan->dev.args.range_on ? 3 : 2) : 1) : 0;
     if (log && loglen) {
         std::strncpy(log, plan->jit_log.c_str(), loglen - 1);
         log[loglen - 1] = 0;
@@ -884,10 +899,10 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
     if (sort_passes) *sort_passes = table ? 0 : plan->host.L.passes;
     if (kernels_per_launch) {
         uint32_t widths = plan->dev.args.has_narrow + plan->dev.args.has_wide;
-        if (table && plan->dev.jit.range) *kernels_per_launch = 4;   // init, table, range, witness + finalize
-        else if (table && plan->dev.jit.static_phases) *kernels_per_launch = 5;   // init, table, tlist, tscan, witness + finalize
-        else if (table && plan->dev.args.count_free) *kernels_per_launch = 2 * widths + 4;   // init, 2x interp, tlist, tscan, finalize
-        else if (table) *kernels_per_launch = 3 * widths + 5;   // init, 3x interp, scan, tlist, tscan, finalize
+        const uint32_t range = table && plan->dev.args.range_on ? 1 : 0;      // the range pass
+        if (table && plan->dev.jit.static_phases) *kernels_per_launch = 5 + range;   // init, table, tlist, tscan, witness + finalize
+        else if (table && plan->dev.args.count_free) *kernels_per_launch = 2 * widths + 4 + range;   // init, 2x interp, tlist, tscan, finalize
+        else if (table) *kernels_per_launch = 3 * widths + 5 + range;   // init, 3x interp, scan, tlist, tscan, finalize
         else *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes;   // init, 2x interp, scan, passes, detect, resolve, finalize
     }
     if (sort_bits) *sort_bits = plan->host.L.sort_bits;
@@ -905,7 +920,7 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
     if (e != cudaSuccess) return cuda_fail(plan->ctx, e);
     const char *all[kMaxStages];
     int nn = stage_names(all, kMaxStages, plan->host.L.passes, plan->dev.args.path, plan->dev.jit.static_phases,
-                         plan->dev.args.count_free != 0, plan->dev.jit.range != nullptr);
+                         plan->dev.args.count_free != 0, plan->dev.args.range_on != 0);
     int n = std::min(nn, plan->nevents - 1);
     for (int i = 0; i < n && i < cap; i++) {
         float t = 0;
@@ -920,10 +935,10 @@ int drf_plan_stage_times(drf_plan *plan, const char **names, float *ms, int cap,
 int drf_plan_range_tuples(const drf_plan *plan, uint64_t *tuples, uint64_t *updates)
 {
     if (!plan || !tuples) return DRF_E_INVALID_ARG;
-    *tuples = plan->dev.jit.range ? plan->range_tuples : 0;
+    *tuples = plan->dev.args.range_on ? plan->host.range_tuples : 0;
     if (updates) {
         *updates = 0;
-        if (plan->dev.jit.range) {
+        if (plan->dev.args.range_on) {
             drf_ctx *ctx = plan->ctx;
             cudaSetDevice(ctx->device);
             cudaStream_t s = plan->last_stream ? plan->last_stream : ctx->stream;

@@ -43,7 +43,8 @@ void BatchHost::expand_witems()
         for (uint32_t g = 0; g < r.groups; g++) *wi++ = WarpItem{r.proto, r.k, g};
 }
 
-Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool expand, uint32_t digit_bits)
+Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool expand, uint32_t digit_bits,
+                 uint64_t range_min)
 {
     // cleared, not reassigned: a reused image keeps its vectors' capacity
     out.insns.clear();
@@ -141,7 +142,97 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
     for (auto &w : ws) out.runs.push_back(BatchHost::Run{w.proto, w.k, w.groups});
     out.nwitems = nwitems;
     if (expand) out.expand_witems();
+    if (out.table_ok) plan_range(ps, out, range_min);
     return Error{};
+}
+
+namespace {
+
+// Whether protocol i of a packed batch takes the range pass: static phases
+// and range accesses that make a quarter of its tuples or more.
+bool range_candidate(const Prepared &p, const DevProto &d, unsigned __int128 &rt)
+{
+    rt = 0;
+    if (!(d.flags & DP_STATIC) || p.range_access.empty()) return false;
+    for (const RangeAccess &r : p.range_access) rt += (unsigned __int128)r.run_iters * p.nthreads;
+    return rt * 4 >= (unsigned __int128)p.tuple_bound();
+}
+
+}  // namespace
+
+void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_t range_min)
+{
+    out.racc.clear();
+    out.rk.clear();
+    out.rc.clear();
+    out.rlive.clear();
+    out.rfirst.clear();
+    out.range_pcs.assign(ps.size(), {});
+    out.range_tuples = 0;
+    // a batch whose range accesses make few tuples runs faster without the
+    // pass (its planning, upload and kernel would cost more than it saves)
+    unsigned __int128 all = 0, rt = 0;
+    for (size_t i = 0; i < ps.size(); i++)
+        if (range_candidate(*ps[i], out.protos[i], rt)) all += rt;
+    if (all == 0 || all < range_min) return;
+    struct E { uint32_t task, k; int64_t c; };
+    std::vector<E> ent;
+    std::vector<std::pair<int64_t, int64_t>> img;
+    for (size_t i = 0; i < ps.size(); i++) {
+        const Prepared &p = *ps[i];
+        const DevProto &d = out.protos[i];
+        if (!range_candidate(p, d, rt)) continue;
+        const size_t k0 = out.racc.size(), e0 = ent.size();
+        uint64_t tuples = 0;
+        for (const RangeAccess &r : p.range_access) {
+            if (r.phase >= d.tab_phases || r.loc >= d.nlocs || r.offsets.empty() || r.modn >= (1ull << 40)) continue;
+            const uint64_t ncells = p.cells[r.loc];
+            const uint64_t sb = d.tab_off + (uint64_t)r.phase * d.cells_sum + out.cbase[d.cells_off + r.loc];
+            const uint32_t k = (uint32_t)out.racc.size();
+            for (int64_t c : r.offsets) {
+                range_image(r, c, ncells, p.nthreads, img);
+                for (const auto &iv : img)
+                    for (uint64_t t = (sb + (uint64_t)iv.first) / kRangeRecs; t <= (sb + (uint64_t)iv.second - 1) / kRangeRecs; t++)
+                        ent.push_back(E{(uint32_t)t, k, c});
+            }
+            out.racc.push_back(RAcc{sb, ncells, r.modn, r.sigma, r.write ? 1u : 0u, p.nthreads, 0u});
+            out.range_pcs[i].push_back(r.pc);
+            tuples += r.run_iters * (uint64_t)p.nthreads;
+        }
+        if (ent.size() > kRangeMaxEntries) {           // too many: this protocol keeps the table pass
+            ent.resize(e0);
+            out.racc.resize(k0);
+            out.range_pcs[i].clear();
+            continue;
+        }
+        for (uint32_t pc : out.range_pcs[i]) out.insns[d.insn_off + pc].a |= AF_RANGE;
+        out.range_tuples += tuples;
+    }
+    std::sort(ent.begin(), ent.end(), [](const E &x, const E &y) {
+        return x.task != y.task ? x.task < y.task : (x.k != y.k ? x.k < y.k : x.c < y.c);
+    });
+    out.rk.reserve(ent.size());
+    out.rc.reserve(ent.size());
+    for (size_t i = 0; i < ent.size(); i++) {
+        if (i == 0 || ent[i].task != ent[i - 1].task) {
+            out.rlive.push_back(ent[i].task);
+            out.rfirst.push_back((uint32_t)i);
+        }
+        out.rk.push_back(ent[i].k);
+        out.rc.push_back(ent[i].c);
+    }
+    if (!out.rlive.empty()) out.rfirst.push_back((uint32_t)ent.size());
+    if (out.range_tuples < range_min) {              // protocols left out: under the minimum after all
+        for (size_t i = 0; i < ps.size(); i++)
+            for (uint32_t pc : out.range_pcs[i]) out.insns[out.protos[i].insn_off + pc].a &= (uint8_t)~AF_RANGE;
+        out.racc.clear();
+        out.rk.clear();
+        out.rc.clear();
+        out.rlive.clear();
+        out.rfirst.clear();
+        out.range_pcs.assign(ps.size(), {});
+        out.range_tuples = 0;
+    }
 }
 
 DeviceBatch::~DeviceBatch()
@@ -192,7 +283,8 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     size_t end = 0;
     const Section sec[] = {section(b.insns, end), section(b.xcode, end), section(b.items, end),
                            section(b.protos, end), section(b.cells, end), section(b.cbase, end),
-                           section(b.witems, end), section(b.iphase, end)};
+                           section(b.witems, end), section(b.iphase, end), section(b.racc, end),
+                           section(b.rk, end), section(b.rc, end), section(b.rlive, end), section(b.rfirst, end)};
     const size_t total = std::max<size_t>(end, 256);
     bool ok = ensure(image, total, &in_use, limit);
     // the previous copy out of the stage must be done before it is rewritten
@@ -256,6 +348,13 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.witems = b.expanded() ? (const WarpItem *)(img + sec[6].off) : nullptr;
     a.iphase = (const uint32_t *)(img + sec[7].off);
     a.count_free = 0;
+    a.racc = (const RAcc *)(img + sec[8].off);
+    a.rk = (const uint32_t *)(img + sec[9].off);
+    a.rc = (const long long *)(img + sec[10].off);
+    a.rlive = (const uint32_t *)(img + sec[11].off);
+    a.rfirst = (const uint32_t *)(img + sec[12].off);
+    a.nlive = (uint32_t)b.rlive.size();
+    a.range_on = 0;
     a.nwitems = (uint32_t)nw;
     a.nprotos = (uint32_t)np;
     a.has_narrow = a.has_wide = 0;
@@ -324,6 +423,7 @@ Error DeviceBatch::size_table(const BatchHost &b, uint64_t n, cudaStream_t s)
     }
     BatchArgs &a = args;
     a.path = PATH_TABLE;
+    a.range_on = a.nlive ? 1u : 0u;
     a.table = table.p;
     a.tab_cells = b.table_cells;
     a.touch = (uint32_t *)touch.p;
@@ -382,6 +482,7 @@ Error DeviceBatch::size_keys(uint64_t n, cudaStream_t s)
         status_launches = 0;
     }
     args.nkeys = n;
+    args.range_on = 0;
     args.ntiles = tiles;
     args.ndtiles = dtiles;
     args.trec = (TileRec *)trec.p;
@@ -528,6 +629,8 @@ int path_pref_of(const drf_opts &o)
     if (o.flags & DRF_OPT_PATH_TABLE) return 2;
     return 0;
 }
+
+uint64_t range_min_of(const drf_opts &o) { return (o.flags & DRF_OPT_RANGE_ANY) ? 0 : kRangeMinTuples; }
 
 int run_batch(drf_ctx *ctx, const BatchHost &b, cudaStream_t s, std::vector<DevResult> &out)
 {

@@ -56,6 +56,18 @@ struct BatchHost {
     // every protocol is DP_STATIC: owner-table launches may leave the count
     // and scan passes out (BatchArgs::count_free)
     bool all_static = false;
+    // the range pass's work (BatchArgs::racc ..): its accesses, and per task
+    // of kRangeRecs owner records that they reach (rlive, ascending) the
+    // entries [rfirst[i], rfirst[i + 1]) of (access rk, offset rc); their
+    // instructions carry AF_RANGE in `insns`.  range_pcs: per protocol, the
+    // pcs (in its own program) of its range accesses; range_tuples: the
+    // access tuples they make.
+    std::vector<RAcc> racc;
+    std::vector<uint32_t> rk;
+    std::vector<int64_t> rc;
+    std::vector<uint32_t> rlive, rfirst;
+    std::vector<std::vector<uint32_t>> range_pcs;
+    uint64_t range_tuples = 0;
     uint64_t table_bytes() const { return table_cells * 4; }   // one 32-bit owner record per cell
 };
 
@@ -65,8 +77,18 @@ constexpr uint64_t kMaxTableBytes = 64ull << 30;
 // Packs prepared protocols (all valid) into a batch; fails with
 // S_KEY_TOO_WIDE when the combined key layout exceeds 64 bits.  digit_bits:
 // the sort path's radix digit width (4..8; 0 = 8).
+constexpr uint64_t kRangeMinTuples = 1ull << 22;   // default: a batch's range tuples below this, no range pass
 Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool expand = true,
-                 uint32_t digit_bits = 0);
+                 uint32_t digit_bits = 0, uint64_t range_min = kRangeMinTuples);
+
+// The range pass's work lists of a packed batch (BatchHost::racc ..): the
+// range accesses (Prepared::range_access) of every protocol with static
+// phases whose range accesses make a quarter of its tuples or more, their
+// offsets listed for the tasks of owner records their cells fall into, and
+// AF_RANGE set on their instructions.  Called by pack_batch when the batch
+// has an owner table.
+void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_t range_min);
+constexpr size_t kRangeMaxEntries = 1u << 20;
 
 // Offset of the results after the control block in a batch's report.
 constexpr size_t kOutResults = 128;
@@ -171,6 +193,10 @@ struct drf_ctx {
     // bounds (DRF_OPT_SPECIALIZE; at most kJitCacheEntries, then cleared)
     std::map<std::string, std::unique_ptr<drf::JitEntry>> jit_cache;
     drf::PrepCache prep_cache;        // prepared protocols of earlier checks and server requests
+    // `host` holds the pack of this prepared protocol under this radix digit
+    // width (a check of the protocol packed just before reuses it)
+    std::shared_ptr<const drf::Prepared> host_of;
+    uint32_t host_digit_bits = 0;
 };
 
 struct drf_plan {
@@ -188,7 +214,6 @@ struct drf_plan {
     drf::PlanConfig cfg;
     std::unique_ptr<drf::JitModule> jit;   // specialized kernels, when the plan uses them
     std::string jit_log;                   // why specialization was not used, when asked for
-    uint64_t range_tuples = 0;             // access tuples of the range pass's accesses (jit_source)
 };
 
 namespace drf {
@@ -214,6 +239,8 @@ constexpr uint64_t kJitMinTuples = 1ull << 21;
 
 // Back-end preference of a context's options: 0 automatic, 1 sort, 2 owner table.
 int path_pref_of(const drf_opts &o);
+// Fewest range-pass tuples a batch needs to take the pass under these options.
+uint64_t range_min_of(const drf_opts &o);
 
 void to_public(const DevResult &d, drf_result *out);
 

@@ -722,252 +722,14 @@ static __device__ __forceinline__ void put_warp_cur(uint32_t *table, uint32_t *t
 
 )DRF";
 
-// The range pass: one block per task of kRangeRecs consecutive owner
-// records, held in shared memory while the accesses that land there are
-// applied.  kRangeRecs is a multiple of the records one touch word covers
-// (32 blocks of 256), so that every task owns its touch words.
-constexpr uint64_t kRangeRecs = 16384;
-constexpr uint32_t kRangeThreads = 512;
-
-const char *kRangeHelpers = R"DRF(
-#define RANGE_RECS 16384u
-#define RANGE_THREADS 512u
-// One range access's constants: its segment's first record, its array's
-// size, the remainder's modulus (0: none), the sign of tid, and whether it
-// writes.
-struct RAcc { unsigned long long sb, ncells, modn; int sigma; unsigned int w; };
-// tids [t0, t0 + len) of one offset of one access, the record (in the
-// task's shared copy) tid t0 updates -- the others follow at +1 (flags bit
-// 0 clear) or -1 -- and whether it writes (flags bit 1)
-struct REnt { uint32_t t0, len; int32_t l0; uint32_t flags; };
-
-// drf::owner_put on a record in shared memory, in two steps so that several
-// updates can be in flight: the claim (a compare-and-swap that also serves
-// as the read), then the bits the record's owner makes missing
-static __device__ __forceinline__ uint32_t range_claim(uint32_t *r, uint32_t tid, uint32_t w)
-{
-    return atomicCAS(r, 0u, (tid + 1u) | (w << 31));
-}
-
-static __device__ __forceinline__ void range_finish(uint32_t *r, uint32_t old, uint32_t tid, uint32_t w)
-{
-    if (old == 0u) return;                 // claimed: the record was empty
-    const uint32_t need = drf::owner_need(old, tid, w);
-    if (need) atomicOr(r, need);
-}
-
-static __device__ __forceinline__ void range_zero(uint32_t *rec)
-{
-    uint4 *v = reinterpret_cast<uint4 *>(rec);
-    for (uint32_t i = threadIdx.x; i < RANGE_RECS / 4u; i += RANGE_THREADS) v[i] = make_uint4(0u, 0u, 0u, 0u);
-}
-
-// The one or two tid intervals of access `A` at offset `c` (its index is
-// (sigma * tid + c) mod modn, or sigma * tid + c) whose records lie in the
-// task's [r0, r1), appended to the list.
-static __device__ __forceinline__ void range_pieces(const RAcc &A, long long c, unsigned long long r0,
-                                                    unsigned long long r1, long long T, REnt *s_ent, uint32_t &s_n)
-{
-    const unsigned long long sb = A.sb, se = A.sb + A.ncells;
-    if (!(sb < r1 && se > r0)) return;
-    const long long lo_c = (long long)((r0 > sb ? r0 : sb) - sb);
-    const long long hi_c = (long long)((r1 < se ? r1 : se) - sb);
-    const long long loc0 = (long long)sb - (long long)r0;
-    long long ta = 0, na = 0, la = 0, tb = 0, nb = 0, lb = 0, te;
-    if (A.modn == 0 && A.sigma == 1) {
-        ta = lo_c - c; if (ta < 0) ta = 0; te = hi_c - c; if (te > T) te = T;
-        na = te - ta; la = ta + c + loc0;
-    } else if (A.modn == 0) {
-        ta = c - hi_c + 1; if (ta < 0) ta = 0; te = c - lo_c + 1; if (te > T) te = T;
-        na = te - ta; la = c - ta + loc0;
-    } else {
-        const long long N = (long long)A.modn, cm = c;     // c is already reduced mod N here
-        if (A.sigma == 1) {                                // tids below N - cm do not wrap around N
-            ta = lo_c - cm; if (ta < 0) ta = 0; te = hi_c - cm;
-            { const long long lim = N - cm < T ? N - cm : T; if (te > lim) te = lim; }
-            na = te - ta; la = ta + cm + loc0;
-            tb = lo_c - cm + N; if (tb < N - cm) tb = N - cm;
-            te = hi_c - cm + N; if (te > T) te = T;
-            nb = te - tb; lb = tb + cm - N + loc0;
-        } else {                                           // tids up to cm do not wrap below 0
-            ta = cm - hi_c + 1; if (ta < 0) ta = 0; te = cm - lo_c + 1;
-            { const long long lim = cm + 1 < T ? cm + 1 : T; if (te > lim) te = lim; }
-            na = te - ta; la = cm - ta + loc0;
-            tb = cm + N - hi_c + 1; if (tb < cm + 1) tb = cm + 1;
-            te = cm + N - lo_c + 1; if (te > T) te = T;
-            nb = te - tb; lb = cm + N - tb + loc0;
-        }
-    }
-    const uint32_t flags = (A.sigma < 0 ? 1u : 0u) | (A.w << 1);
-    if (na > 0) { const uint32_t e = atomicAdd(&s_n, 1u); s_ent[e] = REnt{(uint32_t)ta, (uint32_t)na, (int32_t)la, flags}; }
-    if (nb > 0) { const uint32_t e = atomicAdd(&s_n, 1u); s_ent[e] = REnt{(uint32_t)tb, (uint32_t)nb, (int32_t)lb, flags}; }
-}
-
-// The owner-record update of one access (tid, w) on a record no other
-// thread updates meanwhile: a plain read and write.
-static __device__ __forceinline__ void range_put_plain(uint32_t *r, uint32_t tid, uint32_t w)
-{
-    const uint32_t old = *r;
-    if (old == 0u) { *r = (tid + 1u) | (w << 31); return; }
-    const uint32_t need = drf::owner_need(old, tid, w);
-    if (need) *r = old | need;
-}
-
-// Records [lo, hi) of the task's shared copy that interval x updates.
-static __device__ __forceinline__ void range_span(const REnt &x, int32_t &lo, int32_t &hi)
-{
-    if (x.flags & 1u) { lo = x.l0 - (int32_t)x.len + 1; hi = x.l0 + 1; }
-    else { lo = x.l0; hi = x.l0 + (int32_t)x.len; }
-}
-
-// Applies the listed intervals (s_ent[0 .. s_n)) to the task's records:
-// every (interval, offset) pair spread over the block, four updates in
-// flight per thread.  Within one interval every record has one tid; when
-// no two intervals of the round share a record (checked here for rounds
-// of up to 64 intervals), no two threads update one record and the updates
-// are plain reads and writes, otherwise atomic.  Leaves s_n at 0.
-static __device__ __forceinline__ void range_apply(uint32_t *rec, const REnt *s_ent, uint32_t *s_pre, uint32_t &s_n,
-                                                   uint32_t &s_tot, unsigned long long &s_rt, uint32_t &s_plain)
-{
-    const uint32_t n = s_n;
-    if (threadIdx.x < 32) {
-        // whether the intervals are pairwise disjoint (one warp, lane e
-        // compares entry e with the ones after it)
-        bool clash = n > 64;
-        for (uint32_t e = threadIdx.x; e < n && !clash; e += 32) {
-            int32_t a0, a1;
-            range_span(s_ent[e], a0, a1);
-            for (uint32_t f = e + 1; f < n; f++) {
-                int32_t b0, b1;
-                range_span(s_ent[f], b0, b1);
-                if (a0 < b1 && b0 < a1) { clash = true; break; }
-            }
-        }
-        clash = __any_sync(0xFFFFFFFFu, clash);
-        if (threadIdx.x == 0) s_plain = clash ? 0u : 1u;
-    }
-    if (threadIdx.x < 32) {                // exclusive prefix of the lengths, one warp
-        uint32_t carry = 0;
-        for (uint32_t b = 0; b < n; b += 32) {
-            const uint32_t e = b + threadIdx.x;
-            const uint32_t v = e < n ? s_ent[e].len : 0u;
-            uint32_t inc = v;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-                if ((int)threadIdx.x >= o) inc += y;
-            }
-            if (e < n) s_pre[e] = carry + inc - v;
-            carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
-        }
-        if (threadIdx.x == 0) { s_tot = carry; s_rt += carry; }
-    }
-    __syncthreads();
-    const uint32_t total = s_tot;
-    uint32_t e = 0;
-    if (s_plain) {
-        for (uint32_t q0 = threadIdx.x; q0 < total; q0 += 4u * RANGE_THREADS) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t q = q0 + (uint32_t)k * RANGE_THREADS;
-                if (q < total) {
-                    while (e + 1 < n && s_pre[e + 1] <= q) e++;
-                    const REnt x = s_ent[e];
-                    const uint32_t o = q - s_pre[e];
-                    range_put_plain(rec + (x.l0 + ((x.flags & 1u) ? -(int32_t)o : (int32_t)o)), x.t0 + o,
-                                    (x.flags >> 1) & 1u);
-                }
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_n = 0;
-        return;
-    }
-    for (uint32_t q0 = threadIdx.x; q0 < total; q0 += 4u * RANGE_THREADS) {
-        uint32_t *rp[4];
-        uint32_t tq[4], wq[4], old[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint32_t q = q0 + (uint32_t)k * RANGE_THREADS;
-            rp[k] = nullptr;
-            if (q < total) {
-                while (e + 1 < n && s_pre[e + 1] <= q) e++;
-                const REnt x = s_ent[e];
-                const uint32_t o = q - s_pre[e];
-                tq[k] = x.t0 + o;
-                wq[k] = (x.flags >> 1) & 1u;
-                rp[k] = rec + (x.l0 + ((x.flags & 1u) ? -(int32_t)o : (int32_t)o));
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; k++) old[k] = rp[k] ? range_claim(rp[k], tq[k], wq[k]) : 0u;
-#pragma unroll
-        for (int k = 0; k < 4; k++) if (rp[k]) range_finish(rp[k], old[k], tq[k], wq[k]);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) s_n = 0;
-}
-
-// The task's records at [r0, r1): the blocks the table pass touched merged
-// into the (zeroed) shared copy and cleared in the table, their touch words
-// cleared; returns whether any was touched.
-static __device__ __forceinline__ bool range_merge(const drf::BatchArgs &a, uint32_t *rec, uint32_t *s_bits,
-                                                   unsigned long long r0, uint32_t nrec, bool zeroed)
-{
-    const uint32_t nwords = (nrec + 8191u) >> 13;
-    uint32_t tb = 0;
-    if (threadIdx.x < nwords) {
-        // through L2: this SM's L1 may hold lines the table pass read
-        tb = __ldcg(a.touch + (r0 >> 13) + threadIdx.x);
-        s_bits[threadIdx.x] = tb;
-        if (tb) a.touch[(r0 >> 13) + threadIdx.x] = 0u;
-    }
-    const bool any = __syncthreads_or(tb != 0u) != 0;
-    if (!any) return false;
-    if (!zeroed) { range_zero(rec); __syncthreads(); }
-    uint32_t *const tab = reinterpret_cast<uint32_t *>(a.table);
-    for (uint32_t i = threadIdx.x; i < nrec; i += RANGE_THREADS) {
-        const uint32_t blk = i >> 8;
-        if ((s_bits[blk >> 5] >> (blk & 31u)) & 1u) {
-            const uint32_t v = __ldcg(tab + r0 + i);
-            if (v) { rec[i] = v; tab[r0 + i] = 0u; }
-        }
-    }
-    __syncthreads();
-    return true;
-}
-
-// The task's first racy record (rows are phase-major, then array, then
-// index: the lexicographic order of the witness) into best_pos; records
-// past nrec are zero.
-static __device__ __forceinline__ void range_scan(const drf::BatchArgs &a, const uint32_t *rec, unsigned long long r0,
-                                                  uint32_t nrec, unsigned int &s_best)
-{
-    uint32_t best = 0xFFFFFFFFu;
-    const uint4 *r4 = reinterpret_cast<const uint4 *>(rec);
-    for (uint32_t i = threadIdx.x; i < (nrec + 3u) / 4u; i += RANGE_THREADS) {
-        const uint4 v = r4[i];
-        if (drf::owner_racy(v.x)) { best = 4u * i; break; }
-        if (drf::owner_racy(v.y)) { best = 4u * i + 1u; break; }
-        if (drf::owner_racy(v.z)) { best = 4u * i + 2u; break; }
-        if (drf::owner_racy(v.w)) { best = 4u * i + 3u; break; }
-    }
-    if (threadIdx.x == 0) s_best = 0xFFFFFFFFu;
-    __syncthreads();
-    if (best != 0xFFFFFFFFu) atomicMin(&s_best, best);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_best != 0xFFFFFFFFu) atomicMin(&a.best_pos[0], r0 + s_best);
-}
-)DRF";
-
 constexpr size_t kMaxConstItems = 1024;  // items whose schedule and positions are compiled in
 constexpr uint64_t kMaxPhaseRanges = 1u << 16;   // phases whose item ranges are compiled in
 
 }  // namespace
 
 Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::vector<uint16_t> &item_shape,
-                 bool *static_phases, bool *compiled_schedule, bool *range_pass, uint64_t *range_pass_tuples)
+                 bool *static_phases, bool *compiled_schedule, bool *range_pass)
 {
-    if (range_pass_tuples) *range_pass_tuples = 0;
     if (static_phases) *static_phases = false;
     if (compiled_schedule) *compiled_schedule = false;
     if (range_pass) *range_pass = false;
@@ -1058,53 +820,11 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
         for (uint64_t ph = 0; ph < nph; ph++) o << (ph ? "," : "") << phi[ph] << "u";
         o << "};\n";
     }
-    // The range pass (with static phases, one protocol at the table's
-    // start): the accesses it can take (RangeAccess), their distinct
-    // offsets found here by evaluating their loops, each offset listed for
-    // the tasks its cells fall into.  Used when those accesses make a
-    // quarter of the tuples or more and the lists stay small.
-    struct REntry { uint64_t task; uint32_t k; int64_t c; };
-    std::vector<const RangeAccess *> racc;
-    std::vector<REntry> rent;
-    uint64_t range_tuples = 0;
-    const uint64_t tab_end = d.tab_off + (uint64_t)d.tab_phases * d.cells_sum;
-    if (stat && d.tab_off == 0 && tab_end > 0 && d.nthreads > 0 && (tab_end + kRangeRecs - 1) / kRangeRecs <= (1ull << 24)) {
-        std::vector<std::pair<int64_t, int64_t>> img;
-        for (const RangeAccess &r : p.range_access) {
-            if (r.phase >= d.tab_phases || r.loc >= d.nlocs || r.modn >= (1ull << 40) || racc.size() >= 256) continue;
-            const uint64_t iters = r.run_iters;
-            const std::vector<int64_t> &cs = r.offsets;       // evaluated at preparation
-            const uint64_t ncells = p.cells.at(r.loc);
-            const uint64_t sb = d.tab_off + (uint64_t)r.phase * d.cells_sum + b.cbase.at(d.cells_off + r.loc);
-            const uint32_t k = (uint32_t)racc.size();
-            size_t added = 0;
-            for (int64_t c : cs) {
-                range_image(r, c, ncells, d.nthreads, img);
-                for (const auto &iv : img)
-                    for (uint64_t t = (sb + (uint64_t)iv.first) / kRangeRecs; t <= (sb + (uint64_t)iv.second - 1) / kRangeRecs; t++) {
-                        rent.push_back(REntry{t, k, c});
-                        added++;
-                    }
-            }
-            if (rent.size() > (1u << 18)) { rent.clear(); racc.clear(); break; }
-            racc.push_back(&r);
-            range_tuples += iters * (uint64_t)d.nthreads;
-            (void)added;
-        }
-        if (racc.empty() || (unsigned __int128)range_tuples * 4 < (unsigned __int128)p.tuple_bound()) {
-            racc.clear();
-            rent.clear();
-            range_tuples = 0;
-        }
-    }
-    const bool range = !racc.empty();
+    // The range pass (pack_batch's plan_range): the table pass leaves the
+    // protocol's range accesses to it and only counts them.
+    const bool range = !b.rlive.empty() && !b.range_pcs.empty() && !b.range_pcs[0].empty();
     if (range_pass) *range_pass = range;
-    if (range_pass_tuples) *range_pass_tuples = range_tuples;
-    if (range) {
-        std::set<uint32_t> pcs;
-        for (const RangeAccess *r : racc) pcs.insert(r->pc);
-        g.set_range_skip(pcs);
-    }
+    if (range) g.set_range_skip(std::set<uint32_t>(b.range_pcs[0].begin(), b.range_pcs[0].end()));
     const Mode modes[] = {GM_COUNT, GM_TABLE, GM_CELL};
     for (Mode m : modes)
         for (size_t s = 0; s < keys.size(); s++)
@@ -1353,114 +1073,6 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
 )DRF";
     }
     o << "}\n";
-    if (range) {
-        // the range pass: in place of the touch listing and table scan
-        std::sort(rent.begin(), rent.end(), [](const REntry &x, const REntry &y) {
-            return x.task != y.task ? x.task < y.task : (x.k != y.k ? x.k < y.k : x.c < y.c);
-        });
-        const uint64_t ntasks = (tab_end - d.tab_off + kRangeRecs - 1) / kRangeRecs;
-        std::vector<uint64_t> live;
-        std::vector<uint32_t> first;
-        for (size_t i = 0; i < rent.size(); i++)
-            if (i == 0 || rent[i].task != rent[i - 1].task) { live.push_back(rent[i].task); first.push_back((uint32_t)i); }
-        first.push_back((uint32_t)rent.size());
-        std::vector<uint32_t> bits((ntasks + 31) / 32, 0u);
-        for (uint64_t t : live) bits[t >> 5] |= 1u << (t & 31);
-        o << kRangeHelpers;
-        o << "static __device__ const RAcc r_acc[" << racc.size() << "] = {";
-        for (size_t k = 0; k < racc.size(); k++) {
-            const RangeAccess &r = *racc[k];
-            const uint64_t sb = d.tab_off + (uint64_t)r.phase * d.cells_sum + b.cbase.at(d.cells_off + r.loc);
-            o << (k ? "," : "") << "{" << ulit(sb) << "," << ulit(p.cells.at(r.loc)) << "," << ulit(r.modn) << ","
-              << r.sigma << "," << (r.write ? 1 : 0) << "u}";
-        }
-        o << "};\n";
-        o << "static __device__ const unsigned int r_live[" << live.size() << "] = {";
-        for (size_t i = 0; i < live.size(); i++) o << (i ? "," : "") << live[i] << "u";
-        o << "};\nstatic __device__ const unsigned int r_first[" << first.size() << "] = {";
-        for (size_t i = 0; i < first.size(); i++) o << (i ? "," : "") << first[i] << "u";
-        o << "};\nstatic __device__ const unsigned short r_k[" << rent.size() << "] = {";
-        for (size_t i = 0; i < rent.size(); i++) o << (i ? "," : "") << rent[i].k;
-        o << "};\nstatic __device__ const long long r_c[" << rent.size() << "] = {";
-        for (size_t i = 0; i < rent.size(); i++) o << (i ? "," : "") << lit64(rent[i].c);
-        o << "};\nstatic __device__ const unsigned int r_bits[" << bits.size() << "] = {";
-        for (size_t i = 0; i < bits.size(); i++) o << (i ? "," : "") << bits[i] << "u";
-        o << "};\n";
-        o << "extern \"C\" __global__ void __launch_bounds__(" << kRangeThreads << ") drf_range" << sig
-          << R"DRF(    extern __shared__ uint4 r_dyn[];
-    uint32_t *const rec = reinterpret_cast<uint32_t *>(r_dyn);
-    __shared__ REnt s_ent[2 * RANGE_THREADS];
-    __shared__ uint32_t s_pre[2 * RANGE_THREADS];
-    __shared__ uint32_t s_n, s_tot, s_plain, s_bits[RANGE_RECS / 8192u];
-    __shared__ unsigned int s_best;
-    __shared__ unsigned long long s_rt;   // record updates this block made
-    // the witness pass's hit bits, which the touch listing clears otherwise
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.nhit; i += (uint64_t)gridDim.x * blockDim.x) {
-        a.hit_acc[i] = 0u;
-        a.hit_wr[i] = 0u;
-    }
-    if (threadIdx.x == 0) { s_n = 0; s_rt = 0; }
-    __syncthreads();
-)DRF";
-        o << "    const unsigned long long tab_end = " << ulit(tab_end) << ", tab_off = " << ulit(d.tab_off) << ";\n"
-          << "    const long long T = " << d.nthreads << "ll;\n"
-          << "    // 1. the tasks the range accesses reach, each with its list of (access, offset)\n"
-          << "    for (uint32_t li = blockIdx.x; li < " << live.size() << "u; li += gridDim.x) {\n"
-          << R"DRF(        const unsigned long long r0 = tab_off + (unsigned long long)__ldg(&r_live[li]) * RANGE_RECS;
-        const unsigned long long r1 = r0 + RANGE_RECS < tab_end ? r0 + RANGE_RECS : tab_end;
-        const uint32_t nrec = (uint32_t)(r1 - r0);
-        range_zero(rec);
-        __syncthreads();
-        range_merge(a, rec, s_bits, r0, nrec, true);
-        const uint32_t e1 = __ldg(&r_first[li + 1]);
-        for (uint32_t e0 = __ldg(&r_first[li]); e0 < e1; e0 += RANGE_THREADS) {
-            const uint32_t e = e0 + threadIdx.x;
-            if (e < e1) range_pieces(r_acc[__ldg(&r_k[e])], __ldg(&r_c[e]), r0, r1, T, s_ent, s_n);
-            __syncthreads();
-            range_apply(rec, s_ent, s_pre, s_n, s_tot, s_rt, s_plain);
-        }
-        range_scan(a, rec, r0, nrec, s_best);
-    }
-    // 2. the other tasks: only the table pass's records, where it made any,
-    //    scanned in place -- one warp per touch word (32 blocks of 256
-    //    records), the words of listed tasks skipped (step 1 has them)
-)DRF";
-        const uint64_t nwords_all = (table_blocks(tab_end) + 31) / 32;
-        o << "    {\n"
-          << "    const uint32_t lane = threadIdx.x & 31u;\n"
-          << "    uint32_t *const tab = reinterpret_cast<uint32_t *>(a.table);\n"
-          << "    for (unsigned long long w = (unsigned long long)blockIdx.x * (RANGE_THREADS / 32u) + threadIdx.x / 32u; w < "
-          << ulit(nwords_all) << "; w += (unsigned long long)gridDim.x * (RANGE_THREADS / 32u)) {\n"
-          << "        const unsigned long long task = (w * 8192ull - tab_off) / RANGE_RECS;\n"
-          << R"DRF(        if ((__ldg(&r_bits[task >> 5]) >> (task & 31u)) & 1u) continue;
-        uint32_t bits = __ldcg(a.touch + w);
-        if (!bits) continue;
-        if (lane == 0) a.touch[w] = 0u;
-        unsigned long long best = ~0ull;
-        for (; bits; bits &= bits - 1u) {
-            const unsigned long long blk = w * 32ull + (unsigned long long)(__ffs(bits) - 1);
-            uint4 *src = reinterpret_cast<uint4 *>(tab) + blk * 64ull + lane * 2u;
-            const uint4 v0 = __ldcg(src), v1 = __ldcg(src + 1);
-            const uint32_t r[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-            for (int i = 0; i < 8; i++)
-                if (drf::owner_racy(r[i])) { const unsigned long long pos = blk * 256ull + lane * 8u + (uint32_t)i; if (pos < best) best = pos; }
-            if ((v0.x | v0.y | v0.z | v0.w) != 0u) src[0] = make_uint4(0u, 0u, 0u, 0u);
-            if ((v1.x | v1.y | v1.z | v1.w) != 0u) src[1] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        for (int o = 16; o; o >>= 1) {
-            const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-            best = y < best ? y : best;
-        }
-        if (lane == 0 && best != ~0ull) atomicMin(&a.best_pos[0], best);
-    }
-    }
-    __syncthreads();
-)DRF";
-        o << R"DRF(    if (threadIdx.x == 0 && s_rt) atomicAdd(&a.ctrl->range_tuples, s_rt);
-}
-)DRF";
-    }
     src = o.str();
     if (src.size() > kMaxSourceBytes) return Error::make(S_LIMIT, "specialized source too large");
     return Error{};
@@ -1532,9 +1144,8 @@ Error jit_compile(const std::string &src, std::vector<char> &cubin, std::string 
     return e;
 }
 
-Error jit_load(const std::vector<char> &cubin, JitModule &m, bool want_range)
+Error jit_load(const std::vector<char> &cubin, JitModule &m)
 {
-    static_assert(kJitRangeSmem == kRangeRecs * 4, "the range pass holds its task's records in shared memory");
     cudaError_t ce = cudaLibraryLoadData(&m.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&m.count, m.lib, "drf_count");
     if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&m.table, m.lib, "drf_table");
@@ -1542,22 +1153,6 @@ Error jit_load(const std::vector<char> &cubin, JitModule &m, bool want_range)
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return Error::make(S_CUDA, std::string("loading the specialized kernels: ") + cudaGetErrorString(ce));
-    }
-    if (want_range) {
-        int dev = 0;
-        ce = cudaLibraryGetKernel(&m.range, m.lib, "drf_range");
-        if (ce == cudaSuccess) ce = cudaGetDevice(&dev);
-        if (ce == cudaSuccess)
-            ce = cudaKernelSetAttributeForDevice(m.range, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJitRangeSmem, dev);
-        // all of the SM's unified L1 / shared memory as shared memory, so that
-        // kJitRangeBlocksPerSm blocks fit
-        if (ce == cudaSuccess)
-            ce = cudaKernelSetAttributeForDevice(m.range, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                                 cudaSharedmemCarveoutMaxShared, dev);
-        if (ce != cudaSuccess) {
-            cudaGetLastError();
-            return Error::make(S_CUDA, std::string("loading the range pass: ") + cudaGetErrorString(ce));
-        }
     }
     return Error{};
 }

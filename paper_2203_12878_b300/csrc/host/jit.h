@@ -33,19 +33,11 @@ struct BatchHost;
 // not null) is set when the warp-item schedule is compiled in: the kernels
 // then read neither the batch's warp-item array nor its item descriptors.
 // `b` must hold its expanded warp-item array.
-// *range_pass (when not null) is set when the source also holds the range
-// pass (drf_range): accesses whose index is +-tid plus a function of the
-// loop variables (Prepared::range_access) are applied, task by task of
-// consecutive owner records, in shared memory -- the table pass only counts
-// them -- and the range pass takes the place of the touch listing and table
-// scan: it merges and clears the table pass's records and finds the first
-// racy cell.  The accesses' distinct offsets are found here, by evaluating
-// their loops, and compiled in as per-task lists.
-// *range_pass_tuples: the access tuples the range accesses make (all threads,
-// every iteration; duplicates of an offset are applied once).
+// *range_pass (when not null) is set when the batch's range pass (pack_batch,
+// plan_range) takes some of the protocol's accesses: the generated table
+// pass only counts those, the precompiled range pass applies them.
 Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::vector<uint16_t> &item_shape,
-                 bool *static_phases = nullptr, bool *compiled_schedule = nullptr, bool *range_pass = nullptr,
-                 uint64_t *range_pass_tuples = nullptr);
+                 bool *static_phases = nullptr, bool *compiled_schedule = nullptr, bool *range_pass = nullptr);
 
 // Compiles `src` for sm_103a with NVRTC.  On failure, `log` holds the
 // compiler's log (or why NVRTC is unavailable).
@@ -55,15 +47,12 @@ Error jit_compile(const std::string &src, std::vector<char> &cubin, std::string 
 struct JitModule {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t count = nullptr, table = nullptr, cell = nullptr;
-    cudaKernel_t range = nullptr;      // the range pass, when the source has one
     JitModule() = default;
     JitModule(const JitModule &) = delete;
     JitModule &operator=(const JitModule &) = delete;
     ~JitModule();
 };
 
-// want_range: the source holds the range pass (its dynamic shared memory,
-// kJitRangeSmem bytes, is allowed here).
-Error jit_load(const std::vector<char> &cubin, JitModule &m, bool want_range = false);
+Error jit_load(const std::vector<char> &cubin, JitModule &m);
 
 }  // namespace drf

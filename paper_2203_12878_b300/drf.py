@@ -28,6 +28,7 @@ OPT_AUTOTUNE = 0x2
 OPT_PATH_SORT = 0x4      # force the sort back end
 OPT_PATH_TABLE = 0x8     # force the owner-table back end
 OPT_SPECIALIZE = 0x10    # plans over one protocol may compile kernels specialized to it
+OPT_RANGE_ANY = 0x20     # the owner table's range pass for batches of any size
 PATHS = {1: "sort", 2: "table"}
 
 
@@ -64,7 +65,8 @@ class drf_opts(ctypes.Structure):
 
 class drf_analysis(ctypes.Structure):
     _fields_ = [("tuple_bound", ctypes.c_uint64), ("sync_bound", ctypes.c_uint64), ("items", ctypes.c_uint32),
-                ("wide_arithmetic", ctypes.c_uint32), ("sort_bits", ctypes.c_uint32), ("key_bits", ctypes.c_uint32)]
+                ("wide_arithmetic", ctypes.c_uint32), ("sort_bits", ctypes.c_uint32), ("key_bits", ctypes.c_uint32),
+                ("range_tuples", ctypes.c_uint64)]
 
 
 class drf_server_opts(ctypes.Structure):

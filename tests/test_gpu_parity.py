@@ -16,13 +16,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CELLS = 1
 
 
-PATH_FLAGS = {"sort": drf.OPT_PATH_SORT, "table": drf.OPT_PATH_TABLE}
+PATH_FLAGS = {"sort": drf.OPT_PATH_SORT, "table": drf.OPT_PATH_TABLE,
+              "table+range": drf.OPT_PATH_TABLE | drf.OPT_RANGE_ANY}   # range pass at any size
 TABLE_LIMIT = 64 << 30           # bytes: the largest owner table the library sets up
 
 
-@pytest.fixture(scope="module", params=["sort", "table"])
+@pytest.fixture(scope="module", params=["sort", "table", "table+range"])
 def ctx(request):
-    """A context forced onto one back end; every test using it runs on both."""
+    """A context forced onto one back end; every test using it runs on both
+    (the owner table with and without the range pass)."""
     c = drf.drf_ctx_create(0, flags=PATH_FLAGS[request.param])
     c.path = request.param
     yield c
@@ -56,7 +58,7 @@ def table_fits(p):
 
 def want(oracle, p, ctx=None):
     exp = oracle.check(p.text, p.nthreads, p.cells, p.params, CELLS)
-    if ctx is not None and getattr(ctx, "path", "") == "table" and exp["status"] == "OK" and not table_fits(p):
+    if ctx is not None and getattr(ctx, "path", "").startswith("table") and exp["status"] == "OK" and not table_fits(p):
         return {"status": "LIMIT"}
     return exp
 
@@ -509,3 +511,28 @@ def test_server_splits_a_round_that_does_not_fit(oracle):
     for t, g in zip(texts, got):
         assert same(g, oracle.check(t, 1024, [n], [], CELLS)), t
     assert got[-1]["verdict"] == "RACY"
+
+
+def test_interpreted_batch_runs_the_range_pass(oracle):
+    """An interpreted owner-table plan over a batch: the protocols whose
+    accesses at +-tid plus loop terms make most of their tuples go to the
+    range pass (tasks spanning several protocols' rows), the others to the
+    table pass alone; every result equals the oracle, launch after launch."""
+    c = drf.drf_ctx_create(0, flags=drf.OPT_PATH_TABLE | drf.OPT_RANGE_ANY)
+    try:
+        ps = protogen.config4(master_seed=23, count=40) + [protogen.shifted_small(s) for s in range(20)]
+        ps += [protogen.random_small(s) for s in range(300, 320)]
+        ps = [p for p in ps if want(oracle, p)["status"] == "OK"]
+        plan = drf.drf_plan_create(c, [drf.drf_protocol_compile(p.text) for p in ps],
+                                   [(p.nthreads, p.cells, p.params) for p in ps])
+        try:
+            for _ in range(3):
+                drf.drf_plan_launch(plan)
+                for p, r in zip(ps, drf.drf_plan_results(plan)):
+                    assert same(drf.result_dict(r), want(oracle, p)), p.text
+            tuples, updates = drf.drf_plan_range_tuples(plan)
+            assert tuples > 0 and updates > 0
+        finally:
+            drf.drf_plan_destroy(plan)
+    finally:
+        drf.drf_ctx_destroy(c)

@@ -68,10 +68,24 @@ def test_range_pass_source_compiles(seed):
 
 
 def test_grid_scale_protocol_gets_the_range_pass():
+    """Every owned write (+-tid + 65536 * g(x, y) + d) mod 2^24 of the
+    grid-scale protocol goes to the range pass: 206,241,792 of its
+    221,642,754 tuples; the reads of other tid coefficients stay in the
+    table pass."""
     p = protogen.config3(0, racy=True)
+    st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
+    assert st == "OK"
+    assert a["range_tuples"] == 206241792
     st, src, log = drf.drf_protocol_specialize(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
     assert st == "OK", log
-    assert 'extern "C" __global__ void __launch_bounds__(512) drf_range(' in src
-    # every owned write (tid + 65536 * g(x, y) + d) mod 2^24 is the range pass's
-    import re
-    assert int(re.search(r"const RAcc r_acc\[(\d+)\]", src).group(1)) >= 15
+
+
+def test_protocols_without_shifted_indices_get_no_range_pass():
+    for text, T, n in (("array A;\nwr A[2 * tid];\n", 64, 128),                  # another tid coefficient
+                       ("array A;\nforU x in 0 .. tid { wr A[tid + 64 * x]; }\n", 64, 64 * 64),   # bound reads tid
+                       ("array A;\nforS x in 0 .. 4 { wr A[tid + 64 * x]; sync; }\n", 64, 256)):  # sync in the loop
+        st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile(text), T, [n], [])
+        assert st == "OK" and a["range_tuples"] == 0, text
+    st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile("array A;\nforU x in 0 .. 4 { wr A[tid + 64 * x]; }\n"),
+                                     64, [256], [])
+    assert st == "OK" and a["range_tuples"] == 256          # counted at any size

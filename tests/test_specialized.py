@@ -20,6 +20,14 @@ def sctx():
     drf.drf_ctx_destroy(c)
 
 
+@pytest.fixture(scope="module")
+def rctx():
+    """Specialized plans that take the range pass at any size."""
+    c = drf.drf_ctx_create(0, flags=drf.OPT_SPECIALIZE | drf.OPT_RANGE_ANY)
+    yield c
+    drf.drf_ctx_destroy(c)
+
+
 def want(oracle, p):
     return oracle.check(p.text, p.nthreads, p.cells, p.params, 1)
 
@@ -257,7 +265,7 @@ def test_witness_hits_solved_per_loop(sctx, oracle, chunk):
 
 
 @pytest.mark.parametrize("chunk", range(4))
-def test_range_pass_against_oracle(sctx, oracle, chunk):
+def test_range_pass_against_oracle(rctx, oracle, chunk):
     """Accesses at +-tid plus a function of the loop variables (with and
     without a remainder, arrays of odd sizes across several 16384-record
     tasks, conditions on loop variables) go through the range pass, mixed
@@ -266,8 +274,15 @@ def test_range_pass_against_oracle(sctx, oracle, chunk):
     after launch."""
     kinds = []
     for seed in range(chunk * 20, (chunk + 1) * 20):
-        kinds.append(check(sctx, oracle, protogen.shifted_small(seed)))
+        kinds.append(check(rctx, oracle, protogen.shifted_small(seed)))
     assert kinds.count(3) >= 10, kinds
+
+
+def test_small_protocols_skip_the_range_pass_by_default(sctx, oracle):
+    """Under 2^22 range tuples a check keeps the table pass alone (same
+    results)."""
+    for seed in range(6):
+        assert check(sctx, oracle, protogen.shifted_small(seed)) in (1, 2)
 
 
 def test_config3_runs_the_range_pass(sctx):
@@ -275,6 +290,10 @@ def test_config3_runs_the_range_pass(sctx):
     plan = drf.drf_plan_create(sctx, [drf.drf_protocol_compile(p.text)], [(p.nthreads, p.cells, p.params)])
     try:
         assert drf.drf_plan_specialized(plan)[0] == 3
-        assert drf.drf_plan_info(plan)["kernels_per_launch"] == 4
+        # init, table, range, touch listing, table scan, witness + result
+        assert drf.drf_plan_info(plan)["kernels_per_launch"] == 6
+        drf.drf_plan_launch(plan)
+        tuples, updates = drf.drf_plan_range_tuples(plan)
+        assert tuples == 206241792 and 0 < updates < tuples
     finally:
         drf.drf_plan_destroy(plan)

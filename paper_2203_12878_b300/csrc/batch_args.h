@@ -113,6 +113,7 @@ struct BatchArgs {
     const long long *rc;
     const uint32_t *rlive;
     const uint32_t *rfirst;
+    const uint32_t *rorder;         // the order blocks take tasks in (indices into rlive): most work first
     uint32_t nlive;
     uint32_t range_on;
     void *table;                     // [tab_cells] 32-bit owner records, padded to whole blocks

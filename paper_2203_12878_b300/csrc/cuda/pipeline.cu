@@ -314,10 +314,11 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             V idx = 0;
             // the witness pass runs only protocols none of whose accesses
             // fails, and needs the index only of accesses in the cell's phase
-            // and array
-            // (nor does the table pass the index of an access the range pass applies)
-            const bool need = CELL ? (phase == tg.phase && in.b == tg.loc)
-                                   : TAB ? !(a.range_on && (in.a & AF_RANGE)) : (PHASED || (in.a & AF_EVAL_IN_COUNT));
+            // and array; neither it nor the table pass needs the index of an
+            // access the range pass applies (k_finalize adds its witnesses)
+            const bool rng = a.range_on && (in.a & AF_RANGE);
+            const bool need = CELL ? (phase == tg.phase && in.b == tg.loc && !rng)
+                                   : TAB ? !rng : (PHASED || (in.a & AF_EVAL_IN_COUNT));
             if (ex && need) {
                 if (!eval<V>(xc, in.c, tid, vars, idx)) { err = kErrDiv0; ok = false; }
                 else if (idx < 0 || (uint64_t)(U)idx >= __ldg(cells + in.b)) { err = kErrOob; ok = false; }
@@ -339,10 +340,9 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                 const unsigned long long off =
                     put ? P.tab_off + (uint64_t)phase * P.cells_sum + __ldg(cb + in.b) + (uint64_t)(U)idx : 0ull;
                 // an access the range pass applies is only counted here
-                const bool mine = !(a.range_on && (in.a & AF_RANGE));
-                table_put(a, mine && put && off >= a.shard_lo && off < a.shard_hi, off, tid, in.a & AF_WRITE);
+                table_put(a, !rng && put && off >= a.shard_lo && off < a.shard_hi, off, tid, in.a & AF_WRITE);
             } else if (CELL) {
-                if (ok && phase == tg.phase && in.b == tg.loc && (unsigned long long)(U)idx == tg.idx)
+                if (ok && !rng && phase == tg.phase && in.b == tg.loc && (unsigned long long)(U)idx == tg.idx)
                     hit |= 1u | ((in.a & AF_WRITE) << 1);
             } else if (ok) {
                 count++;
@@ -399,14 +399,18 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             }
             const uint64_t trip = (okb && lo < hi) ? (uint64_t)(U)((U)hi - (U)lo) : 0;
             const uint32_t m = (uint32_t)in.e;
-            // the table pass takes a loop whose accesses the range pass all
-            // applies in one step: it only counts them
-            bool skip = TAB && a.range_on;
+            // the table and witness passes take a loop whose accesses the
+            // range pass all applies in one step: the table pass counts them
+            bool skip = (TAB || CELL) && a.range_on;
             for (uint32_t j = 0; j < m && skip; j++) skip = (load_insn(prog + mpc + 1 + j).a & AF_RANGE) != 0;
             if (!PHASED) {
                 if (okb) { count += (uint32_t)(trip * m); syncs += (uint32_t)(trip * in.b); }
             } else if (skip) {
-                if (okb) { count += (uint32_t)(trip * m); phase += (uint32_t)(trip * in.b); }
+                if (okb) {
+                    if (TAB) count += (uint32_t)(trip * m);
+                    phase += (uint32_t)(trip * in.b);
+                }
+                if (CELL && phase > tg.phase) running = false;
             } else {
                 V rest[kFastMax];
                 U coef[kFastMax], pcon[kFastMax];
@@ -463,7 +467,8 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                                 table_put(a, mine && put && off >= a.shard_lo && off < a.shard_hi, off, tid,
                                           mt & AF_WRITE);
                             } else if (CELL) {
-                                if (act && ph == tg.phase && loc == tg.loc && (unsigned long long)(U)idx == tg.idx)
+                                if (act && !(a.range_on && (mt & AF_RANGE)) && ph == tg.phase && loc == tg.loc &&
+                                    (unsigned long long)(U)idx == tg.idx)
                                     hit |= 1u | ((mt & AF_WRITE) << 1);
                             }
                         }
@@ -1174,11 +1179,12 @@ constexpr uint32_t kRDown = 1u << 31, kRWrite = 1u << 30, kRLen = (1u << 30) - 1
 
 struct RangeShared {
     REnt ent[2 * kRangeChunk];
-    uint32_t pre[2 * kRangeChunk];
+    uint32_t pre[2 * kRangeChunk];                // also the task's racy-record bitmap at its end
     uint32_t n, tot, plain, bits[kRangeRecs / 8192];
-    unsigned long long best;
     unsigned long long updates;                   // record updates the block made
 };
+static_assert(2 * kRangeChunk * 32 >= kRangeRecs, "the racy bitmap needs a bit per record");
+
 
 // The one or two tid intervals of access A at offset c (reduced mod the
 // modulus when there is one) whose records lie in [w0, w1), within the task
@@ -1269,7 +1275,56 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
     __syncthreads();
     const uint32_t total = sh.tot;
     const bool plain = sh.plain != 0;
-    uint32_t e = 0;
+    if (total >= n * 2u * kRangeThreads) {
+        // long intervals: the block takes them one by one, a record per
+        // thread (no position search)
+        for (uint32_t e = 0; e < n; e++) {
+            const REnt x = sh.ent[e];
+            const uint32_t len = x.lenf & kRLen, w = (x.lenf & kRWrite) ? 1u : 0u;
+            const int32_t step = (x.lenf & kRDown) ? -1 : 1;
+            for (uint32_t o0 = threadIdx.x; o0 < len; o0 += 4u * kRangeThreads) {
+                int32_t ri[4];
+                uint32_t old[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t o = o0 + (uint32_t)k * kRangeThreads;
+                    ri[k] = o < len ? x.l0 + step * (int32_t)o : -1;
+                }
+                if (plain) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) old[k] = ri[k] >= 0 ? rec[ri[k]] : 0u;
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        if (ri[k] < 0) continue;
+                        const uint32_t t = x.t0 + o0 + (uint32_t)k * kRangeThreads;
+                        if (old[k] == 0u) rec[ri[k]] = (t + 1u) | (w << 31);
+                        else if (const uint32_t need = owner_need(old[k], t, w)) rec[ri[k]] = old[k] | need;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const uint32_t t = x.t0 + o0 + (uint32_t)k * kRangeThreads;
+                        old[k] = ri[k] >= 0 ? atomicCAS(rec + ri[k], 0u, (t + 1u) | (w << 31)) : 0u;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        if (ri[k] < 0 || old[k] == 0u) continue;
+                        const uint32_t t = x.t0 + o0 + (uint32_t)k * kRangeThreads;
+                        if (const uint32_t need = owner_need(old[k], t, w)) atomicOr(rec + ri[k], need);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) sh.n = 0;
+        return;
+    }
+    // short intervals: positions of the round spread over the block; this
+    // thread's current interval kept in registers (entry e covers positions
+    // [base, nxt) of the round)
+    uint32_t e = 0, base = 0, nxt = 0;
+    REnt x{};
+    if (total) { x = sh.ent[0]; nxt = n > 1 ? sh.pre[1] : total; }
     for (uint32_t q0 = threadIdx.x; q0 < total; q0 += 4u * kRangeThreads) {
         uint32_t *rp[4];
         uint32_t tq[4], wq[4], old[4];
@@ -1278,9 +1333,13 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
             const uint32_t q = q0 + (uint32_t)k * kRangeThreads;
             rp[k] = nullptr;
             if (q < total) {
-                while (e + 1 < n && sh.pre[e + 1] <= q) e++;
-                const REnt x = sh.ent[e];
-                const uint32_t o = q - sh.pre[e];
+                while (q >= nxt) {                    // positions only grow
+                    e++;
+                    base = nxt;
+                    x = sh.ent[e];
+                    nxt = e + 1 < n ? sh.pre[e + 1] : total;
+                }
+                const uint32_t o = q - base;
                 tq[k] = x.t0 + o;
                 wq[k] = (x.lenf & kRWrite) ? 1u : 0u;
                 rp[k] = rec + (x.l0 + ((x.lenf & kRDown) ? -(int32_t)o : (int32_t)o));
@@ -1309,15 +1368,31 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
     if (threadIdx.x == 0) sh.n = 0;
 }
 
-__global__ void __launch_bounds__(kRangeThreads) k_range(BatchArgs a)
+__global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(BatchArgs a)
 {
     pdl_begin();
     extern __shared__ uint4 r_dyn[];
     uint32_t *const rec = reinterpret_cast<uint32_t *>(r_dyn);
+    uint4 *const r4 = r_dyn;
     __shared__ RangeShared sh;
     if (threadIdx.x == 0) { sh.n = 0; sh.updates = 0; }
+    // the shared records are zero at the start of every task: cleared here
+    // once, then by the pass that ends each task
+    for (uint32_t i = threadIdx.x; i < kRangeRecs / 4; i += kRangeThreads) r4[i] = make_uint4(0u, 0u, 0u, 0u);
     uint32_t *const tab = reinterpret_cast<uint32_t *>(a.table);
-    for (uint32_t li = blockIdx.x; li < a.nlive; li += gridDim.x) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // tasks come from a launch-wide counter in rorder's order (most work
+    // first), each block fetching its next task while it works on this one
+    __shared__ uint32_t s_task[2];
+    if (threadIdx.x == 0) s_task[0] = atomicAdd(&a.ctrl->range_next, 1u);
+    __syncthreads();
+    for (uint32_t it = 0;; it++) {
+        const uint32_t oi = s_task[it & 1u];
+        if (oi >= a.nlive) break;
+        // (the slot read next is written here and read after the task's
+        // barriers; the slot just read is rewritten only in the next task)
+        if (threadIdx.x == 0) s_task[(it + 1u) & 1u] = atomicAdd(&a.ctrl->range_next, 1u);
+        const uint32_t li = __ldg(a.rorder + oi);
         const unsigned long long r0 = (unsigned long long)__ldg(a.rlive + li) * kRangeRecs;
         const unsigned long long r1 = r0 + kRangeRecs < a.tab_cells ? r0 + kRangeRecs : a.tab_cells;
         // the window this launch may record (a shard), within the task
@@ -1325,11 +1400,10 @@ __global__ void __launch_bounds__(kRangeThreads) k_range(BatchArgs a)
         const unsigned long long w1 = r1 < a.shard_hi ? r1 : a.shard_hi;
         const uint32_t nrec = (uint32_t)(r1 - r0);
         __syncthreads();                                  // the previous task is done with rec and sh
-        uint4 *r4 = reinterpret_cast<uint4 *>(rec);
-        for (uint32_t i = threadIdx.x; i < kRangeRecs / 4; i += kRangeThreads) r4[i] = make_uint4(0u, 0u, 0u, 0u);
-        // the blocks the table pass touched in the task: merged into the
-        // shared copy and cleared in the table (through L2: this SM's L1 may
-        // hold lines the table pass read), their touch words cleared
+        // the blocks of 256 records the table pass touched in the task:
+        // merged into the shared copy and cleared in the table (through L2:
+        // this SM's L1 may hold lines the table pass read), one warp per
+        // block, their touch words cleared
         const uint32_t nwords = (nrec + 8191u) >> 13;
         uint32_t tb = 0;
         if (threadIdx.x < nwords) {
@@ -1338,11 +1412,20 @@ __global__ void __launch_bounds__(kRangeThreads) k_range(BatchArgs a)
             if (tb) a.touch[(r0 >> 13) + threadIdx.x] = 0u;
         }
         if (__syncthreads_or(tb != 0u)) {
-            for (uint32_t i = threadIdx.x; i < nrec; i += kRangeThreads) {
-                const uint32_t blk = i >> 8;
-                if ((sh.bits[blk >> 5] >> (blk & 31u)) & 1u) {
-                    const uint32_t v = __ldcg(tab + r0 + i);
-                    if (v) { rec[i] = v; tab[r0 + i] = 0u; }
+            const uint32_t nblk = (nrec + 255u) >> 8;
+            for (uint32_t b = warp; b < nblk; b += kRangeThreads / 32) {
+                if (!((sh.bits[b >> 5] >> (b & 31u)) & 1u)) continue;
+                for (uint32_t i = b * 256u + lane * 4u; i < b * 256u + 256u && i < nrec; i += 128u) {
+                    if (i + 4u <= nrec) {                 // 16-byte aligned: r0 and i are multiples of 4
+                        uint4 *g = reinterpret_cast<uint4 *>(tab + r0 + i);
+                        const uint4 v = __ldcg(g);
+                        if (v.x | v.y | v.z | v.w) { r4[i >> 2] = v; *g = make_uint4(0u, 0u, 0u, 0u); }
+                    } else {
+                        for (uint32_t j = i; j < nrec; j++) {
+                            const uint32_t v = __ldcg(tab + r0 + j);
+                            if (v) { rec[j] = v; tab[r0 + j] = 0u; }
+                        }
+                    }
                 }
             }
             __syncthreads();
@@ -1357,30 +1440,81 @@ __global__ void __launch_bounds__(kRangeThreads) k_range(BatchArgs a)
             __syncthreads();
             range_apply(rec, sh);
         }
+        // one pass over the task's records: the racy ones into a bitmap
+        // (sh.pre, free after the last round), every record cleared for the
+        // next task
+        uint32_t *const racy = sh.pre;
+        for (uint32_t i = threadIdx.x; i < kRangeRecs / 32; i += kRangeThreads) racy[i] = 0u;
+        __syncthreads();
+        bool found = false;
+        for (uint32_t q = threadIdx.x; q < kRangeRecs / 4; q += kRangeThreads) {
+            const uint4 v = r4[q];
+            if (v.x | v.y | v.z | v.w) {
+                r4[q] = make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t m = (owner_racy(v.x) ? 1u : 0u) | (owner_racy(v.y) ? 2u : 0u) |
+                                   (owner_racy(v.z) ? 4u : 0u) | (owner_racy(v.w) ? 8u : 0u);
+                if (m) { atomicOr(&racy[q >> 3], m << ((q & 7u) * 4u)); found = true; }
+            }
+        }
         // the first racy record of each protocol whose rows meet the task
         // (rows are phase-major, then array, then index: the lexicographic
-        // order of the witness)
-        uint32_t p = proto_of_record(a, r0);
-        while (true) {
-            const DevProto P = a.protos[p];
-            const unsigned long long pe = P.tab_off + (unsigned long long)P.tab_phases * P.cells_sum;
-            const unsigned long long s0 = P.tab_off > r0 ? P.tab_off : r0, s1 = pe < r1 ? pe : r1;
-            if (s0 < s1) {
-                uint32_t best = 0xFFFFFFFFu;
-                for (uint32_t i = (uint32_t)(s0 - r0) + threadIdx.x; i < (uint32_t)(s1 - r0); i += kRangeThreads)
-                    if (owner_racy(rec[i])) { best = i; break; }
-                if (threadIdx.x == 0) sh.best = ~0ull;
-                __syncthreads();
-                if (best != 0xFFFFFFFFu) atomicMin(&sh.best, r0 + best);
-                __syncthreads();
-                if (threadIdx.x == 0 && sh.best != ~0ull) atomicMin(&a.best_pos[p], sh.best);
+        // order of the witness), by the first warp
+        if (__syncthreads_or(found) && warp == 0) {
+            uint32_t p = proto_of_record(a, r0);
+            while (true) {
+                const DevProto P = a.protos[p];
+                const unsigned long long pe = P.tab_off + (unsigned long long)P.tab_phases * P.cells_sum;
+                const unsigned long long s0 = P.tab_off > r0 ? P.tab_off : r0, s1 = pe < r1 ? pe : r1;
+                if (s0 < s1) {
+                    const uint32_t lo = (uint32_t)(s0 - r0), hi = (uint32_t)(s1 - r0);
+                    for (uint32_t wb = (lo >> 5); wb <= ((hi - 1) >> 5); wb += 32) {
+                        const uint32_t wd = wb + lane;
+                        uint32_t bits = wd <= ((hi - 1) >> 5) ? racy[wd] : 0u;
+                        if (wd == (lo >> 5)) bits &= ~0u << (lo & 31u);
+                        if (wd == ((hi - 1) >> 5) && (hi & 31u)) bits &= (1u << (hi & 31u)) - 1u;
+                        const unsigned any = __ballot_sync(kFull, bits != 0u);
+                        if (any) {
+                            const uint32_t src = (uint32_t)__ffs(any) - 1u;
+                            const uint32_t first = __shfl_sync(kFull, bits, src);
+                            if (lane == 0)
+                                atomicMin(&a.best_pos[p], r0 + (wb + src) * 32u + (uint32_t)(__ffs(first) - 1));
+                            break;
+                        }
+                    }
+                }
+                if (p + 1 >= a.nprotos || __ldg(&a.protos[p + 1].tab_off) >= r1) break;
+                p++;
             }
-            if (p + 1 >= a.nprotos || __ldg(&a.protos[p + 1].tab_off) >= r1) break;
-            p++;
         }
     }
     __syncthreads();
     if (threadIdx.x == 0 && sh.updates) atomicAdd(&a.ctrl->range_tuples, sh.updates);
+}
+
+// The threads whose access (range access A at offset c) lands on table
+// record `rec`: the index sigma * tid + c, taken mod n when A has a modulus
+// (c then in [0, n), and T <= n, so a record has at most two such threads).
+__device__ __forceinline__ int range_hits(const RAcc &A, long long c, unsigned long long rec, uint32_t h[2])
+{
+    if (rec < A.sb || rec >= A.sb + A.ncells) return 0;
+    const long long x = (long long)(rec - A.sb), T = (long long)A.T;
+    long long cand[2] = {-1, -1};
+    if (A.modn == 0) {
+        cand[0] = A.sigma == 1 ? x - c : c - x;
+    } else {
+        const long long N = (long long)A.modn;
+        if (A.sigma == 1) {
+            if (x >= c) cand[0] = x - c;               // no wrap: tid + c < N
+            else cand[1] = x - c + N;                  // wrapped once
+        } else {
+            if (x <= c) cand[0] = c - x;               // no wrap: c - tid >= 0
+            else cand[1] = c + N - x;                  // wrapped once
+        }
+    }
+    int n = 0;
+    for (int q = 0; q < 2; q++)
+        if (cand[q] >= 0 && cand[q] < T) h[n++] = (uint32_t)cand[q];
+    return n;
 }
 
 __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t x)
@@ -1441,6 +1575,29 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
                 for (int q = 0; q < 2 && mw; q++) {
                     two_smallest(w0, w1, (uint32_t)(lo + (uint32_t)(__ffs(mw) - 1) - b0));
                     mw &= mw - 1;
+                }
+            }
+            if (a.range_on) {
+                // the accesses the range pass applied are not in the hit bits
+                // (the interpreted witness pass skips them): the threads whose
+                // offsets land on the racy record, from its task's work list
+                const unsigned long long task = bp / kRangeRecs;
+                uint32_t lo = 0, hi = a.nlive;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) / 2;
+                    if (__ldg(a.rlive + mid) < task) lo = mid + 1; else hi = mid;
+                }
+                if (lo < a.nlive && __ldg(a.rlive + lo) == task) {
+                    const uint32_t e1 = __ldg(a.rfirst + lo + 1);
+                    for (uint32_t e = __ldg(a.rfirst + lo) + t; e < e1; e += kFinalizeThreads) {
+                        const RAcc A = a.racc[__ldg(a.rk + e)];
+                        uint32_t h[2];
+                        const int nh = range_hits(A, __ldg(a.rc + e), bp, h);
+                        for (int q = 0; q < nh; q++) {
+                            two_smallest(t0, t1, h[q]);
+                            if (A.w) two_smallest(w0, w1, h[q]);
+                        }
+                    }
                 }
             }
         } else {

@@ -153,7 +153,7 @@ struct Control {
     unsigned int flags;                // CF_* internal failures
     unsigned long long touched;        // owner-table blocks listed this launch
     unsigned int blocks_done;          // blocks of the witness pass that have finished
-    unsigned int pad;
+    unsigned int range_next;           // range pass: tasks handed out so far
     unsigned long long range_tuples;   // access tuples the range pass applied
 };
 

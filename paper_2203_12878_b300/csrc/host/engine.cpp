@@ -167,6 +167,7 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
     out.rc.clear();
     out.rlive.clear();
     out.rfirst.clear();
+    out.rorder.clear();
     out.range_pcs.assign(ps.size(), {});
     out.range_tuples = 0;
     // a batch whose range accesses make few tuples runs faster without the
@@ -175,7 +176,7 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
     for (size_t i = 0; i < ps.size(); i++)
         if (range_candidate(*ps[i], out.protos[i], rt)) all += rt;
     if (all == 0 || all < range_min) return;
-    struct E { uint32_t task, k; int64_t c; };
+    struct E { uint32_t task, k; int64_t c; uint32_t len; };     // len: records of the task it updates
     std::vector<E> ent;
     std::vector<std::pair<int64_t, int64_t>> img;
     for (size_t i = 0; i < ps.size(); i++) {
@@ -191,9 +192,13 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
             const uint32_t k = (uint32_t)out.racc.size();
             for (int64_t c : r.offsets) {
                 range_image(r, c, ncells, p.nthreads, img);
-                for (const auto &iv : img)
-                    for (uint64_t t = (sb + (uint64_t)iv.first) / kRangeRecs; t <= (sb + (uint64_t)iv.second - 1) / kRangeRecs; t++)
-                        ent.push_back(E{(uint32_t)t, k, c});
+                for (const auto &iv : img) {
+                    const uint64_t g0 = sb + (uint64_t)iv.first, g1 = sb + (uint64_t)iv.second;
+                    for (uint64_t t = g0 / kRangeRecs; t <= (g1 - 1) / kRangeRecs; t++) {
+                        const uint64_t lo = std::max(g0, t * kRangeRecs), hi = std::min(g1, (t + 1) * kRangeRecs);
+                        ent.push_back(E{(uint32_t)t, k, c, (uint32_t)(hi - lo)});
+                    }
+                }
             }
             out.racc.push_back(RAcc{sb, ncells, r.modn, r.sigma, r.write ? 1u : 0u, p.nthreads, 0u});
             out.range_pcs[i].push_back(r.pc);
@@ -213,15 +218,24 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
     });
     out.rk.reserve(ent.size());
     out.rc.reserve(ent.size());
+    std::vector<uint64_t> work;                      // record updates per task
     for (size_t i = 0; i < ent.size(); i++) {
         if (i == 0 || ent[i].task != ent[i - 1].task) {
             out.rlive.push_back(ent[i].task);
             out.rfirst.push_back((uint32_t)i);
+            work.push_back(0);
         }
         out.rk.push_back(ent[i].k);
         out.rc.push_back(ent[i].c);
+        work.back() += ent[i].len;
     }
     if (!out.rlive.empty()) out.rfirst.push_back((uint32_t)ent.size());
+    // blocks take tasks from a shared counter, the largest first, so that
+    // the launch does not end on a few blocks still working through big ones
+    out.rorder.resize(out.rlive.size());
+    for (uint32_t i = 0; i < (uint32_t)out.rorder.size(); i++) out.rorder[i] = i;
+    std::stable_sort(out.rorder.begin(), out.rorder.end(),
+                     [&work](uint32_t x, uint32_t y) { return work[x] > work[y]; });
     if (out.range_tuples < range_min) {              // protocols left out: under the minimum after all
         for (size_t i = 0; i < ps.size(); i++)
             for (uint32_t pc : out.range_pcs[i]) out.insns[out.protos[i].insn_off + pc].a &= (uint8_t)~AF_RANGE;
@@ -230,6 +244,7 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
         out.rc.clear();
         out.rlive.clear();
         out.rfirst.clear();
+        out.rorder.clear();
         out.range_pcs.assign(ps.size(), {});
         out.range_tuples = 0;
     }
@@ -284,7 +299,8 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     const Section sec[] = {section(b.insns, end), section(b.xcode, end), section(b.items, end),
                            section(b.protos, end), section(b.cells, end), section(b.cbase, end),
                            section(b.witems, end), section(b.iphase, end), section(b.racc, end),
-                           section(b.rk, end), section(b.rc, end), section(b.rlive, end), section(b.rfirst, end)};
+                           section(b.rk, end), section(b.rc, end), section(b.rlive, end), section(b.rfirst, end),
+                           section(b.rorder, end)};
     const size_t total = std::max<size_t>(end, 256);
     bool ok = ensure(image, total, &in_use, limit);
     // the previous copy out of the stage must be done before it is rewritten
@@ -353,6 +369,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.rc = (const long long *)(img + sec[10].off);
     a.rlive = (const uint32_t *)(img + sec[11].off);
     a.rfirst = (const uint32_t *)(img + sec[12].off);
+    a.rorder = (const uint32_t *)(img + sec[13].off);
     a.nlive = (uint32_t)b.rlive.size();
     a.range_on = 0;
     a.nwitems = (uint32_t)nw;

@@ -59,13 +59,14 @@ struct BatchHost {
     // the range pass's work (BatchArgs::racc ..): its accesses, and per task
     // of kRangeRecs owner records that they reach (rlive, ascending) the
     // entries [rfirst[i], rfirst[i + 1]) of (access rk, offset rc); their
-    // instructions carry AF_RANGE in `insns`.  range_pcs: per protocol, the
+    // instructions carry AF_RANGE in `insns`; rorder, the task indices by
+    // decreasing record updates (the order blocks take them in).  range_pcs: per protocol, the
     // pcs (in its own program) of its range accesses; range_tuples: the
     // access tuples they make.
     std::vector<RAcc> racc;
     std::vector<uint32_t> rk;
     std::vector<int64_t> rc;
-    std::vector<uint32_t> rlive, rfirst;
+    std::vector<uint32_t> rlive, rfirst, rorder;
     std::vector<std::vector<uint32_t>> range_pcs;
     uint64_t range_tuples = 0;
     uint64_t table_bytes() const { return table_cells * 4; }   // one 32-bit owner record per cell

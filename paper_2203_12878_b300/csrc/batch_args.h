@@ -29,21 +29,51 @@ enum : uint32_t {
     TR_SINGLE = 4,        // the tile lies inside one segment that crosses both edges
 };
 
-// One range access of a batch (the range pass): the first owner record of
-// its (phase, array) segment, its array's size, the remainder's modulus (0:
-// none), the sign of tid in its index, whether it writes, and its
-// protocol's thread count.
-struct RAcc {
-    unsigned long long sb, ncells, modn;
-    int sigma;
-    unsigned int w, T, pad;
+// One piece of the range pass's work: the threads t0 .. t0 + len - 1 of
+// one range access at one offset, whose records (relative to the first
+// record of their task) are l0, l0 + 1, ... -- or l0, l0 - 1, ... with
+// kRDown -- and whether they write (kRWrite); lenf holds len and the flags.
+struct RPiece {
+    uint32_t t0, lenf;
+    int32_t l0;
+    uint32_t pad;
 };
+constexpr uint32_t kRDown = 1u << 31, kRWrite = 1u << 30, kRLen = (1u << 30) - 1;
+
+// A task of the range pass: its index (its records start at task *
+// kRangeRecs) and its pieces [p0, p1).
+struct RTask {
+    uint32_t task, p0, p1, pad;
+};
+
+#if defined(__CUDACC__)
+#define DRF_HD __host__ __device__
+#else
+#define DRF_HD
+#endif
+
+// The part of a piece (threads t0 + o, o < len, at records l0 + o, or
+// l0 - o when `down`) whose records lie in [w0, w1): its first thread, first
+// record and length (0 when none).
+DRF_HD inline void range_clip(long long t0, long long l0, long long len, bool down, long long w0, long long w1,
+                              long long &ct0, long long &cl0, long long &clen)
+{
+    long long olo, ohi;
+    if (!down) { olo = w0 - l0; ohi = w1 - l0; }
+    else { olo = l0 - w1 + 1; ohi = l0 - w0 + 1; }
+    if (olo < 0) olo = 0;
+    if (ohi > len) ohi = len;
+    if (olo >= ohi) { ct0 = t0; cl0 = l0; clen = 0; return; }
+    ct0 = t0 + olo;
+    cl0 = down ? l0 - olo : l0 + olo;
+    clen = ohi - olo;
+}
 
 // Owner records per task of the range pass: a multiple of the 8,192 records
 // one touch word covers, so that every task owns its touch words.
 constexpr uint32_t kRangeRecs = 16384;
 constexpr uint32_t kRangeThreads = 512;
-constexpr uint32_t kRangeChunk = 256;                       // entries turned into intervals per round
+constexpr uint32_t kRangeChunk = 512;                       // pieces applied per round
 constexpr uint32_t kRangeSmem = kRangeRecs * 4;             // dynamic shared memory of a range block
 constexpr uint32_t kRangeBlocksPerSm = 3;
 
@@ -105,15 +135,14 @@ struct BatchArgs {
     // [0, ~0) otherwise.
     unsigned long long shard_lo, shard_hi;
     // The range pass (owner-table launches): tasks of kRangeRecs records
-    // that range accesses reach (rlive, ascending), each with its entries
-    // [rfirst[i], rfirst[i + 1]) of (access rk, offset rc); the table pass
+    // that range accesses reach (rlive, ascending), each with its pieces
+    // [rfirst[i], rfirst[i + 1]) of rpiece; rtask, the same tasks in the
+    // order blocks take them (most record updates first).  The table pass
     // leaves accesses marked AF_RANGE alone when range_on is set.
-    const RAcc *racc;
-    const uint32_t *rk;
-    const long long *rc;
+    const RPiece *rpiece;
+    const RTask *rtask;
     const uint32_t *rlive;
     const uint32_t *rfirst;
-    const uint32_t *rorder;         // the order blocks take tasks in (indices into rlive): most work first
     uint32_t nlive;
     uint32_t range_on;
     void *table;                     // [tab_cells] 32-bit owner records, padded to whole blocks

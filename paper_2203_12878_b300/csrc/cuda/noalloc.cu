@@ -141,12 +141,10 @@ extern "C" int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_
     a.count_free = 0;
     a.shard_lo = 0;
     a.shard_hi = ~0ull;
-    a.racc = nullptr;                     // the sort path: no range pass
-    a.rk = nullptr;
-    a.rc = nullptr;
+    a.rpiece = nullptr;                   // the sort path: no range pass
+    a.rtask = nullptr;
     a.rlive = nullptr;
     a.rfirst = nullptr;
-    a.rorder = nullptr;
     a.nlive = 0;
     a.range_on = 0;
     a.nwitems = (uint32_t)nw;

@@ -34,8 +34,20 @@ __device__ __forceinline__ uint32_t owner_need(uint32_t cur, uint32_t tid, uint3
     return need;
 }
 
+// The record after one access by the thread whose tid + 1 is `t1`
+// (`wbit`: kOwnerWritten when it writes, else 0), for a record no other
+// thread updates meanwhile (a plain read and write): an empty record takes
+// the thread as first accessor, a non-empty one gains the bits the access
+// implies.  Branch-free; the result equals `cur` when nothing changes.
+__device__ __forceinline__ uint32_t owner_merge(uint32_t cur, uint32_t t1, uint32_t wbit)
+{
+    const uint32_t multi = (cur & kOwnerRep) != t1 ? kOwnerMulti : 0u;
+    return cur == 0u ? (t1 | wbit) : (cur | wbit | multi);
+}
+
 // One access by thread `tid` (w: it writes).  `cur` is a copy of the record
-// read through L1 (it may be stale; the record itself only gains bits).  An
+// read earlier in this launch (it may be out of date; the record itself only
+// gains bits, so an old copy costs at most a redundant update).  An
 // empty copy claims the record (first accessor) by compare-and-swap.
 // Returns true when this call turned the record from zero into non-zero.
 __device__ __forceinline__ bool owner_put(uint32_t *cell, uint32_t cur, uint32_t tid, uint32_t w)

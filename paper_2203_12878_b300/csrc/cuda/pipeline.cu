@@ -208,8 +208,10 @@ enum : int {
 // Applies each valid lane's access to its owner record (owner.cuh); the
 // update that creates a record marks its block as touched.  When every valid
 // lane hits one cell (an index that does not depend on tid), one lane
-// updates the record for the warp.  The record is read through L1 first; the
-// update is skipped when the copy already implies it.
+// updates the record for the warp.  The record is read first (through L2,
+// where every SM sees the same record; nothing here relies on what an SM's
+// L1 may still hold from earlier launches); the update is skipped when the
+// copy already implies it.
 __device__ __forceinline__ void table_put(const BatchArgs &a, bool ok, unsigned long long off, uint32_t tid,
                                           uint32_t w)
 {
@@ -222,10 +224,10 @@ __device__ __forceinline__ void table_put(const BatchArgs &a, bool ok, unsigned 
     if (__all_sync(kFull, !ok || off == off0)) {
         const unsigned wm = __ballot_sync(kFull, ok && w);
         if ((int)(threadIdx.x & 31) == lead)
-            created = __popc(m) >= 2 ? owner_put_many(cell, __ldca(cell), wm != 0)
-                                     : owner_put(cell, __ldca(cell), tid, w);
+            created = __popc(m) >= 2 ? owner_put_many(cell, __ldcg(cell), wm != 0)
+                                     : owner_put(cell, __ldcg(cell), tid, w);
     } else if (ok) {
-        created = owner_put(cell, __ldca(cell), tid, w);
+        created = owner_put(cell, __ldcg(cell), tid, w);
     }
     if (created) owner_touch(a.touch, off, kTabBlockLog);
 }
@@ -539,17 +541,11 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
 // has completed and its writes are visible.  Under a plain launch both are
 // no-ops.
 //
-// Then a device-scope acquire fence.  Without it a kernel that follows init
-// directly (no count or scan pass in between) was seen reading, through its
-// SM's L1, owner-record lines that an earlier launch's table pass had
-// loaded before the scan cleared them: a stale non-zero copy made the
-// update skip its claim and OR bits into an empty record (no touch mark, so
-// the record also outlived the launch) -- a false race, in the server test
-// after the suite's earlier work, in three of four runs.  The fence orders
-// every later load of the thread after all writes that happened before the
-// wait returned; with it (and, separately, with record reads through L2)
-// the same runs found no such case.  Every load after it that goes through
-// L1 therefore returns data of this launch or later.
+// Then a device-scope acquire fence, so that no later load of the thread is
+// ordered before the writes the wait made visible.  It is a defence only:
+// the kernels read data that earlier kernels of a launch write through L2
+// (ld.global.cg), owner records included, and do not depend on what an SM's
+// L1 may still hold.
 __device__ __forceinline__ void pdl_begin()
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -1168,67 +1164,16 @@ __global__ void __launch_bounds__(kTabScanThreads) k_tscan(BatchArgs a)
 // task's first racy record per protocol.  The table scan that follows reads
 // the table pass's records elsewhere.
 
-// tids [t0, t0 + len) of one offset of one access, the record (in the
-// task's shared copy) tid t0 updates -- the others follow at +1, or -1 with
-// bit 31 of lenf set -- and whether they write (bit 30 of lenf)
-struct REnt {
-    uint32_t t0, lenf;
-    int32_t l0;
-};
-constexpr uint32_t kRDown = 1u << 31, kRWrite = 1u << 30, kRLen = (1u << 30) - 1;
-
 struct RangeShared {
-    REnt ent[2 * kRangeChunk];
-    uint32_t pre[2 * kRangeChunk];                // also the task's racy-record bitmap at its end
+    RPiece ent[kRangeChunk];                      // the round's pieces
+    uint32_t pre[kRangeChunk];                    // also the task's racy-record bitmap at its end
     uint32_t n, tot, plain, bits[kRangeRecs / 8192];
     unsigned long long updates;                   // record updates the block made
 };
-static_assert(2 * kRangeChunk * 32 >= kRangeRecs, "the racy bitmap needs a bit per record");
+static_assert(kRangeChunk * 32 >= kRangeRecs, "the racy bitmap needs a bit per record");
 
 
-// The one or two tid intervals of access A at offset c (reduced mod the
-// modulus when there is one) whose records lie in [w0, w1), within the task
-// starting at record r0.
-__device__ __forceinline__ void range_pieces(const RAcc &A, long long c, unsigned long long r0, unsigned long long w0,
-                                             unsigned long long w1, RangeShared &sh)
-{
-    const unsigned long long sb = A.sb, se = A.sb + A.ncells;
-    if (!(sb < w1 && se > w0)) return;
-    const long long T = (long long)A.T;
-    const long long lo_c = (long long)((w0 > sb ? w0 : sb) - sb);
-    const long long hi_c = (long long)((w1 < se ? w1 : se) - sb);
-    const long long loc0 = (long long)sb - (long long)r0;
-    long long ta = 0, na = 0, la = 0, tb = 0, nb = 0, lb = 0, te;
-    if (A.modn == 0 && A.sigma == 1) {
-        ta = lo_c - c; if (ta < 0) ta = 0; te = hi_c - c; if (te > T) te = T;
-        na = te - ta; la = ta + c + loc0;
-    } else if (A.modn == 0) {
-        ta = c - hi_c + 1; if (ta < 0) ta = 0; te = c - lo_c + 1; if (te > T) te = T;
-        na = te - ta; la = c - ta + loc0;
-    } else {
-        const long long N = (long long)A.modn, cm = c;
-        if (A.sigma == 1) {                         // tids below N - cm do not wrap around N
-            ta = lo_c - cm; if (ta < 0) ta = 0; te = hi_c - cm;
-            { const long long lim = N - cm < T ? N - cm : T; if (te > lim) te = lim; }
-            na = te - ta; la = ta + cm + loc0;
-            tb = lo_c - cm + N; if (tb < N - cm) tb = N - cm;
-            te = hi_c - cm + N; if (te > T) te = T;
-            nb = te - tb; lb = tb + cm - N + loc0;
-        } else {                                    // tids up to cm do not wrap below 0
-            ta = cm - hi_c + 1; if (ta < 0) ta = 0; te = cm - lo_c + 1;
-            { const long long lim = cm + 1 < T ? cm + 1 : T; if (te > lim) te = lim; }
-            na = te - ta; la = cm - ta + loc0;
-            tb = cm + N - hi_c + 1; if (tb < cm + 1) tb = cm + 1;
-            te = cm + N - lo_c + 1; if (te > T) te = T;
-            nb = te - tb; lb = cm + N - tb + loc0;
-        }
-    }
-    const uint32_t f = (A.sigma < 0 ? kRDown : 0u) | (A.w ? kRWrite : 0u);
-    if (na > 0) { const uint32_t e = atomicAdd(&sh.n, 1u); sh.ent[e] = REnt{(uint32_t)ta, (uint32_t)na | f, (int32_t)la}; }
-    if (nb > 0) { const uint32_t e = atomicAdd(&sh.n, 1u); sh.ent[e] = REnt{(uint32_t)tb, (uint32_t)nb | f, (int32_t)lb}; }
-}
-
-__device__ __forceinline__ void range_span(const REnt &x, int32_t &lo, int32_t &hi)
+__device__ __forceinline__ void range_span(const RPiece &x, int32_t &lo, int32_t &hi)
 {
     const int32_t len = (int32_t)(x.lenf & kRLen);
     if (x.lenf & kRDown) { lo = x.l0 - len + 1; hi = x.l0 + 1; }
@@ -1279,10 +1224,32 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
         // long intervals: the block takes them one by one, a record per
         // thread (no position search)
         for (uint32_t e = 0; e < n; e++) {
-            const REnt x = sh.ent[e];
+            const RPiece x = sh.ent[e];
             const uint32_t len = x.lenf & kRLen, w = (x.lenf & kRWrite) ? 1u : 0u;
             const int32_t step = (x.lenf & kRDown) ? -1 : 1;
-            for (uint32_t o0 = threadIdx.x; o0 < len; o0 += 4u * kRangeThreads) {
+            uint32_t o0 = threadIdx.x;
+            if (plain) {
+                // four records per thread and step, every one in the interval
+                const uint32_t wbit = w << 31;
+                const int32_t d = step * (int32_t)kRangeThreads;
+                for (; o0 + 3u * kRangeThreads < len; o0 += 4u * kRangeThreads) {
+                    const int32_t i0 = x.l0 + step * (int32_t)o0;
+                    const uint32_t t1 = x.t0 + o0 + 1u;
+                    uint32_t old[4];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) old[k] = rec[i0 + k * d];
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        rec[i0 + k * d] = owner_merge(old[k], t1 + (uint32_t)k * kRangeThreads, wbit);
+                }
+                for (; o0 < len; o0 += kRangeThreads) {
+                    const int32_t i = x.l0 + step * (int32_t)o0;
+                    rec[i] = owner_merge(rec[i], x.t0 + o0 + 1u, wbit);
+                }
+                continue;
+            }
+            // intervals that share records: claims by compare-and-swap
+            for (; o0 < len; o0 += 4u * kRangeThreads) {
                 int32_t ri[4];
                 uint32_t old[4];
 #pragma unroll
@@ -1290,28 +1257,16 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
                     const uint32_t o = o0 + (uint32_t)k * kRangeThreads;
                     ri[k] = o < len ? x.l0 + step * (int32_t)o : -1;
                 }
-                if (plain) {
 #pragma unroll
-                    for (int k = 0; k < 4; k++) old[k] = ri[k] >= 0 ? rec[ri[k]] : 0u;
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t t = x.t0 + o0 + (uint32_t)k * kRangeThreads;
+                    old[k] = ri[k] >= 0 ? atomicCAS(rec + ri[k], 0u, (t + 1u) | (w << 31)) : 0u;
+                }
 #pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        if (ri[k] < 0) continue;
-                        const uint32_t t = x.t0 + o0 + (uint32_t)k * kRangeThreads;
-                        if (old[k] == 0u) rec[ri[k]] = (t + 1u) | (w << 31);
-                        else if (const uint32_t need = owner_need(old[k], t, w)) rec[ri[k]] = old[k] | need;
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        const uint32_t t = x.t0 + o0 + (uint32_t)k * kRangeThreads;
-                        old[k] = ri[k] >= 0 ? atomicCAS(rec + ri[k], 0u, (t + 1u) | (w << 31)) : 0u;
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        if (ri[k] < 0 || old[k] == 0u) continue;
-                        const uint32_t t = x.t0 + o0 + (uint32_t)k * kRangeThreads;
-                        if (const uint32_t need = owner_need(old[k], t, w)) atomicOr(rec + ri[k], need);
-                    }
+                for (int k = 0; k < 4; k++) {
+                    if (ri[k] < 0 || old[k] == 0u) continue;
+                    const uint32_t t = x.t0 + o0 + (uint32_t)k * kRangeThreads;
+                    if (const uint32_t need = owner_need(old[k], t, w)) atomicOr(rec + ri[k], need);
                 }
             }
         }
@@ -1323,7 +1278,7 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
     // thread's current interval kept in registers (entry e covers positions
     // [base, nxt) of the round)
     uint32_t e = 0, base = 0, nxt = 0;
-    REnt x{};
+    RPiece x{};
     if (total) { x = sh.ent[0]; nxt = n > 1 ? sh.pre[1] : total; }
     for (uint32_t q0 = threadIdx.x; q0 < total; q0 += 4u * kRangeThreads) {
         uint32_t *rp[4];
@@ -1349,11 +1304,8 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
 #pragma unroll
             for (int k = 0; k < 4; k++) old[k] = rp[k] ? *rp[k] : 0u;
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (!rp[k]) continue;
-                if (old[k] == 0u) *rp[k] = (tq[k] + 1u) | (wq[k] << 31);
-                else if (const uint32_t need = owner_need(old[k], tq[k], wq[k])) *rp[k] = old[k] | need;
-            }
+            for (int k = 0; k < 4; k++)
+                if (rp[k]) *rp[k] = owner_merge(old[k], tq[k] + 1u, wq[k] << 31);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; k++) old[k] = rp[k] ? atomicCAS(rp[k], 0u, (tq[k] + 1u) | (wq[k] << 31)) : 0u;
@@ -1381,19 +1333,34 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
     for (uint32_t i = threadIdx.x; i < kRangeRecs / 4; i += kRangeThreads) r4[i] = make_uint4(0u, 0u, 0u, 0u);
     uint32_t *const tab = reinterpret_cast<uint32_t *>(a.table);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // tasks come from a launch-wide counter in rorder's order (most work
-    // first), each block fetching its next task while it works on this one
-    __shared__ uint32_t s_task[2];
-    if (threadIdx.x == 0) s_task[0] = atomicAdd(&a.ctrl->range_next, 1u);
+    // tasks come from a launch-wide counter in rtask's order (most work
+    // first); thread 0 fetches the next task and reads its record while the
+    // block works on this one
+    __shared__ RTask s_task[2];
+    const RTask none{~0u, 0u, 0u, 0u};
+    auto task_at = [&a, &none](uint32_t i) {
+        if (i >= a.nlive) return none;
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.rtask) + i);
+        return RTask{v.x, v.y, v.z, v.w};
+    };
+    uint32_t nx = 0;                                      // thread 0: the index of the task after this one
+    if (threadIdx.x == 0) {
+        s_task[0] = task_at(atomicAdd(&a.ctrl->range_next, 1u));
+        nx = atomicAdd(&a.ctrl->range_next, 1u);
+    }
     __syncthreads();
     for (uint32_t it = 0;; it++) {
-        const uint32_t oi = s_task[it & 1u];
-        if (oi >= a.nlive) break;
-        // (the slot read next is written here and read after the task's
-        // barriers; the slot just read is rewritten only in the next task)
-        if (threadIdx.x == 0) s_task[(it + 1u) & 1u] = atomicAdd(&a.ctrl->range_next, 1u);
-        const uint32_t li = __ldg(a.rorder + oi);
-        const unsigned long long r0 = (unsigned long long)__ldg(a.rlive + li) * kRangeRecs;
+        const RTask tk = s_task[it & 1u];
+        if (tk.task == ~0u) break;
+        // thread 0: the next task's record (stored in the other slot before
+        // this task's last barrier; this slot is rewritten only in the next
+        // task, after every thread has read it)
+        RTask nt = none;
+        if (threadIdx.x == 0) {
+            nt = task_at(nx);
+            if (nx < a.nlive) nx = atomicAdd(&a.ctrl->range_next, 1u);
+        }
+        const unsigned long long r0 = (unsigned long long)tk.task * kRangeRecs;
         const unsigned long long r1 = r0 + kRangeRecs < a.tab_cells ? r0 + kRangeRecs : a.tab_cells;
         // the window this launch may record (a shard), within the task
         const unsigned long long w0 = r0 > a.shard_lo ? r0 : a.shard_lo;
@@ -1430,13 +1397,23 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
             }
             __syncthreads();
         }
-        const uint32_t e1 = __ldg(a.rfirst + li + 1);
-        for (uint32_t e0 = __ldg(a.rfirst + li); e0 < e1 && w0 < w1; e0 += kRangeChunk) {
-            const uint32_t e = e0 + threadIdx.x;
-            if (threadIdx.x < kRangeChunk && e < e1) {
-                const RAcc A = a.racc[__ldg(a.rk + e)];
-                range_pieces(A, __ldg(a.rc + e), r0, w0, w1, sh);
+        // the task's pieces, a round of up to kRangeChunk at a time; a shard
+        // keeps the part of each inside its window
+        const bool whole = w0 == r0 && w1 == r1;
+        for (uint32_t p0 = tk.p0; p0 < tk.p1 && w0 < w1; p0 += kRangeChunk) {
+            const uint32_t np = tk.p1 - p0 < kRangeChunk ? tk.p1 - p0 : kRangeChunk;
+            if (threadIdx.x < np) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.rpiece) + p0 + threadIdx.x);
+                RPiece x{v.x, v.y, (int32_t)v.z, 0u};
+                if (!whole) {
+                    long long ct0, cl0, clen;
+                    range_clip(x.t0, x.l0, x.lenf & kRLen, (x.lenf & kRDown) != 0, (long long)(w0 - r0),
+                               (long long)(w1 - r0), ct0, cl0, clen);
+                    x = RPiece{(uint32_t)ct0, (uint32_t)clen | (x.lenf & ~kRLen), (int32_t)cl0, 0u};
+                }
+                sh.ent[threadIdx.x] = x;
             }
+            if (threadIdx.x == 0) sh.n = np;
             __syncthreads();
             range_apply(rec, sh);
         }
@@ -1456,6 +1433,7 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
                 if (m) { atomicOr(&racy[q >> 3], m << ((q & 7u) * 4u)); found = true; }
             }
         }
+        if (threadIdx.x == 0) s_task[(it + 1u) & 1u] = nt;
         // the first racy record of each protocol whose rows meet the task
         // (rows are phase-major, then array, then index: the lexicographic
         // order of the witness), by the first warp
@@ -1489,32 +1467,6 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
     }
     __syncthreads();
     if (threadIdx.x == 0 && sh.updates) atomicAdd(&a.ctrl->range_tuples, sh.updates);
-}
-
-// The threads whose access (range access A at offset c) lands on table
-// record `rec`: the index sigma * tid + c, taken mod n when A has a modulus
-// (c then in [0, n), and T <= n, so a record has at most two such threads).
-__device__ __forceinline__ int range_hits(const RAcc &A, long long c, unsigned long long rec, uint32_t h[2])
-{
-    if (rec < A.sb || rec >= A.sb + A.ncells) return 0;
-    const long long x = (long long)(rec - A.sb), T = (long long)A.T;
-    long long cand[2] = {-1, -1};
-    if (A.modn == 0) {
-        cand[0] = A.sigma == 1 ? x - c : c - x;
-    } else {
-        const long long N = (long long)A.modn;
-        if (A.sigma == 1) {
-            if (x >= c) cand[0] = x - c;               // no wrap: tid + c < N
-            else cand[1] = x - c + N;                  // wrapped once
-        } else {
-            if (x <= c) cand[0] = c - x;               // no wrap: c - tid >= 0
-            else cand[1] = c + N - x;                  // wrapped once
-        }
-    }
-    int n = 0;
-    for (int q = 0; q < 2; q++)
-        if (cand[q] >= 0 && cand[q] < T) h[n++] = (uint32_t)cand[q];
-    return n;
 }
 
 __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t x)
@@ -1579,8 +1531,8 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
             }
             if (a.range_on) {
                 // the accesses the range pass applied are not in the hit bits
-                // (the interpreted witness pass skips them): the threads whose
-                // offsets land on the racy record, from its task's work list
+                // (the interpreted witness pass skips them): the threads of
+                // the pieces of the racy record's task that land on it
                 const unsigned long long task = bp / kRangeRecs;
                 uint32_t lo = 0, hi = a.nlive;
                 while (lo < hi) {
@@ -1588,15 +1540,15 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
                     if (__ldg(a.rlive + mid) < task) lo = mid + 1; else hi = mid;
                 }
                 if (lo < a.nlive && __ldg(a.rlive + lo) == task) {
+                    const long long x = (long long)(bp - task * kRangeRecs);
                     const uint32_t e1 = __ldg(a.rfirst + lo + 1);
                     for (uint32_t e = __ldg(a.rfirst + lo) + t; e < e1; e += kFinalizeThreads) {
-                        const RAcc A = a.racc[__ldg(a.rk + e)];
-                        uint32_t h[2];
-                        const int nh = range_hits(A, __ldg(a.rc + e), bp, h);
-                        for (int q = 0; q < nh; q++) {
-                            two_smallest(t0, t1, h[q]);
-                            if (A.w) two_smallest(w0, w1, h[q]);
-                        }
+                        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.rpiece) + e);
+                        const long long o = (v.y & kRDown) ? (long long)(int32_t)v.z - x : x - (long long)(int32_t)v.z;
+                        if (o < 0 || o >= (long long)(v.y & kRLen)) continue;
+                        const uint32_t tid = v.x + (uint32_t)o;          // the piece's thread at the record
+                        two_smallest(t0, t1, tid);
+                        if (v.y & kRWrite) two_smallest(w0, w1, tid);
                     }
                 }
             }

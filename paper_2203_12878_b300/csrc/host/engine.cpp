@@ -20,6 +20,7 @@ bool ensure(DevBuf &b, size_t bytes, size_t *in_use, uint64_t limit)
         return false;
     }
     b.cap = want;
+    b.gen++;
     *in_use += want;
     return true;
 }
@@ -29,6 +30,7 @@ void release(DevBuf &b, size_t *in_use)
     if (b.p) {
         cudaFree(b.p);
         *in_use -= b.cap;
+        b.gen++;
     }
     b.p = nullptr;
     b.cap = 0;
@@ -146,7 +148,36 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
     return Error{};
 }
 
+
 namespace {
+
+// The threads of range access r at offset c (reduced mod the modulus when
+// there is one) as at most two runs of consecutive tids whose cells follow
+// each other up or down the array: (first tid, count, first cell, down).
+struct Run { int64_t t0, len, cell0; bool down; };
+
+int range_runs(const RangeAccess &r, int64_t c, uint32_t T, Run out[2])
+{
+    const int64_t t = (int64_t)T;
+    int n = 0;
+    auto add = [&](int64_t a, int64_t b, int64_t cell0, bool down) {
+        if (a < b) out[n++] = Run{a, b - a, cell0, down};
+    };
+    if (!r.modn) {
+        if (r.sigma == 1) add(std::max<int64_t>(0, -c), t, c + std::max<int64_t>(0, -c), false);
+        else add(0, t, c, true);                       // cells below 0 are clipped by the caller
+        return n;
+    }
+    const int64_t N = (int64_t)r.modn;                 // c in [0, N), T <= N: at most one wrap
+    if (r.sigma == 1) {
+        add(0, std::min(t, N - c), c, false);          // tid + c < N
+        add(N - c, t, 0, false);                       // wrapped: tid + c - N
+    } else {
+        add(0, std::min(t, c + 1), c, true);           // c - tid >= 0
+        add(c + 1, t, N - 1, true);                    // wrapped: c - tid + N
+    }
+    return n;
+}
 
 // Whether protocol i of a packed batch takes the range pass: static phases
 // and range accesses that make a quarter of its tuples or more.
@@ -158,66 +189,83 @@ bool range_candidate(const Prepared &p, const DevProto &d, unsigned __int128 &rt
     return rt * 4 >= (unsigned __int128)p.tuple_bound();
 }
 
+void clear_range(BatchHost &out, size_t nprotos)
+{
+    out.rpiece.clear();
+    out.rtask.clear();
+    out.rlive.clear();
+    out.rfirst.clear();
+    out.range_pcs.assign(nprotos, {});
+    out.range_tuples = 0;
+}
+
 }  // namespace
 
 void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_t range_min)
 {
-    out.racc.clear();
-    out.rk.clear();
-    out.rc.clear();
-    out.rlive.clear();
-    out.rfirst.clear();
-    out.rorder.clear();
-    out.range_pcs.assign(ps.size(), {});
-    out.range_tuples = 0;
+    clear_range(out, ps.size());
     // a batch whose range accesses make few tuples runs faster without the
     // pass (its planning, upload and kernel would cost more than it saves)
     unsigned __int128 all = 0, rt = 0;
     for (size_t i = 0; i < ps.size(); i++)
         if (range_candidate(*ps[i], out.protos[i], rt)) all += rt;
     if (all == 0 || all < range_min) return;
-    struct E { uint32_t task, k; int64_t c; uint32_t len; };     // len: records of the task it updates
+    struct E { uint32_t task; RPiece piece; };
     std::vector<E> ent;
-    std::vector<std::pair<int64_t, int64_t>> img;
     for (size_t i = 0; i < ps.size(); i++) {
         const Prepared &p = *ps[i];
         const DevProto &d = out.protos[i];
         if (!range_candidate(p, d, rt)) continue;
-        const size_t k0 = out.racc.size(), e0 = ent.size();
+        const size_t e0 = ent.size();
         uint64_t tuples = 0;
         for (const RangeAccess &r : p.range_access) {
             if (r.phase >= d.tab_phases || r.loc >= d.nlocs || r.offsets.empty() || r.modn >= (1ull << 40)) continue;
-            const uint64_t ncells = p.cells[r.loc];
-            const uint64_t sb = d.tab_off + (uint64_t)r.phase * d.cells_sum + out.cbase[d.cells_off + r.loc];
-            const uint32_t k = (uint32_t)out.racc.size();
+            // (offsets far outside any array would only fail the check: the
+            // table pass keeps such an access)
+            if (std::any_of(r.offsets.begin(), r.offsets.end(),
+                            [](int64_t c) { return c < -(1ll << 50) || c > (1ll << 50); }))
+                continue;
+            const int64_t ncells = (int64_t)p.cells[r.loc];
+            const int64_t sb = (int64_t)(d.tab_off + (uint64_t)r.phase * d.cells_sum + out.cbase[d.cells_off + r.loc]);
+            const uint32_t wf = r.write ? kRWrite : 0u;
             for (int64_t c : r.offsets) {
-                range_image(r, c, ncells, p.nthreads, img);
-                for (const auto &iv : img) {
-                    const uint64_t g0 = sb + (uint64_t)iv.first, g1 = sb + (uint64_t)iv.second;
-                    for (uint64_t t = g0 / kRangeRecs; t <= (g1 - 1) / kRangeRecs; t++) {
-                        const uint64_t lo = std::max(g0, t * kRangeRecs), hi = std::min(g1, (t + 1) * kRangeRecs);
-                        ent.push_back(E{(uint32_t)t, k, c, (uint32_t)(hi - lo)});
+                Run runs[2];
+                const int nr = range_runs(r, c, p.nthreads, runs);
+                for (int q = 0; q < nr; q++) {
+                    // within the array, then cut at task boundaries
+                    long long t0, l0, len;
+                    range_clip(runs[q].t0, sb + runs[q].cell0, runs[q].len, runs[q].down, sb, sb + ncells, t0, l0, len);
+                    while (len > 0) {
+                        const long long task = l0 / (long long)kRangeRecs, base = task * (long long)kRangeRecs;
+                        long long ct0, cl0, clen;
+                        range_clip(t0, l0, len, runs[q].down, base, base + (long long)kRangeRecs, ct0, cl0, clen);
+                        const uint32_t f = (runs[q].down ? kRDown : 0u) | wf;
+                        ent.push_back(E{(uint32_t)task, RPiece{(uint32_t)ct0, (uint32_t)clen | f, (int32_t)(cl0 - base), 0u}});
+                        t0 += clen;
+                        l0 = runs[q].down ? l0 - clen : l0 + clen;
+                        len -= clen;
                     }
                 }
             }
-            out.racc.push_back(RAcc{sb, ncells, r.modn, r.sigma, r.write ? 1u : 0u, p.nthreads, 0u});
             out.range_pcs[i].push_back(r.pc);
             tuples += r.run_iters * (uint64_t)p.nthreads;
         }
         if (ent.size() > kRangeMaxEntries) {           // too many: this protocol keeps the table pass
             ent.resize(e0);
-            out.racc.resize(k0);
             out.range_pcs[i].clear();
             continue;
         }
         for (uint32_t pc : out.range_pcs[i]) out.insns[d.insn_off + pc].a |= AF_RANGE;
         out.range_tuples += tuples;
     }
-    std::sort(ent.begin(), ent.end(), [](const E &x, const E &y) {
-        return x.task != y.task ? x.task < y.task : (x.k != y.k ? x.k < y.k : x.c < y.c);
-    });
-    out.rk.reserve(ent.size());
-    out.rc.reserve(ent.size());
+    if (out.range_tuples < range_min) {              // protocols left out: under the minimum after all
+        for (size_t i = 0; i < ps.size(); i++)
+            for (uint32_t pc : out.range_pcs[i]) out.insns[out.protos[i].insn_off + pc].a &= (uint8_t)~AF_RANGE;
+        clear_range(out, ps.size());
+        return;
+    }
+    std::stable_sort(ent.begin(), ent.end(), [](const E &x, const E &y) { return x.task < y.task; });
+    out.rpiece.reserve(ent.size());
     std::vector<uint64_t> work;                      // record updates per task
     for (size_t i = 0; i < ent.size(); i++) {
         if (i == 0 || ent[i].task != ent[i - 1].task) {
@@ -225,29 +273,17 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
             out.rfirst.push_back((uint32_t)i);
             work.push_back(0);
         }
-        out.rk.push_back(ent[i].k);
-        out.rc.push_back(ent[i].c);
-        work.back() += ent[i].len;
+        out.rpiece.push_back(ent[i].piece);
+        work.back() += ent[i].piece.lenf & kRLen;
     }
     if (!out.rlive.empty()) out.rfirst.push_back((uint32_t)ent.size());
     // blocks take tasks from a shared counter, the largest first, so that
     // the launch does not end on a few blocks still working through big ones
-    out.rorder.resize(out.rlive.size());
-    for (uint32_t i = 0; i < (uint32_t)out.rorder.size(); i++) out.rorder[i] = i;
-    std::stable_sort(out.rorder.begin(), out.rorder.end(),
-                     [&work](uint32_t x, uint32_t y) { return work[x] > work[y]; });
-    if (out.range_tuples < range_min) {              // protocols left out: under the minimum after all
-        for (size_t i = 0; i < ps.size(); i++)
-            for (uint32_t pc : out.range_pcs[i]) out.insns[out.protos[i].insn_off + pc].a &= (uint8_t)~AF_RANGE;
-        out.racc.clear();
-        out.rk.clear();
-        out.rc.clear();
-        out.rlive.clear();
-        out.rfirst.clear();
-        out.rorder.clear();
-        out.range_pcs.assign(ps.size(), {});
-        out.range_tuples = 0;
-    }
+    std::vector<uint32_t> order(out.rlive.size());
+    for (uint32_t i = 0; i < (uint32_t)order.size(); i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&work](uint32_t x, uint32_t y) { return work[x] > work[y]; });
+    out.rtask.reserve(order.size());
+    for (uint32_t i : order) out.rtask.push_back(RTask{out.rlive[i], out.rfirst[i], out.rfirst[i + 1], 0u});
 }
 
 DeviceBatch::~DeviceBatch()
@@ -298,9 +334,8 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     size_t end = 0;
     const Section sec[] = {section(b.insns, end), section(b.xcode, end), section(b.items, end),
                            section(b.protos, end), section(b.cells, end), section(b.cbase, end),
-                           section(b.witems, end), section(b.iphase, end), section(b.racc, end),
-                           section(b.rk, end), section(b.rc, end), section(b.rlive, end), section(b.rfirst, end),
-                           section(b.rorder, end)};
+                           section(b.witems, end), section(b.iphase, end), section(b.rpiece, end),
+                           section(b.rtask, end), section(b.rlive, end), section(b.rfirst, end)};
     const size_t total = std::max<size_t>(end, 256);
     bool ok = ensure(image, total, &in_use, limit);
     // the previous copy out of the stage must be done before it is rewritten
@@ -364,12 +399,10 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.witems = b.expanded() ? (const WarpItem *)(img + sec[6].off) : nullptr;
     a.iphase = (const uint32_t *)(img + sec[7].off);
     a.count_free = 0;
-    a.racc = (const RAcc *)(img + sec[8].off);
-    a.rk = (const uint32_t *)(img + sec[9].off);
-    a.rc = (const long long *)(img + sec[10].off);
-    a.rlive = (const uint32_t *)(img + sec[11].off);
-    a.rfirst = (const uint32_t *)(img + sec[12].off);
-    a.rorder = (const uint32_t *)(img + sec[13].off);
+    a.rpiece = (const RPiece *)(img + sec[8].off);
+    a.rtask = (const RTask *)(img + sec[9].off);
+    a.rlive = (const uint32_t *)(img + sec[10].off);
+    a.rfirst = (const uint32_t *)(img + sec[11].off);
     a.nlive = (uint32_t)b.rlive.size();
     a.range_on = 0;
     a.nwitems = (uint32_t)nw;
@@ -420,19 +453,19 @@ Error DeviceBatch::size_table(const BatchHost &b, uint64_t n, cudaStream_t s)
     const size_t tb = std::max<uint64_t>(recs * 4, 16);
     const size_t wb = std::max<uint64_t>(touch_words(b.table_cells) * 4, 16);
     const uint64_t nhit = (b.ncols + 31) / 32 + 1;
-    void *old_table = table.p, *old_touch = touch.p;
+    const uint64_t old_table = table.gen, old_touch = touch.gen;
     const size_t lb = std::max<uint64_t>(table_blocks(b.table_cells) * 4, 16);
     if (!ensure(table, tb, &in_use, limit) || !ensure(touch, wb, &in_use, limit) ||
         !ensure(tlist, lb, &in_use, limit) || !ensure(hit, nhit * 8, &in_use, limit)) {
         cudaGetLastError();
         // the table or its touch bits may have moved to fresh memory that was
         // not cleared: clear them when the next launch sizes them
-        if (table.p != old_table || touch.p != old_touch) table_dirty = true;
+        if (table.gen != old_table || touch.gen != old_touch) table_dirty = true;
         return Error::make(S_NOMEM, "device allocation of a " + std::to_string(tb) + "-byte owner table failed");
     }
     // the kernels keep the table and its touch bits all zero between
     // launches; fresh memory (or a failed launch) needs one clear
-    if (table.p != old_table || touch.p != old_touch || table_dirty) {
+    if (table.gen != old_table || touch.gen != old_touch || table_dirty) {
         if (cudaMemsetAsync(table.p, 0, table.cap, s) != cudaSuccess ||
             cudaMemsetAsync(touch.p, 0, touch.cap, s) != cudaSuccess)
             return Error::make(S_CUDA, "memset failed");
@@ -483,7 +516,7 @@ Error DeviceBatch::size_keys(uint64_t n, cudaStream_t s)
     const uint32_t tiles = radix_tiles(n, args.radix_items);
     const size_t kb = std::max<uint64_t>(n, 1) * 8;
     const size_t sb = std::max<size_t>((size_t)args.L.passes * tiles * kRadixBins * 8, 16);
-    size_t old_status = status.cap;
+    const uint64_t old_status = status.gen;
     const uint32_t dtiles = detect_tiles(n);
     bool ok = ensure(keys0, kb, &in_use, limit) && ensure(keys1, kb, &in_use, limit) &&
               ensure(status, sb, &in_use, limit) &&
@@ -494,7 +527,7 @@ Error DeviceBatch::size_keys(uint64_t n, cudaStream_t s)
     }
     // fresh look-back words must not carry a stale tag; clear them when the
     // buffer is new and well before the 22-bit launch tag wraps
-    if (status.cap != old_status || status_launches >= (1ull << 21)) {
+    if (status.gen != old_status || status_launches >= (1ull << 21)) {
         if (cudaMemsetAsync(status.p, 0, status.cap, s) != cudaSuccess) return Error::make(S_CUDA, "memset failed");
         status_launches = 0;
     }

@@ -22,6 +22,10 @@ namespace drf {
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
+    // bumped by every allocation and release: memory that must start out
+    // zero is cleared when this changes (a new allocation can come back at
+    // the address just freed, so the address says nothing)
+    uint64_t gen = 0;
 };
 
 // Grow-only device allocation; returns false on failure.
@@ -56,17 +60,16 @@ struct BatchHost {
     // every protocol is DP_STATIC: owner-table launches may leave the count
     // and scan passes out (BatchArgs::count_free)
     bool all_static = false;
-    // the range pass's work (BatchArgs::racc ..): its accesses, and per task
-    // of kRangeRecs owner records that they reach (rlive, ascending) the
-    // entries [rfirst[i], rfirst[i + 1]) of (access rk, offset rc); their
-    // instructions carry AF_RANGE in `insns`; rorder, the task indices by
-    // decreasing record updates (the order blocks take them in).  range_pcs: per protocol, the
+    // the range pass's work (BatchArgs::rpiece ..): per task of kRangeRecs
+    // owner records that range accesses reach (rlive, ascending) its pieces
+    // [rfirst[i], rfirst[i + 1]) of rpiece, and the tasks again in the order
+    // blocks take them (rtask: most record updates first); the accesses'
+    // instructions carry AF_RANGE in `insns`.  range_pcs: per protocol, the
     // pcs (in its own program) of its range accesses; range_tuples: the
     // access tuples they make.
-    std::vector<RAcc> racc;
-    std::vector<uint32_t> rk;
-    std::vector<int64_t> rc;
-    std::vector<uint32_t> rlive, rfirst, rorder;
+    std::vector<RPiece> rpiece;
+    std::vector<RTask> rtask;
+    std::vector<uint32_t> rlive, rfirst;
     std::vector<std::vector<uint32_t>> range_pcs;
     uint64_t range_tuples = 0;
     uint64_t table_bytes() const { return table_cells * 4; }   // one 32-bit owner record per cell
@@ -82,14 +85,14 @@ constexpr uint64_t kRangeMinTuples = 1ull << 22;   // default: a batch's range t
 Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool expand = true,
                  uint32_t digit_bits = 0, uint64_t range_min = kRangeMinTuples);
 
-// The range pass's work lists of a packed batch (BatchHost::racc ..): the
+// The range pass's work of a packed batch (BatchHost::rpiece ..): the
 // range accesses (Prepared::range_access) of every protocol with static
-// phases whose range accesses make a quarter of its tuples or more, their
-// offsets listed for the tasks of owner records their cells fall into, and
-// AF_RANGE set on their instructions.  Called by pack_batch when the batch
-// has an owner table.
+// phases whose range accesses make a quarter of its tuples or more, each
+// offset's threads cut into pieces at the boundaries of the tasks of owner
+// records their cells fall into, and AF_RANGE set on their instructions.
+// Called by pack_batch when the batch has an owner table.
 void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_t range_min);
-constexpr size_t kRangeMaxEntries = 1u << 20;
+constexpr size_t kRangeMaxEntries = 1u << 20;                // pieces of a batch at most
 
 // Offset of the results after the control block in a batch's report.
 constexpr size_t kOutResults = 128;

@@ -369,7 +369,7 @@ class Gen {
             if (skip_.count(q)) continue;
             const std::string sfx = std::to_string(slot_++);
             body_ << "        const toff_t o" << sfx << " = kr ? " << offset("phase", A.b, idx[q - pc]) << " : (toff_t)0;\n";
-            body_ << "        const uint32_t c" << sfx << " = kr ? __ldca(tab + o" << sfx << ") : 0u;\n";
+            body_ << "        const uint32_t c" << sfx << " = kr ? __ldcg(tab + o" << sfx << ") : 0u;\n";
             S.push_back(Slot{"kr", "o" + sfx, "c" + sfx, (A.a & AF_WRITE) != 0, !uses_tid(A.c)});
         }
         updates(S);
@@ -527,7 +527,7 @@ class Gen {
                         body_ << ";\n";
                         body_ << "        const toff_t o" << sfx << " = k" << sfx << " ? "
                               << offset("h" + sfx, A.b, "i" + sfx) << " : (toff_t)0;\n";
-                        body_ << "        const uint32_t c" << sfx << " = k" << sfx << " ? __ldca(tab + o" << sfx << ") : 0u;\n";
+                        body_ << "        const uint32_t c" << sfx << " = k" << sfx << " ? __ldcg(tab + o" << sfx << ") : 0u;\n";
                         S.push_back(Slot{"k" + sfx, "o" + sfx, "c" + sfx, (A.a & AF_WRITE) != 0, !uses_tid(A.c)});
                         acts.push_back("a" + qs);
                         ks.push_back("k" + sfx);
@@ -670,7 +670,7 @@ struct CellTarget { uint32_t phase, loc; unsigned long long idx; };
 struct __align__(16) IJ { uint32_t j[4]; uint32_t chunk, phase, phase_end, pad; };
 
 // Apply an access to its cell's owner record given a copy `cur` of it read
-// through L1 (drf::owner_put); the update that creates the record marks its
+// through L2 (drf::owner_put); the update that creates the record marks its
 // block as touched.
 static __device__ __forceinline__ void put_cur(uint32_t *table, uint32_t *touch, toff_t off, uint32_t cur, uint32_t tid,
                                                uint32_t w)
@@ -879,9 +879,7 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
     const std::string loop_head = lh.str();
     // every kernel lets its successor launch, then waits for its predecessor
     // (programmatic dependent launch; no-ops under a plain launch), then
-    // issues a device-scope acquire fence so that none of its loads through
-    // L1 returns data older than what the wait made visible (the pipeline's
-    // pdl_begin says why)
+    // issues a device-scope acquire fence, as the pipeline's pdl_begin does
     const char *sig = "(drf::BatchArgs a, const uint16_t *__restrict__ shape)\n{\n    (void)shape;\n"
                       "    asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n"
                       "    asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"

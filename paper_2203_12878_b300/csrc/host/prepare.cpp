@@ -990,34 +990,6 @@ bool range_offsets(const std::vector<uint64_t> &xcode, const RangeAccess &r, uin
     return true;
 }
 
-// Index intervals [lo, hi) of the cells access `r` (array of ncells) reaches
-// over threads [0, T) at offset c (already reduced when the index has a
-// remainder).
-void range_image(const RangeAccess &r, int64_t c, uint64_t ncells, uint32_t T, std::vector<std::pair<int64_t, int64_t>> &out)
-{
-    out.clear();
-    const int64_t t = (int64_t)T, n = (int64_t)ncells;
-    auto add = [&](int64_t lo, int64_t hi) {
-        lo = std::max<int64_t>(lo, 0);
-        hi = std::min<int64_t>(hi, n);
-        if (lo < hi) out.emplace_back(lo, hi);
-    };
-    if (!r.modn) {
-        if (r.sigma == 1) add(c, c + t);
-        else add(c - t + 1, c + 1);
-        return;
-    }
-    const int64_t N = (int64_t)r.modn;
-    if (r.sigma == 1) {
-        add(c, std::min(c + t, N));
-        if (c + t > N) add(0, c + t - N);
-    } else {
-        add(c - std::min(t - 1, c), c + 1);
-        if (t - 1 > c) add(N - (t - 1 - c), N);
-    }
-}
-
-
 Error prepare(const uint8_t *bc, size_t len, uint32_t nthreads, uint32_t nlocs, const uint64_t *cells,
               uint32_t nparams, const int64_t *params, const PrepareOpts &opts, Prepared &out)
 {

@@ -62,10 +62,6 @@ bool host_eval(const std::vector<uint64_t> &xc, int32_t off, int64_t tid, const 
 // fails or more than `cap` iterations would be visited.
 bool range_offsets(const std::vector<uint64_t> &xcode, const RangeAccess &r, uint64_t cap, std::vector<int64_t> &cs,
                    uint64_t &iters);
-// Index intervals [lo, hi) of the cells a range access (array of ncells)
-// reaches over threads [0, T) at offset c.
-void range_image(const RangeAccess &r, int64_t c, uint64_t ncells, uint32_t T,
-                 std::vector<std::pair<int64_t, int64_t>> &out);
 
 struct Prepared {
     uint32_t nthreads = 0;

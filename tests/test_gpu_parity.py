@@ -242,9 +242,12 @@ def test_server_results_equal_alone(ctx, oracle, poll_us):
     finally:
         drf.drf_ctx_destroy(s)
     assert stats["completed"] == len(ps) and stats["rounds"] >= 2
-    for p, o in zip(ps, out):
+    for i, (p, o) in enumerate(zip(ps, out)):
         assert o is not None
-        assert same(drf.result_dict(o[0]), want(oracle, p, ctx))
+        got = drf.result_dict(o[0])
+        if not same(got, want(oracle, p, ctx)):
+            print(json.dumps({"i": i, "got": got, "stats": stats}))
+        assert same(got, want(oracle, p, ctx))
 
 
 def test_server_rejects_bad_options():

@@ -126,3 +126,31 @@ def test_server_bursts_on_reused_buffers(oracle, flags):
     finally:
         drf.drf_ctx_destroy(ctx)
     assert stats["completed"] == done and stats["rounds"] >= 12
+
+
+def test_grown_table_starts_clear(oracle):
+    """A context's owner table grows (free, then a larger allocation) right
+    after another context freed buffers full of non-zero sort keys, which the
+    allocator may hand back at the table's old address: the grown table is
+    cleared all the same (it once was not when the address came back
+    unchanged, and a stale word showed up as a race with a single accessor).
+    Race-free protocols of growing table size, every result against the
+    oracle."""
+    t = drf.drf_ctx_create(0, flags=drf.OPT_PATH_TABLE)
+    try:
+        for step, cells in enumerate((1 << 12, 1 << 16, 1 << 19, 1 << 21, 1 << 23)):
+            s = drf.drf_ctx_create(0, flags=drf.OPT_PATH_SORT)
+            try:
+                k = protogen.Protocol("array A;\nforU x in 0 .. 64 { rd A[(tid + 977 * x) % 65536]; }\n",
+                                      65536, [65536], [])
+                drf.drf_check(s, drf.drf_protocol_compile(k.text), k.nthreads, k.cells, k.params)
+            finally:
+                drf.drf_ctx_destroy(s)
+            p = protogen.Protocol("array A, B;\nwr A[tid];\nsync;\nrd A[(tid + 1) %% %d];\nwr B[tid];\n" % cells,
+                                  cells, [cells, cells], [])
+            got = drf.result_dict(drf.drf_check(t, drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params))
+            exp = oracle.check(p.text, p.nthreads, p.cells, p.params, oracle.METHOD_CELLS)
+            exp.pop("message", None)
+            assert got == exp, (step, cells, got)
+    finally:
+        drf.drf_ctx_destroy(t)

@@ -31,19 +31,22 @@ enum : uint32_t {
 
 // One piece of the range pass's work: the threads t0 .. t0 + len - 1 of
 // one range access at one offset, whose records (relative to the first
-// record of their task) are l0, l0 + 1, ... -- or l0, l0 - 1, ... with
-// kRDown -- and whether they write (kRWrite); lenf holds len and the flags.
+// record of their task) are l0, l0 + step, l0 + 2 step, ... (step: the
+// access's tid coefficient, never 0), and whether they write (kRWrite);
+// lenf holds len and the flag.
 struct RPiece {
     uint32_t t0, lenf;
-    int32_t l0;
-    uint32_t pad;
+    int32_t l0, step;
 };
-constexpr uint32_t kRDown = 1u << 31, kRWrite = 1u << 30, kRLen = (1u << 30) - 1;
+constexpr uint32_t kRWrite = 1u << 30, kRLen = (1u << 30) - 1;
 
 // A task of the range pass: its index (its records start at task *
-// kRangeRecs) and its pieces [p0, p1).
+// kRangeRecs), its pieces [p0, p1), and the part of its records this entry
+// covers, in blocks of 256 records: [win & 0xFFFF, win >> 16) (a task with
+// much work is split into several entries over disjoint parts, each taken
+// by its own block).
 struct RTask {
-    uint32_t task, p0, p1, pad;
+    uint32_t task, p0, p1, win;
 };
 
 #if defined(__CUDACC__)
@@ -52,20 +55,29 @@ struct RTask {
 #define DRF_HD
 #endif
 
-// The part of a piece (threads t0 + o, o < len, at records l0 + o, or
-// l0 - o when `down`) whose records lie in [w0, w1): its first thread, first
-// record and length (0 when none).
-DRF_HD inline void range_clip(long long t0, long long l0, long long len, bool down, long long w0, long long w1,
+// Floor of x / d for d > 0.
+DRF_HD inline long long range_floordiv(long long x, long long d) { return x >= 0 ? x / d : -((-x + d - 1) / d); }
+
+// The part of a piece (threads t0 + o, o < len, at records l0 + step * o,
+// step != 0) whose records lie in [w0, w1): its first thread, first record
+// and length (0 when none).
+DRF_HD inline void range_clip(long long t0, long long l0, long long len, long long step, long long w0, long long w1,
                               long long &ct0, long long &cl0, long long &clen)
 {
-    long long olo, ohi;
-    if (!down) { olo = w0 - l0; ohi = w1 - l0; }
-    else { olo = l0 - w1 + 1; ohi = l0 - w0 + 1; }
+    long long olo, ohi;                           // w0 <= l0 + step * o < w1
+    if (step > 0) {
+        olo = range_floordiv(w0 - l0 + step - 1, step);
+        ohi = range_floordiv(w1 - l0 + step - 1, step);
+    } else {
+        const long long b = -step;
+        olo = range_floordiv(l0 - w1, b) + 1;
+        ohi = range_floordiv(l0 - w0, b) + 1;
+    }
     if (olo < 0) olo = 0;
     if (ohi > len) ohi = len;
     if (olo >= ohi) { ct0 = t0; cl0 = l0; clen = 0; return; }
     ct0 = t0 + olo;
-    cl0 = down ? l0 - olo : l0 + olo;
+    cl0 = l0 + step * olo;
     clen = ohi - olo;
 }
 
@@ -144,6 +156,7 @@ struct BatchArgs {
     const uint32_t *rlive;
     const uint32_t *rfirst;
     uint32_t nlive;
+    uint32_t nrtask;                // entries of rtask (nlive or more: parts of split tasks)
     uint32_t range_on;
     void *table;                     // [tab_cells] 32-bit owner records, padded to whole blocks
     uint64_t tab_cells;

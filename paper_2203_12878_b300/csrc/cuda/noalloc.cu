@@ -146,6 +146,7 @@ extern "C" int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_
     a.rlive = nullptr;
     a.rfirst = nullptr;
     a.nlive = 0;
+    a.nrtask = 0;
     a.range_on = 0;
     a.nwitems = (uint32_t)nw;
     a.nprotos = 1;

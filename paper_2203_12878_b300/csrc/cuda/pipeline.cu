@@ -1172,12 +1172,25 @@ struct RangeShared {
 };
 static_assert(kRangeChunk * 32 >= kRangeRecs, "the racy bitmap needs a bit per record");
 
-
+// The records [lo, hi) a piece's span covers (every step-th of them its own).
 __device__ __forceinline__ void range_span(const RPiece &x, int32_t &lo, int32_t &hi)
 {
     const int32_t len = (int32_t)(x.lenf & kRLen);
-    if (x.lenf & kRDown) { lo = x.l0 - len + 1; hi = x.l0 + 1; }
-    else { lo = x.l0; hi = x.l0 + len; }
+    const int32_t last = x.l0 + x.step * (len - 1);
+    lo = len ? min(x.l0, last) : 0;
+    hi = len ? max(x.l0, last) + 1 : 0;
+}
+
+// Whether two pieces may share a record: their spans overlap, unless both
+// step by the same |s| > 1 from records in different residue classes mod s.
+__device__ __forceinline__ bool range_meet(const RPiece &x, const RPiece &y)
+{
+    int32_t a0, a1, b0, b1;
+    range_span(x, a0, a1);
+    range_span(y, b0, b1);
+    if (!(a0 < b1 && b0 < a1)) return false;
+    const int32_t s = abs(x.step);
+    return !(s > 1 && s == abs(y.step) && (x.l0 - y.l0) % s != 0);
 }
 
 // Applies the round's intervals (sh.ent[0 .. sh.n)) to the task's records:
@@ -1193,13 +1206,9 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
     if (threadIdx.x < 32) {
         bool clash = n > 64;
         for (uint32_t e = threadIdx.x; e < n && !clash; e += 32) {
-            int32_t a0, a1;
-            range_span(sh.ent[e], a0, a1);
-            for (uint32_t f = e + 1; f < n; f++) {
-                int32_t b0, b1;
-                range_span(sh.ent[f], b0, b1);
-                if (a0 < b1 && b0 < a1) { clash = true; break; }
-            }
+            const RPiece x = sh.ent[e];
+            for (uint32_t f = e + 1; f < n; f++)
+                if (range_meet(x, sh.ent[f])) { clash = true; break; }
         }
         clash = __any_sync(kFull, clash);
         // exclusive prefix of the lengths
@@ -1226,7 +1235,7 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
         for (uint32_t e = 0; e < n; e++) {
             const RPiece x = sh.ent[e];
             const uint32_t len = x.lenf & kRLen, w = (x.lenf & kRWrite) ? 1u : 0u;
-            const int32_t step = (x.lenf & kRDown) ? -1 : 1;
+            const int32_t step = x.step;
             uint32_t o0 = threadIdx.x;
             if (plain) {
                 // four records per thread and step, every one in the interval
@@ -1297,7 +1306,7 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
                 const uint32_t o = q - base;
                 tq[k] = x.t0 + o;
                 wq[k] = (x.lenf & kRWrite) ? 1u : 0u;
-                rp[k] = rec + (x.l0 + ((x.lenf & kRDown) ? -(int32_t)o : (int32_t)o));
+                rp[k] = rec + (x.l0 + x.step * (int32_t)o);
             }
         }
         if (plain) {
@@ -1339,7 +1348,7 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
     __shared__ RTask s_task[2];
     const RTask none{~0u, 0u, 0u, 0u};
     auto task_at = [&a, &none](uint32_t i) {
-        if (i >= a.nlive) return none;
+        if (i >= a.nrtask) return none;
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.rtask) + i);
         return RTask{v.x, v.y, v.z, v.w};
     };
@@ -1358,29 +1367,36 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
         RTask nt = none;
         if (threadIdx.x == 0) {
             nt = task_at(nx);
-            if (nx < a.nlive) nx = atomicAdd(&a.ctrl->range_next, 1u);
+            if (nx < a.nrtask) nx = atomicAdd(&a.ctrl->range_next, 1u);
         }
         const unsigned long long r0 = (unsigned long long)tk.task * kRangeRecs;
         const unsigned long long r1 = r0 + kRangeRecs < a.tab_cells ? r0 + kRangeRecs : a.tab_cells;
-        // the window this launch may record (a shard), within the task
-        const unsigned long long w0 = r0 > a.shard_lo ? r0 : a.shard_lo;
-        const unsigned long long w1 = r1 < a.shard_hi ? r1 : a.shard_hi;
         const uint32_t nrec = (uint32_t)(r1 - r0);
+        // this entry's part of the task (blocks [blo, bhi) of 256 records),
+        // and within it the window this launch may record (a shard)
+        const uint32_t blo = tk.win & 0xFFFFu, bhi = tk.win >> 16;
+        const uint32_t rlo = blo * 256u, rhi = bhi * 256u < nrec ? bhi * 256u : nrec;
+        const unsigned long long w0 = r0 + rlo > a.shard_lo ? r0 + rlo : a.shard_lo;
+        const unsigned long long w1 = r0 + rhi < a.shard_hi ? r0 + rhi : a.shard_hi;
         __syncthreads();                                  // the previous task is done with rec and sh
-        // the blocks of 256 records the table pass touched in the task:
+        // the blocks of 256 records the table pass touched in the part:
         // merged into the shared copy and cleared in the table (through L2:
         // this SM's L1 may hold lines the table pass read), one warp per
-        // block, their touch words cleared
+        // block; their touch bits cleared (atomically: another part of the
+        // task may clear other bits of the same word at the same time)
         const uint32_t nwords = (nrec + 8191u) >> 13;
         uint32_t tb = 0;
         if (threadIdx.x < nwords) {
-            tb = __ldcg(a.touch + (r0 >> 13) + threadIdx.x);
+            const uint32_t b0 = threadIdx.x * 32u;            // the word's first block in the task
+            const uint32_t lo = blo > b0 ? blo - b0 : 0u, hi = bhi < b0 + 32u ? (bhi > b0 ? bhi - b0 : 0u) : 32u;
+            const uint32_t mask = lo < hi ? (hi - lo == 32u ? ~0u : ((1u << (hi - lo)) - 1u) << lo) : 0u;
+            tb = mask ? __ldcg(a.touch + (r0 >> 13) + threadIdx.x) & mask : 0u;
             sh.bits[threadIdx.x] = tb;
-            if (tb) a.touch[(r0 >> 13) + threadIdx.x] = 0u;
+            if (tb) atomicAnd(a.touch + (r0 >> 13) + threadIdx.x, ~tb);
         }
         if (__syncthreads_or(tb != 0u)) {
-            const uint32_t nblk = (nrec + 255u) >> 8;
-            for (uint32_t b = warp; b < nblk; b += kRangeThreads / 32) {
+            const uint32_t nblk = (rhi + 255u) >> 8;
+            for (uint32_t b = blo + warp; b < nblk; b += kRangeThreads / 32) {
                 if (!((sh.bits[b >> 5] >> (b & 31u)) & 1u)) continue;
                 for (uint32_t i = b * 256u + lane * 4u; i < b * 256u + 256u && i < nrec; i += 128u) {
                     if (i + 4u <= nrec) {                 // 16-byte aligned: r0 and i are multiples of 4
@@ -1397,19 +1413,19 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
             }
             __syncthreads();
         }
-        // the task's pieces, a round of up to kRangeChunk at a time; a shard
-        // keeps the part of each inside its window
+        // the task's pieces, a round of up to kRangeChunk at a time; a part
+        // of a task, or a shard, keeps what lies inside its window
         const bool whole = w0 == r0 && w1 == r1;
         for (uint32_t p0 = tk.p0; p0 < tk.p1 && w0 < w1; p0 += kRangeChunk) {
             const uint32_t np = tk.p1 - p0 < kRangeChunk ? tk.p1 - p0 : kRangeChunk;
             if (threadIdx.x < np) {
                 const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.rpiece) + p0 + threadIdx.x);
-                RPiece x{v.x, v.y, (int32_t)v.z, 0u};
+                RPiece x{v.x, v.y, (int32_t)v.z, (int32_t)v.w};
                 if (!whole) {
                     long long ct0, cl0, clen;
-                    range_clip(x.t0, x.l0, x.lenf & kRLen, (x.lenf & kRDown) != 0, (long long)(w0 - r0),
-                               (long long)(w1 - r0), ct0, cl0, clen);
-                    x = RPiece{(uint32_t)ct0, (uint32_t)clen | (x.lenf & ~kRLen), (int32_t)cl0, 0u};
+                    range_clip(x.t0, x.l0, x.lenf & kRLen, x.step, (long long)(w0 - r0), (long long)(w1 - r0), ct0,
+                               cl0, clen);
+                    x = RPiece{(uint32_t)ct0, (uint32_t)clen | (x.lenf & ~kRLen), (int32_t)cl0, x.step};
                 }
                 sh.ent[threadIdx.x] = x;
             }
@@ -1424,7 +1440,7 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
         for (uint32_t i = threadIdx.x; i < kRangeRecs / 32; i += kRangeThreads) racy[i] = 0u;
         __syncthreads();
         bool found = false;
-        for (uint32_t q = threadIdx.x; q < kRangeRecs / 4; q += kRangeThreads) {
+        for (uint32_t q = (rlo >> 2) + threadIdx.x; q < (rhi + 3u) >> 2; q += kRangeThreads) {
             const uint4 v = r4[q];
             if (v.x | v.y | v.z | v.w) {
                 r4[q] = make_uint4(0u, 0u, 0u, 0u);
@@ -1438,11 +1454,12 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
         // (rows are phase-major, then array, then index: the lexicographic
         // order of the witness), by the first warp
         if (__syncthreads_or(found) && warp == 0) {
-            uint32_t p = proto_of_record(a, r0);
+            uint32_t p = proto_of_record(a, r0 + rlo);
             while (true) {
                 const DevProto P = a.protos[p];
                 const unsigned long long pe = P.tab_off + (unsigned long long)P.tab_phases * P.cells_sum;
-                const unsigned long long s0 = P.tab_off > r0 ? P.tab_off : r0, s1 = pe < r1 ? pe : r1;
+                const unsigned long long s0 = P.tab_off > r0 + rlo ? P.tab_off : r0 + rlo;
+                const unsigned long long s1 = pe < r0 + rhi ? pe : r0 + rhi;
                 if (s0 < s1) {
                     const uint32_t lo = (uint32_t)(s0 - r0), hi = (uint32_t)(s1 - r0);
                     for (uint32_t wb = (lo >> 5); wb <= ((hi - 1) >> 5); wb += 32) {
@@ -1460,7 +1477,7 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
                         }
                     }
                 }
-                if (p + 1 >= a.nprotos || __ldg(&a.protos[p + 1].tab_off) >= r1) break;
+                if (p + 1 >= a.nprotos || __ldg(&a.protos[p + 1].tab_off) >= r0 + rhi) break;
                 p++;
             }
         }
@@ -1544,7 +1561,10 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
                     const uint32_t e1 = __ldg(a.rfirst + lo + 1);
                     for (uint32_t e = __ldg(a.rfirst + lo) + t; e < e1; e += kFinalizeThreads) {
                         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.rpiece) + e);
-                        const long long o = (v.y & kRDown) ? (long long)(int32_t)v.z - x : x - (long long)(int32_t)v.z;
+                        // x = l0 + step * o for some o < len
+                        const long long d = x - (long long)(int32_t)v.z, st = (long long)(int32_t)v.w;
+                        if (d % st != 0) continue;
+                        const long long o = d / st;
                         if (o < 0 || o >= (long long)(v.y & kRLen)) continue;
                         const uint32_t tid = v.x + (uint32_t)o;          // the piece's thread at the record
                         two_smallest(t0, t1, tid);
@@ -1707,7 +1727,7 @@ static void launch_range(const BatchArgs &a, cudaStream_t s, int sms)
         ready[dev] = true;
     }
     const uint32_t want = (uint32_t)sms * kRangeBlocksPerSm;
-    PdlConfig c(dim3(a.nlive < want ? (a.nlive ? a.nlive : 1) : want), dim3(kRangeThreads), s);
+    PdlConfig c(dim3(a.nrtask < want ? (a.nrtask ? a.nrtask : 1) : want), dim3(kRangeThreads), s);
     c.cfg.dynamicSmemBytes = kRangeSmem;
     cudaLaunchKernelEx(&c.cfg, k_range, a);
 }

@@ -152,30 +152,28 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
 namespace {
 
 // The threads of range access r at offset c (reduced mod the modulus when
-// there is one) as at most two runs of consecutive tids whose cells follow
-// each other up or down the array: (first tid, count, first cell, down).
-struct Run { int64_t t0, len, cell0; bool down; };
+// there is one) as at most two runs of consecutive tids whose cells are
+// sigma apart: (first tid, count, first tid's cell).  Cells outside the
+// array are clipped by the caller.
+struct Run { int64_t t0, len, cell0; };
 
 int range_runs(const RangeAccess &r, int64_t c, uint32_t T, Run out[2])
 {
-    const int64_t t = (int64_t)T;
+    const int64_t t = (int64_t)T, s = r.sigma;
     int n = 0;
-    auto add = [&](int64_t a, int64_t b, int64_t cell0, bool down) {
-        if (a < b) out[n++] = Run{a, b - a, cell0, down};
+    auto add = [&](int64_t a, int64_t b, int64_t cell0) {
+        if (a < b) out[n++] = Run{a, b - a, cell0};
     };
     if (!r.modn) {
-        if (r.sigma == 1) add(std::max<int64_t>(0, -c), t, c + std::max<int64_t>(0, -c), false);
-        else add(0, t, c, true);                       // cells below 0 are clipped by the caller
+        add(0, t, c);
         return n;
     }
-    const int64_t N = (int64_t)r.modn;                 // c in [0, N), T <= N: at most one wrap
-    if (r.sigma == 1) {
-        add(0, std::min(t, N - c), c, false);          // tid + c < N
-        add(N - c, t, 0, false);                       // wrapped: tid + c - N
-    } else {
-        add(0, std::min(t, c + 1), c, true);           // c - tid >= 0
-        add(c + 1, t, N - 1, true);                    // wrapped: c - tid + N
-    }
+    // c in [0, N) and (T - 1) * |sigma| < N: the index wraps at most once,
+    // from tid t1 on
+    const int64_t N = (int64_t)r.modn;
+    const int64_t t1 = s > 0 ? (N - c + s - 1) / s : c / -s + 1;
+    add(0, std::min(t, t1), c);
+    add(t1, t, c + s * t1 + (s > 0 ? -N : N));
     return n;
 }
 
@@ -228,21 +226,22 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
             const int64_t ncells = (int64_t)p.cells[r.loc];
             const int64_t sb = (int64_t)(d.tab_off + (uint64_t)r.phase * d.cells_sum + out.cbase[d.cells_off + r.loc]);
             const uint32_t wf = r.write ? kRWrite : 0u;
+            const long long s = r.sigma;
             for (int64_t c : r.offsets) {
                 Run runs[2];
                 const int nr = range_runs(r, c, p.nthreads, runs);
                 for (int q = 0; q < nr; q++) {
                     // within the array, then cut at task boundaries
                     long long t0, l0, len;
-                    range_clip(runs[q].t0, sb + runs[q].cell0, runs[q].len, runs[q].down, sb, sb + ncells, t0, l0, len);
+                    range_clip(runs[q].t0, sb + runs[q].cell0, runs[q].len, s, sb, sb + ncells, t0, l0, len);
                     while (len > 0) {
                         const long long task = l0 / (long long)kRangeRecs, base = task * (long long)kRangeRecs;
                         long long ct0, cl0, clen;
-                        range_clip(t0, l0, len, runs[q].down, base, base + (long long)kRangeRecs, ct0, cl0, clen);
-                        const uint32_t f = (runs[q].down ? kRDown : 0u) | wf;
-                        ent.push_back(E{(uint32_t)task, RPiece{(uint32_t)ct0, (uint32_t)clen | f, (int32_t)(cl0 - base), 0u}});
+                        range_clip(t0, l0, len, s, base, base + (long long)kRangeRecs, ct0, cl0, clen);
+                        ent.push_back(E{(uint32_t)task, RPiece{(uint32_t)ct0, (uint32_t)clen | wf, (int32_t)(cl0 - base),
+                                                               (int32_t)s}});
                         t0 += clen;
-                        l0 = runs[q].down ? l0 - clen : l0 + clen;
+                        l0 += s * clen;
                         len -= clen;
                     }
                 }
@@ -277,13 +276,27 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
         work.back() += ent[i].piece.lenf & kRLen;
     }
     if (!out.rlive.empty()) out.rfirst.push_back((uint32_t)ent.size());
-    // blocks take tasks from a shared counter, the largest first, so that
-    // the launch does not end on a few blocks still working through big ones
-    std::vector<uint32_t> order(out.rlive.size());
-    for (uint32_t i = 0; i < (uint32_t)order.size(); i++) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&work](uint32_t x, uint32_t y) { return work[x] > work[y]; });
-    out.rtask.reserve(order.size());
-    for (uint32_t i : order) out.rtask.push_back(RTask{out.rlive[i], out.rfirst[i], out.rfirst[i + 1], 0u});
+    // a task with much work is split into parts over disjoint blocks of its
+    // records (a part per kRangeSplitWork record updates, assuming them
+    // spread evenly), each taken by its own block; blocks take the parts
+    // from a shared counter, the largest first, so that the launch does not
+    // end on a few blocks still working through big ones
+    struct Part { RTask t; uint64_t work; };
+    std::vector<Part> parts;
+    parts.reserve(out.rlive.size());
+    const uint64_t nblk_all = (out.table_cells + 255) / 256;
+    for (size_t i = 0; i < out.rlive.size(); i++) {
+        const uint64_t first = (uint64_t)out.rlive[i] * (kRangeRecs / 256);
+        const uint32_t nblk = (uint32_t)std::min<uint64_t>(kRangeRecs / 256, nblk_all - first);
+        const uint32_t k = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(nblk, (work[i] + kRangeSplitWork - 1) / kRangeSplitWork));
+        for (uint32_t q = 0; q < k; q++) {
+            const uint32_t b0 = nblk * q / k, b1 = nblk * (q + 1) / k;
+            parts.push_back(Part{RTask{out.rlive[i], out.rfirst[i], out.rfirst[i + 1], b0 | (b1 << 16)}, work[i] / k});
+        }
+    }
+    std::stable_sort(parts.begin(), parts.end(), [](const Part &x, const Part &y) { return x.work > y.work; });
+    out.rtask.reserve(parts.size());
+    for (const Part &x : parts) out.rtask.push_back(x.t);
 }
 
 DeviceBatch::~DeviceBatch()
@@ -404,6 +417,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.rlive = (const uint32_t *)(img + sec[10].off);
     a.rfirst = (const uint32_t *)(img + sec[11].off);
     a.nlive = (uint32_t)b.rlive.size();
+    a.nrtask = (uint32_t)b.rtask.size();
     a.range_on = 0;
     a.nwitems = (uint32_t)nw;
     a.nprotos = (uint32_t)np;

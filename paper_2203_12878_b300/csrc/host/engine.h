@@ -92,7 +92,8 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
 // records their cells fall into, and AF_RANGE set on their instructions.
 // Called by pack_batch when the batch has an owner table.
 void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_t range_min);
-constexpr size_t kRangeMaxEntries = 1u << 20;                // pieces of a batch at most
+constexpr size_t kRangeMaxEntries = 1u << 24;                // pieces of a batch at most
+constexpr uint64_t kRangeSplitWork = 1u << 15;               // record updates per part of a task
 
 // Offset of the results after the control block in a batch's report.
 constexpr size_t kOutResults = 128;

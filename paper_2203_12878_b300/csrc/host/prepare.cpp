@@ -784,11 +784,12 @@ struct RangeFinder {
             Lowerer::Lin d = lw.linear(*e->b);
             if (!d.ok || !d.terms.empty() || d.c0 <= 0 || d.c0 >= ((i128)1 << 62)) return;
             modn = (uint64_t)d.c0;
-            if (T > modn) return;             // at most two tid intervals per cell range
             e = e->a.get();
         }
         i128 k = 0;
-        if (!tid_coef(*e, k) || (k != 1 && k != -1)) return;
+        if (!tid_coef(*e, k) || k == 0 || k > kRangeMaxSigma || k < -kRangeMaxSigma) return;
+        // with a remainder, the index wraps at most once over the threads
+        if (modn && (i128)(T ? T - 1 : 0) * (k < 0 ? -k : k) >= (i128)modn) return;
         RangeAccess r;
         r.pc = pc;
         r.phase = (uint32_t)phase;

@@ -36,6 +36,12 @@ Workload families (all seeded with ``random.Random``):
                      loop variables (with or without a remainder), mixed with
                      accesses of other tid coefficients and conditions on the
                      loop variables; races arise where such ranges overlap.
+* ``strided_small``-- the same sizes with indices a * tid plus a function of
+                     the loop variables, a in +-{2, 3, 5, 7, 8} (with a
+                     remainder that wraps at most once over the threads, or
+                     none and kept in range), mixed with +-tid, tid-free and
+                     conditional accesses; quiet seeds write only cells
+                     a * (tid + T * k) and are race-free by construction.
 """
 from __future__ import annotations
 
@@ -463,6 +469,74 @@ def shifted_small(seed: int) -> Protocol:
                 text = f"{kw} {v} in 0 .. {t} {{\n{text}\n}}"
             lines.append(text)
     return Protocol("\n".join(lines) + "\n", nthreads, cells, [], {"seed": seed})
+
+
+# --------------------------------------------------------- strided_small --
+
+def strided_small(seed: int) -> Protocol:
+    """A protocol of the shape described in the module header
+    (``strided_small``): every index provably inside its array, the same
+    sync structure for every thread."""
+    r = random.Random(0x57D1 ^ (seed * 2654435761))
+    nthreads = r.choice([r.randint(64, 600), r.randint(600, 2000)])
+    narrays = r.randint(1, 3)
+    names = "ABC"[:narrays]
+    quiet = r.random() < 0.4
+    strides = [2, 3, 5, 7, 8, -2, -3, -5, -7, -8]
+    cells = [r.randint(8 * nthreads + 1, 9 * nthreads + 20000) for _ in range(narrays)]
+    kq = r.choice(strides[:5])      # quiet seeds: the one stride of every write
+    if quiet:
+        cells = [max(c, 8 * nthreads * 6 + 1) for c in cells]
+    lines = [f"array {', '.join(names)};"]
+    for ph in range(r.randint(1, 3)):
+        if ph:
+            lines.append("sync;")
+        for _ in range(r.randint(1, 3)):
+            depth = r.randint(1, 2)
+            vs = ["x", "y"][:depth]
+            trips = [r.randint(1, 5) for _ in vs]
+            body = []
+            for _ in range(r.randint(1, 3)):
+                a = r.randrange(narrays)
+                n = cells[a]
+                if quiet:
+                    w = ph % narrays
+                    if a == w:              # distinct cells kq * (tid + T * j), j < 6, per thread and j
+                        body.append(f"wr {names[a]}[{kq} * (tid + {nthreads} * (({' + '.join(vs)}) % 6))];")
+                    elif narrays > 1:
+                        body.append(f"rd {names[a]}[({r.choice(strides)} * tid + {r.randint(0, 999)} * {vs[0]}) % {n}];")
+                    continue
+                mode = r.choice(["rd", "wr", "wr"])
+                kind = r.random()
+                k = r.choice(strides)
+                if kind < 0.4:              # (a * tid + f) mod m, one wrap at most: (T - 1) |a| < m <= n
+                    m = r.randint((nthreads - 1) * abs(k) + 1, n)
+                    f = " + ".join(f"{r.randint(0, 3000)} * {v}" for v in vs)
+                    body.append(f"{mode} {names[a]}[({k} * tid + {f} + {r.randint(-4000, 4000)}) % {m}];")
+                elif kind < 0.65:           # a * tid + g + base, no remainder, in range
+                    span = n - abs(k) * (nthreads - 1) - 1
+                    gm = max(1, span // 12)
+                    g = f"(({' + '.join(f'{r.randint(1, 5)} * {v}' for v in vs)}) % {gm})"
+                    base = 0 if k > 0 else abs(k) * (nthreads - 1)
+                    body.append(f"{mode} {names[a]}[{k} * tid + {base} + {g} * {r.randint(0, 8)}];")
+                elif kind < 0.8:            # +-tid with a remainder
+                    m = r.randint(nthreads, n)
+                    body.append(f"{mode} {names[a]}[({r.choice(['', '-1 * '])}tid + {r.randint(0, 99)} * {vs[-1]}) % {m}];")
+                elif kind < 0.9:            # the same cell for every thread
+                    body.append(f"rd {names[a]}[({vs[-1]} * 13) % {n}];")
+                else:                       # a condition on a loop variable
+                    body.append(f"if ({vs[0]} < {r.randint(1, 4)}) {{ {mode} {names[a]}[({k} * tid + 11 * {vs[0]}) % {n}]; }}")
+            if not body:
+                body.append("skip;")
+            text = "\n".join(body)
+            kws, synced = [], True        # forS only inside forS (Fig. 1)
+            for _ in vs:
+                kws.append("forS" if synced and r.random() < 0.3 else "forU")
+                synced = kws[-1] == "forS"
+            for v, t, kw in reversed(list(zip(vs, trips, kws))):
+                text = f"{kw} {v} in 0 .. {t} {{\n{text}\n}}"
+            lines.append(text)
+    return Protocol("\n".join(lines) + "\n", nthreads, cells, [], {"seed": seed, "quiet": quiet})
 
 
 # --------------------------------------------------------------- config 2 --

@@ -524,6 +524,7 @@ def test_interpreted_batch_runs_the_range_pass(oracle):
     c = drf.drf_ctx_create(0, flags=drf.OPT_PATH_TABLE | drf.OPT_RANGE_ANY)
     try:
         ps = protogen.config4(master_seed=23, count=40) + [protogen.shifted_small(s) for s in range(20)]
+        ps += [protogen.strided_small(s) for s in range(100, 120)]
         ps += [protogen.random_small(s) for s in range(300, 320)]
         ps = [p for p in ps if want(oracle, p)["status"] == "OK"]
         plan = drf.drf_plan_create(c, [drf.drf_protocol_compile(p.text) for p in ps],

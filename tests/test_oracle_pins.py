@@ -348,3 +348,17 @@ def test_single_cell_helper_agrees_with_whole_check(oracle):
                {k: got[k] for k in ("tid_i", "tid_j", "i_writes", "j_writes")}
         n += 1
     assert n > 50
+
+
+def test_strided_quiet_seeds_race_free(oracle):
+    """Quiet strided_small seeds write only cells a * (tid + T * j), j < 6
+    (distinct per thread and j), and read only other arrays: race-free by
+    construction, as the oracle finds."""
+    n = 0
+    for s in range(40):
+        p = protogen.strided_small(s)
+        if not p.meta["quiet"]:
+            continue
+        n += 1
+        assert oracle.check(p.text, p.nthreads, p.cells, p.params, CELLS)["verdict"] == "DRF", p.text
+    assert n >= 10

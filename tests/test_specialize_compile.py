@@ -68,20 +68,23 @@ def test_range_pass_source_compiles(seed):
 
 
 def test_grid_scale_protocol_gets_the_range_pass():
-    """Every owned write (+-tid + 65536 * g(x, y) + d) mod 2^24 of the
-    grid-scale protocol goes to the range pass: 206,241,792 of its
-    221,642,754 tuples; the reads of other tid coefficients stay in the
-    table pass."""
+    """Every access of the grid-scale protocol at a * tid plus a function of
+    the loop variables (the owned writes with a = +-1, the reads with a in
+    -8..3) goes to the range pass: 220,790,784 of its 221,642,754 tuples;
+    the tid-free read D[5x - 6] (13 x 65,536) and the two guarded writes of
+    the planted race stay in the table pass."""
     p = protogen.config3(0, racy=True)
     st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
     assert st == "OK"
-    assert a["range_tuples"] == 206241792
+    assert a["range_tuples"] == 221642754 - 13 * 65536 - 2
     st, src, log = drf.drf_protocol_specialize(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
     assert st == "OK", log
 
 
 def test_protocols_without_shifted_indices_get_no_range_pass():
-    for text, T, n in (("array A;\nwr A[2 * tid];\n", 64, 128),                  # another tid coefficient
+    for text, T, n in (("array A;\nwr A[100 * tid];\n", 64, 6400),               # a coefficient above 64
+                       ("array A;\nwr A[(3 * tid) % 150];\n", 64, 150),         # wraps twice over the threads
+                       ("array A;\nwr A[tid * tid];\n", 64, 4096),                # not linear in tid
                        ("array A;\nforU x in 0 .. tid { wr A[tid + 64 * x]; }\n", 64, 64 * 64),   # bound reads tid
                        ("array A;\nforS x in 0 .. 4 { wr A[tid + 64 * x]; sync; }\n", 64, 256)):  # sync in the loop
         st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile(text), T, [n], [])
@@ -89,3 +92,6 @@ def test_protocols_without_shifted_indices_get_no_range_pass():
     st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile("array A;\nforU x in 0 .. 4 { wr A[tid + 64 * x]; }\n"),
                                      64, [256], [])
     assert st == "OK" and a["range_tuples"] == 256          # counted at any size
+    st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile("array A;\nforU x in 0 .. 4 { wr A[(-3 * tid + x) % 200]; }\n"),
+                                     64, [256], [])
+    assert st == "OK" and a["range_tuples"] == 256          # stride -3, one wrap

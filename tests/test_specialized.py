@@ -129,10 +129,11 @@ def test_record_width_boundary(sctx, oracle):
 
 
 def test_config2_full_size(sctx, oracle):
-    """The benchmarked protocol at full size, launch after launch; its sync
+    """The 1,024-thread protocol at full size, launch after launch; its sync
     structure is the same for every thread, so the plan runs with static
-    phases."""
-    assert check(sctx, oracle, protogen.config2(0)) == 2
+    phases, and its accesses at a * tid plus a loop function (|a| <= 8) make
+    most of its tuples, so it takes the range pass."""
+    assert check(sctx, oracle, protogen.config2(0)) == 3
 
 
 @pytest.mark.parametrize("seed,racy", [(0, True), (0, False), (1, True), (1, False)])
@@ -278,6 +279,19 @@ def test_range_pass_against_oracle(rctx, oracle, chunk):
     assert kinds.count(3) >= 10, kinds
 
 
+@pytest.mark.parametrize("chunk", range(4))
+def test_strided_range_pass_against_oracle(rctx, oracle, chunk):
+    """Accesses at a * tid plus a function of the loop variables, |a| in
+    2..8 (pieces whose records lie a apart, interleaving without meeting
+    when their offsets differ mod a), with and without a remainder, mixed
+    with +-tid, tid-free and conditional accesses: every result field equals
+    the oracle's, launch after launch."""
+    kinds = []
+    for seed in range(chunk * 20, (chunk + 1) * 20):
+        kinds.append(check(rctx, oracle, protogen.strided_small(seed)))
+    assert kinds.count(3) >= 15, kinds
+
+
 def test_small_protocols_skip_the_range_pass_by_default(sctx, oracle):
     """Under 2^22 range tuples a check keeps the table pass alone (same
     results)."""
@@ -294,6 +308,6 @@ def test_config3_runs_the_range_pass(sctx):
         assert drf.drf_plan_info(plan)["kernels_per_launch"] == 6
         drf.drf_plan_launch(plan)
         tuples, updates = drf.drf_plan_range_tuples(plan)
-        assert tuples == 206241792 and 0 < updates < tuples
+        assert tuples == 221642754 - 13 * 65536 - 2 and 0 < updates < tuples
     finally:
         drf.drf_plan_destroy(plan)

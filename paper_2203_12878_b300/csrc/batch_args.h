@@ -33,12 +33,14 @@ enum : uint32_t {
 // one range access at one offset, whose records (relative to the first
 // record of their task) are l0, l0 + step, l0 + 2 step, ... (step: the
 // access's tid coefficient, never 0), and whether they write (kRWrite);
-// lenf holds len and the flag.
+// lenf holds len and the flags.  With kRSat the piece stands for records
+// that two or more different threads reach: each gets the "second thread"
+// bit (and "written" with kRWrite), and t0 is unused.
 struct RPiece {
     uint32_t t0, lenf;
     int32_t l0, step;
 };
-constexpr uint32_t kRWrite = 1u << 30, kRLen = (1u << 30) - 1;
+constexpr uint32_t kRSat = 1u << 31, kRWrite = 1u << 30, kRLen = (1u << 30) - 1;
 
 // A task of the range pass: its index (its records start at task *
 // kRangeRecs), its pieces [p0, p1), and the part of its records this entry
@@ -147,11 +149,14 @@ struct BatchArgs {
     // [0, ~0) otherwise.
     unsigned long long shard_lo, shard_hi;
     // The range pass (owner-table launches): tasks of kRangeRecs records
-    // that range accesses reach (rlive, ascending), each with its pieces
-    // [rfirst[i], rfirst[i + 1]) of rpiece; rtask, the same tasks in the
-    // order blocks take them (most record updates first).  The table pass
+    // that range accesses reach (rlive, ascending), each with its pieces as
+    // cut [rfirst[i], rfirst[i + 1]) of wpiece (what the witness search
+    // reads); rtask, the same tasks (or parts of them) in the order blocks
+    // take them (most record updates first), each with its merged pieces
+    // [p0, p1) of rpiece (what the range pass applies).  The table pass
     // leaves accesses marked AF_RANGE alone when range_on is set.
     const RPiece *rpiece;
+    const RPiece *wpiece;
     const RTask *rtask;
     const uint32_t *rlive;
     const uint32_t *rfirst;

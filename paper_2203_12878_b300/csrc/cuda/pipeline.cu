@@ -1237,6 +1237,17 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
             const uint32_t len = x.lenf & kRLen, w = (x.lenf & kRWrite) ? 1u : 0u;
             const int32_t step = x.step;
             uint32_t o0 = threadIdx.x;
+            if (x.lenf & kRSat) {
+                // records two or more threads reach: "second thread" (and
+                // "written") whatever they held
+                const uint32_t bits = kOwnerMulti | (w << 31);
+                for (; o0 < len; o0 += kRangeThreads) {
+                    uint32_t *const r = rec + (x.l0 + step * (int32_t)o0);
+                    if (plain) *r |= bits;
+                    else if ((*r & bits) != bits) atomicOr(r, bits);
+                }
+                continue;
+            }
             if (plain) {
                 // four records per thread and step, every one in the interval
                 const uint32_t wbit = w << 31;
@@ -1257,25 +1268,29 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
                 }
                 continue;
             }
-            // intervals that share records: claims by compare-and-swap
+            // pieces that share records: a plain read first (a record
+            // another piece has already saturated needs nothing), then a
+            // claim by compare-and-swap or the missing bits
             for (; o0 < len; o0 += 4u * kRangeThreads) {
                 int32_t ri[4];
-                uint32_t old[4];
+                uint32_t cur[4];
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     const uint32_t o = o0 + (uint32_t)k * kRangeThreads;
                     ri[k] = o < len ? x.l0 + step * (int32_t)o : -1;
                 }
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const uint32_t t = x.t0 + o0 + (uint32_t)k * kRangeThreads;
-                    old[k] = ri[k] >= 0 ? atomicCAS(rec + ri[k], 0u, (t + 1u) | (w << 31)) : 0u;
-                }
+                for (int k = 0; k < 4; k++) cur[k] = ri[k] >= 0 ? rec[ri[k]] : 0u;
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    if (ri[k] < 0 || old[k] == 0u) continue;
+                    if (ri[k] < 0) continue;
                     const uint32_t t = x.t0 + o0 + (uint32_t)k * kRangeThreads;
-                    if (const uint32_t need = owner_need(old[k], t, w)) atomicOr(rec + ri[k], need);
+                    uint32_t c = cur[k];
+                    if (c == 0u) {
+                        c = atomicCAS(rec + ri[k], 0u, (t + 1u) | (w << 31));
+                        if (c == 0u) continue;
+                    }
+                    if (const uint32_t need = owner_need(c, t, w)) atomicOr(rec + ri[k], need);
                 }
             }
         }
@@ -1289,13 +1304,16 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
     uint32_t e = 0, base = 0, nxt = 0;
     RPiece x{};
     if (total) { x = sh.ent[0]; nxt = n > 1 ? sh.pre[1] : total; }
+    // per position: its record ri (-1: none), its thread + 1 (t1; 0 for a
+    // kRSat piece) and the bits it brings (wb: "written" for a writer; for
+    // kRSat also "second thread")
     for (uint32_t q0 = threadIdx.x; q0 < total; q0 += 4u * kRangeThreads) {
-        uint32_t *rp[4];
-        uint32_t tq[4], wq[4], old[4];
+        int32_t ri[4];
+        uint32_t t1[4], wb[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const uint32_t q = q0 + (uint32_t)k * kRangeThreads;
-            rp[k] = nullptr;
+            ri[k] = -1;
             if (q < total) {
                 while (q >= nxt) {                    // positions only grow
                     e++;
@@ -1304,24 +1322,28 @@ __device__ void range_apply(uint32_t *rec, RangeShared &sh)
                     nxt = e + 1 < n ? sh.pre[e + 1] : total;
                 }
                 const uint32_t o = q - base;
-                tq[k] = x.t0 + o;
-                wq[k] = (x.lenf & kRWrite) ? 1u : 0u;
-                rp[k] = rec + (x.l0 + x.step * (int32_t)o);
+                const bool sat = (x.lenf & kRSat) != 0;
+                t1[k] = sat ? 0u : x.t0 + o + 1u;
+                wb[k] = ((x.lenf & kRWrite) ? kOwnerWritten : 0u) | (sat ? kOwnerMulti : 0u);
+                ri[k] = x.l0 + x.step * (int32_t)o;
             }
         }
         if (plain) {
+            uint32_t old[4];
 #pragma unroll
-            for (int k = 0; k < 4; k++) old[k] = rp[k] ? *rp[k] : 0u;
+            for (int k = 0; k < 4; k++) old[k] = ri[k] >= 0 ? rec[ri[k]] : 0u;
 #pragma unroll
             for (int k = 0; k < 4; k++)
-                if (rp[k]) *rp[k] = owner_merge(old[k], tq[k] + 1u, wq[k] << 31);
+                if (ri[k] >= 0) rec[ri[k]] = t1[k] ? owner_merge(old[k], t1[k], wb[k]) : old[k] | wb[k];
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; k++) old[k] = rp[k] ? atomicCAS(rp[k], 0u, (tq[k] + 1u) | (wq[k] << 31)) : 0u;
-#pragma unroll
             for (int k = 0; k < 4; k++) {
-                if (!rp[k] || old[k] == 0u) continue;
-                if (const uint32_t need = owner_need(old[k], tq[k], wq[k])) atomicOr(rp[k], need);
+                if (ri[k] < 0) continue;
+                uint32_t *const r = rec + ri[k];
+                if (!t1[k]) { atomicOr(r, wb[k]); continue; }
+                const uint32_t c = atomicCAS(r, 0u, t1[k] | wb[k]);
+                if (c == 0u) continue;
+                if (const uint32_t need = owner_need(c, t1[k] - 1u, wb[k] >> 31)) atomicOr(r, need);
             }
         }
     }
@@ -1560,7 +1582,7 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
                     const long long x = (long long)(bp - task * kRangeRecs);
                     const uint32_t e1 = __ldg(a.rfirst + lo + 1);
                     for (uint32_t e = __ldg(a.rfirst + lo) + t; e < e1; e += kFinalizeThreads) {
-                        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.rpiece) + e);
+                        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.wpiece) + e);
                         // x = l0 + step * o for some o < len
                         const long long d = x - (long long)(int32_t)v.z, st = (long long)(int32_t)v.w;
                         if (d % st != 0) continue;

@@ -2,6 +2,7 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <map>
 #include <cstring>
 #include <numeric>
 
@@ -187,9 +188,95 @@ bool range_candidate(const Prepared &p, const DevProto &d, unsigned __int128 &rt
     return rt * 4 >= (unsigned __int128)p.tuple_bound();
 }
 
+// One task's pieces as the range pass applies them.  Pieces of one step s
+// whose records fall in one residue class mod |s| are compared record by
+// record along that class: records that pieces of one base (record minus
+// s times thread: the same thread at every record) reach keep that base's
+// threads, in one piece however many accesses and offsets repeat them;
+// records that two or more bases reach -- two different threads -- become
+// kRSat pieces, which only set "second thread" (and "written" where some
+// covering piece writes).  Pieces of different steps are left as they are;
+// the kernel checks which pieces meet.
+void merge_pieces(const RPiece *in, size_t n, std::vector<RPiece> &out)
+{
+    out.clear();
+    struct P { int64_t s, a, r, base, u0, u1; bool w; };    // lattice coordinates u: record = r + a * u
+    std::vector<P> ps;
+    ps.reserve(n);
+    for (size_t i = 0; i < n; i++) {
+        const RPiece &x = in[i];
+        const int64_t len = x.lenf & kRLen;
+        if (!len) continue;
+        const int64_t s = x.step, a = s < 0 ? -s : s, l0 = x.l0;
+        const int64_t r = ((l0 % a) + a) % a, ul = (l0 - r) / a;
+        const int64_t u0 = s > 0 ? ul : ul - len + 1, u1 = s > 0 ? ul + len : ul + 1;
+        ps.push_back(P{s, a, r, l0 - s * (int64_t)x.t0, u0, u1, (x.lenf & kRWrite) != 0});
+    }
+    std::sort(ps.begin(), ps.end(), [](const P &x, const P &y) {
+        return x.s != y.s ? x.s < y.s : x.r != y.r ? x.r < y.r : x.u0 < y.u0;
+    });
+    struct Ev { int64_t u; int d; size_t k; };
+    std::vector<Ev> ev;
+    for (size_t g0 = 0; g0 < ps.size();) {
+        size_t g1 = g0;
+        while (g1 < ps.size() && ps[g1].s == ps[g0].s && ps[g1].r == ps[g0].r) g1++;
+        const int64_t s = ps[g0].s, a = ps[g0].a, r = ps[g0].r;
+        ev.clear();
+        for (size_t k = g0; k < g1; k++) {
+            ev.push_back(Ev{ps[k].u0, +1, k});
+            ev.push_back(Ev{ps[k].u1, -1, k});
+        }
+        std::sort(ev.begin(), ev.end(), [](const Ev &x, const Ev &y) { return x.u < y.u; });
+        // active pieces per base: (count, writers)
+        std::map<int64_t, std::pair<int, int>> act;
+        int writers = 0;
+        // the output run being extended: kind 0 none, 1 one base, 2 saturated
+        int kind = 0;
+        int64_t run_u0 = 0, run_base = 0;
+        bool run_w = false;
+        auto close = [&](int64_t u_end) {
+            if (kind == 0 || u_end <= run_u0) { kind = 0; return; }
+            const int64_t len = u_end - run_u0;
+            const uint32_t wf = run_w ? kRWrite : 0u;
+            if (kind == 2) {
+                out.push_back(RPiece{0u, (uint32_t)len | kRSat | wf, (int32_t)(r + a * run_u0), (int32_t)a});
+            } else if (s > 0) {
+                const int64_t l0 = r + a * run_u0;
+                out.push_back(RPiece{(uint32_t)((l0 - run_base) / s), (uint32_t)len | wf, (int32_t)l0, (int32_t)s});
+            } else {
+                const int64_t l0 = r + a * (u_end - 1);           // threads ascend as records descend
+                out.push_back(RPiece{(uint32_t)((l0 - run_base) / s), (uint32_t)len | wf, (int32_t)l0, (int32_t)s});
+            }
+            kind = 0;
+        };
+        for (size_t e = 0; e < ev.size();) {
+            const int64_t u = ev[e].u;
+            for (; e < ev.size() && ev[e].u == u; e++) {
+                const P &p = ps[ev[e].k];
+                auto &c = act[p.base];
+                c.first += ev[e].d;
+                c.second += p.w ? ev[e].d : 0;
+                writers += p.w ? ev[e].d : 0;
+                if (c.first == 0) act.erase(p.base);
+            }
+            // the state from u on
+            const int nk = act.empty() ? 0 : act.size() == 1 ? 1 : 2;
+            const int64_t nb = nk == 1 ? act.begin()->first : 0;
+            const bool nw = writers > 0;
+            if (nk != kind || nw != run_w || (nk == 1 && nb != run_base)) {
+                close(u);
+                if (nk) { kind = nk; run_u0 = u; run_base = nb; run_w = nw; }
+            }
+        }
+        close(ev.empty() ? 0 : ev.back().u);
+        g0 = g1;
+    }
+}
+
 void clear_range(BatchHost &out, size_t nprotos)
 {
     out.rpiece.clear();
+    out.wpiece.clear();
     out.rtask.clear();
     out.rlive.clear();
     out.rfirst.clear();
@@ -264,18 +351,29 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
         return;
     }
     std::stable_sort(ent.begin(), ent.end(), [](const E &x, const E &y) { return x.task < y.task; });
-    out.rpiece.reserve(ent.size());
-    std::vector<uint64_t> work;                      // record updates per task
+    out.wpiece.reserve(ent.size());
     for (size_t i = 0; i < ent.size(); i++) {
         if (i == 0 || ent[i].task != ent[i - 1].task) {
             out.rlive.push_back(ent[i].task);
             out.rfirst.push_back((uint32_t)i);
-            work.push_back(0);
         }
-        out.rpiece.push_back(ent[i].piece);
-        work.back() += ent[i].piece.lenf & kRLen;
+        out.wpiece.push_back(ent[i].piece);
     }
     if (!out.rlive.empty()) out.rfirst.push_back((uint32_t)ent.size());
+    // each task's pieces merged (merge_pieces): [mfirst[i], mfirst[i + 1])
+    // of rpiece, and the record updates they make
+    std::vector<uint32_t> mfirst;
+    std::vector<uint64_t> work;
+    std::vector<RPiece> tmp;
+    for (size_t i = 0; i < out.rlive.size(); i++) {
+        mfirst.push_back((uint32_t)out.rpiece.size());
+        merge_pieces(out.wpiece.data() + out.rfirst[i], out.rfirst[i + 1] - out.rfirst[i], tmp);
+        uint64_t w = 0;
+        for (const RPiece &x : tmp) w += x.lenf & kRLen;
+        out.rpiece.insert(out.rpiece.end(), tmp.begin(), tmp.end());
+        work.push_back(w);
+    }
+    mfirst.push_back((uint32_t)out.rpiece.size());
     // a task with much work is split into parts over disjoint blocks of its
     // records (a part per kRangeSplitWork record updates, assuming them
     // spread evenly), each taken by its own block; blocks take the parts
@@ -291,7 +389,7 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
         const uint32_t k = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(nblk, (work[i] + kRangeSplitWork - 1) / kRangeSplitWork));
         for (uint32_t q = 0; q < k; q++) {
             const uint32_t b0 = nblk * q / k, b1 = nblk * (q + 1) / k;
-            parts.push_back(Part{RTask{out.rlive[i], out.rfirst[i], out.rfirst[i + 1], b0 | (b1 << 16)}, work[i] / k});
+            parts.push_back(Part{RTask{out.rlive[i], mfirst[i], mfirst[i + 1], b0 | (b1 << 16)}, work[i] / k});
         }
     }
     std::stable_sort(parts.begin(), parts.end(), [](const Part &x, const Part &y) { return x.work > y.work; });
@@ -348,7 +446,8 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     const Section sec[] = {section(b.insns, end), section(b.xcode, end), section(b.items, end),
                            section(b.protos, end), section(b.cells, end), section(b.cbase, end),
                            section(b.witems, end), section(b.iphase, end), section(b.rpiece, end),
-                           section(b.rtask, end), section(b.rlive, end), section(b.rfirst, end)};
+                           section(b.rtask, end), section(b.rlive, end), section(b.rfirst, end),
+                           section(b.wpiece, end)};
     const size_t total = std::max<size_t>(end, 256);
     bool ok = ensure(image, total, &in_use, limit);
     // the previous copy out of the stage must be done before it is rewritten
@@ -416,6 +515,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.rtask = (const RTask *)(img + sec[9].off);
     a.rlive = (const uint32_t *)(img + sec[10].off);
     a.rfirst = (const uint32_t *)(img + sec[11].off);
+    a.wpiece = (const RPiece *)(img + sec[12].off);
     a.nlive = (uint32_t)b.rlive.size();
     a.nrtask = (uint32_t)b.rtask.size();
     a.range_on = 0;

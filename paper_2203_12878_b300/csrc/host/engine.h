@@ -62,12 +62,13 @@ struct BatchHost {
     bool all_static = false;
     // the range pass's work (BatchArgs::rpiece ..): per task of kRangeRecs
     // owner records that range accesses reach (rlive, ascending) its pieces
-    // [rfirst[i], rfirst[i + 1]) of rpiece, and the tasks again in the order
-    // blocks take them (rtask: most record updates first); the accesses'
-    // instructions carry AF_RANGE in `insns`.  range_pcs: per protocol, the
-    // pcs (in its own program) of its range accesses; range_tuples: the
-    // access tuples they make.
-    std::vector<RPiece> rpiece;
+    // as cut [rfirst[i], rfirst[i + 1]) of wpiece, and the tasks again (or
+    // their parts) in the order blocks take them (rtask: most record updates
+    // first) with their merged pieces in rpiece; the accesses' instructions
+    // carry AF_RANGE in `insns`.  range_pcs: per protocol, the pcs (in its
+    // own program) of its range accesses; range_tuples: the access tuples
+    // they make.
+    std::vector<RPiece> rpiece, wpiece;
     std::vector<RTask> rtask;
     std::vector<uint32_t> rlive, rfirst;
     std::vector<std::vector<uint32_t>> range_pcs;

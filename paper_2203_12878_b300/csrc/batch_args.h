@@ -32,7 +32,8 @@ enum : uint32_t {
 // One piece of the range pass's work: the threads t0 .. t0 + len - 1 of
 // one range access at one offset, whose records (relative to the first
 // record of their task) are l0, l0 + step, l0 + 2 step, ... (step: the
-// access's tid coefficient, never 0), and whether they write (kRWrite);
+// access's tid coefficient; 0 -- every thread at l0 -- only among the
+// pieces as cut, never among the merged ones), and whether they write (kRWrite);
 // lenf holds len and the flags.  With kRSat the piece stands for records
 // that two or more different threads reach: each gets the "second thread"
 // bit (and "written" with kRWrite), and t0 is unused.
@@ -60,14 +61,17 @@ struct RTask {
 // Floor of x / d for d > 0.
 DRF_HD inline long long range_floordiv(long long x, long long d) { return x >= 0 ? x / d : -((-x + d - 1) / d); }
 
-// The part of a piece (threads t0 + o, o < len, at records l0 + step * o,
-// step != 0) whose records lie in [w0, w1): its first thread, first record
-// and length (0 when none).
+// The part of a piece (threads t0 + o, o < len, at records l0 + step * o;
+// step 0: every thread at l0) whose records lie in [w0, w1): its first
+// thread, first record and length (0 when none).
 DRF_HD inline void range_clip(long long t0, long long l0, long long len, long long step, long long w0, long long w1,
                               long long &ct0, long long &cl0, long long &clen)
 {
     long long olo, ohi;                           // w0 <= l0 + step * o < w1
-    if (step > 0) {
+    if (step == 0) {
+        olo = 0;
+        ohi = l0 >= w0 && l0 < w1 ? len : 0;
+    } else if (step > 0) {
         olo = range_floordiv(w0 - l0 + step - 1, step);
         ohi = range_floordiv(w1 - l0 + step - 1, step);
     } else {

@@ -1583,11 +1583,21 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
                     const uint32_t e1 = __ldg(a.rfirst + lo + 1);
                     for (uint32_t e = __ldg(a.rfirst + lo) + t; e < e1; e += kFinalizeThreads) {
                         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.wpiece) + e);
-                        // x = l0 + step * o for some o < len
                         const long long d = x - (long long)(int32_t)v.z, st = (long long)(int32_t)v.w;
+                        const long long len = (long long)(v.y & kRLen);
+                        if (st == 0) {
+                            // every thread of the piece at l0: its two smallest
+                            if (d != 0 || len == 0) continue;
+                            for (uint32_t q = 0; q < 2 && q < len; q++) {
+                                two_smallest(t0, t1, v.x + q);
+                                if (v.y & kRWrite) two_smallest(w0, w1, v.x + q);
+                            }
+                            continue;
+                        }
+                        // x = l0 + step * o for some o < len
                         if (d % st != 0) continue;
                         const long long o = d / st;
-                        if (o < 0 || o >= (long long)(v.y & kRLen)) continue;
+                        if (o < 0 || o >= len) continue;
                         const uint32_t tid = v.x + (uint32_t)o;          // the piece's thread at the record
                         two_smallest(t0, t1, tid);
                         if (v.y & kRWrite) two_smallest(w0, w1, tid);

@@ -165,7 +165,7 @@ int range_runs(const RangeAccess &r, int64_t c, uint32_t T, Run out[2])
     auto add = [&](int64_t a, int64_t b, int64_t cell0) {
         if (a < b) out[n++] = Run{a, b - a, cell0};
     };
-    if (!r.modn) {
+    if (!r.modn || s == 0) {
         add(0, t, c);
         return n;
     }
@@ -200,13 +200,32 @@ bool range_candidate(const Prepared &p, const DevProto &d, unsigned __int128 &rt
 void merge_pieces(const RPiece *in, size_t n, std::vector<RPiece> &out)
 {
     out.clear();
+    // pieces of step 0 (every thread of the piece on one record): per
+    // record, one thread stays a one-record piece, two or more saturate it
+    struct Z { int32_t l0; uint32_t t0, t1; bool w; };     // threads [t0, t1)
+    std::vector<Z> zs;
+    for (size_t i = 0; i < n; i++)
+        if (in[i].step == 0 && (in[i].lenf & kRLen))
+            zs.push_back(Z{in[i].l0, in[i].t0, in[i].t0 + (in[i].lenf & kRLen), (in[i].lenf & kRWrite) != 0});
+    std::sort(zs.begin(), zs.end(), [](const Z &x, const Z &y) { return x.l0 < y.l0; });
+    for (size_t i = 0; i < zs.size();) {
+        size_t j = i;
+        bool w = false, many = false;
+        for (; j < zs.size() && zs[j].l0 == zs[i].l0; j++) {
+            w = w || zs[j].w;
+            many = many || zs[j].t1 - zs[j].t0 > 1 || zs[j].t0 != zs[i].t0;
+        }
+        const uint32_t wf = w ? kRWrite : 0u;
+        out.push_back(many ? RPiece{0u, 1u | kRSat | wf, zs[i].l0, 1} : RPiece{zs[i].t0, 1u | wf, zs[i].l0, 1});
+        i = j;
+    }
     struct P { int64_t s, a, r, base, u0, u1; bool w; };    // lattice coordinates u: record = r + a * u
     std::vector<P> ps;
     ps.reserve(n);
     for (size_t i = 0; i < n; i++) {
         const RPiece &x = in[i];
         const int64_t len = x.lenf & kRLen;
-        if (!len) continue;
+        if (!len || x.step == 0) continue;
         const int64_t s = x.step, a = s < 0 ? -s : s, l0 = x.l0;
         const int64_t r = ((l0 % a) + a) % a, ul = (l0 - r) / a;
         const int64_t u0 = s > 0 ? ul : ul - len + 1, u1 = s > 0 ? ul + len : ul + 1;

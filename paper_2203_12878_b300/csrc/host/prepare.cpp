@@ -787,7 +787,7 @@ struct RangeFinder {
             e = e->a.get();
         }
         i128 k = 0;
-        if (!tid_coef(*e, k) || k == 0 || k > kRangeMaxSigma || k < -kRangeMaxSigma) return;
+        if (!tid_coef(*e, k) || k > kRangeMaxSigma || k < -kRangeMaxSigma) return;
         // with a remainder, the index wraps at most once over the threads
         if (modn && (i128)(T ? T - 1 : 0) * (k < 0 ? -k : k) >= (i128)modn) return;
         RangeAccess r;

@@ -24,11 +24,12 @@ struct PrepareOpts {
 // An access the owner table's range pass can apply cell by cell: it runs in
 // one phase (no enclosing loop holds a sync), its enclosing loops' bounds
 // and conditions do not read tid, and its index is (sigma * tid + c) or
-// (sigma * tid + c) mod modn with sigma a non-zero integer of magnitude at
-// most kRangeMaxSigma and c a function of the loop variables alone (with a
-// remainder, (T - 1) * |sigma| < modn).  The threads that reach a given
-// range of cells in one iteration are then one or two runs of consecutive
-// tids, their cells sigma apart, found without visiting the others.
+// (sigma * tid + c) mod modn with sigma an integer of magnitude at most
+// kRangeMaxSigma (0: one cell for every thread) and c a function of the loop
+// variables alone (with a remainder, (T - 1) * |sigma| < modn).  The threads
+// that reach a given range of cells in one iteration are then one or two
+// runs of consecutive tids, their cells sigma apart, found without visiting
+// the others.
 constexpr int32_t kRangeMaxSigma = 64;
 struct RangeLoop {
     uint32_t reg;                 // the loop variable's register
@@ -39,7 +40,7 @@ struct RangeAccess {
     uint32_t pc;                  // its I_ACCESS or I_FASTACC instruction
     uint32_t phase, loc;
     bool write;
-    int32_t sigma;                // tid's coefficient: non-zero, |sigma| <= kRangeMaxSigma
+    int32_t sigma;                // tid's coefficient, |sigma| <= kRangeMaxSigma
     uint64_t modn;                // 0: no remainder; else the index is a Euclidean remainder by modn
     int32_t cexpr;                // expression code of the index before the remainder, at tid = 0
     std::vector<RangeLoop> loops; // enclosing loops, outermost first

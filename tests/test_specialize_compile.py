@@ -70,13 +70,13 @@ def test_range_pass_source_compiles(seed):
 def test_grid_scale_protocol_gets_the_range_pass():
     """Every access of the grid-scale protocol at a * tid plus a function of
     the loop variables (the owned writes with a = +-1, the reads with a in
-    -8..3) goes to the range pass: 220,790,784 of its 221,642,754 tuples;
-    the tid-free read D[5x - 6] (13 x 65,536) and the two guarded writes of
-    the planted race stay in the table pass."""
+    -8..3, the tid-free read D[5x - 6] with a = 0) goes to the range pass:
+    all of its 221,642,754 tuples but the two guarded writes of the planted
+    race, which stay in the table pass."""
     p = protogen.config3(0, racy=True)
     st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
     assert st == "OK"
-    assert a["range_tuples"] == 221642754 - 13 * 65536 - 2
+    assert a["range_tuples"] == 221642754 - 2
     st, src, log = drf.drf_protocol_specialize(drf.drf_protocol_compile(p.text), p.nthreads, p.cells, p.params)
     assert st == "OK", log
 

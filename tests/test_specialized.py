@@ -292,6 +292,19 @@ def test_strided_range_pass_against_oracle(rctx, oracle, chunk):
     assert kinds.count(3) >= 15, kinds
 
 
+@pytest.mark.parametrize("text,T,cells", [
+    ("array A;\nforU x in 0 .. 4 { rd A[x]; }\nsync;\nwr A[3];\n", 64, [8]),            # all threads write one cell
+    ("array A;\nforU x in 0 .. 9 { rd A[(x * 7) % 5]; }\n", 300, [5]),                  # shared reads only
+    ("array A, B;\nforU x in 0 .. 6 { rd A[x]; wr B[tid + 64 * x]; }\nwr A[5];\n", 64, [8, 512]),
+    ("array A;\nforU x in 0 .. 3 { wr A[2 * tid + x]; }\nsync;\nrd A[7];\n", 1, [8]),    # one thread
+])
+def test_range_pass_tid_free_accesses(rctx, oracle, text, T, cells):
+    """Accesses whose index does not depend on tid go to the range pass as
+    one record per offset, saturated when two or more threads reach it; the
+    witness comes from the two smallest threads of such a piece."""
+    assert check(rctx, oracle, protogen.Protocol(text, T, cells, [])) == 3
+
+
 def test_small_protocols_skip_the_range_pass_by_default(sctx, oracle):
     """Under 2^22 range tuples a check keeps the table pass alone (same
     results)."""
@@ -308,6 +321,6 @@ def test_config3_runs_the_range_pass(sctx):
         assert drf.drf_plan_info(plan)["kernels_per_launch"] == 6
         drf.drf_plan_launch(plan)
         tuples, updates = drf.drf_plan_range_tuples(plan)
-        assert tuples == 221642754 - 13 * 65536 - 2 and 0 < updates < tuples
+        assert tuples == 221642754 - 2 and 0 < updates < tuples
     finally:
         drf.drf_plan_destroy(plan)

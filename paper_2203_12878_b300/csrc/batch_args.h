@@ -166,6 +166,12 @@ struct BatchArgs {
     const uint32_t *rfirst;
     uint32_t nlive;
     uint32_t nrtask;                // entries of rtask (nlive or more: parts of split tasks)
+    // per protocol, the access tuples of its range accesses (host-counted);
+    // with rcount set the table pass counts only the other accesses and
+    // these are added (k_init per protocol, k_range the launch's rtotal)
+    const unsigned long long *rtup;
+    unsigned long long rtotal;
+    uint32_t rcount;
     uint32_t range_on;
     void *table;                     // [tab_cells] 32-bit owner records, padded to whole blocks
     uint64_t tab_cells;

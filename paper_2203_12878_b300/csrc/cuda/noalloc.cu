@@ -142,11 +142,15 @@ extern "C" int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_
     a.shard_lo = 0;
     a.shard_hi = ~0ull;
     a.rpiece = nullptr;                   // the sort path: no range pass
+    a.wpiece = nullptr;
     a.rtask = nullptr;
     a.rlive = nullptr;
     a.rfirst = nullptr;
     a.nlive = 0;
     a.nrtask = 0;
+    a.rtup = nullptr;
+    a.rtotal = 0;
+    a.rcount = 0;
     a.range_on = 0;
     a.nwitems = (uint32_t)nw;
     a.nprotos = 1;

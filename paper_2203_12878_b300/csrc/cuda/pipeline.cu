@@ -349,7 +349,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             } else if (ok) {
                 count++;
             }
-            if (TAB && ok) count++;
+            if (TAB && ok && !(rng && a.rcount)) count++;      // (range tuples: counted on the host)
             if (ok) pc++;
             break;
         }
@@ -361,6 +361,10 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             }
             break;
         case I_LOOP:
+            if (ex && (TAB || CELL) && a.range_on && (in.b & LB_RANGE_ONLY)) {
+                pc = (uint32_t)in.e + 1;            // the range pass has the whole loop
+                break;
+            }
             if (ex) {
                 V lo, hi;
                 if (!eval<V>(xc, in.c, tid, vars, lo) || !eval<V>(xc, in.d, tid, vars, hi)) {
@@ -409,7 +413,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                 if (okb) { count += (uint32_t)(trip * m); syncs += (uint32_t)(trip * in.b); }
             } else if (skip) {
                 if (okb) {
-                    if (TAB) count += (uint32_t)(trip * m);
+                    if (TAB && !a.rcount) count += (uint32_t)(trip * m);
                     phase += (uint32_t)(trip * in.b);
                 }
                 if (CELL && phase > tg.phase) running = false;
@@ -477,7 +481,12 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                     }
                 }
                 if (okb) phase += (uint32_t)(trip * spi);
-                if (TAB && okb) count += (uint32_t)(trip * m);
+                if (TAB && okb) {
+                    uint32_t mc = m;                  // range accesses' tuples are counted on the host
+                    if (a.rcount)
+                        for (uint32_t j = 0; j < m; j++) mc -= (meta[j] & AF_RANGE) ? 1u : 0u;
+                    count += (uint32_t)(trip * mc);
+                }
                 if (CELL && phase > tg.phase) running = false;
             }
             if (okb) pc = mpc + 1 + m;
@@ -561,7 +570,7 @@ __global__ void k_init(BatchArgs a)
         a.err_key[i] = kNone;
         a.div_tid[i] = 0xFFFFFFFFu;
         a.best_pos[i] = kNone;
-        a.ptuples[i] = 0;
+        a.ptuples[i] = a.rcount && a.rtup ? a.rtup[i] : 0ull;    // range tuples: counted on the host
     }
     if (i < (uint64_t)kMaxPasses * kRadixBins) a.hist[i] = 0;
     if (i < a.nwblocks) a.blocksum[i] = 0;
@@ -1506,6 +1515,7 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
     }
     __syncthreads();
     if (threadIdx.x == 0 && sh.updates) atomicAdd(&a.ctrl->range_tuples, sh.updates);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.rcount) atomicAdd(&a.ctrl->total, a.rtotal);
 }
 
 __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t x)
@@ -1771,8 +1781,21 @@ static bool schedule_missing(const BatchArgs &a, const JitLaunch *j)
     return a.nwitems && !a.witems && !(j && j->csched);
 }
 
-cudaError_t launch_front(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev, const JitLaunch *j)
+// The launch's arguments with rcount set when the table pass counts the
+// tuples (an interpreted launch without count pass, or specialized kernels
+// with static phases that leave the range accesses to the range pass) and
+// the range pass runs: the range accesses' tuples then come from the host.
+static BatchArgs with_rcount(const BatchArgs &a, const JitLaunch *j)
 {
+    BatchArgs b = a;
+    const bool jit_counts = j && j->table && j->static_phases;
+    b.rcount = a.range_on && a.path == PATH_TABLE && a.rtup && (jit_counts ? j->range : a.count_free != 0) ? 1u : 0u;
+    return b;
+}
+
+cudaError_t launch_front(const BatchArgs &a0, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev, const JitLaunch *j)
+{
+    const BatchArgs a = with_rcount(a0, j);
     if (schedule_missing(a, j)) return cudaErrorInvalidValue;
     uint64_t init_n = a.nprotos;
     if (init_n < (uint64_t)kMaxPasses * kRadixBins) init_n = (uint64_t)kMaxPasses * kRadixBins;
@@ -1810,9 +1833,10 @@ static void launch_interp_pdl(const BatchArgs &a, cudaStream_t s, int sms)
     if (a.has_wide) launch_pdl(k_interp<MODE, true>, dim3(interp_grid(a.nwitems, sms)), dim3(256), s, a);
 }
 
-static cudaError_t launch_back_table(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev,
+static cudaError_t launch_back_table(const BatchArgs &a0, cudaStream_t s, int sms, cudaEvent_t *ev, int *nev,
                                      const JitLaunch *j)
 {
+    const BatchArgs a = with_rcount(a0, j);
     if (j && j->table && j->range && !a.range_on) return cudaErrorInvalidValue;   // its range accesses would be lost
     if (j && j->table) launch_jit(j->table, a, j, s, sms);
     else launch_interp_pdl<M_TABLE>(a, s, sms);

@@ -32,7 +32,7 @@ enum : uint8_t {
     I_END = 0,
     I_ACCESS = 1,    // a: flags (AF_*), b: array, c: index expression
     I_SYNC = 2,
-    I_LOOP = 3,      // a: variable register, c: lo expression, d: hi expression, e: pc of the ENDLOOP
+    I_LOOP = 3,      // a: variable register, b: LB_* flags, c: lo expression, d: hi expression, e: pc of the ENDLOOP
     I_ENDLOOP = 4,   // a: variable register, c: first pc of the body
     I_IF = 5,        // c: condition expression, d: pc to continue at when false
     I_JUMP = 6,      // c: target pc
@@ -50,6 +50,12 @@ enum : uint8_t {
 };
 
 enum : uint8_t { FP_NONE = 0, FP_MASK = 1, FP_MOD = 2, FP_DIV = 3 };
+
+// I_LOOP flags, set when a batch is packed: LB_RANGE_ONLY -- the loop's body
+// holds no sync and no access but range accesses (AF_RANGE), so a launch
+// that runs the range pass need not enter it in the table and witness
+// passes (its tuples are counted on the host).
+enum : uint16_t { LB_RANGE_ONLY = 1 };
 constexpr uint32_t kFastMax = 4;    // accesses per fast loop body
 
 enum : uint8_t {

@@ -292,6 +292,25 @@ void merge_pieces(const RPiece *in, size_t n, std::vector<RPiece> &out)
     }
 }
 
+// Sets (or, with set false, clears) LB_RANGE_ONLY on every loop of one
+// protocol's program whose body holds no sync and only AF_RANGE accesses.
+void mark_range_loops(Insn *in, size_t n, bool set)
+{
+    for (size_t pc = 0; pc < n; pc++) {
+        if (in[pc].op != I_LOOP) continue;
+        if (!set) { in[pc].b &= (uint16_t)~LB_RANGE_ONLY; continue; }
+        const size_t e = (size_t)in[pc].e;
+        bool only = e < n;
+        for (size_t q = pc + 1; only && q <= e; q++) {
+            const Insn &x = in[q];
+            if (x.op == I_SYNC || x.op == I_END) only = false;
+            else if ((x.op == I_ACCESS || x.op == I_FASTACC) && !(x.a & AF_RANGE)) only = false;
+            else if (x.op == I_FASTLOOP && x.b != 0) only = false;
+        }
+        if (only) in[pc].b |= LB_RANGE_ONLY;
+    }
+}
+
 void clear_range(BatchHost &out, size_t nprotos)
 {
     out.rpiece.clear();
@@ -301,6 +320,7 @@ void clear_range(BatchHost &out, size_t nprotos)
     out.rfirst.clear();
     out.range_pcs.assign(nprotos, {});
     out.range_tuples = 0;
+    out.rtup.clear();
 }
 
 }  // namespace
@@ -361,11 +381,16 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
             continue;
         }
         for (uint32_t pc : out.range_pcs[i]) out.insns[d.insn_off + pc].a |= AF_RANGE;
+        mark_range_loops(&out.insns[d.insn_off], p.insns.size(), true);
         out.range_tuples += tuples;
+        if (out.rtup.empty()) out.rtup.assign(ps.size(), 0);
+        out.rtup[i] = tuples;
     }
     if (out.range_tuples < range_min) {              // protocols left out: under the minimum after all
-        for (size_t i = 0; i < ps.size(); i++)
+        for (size_t i = 0; i < ps.size(); i++) {
             for (uint32_t pc : out.range_pcs[i]) out.insns[out.protos[i].insn_off + pc].a &= (uint8_t)~AF_RANGE;
+            if (!out.range_pcs[i].empty()) mark_range_loops(&out.insns[out.protos[i].insn_off], ps[i]->insns.size(), false);
+        }
         clear_range(out, ps.size());
         return;
     }
@@ -466,7 +491,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
                            section(b.protos, end), section(b.cells, end), section(b.cbase, end),
                            section(b.witems, end), section(b.iphase, end), section(b.rpiece, end),
                            section(b.rtask, end), section(b.rlive, end), section(b.rfirst, end),
-                           section(b.wpiece, end)};
+                           section(b.wpiece, end), section(b.rtup, end)};
     const size_t total = std::max<size_t>(end, 256);
     bool ok = ensure(image, total, &in_use, limit);
     // the previous copy out of the stage must be done before it is rewritten
@@ -535,6 +560,9 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.rlive = (const uint32_t *)(img + sec[10].off);
     a.rfirst = (const uint32_t *)(img + sec[11].off);
     a.wpiece = (const RPiece *)(img + sec[12].off);
+    a.rtup = b.rtup.empty() ? nullptr : (const unsigned long long *)(img + sec[13].off);
+    a.rtotal = b.rtup.empty() ? 0ull : b.range_tuples;
+    a.rcount = 0;
     a.nlive = (uint32_t)b.rlive.size();
     a.nrtask = (uint32_t)b.rtask.size();
     a.range_on = 0;

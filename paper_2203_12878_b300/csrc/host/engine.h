@@ -73,6 +73,7 @@ struct BatchHost {
     std::vector<uint32_t> rlive, rfirst;
     std::vector<std::vector<uint32_t>> range_pcs;
     uint64_t range_tuples = 0;
+    std::vector<unsigned long long> rtup;      // per protocol: the tuples of its range accesses
     uint64_t table_bytes() const { return table_cells * 4; }   // one 32-bit owner record per cell
 };
 

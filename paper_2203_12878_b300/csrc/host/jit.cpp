@@ -360,7 +360,9 @@ class Gen {
             body_ << "        if (" << idx.back() << " < 0 || (uint64_t)(" << U_ << ")" << idx.back() << " >= "
                   << ulit(p_.cells.at(A.b)) << ") goto done;\n";
         }
-        body_ << "        nacc += " << (end - pc) << "u;\n";
+        uint32_t kept_run = 0;                 // (the range pass's tuples are counted on the host)
+        for (uint32_t q = pc; q < end; q++) kept_run += skip_.count(q) ? 0u : 1u;
+        if (kept_run) body_ << "        nacc += " << kept_run << "u;\n";
         body_ << "        const bool kr = phase < " << d_.tab_phases << "u;\n";
         body_ << "        if (!kr) atomicOr(&a.ctrl->flags, (unsigned)drf::CF_TABLE_RANGE);\n";
         std::vector<Slot> S;
@@ -374,6 +376,22 @@ class Gen {
         }
         updates(S);
         body_ << "    }\n";
+        return true;
+    }
+
+    // Whether the loop at pc holds no sync and no access but the range
+    // pass's (the host's LB_RANGE_ONLY rule, on this program).
+    bool range_only_loop(uint32_t pc) const
+    {
+        if (skip_.empty()) return false;
+        const uint32_t e = (uint32_t)p_.insns.at(pc).e;
+        if (e >= p_.insns.size()) return false;
+        for (uint32_t q = pc + 1; q <= e; q++) {
+            const Insn &x = p_.insns[q];
+            if (x.op == I_SYNC || x.op == I_END) return false;
+            if ((x.op == I_ACCESS || x.op == I_FASTACC) && !skip_.count(q)) return false;
+            if (x.op == I_FASTLOOP && x.b != 0) return false;
+        }
         return true;
     }
 
@@ -407,6 +425,10 @@ class Gen {
             if (mode_ == GM_CELL) body_ << "    if (phase > tg.phase) goto done;\n";
             return true;
         case I_LOOP: {
+            if (mode_ == GM_TABLE && range_only_loop(pc)) {
+                next = (uint32_t)in.e + 1;        // the range pass has the whole loop
+                return true;
+            }
             body_ << "    {\n";
             std::string lo = expr(in.c), hi = expr(in.d);
             if (!error.empty()) return false;
@@ -483,8 +505,8 @@ class Gen {
             uint32_t kept = 0;
             for (uint32_t j = 0; j < m; j++) kept += skip_.count(pc + 1 + j) ? 0 : 1;
             if (mode_ == GM_TABLE && kept == 0) {
-                // every access of the loop is the range pass's: count them
-                body_ << "        nacc += (uint32_t)(trip * " << m << "u);\n";
+                // every access of the loop is the range pass's (its tuples are
+                // counted on the host)
                 if (spi) body_ << "        phase += (uint32_t)(trip * " << spi << "u);\n";
                 body_ << "        }\n    }\n";
                 return true;
@@ -498,7 +520,7 @@ class Gen {
                 // pass occupancy hides the claims' round trips better (groups
                 // of 2, 4, 8, 16 accesses measured 3-30% slower)
                 const uint32_t UF = 1;
-                body_ << "        nacc += (uint32_t)(trip * " << m << "u);\n";
+                body_ << "        nacc += (uint32_t)(trip * " << kept << "u);\n";
                 body_ << "        for (uint64_t t = 0; t < trip; t += " << UF << "u) {\n";
                 std::vector<Slot> S;
                 std::vector<std::string> acts, ks;

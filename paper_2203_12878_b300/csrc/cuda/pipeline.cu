@@ -1561,6 +1561,7 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
         if (TABLE) {
             // this protocol's bits: [tid_off, tid_off + T) of the hit arrays
             const uint64_t b0 = P.tid_off, b1 = P.tid_off + P.nthreads;
+#pragma unroll 4
             for (uint64_t wd = (b0 >> 5) + t; wd <= ((b1 - 1) >> 5); wd += kFinalizeThreads) {
                 uint32_t ma = __ldcg(a.hit_acc + wd), mw = __ldcg(a.hit_wr + wd);
                 const uint64_t lo = wd * 32;
@@ -1583,12 +1584,20 @@ __global__ void __launch_bounds__(THREADS) k_finalize(BatchArgs a)
                 // (the interpreted witness pass skips them): the threads of
                 // the pieces of the racy record's task that land on it
                 const unsigned long long task = bp / kRangeRecs;
-                uint32_t lo = 0, hi = a.nlive;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) / 2;
-                    if (__ldg(a.rlive + mid) < task) lo = mid + 1; else hi = mid;
-                }
-                if (lo < a.nlive && __ldg(a.rlive + lo) == task) {
+                // the task's index in rlive (ascending), in two rounds of loads:
+                // the slice of rlive (one per thread) that can hold it, then
+                // its entries side by side
+                __shared__ uint32_t s_slice, s_li;
+                if (t == 0) { s_slice = 0; s_li = 0xFFFFFFFFu; }
+                __syncthreads();
+                const uint32_t per = (a.nlive + kFinalizeThreads - 1) / kFinalizeThreads;
+                if (t * per < a.nlive && __ldg(a.rlive + t * per) <= task) atomicMax(&s_slice, t);
+                __syncthreads();
+                for (uint32_t q = s_slice * per + t; q < s_slice * per + per && q < a.nlive; q += kFinalizeThreads)
+                    if (__ldg(a.rlive + q) == task) s_li = q;
+                __syncthreads();
+                const uint32_t lo = s_li;
+                if (lo != 0xFFFFFFFFu) {
                     const long long x = (long long)(bp - task * kRangeRecs);
                     const uint32_t e1 = __ldg(a.rfirst + lo + 1);
                     for (uint32_t e = __ldg(a.rfirst + lo) + t; e < e1; e += kFinalizeThreads) {
@@ -1858,9 +1867,9 @@ static cudaError_t launch_back_table(const BatchArgs &a0, cudaStream_t s, int sm
     if (j && j->cell) launch_jit(j->cell, a, j, s, sms);
     else launch_interp_pdl<M_CELL>(a, s, sms);
     mark(ev, nev, s);
-    // specialized kernels with static phases write the result from the
-    // witness pass's last block
-    if (!(j && j->cell && j->static_phases)) {
+    // specialized kernels with static phases and no range pass write the
+    // result from the witness pass's last block
+    if (!(j && j->cell && j->static_phases && !j->range)) {
         launch_pdl(k_finalize<true>, dim3(a.nprotos), dim3(kFinalizeThreads), s, a);
         mark(ev, nev, s);
     }
@@ -1908,13 +1917,13 @@ int stage_names(const char **names, int cap, uint32_t passes, uint32_t path, boo
         all[n++] = "table";
         if (range) all[n++] = "range";
         all[n++] = "tscan";
-        all[n++] = static_phases ? "witness+finalize" : "witness";
+        all[n++] = static_phases && !range ? "witness+finalize" : "witness";
     } else {
         all[n++] = "emit";
         for (uint32_t q = 0; q < passes && q < (uint32_t)kMaxPasses; q++) all[n++] = radix[q];
         all[n++] = "detect";
     }
-    if (!(static_phases && path == PATH_TABLE)) all[n++] = "finalize";
+    if (!(static_phases && path == PATH_TABLE && !range)) all[n++] = "finalize";
     for (int i = 0; i < n && i < cap; i++) names[i] = all[i];
     return n;
 }

@@ -900,7 +900,9 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
     if (kernels_per_launch) {
         uint32_t widths = plan->dev.args.has_narrow + plan->dev.args.has_wide;
         const uint32_t range = table && plan->dev.args.range_on ? 1 : 0;      // the range pass
-        if (table && plan->dev.jit.static_phases) *kernels_per_launch = 5 + range;   // init, table, tlist, tscan, witness + finalize
+        // init, table, (range,) tlist, tscan, witness + finalize (with the
+        // range pass the finalize pass is its own kernel)
+        if (table && plan->dev.jit.static_phases) *kernels_per_launch = 5 + 2 * range;
         else if (table && plan->dev.args.count_free) *kernels_per_launch = 2 * widths + 4 + range;   // init, 2x interp, tlist, tscan, finalize
         else if (table) *kernels_per_launch = 3 * widths + 5 + range;   // init, 3x interp, scan, tlist, tscan, finalize
         else *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes;   // init, 2x interp, scan, passes, detect, resolve, finalize

@@ -2,6 +2,7 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <cstring>
 #include <numeric>
@@ -37,9 +38,16 @@ void release(DevBuf &b, size_t *in_use)
     b.cap = 0;
 }
 
+void BatchHost::renew()
+{
+    static std::atomic<uint64_t> counter{0};
+    version = ++counter;
+}
+
 void BatchHost::expand_witems()
 {
     if (expanded()) return;
+    renew();
     witems.resize(nwitems);
     WarpItem *wi = witems.data();
     for (const Run &r : runs)
@@ -146,6 +154,7 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
     out.nwitems = nwitems;
     if (expand) out.expand_witems();
     if (out.table_ok) plan_range(ps, out, range_min);
+    out.renew();
     return Error{};
 }
 
@@ -494,9 +503,12 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
                            section(b.wpiece, end), section(b.rtup, end)};
     const size_t total = std::max<size_t>(end, 256);
     bool ok = ensure(image, total, &in_use, limit);
+    // the stage already holds this image (the same pack loaded again): it is
+    // copied to the device as it is
+    const bool restage = !(b.version && staged_version == b.version && stage && stage_cap >= total);
     // the previous copy out of the stage must be done before it is rewritten
-    if (ok && staged_pending) ok = cudaEventSynchronize(staged) == cudaSuccess;
-    staged_pending = false;
+    if (ok && staged_pending && restage) ok = cudaEventSynchronize(staged) == cudaSuccess;
+    if (restage) staged_pending = false;
     if (ok && stage_cap < total) {
         const size_t want = std::max(total, stage_cap + stage_cap / 4);
         if (stage) cudaFreeHost(stage);
@@ -508,8 +520,12 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     }
     if (ok && !staged) ok = cudaEventCreateWithFlags(&staged, cudaEventDisableTiming) == cudaSuccess;
     if (ok) {
-        for (const Section &x : sec)
-            if (x.bytes) std::memcpy((char *)stage + x.off, x.src, x.bytes);
+        if (restage) {
+            staged_version = 0;
+            for (const Section &x : sec)
+                if (x.bytes) std::memcpy((char *)stage + x.off, x.src, x.bytes);
+            staged_version = b.version;
+        }
         ok = cudaMemcpyAsync(image.p, stage, end ? end : 16, cudaMemcpyHostToDevice, s) == cudaSuccess &&
              cudaEventRecord(staged, s) == cudaSuccess;
         staged_pending = ok;

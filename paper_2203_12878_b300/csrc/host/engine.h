@@ -49,6 +49,11 @@ struct BatchHost {
     std::vector<WarpItem> witems;
     bool expanded() const { return witems.size() == nwitems; }
     void expand_witems();
+    // a number no other image content had (process-wide), renewed whenever
+    // the image changes: a device batch that staged this version need not
+    // stage it again
+    uint64_t version = 0;
+    void renew();
     uint64_t ncols = 0;
     uint64_t lanes = 0;
     uint64_t tuple_bound = 0;
@@ -110,6 +115,7 @@ struct DeviceBatch {
     size_t stage_cap = 0;
     cudaEvent_t staged = nullptr;     // recorded after the copy out of `stage`
     bool staged_pending = false;
+    uint64_t staged_version = 0;      // BatchHost::version the stage holds (0: none)
     DevBuf cnt, syn, phs, erro, totsyn, wcnt, wbase, blocksum;
     DevBuf keys0, keys1, hist, status, trec;
     DevBuf err_key, div_tid, best_pos, ptuples, epoch;

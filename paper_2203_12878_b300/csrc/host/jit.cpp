@@ -403,6 +403,7 @@ class Gen {
             return true;
         case I_ACCESS: {
             if (mode_ == GM_TABLE) return access_run(k, pc, next);
+            if (mode_ == GM_CELL && skip_.count(pc)) return true;     // its witnesses come from the range pass
             const bool write = (in.a & AF_WRITE) != 0;
             body_ << "    {\n";
             if (mode_ == GM_COUNT && !(in.a & AF_EVAL_IN_COUNT)) {
@@ -425,8 +426,8 @@ class Gen {
             if (mode_ == GM_CELL) body_ << "    if (phase > tg.phase) goto done;\n";
             return true;
         case I_LOOP: {
-            if (mode_ == GM_TABLE && range_only_loop(pc)) {
-                next = (uint32_t)in.e + 1;        // the range pass has the whole loop
+            if (mode_ != GM_COUNT && range_only_loop(pc)) {
+                next = (uint32_t)in.e + 1;        // the range pass has the whole loop (and its witnesses)
                 return true;
             }
             body_ << "    {\n";
@@ -574,8 +575,11 @@ class Gen {
             // solutions are x0 + i * (n / g), x0 from the inverse of coef / g
             // modulo n / g -- constants of the access, computed here.  Other
             // accesses iterate the loop.
+            // (accesses the range pass applies give their witnesses there)
             std::vector<bool> solved(m, false);
+            for (uint32_t j = 0; j < m; j++) solved[j] = skip_.count(pc + 1 + j) != 0;
             for (uint32_t j = 0; j < m && spi == 0; j++) {
+                if (solved[j]) continue;
                 const Insn &A = p_.insns.at(pc + 1 + j);
                 const uint32_t post = (A.a >> 2) & 3;
                 const int64_t pk = (int64_t)p_.xcode.at((size_t)A.d + 1);
@@ -635,6 +639,7 @@ class Gen {
             for (uint32_t j = 0; j < m; j++) all_solved = all_solved && solved[j];
             if (spi) {
                 for (uint32_t j = 0; j < m; j++) {
+                    if (solved[j]) continue;
                     const Insn &A = p_.insns.at(pc + 1 + j);
                     body_ << "        {\n"
                           << "        const long long dt = (long long)tg.phase - (long long)phase - " << (uint32_t)A.e << "ll;\n"
@@ -965,9 +970,9 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
           << "    }\n}\n";
     }
     // witness pass: which threads access / write the first racy cell; with
-    // static phases its last block to finish also writes the result (the
-    // finalize pass of the interpreted pipeline), so the launch needs no
-    // further kernel
+    // static phases and no range pass its last block to finish also writes
+    // the result (the finalize pass of the interpreted pipeline), so the
+    // launch needs no further kernel
     o << "extern \"C\" __global__ void __launch_bounds__(256) drf_cell" << sig
       << "    const unsigned long long bp = __ldcg(&a.best_pos[0]);\n"
       << "    const bool live = !(bp == ~0ull || __ldcg(&a.err_key[0]) != ~0ull || __ldcg(&a.div_tid[0]) != 0xFFFFFFFFu);\n"
@@ -1027,7 +1032,9 @@ Error jit_source(const Prepared &p, const BatchHost &b, std::string &src, std::v
     }
     }
 )DRF";
-    if (stat) {
+    // (with the range pass the interpreted finalize pass runs instead: it
+    // adds the witnesses the range pass holds)
+    if (stat && !range) {
         // the last block: the two smallest accessors and writers of the cell
         // from the hit bits (static phases: no evaluation error or barrier
         // divergence can occur), then the protocol's result

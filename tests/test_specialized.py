@@ -317,8 +317,8 @@ def test_config3_runs_the_range_pass(sctx):
     plan = drf.drf_plan_create(sctx, [drf.drf_protocol_compile(p.text)], [(p.nthreads, p.cells, p.params)])
     try:
         assert drf.drf_plan_specialized(plan)[0] == 3
-        # init, table, range, touch listing, table scan, witness + result
-        assert drf.drf_plan_info(plan)["kernels_per_launch"] == 6
+        # init, table, range, touch listing, table scan, witness, result
+        assert drf.drf_plan_info(plan)["kernels_per_launch"] == 7
         drf.drf_plan_launch(plan)
         tuples, updates = drf.drf_plan_range_tuples(plan)
         assert tuples == 221642754 - 2 and 0 < updates < tuples

@@ -316,6 +316,14 @@ def roofline(kinds, steps, n, info, dev, clocks):
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                 "traffic": traffic, "launch_ms": round(dom_ms, 4),
                 "algorithmic_bytes_per_launch": bytes_per[dominant]}
+        # the sort pipeline as a whole: algorithmic key bytes per tuple
+        # (emit writes 8, each radix pass reads and writes 16, detection
+        # reads 8) and each stage's share of HBM at its measured time
+        npass = len(radix_launches) // steps if radix_launches else 0
+        roof["bytes_per_tuple"] = 8 + 16 * npass + 8
+        roof["stage_hbm_frac"] = {
+            k: round(bytes_per[k] * (npass if k == "radix" else 1) / (totals[k] * 1e-3) / 1e9 / peak, 4)
+            for k in bytes_per if totals.get(k)}
     elif dominant in ("table", "emit", "count", "witness", "range"):
         # the range pass applies its share of the tuples (counted on the
         # device); the table pass then applies the rest
@@ -325,7 +333,8 @@ def roofline(kinds, steps, n, info, dev, clocks):
         ops = TABLE_OPS_PER_TUPLE * units
         achieved = ops / (dom_ms * 1e-3) / 1e12
         peak_ops, src = alu_peak(dev, clocks)
-        kernel = (f"drf_{dominant} (specialized)" if info.get("specialized") and dominant in ("table", "range")
+        kernel = ("k_range" if dominant == "range"
+                  else f"drf_{dominant} (specialized)" if info.get("specialized") and dominant == "table"
                   else f"k_interp<{dominant}>")
         roof = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3), "peak": round(peak_ops / 1e12, 2),
                 "unit": "Tops/s", "frac": round(achieved * 1e12 / peak_ops, 4), "peak_source": f"derived: {src}",

@@ -172,9 +172,13 @@ typedef struct {
  * interpreter. */
 #define DRF_OPT_SPECIALIZE     0x10u
 /* The owner table's range pass (drf_plan_specialized) for batches of any
- * size.  By default a batch takes it only when its range accesses make 2^22
- * access tuples or more: below that, planning its work lists, uploading them
- * and the extra kernel cost more than the table pass they relieve.  Results
+ * size, checked by any entry point.  By default plans and single-protocol
+ * checks take it when its range accesses make 2^22 access tuples or more
+ * (below that, planning its work lists, uploading them and the extra kernel
+ * cost more than the table pass they relieve; a repeated drf_check of one
+ * protocol plans it once), and checks of several protocols at once and the
+ * server's rounds do not (the host planning of a batch checked once, about
+ * 0.1 ms per protocol, costs more than the device time it saves).  Results
  * are the same either way. */
 #define DRF_OPT_RANGE_ANY      0x20u
 

@@ -195,7 +195,7 @@ constexpr int kDetectThreads = 256;
 constexpr int kDetectItems = 16;
 constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 4096 keys
 constexpr int kFinalizeThreads = 128;
-constexpr int kFinalizeWideThreads = 1024;   // sort-path finalize blocks of a batch of at most kFinalizeWideProtos
+constexpr int kFinalizeWideThreads = 1024;   // finalize blocks of a batch of at most kFinalizeWideProtos
 constexpr uint32_t kFinalizeWideProtos = 16;
 constexpr int kScanThreads = 256;
 constexpr int kWScanPerBlock = 4096;                        // warp-items per scan block

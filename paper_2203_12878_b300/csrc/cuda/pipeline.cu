@@ -1870,7 +1870,12 @@ static cudaError_t launch_back_table(const BatchArgs &a0, cudaStream_t s, int sm
     // specialized kernels with static phases and no range pass write the
     // result from the witness pass's last block
     if (!(j && j->cell && j->static_phases && !j->range)) {
-        launch_pdl(k_finalize<true>, dim3(a.nprotos), dim3(kFinalizeThreads), s, a);
+        // a few protocols: wide blocks, so that each protocol's hit words
+        // and witness search take few rounds of loads
+        if (a.nprotos <= kFinalizeWideProtos)
+            launch_pdl(k_finalize<true, kFinalizeWideThreads>, dim3(a.nprotos), dim3(kFinalizeWideThreads), s, a);
+        else
+            launch_pdl(k_finalize<true>, dim3(a.nprotos), dim3(kFinalizeThreads), s, a);
         mark(ev, nev, s);
     }
     return cudaGetLastError();

@@ -293,7 +293,8 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
                            ctx->host_digit_bits == ctx->opts.radix_bits && (bh.expanded() || jit_try);
     if (!same_pack) {
         ctx->host_of.reset();
-        e = pack_batch(valid, bh, !jit_try, ctx->opts.radix_bits, range_min_of(ctx->opts));
+        e = pack_batch(valid, bh, !jit_try, ctx->opts.radix_bits,
+                       valid.size() == 1 ? range_min_of(ctx->opts) : range_min_once(ctx->opts));
         if (e.ok() && valid.size() == 1) {
             ctx->host_of = preps[where[0]];
             ctx->host_digit_bits = ctx->opts.radix_bits;
@@ -302,7 +303,7 @@ int drf_check_batch(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, c
     if (e.status == S_KEY_TOO_WIDE && valid.size() > 1) {
         // the combined key does not fit: check the protocols one by one
         for (size_t j = 0; j < valid.size(); j++) {
-            Error ej = pack_batch({valid[j]}, bh, true, ctx->opts.radix_bits, range_min_of(ctx->opts));
+            Error ej = pack_batch({valid[j]}, bh, true, ctx->opts.radix_bits, range_min_once(ctx->opts));
             if (!ej.ok()) { error_result(ej.status, &out[where[j]]); continue; }
             std::vector<DevResult> r;
             int st = run_batch(ctx, bh, s, r);

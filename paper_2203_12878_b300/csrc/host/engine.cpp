@@ -3,7 +3,6 @@
 
 #include <algorithm>
 #include <atomic>
-#include <map>
 #include <cstring>
 #include <numeric>
 
@@ -212,7 +211,8 @@ void merge_pieces(const RPiece *in, size_t n, std::vector<RPiece> &out)
     // pieces of step 0 (every thread of the piece on one record): per
     // record, one thread stays a one-record piece, two or more saturate it
     struct Z { int32_t l0; uint32_t t0, t1; bool w; };     // threads [t0, t1)
-    std::vector<Z> zs;
+    static thread_local std::vector<Z> zs;                  // (scratch kept between calls)
+    zs.clear();
     for (size_t i = 0; i < n; i++)
         if (in[i].step == 0 && (in[i].lenf & kRLen))
             zs.push_back(Z{in[i].l0, in[i].t0, in[i].t0 + (in[i].lenf & kRLen), (in[i].lenf & kRWrite) != 0});
@@ -229,8 +229,8 @@ void merge_pieces(const RPiece *in, size_t n, std::vector<RPiece> &out)
         i = j;
     }
     struct P { int64_t s, a, r, base, u0, u1; bool w; };    // lattice coordinates u: record = r + a * u
-    std::vector<P> ps;
-    ps.reserve(n);
+    static thread_local std::vector<P> ps;
+    ps.clear();
     for (size_t i = 0; i < n; i++) {
         const RPiece &x = in[i];
         const int64_t len = x.lenf & kRLen;
@@ -244,7 +244,11 @@ void merge_pieces(const RPiece *in, size_t n, std::vector<RPiece> &out)
         return x.s != y.s ? x.s < y.s : x.r != y.r ? x.r < y.r : x.u0 < y.u0;
     });
     struct Ev { int64_t u; int d; size_t k; };
-    std::vector<Ev> ev;
+    static thread_local std::vector<Ev> ev;
+    // active pieces per base (count, writers): a few at a time, kept in a
+    // short list
+    struct Act { int64_t base; int cnt, wr; };
+    static thread_local std::vector<Act> act;
     for (size_t g0 = 0; g0 < ps.size();) {
         size_t g1 = g0;
         while (g1 < ps.size() && ps[g1].s == ps[g0].s && ps[g1].r == ps[g0].r) g1++;
@@ -255,8 +259,7 @@ void merge_pieces(const RPiece *in, size_t n, std::vector<RPiece> &out)
             ev.push_back(Ev{ps[k].u1, -1, k});
         }
         std::sort(ev.begin(), ev.end(), [](const Ev &x, const Ev &y) { return x.u < y.u; });
-        // active pieces per base: (count, writers)
-        std::map<int64_t, std::pair<int, int>> act;
+        act.clear();
         int writers = 0;
         // the output run being extended: kind 0 none, 1 one base, 2 saturated
         int kind = 0;
@@ -281,15 +284,17 @@ void merge_pieces(const RPiece *in, size_t n, std::vector<RPiece> &out)
             const int64_t u = ev[e].u;
             for (; e < ev.size() && ev[e].u == u; e++) {
                 const P &p = ps[ev[e].k];
-                auto &c = act[p.base];
-                c.first += ev[e].d;
-                c.second += p.w ? ev[e].d : 0;
+                size_t q = 0;
+                while (q < act.size() && act[q].base != p.base) q++;
+                if (q == act.size()) act.push_back(Act{p.base, 0, 0});
+                act[q].cnt += ev[e].d;
+                act[q].wr += p.w ? ev[e].d : 0;
                 writers += p.w ? ev[e].d : 0;
-                if (c.first == 0) act.erase(p.base);
+                if (act[q].cnt == 0) { act[q] = act.back(); act.pop_back(); }
             }
             // the state from u on
             const int nk = act.empty() ? 0 : act.size() == 1 ? 1 : 2;
-            const int64_t nb = nk == 1 ? act.begin()->first : 0;
+            const int64_t nb = nk == 1 ? act[0].base : 0;
             const bool nw = writers > 0;
             if (nk != kind || nw != run_w || (nk == 1 && nb != run_base)) {
                 close(u);
@@ -858,6 +863,8 @@ int path_pref_of(const drf_opts &o)
 }
 
 uint64_t range_min_of(const drf_opts &o) { return (o.flags & DRF_OPT_RANGE_ANY) ? 0 : kRangeMinTuples; }
+
+uint64_t range_min_once(const drf_opts &o) { return (o.flags & DRF_OPT_RANGE_ANY) ? 0 : ~0ull; }
 
 int run_batch(drf_ctx *ctx, const BatchHost &b, cudaStream_t s, std::vector<DevResult> &out)
 {

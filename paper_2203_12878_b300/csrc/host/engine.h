@@ -254,6 +254,9 @@ constexpr uint64_t kJitMinTuples = 1ull << 21;
 int path_pref_of(const drf_opts &o);
 // Fewest range-pass tuples a batch needs to take the pass under these options.
 uint64_t range_min_of(const drf_opts &o);
+// The same for a batch of several protocols checked once (drf_check_batch,
+// the server's rounds): none without DRF_OPT_RANGE_ANY.
+uint64_t range_min_once(const drf_opts &o);
 
 void to_public(const DevResult &d, drf_result *out);
 

@@ -255,7 +255,7 @@ private:
         std::string err;
         std::vector<DevResult> dr;
         std::vector<const Prepared *> part(ps.begin() + (long)lo, ps.begin() + (long)hi);
-        Error e = pack_batch(part, bh, true, ctx_->opts.radix_bits, range_min_of(ctx_->opts));
+        Error e = pack_batch(part, bh, true, ctx_->opts.radix_bits, range_min_once(ctx_->opts));
         int st = e.status;
         if (e.ok()) st = run_batch(lane.dev, ctx_->sms, lane.s, bh, dr, err);
         if (st == S_OK) {

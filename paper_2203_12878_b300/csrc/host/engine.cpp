@@ -492,8 +492,9 @@ Section section(const std::vector<T> &v, size_t &end)
 
 }  // namespace
 
-Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
+Error DeviceBatch::load(const BatchHost &b, cudaStream_t s, bool schedule)
 {
+    static const std::vector<WarpItem> no_witems;
     const uint64_t np = b.protos.size();
     const uint64_t nw = b.nwitems;
     const uint32_t nwblocks = (uint32_t)std::max<uint64_t>(1, (nw + kWScanPerBlock - 1) / kWScanPerBlock);
@@ -503,14 +504,15 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     size_t end = 0;
     const Section sec[] = {section(b.insns, end), section(b.xcode, end), section(b.items, end),
                            section(b.protos, end), section(b.cells, end), section(b.cbase, end),
-                           section(b.witems, end), section(b.iphase, end), section(b.rpiece, end),
+                           section(schedule ? b.witems : no_witems, end), section(b.iphase, end), section(b.rpiece, end),
                            section(b.rtask, end), section(b.rlive, end), section(b.rfirst, end),
                            section(b.wpiece, end), section(b.rtup, end)};
     const size_t total = std::max<size_t>(end, 256);
     bool ok = ensure(image, total, &in_use, limit);
     // the stage already holds this image (the same pack loaded again): it is
     // copied to the device as it is
-    const bool restage = !(b.version && staged_version == b.version && stage && stage_cap >= total);
+    const bool restage = !(b.version && staged_version == b.version && staged_schedule == schedule && stage &&
+                           stage_cap >= total);
     // the previous copy out of the stage must be done before it is rewritten
     if (ok && staged_pending && restage) ok = cudaEventSynchronize(staged) == cudaSuccess;
     if (restage) staged_pending = false;
@@ -530,6 +532,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
             for (const Section &x : sec)
                 if (x.bytes) std::memcpy((char *)stage + x.off, x.src, x.bytes);
             staged_version = b.version;
+            staged_schedule = schedule;
         }
         ok = cudaMemcpyAsync(image.p, stage, end ? end : 16, cudaMemcpyHostToDevice, s) == cudaSuccess &&
              cudaEventRecord(staged, s) == cudaSuccess;
@@ -573,7 +576,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s)
     a.cells = (const uint64_t *)(img + sec[4].off);
     a.cbase = (const uint64_t *)(img + sec[5].off);
     // without its expansion, kernels that read the schedule refuse to launch
-    a.witems = b.expanded() ? (const WarpItem *)(img + sec[6].off) : nullptr;
+    a.witems = schedule && b.expanded() ? (const WarpItem *)(img + sec[6].off) : nullptr;
     a.iphase = (const uint32_t *)(img + sec[7].off);
     a.count_free = 0;
     a.rpiece = (const RPiece *)(img + sec[8].off);
@@ -800,7 +803,7 @@ int run_batch_jit(drf_ctx *ctx, const BatchHost &b, const JitLaunch &j, cudaStre
     DeviceBatch &w = ctx->work;
     w.limit = ctx->opts.max_device_bytes;
     w.path_pref = 2;                               // specialized kernels run the owner-table back end
-    Error e = w.load(b, s);
+    Error e = w.load(b, s, !j.csched);             // a compiled-in schedule needs no warp-item array
     if (e.ok()) e = w.choose_path(b, b.tuple_bound, s);
     if (!e.ok() || w.args.path != PATH_TABLE) {
         ctx->last_error = e.message;

@@ -116,6 +116,7 @@ struct DeviceBatch {
     cudaEvent_t staged = nullptr;     // recorded after the copy out of `stage`
     bool staged_pending = false;
     uint64_t staged_version = 0;      // BatchHost::version the stage holds (0: none)
+    bool staged_schedule = false;     // ... and whether with the warp-item array
     DevBuf cnt, syn, phs, erro, totsyn, wcnt, wbase, blocksum;
     DevBuf keys0, keys1, hist, status, trec;
     DevBuf err_key, div_tid, best_pos, ptuples, epoch;
@@ -146,7 +147,9 @@ struct DeviceBatch {
     cudaError_t fetch(cudaStream_t s, bool ctrl_only);
     // Uploads the batch and sizes every buffer that does not depend on the
     // tuple count.
-    Error load(const BatchHost &b, cudaStream_t s);
+    // schedule false: the warp-item array is left out (kernels with the
+    // schedule compiled in do not read it)
+    Error load(const BatchHost &b, cudaStream_t s, bool schedule = true);
     // Sizes the key and look-back buffers for n tuples (sort path).
     Error size_keys(uint64_t n, cudaStream_t s);
     // Sizes the owner table, its touch bits and the witness hit bits

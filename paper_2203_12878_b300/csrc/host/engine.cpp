@@ -161,29 +161,31 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
 namespace {
 
 // The threads of range access r at offset c (reduced mod the modulus when
-// there is one) as at most two runs of consecutive tids whose cells are
-// sigma apart: (first tid, count, first tid's cell).  Cells outside the
-// array are clipped by the caller.
+// there is one) as runs of consecutive tids whose cells are sigma apart:
+// (first tid, count, first tid's cell) -- one run without a remainder (or
+// for sigma 0), else one per wrap of the index around the modulus (at most
+// kRangeMaxWraps + 1).  Cells outside the array are clipped by the caller.
 struct Run { int64_t t0, len, cell0; };
 
-int range_runs(const RangeAccess &r, int64_t c, uint32_t T, Run out[2])
+void range_runs(const RangeAccess &r, int64_t c, uint32_t T, std::vector<Run> &out)
 {
+    out.clear();
     const int64_t t = (int64_t)T, s = r.sigma;
-    int n = 0;
-    auto add = [&](int64_t a, int64_t b, int64_t cell0) {
-        if (a < b) out[n++] = Run{a, b - a, cell0};
-    };
     if (!r.modn || s == 0) {
-        add(0, t, c);
-        return n;
+        if (t > 0) out.push_back(Run{0, t, c});
+        return;
     }
-    // c in [0, N) and (T - 1) * |sigma| < N: the index wraps at most once,
-    // from tid t1 on
+    // c in [0, N): the index sigma * tid + c lies in [q N, (q + 1) N) for one
+    // q per run; the run ends where q changes
     const int64_t N = (int64_t)r.modn;
-    const int64_t t1 = s > 0 ? (N - c + s - 1) / s : c / -s + 1;
-    add(0, std::min(t, t1), c);
-    add(t1, t, c + s * t1 + (s > 0 ? -N : N));
-    return n;
+    for (int64_t a = 0; a < t;) {
+        const int64_t v = s * a + c;
+        const int64_t q = v >= 0 ? v / N : -((-v + N - 1) / N);
+        int64_t b = s > 0 ? ((q + 1) * N - c + s - 1) / s : range_floordiv(c - q * N, -s) + 1;
+        if (b > t) b = t;
+        out.push_back(Run{a, b - a, v - q * N});
+        a = b;
+    }
 }
 
 // Whether protocol i of a packed batch takes the range pass: static phases
@@ -367,10 +369,10 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
             const int64_t sb = (int64_t)(d.tab_off + (uint64_t)r.phase * d.cells_sum + out.cbase[d.cells_off + r.loc]);
             const uint32_t wf = r.write ? kRWrite : 0u;
             const long long s = r.sigma;
+            std::vector<Run> runs;
             for (int64_t c : r.offsets) {
-                Run runs[2];
-                const int nr = range_runs(r, c, p.nthreads, runs);
-                for (int q = 0; q < nr; q++) {
+                range_runs(r, c, p.nthreads, runs);
+                for (size_t q = 0; q < runs.size(); q++) {
                     // within the array, then cut at task boundaries
                     long long t0, l0, len;
                     range_clip(runs[q].t0, sb + runs[q].cell0, runs[q].len, s, sb, sb + ncells, t0, l0, len);

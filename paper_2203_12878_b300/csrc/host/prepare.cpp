@@ -788,8 +788,9 @@ struct RangeFinder {
         }
         i128 k = 0;
         if (!tid_coef(*e, k) || k > kRangeMaxSigma || k < -kRangeMaxSigma) return;
-        // with a remainder, the index wraps at most once over the threads
-        if (modn && (i128)(T ? T - 1 : 0) * (k < 0 ? -k : k) >= (i128)modn) return;
+        // with a remainder, the index wraps around it at most kRangeMaxWraps
+        // times over the threads (a run of consecutive tids per wrap)
+        if (modn && (i128)(T ? T - 1 : 0) * (k < 0 ? -k : k) >= (i128)modn * kRangeMaxWraps) return;
         RangeAccess r;
         r.pc = pc;
         r.phase = (uint32_t)phase;

@@ -26,11 +26,12 @@ struct PrepareOpts {
 // and conditions do not read tid, and its index is (sigma * tid + c) or
 // (sigma * tid + c) mod modn with sigma an integer of magnitude at most
 // kRangeMaxSigma (0: one cell for every thread) and c a function of the loop
-// variables alone (with a remainder, (T - 1) * |sigma| < modn).  The threads
-// that reach a given range of cells in one iteration are then one or two
-// runs of consecutive tids, their cells sigma apart, found without visiting
-// the others.
+// variables alone (with a remainder, (T - 1) * |sigma| < kRangeMaxWraps *
+// modn).  The threads that reach a given range of cells in one iteration
+// are then a few runs of consecutive tids (one per wrap of the index around
+// the modulus), their cells sigma apart, found without visiting the others.
 constexpr int32_t kRangeMaxSigma = 64;
+constexpr int32_t kRangeMaxWraps = 64;
 struct RangeLoop {
     uint32_t reg;                 // the loop variable's register
     int32_t lo, hi;               // expression code of the bounds

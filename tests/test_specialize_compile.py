@@ -83,7 +83,7 @@ def test_grid_scale_protocol_gets_the_range_pass():
 
 def test_protocols_without_shifted_indices_get_no_range_pass():
     for text, T, n in (("array A;\nwr A[100 * tid];\n", 64, 6400),               # a coefficient above 64
-                       ("array A;\nwr A[(3 * tid) % 150];\n", 64, 150),         # wraps twice over the threads
+                       ("array A;\nwr A[(64 * tid) % 65];\n", 100, 65),         # wraps more than 64 times
                        ("array A;\nwr A[tid * tid];\n", 64, 4096),                # not linear in tid
                        ("array A;\nforU x in 0 .. tid { wr A[tid + 64 * x]; }\n", 64, 64 * 64),   # bound reads tid
                        ("array A;\nforS x in 0 .. 4 { wr A[tid + 64 * x]; sync; }\n", 64, 256)):  # sync in the loop
@@ -95,3 +95,6 @@ def test_protocols_without_shifted_indices_get_no_range_pass():
     st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile("array A;\nforU x in 0 .. 4 { wr A[(-3 * tid + x) % 200]; }\n"),
                                      64, [256], [])
     assert st == "OK" and a["range_tuples"] == 256          # stride -3, one wrap
+    st, a = drf.drf_protocol_analyze(drf.drf_protocol_compile("array A;\nrd A[(6 * tid + 1) % 4096];\n"),
+                                     853, [4096], [])
+    assert st == "OK" and a["range_tuples"] == 853          # stride 6, two wraps

@@ -410,16 +410,21 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
         clear_range(out, ps.size());
         return;
     }
-    std::stable_sort(ent.begin(), ent.end(), [](const E &x, const E &y) { return x.task < y.task; });
-    out.wpiece.reserve(ent.size());
-    for (size_t i = 0; i < ent.size(); i++) {
-        if (i == 0 || ent[i].task != ent[i - 1].task) {
-            out.rlive.push_back(ent[i].task);
-            out.rfirst.push_back((uint32_t)i);
+    // the pieces grouped by task, tasks ascending, each task's pieces in the
+    // order they were cut (a counting sort over the table's tasks)
+    const uint64_t ntasks = (out.table_cells + kRangeRecs - 1) / kRangeRecs;
+    std::vector<uint32_t> at(ntasks + 1, 0);
+    for (const E &x : ent) at[x.task + 1]++;
+    for (uint64_t t = 0; t < ntasks; t++) {
+        if (at[t + 1]) {
+            out.rlive.push_back((uint32_t)t);
+            out.rfirst.push_back(at[t]);
         }
-        out.wpiece.push_back(ent[i].piece);
+        at[t + 1] += at[t];
     }
     if (!out.rlive.empty()) out.rfirst.push_back((uint32_t)ent.size());
+    out.wpiece.resize(ent.size());
+    for (const E &x : ent) out.wpiece[at[x.task]++] = x.piece;
     // each task's pieces merged (merge_pieces): [mfirst[i], mfirst[i + 1])
     // of rpiece, and the record updates they make
     std::vector<uint32_t> mfirst;

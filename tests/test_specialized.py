@@ -305,6 +305,20 @@ def test_range_pass_tid_free_accesses(rctx, oracle, text, T, cells):
     assert check(rctx, oracle, protogen.Protocol(text, T, cells, [])) == 3
 
 
+@pytest.mark.parametrize("text,T,cells", [
+    ("array A;\nforU x in 0 .. 5 { rd A[(6 * tid + x) % 4096]; }\nwr A[(7 * tid + 3) % 4096];\n", 853, [4096]),
+    ("array A;\nforU x in 0 .. 4 { rd A[(-5 * tid + 2 * x) % 1000]; }\nsync;\nwr A[(-3 * tid + 1) % 1000];\n",
+     700, [1000]),
+    ("array A;\nwr A[(4 * tid) % 1000];\n", 600, [1000]),                            # t and t + 250 collide
+    ("array A, B;\nforU x in 0 .. 3 { wr B[(9 * tid + 1000 * x) % 3001]; rd A[(2 * tid) % 999]; }\n", 2000, [999, 3001]),
+])
+def test_range_pass_multi_wrap(rctx, oracle, text, T, cells):
+    """Indices that wrap around their modulus several times over the
+    threads: one run of tids per wrap, the runs of one offset meeting (or
+    not) in the task's records."""
+    assert check(rctx, oracle, protogen.Protocol(text, T, cells, [])) == 3
+
+
 def test_small_protocols_skip_the_range_pass_by_default(sctx, oracle):
     """Under 2^22 range tuples a check keeps the table pass alone (same
     results)."""

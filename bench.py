@@ -403,7 +403,9 @@ def run_ours(args, rank, world):
     assert drf.result_dict(drf.drf_plan_results(pplan)[0]) == res
     drf.drf_plan_destroy(pplan)
     drf.drf_ctx_destroy(pctx)
-    range_tuples, range_updates = drf.drf_plan_range_tuples(plan) if specialized == 3 else (None, None)
+    range_tuples, range_updates = drf.drf_plan_range_tuples(plan)     # interpreted plans may run it too
+    if not range_tuples:
+        range_tuples, range_updates = None, None
     roof, stages = roofline(kinds, prof_steps, n, {**info, "specialized": specialized, "range_tuples": range_tuples},
                             dev, clocks)
 

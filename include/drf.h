@@ -257,8 +257,10 @@ typedef struct {
     uint32_t sort_bits;
     uint32_t key_bits;
     /* access tuples the owner table's range pass takes when the protocol is
-     * checked alone on the owner-table path: its accesses at +-tid plus a
-     * function of the loop variables, applied cell range by cell range in
+     * checked alone on the owner-table path: its accesses at a * tid plus a
+     * function of the loop variables (|a| <= 64, under a remainder that wraps
+     * at most 64 times over the threads), in loops and conditions that do
+     * not read tid and hold no sync, applied cell range by cell range in
      * shared memory (0 when it has none or they make under a quarter of its
      * tuples); counted at any size (see DRF_OPT_RANGE_ANY for when checks
      * take the pass) */
@@ -460,14 +462,14 @@ int drf_plan_config(const drf_plan *plan, uint32_t *granularity, uint32_t *radix
  * protocol's sync structure is the same for every thread and no evaluation
  * can fail, so each item's phase is compiled in and a launch runs neither
  * the count nor the scan pass; the owner-table pass counts the tuples), or
- * 3 (as 2, and the launch runs the range pass: accesses whose index is +tid
- * or -tid plus a function of the loop variables -- possibly under a
- * remainder -- in loops and conditions that do not read tid are applied
- * cell range by cell range in shared memory, the threads reaching a range
- * found as one or two tid intervals per loop iteration; the owner-table
- * pass applies the other accesses and the range pass merges their records,
- * then finds the first racy cell).  When specialization was asked for but
- * not used, log (may be NULL) receives why. */
+ * 3 (as 2, and the launch runs the range pass: the accesses that
+ * drf_analysis.range_tuples counts are applied cell range by cell range in
+ * shared memory, the threads reaching a range found as runs of consecutive
+ * tids per offset; the owner-table pass applies the other accesses and the
+ * range pass merges their records, then finds the first racy cell).
+ * Interpreted plans run the range pass too (reported by
+ * drf_plan_range_tuples).  When specialization was asked for but not used,
+ * log (may be NULL) receives why. */
 int drf_plan_specialized(const drf_plan *plan, uint32_t *specialized, char *log, size_t loglen);
 
 /* The back end a plan runs: DRF_PATH_SORT or DRF_PATH_TABLE (see
@@ -475,8 +477,8 @@ int drf_plan_specialized(const drf_plan *plan, uint32_t *specialized, char *log,
  * (the owner table once per granularity) when the owner table fits. */
 int drf_plan_path(const drf_plan *plan, uint32_t *path);
 
-/* The range pass of a plan (drf_plan_specialized reports 3; zeros
- * otherwise): *tuples, the access tuples its accesses make in one launch
+/* The range pass of a plan (zeros when the plan does not run it): *tuples,
+ * the access tuples its accesses make in one launch
  * (every thread, every iteration; the owner-table pass applies the other
  * tuples); *updates (may be NULL), the record updates its last launch made
  * -- fewer, since the iterations of an access that share an offset apply

@@ -424,7 +424,9 @@ def run_ours(args, rank, world):
                 octx = drf.drf_ctx_create(dev, flags=drf.OPT_PROFILE_STAGES | oflags)
                 oplan = drf.drf_plan_create(octx, [bc], bounds)
                 _, okinds, _, _, _ = time_steps(oplan, osteps, 3, stream, flush, stages=True, warm_s=args.warmup_seconds)
-                oroof, ostages = roofline(okinds, osteps, n, drf.drf_plan_info(oplan), dev, clocks)
+                ort = drf.drf_plan_range_tuples(oplan)[0] or None
+                oroof, ostages = roofline(okinds, osteps, n, {**drf.drf_plan_info(oplan), "range_tuples": ort}, dev,
+                                          clocks)
                 others.append({"path": drf.drf_plan_path(oplan), "specialized": False,
                                "ms_per_step": statistics.mean(oms), "value": n / (statistics.mean(oms) * 1e-3),
                                "stages_ms": ostages, "roofline": oroof})

@@ -304,8 +304,11 @@ def roofline(kinds, steps, n, info, dev, clocks):
     dominant = max(totals, key=totals.get)
     peak, peak_kind = _peaks()
     # algorithmic bytes per launch: radix pass = read + write every key (16 B);
-    # emit = write every key (8 B); detect = read every key (8 B)
-    bytes_per = {"radix": 16 * n, "emit": 8 * n, "detect": 8 * n}
+    # emit = write every key (8 B); detect = read every key (8 B).  A forced
+    # sort path emits one key per distinct (thread, offset) of the range
+    # accesses, so it may sort fewer keys than there are tuples.
+    nk = info.get("keys") or n
+    bytes_per = {"radix": 16 * nk, "emit": 8 * nk, "detect": 8 * nk}
     radix_launches = [t for _, t in kinds.get("radix", []) if t > 0.002]
     dom_ms = (statistics.mean(radix_launches) if dominant == "radix" and radix_launches
               else totals[dominant] / max(1, len(kinds[dominant]) // steps))
@@ -320,7 +323,8 @@ def roofline(kinds, steps, n, info, dev, clocks):
         # (emit writes 8, each radix pass reads and writes 16, detection
         # reads 8) and each stage's share of HBM at its measured time
         npass = len(radix_launches) // steps if radix_launches else 0
-        roof["bytes_per_tuple"] = 8 + 16 * npass + 8
+        roof["keys_per_launch"] = nk
+        roof["bytes_per_tuple"] = round((8 + 16 * npass + 8) * nk / n, 2)
         roof["stage_hbm_frac"] = {
             k: round(bytes_per[k] * (npass if k == "radix" else 1) / (totals[k] * 1e-3) / 1e9 / peak, 4)
             for k in bytes_per if totals.get(k)}
@@ -406,8 +410,8 @@ def run_ours(args, rank, world):
     range_tuples, range_updates = drf.drf_plan_range_tuples(plan)     # interpreted plans may run it too
     if not range_tuples:
         range_tuples, range_updates = None, None
-    roof, stages = roofline(kinds, prof_steps, n, {**info, "specialized": specialized, "range_tuples": range_tuples},
-                            dev, clocks)
+    roof, stages = roofline(kinds, prof_steps, n, {**info, "specialized": specialized, "range_tuples": range_tuples,
+                                                   "keys": drf.drf_plan_keys(plan)}, dev, clocks)
 
     # the interpreted back ends on the same protocol, for comparison
     others = []
@@ -425,8 +429,8 @@ def run_ours(args, rank, world):
                 oplan = drf.drf_plan_create(octx, [bc], bounds)
                 _, okinds, _, _, _ = time_steps(oplan, osteps, 3, stream, flush, stages=True, warm_s=args.warmup_seconds)
                 ort = drf.drf_plan_range_tuples(oplan)[0] or None
-                oroof, ostages = roofline(okinds, osteps, n, {**drf.drf_plan_info(oplan), "range_tuples": ort}, dev,
-                                          clocks)
+                oroof, ostages = roofline(okinds, osteps, n, {**drf.drf_plan_info(oplan), "range_tuples": ort,
+                                                              "keys": drf.drf_plan_keys(oplan)}, dev, clocks)
                 others.append({"path": drf.drf_plan_path(oplan), "specialized": False,
                                "ms_per_step": statistics.mean(oms), "value": n / (statistics.mean(oms) * 1e-3),
                                "stages_ms": ostages, "roofline": oroof})

@@ -435,6 +435,12 @@ int drf_plan_results(drf_plan *plan, drf_result *out);
 int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
                   uint32_t *kernels_per_launch, uint32_t *sort_bits);
 
+/* The keys a sort-path plan sorts per launch (0 on the owner table): the
+ * tuples, except that a forced sort path (DRF_OPT_PATH_SORT) emits the
+ * range accesses' keys (drf_analysis.range_tuples) once per distinct
+ * (thread, offset) -- iterations that repeat an access add no key. */
+int drf_plan_keys(const drf_plan *plan, uint64_t *keys);
+
 /* Per-stage device times (milliseconds) of the last launch, when the context
  * was created with DRF_OPT_PROFILE_STAGES: names[i] (static strings) and
  * ms[i] for i < *count (cap entries at most).  Waits for the launch. */

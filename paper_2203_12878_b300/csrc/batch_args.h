@@ -52,6 +52,14 @@ struct RTask {
     uint32_t task, p0, p1, win;
 };
 
+// One range piece's keys on the sort path: its o-th thread's key is
+// k0 + o * d (modulo 2^64: the index field steps by the piece's step and
+// the thread field by one, neither leaving its field), at key position
+// pre + o of the range keys, for o < len.
+struct RKeys {
+    unsigned long long pre, k0, d, len;
+};
+
 #if defined(__CUDACC__)
 #define DRF_HD __host__ __device__
 #else
@@ -172,6 +180,15 @@ struct BatchArgs {
     const unsigned long long *rtup;
     unsigned long long rtotal;
     uint32_t rcount;
+    // The sort path with the range pieces (range_keys): the count and emit
+    // passes leave the range accesses out, and k_range_emit writes one key
+    // per (piece as cut, thread) -- nrkeys keys from position
+    // nkeys - nrkeys on, wkeys[0 .. nwkeys) in key order -- with their
+    // digit histograms.
+    const RKeys *wkeys;
+    unsigned long long nrkeys;
+    uint32_t nwkeys;
+    uint32_t range_keys;
     uint32_t range_on;
     void *table;                     // [tab_cells] 32-bit owner records, padded to whole blocks
     uint64_t tab_cells;

@@ -151,6 +151,10 @@ extern "C" int drf_check_noalloc(const uint8_t *bytecode, size_t len, const drf_
     a.rtup = nullptr;
     a.rtotal = 0;
     a.rcount = 0;
+    a.wkeys = nullptr;
+    a.nrkeys = 0;
+    a.nwkeys = 0;
+    a.range_keys = 0;
     a.range_on = 0;
     a.nwitems = (uint32_t)nw;
     a.nprotos = 1;

@@ -319,22 +319,25 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             // and array; neither it nor the table pass needs the index of an
             // access the range pass applies (k_finalize adds its witnesses)
             const bool rng = a.range_on && (in.a & AF_RANGE);
+            // (the sort path with range keys: k_range_emit writes these keys)
+            const bool rngk = a.range_keys && (in.a & AF_RANGE);
             const bool need = CELL ? (phase == tg.phase && in.b == tg.loc && !rng)
-                                   : TAB ? !rng : (PHASED || (in.a & AF_EVAL_IN_COUNT));
+                                   : TAB ? !rng : !rngk && (PHASED || (in.a & AF_EVAL_IN_COUNT));
             if (ex && need) {
                 if (!eval<V>(xc, in.c, tid, vars, idx)) { err = kErrDiv0; ok = false; }
                 else if (idx < 0 || (uint64_t)(U)idx >= __ldg(cells + in.b)) { err = kErrOob; ok = false; }
             }
             if (ex && !ok) running = false;
             if (EMIT) {
-                unsigned em = __ballot_sync(kFull, ok);
-                if (ok) {
+                const bool ke = ok && !rngk;
+                unsigned em = __ballot_sync(kFull, ke);
+                if (ke) {
                     unsigned long long pos = cursor + __popc(em & lanemask_lt());
                     unsigned long long key = make_key(p, phase, in.b, (unsigned long long)(U)idx, tidpart, in.a & AF_WRITE, L);
                     if (pos < wend && pos < a.nkeys) a.keys[0][pos] = key;
                     else atomicOr(&a.ctrl->flags, CF_EMIT_OVERFLOW);
                 }
-                hist_add(sh, L, key_or_zero(ok, p, phase, in.b, (unsigned long long)(U)idx, tidpart, in.a, L), ok);
+                hist_add(sh, L, key_or_zero(ke, p, phase, in.b, (unsigned long long)(U)idx, tidpart, in.a, L), ke);
                 cursor += __popc(em);
             } else if (TAB) {
                 const bool put = ok && phase < P.tab_phases;
@@ -346,7 +349,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             } else if (CELL) {
                 if (ok && !rng && phase == tg.phase && in.b == tg.loc && (unsigned long long)(U)idx == tg.idx)
                     hit |= 1u | ((in.a & AF_WRITE) << 1);
-            } else if (ok) {
+            } else if (ok && !rngk) {
                 count++;
             }
             if (TAB && ok && !(rng && a.rcount)) count++;      // (range tuples: counted on the host)
@@ -361,7 +364,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             }
             break;
         case I_LOOP:
-            if (ex && (TAB || CELL) && a.range_on && (in.b & LB_RANGE_ONLY)) {
+            if (ex && (((TAB || CELL) && a.range_on) || (!TAB && !CELL && a.range_keys)) && (in.b & LB_RANGE_ONLY)) {
                 pc = (uint32_t)in.e + 1;            // the range pass has the whole loop
                 break;
             }
@@ -407,10 +410,14 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
             const uint32_t m = (uint32_t)in.e;
             // the table and witness passes take a loop whose accesses the
             // range pass all applies in one step: the table pass counts them
-            bool skip = (TAB || CELL) && a.range_on;
+            bool skip = ((TAB || CELL) && a.range_on) || (EMIT && a.range_keys);
             for (uint32_t j = 0; j < m && skip; j++) skip = (load_insn(prog + mpc + 1 + j).a & AF_RANGE) != 0;
             if (!PHASED) {
-                if (okb) { count += (uint32_t)(trip * m); syncs += (uint32_t)(trip * in.b); }
+                // (with range keys the range accesses' tuples are the pieces')
+                uint32_t mc = m;
+                if (a.range_keys)
+                    for (uint32_t j = 0; j < m; j++) mc -= (load_insn(prog + mpc + 1 + j).a & AF_RANGE) ? 1u : 0u;
+                if (okb) { count += (uint32_t)(trip * mc); syncs += (uint32_t)(trip * in.b); }
             } else if (skip) {
                 if (okb) {
                     if (TAB && !a.rcount) count += (uint32_t)(trip * m);
@@ -450,7 +457,7 @@ __device__ void run_item(const BatchArgs &a, uint32_t p, const DevProto &P, cons
                             const V v = (V)((U)rest[j] + coef[j] * (U)x);
                             const V idx = fast_post<V, U>(v, (mt >> 2) & 3, pcon[j]);
                             const uint32_t ph = ph0 + (mt >> 24), loc = (mt >> 8) & 0xFFFF;
-                            if (EMIT) {
+                            if (EMIT && !(a.range_keys && (mt & AF_RANGE))) {
                                 const unsigned long long key =
                                     act ? make_key(p, ph, loc, (unsigned long long)(U)idx, tidpart, mt & AF_WRITE, L)
                                         : 0ull;
@@ -1518,6 +1525,96 @@ __global__ void __launch_bounds__(kRangeThreads, kRangeBlocksPerSm) k_range(Batc
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.rcount) atomicAdd(&a.ctrl->total, a.rtotal);
 }
 
+// The sort path's keys of the range accesses (BatchArgs::range_keys): one
+// per (piece as cut, thread), with their digit histograms, as the
+// interpreted emit pass writes the other accesses' keys.  Block b writes the
+// range keys [nrkeys * b / G, nrkeys * (b + 1) / G): its warp 0 finds the
+// piece holding the first of them (a 32-way search of the pieces' key
+// positions), then the block stages kREmitThreads pieces at a time in
+// shared memory, and each thread writes every kREmitThreads-th key of the
+// staged span, k0 + o * d, coalesced with its neighbours'.
+constexpr int kREmitThreads = 512;
+
+__global__ void __launch_bounds__(kREmitThreads) k_range_emit(BatchArgs a)
+{
+    pdl_begin();
+    __shared__ EmitShared sh;
+    __shared__ unsigned long long s_pre[kREmitThreads + 1], s_k0[kREmitThreads], s_d[kREmitThreads];
+    __shared__ uint32_t s_e0;
+    for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) (&sh.hist[0][0])[i] = 0;
+    const KeyLayout L = a.L;
+    const uint32_t t = threadIdx.x, lane = t & 31;
+    const unsigned long long total = a.nrkeys, base = a.nkeys - a.nrkeys;
+    const unsigned long long kb0 = total * blockIdx.x / gridDim.x, kb1 = total * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t n = a.nwkeys;
+    if (t < 32) {
+        // the last piece whose first key is at or before kb0 (pieces are
+        // never empty, and wkeys[0].pre is 0)
+        uint32_t lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const uint32_t step = (hi - lo + 31) / 32, q = lo + lane * step;
+            const bool le = q < hi && __ldg(&a.wkeys[q].pre) <= kb0;
+            const unsigned m = __ballot_sync(kFull, le);
+            const uint32_t last = 31u - (uint32_t)__clz(m);
+            const uint32_t nlo = lo + last * step;
+            hi = nlo + step < hi ? nlo + step : hi;
+            lo = nlo;
+        }
+        if (t == 0) s_e0 = lo;
+    }
+    __syncthreads();
+    uint32_t e0 = s_e0;
+    unsigned long long k = kb0;
+    while (k < kb1) {
+        {
+            const uint32_t e = e0 + t;
+            if (e < n) {
+                const RKeys w = a.wkeys[e];
+                s_pre[t] = w.pre;
+                s_k0[t] = w.k0;
+                s_d[t] = w.d;
+            } else {
+                s_pre[t] = total;
+                s_k0[t] = s_d[t] = 0;
+            }
+            if (t == 0) s_pre[kREmitThreads] = e0 + kREmitThreads < n ? __ldg(&a.wkeys[e0 + kREmitThreads].pre) : total;
+        }
+        __syncthreads();
+        const unsigned long long kend = s_pre[kREmitThreads] < kb1 ? s_pre[kREmitThreads] : kb1;
+        uint32_t j = 0;                                    // this thread's staged piece
+        for (unsigned long long k1 = k; k1 < kend; k1 += kREmitThreads) {
+            const unsigned long long kk = k1 + t;
+            const bool ok = kk < kend;
+            unsigned long long key = 0;
+            if (ok) {
+                if (s_pre[j + 1] <= kk) {
+                    // past the piece: the last staged piece starting at or before kk
+                    uint32_t lo = j + 1, hi = kREmitThreads;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) / 2;
+                        if (s_pre[mid] <= kk) lo = mid; else hi = mid - 1;
+                    }
+                    j = lo;
+                }
+                key = s_k0[j] + (kk - s_pre[j]) * s_d[j];
+                const unsigned long long pos = base + kk;
+                if (pos < a.nkeys) a.keys[0][pos] = key;
+                else atomicOr(&a.ctrl->flags, CF_EMIT_OVERFLOW);
+            }
+            hist_add(&sh, L, key, ok);
+        }
+        k = kend;
+        e0 += kREmitThreads;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < (int)(L.passes * kRadixBins); i += blockDim.x) {
+        const unsigned int h = (&sh.hist[0][0])[i];
+        if (h) atomicAdd(&a.hist[i], (unsigned long long)h);
+    }
+    // the launch's key total counts these keys too (the count pass did not)
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.ctrl->total, a.nrkeys);
+}
+
 __device__ __forceinline__ void two_smallest(uint32_t &f, uint32_t &s, uint32_t x)
 {
     if (x == f || x == s) return;
@@ -1798,7 +1895,10 @@ static BatchArgs with_rcount(const BatchArgs &a, const JitLaunch *j)
 {
     BatchArgs b = a;
     const bool jit_counts = j && j->table && j->static_phases;
-    b.rcount = a.range_on && a.path == PATH_TABLE && a.rtup && (jit_counts ? j->range : a.count_free != 0) ? 1u : 0u;
+    b.rcount = (a.range_on && a.path == PATH_TABLE && a.rtup && (jit_counts ? j->range : a.count_free != 0)) ||
+                       (a.range_keys && a.rtup)
+                   ? 1u
+                   : 0u;
     return b;
 }
 
@@ -1886,6 +1986,13 @@ cudaError_t launch_back(const BatchArgs &a, cudaStream_t s, int sms, cudaEvent_t
     if (schedule_missing(a, j)) return cudaErrorInvalidValue;
     if (a.path == PATH_TABLE) return launch_back_table(a, s, sms, ev, nev, j);
     launch_interp<M_EMIT>(a, s, sms);
+    if (a.range_keys) {
+        // the range accesses' keys, from the pieces
+        // blocks of at least 8 keys per thread, up to 4 per SM
+        const unsigned long long need = (a.nrkeys + 8 * kREmitThreads - 1) / (8 * kREmitThreads);
+        const uint32_t want = (uint32_t)sms * 4;
+        k_range_emit<<<need < want ? (uint32_t)(need ? need : 1) : want, kREmitThreads, 0, s>>>(a);
+    }
     mark(ev, nev, s);
     for (uint32_t q = 0; q < a.L.passes; q++) {
         if (a.ntiles) {

@@ -628,8 +628,10 @@ int build_plan(drf_ctx *ctx, uint32_t n, const uint8_t *const *bytecodes, const 
         delete plan;
         return cuda_fail(ctx, ce);
     }
-    plan->tuples = d.host_ctrl()->total;
-    e = d.choose_path(plan->host, plan->tuples, s);
+    // (the count pass leaves out the range accesses whose keys come from the pieces)
+    const uint64_t counted = d.host_ctrl()->total;
+    plan->tuples = counted + (d.args.range_keys ? plan->host.range_tuples : 0);
+    e = d.choose_path(plan->host, counted, s);
     if (!e.ok()) { delete plan; return fail(ctx, e.status, e.message); }
     plan->cfg.path = d.args.path == PATH_TABLE ? 2 : 1;
     if (cfg.jit && d.args.path != PATH_TABLE) { delete plan; return fail(ctx, DRF_E_LIMIT, "specialization needs the owner table"); }
@@ -906,9 +908,17 @@ int drf_plan_info(const drf_plan *plan, uint64_t *tuples, uint32_t *sort_passes,
         if (table && plan->dev.jit.static_phases) *kernels_per_launch = 5 + 2 * range;
         else if (table && plan->dev.args.count_free) *kernels_per_launch = 2 * widths + 4 + range;   // init, 2x interp, tlist, tscan, finalize
         else if (table) *kernels_per_launch = 3 * widths + 5 + range;   // init, 3x interp, scan, tlist, tscan, finalize
-        else *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes;   // init, 2x interp, scan, passes, detect, resolve, finalize
+        else *kernels_per_launch = 2 * widths + 5 + plan->host.L.passes +   // init, 2x interp, scan, passes, detect, resolve, finalize
+                                   (plan->dev.args.range_keys ? 1 : 0);     // (the range accesses' keys)
     }
     if (sort_bits) *sort_bits = plan->host.L.sort_bits;
+    return DRF_OK;
+}
+
+int drf_plan_keys(const drf_plan *plan, uint64_t *keys)
+{
+    if (!plan || !keys) return DRF_E_INVALID_ARG;
+    *keys = plan->dev.args.path == PATH_TABLE ? 0 : plan->dev.args.nkeys;
     return DRF_OK;
 }
 

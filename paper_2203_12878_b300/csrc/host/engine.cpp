@@ -152,7 +152,7 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
     for (auto &w : ws) out.runs.push_back(BatchHost::Run{w.proto, w.k, w.groups});
     out.nwitems = nwitems;
     if (expand) out.expand_witems();
-    if (out.table_ok) plan_range(ps, out, range_min);
+    plan_range(ps, out, range_min);                // (clears the previous pack's range work when none)
     out.renew();
     return Error{};
 }
@@ -337,6 +337,8 @@ void clear_range(BatchHost &out, size_t nprotos)
     out.range_pcs.assign(nprotos, {});
     out.range_tuples = 0;
     out.rtup.clear();
+    out.wkeys.clear();
+    out.nrkeys = 0;
 }
 
 }  // namespace
@@ -344,13 +346,16 @@ void clear_range(BatchHost &out, size_t nprotos)
 void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_t range_min)
 {
     clear_range(out, ps.size());
+    if (!out.table_ok) return;                     // the pieces are laid out in the owner table's records
     // a batch whose range accesses make few tuples runs faster without the
     // pass (its planning, upload and kernel would cost more than it saves)
     unsigned __int128 all = 0, rt = 0;
     for (size_t i = 0; i < ps.size(); i++)
         if (range_candidate(*ps[i], out.protos[i], rt)) all += rt;
     if (all == 0 || all < range_min) return;
-    struct E { uint32_t task; RPiece piece; };
+    // each piece as cut, with its task and its first thread's sort key
+    struct E { uint32_t task; RPiece piece; unsigned long long k0; };
+    const KeyLayout &L = out.L;
     std::vector<E> ent;
     for (size_t i = 0; i < ps.size(); i++) {
         const Prepared &p = *ps[i];
@@ -380,8 +385,13 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
                         const long long task = l0 / (long long)kRangeRecs, base = task * (long long)kRangeRecs;
                         long long ct0, cl0, clen;
                         range_clip(t0, l0, len, s, base, base + (long long)kRangeRecs, ct0, cl0, clen);
+                        // the key fields of the interpreted emit pass
+                        unsigned long long k0 = ((unsigned long long)i << L.phase_bits) | r.phase;
+                        k0 = (k0 << L.loc_bits) | r.loc;
+                        k0 = (k0 << L.idx_bits) | (unsigned long long)(cl0 - sb);
+                        k0 = (k0 << L.sort_lo) | ((unsigned long long)ct0 << 1) | (r.write ? 1u : 0u);
                         ent.push_back(E{(uint32_t)task, RPiece{(uint32_t)ct0, (uint32_t)clen | wf, (int32_t)(cl0 - base),
-                                                               (int32_t)s}});
+                                                               (int32_t)s}, k0});
                         t0 += clen;
                         l0 += s * clen;
                         len -= clen;
@@ -424,7 +434,18 @@ void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_
     }
     if (!out.rlive.empty()) out.rfirst.push_back((uint32_t)ent.size());
     out.wpiece.resize(ent.size());
-    for (const E &x : ent) out.wpiece[at[x.task]++] = x.piece;
+    out.wkeys.resize(ent.size());
+    for (const E &x : ent) {
+        const uint32_t q = at[x.task]++;
+        out.wpiece[q] = x.piece;
+        // next thread: index field + step, thread field + 1
+        out.wkeys[q] = RKeys{0, x.k0, ((unsigned long long)(long long)x.piece.step << L.sort_lo) + 2ull,
+                             x.piece.lenf & kRLen};
+    }
+    for (RKeys &k : out.wkeys) {
+        k.pre = out.nrkeys;
+        out.nrkeys += k.len;
+    }
     // each task's pieces merged (merge_pieces): [mfirst[i], mfirst[i + 1])
     // of rpiece, and the record updates they make
     std::vector<uint32_t> mfirst;
@@ -513,7 +534,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s, bool schedule)
                            section(b.protos, end), section(b.cells, end), section(b.cbase, end),
                            section(schedule ? b.witems : no_witems, end), section(b.iphase, end), section(b.rpiece, end),
                            section(b.rtask, end), section(b.rlive, end), section(b.rfirst, end),
-                           section(b.wpiece, end), section(b.rtup, end)};
+                           section(b.wpiece, end), section(b.rtup, end), section(b.wkeys, end)};
     const size_t total = std::max<size_t>(end, 256);
     bool ok = ensure(image, total, &in_use, limit);
     // the stage already holds this image (the same pack loaded again): it is
@@ -594,6 +615,11 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s, bool schedule)
     a.rtup = b.rtup.empty() ? nullptr : (const unsigned long long *)(img + sec[13].off);
     a.rtotal = b.rtup.empty() ? 0ull : b.range_tuples;
     a.rcount = 0;
+    a.wkeys = (const RKeys *)(img + sec[14].off);
+    // a forced sort path emits the range accesses' keys from the pieces
+    a.range_keys = (path_pref == 1 && b.nrkeys && !b.rtup.empty()) ? 1u : 0u;
+    a.nrkeys = a.range_keys ? b.nrkeys : 0ull;
+    a.nwkeys = a.range_keys ? (uint32_t)b.wkeys.size() : 0u;
     a.nlive = (uint32_t)b.rlive.size();
     a.nrtask = (uint32_t)b.rtask.size();
     a.range_on = 0;
@@ -705,6 +731,7 @@ Error DeviceBatch::choose_path(const BatchHost &b, uint64_t n, cudaStream_t s)
 
 Error DeviceBatch::size_keys(uint64_t n, cudaStream_t s)
 {
+    n += args.range_keys ? args.nrkeys : 0;        // the range accesses' keys follow the counted ones
     const uint32_t tiles = radix_tiles(n, args.radix_items);
     const size_t kb = std::max<uint64_t>(n, 1) * 8;
     const size_t sb = std::max<size_t>((size_t)args.L.passes * tiles * kRadixBins * 8, 16);

@@ -79,6 +79,10 @@ struct BatchHost {
     std::vector<std::vector<uint32_t>> range_pcs;
     uint64_t range_tuples = 0;
     std::vector<unsigned long long> rtup;      // per protocol: the tuples of its range accesses
+    // the sort path's keys of the range accesses: per piece as cut, its
+    // keys' position, first key and step, and their total
+    std::vector<RKeys> wkeys;
+    uint64_t nrkeys = 0;
     uint64_t table_bytes() const { return table_cells * 4; }   // one 32-bit owner record per cell
 };
 
@@ -97,7 +101,7 @@ Error pack_batch(const std::vector<const Prepared *> &ps, BatchHost &out, bool e
 // phases whose range accesses make a quarter of its tuples or more, each
 // offset's threads cut into pieces at the boundaries of the tasks of owner
 // records their cells fall into, and AF_RANGE set on their instructions.
-// Called by pack_batch when the batch has an owner table.
+// Called by pack_batch; a batch without an owner table gets none.
 void plan_range(const std::vector<const Prepared *> &ps, BatchHost &out, uint64_t range_min);
 constexpr size_t kRangeMaxEntries = 1u << 24;                // pieces of a batch at most
 constexpr uint64_t kRangeSplitWork = 1u << 15;               // record updates per part of a task

@@ -117,6 +117,7 @@ _SIGS = {
                                        ctypes.POINTER(drf_bounds), ctypes.POINTER(_P)]),
     "drf_plan_launch": (ctypes.c_int, [_P, _P]),
     "drf_plan_results": (ctypes.c_int, [_P, ctypes.POINTER(drf_result)]),
+    "drf_plan_keys": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "drf_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
                                      ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "drf_plan_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
@@ -450,6 +451,14 @@ def drf_plan_info(plan) -> dict:
     if st != 0:
         raise DrfError(st)
     return {"tuples": t.value, "sort_passes": p.value, "kernels_per_launch": k.value, "sort_bits": b.value}
+
+
+def drf_plan_keys(plan) -> int:
+    k = ctypes.c_uint64()
+    st = lib().drf_plan_keys(plan, ctypes.byref(k))
+    if st != 0:
+        raise DrfError(st)
+    return k.value
 
 
 def drf_plan_stage_times(plan) -> list:

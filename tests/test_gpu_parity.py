@@ -17,14 +17,15 @@ CELLS = 1
 
 
 PATH_FLAGS = {"sort": drf.OPT_PATH_SORT, "table": drf.OPT_PATH_TABLE,
-              "table+range": drf.OPT_PATH_TABLE | drf.OPT_RANGE_ANY}   # range pass at any size
+              "table+range": drf.OPT_PATH_TABLE | drf.OPT_RANGE_ANY,   # range pass at any size
+              "sort+range": drf.OPT_PATH_SORT | drf.OPT_RANGE_ANY}     # range accesses' keys from the pieces
 TABLE_LIMIT = 64 << 30           # bytes: the largest owner table the library sets up
 
 
-@pytest.fixture(scope="module", params=["sort", "table", "table+range"])
+@pytest.fixture(scope="module", params=["sort", "table", "table+range", "sort+range"])
 def ctx(request):
     """A context forced onto one back end; every test using it runs on both
-    (the owner table with and without the range pass)."""
+    (each with and without the range pieces)."""
     c = drf.drf_ctx_create(0, flags=PATH_FLAGS[request.param])
     c.path = request.param
     yield c
@@ -514,6 +515,32 @@ def test_server_splits_a_round_that_does_not_fit(oracle):
     for t, g in zip(texts, got):
         assert same(g, oracle.check(t, 1024, [n], [], CELLS)), t
     assert got[-1]["verdict"] == "RACY"
+
+
+def test_sort_path_batch_emits_range_keys(oracle):
+    """A forced sort path over a batch: the range accesses' keys come from
+    the pieces (one per distinct thread and offset), the others from the
+    interpreter; fewer keys than tuples, every result equal to the oracle,
+    launch after launch."""
+    c = drf.drf_ctx_create(0, flags=drf.OPT_PATH_SORT | drf.OPT_RANGE_ANY)
+    try:
+        ps = protogen.config4(master_seed=29, count=40) + [protogen.shifted_small(s) for s in range(40, 60)]
+        ps += [protogen.strided_small(s) for s in range(200, 220)] + [protogen.random_small(s) for s in range(330, 340)]
+        ps = [p for p in ps if want(oracle, p)["status"] == "OK"]
+        plan = drf.drf_plan_create(c, [drf.drf_protocol_compile(p.text) for p in ps],
+                                   [(p.nthreads, p.cells, p.params) for p in ps])
+        try:
+            assert drf.drf_plan_path(plan) == "sort"
+            for _ in range(3):
+                drf.drf_plan_launch(plan)
+                for p, r in zip(ps, drf.drf_plan_results(plan)):
+                    assert same(drf.result_dict(r), want(oracle, p)), p.text
+            info = drf.drf_plan_info(plan)
+            assert 0 < drf.drf_plan_keys(plan) < info["tuples"]
+        finally:
+            drf.drf_plan_destroy(plan)
+    finally:
+        drf.drf_ctx_destroy(c)
 
 
 def test_interpreted_batch_runs_the_range_pass(oracle):

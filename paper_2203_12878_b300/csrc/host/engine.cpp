@@ -523,6 +523,9 @@ Section section(const std::vector<T> &v, size_t &end)
 Error DeviceBatch::load(const BatchHost &b, cudaStream_t s, bool schedule)
 {
     static const std::vector<WarpItem> no_witems;
+    static const std::vector<RKeys> no_wkeys;
+    // the range pieces' key templates: only for the sort path's range keys
+    const bool keys = path_pref == 1 && b.nrkeys && !b.rtup.empty();
     const uint64_t np = b.protos.size();
     const uint64_t nw = b.nwitems;
     const uint32_t nwblocks = (uint32_t)std::max<uint64_t>(1, (nw + kWScanPerBlock - 1) / kWScanPerBlock);
@@ -534,13 +537,13 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s, bool schedule)
                            section(b.protos, end), section(b.cells, end), section(b.cbase, end),
                            section(schedule ? b.witems : no_witems, end), section(b.iphase, end), section(b.rpiece, end),
                            section(b.rtask, end), section(b.rlive, end), section(b.rfirst, end),
-                           section(b.wpiece, end), section(b.rtup, end), section(b.wkeys, end)};
+                           section(b.wpiece, end), section(b.rtup, end), section(keys ? b.wkeys : no_wkeys, end)};
     const size_t total = std::max<size_t>(end, 256);
     bool ok = ensure(image, total, &in_use, limit);
     // the stage already holds this image (the same pack loaded again): it is
     // copied to the device as it is
-    const bool restage = !(b.version && staged_version == b.version && staged_schedule == schedule && stage &&
-                           stage_cap >= total);
+    const bool restage = !(b.version && staged_version == b.version && staged_schedule == schedule &&
+                           staged_keys == keys && stage && stage_cap >= total);
     // the previous copy out of the stage must be done before it is rewritten
     if (ok && staged_pending && restage) ok = cudaEventSynchronize(staged) == cudaSuccess;
     if (restage) staged_pending = false;
@@ -561,6 +564,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s, bool schedule)
                 if (x.bytes) std::memcpy((char *)stage + x.off, x.src, x.bytes);
             staged_version = b.version;
             staged_schedule = schedule;
+            staged_keys = keys;
         }
         ok = cudaMemcpyAsync(image.p, stage, end ? end : 16, cudaMemcpyHostToDevice, s) == cudaSuccess &&
              cudaEventRecord(staged, s) == cudaSuccess;
@@ -617,7 +621,7 @@ Error DeviceBatch::load(const BatchHost &b, cudaStream_t s, bool schedule)
     a.rcount = 0;
     a.wkeys = (const RKeys *)(img + sec[14].off);
     // a forced sort path emits the range accesses' keys from the pieces
-    a.range_keys = (path_pref == 1 && b.nrkeys && !b.rtup.empty()) ? 1u : 0u;
+    a.range_keys = keys ? 1u : 0u;
     a.nrkeys = a.range_keys ? b.nrkeys : 0ull;
     a.nwkeys = a.range_keys ? (uint32_t)b.wkeys.size() : 0u;
     a.nlive = (uint32_t)b.rlive.size();

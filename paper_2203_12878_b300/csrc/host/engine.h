@@ -121,6 +121,7 @@ struct DeviceBatch {
     bool staged_pending = false;
     uint64_t staged_version = 0;      // BatchHost::version the stage holds (0: none)
     bool staged_schedule = false;     // ... and whether with the warp-item array
+    bool staged_keys = false;         // ... and whether with the range pieces' key templates
     DevBuf cnt, syn, phs, erro, totsyn, wcnt, wbase, blocksum;
     DevBuf keys0, keys1, hist, status, trec;
     DevBuf err_key, div_tid, best_pos, ptuples, epoch;

@@ -354,6 +354,21 @@ def roofline(kinds, steps, n, info, dev, clocks):
     return roof, {k: round(v, 4) for k, v in sorted(totals.items())}
 
 
+def materialize_scan_fractions(tuples_per_s, sort_bits, peak_gbs):
+    """The throughput as HBM fractions of a materialize-and-scan checker of
+    the same protocol: one 8-byte key per tuple written, sorted by
+    ceil(S / 8) LSD passes of 8-bit digits over its S sorted bits (16 B per
+    key and pass) and read once by detection, i.e. 16 (1 + ceil(S / 8)) B per
+    tuple (pipeline_frac), and the 16 B per tuple no such design moves less
+    than (lower_bound_frac: one key written and read once).  Above 1 means the
+    check ran faster than that design could at the measured copy bandwidth."""
+    passes = -(-int(sort_bits) // 8) if sort_bits else 0
+    per_tuple = 16 * (1 + passes)
+    return {"sort_bits": sort_bits, "reference_passes": passes, "reference_bytes_per_tuple": per_tuple,
+            "pipeline_frac": round(tuples_per_s * per_tuple / (peak_gbs * 1e9), 4),
+            "lower_bound_frac": round(tuples_per_s * 16 / (peak_gbs * 1e9), 4), "peak_gbs": peak_gbs}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2203_12878_b300 import drf
@@ -431,9 +446,12 @@ def run_ours(args, rank, world):
                 ort = drf.drf_plan_range_tuples(oplan)[0] or None
                 oroof, ostages = roofline(okinds, osteps, n, {**drf.drf_plan_info(oplan), "range_tuples": ort,
                                                               "keys": drf.drf_plan_keys(oplan)}, dev, clocks)
+                ovalue = n / (statistics.mean(oms) * 1e-3)
                 others.append({"path": drf.drf_plan_path(oplan), "specialized": False,
-                               "ms_per_step": statistics.mean(oms), "value": n / (statistics.mean(oms) * 1e-3),
-                               "stages_ms": ostages, "roofline": oroof})
+                               "ms_per_step": statistics.mean(oms), "value": ovalue,
+                               "stages_ms": ostages, "roofline": oroof,
+                               "materialize_scan_equivalent": materialize_scan_fractions(
+                                   ovalue, info["sort_bits"], _peaks()[0])})
                 drf.drf_plan_destroy(oplan)
                 drf.drf_ctx_destroy(octx)
             except drf.DrfError as e:
@@ -487,6 +505,11 @@ def run_ours(args, rank, world):
                              "table alone (2.1 GB) is larger than L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
+            # the whole step (and the end-to-end call) against the HBM time a
+            # materialize-and-scan checker needs for the same tuples
+            "materialize_scan_equivalent": {
+                "device": materialize_scan_fractions(world * n / (ms * 1e-3), info["sort_bits"], _peaks()[0]),
+                "e2e": materialize_scan_fractions(n / e2e_s, info["sort_bits"], _peaks()[0])},
             "stages_ms": stages,
             "stages_note": (f"per-stage device times from {prof_steps} further steps of the same configuration "
                             f"with an event node between kernels (mean {statistics.mean(pms):.4f} ms per step "

@@ -1,13 +1,21 @@
 // Test helper (host only, no GPU): lowers one protocol, packs it with the
-// range pass planned whatever its size, and writes the sort-path keys of its
-// range pieces -- k0 + o * d for each piece's threads o -- so that a CPU test
-// can compare them with the oracle's accesses.
+// range pass planned whatever its size, and writes what the range pass was
+// planned to do, so that a CPU test can compare it with the oracle's
+// accesses.
 //
-//   range_keys_dump OUT NTHREADS BYTECODE_HEX CELLS...
+//   range_keys_dump [--pieces] OUT NTHREADS BYTECODE_HEX CELLS...
 //
-// OUT: 8 little-endian uint64 (proto, phase, loc, index and tid bits of the
-// key layout, the protocol's access instructions, those of them in the range
-// pass, the number of keys), then the keys.
+// Keys (default): 8 little-endian uint64 (proto, phase, loc, index and tid
+// bits of the key layout, the protocol's access instructions, those of them
+// in the range pass, the number of keys), then the sort-path keys of the
+// range pieces, k0 + o * d for each piece's threads o.
+//
+// --pieces: uint64 header (records per task, tab_off, cells_sum, tab_phases,
+// nlocs, the number of task entries, of merged pieces, the access
+// instructions and those in the range pass), the nlocs array offsets within a
+// phase row (cbase), then the task entries (task, p0, p1, win: 4 uint32 each)
+// and the merged pieces (t0, lenf, l0, step: 4 x 32 bits each), as the range
+// kernel receives them.
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -21,8 +29,13 @@ using namespace drf;
 
 int main(int argc, char **argv)
 {
+    const bool pieces = argc > 1 && std::string(argv[1]) == "--pieces";
+    if (pieces) {
+        argv++;
+        argc--;
+    }
     if (argc < 4) {
-        std::fprintf(stderr, "usage: %s OUT NTHREADS BYTECODE_HEX CELLS...\n", argv[0]);
+        std::fprintf(stderr, "usage: %s [--pieces] OUT NTHREADS BYTECODE_HEX CELLS...\n", argv[0]);
         return 2;
     }
     const uint32_t nthreads = (uint32_t)std::strtoul(argv[2], nullptr, 10);
@@ -50,6 +63,19 @@ int main(int argc, char **argv)
             acc++;
             racc += (in.a & AF_RANGE) ? 1 : 0;
         }
+    if (pieces) {
+        const DevProto &d = bh.protos.at(0);
+        std::vector<uint64_t> hdr = {kRangeRecs, d.tab_off, d.cells_sum, d.tab_phases, d.nlocs,
+                                     bh.rtask.size(), bh.rpiece.size(), acc, racc};
+        for (uint32_t l = 0; l < d.nlocs; l++) hdr.push_back(bh.cbase[d.cells_off + l]);
+        FILE *f = std::fopen(argv[1], "wb");
+        bool ok = f && std::fwrite(hdr.data(), 8, hdr.size(), f) == hdr.size();
+        ok = ok && (bh.rtask.empty() || std::fwrite(bh.rtask.data(), sizeof(RTask), bh.rtask.size(), f) == bh.rtask.size());
+        ok = ok && (bh.rpiece.empty() ||
+                    std::fwrite(bh.rpiece.data(), sizeof(RPiece), bh.rpiece.size(), f) == bh.rpiece.size());
+        if (f) std::fclose(f);
+        return ok ? 0 : 1;
+    }
     std::vector<uint64_t> out = {bh.L.proto_bits, bh.L.phase_bits, bh.L.loc_bits, bh.L.idx_bits, bh.L.tid_bits,
                                  acc, racc, bh.nrkeys};
     for (const RKeys &k : bh.wkeys) {

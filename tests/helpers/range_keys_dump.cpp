@@ -5,10 +5,11 @@
 //
 //   range_keys_dump [--pieces] OUT NTHREADS BYTECODE_HEX CELLS...
 //
-// Keys (default): 8 little-endian uint64 (proto, phase, loc, index and tid
+// Keys (default): 9 little-endian uint64 (proto, phase, loc, index and tid
 // bits of the key layout, the protocol's access instructions, those of them
-// in the range pass, the number of keys), then the sort-path keys of the
-// range pieces, k0 + o * d for each piece's threads o.
+// in the range pass, the access tuples those make as counted on the host,
+// the number of keys), then the sort-path keys of the range pieces,
+// k0 + o * d for each piece's threads o.
 //
 // --pieces: uint64 header (records per task, tab_off, cells_sum, tab_phases,
 // nlocs, the number of task entries, of merged pieces, the access
@@ -77,15 +78,16 @@ int main(int argc, char **argv)
         return ok ? 0 : 1;
     }
     std::vector<uint64_t> out = {bh.L.proto_bits, bh.L.phase_bits, bh.L.loc_bits, bh.L.idx_bits, bh.L.tid_bits,
-                                 acc, racc, bh.nrkeys};
+                                 acc, racc, bh.range_tuples, bh.nrkeys};
+    const size_t hdr = out.size();
     for (const RKeys &k : bh.wkeys) {
-        if (k.pre != out.size() - 8) {
+        if (k.pre != out.size() - hdr) {
             std::fprintf(stderr, "piece keys out of order\n");
             return 1;
         }
         for (uint64_t o = 0; o < k.len; o++) out.push_back(k.k0 + o * k.d);
     }
-    if (out.size() - 8 != bh.nrkeys) {
+    if (out.size() - hdr != bh.nrkeys) {
         std::fprintf(stderr, "key count mismatch\n");
         return 1;
     }

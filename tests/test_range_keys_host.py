@@ -48,9 +48,10 @@ def planned_keys(helper, tmp_path, p):
     out = tmp_path / "keys.bin"
     subprocess.run([helper, str(out), str(p.nthreads), bytes(bc).hex(), *map(str, p.cells)], check=True)
     raw = np.fromfile(out, dtype=np.uint64)
-    pb, phb, lb, ib, tb, acc, racc, n = (int(x) for x in raw[:8])
-    keys = raw[8:]
+    pb, phb, lb, ib, tb, acc, racc, rtuples, n = (int(x) for x in raw[:9])
+    keys = raw[9:]
     assert len(keys) == n
+    planned_keys.range_tuples = rtuples
     one = np.uint64(1)
     field = keys >> np.uint64(tb + 1)
     rows = np.stack([
@@ -84,6 +85,8 @@ def test_grid_protocol_range_keys_are_its_accesses(helper, tmp_path, oracle, nth
     want = oracle.tuples(p.text, p.nthreads, p.cells, p.params)
     assert as_set(rows) == as_set(want)
     assert len(rows) < len(want)
+    # the host's count of the range accesses' tuples is every tuple here
+    assert planned_keys.range_tuples == len(want)
 
 
 def test_grid_protocol_planted_write_stays_with_the_interpreter(helper, tmp_path, oracle):
@@ -116,10 +119,12 @@ def test_wrapping_and_tid_free_range_keys(helper, tmp_path, oracle, text, T, cel
     p = protogen.Protocol(text, T, cells, [])
     acc, racc, rows = planned_keys(helper, tmp_path, p)
     assert racc > 0
-    want = as_set(oracle.tuples(p.text, p.nthreads, p.cells, p.params))
+    ref = oracle.tuples(p.text, p.nthreads, p.cells, p.params)
+    want = as_set(ref)
     got = as_set(rows)
     if acc == racc:
         assert got == want
+        assert planned_keys.range_tuples == len(ref)
     else:
         assert got <= want and got
 
@@ -131,12 +136,14 @@ def test_strided_range_keys_are_accesses(helper, tmp_path, oracle, seed):
     accesses, and all of them when every access is a range access."""
     p = protogen.strided_small(seed)
     acc, racc, rows = planned_keys(helper, tmp_path, p)
-    want = as_set(oracle.tuples(p.text, p.nthreads, p.cells, p.params))
+    ref = oracle.tuples(p.text, p.nthreads, p.cells, p.params)
+    want = as_set(ref)
     got = as_set(rows)
     if racc == 0:
         assert not got
     elif acc == racc:
         assert got == want
+        assert planned_keys.range_tuples == len(ref)
     else:
         assert got <= want and got
 

@@ -139,6 +139,9 @@ typedef struct {
  * Definition 1 exactly and return identical results:
  *   sort path   -- one 64-bit key per access (phase, array, index, tid, mode),
  *                  radix-sorted on the cell fields, racy segments detected;
+ *                  with the range pieces planned (see DRF_OPT_RANGE_ANY) the
+ *                  range accesses' keys are written from the pieces, one per
+ *                  distinct (thread, offset) (drf_plan_keys);
  *   owner table -- one 32-bit record per (phase, array, index) cell, rows
  *                  up to the static bound on syncs: the first accessor, "a
  *                  second thread accessed it", "it was written"; a cell is
@@ -171,8 +174,9 @@ typedef struct {
  * give the owner table, and forced sort-path contexts, keep the
  * interpreter. */
 #define DRF_OPT_SPECIALIZE     0x10u
-/* The owner table's range pass (drf_plan_specialized) for batches of any
- * size, checked by any entry point.  By default plans and single-protocol
+/* The range pieces for batches of any size, checked by any entry point:
+ * the owner table's range pass (drf_plan_specialized), or on a forced sort
+ * path the range accesses' keys written from the pieces.  By default plans and single-protocol
  * checks take it when its range accesses make 2^22 access tuples or more
  * (below that, planning its work lists, uploading them and the extra kernel
  * cost more than the table pass they relieve; a repeated drf_check of one
